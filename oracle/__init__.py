@@ -1,0 +1,224 @@
+"""FP64 CPU oracle for the mapping path (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  The product package never does, and
+the two share no code.  The oracle itself is ``oracle.cpp`` (plain C++,
+FP64, ``-O2 -ffp-contract=off``); this file compiles it and wraps its C
+interface with ctypes and numpy.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+BV = 512
+
+
+def build(force: bool = False) -> str:
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+                               "-shared", "-o", _LIB, _SRC])
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    L = ctypes.CDLL(_LIB)
+    P, I64, D, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    sig = {
+        "orc_new": ([D, D, I, I, D, D, D], P),
+        "orc_free": ([P], None),
+        "orc_set_bands": ([P, D, D], None),
+        "orc_set_track": ([P, P, I64], None),
+        "orc_integrate": ([P, P, P, P, P, I64, P, I], I),
+        "orc_stats": ([P, P], None),
+        "orc_num_alloc": ([P], I64),
+        "orc_get_alloc": ([P, P, I64], I64),
+        "orc_get_touched": ([P, P, I64], I64),
+        "orc_read_block": ([P, P, P, P, P, P, P, P], I),
+        "orc_write_block": ([P, P, P, P, P], I),
+        "orc_mesh_build": ([P, I, P, I64, P], P),
+        "orc_mesh_fetch": ([P, P, P, P, P, P, P, P, P], None),
+        "orc_mesh_free": ([P], None),
+        "orc_edge_key": ([I64, I64, I64, I], I64),
+        "orc_query": ([P, P, I64, P, P, P], None),
+        "orc_pose_terms": ([P, P, I64, P, P, P, P, P], I64),
+        "orc_align": ([P, P, I64, P, I, P], I),
+        "orc_se3_exp": ([P, P, P], None),
+        "orc_palette": ([I, P], None),
+        "orc_point_blocks": ([P, P, P, P, I64], I64),
+        "orc_point_band": ([P, P, P, P, P], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _p(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+STAT_NAMES = ("valid_points", "pixel_points", "ambiguous_points", "touched_blocks", "new_blocks",
+              "voxels_updated", "voxels_semantic", "voxels_seen", "taint_events")
+
+
+class OracleMap:
+    """Plain FP64 mapper: one std::unordered_map of 8^3-voxel blocks."""
+
+    def __init__(self, voxel_size, truncation, n_classes=20, weight_mode=0, p_hit=0.9,
+                 logp_floor=-30.0, lik_floor=1e-6):
+        self.L = _load()
+        self.C = n_classes
+        self.h = self.L.orc_new(voxel_size, truncation, n_classes, weight_mode, p_hit, logp_floor, lik_floor)
+        self.voxel_size = voxel_size
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.L.orc_free(self.h)
+            self.h = None
+
+    def set_bands(self, delta_px, eps_psi):
+        self.L.orc_set_bands(self.h, delta_px, eps_psi)
+
+    def set_track(self, coords):
+        c = np.ascontiguousarray(coords, np.int32).reshape(-1, 3)
+        self.L.orc_set_track(self.h, _p(c), len(c))
+
+    def integrate(self, lidar, points, T, labels=None, probs=None, nthreads=0):
+        lid = np.array([lidar.H, lidar.W, lidar.fov_up, lidar.fov_down, lidar.r_min, lidar.r_max], np.float64)
+        pts = np.ascontiguousarray(points, np.float32)
+        lab = None if labels is None else np.ascontiguousarray(labels, np.int32)
+        pr = None if probs is None else np.ascontiguousarray(probs, np.float32)
+        T = np.ascontiguousarray(T, np.float64)
+        rc = self.L.orc_integrate(self.h, _p(lid), _p(pts), _p(lab), _p(pr), len(pts), _p(T), nthreads)
+        assert rc == 0
+        return self.stats()
+
+    def stats(self):
+        out = np.zeros(9, np.int64)
+        self.L.orc_stats(self.h, _p(out))
+        return dict(zip(STAT_NAMES, out.tolist()))
+
+    def alloc_blocks(self):
+        n = self.L.orc_num_alloc(self.h)
+        out = np.zeros((max(n, 1), 3), np.int32)
+        self.L.orc_get_alloc(self.h, _p(out), n)
+        return out[:n]
+
+    def touched_blocks(self):
+        n = self.L.orc_get_touched(self.h, None, 0)
+        out = np.zeros((max(n, 1), 3), np.int32)
+        self.L.orc_get_touched(self.h, _p(out), n)
+        return out[:n]
+
+    def read_block(self, coord):
+        c = np.ascontiguousarray(coord, np.int32)
+        D = np.zeros(BV)
+        W = np.zeros(BV)
+        lp = np.zeros((self.C, BV))
+        taint = np.zeros(BV, np.uint8)
+        lab = np.zeros(BV, np.int32)
+        gap = np.zeros(BV)
+        rc = self.L.orc_read_block(self.h, _p(c), _p(D), _p(W), _p(lp), _p(taint), _p(lab), _p(gap))
+        if rc != 0:
+            return None
+        return dict(D=D, W=W, logP=lp, taint=taint, label=lab, gap=gap)
+
+    def write_block(self, coord, D, W, logP=None):
+        c = np.ascontiguousarray(coord, np.int32)
+        D = np.ascontiguousarray(D, np.float64)
+        W = np.ascontiguousarray(W, np.float64)
+        lp = None if logP is None else np.ascontiguousarray(logP, np.float64)
+        self.L.orc_write_block(self.h, _p(c), _p(D), _p(W), _p(lp))
+
+    def mesh(self, blocks=None):
+        counts = np.zeros(2, np.int64)
+        if blocks is None:
+            hm = self.L.orc_mesh_build(self.h, 0, None, 0, _p(counts))
+        else:
+            b = np.ascontiguousarray(blocks, np.int32).reshape(-1, 3)
+            hm = self.L.orc_mesh_build(self.h, 1, _p(b), len(b), _p(counts))
+        nv, nt = int(counts[0]), int(counts[1])
+        out = dict(vkey=np.zeros(nv, np.int64), vpos=np.zeros((nv, 3)), vlab=np.zeros(nv, np.int32),
+                   vgap=np.zeros(nv), vtaint=np.zeros(nv, np.uint8), tkeys=np.zeros((nt, 3), np.int64),
+                   tanchor=np.zeros((nt, 3), np.int32), ttaint=np.zeros(nt, np.uint8))
+        if nv or nt:
+            self.L.orc_mesh_fetch(hm, *(_p(out[k]) if out[k].size else None for k in
+                                       ("vkey", "vpos", "vlab", "vgap", "vtaint", "tkeys", "tanchor", "ttaint")))
+        self.L.orc_mesh_free(hm)
+        return out
+
+    def query(self, xyz):
+        x = np.ascontiguousarray(xyz, np.float64).reshape(-1, 3)
+        sdf = np.zeros(len(x))
+        valid = np.zeros(len(x), np.uint8)
+        grad = np.zeros((len(x), 3))
+        self.L.orc_query(self.h, _p(x), len(x), _p(sdf), _p(valid), _p(grad))
+        return sdf, valid.astype(bool), grad
+
+    def pose_terms(self, points, T):
+        pts = np.ascontiguousarray(points, np.float32)
+        T = np.ascontiguousarray(T, np.float64)
+        loss = np.zeros(1)
+        dL = np.zeros(6)
+        H = np.zeros((6, 6))
+        g = np.zeros(6)
+        nv = self.L.orc_pose_terms(self.h, _p(pts), len(pts), _p(T), _p(loss), _p(dL), _p(H), _p(g))
+        return dict(loss=float(loss[0]), dL=dL, H=H, g=g, n_valid=int(nv))
+
+    def align(self, points, T0, iters=20):
+        pts = np.ascontiguousarray(points, np.float32)
+        T0 = np.ascontiguousarray(T0, np.float64)
+        out = np.zeros((4, 4))
+        rc = self.L.orc_align(self.h, _p(pts), len(pts), _p(T0), iters, _p(out))
+        assert rc == 0
+        return out
+
+    def point_blocks(self, pt, T):
+        p = np.ascontiguousarray(pt, np.float32)
+        T = np.ascontiguousarray(T, np.float64)
+        out = np.zeros((64, 3), np.int32)
+        n = self.L.orc_point_blocks(self.h, _p(p), _p(T), _p(out), 64)
+        return out[:n]
+
+    def point_band(self, pt, T):
+        p = np.ascontiguousarray(pt, np.float32)
+        T = np.ascontiguousarray(T, np.float64)
+        e0 = np.zeros(3, np.float32)
+        e1 = np.zeros(3, np.float32)
+        self.L.orc_point_band(self.h, _p(p), _p(T), _p(e0), _p(e1))
+        return e0, e1
+
+
+def edge_key(x, y, z, axis) -> int:
+    return int(_load().orc_edge_key(int(x), int(y), int(z), int(axis)))
+
+
+def se3_exp(xi):
+    xi = np.ascontiguousarray(xi, np.float64)
+    R = np.zeros(9)
+    t = np.zeros(3)
+    _load().orc_se3_exp(_p(xi), _p(R), _p(t))
+    T = np.eye(4)
+    T[:3, :3] = R.reshape(3, 3)
+    T[:3, 3] = t
+    return T
+
+
+def palette(C):
+    out = np.zeros((C, 3), np.uint8)
+    _load().orc_palette(C, _p(out))
+    return out

@@ -1,0 +1,979 @@
+/*
+ * FP64 CPU oracle for the per-frame metric-semantic mapping path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the tests, the package smoke check and the
+ * benchmark's CPU-baseline leg may.  It shares no code, header, table or
+ * constant generator with the CUDA path.
+ *
+ * What it follows (Liu et al., "Real-Time Metric-Semantic Mapping for
+ * Autonomous Navigation in Outdoor Environments", 2024):
+ *   - Sec. III-C.1, range-image equation: u = (pi - atan2(y, x)) / dphi,
+ *     v = (acos(z / r) - theta0) / dtheta.
+ *   - Sec. III-C.2: voxel centre x_i = nu * v_i; two-level storage, a hash of
+ *     8x8x8-voxel blocks; projective distance psi along the ray, negative
+ *     behind the surface; linear weight W_i = (psi + tau) / (2 tau); the
+ *     running-average update of D and W with truncation Gamma(d, tau).
+ *   - Sec. III-C.3, Eq. (bayesian_filter): uniform prior per new voxel and
+ *     the recursive Bayesian product with the per-pixel class likelihood,
+ *     normalised by Z; mesh by marching cubes with each vertex labelled by
+ *     its most probable class.
+ *
+ * Readings where the paper is silent (each is also listed in the design
+ * notes): nearest point wins a pixel; blocks are allocated along
+ * [p - tau d, p + tau d] of every valid point; voxels of the touched
+ * blocks only are updated; psi < -tau is skipped; the linear weight is
+ * clamped to [0, 1]; the semantic update is gated to |psi| <= tau; the
+ * hard-label likelihood is p_hit / (1 - p_hit)/(C - 1); log-probabilities
+ * are floored; marching-cubes faces with four crossings separate the inside
+ * corners; a cube needs all 8 corners observed (W > 0).
+ *
+ * Precision: every value is FP64.  Two integer decisions are taken in the
+ * precision the GPU takes them in, as both sides of a parity check must:
+ * the per-point range used for validity and for the nearest-point winner
+ * (FP32 norm), and the block-allocation band endpoints (FP32 recipe below).
+ * Pixel choices are FP64; a voxel projection within delta_px of a pixel
+ * boundary, or a psi within eps_psi of +-tau, marks the voxel "tainted"
+ * (the FP32 GPU may legitimately decide the other way), sticky for the
+ * rest of the run, so that parity tests can compare untainted voxels
+ * strictly.
+ */
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+constexpr int BS = 8;            // voxels per block side (Sec. III-C.2)
+constexpr int BV = BS * BS * BS;
+constexpr double PI = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// integer helpers
+// ---------------------------------------------------------------------------
+inline int64_t floordiv(int64_t a, int64_t b) {
+    int64_t q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+struct I3 {
+    int64_t x, y, z;
+    bool operator==(const I3 &o) const { return x == o.x && y == o.y && z == o.z; }
+    bool operator<(const I3 &o) const {
+        if (x != o.x) return x < o.x;
+        if (y != o.y) return y < o.y;
+        return z < o.z;
+    }
+};
+struct I3Hash {
+    size_t operator()(const I3 &k) const {
+        uint64_t h = (uint64_t)k.x * 0x9E3779B97F4A7C15ULL;
+        h ^= (uint64_t)k.y * 0xC2B2AE3D27D4EB4FULL + (h << 6) + (h >> 2);
+        h ^= (uint64_t)k.z * 0x165667B19E3779F9ULL + (h << 6) + (h >> 2);
+        return (size_t)h;
+    }
+};
+
+// Global key of a lattice edge: its lower end voxel and its axis.  The
+// order of keys is lexicographic in (z, y, x, axis); this order decides
+// which loop vertex starts a triangle fan.
+inline int64_t edge_key(int64_t x, int64_t y, int64_t z, int axis) {
+    const int64_t bias = (int64_t)1 << 19;
+    return ((((z + bias) << 20 | (y + bias)) << 20 | (x + bias)) << 2) | axis;
+}
+
+// ---------------------------------------------------------------------------
+// map state
+// ---------------------------------------------------------------------------
+struct Block {
+    std::vector<double> D, W, logP;  // D[512], W[512], logP[C][512] (class-major)
+    std::vector<uint8_t> taint;      // bit 0: distance/weight, bit 1: semantics
+};
+
+struct Lidar {
+    int H, W;
+    double fov_up, fov_down, r_min, r_max;
+    double dphi, dtheta, theta0;
+};
+
+struct Stats {
+    int64_t valid_points = 0, pixel_points = 0, ambiguous_points = 0;
+    int64_t touched_blocks = 0, new_blocks = 0;
+    int64_t voxels_updated = 0, voxels_semantic = 0, voxels_seen = 0;
+    int64_t taint_events = 0;
+};
+
+struct Map {
+    double nu, tau;
+    int C;
+    int weight_mode;                 // 0: linear weight (Sec. III-C.2), 1: constant 1
+    double p_hit, logp_floor, lik_floor;
+    double delta_px = 1e-3;          // pixel-boundary ambiguity band, in pixels
+    double eps_psi;                  // psi ambiguity band around +-tau, metres
+    std::unordered_map<I3, Block, I3Hash> blocks;
+    bool track = false;              // keep voxel data only for track_keys
+    std::unordered_set<I3, I3Hash> track_keys;
+    std::unordered_set<I3, I3Hash> alloc;   // every allocated block (keys)
+    std::vector<I3> touched;                // U_k of the last frame
+    Stats st;
+    int64_t frame = 0;
+};
+
+Block new_block(int C) {
+    Block b;
+    b.D.assign(BV, 0.0);
+    b.W.assign(BV, 0.0);
+    // uniform prior over the classes for every new voxel (Sec. III-C.3)
+    b.logP.assign((size_t)C * BV, -std::log((double)C));
+    b.taint.assign(BV, 0);
+    return b;
+}
+
+inline int vidx(int lx, int ly, int lz) { return lx + BS * (ly + BS * lz); }
+
+// ---------------------------------------------------------------------------
+// FP32 decisions shared in precision (not in code) with the GPU path
+// ---------------------------------------------------------------------------
+// Range of a LiDAR-frame point as the GPU computes it: ((x*x + y*y) + z*z),
+// then a correctly rounded square root, all in IEEE single precision.
+inline float range_f32(float x, float y, float z) {
+    float s = x * x;
+    s = s + y * y;
+    s = s + z * z;
+    return std::sqrt(s);
+}
+
+struct BandConst {
+    float Rv[9];   // R / nu, row-major, rounded once from FP64
+    float tv[3];   // t / nu + 1/2, rounded once from FP64
+    float tau;
+};
+
+/*
+ * Band endpoints of one point in "voxel units plus one half" (so voxel v
+ * occupies [v, v + 1) and block b occupies [8 b, 8 b + 8) on every axis):
+ *   q = tau / l, f0 = max(0, 1 - q), f1 = 1 + q,
+ *   s = (Rv[k0] x0 + Rv[k1] x1) + Rv[k2] x2,   e0 = tv + s f0,  e1 = tv + s f1.
+ * Every operation is one IEEE single-precision operation, in this order.
+ */
+inline void band_endpoints(const BandConst &bc, float x0, float x1, float x2, float l, float e0[3], float e1[3]) {
+    float q = bc.tau / l;
+    float f0 = 1.0f - q;
+    if (f0 < 0.0f) f0 = 0.0f;
+    float f1 = 1.0f + q;
+    for (int k = 0; k < 3; ++k) {
+        float s = bc.Rv[3 * k] * x0;
+        s = s + bc.Rv[3 * k + 1] * x1;
+        s = s + bc.Rv[3 * k + 2] * x2;
+        float a = s * f0;
+        float b = s * f1;
+        e0[k] = bc.tv[k] + a;
+        e1[k] = bc.tv[k] + b;
+    }
+}
+
+/*
+ * Blocks met by the segment e(t) = e0 + t (e1 - e0), t in [0, 1], against
+ * half-open blocks [8b, 8b+8).  The path starts in the block of e0, ends in
+ * the block of e1 and, between them, crosses one block plane per event; the
+ * events are ordered by the crossing parameter t* = (P - e0) / (e1 - e0)
+ * (single precision).  A plane crossed upward is entered at t* itself; a
+ * plane crossed downward is left only after t*; events with equal t* and
+ * equal kind apply together.
+ */
+void band_blocks(const float e0[3], const float e1[3], std::vector<I3> &out) {
+    struct Ev { float t; int phase; int axis; int step; };
+    Ev ev[64];
+    int nev = 0;
+    int64_t cur[3];
+    for (int k = 0; k < 3; ++k) {
+        int64_t b0 = (int64_t)std::floor(e0[k] / 8.0f);
+        int64_t b1 = (int64_t)std::floor(e1[k] / 8.0f);
+        cur[k] = b0;
+        float d = e1[k] - e0[k];
+        if (b1 > b0) {
+            for (int64_t b = b0 + 1; b <= b1 && nev < 64; ++b) {
+                float P = (float)(8 * b);
+                float num = P - e0[k];
+                ev[nev++] = {num / d, 0, k, +1};
+            }
+        } else if (b1 < b0) {
+            for (int64_t b = b0; b > b1 && nev < 64; --b) {
+                float P = (float)(8 * b);
+                float num = P - e0[k];
+                ev[nev++] = {num / d, 1, k, -1};
+            }
+        }
+    }
+    std::sort(ev, ev + nev, [](const Ev &a, const Ev &b) {
+        if (a.t != b.t) return a.t < b.t;
+        return a.phase < b.phase;
+    });
+    out.push_back({cur[0], cur[1], cur[2]});
+    int i = 0;
+    while (i < nev) {
+        int j = i;
+        while (j < nev && ev[j].t == ev[i].t && ev[j].phase == ev[i].phase) {
+            cur[ev[j].axis] += ev[j].step;
+            ++j;
+        }
+        out.push_back({cur[0], cur[1], cur[2]});
+        i = j;
+    }
+}
+
+BandConst band_const(const Map &m, const double R[9], const double t[3]) {
+    BandConst bc;
+    for (int i = 0; i < 9; ++i) bc.Rv[i] = (float)(R[i] / m.nu);
+    for (int k = 0; k < 3; ++k) bc.tv[k] = (float)(t[k] / m.nu + 0.5);
+    bc.tau = (float)m.tau;
+    return bc;
+}
+
+inline double dist_to_int(double a) { return std::fabs(a - std::floor(a + 0.5)); }
+
+// ---------------------------------------------------------------------------
+// one frame
+// ---------------------------------------------------------------------------
+int integrate(Map &m, const Lidar &L, const float *pts, const int32_t *labels, const float *probs,
+              int64_t n, const double T[16], int nthreads) {
+    m.st = Stats();
+    const int C = m.C;
+    double R[9], t[3];
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) R[3 * r + c] = T[4 * r + c];
+        t[r] = T[4 * r + 3];
+    }
+    const int64_t NP = (int64_t)L.H * L.W;
+
+    // --- measurement preprocessing: range image (Sec. III-C.1) -------------
+    std::vector<int64_t> win(NP, -1);
+    std::vector<float> win_l(NP, 0.0f);
+    std::vector<float> lr(n);
+    std::vector<uint8_t> valid(n, 0);
+    const float rmin_f = (float)L.r_min, rmax_f = (float)L.r_max;
+    for (int64_t i = 0; i < n; ++i) {
+        float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+        if (!(std::isfinite(x) && std::isfinite(y) && std::isfinite(z))) continue;
+        float l = range_f32(x, y, z);
+        lr[i] = l;
+        if (!(l >= rmin_f && l <= rmax_f)) continue;
+        valid[i] = 1;
+        m.st.valid_points++;
+        double X = x, Y = y, Z = z;
+        double r = std::sqrt(X * X + Y * Y + Z * Z);
+        double uc = (PI - std::atan2(Y, X)) / L.dphi;
+        double vc = (std::acos(Z / r) - L.theta0) / L.dtheta;
+        if (dist_to_int(uc + 0.5) < m.delta_px || dist_to_int(vc + 0.5) < m.delta_px) m.st.ambiguous_points++;
+        int64_t u = (int64_t)std::floor(uc + 0.5);
+        int64_t v = (int64_t)std::floor(vc + 0.5);
+        u = ((u % L.W) + L.W) % L.W;
+        if (v < 0 || v >= L.H) continue;
+        m.st.pixel_points++;
+        int64_t p = v * L.W + u;
+        // nearest point wins the pixel; equal ranges go to the lower index
+        if (win[p] < 0 || l < win_l[p] || (l == win_l[p] && i < win[p])) {
+            win[p] = i;
+            win_l[p] = l;
+        }
+    }
+    // per-pixel log-likelihood of each class (Eq. bayesian_filter's P(O = l | I_k))
+    std::vector<double> logL;
+    std::vector<uint8_t> has_sem(NP, 0);
+    logL.assign((size_t)NP * C, 0.0);
+    for (int64_t p = 0; p < NP; ++p) {
+        int64_t i = win[p];
+        if (i < 0) continue;
+        double *row = &logL[(size_t)p * C];
+        if (probs) {
+            for (int c = 0; c < C; ++c) row[c] = std::log(std::max((double)probs[(size_t)i * C + c], m.lik_floor));
+            has_sem[p] = 1;
+        } else if (labels && labels[i] >= 0 && labels[i] < C) {
+            double lo = std::log((1.0 - m.p_hit) / (C - 1)), hi = std::log(m.p_hit);
+            for (int c = 0; c < C; ++c) row[c] = (c == labels[i]) ? hi : lo;
+            has_sem[p] = 1;
+        }
+    }
+
+    // --- block allocation along each point's truncation band ------------------
+    BandConst bc = band_const(m, R, t);
+    std::unordered_set<I3, I3Hash> touched;
+    std::vector<I3> tmp;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!valid[i]) continue;
+        float e0[3], e1[3];
+        band_endpoints(bc, pts[3 * i], pts[3 * i + 1], pts[3 * i + 2], lr[i], e0, e1);
+        tmp.clear();
+        band_blocks(e0, e1, tmp);
+        for (const I3 &b : tmp) touched.insert(b);
+    }
+    m.touched.assign(touched.begin(), touched.end());
+    std::sort(m.touched.begin(), m.touched.end());
+    m.st.touched_blocks = (int64_t)m.touched.size();
+    std::vector<Block *> work;
+    std::vector<I3> work_key;
+    for (const I3 &b : m.touched) {
+        if (m.alloc.insert(b).second) m.st.new_blocks++;
+        if (m.track && !m.track_keys.count(b)) continue;
+        auto it = m.blocks.find(b);
+        if (it == m.blocks.end()) it = m.blocks.emplace(b, new_block(C)).first;
+        work.push_back(&it->second);
+        work_key.push_back(b);
+    }
+
+    // --- projective TSDF + Bayesian semantic update, per voxel ----------------
+    const double nu = m.nu, tau = m.tau;
+    int64_t n_upd = 0, n_sem = 0, n_seen = 0, n_taint = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : n_upd, n_sem, n_seen, n_taint)
+#endif
+    for (int64_t wi = 0; wi < (int64_t)work.size(); ++wi) {
+        Block &blk = *work[wi];
+        const I3 bk = work_key[wi];
+        std::vector<double> a(C);
+        for (int lz = 0; lz < BS; ++lz)
+            for (int ly = 0; ly < BS; ++ly)
+                for (int lx = 0; lx < BS; ++lx) {
+                    const int vi = vidx(lx, ly, lz);
+                    // voxel centre x_i = nu * v_i (Sec. III-C.2)
+                    double xw[3] = {nu * (double)(BS * bk.x + lx), nu * (double)(BS * bk.y + ly),
+                                    nu * (double)(BS * bk.z + lz)};
+                    double d[3] = {xw[0] - t[0], xw[1] - t[1], xw[2] - t[2]};
+                    double xl[3];
+                    for (int k = 0; k < 3; ++k) xl[k] = R[k] * d[0] + R[3 + k] * d[1] + R[6 + k] * d[2];
+                    double rho = std::sqrt(xl[0] * xl[0] + xl[1] * xl[1] + xl[2] * xl[2]);
+                    if (!(rho > 0.0)) continue;
+                    n_seen++;
+                    double uc = (PI - std::atan2(xl[1], xl[0])) / L.dphi;
+                    double vc = (std::acos(xl[2] / rho) - L.theta0) / L.dtheta;
+                    if (dist_to_int(uc + 0.5) < m.delta_px || dist_to_int(vc + 0.5) < m.delta_px) {
+                        blk.taint[vi] |= 3;
+                        n_taint++;
+                    }
+                    int64_t u = (int64_t)std::floor(uc + 0.5);
+                    int64_t v = (int64_t)std::floor(vc + 0.5);
+                    u = ((u % L.W) + L.W) % L.W;
+                    if (v < 0 || v >= L.H) continue;
+                    int64_t p = v * L.W + u;
+                    int64_t wpt = win[p];
+                    if (wpt < 0) continue;
+                    double P0 = pts[3 * wpt], P1 = pts[3 * wpt + 1], P2 = pts[3 * wpt + 2];
+                    double r = std::sqrt(P0 * P0 + P1 * P1 + P2 * P2);
+                    // projective signed distance along the ray: > 0 in front of the surface
+                    double psi = r - rho;
+                    if (std::fabs(psi + tau) < m.eps_psi) { blk.taint[vi] |= 3; n_taint++; }
+                    if (std::fabs(psi - tau) < m.eps_psi) { blk.taint[vi] |= 2; n_taint++; }
+                    if (psi < -tau) continue;
+                    double w;
+                    if (m.weight_mode == 0) {
+                        // linear weight (psi + tau) / (2 tau), clamped to [0, 1]
+                        w = (psi + tau) / (2.0 * tau);
+                        if (w > 1.0) w = 1.0;
+                        if (w < 0.0) w = 0.0;
+                    } else {
+                        w = 1.0;
+                    }
+                    if (!(w > 0.0)) continue;
+                    // truncation Gamma(d, tau): min(d, tau) for d >= 0, max(d, -tau) otherwise
+                    double sdf = psi >= 0.0 ? std::min(psi, tau) : std::max(psi, -tau);
+                    double Wo = blk.W[vi];
+                    blk.D[vi] = (Wo * blk.D[vi] + w * sdf) / (Wo + w);
+                    blk.W[vi] = Wo + w;
+                    n_upd++;
+                    if (std::fabs(psi) <= tau && has_sem[p]) {
+                        // recursive Bayesian update in log space, normalised by Z
+                        const double *lrow = &logL[(size_t)p * C];
+                        double mx = -INFINITY;
+                        for (int c = 0; c < C; ++c) {
+                            a[c] = blk.logP[(size_t)c * BV + vi] + lrow[c];
+                            mx = std::max(mx, a[c]);
+                        }
+                        double s = 0.0;
+                        for (int c = 0; c < C; ++c) s += std::exp(a[c] - mx);
+                        double lse = mx + std::log(s);
+                        for (int c = 0; c < C; ++c)
+                            blk.logP[(size_t)c * BV + vi] = std::max(a[c] - lse, m.logp_floor);
+                        n_sem++;
+                    }
+                }
+    }
+    m.st.voxels_updated = n_upd;
+    m.st.voxels_semantic = n_sem;
+    m.st.voxels_seen = n_seen;
+    m.st.taint_events = n_taint;
+    m.frame++;
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// voxel access
+// ---------------------------------------------------------------------------
+struct VoxRef {
+    const Block *b = nullptr;
+    int vi = 0;
+};
+
+VoxRef voxel(const Map &m, int64_t x, int64_t y, int64_t z) {
+    VoxRef r;
+    I3 k{floordiv(x, BS), floordiv(y, BS), floordiv(z, BS)};
+    auto it = m.blocks.find(k);
+    if (it == m.blocks.end()) return r;
+    r.b = &it->second;
+    r.vi = vidx((int)(x - BS * k.x), (int)(y - BS * k.y), (int)(z - BS * k.z));
+    return r;
+}
+
+// most probable class, lowest index on exact ties; gap to the runner-up
+int argmax_label(const Map &m, const Block &b, int vi, double *gap) {
+    int best = 0;
+    double bv = b.logP[vi], second = -INFINITY;
+    for (int c = 1; c < m.C; ++c) {
+        double v = b.logP[(size_t)c * BV + vi];
+        if (v > bv) { second = bv; bv = v; best = c; }
+        else if (v > second) second = v;
+    }
+    if (gap) *gap = m.C > 1 ? bv - second : INFINITY;
+    return best;
+}
+
+// ---------------------------------------------------------------------------
+// marching cubes by face walk (no case table)
+// ---------------------------------------------------------------------------
+struct MeshVertex {
+    double pos[3];
+    int label;
+    double gap;
+    uint8_t taint;
+};
+struct MeshTri {
+    int64_t k[3];
+    I3 anchor;      // voxel anchoring the cube (its lowest corner)
+    uint8_t taint;
+};
+struct Mesh {
+    std::map<int64_t, MeshVertex> verts;
+    std::vector<MeshTri> tris;
+};
+
+struct Face { int c[4]; };   // corners counter-clockwise about the outward normal
+
+// Derive the six faces of the unit cube with corners id = dx + 2 dy + 4 dz.
+std::vector<Face> cube_faces() {
+    std::vector<Face> faces;
+    for (int axis = 0; axis < 3; ++axis)
+        for (int side = 0; side < 2; ++side) {
+            int a1 = (axis + 1) % 3, a2 = (axis + 2) % 3;
+            // square (0,0),(1,0),(1,1),(0,1) in the (a1, a2) plane; a1 x a2 = +axis
+            int uv[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
+            Face f;
+            for (int j = 0; j < 4; ++j) {
+                int off[3] = {0, 0, 0};
+                off[axis] = side;
+                off[a1] = uv[j][0];
+                off[a2] = uv[j][1];
+                f.c[j] = off[0] + 2 * off[1] + 4 * off[2];
+            }
+            if (side == 0) std::swap(f.c[1], f.c[3]);   // outward normal is -axis: reverse
+            faces.push_back(f);
+        }
+    return faces;
+}
+
+// Mesh the cubes anchored in block bk; vertices are keyed globally.
+void mesh_block(const Map &m, const I3 &bk, Mesh &out) {
+    static const std::vector<Face> faces = cube_faces();
+    if (m.blocks.find(bk) == m.blocks.end()) return;
+    for (int lz = 0; lz < BS; ++lz)
+        for (int ly = 0; ly < BS; ++ly)
+            for (int lx = 0; lx < BS; ++lx) {
+                int64_t ax = BS * bk.x + lx, ay = BS * bk.y + ly, az = BS * bk.z + lz;
+                double Dc[8];
+                bool in[8];
+                VoxRef vr[8];
+                bool ok = true;
+                uint8_t ctaint = 0;
+                for (int c = 0; c < 8 && ok; ++c) {
+                    vr[c] = voxel(m, ax + (c & 1), ay + ((c >> 1) & 1), az + ((c >> 2) & 1));
+                    if (!vr[c].b || !(vr[c].b->W[vr[c].vi] > 0.0)) { ok = false; break; }
+                    Dc[c] = vr[c].b->D[vr[c].vi];
+                    in[c] = Dc[c] < 0.0;
+                    if (std::fabs(Dc[c]) < 1e-6) ctaint |= 1;
+                    ctaint |= vr[c].b->taint[vr[c].vi] & 1;
+                }
+                // also taint when any corner might be observed on one side only
+                if (!ok) continue;
+                int nin = 0;
+                for (int c = 0; c < 8; ++c) nin += in[c];
+                if (nin == 0 || nin == 8) continue;
+                // vertex of the crossing edge between corners ca, cb (differ in one axis)
+                auto vkey = [&](int ca, int cb) -> int64_t {
+                    int lo = std::min(ca, cb), hi = std::max(ca, cb);
+                    int axis = (hi - lo) == 1 ? 0 : ((hi - lo) == 2 ? 1 : 2);
+                    int64_t k = edge_key(ax + (lo & 1), ay + ((lo >> 1) & 1), az + ((lo >> 2) & 1), axis);
+                    if (!out.verts.count(k)) {
+                        double Da = Dc[lo], Db = Dc[hi];
+                        double tt = Da / (Da - Db);
+                        double base[3] = {(double)(ax + (lo & 1)), (double)(ay + ((lo >> 1) & 1)),
+                                          (double)(az + ((lo >> 2) & 1))};
+                        MeshVertex mv;
+                        for (int q = 0; q < 3; ++q) mv.pos[q] = m.nu * base[q];
+                        mv.pos[axis] = m.nu * (base[axis] + tt);
+                        // label from the endpoint nearer the surface (lower end on ties)
+                        int pick = std::fabs(Db) < std::fabs(Da) ? hi : lo;
+                        mv.label = argmax_label(m, *vr[pick].b, vr[pick].vi, &mv.gap);
+                        mv.taint = (uint8_t)(vr[pick].b->taint[vr[pick].vi] | vr[lo].b->taint[vr[lo].vi] |
+                                             vr[hi].b->taint[vr[hi].vi]);
+                        out.verts.emplace(k, mv);
+                    }
+                    return k;
+                };
+                // directed segments: on each face, each entering edge (out -> in,
+                // counter-clockwise) joins the next leaving edge (in -> out)
+                std::map<int64_t, int64_t> next;
+                for (const Face &f : faces) {
+                    for (int j = 0; j < 4; ++j) {
+                        int ca = f.c[j], cb = f.c[(j + 1) % 4];
+                        if (!(!in[ca] && in[cb])) continue;
+                        for (int s = 1; s < 4; ++s) {
+                            int cc = f.c[(j + s) % 4], cd = f.c[(j + s + 1) % 4];
+                            if (in[cc] && !in[cd]) {
+                                next[vkey(ca, cb)] = vkey(cc, cd);
+                                break;
+                            }
+                        }
+                    }
+                }
+                // loops, each fanned from its lowest key
+                std::unordered_set<int64_t> seen;
+                for (auto &kv : next) {
+                    if (seen.count(kv.first)) continue;
+                    std::vector<int64_t> loop;
+                    int64_t cur = kv.first;
+                    while (!seen.count(cur)) {
+                        seen.insert(cur);
+                        loop.push_back(cur);
+                        cur = next.at(cur);
+                    }
+                    auto mn = std::min_element(loop.begin(), loop.end());
+                    std::rotate(loop.begin(), mn, loop.end());
+                    for (size_t q = 1; q + 1 < loop.size(); ++q) {
+                        MeshTri tr;
+                        tr.k[0] = loop[0];
+                        tr.k[1] = loop[q];
+                        tr.k[2] = loop[q + 1];
+                        tr.anchor = {ax, ay, az};
+                        tr.taint = ctaint;
+                        out.tris.push_back(tr);
+                    }
+                }
+            }
+}
+
+// ---------------------------------------------------------------------------
+// trilinear SDF query and its gradients
+// ---------------------------------------------------------------------------
+bool query(const Map &m, const double x[3], double *sdf, double grad[3]) {
+    double g[3], f[3];
+    int64_t v0[3];
+    for (int k = 0; k < 3; ++k) {
+        g[k] = x[k] / m.nu;
+        v0[k] = (int64_t)std::floor(g[k]);
+        f[k] = g[k] - (double)v0[k];
+    }
+    double Dc[8];
+    for (int c = 0; c < 8; ++c) {
+        VoxRef r = voxel(m, v0[0] + (c & 1), v0[1] + ((c >> 1) & 1), v0[2] + ((c >> 2) & 1));
+        if (!r.b || !(r.b->W[r.vi] > 0.0)) {
+            *sdf = NAN;
+            if (grad) grad[0] = grad[1] = grad[2] = 0.0;
+            return false;
+        }
+        Dc[c] = r.b->D[r.vi];
+    }
+    double s = 0.0, dg[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < 8; ++c) {
+        int b[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+        double wk[3], dk[3];
+        for (int k = 0; k < 3; ++k) {
+            wk[k] = b[k] ? f[k] : 1.0 - f[k];
+            dk[k] = b[k] ? 1.0 : -1.0;
+        }
+        s += wk[0] * wk[1] * wk[2] * Dc[c];
+        dg[0] += dk[0] * wk[1] * wk[2] * Dc[c];
+        dg[1] += wk[0] * dk[1] * wk[2] * Dc[c];
+        dg[2] += wk[0] * wk[1] * dk[2] * Dc[c];
+    }
+    *sdf = s;
+    if (grad)
+        for (int k = 0; k < 3; ++k) grad[k] = dg[k] / m.nu;
+    return true;
+}
+
+// SE(3) exponential of (rho, phi): rotation by Rodrigues' formula, translation V(phi) rho.
+void se3_exp(const double xi[6], double R[9], double t[3]) {
+    const double *rho = xi, *phi = xi + 3;
+    double th = std::sqrt(phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2]);
+    double K[9] = {0, -phi[2], phi[1], phi[2], 0, -phi[0], -phi[1], phi[0], 0};
+    double K2[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s += K[3 * i + k] * K[3 * k + j];
+            K2[3 * i + j] = s;
+        }
+    double A, Bc, Cc;
+    if (th < 1e-8) {
+        A = 1.0 - th * th / 6.0;
+        Bc = 0.5 - th * th / 24.0;
+        Cc = 1.0 / 6.0 - th * th / 120.0;
+    } else {
+        A = std::sin(th) / th;
+        Bc = (1.0 - std::cos(th)) / (th * th);
+        Cc = (th - std::sin(th)) / (th * th * th);
+    }
+    double V[9];
+    for (int i = 0; i < 9; ++i) {
+        double I = (i % 4 == 0) ? 1.0 : 0.0;
+        R[i] = I + A * K[i] + Bc * K2[i];
+        V[i] = I + Bc * K[i] + Cc * K2[i];
+    }
+    for (int i = 0; i < 3; ++i) t[i] = V[3 * i] * rho[0] + V[3 * i + 1] * rho[1] + V[3 * i + 2] * rho[2];
+}
+
+}  // namespace
+
+// ===========================================================================
+// C interface (ctypes)
+// ===========================================================================
+extern "C" {
+
+void *orc_new(double voxel_size, double truncation, int n_classes, int weight_mode, double p_hit,
+              double logp_floor, double lik_floor) {
+    Map *m = new Map();
+    m->nu = voxel_size;
+    m->tau = truncation;
+    m->C = n_classes;
+    m->weight_mode = weight_mode;
+    m->p_hit = p_hit;
+    m->logp_floor = logp_floor;
+    m->lik_floor = lik_floor;
+    m->eps_psi = 1e-5 * voxel_size;
+    return m;
+}
+
+void orc_free(void *h) { delete (Map *)h; }
+
+void orc_set_bands(void *h, double delta_px, double eps_psi) {
+    Map *m = (Map *)h;
+    m->delta_px = delta_px;
+    m->eps_psi = eps_psi;
+}
+
+// Keep voxel data only for the listed blocks; allocation is still tracked for all.
+void orc_set_track(void *h, const int32_t *coords, int64_t n) {
+    Map *m = (Map *)h;
+    m->track = true;
+    m->track_keys.clear();
+    for (int64_t i = 0; i < n; ++i) m->track_keys.insert({coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]});
+}
+
+// lidar6 = {H, W, fov_up, fov_down, r_min, r_max} (angles in radians)
+int orc_integrate(void *h, const double *lidar6, const float *pts, const int32_t *labels, const float *probs,
+                  int64_t n, const double *T16, int nthreads) {
+    Map *m = (Map *)h;
+    Lidar L;
+    L.H = (int)lidar6[0];
+    L.W = (int)lidar6[1];
+    L.fov_up = lidar6[2];
+    L.fov_down = lidar6[3];
+    L.r_min = lidar6[4];
+    L.r_max = lidar6[5];
+    L.dphi = 2.0 * PI / L.W;
+    L.dtheta = (L.fov_up - L.fov_down) / (L.H - 1);
+    L.theta0 = PI / 2.0 - L.fov_up;
+    return integrate(*m, L, pts, labels, probs, n, T16, nthreads);
+}
+
+// valid, in-pixel, ambiguous points; touched, new blocks; updated, semantic, seen voxels; taint events
+void orc_stats(void *h, int64_t *out) {
+    Map *m = (Map *)h;
+    const Stats &s = m->st;
+    int64_t v[9] = {s.valid_points, s.pixel_points, s.ambiguous_points, s.touched_blocks, s.new_blocks,
+                    s.voxels_updated, s.voxels_semantic, s.voxels_seen, s.taint_events};
+    std::memcpy(out, v, sizeof(v));
+}
+
+int64_t orc_num_alloc(void *h) { return (int64_t)((Map *)h)->alloc.size(); }
+
+// all allocated blocks, sorted (x, y, z)
+int64_t orc_get_alloc(void *h, int32_t *coords, int64_t cap) {
+    Map *m = (Map *)h;
+    std::vector<I3> v(m->alloc.begin(), m->alloc.end());
+    std::sort(v.begin(), v.end());
+    int64_t n = std::min<int64_t>(cap, (int64_t)v.size());
+    for (int64_t i = 0; i < n; ++i) {
+        coords[3 * i] = (int32_t)v[i].x;
+        coords[3 * i + 1] = (int32_t)v[i].y;
+        coords[3 * i + 2] = (int32_t)v[i].z;
+    }
+    return (int64_t)v.size();
+}
+
+// blocks touched by the last frame, sorted
+int64_t orc_get_touched(void *h, int32_t *coords, int64_t cap) {
+    Map *m = (Map *)h;
+    int64_t n = std::min<int64_t>(cap, (int64_t)m->touched.size());
+    for (int64_t i = 0; i < n; ++i) {
+        coords[3 * i] = (int32_t)m->touched[i].x;
+        coords[3 * i + 1] = (int32_t)m->touched[i].y;
+        coords[3 * i + 2] = (int32_t)m->touched[i].z;
+    }
+    return (int64_t)m->touched.size();
+}
+
+// Copy one block's voxels; returns 0 when the block holds data, -1 otherwise.
+int orc_read_block(void *h, const int32_t *coord, double *D, double *W, double *logP, uint8_t *taint,
+                   int32_t *label, double *gap) {
+    Map *m = (Map *)h;
+    auto it = m->blocks.find({coord[0], coord[1], coord[2]});
+    if (it == m->blocks.end()) return -1;
+    const Block &b = it->second;
+    if (D) std::memcpy(D, b.D.data(), sizeof(double) * BV);
+    if (W) std::memcpy(W, b.W.data(), sizeof(double) * BV);
+    if (logP) std::memcpy(logP, b.logP.data(), sizeof(double) * BV * m->C);
+    if (taint) std::memcpy(taint, b.taint.data(), BV);
+    if (label)
+        for (int vi = 0; vi < BV; ++vi) label[vi] = argmax_label(*m, b, vi, gap ? gap + vi : nullptr);
+    return 0;
+}
+
+// Overwrite (creating if needed) one block's voxels: test fixtures for meshing and queries.
+int orc_write_block(void *h, const int32_t *coord, const double *D, const double *W, const double *logP) {
+    Map *m = (Map *)h;
+    I3 k{coord[0], coord[1], coord[2]};
+    auto it = m->blocks.find(k);
+    if (it == m->blocks.end()) it = m->blocks.emplace(k, new_block(m->C)).first;
+    m->alloc.insert(k);
+    Block &b = it->second;
+    if (D) std::memcpy(b.D.data(), D, sizeof(double) * BV);
+    if (W) std::memcpy(b.W.data(), W, sizeof(double) * BV);
+    if (logP) std::memcpy(b.logP.data(), logP, sizeof(double) * BV * m->C);
+    return 0;
+}
+
+// --- meshing: build into a handle, then fetch ------------------------------
+// scope 0: all blocks holding data; 1: the listed blocks only.
+void *orc_mesh_build(void *h, int scope, const int32_t *coords, int64_t n, int64_t *counts) {
+    Map *m = (Map *)h;
+    Mesh *mesh = new Mesh();
+    std::vector<I3> keys;
+    if (scope == 0) {
+        for (auto &kv : m->blocks) keys.push_back(kv.first);
+        std::sort(keys.begin(), keys.end());
+    } else {
+        for (int64_t i = 0; i < n; ++i) keys.push_back({coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]});
+    }
+    for (const I3 &k : keys) mesh_block(*m, k, *mesh);
+    counts[0] = (int64_t)mesh->verts.size();
+    counts[1] = (int64_t)mesh->tris.size();
+    return mesh;
+}
+
+// vertices sorted by key: key, position (m), label, gap to runner-up class, taint bits
+// triangles: three keys, cube anchor voxel, taint (corner |D| < 1e-6 or distance-tainted corner)
+void orc_mesh_fetch(void *hm, int64_t *vkey, double *vpos, int32_t *vlab, double *vgap, uint8_t *vtaint,
+                    int64_t *tkeys, int32_t *tanchor, uint8_t *ttaint) {
+    Mesh *mesh = (Mesh *)hm;
+    int64_t i = 0;
+    for (auto &kv : mesh->verts) {
+        vkey[i] = kv.first;
+        for (int q = 0; q < 3; ++q) vpos[3 * i + q] = kv.second.pos[q];
+        vlab[i] = kv.second.label;
+        vgap[i] = kv.second.gap;
+        vtaint[i] = kv.second.taint;
+        ++i;
+    }
+    for (size_t j = 0; j < mesh->tris.size(); ++j) {
+        const MeshTri &t = mesh->tris[j];
+        for (int q = 0; q < 3; ++q) tkeys[3 * j + q] = t.k[q];
+        tanchor[3 * j] = (int32_t)t.anchor.x;
+        tanchor[3 * j + 1] = (int32_t)t.anchor.y;
+        tanchor[3 * j + 2] = (int32_t)t.anchor.z;
+        ttaint[j] = t.taint;
+    }
+}
+
+void orc_mesh_free(void *hm) { delete (Mesh *)hm; }
+
+int64_t orc_edge_key(int64_t x, int64_t y, int64_t z, int axis) { return edge_key(x, y, z, axis); }
+
+// --- queries ----------------------------------------------------------------
+void orc_query(void *h, const double *xyz, int64_t n, double *sdf, uint8_t *valid, double *grad) {
+    Map *m = (Map *)h;
+    for (int64_t i = 0; i < n; ++i) {
+        double s, g[3];
+        bool ok = query(*m, xyz + 3 * i, &s, g);
+        sdf[i] = s;
+        valid[i] = ok ? 1 : 0;
+        if (grad)
+            for (int k = 0; k < 3; ++k) grad[3 * i + k] = g[k];
+    }
+}
+
+/*
+ * Loss L = sum_i D(T p_i)^2 over valid queries, its gradient with respect
+ * to the left se(3) perturbation xi = (rho, phi) of T (dx/dxi = [I | -[x]x]),
+ * and the Gauss-Newton system H = sum J^T J, g = sum J^T D with
+ * J_i = grad D(x_i)^T [I | -[x_i]x].  Returns the number of valid points.
+ */
+int64_t orc_pose_terms(void *h, const float *pts, int64_t n, const double *T16, double *loss, double *dL,
+                       double *Hm, double *gv) {
+    Map *m = (Map *)h;
+    double L = 0.0, G[6] = {0}, H[36] = {0}, g6[6] = {0};
+    int64_t nv = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double p[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
+        if (!(std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]))) continue;
+        double x[3];
+        for (int r = 0; r < 3; ++r) x[r] = T16[4 * r] * p[0] + T16[4 * r + 1] * p[1] + T16[4 * r + 2] * p[2] + T16[4 * r + 3];
+        double s, gr[3];
+        if (!query(*m, x, &s, gr)) continue;
+        ++nv;
+        double J[6] = {gr[0], gr[1], gr[2], x[1] * gr[2] - x[2] * gr[1], x[2] * gr[0] - x[0] * gr[2],
+                       x[0] * gr[1] - x[1] * gr[0]};
+        L += s * s;
+        for (int a = 0; a < 6; ++a) {
+            G[a] += 2.0 * s * J[a];
+            g6[a] += J[a] * s;
+            for (int b = 0; b < 6; ++b) H[6 * a + b] += J[a] * J[b];
+        }
+    }
+    if (loss) *loss = L;
+    if (dL) std::memcpy(dL, G, sizeof(G));
+    if (Hm) std::memcpy(Hm, H, sizeof(H));
+    if (gv) std::memcpy(gv, g6, sizeof(g6));
+    return nv;
+}
+
+/*
+ * Gauss-Newton scan-to-map alignment: iters steps of
+ * (H + mu I) delta = -g with mu = 1e-6 (trace(H)/6 + 1e-12), T <- Exp(delta) T.
+ */
+int orc_align(void *h, const float *pts, int64_t n, const double *T0, int iters, double *T_out) {
+    double T[16];
+    std::memcpy(T, T0, sizeof(T));
+    for (int it = 0; it < iters; ++it) {
+        double H[36], g[6];
+        orc_pose_terms(h, pts, n, T, nullptr, nullptr, H, g);
+        double tr = 0.0;
+        for (int a = 0; a < 6; ++a) tr += H[7 * a];
+        double mu = 1e-6 * (tr / 6.0 + 1e-12);
+        // solve (H + mu I) x = -g by Gaussian elimination with partial pivoting
+        double A[6][7];
+        for (int a = 0; a < 6; ++a) {
+            for (int b = 0; b < 6; ++b) A[a][b] = H[6 * a + b] + (a == b ? mu : 0.0);
+            A[a][6] = -g[a];
+        }
+        for (int c = 0; c < 6; ++c) {
+            int piv = c;
+            for (int r = c + 1; r < 6; ++r)
+                if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+            for (int k = 0; k < 7; ++k) std::swap(A[c][k], A[piv][k]);
+            if (A[c][c] == 0.0) return -1;
+            for (int r = c + 1; r < 6; ++r) {
+                double f = A[r][c] / A[c][c];
+                for (int k = c; k < 7; ++k) A[r][k] -= f * A[c][k];
+            }
+        }
+        double d[6];
+        for (int c = 5; c >= 0; --c) {
+            double s = A[c][6];
+            for (int k = c + 1; k < 6; ++k) s -= A[c][k] * d[k];
+            d[c] = s / A[c][c];
+        }
+        double dR[9], dt[3];
+        se3_exp(d, dR, dt);
+        double Tn[16];
+        std::memcpy(Tn, T, sizeof(T));
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c)
+                Tn[4 * r + c] = dR[3 * r] * T[c] + dR[3 * r + 1] * T[4 + c] + dR[3 * r + 2] * T[8 + c];
+            Tn[4 * r + 3] = dR[3 * r] * T[3] + dR[3 * r + 1] * T[7] + dR[3 * r + 2] * T[11] + dt[r];
+        }
+        std::memcpy(T, Tn, sizeof(T));
+    }
+    std::memcpy(T_out, T, sizeof(T));
+    return 0;
+}
+
+void orc_se3_exp(const double *xi, double *R9, double *t3) { se3_exp(xi, R9, t3); }
+
+// HSV palette with hue l / C of a full turn, full saturation and value
+void orc_palette(int C, uint8_t *rgb) {
+    for (int l = 0; l < C; ++l) {
+        double h = 6.0 * (double)l / (double)C;
+        int sector = (int)std::floor(h);
+        double f = h - sector;
+        double v = 1.0, p = 0.0, q = 1.0 - f, t = f;
+        double r, g, b;
+        switch (sector % 6) {
+            case 0: r = v; g = t; b = p; break;
+            case 1: r = q; g = v; b = p; break;
+            case 2: r = p; g = v; b = t; break;
+            case 3: r = p; g = q; b = v; break;
+            case 4: r = t; g = p; b = v; break;
+            default: r = v; g = p; b = q; break;
+        }
+        rgb[3 * l] = (uint8_t)std::lround(255.0 * r);
+        rgb[3 * l + 1] = (uint8_t)std::lround(255.0 * g);
+        rgb[3 * l + 2] = (uint8_t)std::lround(255.0 * b);
+    }
+}
+
+// Band blocks of one point (test hook for the allocation pins).
+int64_t orc_point_blocks(void *h, const float *pt, const double *T16, int32_t *out, int64_t cap) {
+    Map *m = (Map *)h;
+    double R[9], t[3];
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) R[3 * r + c] = T16[4 * r + c];
+        t[r] = T16[4 * r + 3];
+    }
+    BandConst bc = band_const(*m, R, t);
+    float l = range_f32(pt[0], pt[1], pt[2]);
+    float e0[3], e1[3];
+    band_endpoints(bc, pt[0], pt[1], pt[2], l, e0, e1);
+    std::vector<I3> v;
+    band_blocks(e0, e1, v);
+    int64_t n = std::min<int64_t>(cap, (int64_t)v.size());
+    for (int64_t i = 0; i < n; ++i) {
+        out[3 * i] = (int32_t)v[i].x;
+        out[3 * i + 1] = (int32_t)v[i].y;
+        out[3 * i + 2] = (int32_t)v[i].z;
+    }
+    return (int64_t)v.size();
+}
+
+// FP32 band endpoints of one point (test hook)
+void orc_point_band(void *h, const float *pt, const double *T16, float *e0, float *e1) {
+    Map *m = (Map *)h;
+    double R[9], t[3];
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) R[3 * r + c] = T16[4 * r + c];
+        t[r] = T16[4 * r + 3];
+    }
+    BandConst bc = band_const(*m, R, t);
+    float l = range_f32(pt[0], pt[1], pt[2]);
+    band_endpoints(bc, pt[0], pt[1], pt[2], l, e0, e1);
+}
+
+}  // extern "C"
