@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Benchmark of the per-frame metric-semantic mapping path on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload loop64|line16] [--storage fp32|fp16]
+
+One step = one scan fused into the map by integrate_scan: range image,
+band allocation, projective TSDF + Bayesian semantic fusion of the touched
+blocks, incremental marching cubes of the touched blocks and their
+neighbours.  Default workload: the 64 x 2048 scanner (131,072 points per
+scan, +-22.5 deg, 100 m) on a 400 m loop through a seeded 200 m x 200 m
+scene, 20-way class-probability vectors, 0.1 m voxels, 0.3 m truncation
+(synthetic stand-in for the paper's public LiDAR sequences).  Scan k >= 200
+repeats the loop (a second lap).
+
+Inputs for every timed scan are resident in HBM before timing starts; L2 is
+flushed (a 512 MB write) before each timed scan, outside its events.  Rank 0
+prints one JSON line.  Under torchrun every rank maps its own replica
+(independent scene seed) and ``value`` sums all ranks' points over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+PHASES = ("reset", "range_image", "pixels", "alloc", "integrate", "dirty", "mesh")
+KERNEL_FILES = {"range_image": "k_scan.cu", "pixels": "k_scan.cu", "alloc": "k_alloc.cu",
+                "integrate": "k_integrate.cu", "dirty": "k_alloc.cu", "mesh": "k_mesh.cu"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=195)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["loop64", "line16"], default="loop64")
+    ap.add_argument("--storage", choices=["fp32", "fp16"], default="fp32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--flush-mb", type=int, default=512)
+    return ap.parse_args()
+
+
+def workload(name, rank=0):
+    w = synth.loop64() if name == "loop64" else synth.line16()
+    if rank:
+        from dataclasses import replace
+        w = replace(w, seed=w.seed + 1000 * rank)
+    return w
+
+
+def frames_for(w, n, nthreads=0):
+    scene = synth.make_scene(w)
+    Ts = synth.trajectory(w, n)
+    for k in range(n):
+        yield synth.make_frame(w, scene, Ts[k], k, nthreads=nthreads)
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes per kernel (HBM traffic the method must do), per frame
+# --------------------------------------------------------------------------
+def algorithmic_bytes(st, n_points, H, W, C, s):
+    """st: per-frame counters (MAP_STAT_* order); s: bytes per stored scalar (4 FP32, 2 FP16).
+
+    integrate: each updated voxel reads and writes {D, W} (2 s each way); each
+      semantically updated voxel reads and writes C log-probabilities and
+      writes its label byte; plus a 16-byte work-list/hash record per touched block.
+    mesh: per re-meshed block, {D, W} + label of its 9^3 staged voxels, its
+      segment record, and the emitted vertices (16 B + 8 B key) and triangles (8 B).
+    range_image: the points (12 B each).  pixels: the winners' probability rows
+      (C * 4 B), the per-pixel outputs.  alloc: the points again.
+    """
+    upd, sem, touched, dirty, mv, mt = st[4], st[5], st[2], st[6], st[7], st[8]
+    return {
+        "integrate": upd * 2 * (2 * s) + sem * (2 * C * s + 1) + touched * 16,
+        "mesh": dirty * (729 * (2 * s + 1) + 16) + mv * 24 + mt * 8,
+        "range_image": n_points * 12,
+        "pixels": H * W * (C * 4 + 16 + 1) + H * W * C * 4,
+        "alloc": n_points * 12,
+        "dirty": touched * 8 * 12,
+        "reset": H * W * 8,
+    }
+
+
+class ClockSampler:
+    """Samples SM clock and throttle reasons via NVML in a background thread."""
+
+    REASONS = {"gpu_idle": 0x1, "applications_clocks_setting": 0x2, "sw_power_cap": 0x4, "hw_slowdown": 0x8,
+               "sync_boost": 0x10, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+               "hw_power_brake_slowdown": 0x80, "display_clock_setting": 0x100}
+
+    def __init__(self, index, period=0.005):
+        self.samples, self.reasons = [], 0
+        self.period, self.ok = period, False
+        self.stop_ev = threading.Event()
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self.nv = pynvml
+            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+            self.ok = True
+        except Exception as e:   # pragma: no cover
+            self.err = str(e)
+
+    def _run(self):
+        nv = self.nv
+        while not self.stop_ev.is_set():
+            try:
+                self.samples.append(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM))
+                try:
+                    r = nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                except AttributeError:
+                    r = nv.nvmlDeviceGetCurrentClocksThrottleReasons(self.h)
+                self.reasons |= int(r)
+            except Exception:
+                pass
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self.ok:
+            self.t = threading.Thread(target=self._run, daemon=True)
+            self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        if self.ok:
+            self.stop_ev.set()
+            self.t.join()
+
+    def summary(self):
+        if not self.ok:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvml unavailable"]}
+        names = [k for k, v in self.REASONS.items() if self.reasons & v and k != "gpu_idle"]
+        return {"sm_mhz": float(np.median(self.samples)) if self.samples else None, "sm_max_mhz": self.max_mhz,
+                "reasons": names, "samples": len(self.samples)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+def traffic_record(kernel):
+    """Per-launch DRAM bytes from the committed ncu summary, if it matches the current source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p)).get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2412_00291_b300", "csrc", KERNEL_FILES.get(kernel, ""))
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec.get("source_sha"):
+        return None
+    return rec
+
+
+def cpu_baseline(w, budget_s=15.0, max_frames=8, col_stride=1):
+    """The FP64 oracle as it stands, on all host cores, over the first scans of the workload."""
+    import oracle
+    nthreads = os.cpu_count() or 1
+    m = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    done_pts, secs, k = 0, 0.0, 0
+    for f in frames_for(w, max_frames):
+        pts, pr, lab = f.points, f.probs, f.labels
+        if col_stride > 1:
+            sel = (np.arange(len(pts)) % w.lidar.W) % col_stride == 0
+            pts = pts[sel]
+            pr = pr[sel] if pr is not None else None
+            lab = lab[sel]
+        t0 = time.perf_counter()
+        m.integrate(w.lidar, pts, f.T, labels=None if pr is not None else lab, probs=pr, nthreads=nthreads)
+        secs += time.perf_counter() - t0
+        done_pts += len(pts)
+        k += 1
+        if secs > budget_s:
+            break
+    return {"value": done_pts / secs, "unit": "points/s", "cores": nthreads, "kind": "oracle",
+            "sample": f"first {k} scans of {w.name}" + (f", every {col_stride}th column" if col_stride > 1 else "") +
+                      f" ({done_pts} points, {secs:.1f} s, fresh map, FP64, OpenMP over blocks)"}
+
+
+def run_reference(args, rank, world):
+    """The oracle arm: each step fuses a bounded sample (every 8th column) of scan k."""
+    if rank != 0:
+        return
+    import oracle
+    w = workload(args.workload)
+    nthreads = os.cpu_count() or 1
+    m = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    stride = 8
+    times, pts_done = [], 0
+    for k, f in enumerate(frames_for(w, args.warmup + args.steps)):
+        sel = (np.arange(len(f.points)) % w.lidar.W) % stride == 0
+        pts = f.points[sel]
+        pr = f.probs[sel] if f.probs is not None else None
+        lab = f.labels[sel]
+        t0 = time.perf_counter()
+        m.integrate(w.lidar, pts, f.T, labels=None if pr is not None else lab, probs=pr, nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            pts_done += len(pts)
+    total = sum(times)
+    v = pts_done / total
+    line = {"metric": "scan points fused/s (64x2048, 0.1 m voxels)", "value": v, "unit": "points/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / max(1, len(times)), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "sample": f"every {stride}th column of each scan", "threads": nthreads},
+            "cpu_baseline": {"value": v, "unit": "points/s", "cores": nthreads, "kind": "oracle",
+                             "sample": f"{len(times)} scans of {w.name}, every {stride}th column"},
+            "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2412_00291_b300 as P
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = workload(args.workload, rank)
+    L = w.lidar
+    lid = P.lidar_intrinsics(L.H, L.W, L.fov_up, L.fov_down, L.r_min, L.r_max)
+    n_total = args.warmup + args.steps
+    C = w.n_classes
+    # --- inputs resident in HBM -------------------------------------------
+    t_gen = time.perf_counter()
+    pts_d, lab_d, pr_d, Ts, host = [], [], [], [], []
+    for f in frames_for(w, n_total):
+        pts_d.append(torch.from_numpy(f.points).to(dev))
+        if f.probs is not None:
+            pr_d.append(torch.from_numpy(f.probs).to(dev))
+        else:
+            lab_d.append(torch.from_numpy(f.labels).to(dev))
+        Ts.append(f.T.copy())
+        if not args.no_e2e:
+            hp = torch.from_numpy(f.points).pin_memory()
+            hq = torch.from_numpy(f.probs if f.probs is not None else f.labels).pin_memory()
+            host.append((hp, hq))
+    t_gen = time.perf_counter() - t_gen
+    storage = 0 if args.storage == "fp32" else 1
+    s_bytes = 4 if storage == 0 else 2
+    tsdf = P.SemanticTSDF(w.voxel_size, w.truncation, C, storage=storage)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device=dev)
+
+    def step(k):
+        if pr_d:
+            tsdf.integrate(lid, pts_d[k], Ts[k], probs=pr_d[k])
+        else:
+            tsdf.integrate(lid, pts_d[k], Ts[k], labels=lab_d[k])
+
+    for k in range(args.warmup):
+        step(k)
+    tsdf.stats()
+    launches0 = tsdf.stats()["kernel_launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    P.map_profile_begin(tsdf.h, args.steps)
+    with ClockSampler(local_rank) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step(args.warmup + i)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    phase_ms, fstats = P.map_profile_end(tsdf.h, args.steps)
+    st_last = tsdf.stats()
+    launches = st_last["kernel_launches"] - launches0
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    total_ms = float(step_ms.sum())
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    n_points = L.H * L.W
+    value = world * args.steps * n_points / (total_ms * 1e-3)
+    # --- roofline of the dominant kernel ------------------------------------
+    peak, peak_kind = measured_peaks()
+    per_kernel = {}
+    for j, name in enumerate(PHASES):
+        if name == "reset":
+            continue
+        bytes_f = np.array([algorithmic_bytes(fs, n_points, L.H, L.W, C, s_bytes)[name] for fs in fstats], float)
+        t = phase_ms[:, j].astype(float)
+        per_kernel[name] = {"ms_mean": float(t.mean()), "share": float(t.sum() / phase_ms.sum()),
+                            "bytes_mean": float(bytes_f.mean()),
+                            "gbs": float(bytes_f.sum() / (t.sum() * 1e-3) / 1e9)}
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["share"])
+    ach = per_kernel[dom]["gbs"]
+    tr = traffic_record(dom)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_source": f"{peak_kind} hbm_gbs", "traffic": tr["bytes_per_launch"] if tr else None,
+            "algorithmic_bytes_per_launch": per_kernel[dom]["bytes_mean"]}
+    frame_bytes = float(np.mean([sum(algorithmic_bytes(fs, n_points, L.H, L.W, C, s_bytes).values())
+                                 for fs in fstats]))
+    # --- end to end through the host-buffer entry point ----------------------
+    e2e = None
+    if not args.no_e2e:
+        tsdf2 = P.SemanticTSDF(w.voxel_size, w.truncation, C, storage=storage)
+        for k in range(args.warmup):
+            hp, hq = host[k]
+            tsdf2.integrate_host(lid, hp, Ts[k], **({"probs": hq} if pr_d else {"labels": hq}))
+        tsdf2.stats()
+        e2e_s = 0.0
+        for i in range(args.steps):
+            k = args.warmup + i
+            hp, hq = host[k]
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tsdf2.integrate_host(lid, hp, Ts[k], **({"probs": hq} if pr_d else {"labels": hq}))
+            tsdf2.stats()                       # device -> host read of the step's counters
+            e2e_s += time.perf_counter() - t0
+        h2d = n_points * 12 + (n_points * C * 4 if pr_d else n_points * 4)
+        e2e = {"value": world * args.steps * n_points / e2e_s, "unit": "points/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 16 * 8, "ms_per_step": 1e3 * e2e_s / args.steps}
+        tsdf2.close()
+    # --- CPU baseline: the oracle on the host cores --------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+    if rank != 0:
+        return
+    clocks = clk.summary()
+    line = {
+        "metric": "scan points fused/s (64x2048, 0.1 m voxels)" if args.workload == "loop64"
+        else "scan points fused/s (16x1024, 0.2 m voxels)",
+        "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp32" if storage == 0 else "fp16-storage/fp32-math", "data": "synthetic",
+        "config": {"workload": w.name, "points_per_scan": n_points, "voxel_size": w.voxel_size,
+                   "truncation": w.truncation, "n_classes": C, "labels": w.label_mode,
+                   "l2": f"flushed ({args.flush_mb} MB write) before every timed scan, outside its events",
+                   "ms_median": float(np.median(step_ms)), "ms_p95": float(np.percentile(step_ms, 95)),
+                   "bracketed_wall_s_incl_flush": t_wall, "parallelism": f"replicas x{world}",
+                   "frame_algorithmic_bytes": frame_bytes,
+                   "frame_gbs": frame_bytes / (total_ms / args.steps * 1e-3) / 1e9,
+                   "touched_blocks_mean": float(fstats[:, 2].mean()),
+                   "voxels_updated_mean": float(fstats[:, 4].mean()),
+                   "voxels_semantic_mean": float(fstats[:, 5].mean()),
+                   "map_blocks_end": st_last["total_blocks"], "input_gen_s": t_gen},
+        "roofline": roof,
+        "kernels": per_kernel,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    tsdf.close()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,247 @@
+/*
+ * semtsdf: per-frame metric-semantic TSDF mapping on one B300 (sm_103a).
+ *
+ * C ABI of the product library (libsemtsdf.so).  Plain pointers and sizes;
+ * no C++ or PyTorch types.  Streams are passed as `void *` holding a
+ * `cudaStream_t` (NULL = the legacy default stream).
+ *
+ * Method (Liu et al. 2024, "Real-Time Metric-Semantic Mapping for
+ * Autonomous Navigation in Outdoor Environments"):
+ *   - Sec. III-C.1: each scan is projected into a range image with
+ *     u = (pi - atan2(y, x)) / dphi, v = (acos(z / r) - theta0) / dtheta.
+ *   - Sec. III-C.2: voxels x_i = nu * v_i stored in 8x8x8 blocks behind a
+ *     hash table; projective distance psi along the ray; linear weight
+ *     (psi + tau) / (2 tau); running-average update of D and W with the
+ *     truncation Gamma(d, tau).
+ *   - Sec. III-C.3, Eq. (bayesian_filter): per-voxel class distribution,
+ *     uniform at allocation, multiplied by each scan's class likelihood and
+ *     renormalised; marching-cubes mesh whose vertices take the most
+ *     probable class.
+ *
+ * Conventions shared by every call:
+ *   - Errors are returned as map_status; nothing aborts, traps or exits.
+ *     Errors found on the device (pool, hash or mesh arena exhausted, a
+ *     bounded wait that gave up) are latched in a device word and reported
+ *     by the next call that synchronises (map_sync, map_get_frame_stats,
+ *     the parity helpers) as MAP_ERR_CAPACITY or MAP_ERR_TIMEOUT.
+ *   - Device input pointers stay owned by the caller, are only read, and
+ *     must stay valid until the stream has executed the call.
+ *   - The map owns all map storage, scratch buffers and mesh buffers.
+ *   - Only the calls documented as synchronising block the host.
+ *   - One map is used from one host thread at a time.
+ */
+#ifndef SEMTSDF_H
+#define SEMTSDF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct map_t map_t;
+
+typedef enum {
+    MAP_OK = 0,
+    MAP_ERR_ARG = 1,        /* a null pointer, a bad size or an inconsistent config  */
+    MAP_ERR_CUDA = 2,       /* a CUDA runtime call failed (see map_last_error)       */
+    MAP_ERR_CAPACITY = 3,   /* block pool, hash table, work list or mesh arena full   */
+    MAP_ERR_BAD_POSE = 4,   /* T_world_lidar is not a rigid transform                 */
+    MAP_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up                     */
+    MAP_ERR_STATE = 6,      /* call not valid in the map's current state              */
+    MAP_ERR_NOMEM = 7       /* device or pinned host allocation failed                */
+} map_status;
+
+/* Spinning multi-beam LiDAR (Sec. III-C.1).  Beam v (0 = top) has polar
+ * angle theta0 + v * dtheta, theta0 = pi/2 - fov_up,
+ * dtheta = (fov_up - fov_down) / (H - 1); column u has azimuth
+ * pi - u * 2 pi / W.  Angles in radians.  Points with range outside
+ * [r_min, r_max] or any non-finite coordinate are ignored. */
+typedef struct {
+    int32_t H, W;
+    double fov_up, fov_down;
+    double r_min, r_max;
+} lidar_intrinsics;
+
+/* Map parameters.  Fill with map_config_default() and override. */
+typedef struct {
+    double voxel_size;        /* nu, metres (Sec. III-C.2)                               */
+    double truncation;        /* tau, metres; the band [p - tau d, p + tau d] is allocated */
+    int32_t n_classes;        /* C >= 2 (Eq. bayesian_filter)                            */
+    int32_t weight_mode;      /* 0: linear (psi + tau)/(2 tau) clamped to [0, 1]; 1: 1   */
+    double p_hit;             /* hard-label likelihood of the given class (default 0.9)  */
+    double logp_floor;        /* lower bound of stored log-probabilities (default -30)   */
+    double lik_floor;         /* lower bound of probability-vector entries (1e-6)        */
+    int32_t storage;          /* 0: FP32 {D, W} and log-probabilities; 1: FP16 storage   */
+    int32_t reserved0;
+    int64_t max_blocks;       /* block pool size (8^3 voxels each)                        */
+    int64_t hash_capacity;    /* hash slots, rounded up to a power of two                 */
+    int64_t max_points;       /* largest scan accepted by integrate_scan                  */
+    int64_t max_pixels;       /* largest H * W accepted                                    */
+    int64_t mesh_vertex_capacity;    /* mesh arena sizes (vertices / triangles)          */
+    int64_t mesh_triangle_capacity;
+} map_config;
+
+/* Device view of an extracted mesh (owned by the map; valid until the next
+ * extract_mesh, integrate_scan or map_destroy on that map).
+ * positions[n_vertices][3] float32 (metres, world frame);
+ * colors[n_vertices][4] uint8 = {r, g, b, label}: label is the most probable
+ *   class of the edge endpoint nearer the surface, rgb its palette colour;
+ * vertex_keys[n_vertices]: lattice edge of the vertex, bits [0,2) axis,
+ *   [2,22) x + 2^19, [22,42) y + 2^19, [42,62) z + 2^19 of its lower voxel;
+ *   vertices on block seams appear once per block that uses them, so equal
+ *   keys mark one welded vertex;
+ * triangles[n_triangles][3] int32 indices into the vertex arrays, wound so
+ *   the normal points to positive distance (free space);
+ * triangle_anchors[n_triangles][3] int32 voxel anchoring the triangle's cube. */
+typedef struct {
+    int64_t n_vertices, n_triangles;
+    float *positions;
+    uint8_t *colors;
+    int64_t *vertex_keys;
+    int32_t *triangles;
+    int32_t *triangle_anchors;
+} mesh_view;
+
+/* Per-frame counters (map_get_frame_stats), all counts of the last frame. */
+enum {
+    MAP_STAT_VALID_POINTS = 0,   /* finite points with r_min <= r <= r_max      */
+    MAP_STAT_PIXEL_POINTS = 1,   /* valid points that fall on a beam row        */
+    MAP_STAT_TOUCHED_BLOCKS = 2, /* blocks met by a truncation band (U_k)       */
+    MAP_STAT_NEW_BLOCKS = 3,     /* of those, allocated this frame              */
+    MAP_STAT_VOXELS_UPDATED = 4, /* voxels whose D, W were updated              */
+    MAP_STAT_VOXELS_SEMANTIC = 5,/* voxels whose class distribution was updated */
+    MAP_STAT_DIRTY_BLOCKS = 6,   /* blocks re-meshed (touched + -x/-y/-z nbrs)  */
+    MAP_STAT_MESH_VERTICES = 7,  /* vertices emitted by this frame's re-mesh    */
+    MAP_STAT_MESH_TRIANGLES = 8, /* triangles emitted by this frame's re-mesh   */
+    MAP_STAT_TOTAL_BLOCKS = 9,   /* blocks allocated in the map so far          */
+    MAP_STAT_ERROR_BITS = 10,    /* latched device error bits                   */
+    MAP_STAT_KERNEL_LAUNCHES = 11, /* kernels this map has launched so far      */
+    MAP_STAT_COUNT = 16
+};
+
+/* Defaults: weight_mode 0, p_hit 0.9, logp_floor -30, lik_floor 1e-6,
+ * FP32 storage, capacities for a 64 x 2048 scanner at 0.1 m. */
+map_status map_config_default(map_config *cfg);
+
+/* Create an empty map; allocates and initialises all device storage (every
+ * pool voxel starts at D = 0, W = 0 and the uniform class distribution). */
+map_status map_create(const map_config *cfg, map_t **out);
+map_status map_destroy(map_t *map);
+
+/* Fuse one posed scan (Sec. III-C): range image, band allocation, projective
+ * TSDF + Bayesian label update of every voxel of the touched blocks, then
+ * incremental marching cubes over the touched blocks and their -x/-y/-z
+ * neighbours.  Asynchronous on `stream`.
+ *   points_dev   [n][3] float32, LiDAR frame (NaN = no return);
+ *   labels_dev   [n] int32 class per point (< 0 or >= C: no label), or NULL;
+ *   probs_dev    [n][C] float32 class probabilities per point, or NULL;
+ *                exactly one of labels_dev / probs_dev is non-NULL (n > 0);
+ *   T_world_lidar  host double[16], row-major 4x4 world-from-LiDAR pose.
+ * Returns MAP_ERR_ARG for n > max_points or H*W > max_pixels,
+ * MAP_ERR_BAD_POSE when the rotation part is not orthonormal to 1e-6. */
+map_status integrate_scan(map_t *map, const lidar_intrinsics *lidar, const float *points_dev,
+                          const int32_t *labels_dev, const float *probs_dev, int64_t n,
+                          const double T_world_lidar[16], void *stream);
+
+/* Same as integrate_scan, for HOST buffers (pinned for best speed): the
+ * map copies them to its own device staging buffers on `stream` first. */
+map_status integrate_scan_host(map_t *map, const lidar_intrinsics *lidar, const float *points_host,
+                               const int32_t *labels_host, const float *probs_host, int64_t n,
+                               const double T_world_lidar[16], void *stream);
+
+/* Gather every block's current mesh segment into one indexed mesh (device
+ * arrays owned by the map).  Synchronises `stream` to learn the sizes. */
+map_status extract_mesh(map_t *map, mesh_view *out, void *stream);
+
+/* Re-mesh every allocated block from scratch (replacing the incremental
+ * segments); used to check that incremental meshing equals a full pass. */
+map_status map_remesh_all(map_t *map, void *stream);
+
+/* Trilinear interpolation of D at m world points (from the 8 voxel centres
+ * nu * v around x).  sdf_dev[m] float32 (NaN when any of the 8 voxels is
+ * unallocated or unobserved, W = 0), valid_dev[m] uint8 (1 = valid), may be
+ * NULL.  Asynchronous. */
+map_status query_sdf(map_t *map, const float *xyz_dev, int64_t m, float *sdf_dev, uint8_t *valid_dev,
+                     void *stream);
+
+/* Backward of query_sdf: grad_xyz_dev[m][3] = grad_sdf_dev[m] * dD/dx at
+ * each point (0 where invalid).  If pose_grad_dev (double[6]) is non-NULL
+ * the left-perturbation pose gradient sum_i grad_xyz_i^T [I | -[x_i]x] is
+ * ADDED to it (rho first, then phi).  Asynchronous. */
+map_status query_sdf_backward(map_t *map, const float *xyz_dev, const float *grad_sdf_dev, int64_t m,
+                              float *grad_xyz_dev, double *pose_grad_dev, void *stream);
+
+/* Scan-to-map alignment: `iters` Gauss-Newton steps on sum_i D(T p_i)^2,
+ * (H + mu I) delta = -g with mu = 1e-6 (trace(H)/6 + 1e-12) and
+ * T <- Exp(delta) T, all on the device.  points_dev [n][3] float32 LiDAR
+ * frame.  T0 and T_out are host double[16].  Synchronises `stream`. */
+map_status map_align_scan(map_t *map, const float *points_dev, int64_t n, const double T0[16], int32_t iters,
+                          double T_out[16], void *stream);
+
+/* ---- host-side inspection and checkpoint helpers (synchronising) ---- */
+
+/* Wait for the map's work on `stream` and report latched device errors. */
+map_status map_sync(map_t *map, void *stream);
+
+/* Counters of the last integrate_scan (MAP_STAT_*); out has room for
+ * MAP_STAT_COUNT int64 values.  Synchronises `stream`. */
+map_status map_get_frame_stats(map_t *map, int64_t *out, void *stream);
+
+/* Allocated block coordinates (host int32[cap][3], unsorted); *count
+ * receives the number of allocated blocks even when cap is smaller. */
+map_status map_get_blocks(map_t *map, int32_t *coords_host, int64_t cap, int64_t *count);
+
+/* Read n blocks into host arrays (FP32 whatever the storage):
+ * D[n][512], W[n][512], logP[n][C][512], label[n][512] (each may be NULL);
+ * voxel index x + 8 y + 64 z.  found[n] (may be NULL) is 1 for allocated
+ * blocks; others read as zeros / uniform. */
+map_status map_read_blocks(map_t *map, const int32_t *coords_host, int64_t n, float *D, float *W,
+                           float *logP, uint8_t *label, uint8_t *found);
+
+/* Write n blocks from host arrays (allocating them when new): D, W
+ * [n][512]; logP [n][C][512] or NULL (uniform).  The label plane is
+ * recomputed as the argmax.  Marks nothing dirty (call map_remesh_all). */
+map_status map_write_blocks(map_t *map, const int32_t *coords_host, int64_t n, const float *D, const float *W,
+                            const float *logP);
+
+/* ---- phase profiling (CUDA events on the caller's stream) ---- */
+
+/* Phases of one integrate_scan, in launch order. */
+enum {
+    MAP_PHASE_RESET = 0,      /* range-image and counter resets                  */
+    MAP_PHASE_RANGE = 1,      /* range image (Sec. III-C.1)                       */
+    MAP_PHASE_PIXELS = 2,     /* per-pixel range pair and class log-likelihood    */
+    MAP_PHASE_ALLOC = 3,      /* band allocation, hash insert, touched list       */
+    MAP_PHASE_INTEGRATE = 4,  /* projective TSDF + Bayesian fusion                */
+    MAP_PHASE_DIRTY = 5,      /* blocks to re-mesh                                */
+    MAP_PHASE_MESH = 6,       /* incremental marching cubes                       */
+    MAP_PHASE_COUNT = 7
+};
+
+/* Start recording per-phase events for up to max_frames subsequent
+ * integrate_scan calls (earlier recording is discarded). */
+map_status map_profile_begin(map_t *map, int32_t max_frames);
+
+/* Stop recording; synchronises.  ms_out[max_frames][MAP_PHASE_COUNT]
+ * receives each recorded frame's phase durations in milliseconds,
+ * stats_out[max_frames][MAP_STAT_COUNT] (may be NULL) its per-frame
+ * counters (indices 0..8 of MAP_STAT_*), and *n_frames the number of
+ * frames recorded. */
+map_status map_profile_end(map_t *map, float *ms_out, int64_t *stats_out, int32_t *n_frames);
+
+/* Most recent error message for this map (or a global one for map = NULL). */
+const char *map_last_error(map_t *map);
+
+/* Build-time helpers used by host tests (no GPU needed):
+ * the marching-cubes table the kernels use, as triangles of cube-edge ids
+ * (table[256][MAP_MC_MAXTRI][3], -1 padded; cube edge e = axis * 4 + d_a1 +
+ * 2 d_a2 with a1, a2 the next axes cyclically); and the class palette. */
+enum { MAP_MC_MAXTRI = 8 };
+int32_t map_mc_table(int8_t *table_out);
+int32_t map_palette(int32_t n_classes, uint8_t *rgb_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEMTSDF_H */

@@ -266,7 +266,7 @@ int integrate(Map &m, const Lidar &L, const float *pts, const int32_t *labels, c
         if (!(std::isfinite(x) && std::isfinite(y) && std::isfinite(z))) continue;
         float l = range_f32(x, y, z);
         lr[i] = l;
-        if (!(l >= rmin_f && l <= rmax_f)) continue;
+        if (!(l >= rmin_f && l <= rmax_f && l > 0.0f)) continue;
         valid[i] = 1;
         m.st.valid_points++;
         double X = x, Y = y, Z = z;

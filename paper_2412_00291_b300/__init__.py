@@ -1,0 +1,407 @@
+"""Python binding of libsemtsdf (the C ABI in include/semtsdf.h).
+
+Argument marshalling only: every step of the mapping path runs in the CUDA
+kernels of ``_lib/libsemtsdf.so``.  PyTorch supplies device memory and
+streams.  There is no CPU fallback: importing this package fails when the
+library has not been built (``python paper_2412_00291_b300/build.py``).
+
+The functions carry the C names (``map_create``, ``integrate_scan``,
+``extract_mesh``, ``query_sdf`` ...); ``SemanticTSDF`` bundles them for
+convenience and ``QuerySDF`` is the autograd Function of the trilinear query
+(hand-written backward kernel, including the 6-DoF pose gradient).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsemtsdf.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2412_00291_b300/build.py` "
+                      "(there is no CPU fallback)")
+
+import torch  # noqa: E402  (after the library check: fail fast without it)
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+
+MAP_STAT_NAMES = ("valid_points", "pixel_points", "touched_blocks", "new_blocks", "voxels_updated",
+                  "voxels_semantic", "dirty_blocks", "mesh_vertices", "mesh_triangles", "total_blocks",
+                  "error_bits", "kernel_launches")
+STATUS = {0: "MAP_OK", 1: "MAP_ERR_ARG", 2: "MAP_ERR_CUDA", 3: "MAP_ERR_CAPACITY", 4: "MAP_ERR_BAD_POSE",
+          5: "MAP_ERR_TIMEOUT", 6: "MAP_ERR_STATE", 7: "MAP_ERR_NOMEM"}
+MC_MAXTRI = 8
+BV = 512
+
+
+class MapConfig(ctypes.Structure):
+    _fields_ = [("voxel_size", D), ("truncation", D), ("n_classes", I32), ("weight_mode", I32),
+                ("p_hit", D), ("logp_floor", D), ("lik_floor", D), ("storage", I32), ("reserved0", I32),
+                ("max_blocks", I64), ("hash_capacity", I64), ("max_points", I64), ("max_pixels", I64),
+                ("mesh_vertex_capacity", I64), ("mesh_triangle_capacity", I64)]
+
+
+class LidarIntrinsics(ctypes.Structure):
+    _fields_ = [("H", I32), ("W", I32), ("fov_up", D), ("fov_down", D), ("r_min", D), ("r_max", D)]
+
+
+class MeshView(ctypes.Structure):
+    _fields_ = [("n_vertices", I64), ("n_triangles", I64), ("positions", P), ("colors", P),
+                ("vertex_keys", P), ("triangles", P), ("triangle_anchors", P)]
+
+
+_SIGS = {
+    "map_config_default": ([P], I32),
+    "map_create": ([P, P], I32),
+    "map_destroy": ([P], I32),
+    "integrate_scan": ([P, P, P, P, P, I64, P, P], I32),
+    "integrate_scan_host": ([P, P, P, P, P, I64, P, P], I32),
+    "extract_mesh": ([P, P, P], I32),
+    "map_remesh_all": ([P, P], I32),
+    "query_sdf": ([P, P, I64, P, P, P], I32),
+    "query_sdf_backward": ([P, P, P, I64, P, P, P], I32),
+    "map_align_scan": ([P, P, I64, P, I32, P, P], I32),
+    "map_sync": ([P, P], I32),
+    "map_get_frame_stats": ([P, P, P], I32),
+    "map_get_blocks": ([P, P, I64, P], I32),
+    "map_read_blocks": ([P, P, I64, P, P, P, P, P], I32),
+    "map_write_blocks": ([P, P, I64, P, P, P], I32),
+    "map_last_error": ([P], ctypes.c_char_p),
+    "map_profile_begin": ([P, I32], I32),
+    "map_profile_end": ([P, P, P, P], I32),
+    "map_mc_table": ([P], I32),
+    "map_palette": ([I32, P], I32),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+class MapError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status, handle=None):
+    if status != 0:
+        msg = _lib.map_last_error(handle)
+        raise MapError(status, msg.decode() if msg else "")
+
+
+def _np_ptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _dev_ptr(t, dtype, name, shape_last=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    if shape_last is not None and (t.dim() != 2 or t.shape[1] != shape_last):
+        raise ValueError(f"{name} must have shape [n, {shape_last}]")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _pose(T):
+    T = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(4, 4))
+    return T, ctypes.c_void_p(T.ctypes.data)
+
+
+def lidar_intrinsics(H, W, fov_up, fov_down, r_min=0.5, r_max=100.0) -> LidarIntrinsics:
+    """Angles in radians (Sec. III-C.1 sensor model)."""
+    return LidarIntrinsics(int(H), int(W), float(fov_up), float(fov_down), float(r_min), float(r_max))
+
+
+# --------------------------------------------------------------------------
+# C functions, one wrapper each
+# --------------------------------------------------------------------------
+def map_config_default(**overrides) -> MapConfig:
+    cfg = MapConfig()
+    _check(_lib.map_config_default(ctypes.byref(cfg)))
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise AttributeError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def map_create(cfg: MapConfig):
+    h = ctypes.c_void_p()
+    _check(_lib.map_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def map_destroy(h):
+    _check(_lib.map_destroy(h))
+
+
+def integrate_scan(h, lidar: LidarIntrinsics, points, T_world_lidar, labels=None, probs=None, stream=None):
+    n = 0 if points is None else int(points.shape[0])
+    _, Tp = _pose(T_world_lidar)
+    C = None if probs is None else int(probs.shape[1])
+    _check(_lib.integrate_scan(h, ctypes.byref(lidar), _dev_ptr(points, torch.float32, "points", 3),
+                               _dev_ptr(labels, torch.int32, "labels"),
+                               _dev_ptr(probs, torch.float32, "probs", C), n, Tp, _stream(stream)), h)
+
+
+def integrate_scan_host(h, lidar: LidarIntrinsics, points, T_world_lidar, labels=None, probs=None, stream=None):
+    """Host (ideally pinned) buffers: numpy arrays or CPU tensors."""
+    def hp(a, dtype):
+        if a is None:
+            return None
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or a.dtype != dtype or not a.is_contiguous():
+                raise TypeError("host tensor expected")
+            return ctypes.c_void_p(a.data_ptr())
+        return _np_ptr(np.ascontiguousarray(a))
+    n = int(points.shape[0])
+    _, Tp = _pose(T_world_lidar)
+    _check(_lib.integrate_scan_host(h, ctypes.byref(lidar), hp(points, torch.float32), hp(labels, torch.int32),
+                                    hp(probs, torch.float32), n, Tp, _stream(stream)), h)
+
+
+class _CAI:
+    """__cuda_array_interface__ wrapper for map-owned device arrays."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr or 0, False),
+                                         "version": 3, "strides": None}
+
+
+def _view(ptr, shape, dtype):
+    typestr = {torch.float32: "<f4", torch.uint8: "|u1", torch.int64: "<i8", torch.int32: "<i4"}[dtype]
+    if int(np.prod(shape)) == 0:
+        return torch.zeros(shape, dtype=dtype, device="cuda")
+    return torch.as_tensor(_CAI(ptr, shape, typestr), device="cuda")
+
+
+def extract_mesh(h, stream=None, copy=True) -> dict:
+    """Indexed mesh as CUDA tensors (copies unless copy=False; views die at the next integrate)."""
+    mv = MeshView()
+    _check(_lib.extract_mesh(h, ctypes.byref(mv), _stream(stream)), h)
+    nv, nt = mv.n_vertices, mv.n_triangles
+    out = {"positions": _view(mv.positions, (nv, 3), torch.float32),
+           "colors": _view(mv.colors, (nv, 4), torch.uint8),
+           "vertex_keys": _view(mv.vertex_keys, (nv,), torch.int64),
+           "triangles": _view(mv.triangles, (nt, 3), torch.int32),
+           "triangle_anchors": _view(mv.triangle_anchors, (nt, 3), torch.int32)}
+    if copy:
+        out = {k: v.clone() for k, v in out.items()}
+    return out
+
+
+def map_remesh_all(h, stream=None):
+    _check(_lib.map_remesh_all(h, _stream(stream)), h)
+
+
+def query_sdf(h, xyz, stream=None):
+    xyz = xyz.contiguous()
+    m = int(xyz.shape[0])
+    sdf = torch.empty(m, dtype=torch.float32, device=xyz.device)
+    valid = torch.empty(m, dtype=torch.uint8, device=xyz.device)
+    _check(_lib.query_sdf(h, _dev_ptr(xyz, torch.float32, "xyz", 3), m, ctypes.c_void_p(sdf.data_ptr()),
+                          ctypes.c_void_p(valid.data_ptr()), _stream(stream)), h)
+    return sdf, valid.bool()
+
+
+def query_sdf_backward(h, xyz, grad_sdf, pose_grad=None, stream=None):
+    """grad_xyz [m, 3]; adds the (rho, phi) pose gradient into pose_grad (float64 [6]) when given."""
+    xyz = xyz.contiguous()
+    grad_sdf = grad_sdf.contiguous().float()
+    m = int(xyz.shape[0])
+    gx = torch.empty((m, 3), dtype=torch.float32, device=xyz.device)
+    pg = None if pose_grad is None else _dev_ptr(pose_grad, torch.float64, "pose_grad")
+    _check(_lib.query_sdf_backward(h, _dev_ptr(xyz, torch.float32, "xyz", 3),
+                                   _dev_ptr(grad_sdf, torch.float32, "grad_sdf"), m,
+                                   ctypes.c_void_p(gx.data_ptr()), pg, _stream(stream)), h)
+    return gx
+
+
+def map_align_scan(h, points, T0, iters=20, stream=None):
+    _, T0p = _pose(T0)
+    out = np.zeros((4, 4))
+    _check(_lib.map_align_scan(h, _dev_ptr(points, torch.float32, "points", 3), int(points.shape[0]), T0p,
+                               int(iters), _np_ptr(out), _stream(stream)), h)
+    out[3] = [0.0, 0.0, 0.0, 1.0]
+    return out
+
+
+def map_sync(h, stream=None):
+    _check(_lib.map_sync(h, _stream(stream)), h)
+
+
+def map_get_frame_stats(h, stream=None, check=True) -> dict:
+    out = np.zeros(16, np.int64)
+    st = _lib.map_get_frame_stats(h, _np_ptr(out), _stream(stream))
+    if check:
+        _check(st, h)
+    return dict(zip(MAP_STAT_NAMES, out[:len(MAP_STAT_NAMES)].tolist()))
+
+
+def map_get_blocks(h) -> np.ndarray:
+    cnt = ctypes.c_int64()
+    _check(_lib.map_get_blocks(h, None, 0, ctypes.byref(cnt)), h)
+    n = cnt.value
+    out = np.zeros((max(n, 1), 3), np.int32)
+    _check(_lib.map_get_blocks(h, _np_ptr(out), n, ctypes.byref(cnt)), h)
+    return out[:n]
+
+
+def map_read_blocks(h, coords, n_classes, want_logp=True) -> dict:
+    c = np.ascontiguousarray(coords, np.int32).reshape(-1, 3)
+    n = len(c)
+    out = dict(D=np.zeros((n, BV), np.float32), W=np.zeros((n, BV), np.float32),
+               label=np.zeros((n, BV), np.uint8), found=np.zeros(n, np.uint8))
+    lp = np.zeros((n, n_classes, BV), np.float32) if want_logp else None
+    _check(_lib.map_read_blocks(h, _np_ptr(c), n, _np_ptr(out["D"]), _np_ptr(out["W"]), _np_ptr(lp),
+                                _np_ptr(out["label"]), _np_ptr(out["found"])), h)
+    out["logP"] = lp
+    out["found"] = out["found"].astype(bool)
+    return out
+
+
+def map_write_blocks(h, coords, D, W, logP=None):
+    c = np.ascontiguousarray(coords, np.int32).reshape(-1, 3)
+    D = np.ascontiguousarray(D, np.float32)
+    W = np.ascontiguousarray(W, np.float32)
+    lp = None if logP is None else np.ascontiguousarray(logP, np.float32)
+    _check(_lib.map_write_blocks(h, _np_ptr(c), len(c), _np_ptr(D), _np_ptr(W), _np_ptr(lp)), h)
+
+
+PHASES = ("reset", "range_image", "pixels", "alloc", "integrate", "dirty", "mesh")
+
+
+def map_profile_begin(h, max_frames):
+    _check(_lib.map_profile_begin(h, int(max_frames)), h)
+
+
+def map_profile_end(h, max_frames):
+    """Phase durations [frames, 7] (ms, see PHASES) and per-frame counters [frames, 16]."""
+    out = np.zeros((max(int(max_frames), 1), len(PHASES)), np.float32)
+    st = np.zeros((max(int(max_frames), 1), 16), np.int64)
+    n = ctypes.c_int32()
+    _check(_lib.map_profile_end(h, _np_ptr(out), _np_ptr(st), ctypes.byref(n)), h)
+    return out[:n.value], st[:n.value]
+
+
+def map_last_error(h=None) -> str:
+    s = _lib.map_last_error(h)
+    return s.decode() if s else ""
+
+
+def map_mc_table() -> np.ndarray:
+    t = np.full((256, MC_MAXTRI, 3), -1, np.int8)
+    if _lib.map_mc_table(_np_ptr(t)) != 0:
+        raise MapError(6, "marching-cubes table generation failed")
+    return t
+
+
+def map_palette(n_classes) -> np.ndarray:
+    out = np.zeros((n_classes, 3), np.uint8)
+    if _lib.map_palette(int(n_classes), _np_ptr(out)) != 0:
+        raise MapError(1, "bad class count")
+    return out
+
+
+# --------------------------------------------------------------------------
+# convenience object + autograd
+# --------------------------------------------------------------------------
+class SemanticTSDF:
+    """A map: ``SemanticTSDF(voxel_size, truncation, n_classes, **config)``."""
+
+    def __init__(self, voxel_size=0.1, truncation=0.3, n_classes=20, **cfg):
+        self.cfg = map_config_default(voxel_size=voxel_size, truncation=truncation, n_classes=n_classes, **cfg)
+        self.h = map_create(self.cfg)
+        self.n_classes = n_classes
+
+    def close(self):
+        if getattr(self, "h", None):
+            map_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def integrate(self, lidar, points, T, labels=None, probs=None, stream=None):
+        integrate_scan(self.h, lidar, points, T, labels=labels, probs=probs, stream=stream)
+
+    def integrate_host(self, lidar, points, T, labels=None, probs=None, stream=None):
+        integrate_scan_host(self.h, lidar, points, T, labels=labels, probs=probs, stream=stream)
+
+    def stats(self, stream=None, check=True):
+        return map_get_frame_stats(self.h, stream, check)
+
+    def sync(self, stream=None):
+        map_sync(self.h, stream)
+
+    def blocks(self):
+        return map_get_blocks(self.h)
+
+    def read_blocks(self, coords, want_logp=True):
+        return map_read_blocks(self.h, coords, self.n_classes, want_logp)
+
+    def write_block(self, coord, D, W, logP=None):
+        map_write_blocks(self.h, np.asarray(coord).reshape(1, 3), np.asarray(D).reshape(1, BV),
+                         np.asarray(W).reshape(1, BV), None if logP is None else np.asarray(logP)[None])
+
+    def write_blocks(self, coords, D, W, logP=None):
+        map_write_blocks(self.h, coords, D, W, logP)
+
+    def mesh(self, stream=None):
+        return extract_mesh(self.h, stream)
+
+    def remesh_all(self, stream=None):
+        map_remesh_all(self.h, stream)
+
+    def query(self, xyz, stream=None):
+        return query_sdf(self.h, xyz, stream)
+
+    def align(self, points, T0, iters=20, stream=None):
+        return map_align_scan(self.h, points, T0, iters, stream)
+
+
+class QuerySDF(torch.autograd.Function):
+    """sdf = D(xyz) by trilinear interpolation; backward through the CUDA kernel.
+
+    ``QuerySDF.apply(xyz, tsdf_map)``; invalid queries return NaN with zero
+    gradient.  ``pose_gradient(map, xyz, grad_sdf)`` gives the (rho, phi)
+    left-perturbation gradient of the same backward.
+    """
+
+    @staticmethod
+    def forward(ctx, xyz, tsdf_map):
+        sdf, valid = query_sdf(tsdf_map.h, xyz)
+        ctx.save_for_backward(xyz)
+        ctx.tsdf_map = tsdf_map
+        ctx.mark_non_differentiable(valid)
+        return sdf, valid
+
+    @staticmethod
+    def backward(ctx, grad_sdf, grad_valid):
+        (xyz,) = ctx.saved_tensors
+        g = torch.nan_to_num(grad_sdf, nan=0.0)
+        return query_sdf_backward(ctx.tsdf_map.h, xyz, g), None
+
+
+def pose_gradient(tsdf_map, xyz, grad_sdf):
+    pg = torch.zeros(6, dtype=torch.float64, device=xyz.device)
+    query_sdf_backward(tsdf_map.h, xyz, grad_sdf, pose_grad=pg)
+    return pg

@@ -1,0 +1,210 @@
+// Internal definitions shared by the CUDA kernels and the host orchestration
+// of libsemtsdf.  Not part of the public C ABI (see include/semtsdf.h).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace stsdf {
+
+constexpr int BS = 8;                 // voxels per block side (Sec. III-C.2: 8x8x8 VoxelBlocks)
+constexpr int BV = BS * BS * BS;
+constexpr uint64_t EMPTY_KEY = ~0ull;
+constexpr int MAX_PROBES = 256;       // linear-probing bound of the block hash
+constexpr int MAX_AXIS_CROSS = 4;     // band may cross <= 4 block planes per axis (tau <= 16 nu)
+constexpr int MAX_BAND_BLOCKS = 1 + 3 * MAX_AXIS_CROSS;
+constexpr int MC_MAXTRI = 8;          // triangles per cube case in the generated table
+constexpr int MC_EDGES = 3 * 8 * 9 * 9;  // lattice edges a block's cubes can use (1944)
+constexpr float PI_F = 3.14159265358979f;
+
+// latched device error bits
+enum : unsigned {
+    ERR_POOL_FULL = 1u,
+    ERR_HASH_PROBES = 2u,
+    ERR_LIST_FULL = 4u,
+    ERR_ARENA_FULL = 8u,
+    ERR_TIMEOUT = 16u,
+};
+
+// per-frame counters (indices match MAP_STAT_* of the C ABI)
+enum : int {
+    CT_VALID = 0, CT_PIXEL, CT_TOUCHED, CT_NEW, CT_UPD, CT_SEM, CT_DIRTY, CT_MV, CT_MT,
+    CT_COUNT = 16
+};
+
+// Persistent device scalars of a map.
+struct DevState {
+    unsigned long long pool_count;   // blocks allocated so far
+    unsigned long long arena_v;      // append cursors of the mesh arena
+    unsigned long long arena_t;
+    unsigned int err;                // latched ERR_* bits
+    unsigned int pad;
+};
+
+// Block key: 21 bits per block coordinate, biased by 2^20.
+__host__ __device__ inline uint64_t pack_block(int x, int y, int z) {
+    return ((uint64_t)(uint32_t)(x + (1 << 20)) << 42) | ((uint64_t)(uint32_t)(y + (1 << 20)) << 21) |
+           (uint64_t)(uint32_t)(z + (1 << 20));
+}
+__host__ __device__ inline void unpack_block(uint64_t k, int &x, int &y, int &z) {
+    x = (int)((k >> 42) & 0x1FFFFF) - (1 << 20);
+    y = (int)((k >> 21) & 0x1FFFFF) - (1 << 20);
+    z = (int)(k & 0x1FFFFF) - (1 << 20);
+}
+// MurmurHash3 64-bit finaliser (Appleby), used as the table's hash function.
+__host__ __device__ inline uint64_t fmix64(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdULL;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ULL;
+    k ^= k >> 33;
+    return k;
+}
+// Lattice-edge key of a mesh vertex: axis | x, y, z of its lower voxel, 20 bits each.
+__host__ __device__ inline int64_t edge_key(int x, int y, int z, int axis) {
+    const int64_t b = (int64_t)1 << 19;
+    return (int64_t)axis | (((int64_t)x + b) << 2) | (((int64_t)y + b) << 22) | (((int64_t)z + b) << 42);
+}
+
+// Everything a kernel needs about one scan (passed by value).
+struct ScanConst {
+    int H, W, C, n;
+    float inv_dphi, inv_dtheta, theta0;
+    float r_min, r_max;
+    // band endpoints, IEEE single precision recipe: R / nu and t / nu + 1/2
+    float Rv[9], tv[3], tau;
+    // world-to-LiDAR rotation R^T (row-major), used to find a voxel's pixel
+    float Rt[9];
+    // sensor position in voxel units = k + (fhi + flo), k integer, 0 <= f < 1
+    int k[3];
+    float fhi[3], flo[3];
+    float nu, nu2hi, nu2lo;         // nu and nu^2 as an unevaluated float pair
+    float log_phit, log_pmiss, lik_floor, logp_floor;
+    int weight_mode;
+    int frame;
+    int has_probs;
+};
+
+// Device pointers of one map.
+struct MapDev {
+    uint64_t *keys;      // [cap] block keys, EMPTY_KEY when free
+    int *vals;           // [cap] pool slot of the key (-1: pool was full)
+    int *stamp;          // [cap] last frame the block was touched
+    int *dstamp;         // [cap] last frame the block was queued for meshing
+    uint64_t mask;       // cap - 1
+    int max_blocks;
+    int C;
+    int storage;         // 0 FP32, 1 FP16
+    float2 *dw32;        // [slot][512] {D, W}
+    __half2 *dw16;
+    float *lp32;         // [slot][C][512] log-probabilities, class-major
+    __half *lp16;
+    uint8_t *label;      // [slot][512] most probable class
+    uint64_t *slot_key;  // [slot] block key owning the pool slot
+    int4 *seg;           // [slot] mesh segment: vertex offset, count, triangle offset, count
+    float4 *av;          // mesh arena: vertex {x, y, z, rgb|label bits}
+    int64_t *ak;         // mesh arena: vertex edge keys
+    ushort4 *at;         // mesh arena: triangle {i0, i1, i2, cube anchor (local)}
+    long long av_cap, at_cap;
+    DevState *st;
+    float nu;
+};
+
+// Per-frame scratch of one map.
+struct FrameDev {
+    unsigned long long *win;   // [H*W] (float bits of range << 32) | point index
+    float4 *pix;               // [H*W] {r, r^2 hi, r^2 lo, winner index bits (-1: none)}
+    float *logL;               // [H*W][C] per-pixel class log-likelihood
+    uint8_t *sem_ok;           // [H*W] 1 when the pixel carries a class likelihood
+    int *touched;              // [max_blocks] hash slots of U_k
+    int *dirty;                // [max_blocks] hash slots to re-mesh
+    unsigned long long *ctr;   // [CT_COUNT]
+};
+
+// --- error-free transformations (Knuth TwoSum, Dekker/FMA TwoProduct) ----
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+// (ah + al) + (bh + bl) as an unevaluated pair
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float &sh, float &sl) {
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    sh = __fadd_rn(s, e);
+    sl = __fsub_rn(e, __fsub_rn(sh, s));
+}
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &ph, float &pl) {
+    float p, e;
+    two_prod(ah, bh, p, e);
+    e = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
+    ph = __fadd_rn(p, e);
+    pl = __fsub_rn(e, __fsub_rn(ph, p));
+}
+
+// Range of a point exactly as the allocation recipe defines it.
+__device__ __forceinline__ float range_f32(float x, float y, float z) {
+    float s = __fmul_rn(x, x);
+    s = __fadd_rn(s, __fmul_rn(y, y));
+    s = __fadd_rn(s, __fmul_rn(z, z));
+    return __fsqrt_rn(s);
+}
+
+__device__ __forceinline__ int hash_find(const uint64_t *__restrict__ keys, uint64_t mask, uint64_t key) {
+    uint64_t h = fmix64(key) & mask;
+    for (int p = 0; p < MAX_PROBES; ++p) {
+        uint64_t k = keys[h];
+        if (k == key) return (int)h;
+        if (k == EMPTY_KEY) return -1;
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+// Block-wide exclusive scan of one int per thread (blockDim.x multiple of 32, <= 1024).
+__device__ __forceinline__ int block_exclusive_scan(int v, int *s_warp, int &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) s_warp[lane] = t;   // inclusive warp prefix
+    }
+    __syncthreads();
+    int base = wid > 0 ? s_warp[wid - 1] : 0;
+    total = s_warp[nw - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+// sum over the block, result valid in every thread
+__device__ __forceinline__ long long block_sum(long long v, long long *s_tmp) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_tmp[wid] = v;
+    __syncthreads();
+    long long t = 0;
+    for (int i = 0; i < nw; ++i) t += s_tmp[i];
+    __syncthreads();
+    return t;
+}
+
+}  // namespace stsdf

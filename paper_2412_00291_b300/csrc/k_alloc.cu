@@ -1,0 +1,325 @@
+// Block allocation along each point's truncation band, the touched-block list
+// U_k and the list of blocks to re-mesh; plus pool initialisation and the
+// block read/write helpers.
+//
+// Band of a valid point (range r in [r_min, r_max]): the world segment
+// [p - tau d, p + tau d] (start clipped to the sensor when r < tau), d the
+// ray direction, in "voxel units plus one half" so that block b occupies
+// [8b, 8b + 8) on every axis.  Endpoints and crossing parameters follow a
+// fixed IEEE single-precision recipe (correctly rounded intrinsics, no
+// contraction), which makes the allocated block set reproducible bit for bit.
+#include "kernels.h"
+
+namespace stsdf {
+
+// Blocks met by the band of one point, in path order; returns their count.
+__device__ int band_blocks(const ScanConst &sc, float x0, float x1, float x2, float l, int (*out)[3]) {
+    const float q = __fdiv_rn(sc.tau, l);
+    float f0 = __fsub_rn(1.f, q);
+    if (f0 < 0.f) f0 = 0.f;
+    const float f1 = __fadd_rn(1.f, q);
+    float e0[3], e1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float s = __fmul_rn(sc.Rv[3 * k], x0);
+        s = __fadd_rn(s, __fmul_rn(sc.Rv[3 * k + 1], x1));
+        s = __fadd_rn(s, __fmul_rn(sc.Rv[3 * k + 2], x2));
+        e0[k] = __fadd_rn(sc.tv[k], __fmul_rn(s, f0));
+        e1[k] = __fadd_rn(sc.tv[k], __fmul_rn(s, f1));
+    }
+    // crossing events: parameter, kind (0: entered at t, 1: left after t), axis, step
+    float et[3 * MAX_AXIS_CROSS];
+    int einfo[3 * MAX_AXIS_CROSS];
+    int ne = 0;
+    int cur[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int b0 = (int)floorf(__fmul_rn(e0[k], 0.125f));
+        const int b1 = (int)floorf(__fmul_rn(e1[k], 0.125f));
+        cur[k] = b0;
+        const float d = __fsub_rn(e1[k], e0[k]);
+        if (b1 > b0) {
+            for (int b = b0 + 1, c = 0; b <= b1 && c < MAX_AXIS_CROSS; ++b, ++c) {
+                et[ne] = __fdiv_rn(__fsub_rn((float)(8 * b), e0[k]), d);
+                einfo[ne++] = (0 << 4) | (k << 1) | 1;
+            }
+        } else if (b1 < b0) {
+            for (int b = b0, c = 0; b > b1 && c < MAX_AXIS_CROSS; --b, ++c) {
+                et[ne] = __fdiv_rn(__fsub_rn((float)(8 * b), e0[k]), d);
+                einfo[ne++] = (1 << 4) | (k << 1) | 0;
+            }
+        }
+    }
+    // insertion sort by (t, kind)
+    for (int i = 1; i < ne; ++i) {
+        float t = et[i];
+        int inf = einfo[i];
+        int j = i - 1;
+        while (j >= 0 && (et[j] > t || (et[j] == t && (einfo[j] >> 4) > (inf >> 4)))) {
+            et[j + 1] = et[j];
+            einfo[j + 1] = einfo[j];
+            --j;
+        }
+        et[j + 1] = t;
+        einfo[j + 1] = inf;
+    }
+    int nb = 0;
+    out[nb][0] = cur[0];
+    out[nb][1] = cur[1];
+    out[nb][2] = cur[2];
+    ++nb;
+    for (int i = 0; i < ne;) {
+        int j = i;
+        while (j < ne && et[j] == et[i] && (einfo[j] >> 4) == (einfo[i] >> 4)) {
+            const int ax = (einfo[j] >> 1) & 3;
+            cur[ax] += (einfo[j] & 1) ? 1 : -1;
+            ++j;
+        }
+        out[nb][0] = cur[0];
+        out[nb][1] = cur[1];
+        out[nb][2] = cur[2];
+        ++nb;
+        i = j;
+    }
+    return nb;
+}
+
+// Find or insert a block key; lock-free (compare-and-swap on the key slot).
+// The inserting thread takes the next pool slot; readers of vals[] run in
+// later kernels only, so no thread waits on another.
+__device__ int hash_insert(const MapDev &md, uint64_t key, int &is_new) {
+    uint64_t h = fmix64(key) & md.mask;
+    for (int p = 0; p < MAX_PROBES; ++p) {
+        const uint64_t k = md.keys[h];
+        if (k == key) {
+            is_new = 0;
+            return (int)h;
+        }
+        if (k == EMPTY_KEY) {
+            const uint64_t old = atomicCAS((unsigned long long *)&md.keys[h], EMPTY_KEY, key);
+            if (old == EMPTY_KEY) {
+                const unsigned long long s = atomicAdd(&md.st->pool_count, 1ull);
+                if (s < (unsigned long long)md.max_blocks) {
+                    md.vals[h] = (int)s;
+                } else {
+                    md.vals[h] = -1;
+                    atomicOr(&md.st->err, ERR_POOL_FULL);
+                }
+                is_new = 1;
+                return (int)h;
+            }
+            if (old == key) {
+                is_new = 0;
+                return (int)h;
+            }
+        }
+        h = (h + 1) & md.mask;
+    }
+    atomicOr(&md.st->err, ERR_HASH_PROBES);
+    return -1;
+}
+
+__global__ void __launch_bounds__(256) k_alloc(const float *__restrict__ pts, ScanConst sc, MapDev md, FrameDev fd) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int nb = 0;
+    int blocks[MAX_BAND_BLOCKS][3];
+    if (i < sc.n) {
+        const float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+        if (isfinite(x) && isfinite(y) && isfinite(z)) {
+            const float l = range_f32(x, y, z);
+            if (l >= sc.r_min && l <= sc.r_max && l > 0.f) nb = band_blocks(sc, x, y, z, l, blocks);
+        }
+    }
+    int n_new = 0;
+    for (int j = 0; j < nb; ++j) {
+        const uint64_t key = pack_block(blocks[j][0], blocks[j][1], blocks[j][2]);
+        int is_new = 0;
+        const int h = hash_insert(md, key, is_new);
+        if (h < 0) continue;
+        if (is_new) {
+            ++n_new;
+            const int s = md.vals[h];
+            if (s >= 0) md.slot_key[s] = key;
+        }
+        if (atomicExch(&md.stamp[h], sc.frame) != sc.frame) {
+            const unsigned long long idx = atomicAdd(&fd.ctr[CT_TOUCHED], 1ull);
+            if (idx < (unsigned long long)md.max_blocks) fd.touched[idx] = h;
+            else atomicOr(&md.st->err, ERR_LIST_FULL);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) n_new += __shfl_xor_sync(0xffffffffu, n_new, o);
+    if ((threadIdx.x & 31) == 0 && n_new) atomicAdd(&fd.ctr[CT_NEW], (unsigned long long)n_new);
+}
+
+// Blocks to re-mesh: every touched block b and its neighbours b - e,
+// e in {0,1}^3 \ 0 (their cubes reach into b), when allocated.
+__global__ void __launch_bounds__(256) k_dirty(ScanConst sc, MapDev md, FrameDev fd) {
+    unsigned long long nt = *(volatile unsigned long long *)&fd.ctr[CT_TOUCHED];
+    if (nt > (unsigned long long)md.max_blocks) nt = md.max_blocks;
+    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < nt * 8;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+        const int h = fd.touched[e >> 3];
+        const int o = (int)(e & 7);
+        int hh = h;
+        if (o) {
+            int x, y, z;
+            unpack_block(md.keys[h], x, y, z);
+            hh = hash_find(md.keys, md.mask, pack_block(x - (o & 1), y - ((o >> 1) & 1), z - ((o >> 2) & 1)));
+            if (hh < 0) continue;
+        }
+        if (md.vals[hh] < 0) continue;
+        if (atomicExch(&md.dstamp[hh], sc.frame) != sc.frame) {
+            const unsigned long long idx = atomicAdd(&fd.ctr[CT_DIRTY], 1ull);
+            if (idx < (unsigned long long)md.max_blocks) fd.dirty[idx] = hh;
+            else atomicOr(&md.st->err, ERR_LIST_FULL);
+        }
+    }
+}
+
+// Every allocated block into the dirty list (full re-mesh).
+__global__ void k_list_all(MapDev md, FrameDev fd) {
+    for (unsigned long long h = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; h <= md.mask;
+         h += (unsigned long long)gridDim.x * blockDim.x) {
+        if (md.keys[h] == EMPTY_KEY || md.vals[h] < 0) continue;
+        const unsigned long long idx = atomicAdd(&fd.ctr[CT_DIRTY], 1ull);
+        if (idx < (unsigned long long)md.max_blocks) fd.dirty[idx] = (int)h;
+    }
+}
+
+// D = 0, W = 0, uniform class distribution, label 0, empty mesh segment.
+__global__ void k_init_pool(MapDev md) {
+    const long long nvox = (long long)md.max_blocks * BV;
+    const float lp0 = -logf((float)md.C);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nvox;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (md.storage == 0) md.dw32[i] = make_float2(0.f, 0.f);
+        else md.dw16[i] = __floats2half2_rn(0.f, 0.f);
+        md.label[i] = 0;
+        const long long slot = i / BV, v = i - slot * BV;
+        for (int c = 0; c < md.C; ++c) {
+            const long long j = (slot * md.C + c) * BV + v;
+            if (md.storage == 0) md.lp32[j] = lp0;
+            else md.lp16[j] = __float2half_rn(lp0);
+        }
+        if (v == 0) md.seg[slot] = make_int4(0, 0, 0, 0);
+    }
+}
+
+// Write one block (host test fixtures / checkpoint load); allocates it when new.
+__global__ void k_write_block(MapDev md, uint64_t key, const float *D, const float *W, const float *logP) {
+    __shared__ int s_slot;
+    if (threadIdx.x == 0) {
+        int is_new = 0;
+        const int h = hash_insert(md, key, is_new);
+        s_slot = h < 0 ? -1 : md.vals[h];
+        if (s_slot >= 0) md.slot_key[s_slot] = key;
+    }
+    __syncthreads();
+    const int slot = s_slot;
+    if (slot < 0) return;
+    for (int v = threadIdx.x; v < BV; v += blockDim.x) {
+        const long long vox = (long long)slot * BV + v;
+        if (md.storage == 0) md.dw32[vox] = make_float2(D[v], W[v]);
+        else md.dw16[vox] = __floats2half2_rn(D[v], W[v]);
+        int best = 0;
+        float bv = -INFINITY;
+        for (int c = 0; c < md.C; ++c) {
+            const float lp = logP ? logP[c * BV + v] : -logf((float)md.C);
+            const long long j = ((long long)slot * md.C + c) * BV + v;
+            if (md.storage == 0) md.lp32[j] = lp;
+            else md.lp16[j] = __float2half_rn(lp);
+            const float stored = md.storage == 0 ? lp : __half2float(__float2half_rn(lp));
+            if (stored > bv) {
+                bv = stored;
+                best = c;
+            }
+        }
+        md.label[vox] = (uint8_t)best;
+    }
+}
+
+__global__ void k_read_blocks(MapDev md, const uint64_t *keys, int n, float *D, float *W, float *logP,
+                              uint8_t *label, uint8_t *found) {
+    const int b = blockIdx.x;
+    if (b >= n) return;
+    __shared__ int s_slot;
+    if (threadIdx.x == 0) {
+        const int h = hash_find(md.keys, md.mask, keys[b]);
+        s_slot = h < 0 ? -1 : md.vals[h];
+        if (found) found[b] = s_slot >= 0;
+    }
+    __syncthreads();
+    const int slot = s_slot;
+    for (int v = threadIdx.x; v < BV; v += blockDim.x) {
+        const long long o = (long long)b * BV + v;
+        float d = 0.f, w = 0.f;
+        if (slot >= 0) {
+            const long long vox = (long long)slot * BV + v;
+            if (md.storage == 0) {
+                const float2 q = md.dw32[vox];
+                d = q.x;
+                w = q.y;
+            } else {
+                const float2 q = __half22float2(md.dw16[vox]);
+                d = q.x;
+                w = q.y;
+            }
+            if (label) label[o] = md.label[vox];
+        } else if (label) {
+            label[o] = 0;
+        }
+        if (D) D[o] = d;
+        if (W) W[o] = w;
+        if (logP) {
+            for (int c = 0; c < md.C; ++c) {
+                float lp = -logf((float)md.C);
+                if (slot >= 0) {
+                    const long long j = ((long long)slot * md.C + c) * BV + v;
+                    lp = md.storage == 0 ? md.lp32[j] : __half2float(md.lp16[j]);
+                }
+                logP[((long long)b * md.C + c) * BV + v] = lp;
+            }
+        }
+    }
+}
+
+__global__ void k_collect_blocks(MapDev md, int32_t *coords, unsigned long long *count) {
+    for (unsigned long long h = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; h <= md.mask;
+         h += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint64_t k = md.keys[h];
+        if (k == EMPTY_KEY || md.vals[h] < 0) continue;
+        const unsigned long long i = atomicAdd(count, 1ull);
+        if (coords && i < (unsigned long long)md.max_blocks) {
+            int x, y, z;
+            unpack_block(k, x, y, z);
+            coords[3 * i] = x;
+            coords[3 * i + 1] = y;
+            coords[3 * i + 2] = z;
+        }
+    }
+}
+
+void launch_alloc(const float *pts, const ScanConst &sc, const MapDev &md, const FrameDev &fd, cudaStream_t s) {
+    if (sc.n <= 0) return;
+    k_alloc<<<(unsigned)((sc.n + 255) / 256), 256, 0, s>>>(pts, sc, md, fd);
+}
+void launch_dirty(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s) {
+    k_dirty<<<grid, 256, 0, s>>>(sc, md, fd);
+}
+void launch_list_all(const MapDev &md, const FrameDev &fd, int, cudaStream_t s) {
+    k_list_all<<<1024, 256, 0, s>>>(md, fd);
+}
+void launch_init_pool(const MapDev &md, cudaStream_t s) { k_init_pool<<<2048, 256, 0, s>>>(md); }
+void launch_write_block(const MapDev &md, uint64_t key, const float *D, const float *W, const float *logP,
+                        cudaStream_t s) {
+    k_write_block<<<1, 256, 0, s>>>(md, key, D, W, logP);
+}
+void launch_read_blocks(const MapDev &md, const uint64_t *keys, int n, float *D, float *W, float *logP,
+                        uint8_t *label, uint8_t *found, cudaStream_t s) {
+    if (n > 0) k_read_blocks<<<n, 256, 0, s>>>(md, keys, n, D, W, logP, label, found);
+}
+void launch_collect_blocks(const MapDev &md, int32_t *coords, unsigned long long *count, cudaStream_t s) {
+    k_collect_blocks<<<1024, 256, 0, s>>>(md, coords, count);
+}
+
+}  // namespace stsdf

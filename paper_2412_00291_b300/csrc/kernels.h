@@ -1,0 +1,52 @@
+// Launchers of the CUDA kernels (host side), one per kernel file.
+#pragma once
+
+#include "common.cuh"
+
+namespace stsdf {
+
+// k_scan.cu: measurement preprocessing (Sec. III-C.1)
+void launch_range_image(const float *pts, const ScanConst &sc, const FrameDev &fd, cudaStream_t s);
+void launch_pixels(const float *pts, const int32_t *labels, const float *probs, const ScanConst &sc,
+                   const FrameDev &fd, cudaStream_t s);
+
+// k_alloc.cu: band allocation, touched and dirty lists
+void launch_alloc(const float *pts, const ScanConst &sc, const MapDev &md, const FrameDev &fd, cudaStream_t s);
+void launch_dirty(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s);
+void launch_list_all(const MapDev &md, const FrameDev &fd, int frame, cudaStream_t s);
+void launch_init_pool(const MapDev &md, cudaStream_t s);
+void launch_write_block(const MapDev &md, uint64_t key, const float *D, const float *W, const float *logP,
+                        cudaStream_t s);
+void launch_read_blocks(const MapDev &md, const uint64_t *keys, int n, float *D, float *W, float *logP,
+                        uint8_t *label, uint8_t *found, cudaStream_t s);
+void launch_collect_blocks(const MapDev &md, int32_t *coords, unsigned long long *count, cudaStream_t s);
+
+// k_integrate.cu: projective TSDF + Bayesian semantic fusion (Sec. III-C.2, III-C.3)
+void launch_integrate(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s);
+int integrate_blocks_per_sm(int storage, int C);
+
+// k_mesh.cu: incremental marching cubes and mesh gathering
+int mesh_upload_tables(const int8_t *tri, const uint8_t *ntri);
+void launch_mesh(const MapDev &md, const FrameDev &fd, const uchar4 *palette, int grid, cudaStream_t s);
+int mesh_blocks_per_sm();
+struct GatherBufs {
+    long long *voff, *toff;          // [max_blocks] per-slot exclusive offsets within a chunk
+    long long *bsum_v, *bsum_t;      // [chunks]
+    long long *totals;               // [2]
+};
+void launch_seg_scan(const MapDev &md, const GatherBufs &g, int max_blocks, cudaStream_t s);
+// mode 0: compact into (av2, ak2, at2) and rewrite seg; mode 1: write the user mesh arrays
+void launch_seg_gather(const MapDev &md, const GatherBufs &g, int max_blocks, int mode, float4 *av2,
+                       int64_t *ak2, ushort4 *at2, float *pos, uint8_t *col, int64_t *keys, int32_t *tri,
+                       int32_t *anchors, cudaStream_t s);
+void launch_set_cursors(const MapDev &md, const GatherBufs &g, cudaStream_t s);
+
+// k_query.cu: trilinear queries, gradients, Gauss-Newton
+void launch_query(const MapDev &md, const float *xyz, long long m, float *sdf, uint8_t *valid, cudaStream_t s);
+void launch_query_bwd(const MapDev &md, const float *xyz, const float *gsdf, long long m, float *gxyz,
+                      double *pose_grad, cudaStream_t s);
+void launch_gn_terms(const MapDev &md, const float *pts, long long n, const double *T_dev, double *acc,
+                     cudaStream_t s);
+void launch_gn_step(double *T_dev, double *acc, cudaStream_t s);
+
+}  // namespace stsdf

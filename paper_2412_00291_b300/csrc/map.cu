@@ -1,0 +1,691 @@
+// C ABI of libsemtsdf: map lifetime, per-frame orchestration on the caller's
+// stream, mesh extraction, queries, alignment and host inspection helpers.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/semtsdf.h"
+#include "kernels.h"
+
+using namespace stsdf;
+
+struct map_t {
+    map_config cfg;
+    int C = 0;
+    MapDev md{};
+    FrameDev fd{};
+    DevState *st = nullptr;
+    // second mesh arena for compaction
+    float4 *av_alt = nullptr;
+    int64_t *ak_alt = nullptr;
+    ushort4 *at_alt = nullptr;
+    GatherBufs gb{};
+    int nchunks = 0;
+    // host views (pinned) of the last frame's counters and device state
+    unsigned long long *h_ctr = nullptr;
+    DevState *h_st = nullptr;
+    long long *h_totals = nullptr;
+    cudaEvent_t ev_stats = nullptr;
+    bool stats_pending = false;
+    unsigned long long known_arena_v = 0, known_arena_t = 0;
+    // staging for host inputs
+    float *stage_pts = nullptr;
+    int32_t *stage_lab = nullptr;
+    float *stage_probs = nullptr;
+    // extracted mesh
+    long long out_vcap = 0, out_tcap = 0;
+    float *out_pos = nullptr;
+    uint8_t *out_col = nullptr;
+    int64_t *out_keys = nullptr;
+    int32_t *out_tri = nullptr;
+    int32_t *out_anchor = nullptr;
+    // class palette (rgb per class, on the device as uchar4)
+    uint8_t palette[256 * 3];
+    uchar4 *pal_dev = nullptr;
+    // alignment scratch
+    double *gn_T = nullptr, *gn_acc = nullptr;
+    int frame = 0;
+    int grid_integrate = 0, grid_mesh = 0, grid_dirty = 0;
+    // phase profiling: (MAP_PHASE_COUNT + 1) events per recorded frame
+    std::vector<cudaEvent_t> prof_ev;
+    int prof_cap = 0, prof_n = 0;
+    unsigned long long *prof_stats = nullptr;   // device [prof_cap][CT_COUNT]
+    long long launches = 0;                     // kernels launched by this map
+    std::string err;
+};
+
+static std::string g_err;
+
+static map_status fail(map_t *m, map_status s, const std::string &msg) {
+    if (m) m->err = msg;
+    else g_err = msg;
+    return s;
+}
+
+#define CU(call)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail(m, MAP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    } while (0)
+
+static map_status launch_check(map_t *m, const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(m, MAP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return MAP_OK;
+}
+
+extern "C" map_status map_config_default(map_config *cfg) {
+    if (!cfg) return fail(nullptr, MAP_ERR_ARG, "null config");
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->voxel_size = 0.1;
+    cfg->truncation = 0.3;
+    cfg->n_classes = 20;
+    cfg->weight_mode = 0;
+    cfg->p_hit = 0.9;
+    cfg->logp_floor = -30.0;
+    cfg->lik_floor = 1e-6;
+    cfg->storage = 0;
+    cfg->max_blocks = 262144;
+    cfg->hash_capacity = 1 << 20;
+    cfg->max_points = 262144;
+    cfg->max_pixels = 262144;
+    cfg->mesh_vertex_capacity = 32ll << 20;
+    cfg->mesh_triangle_capacity = 64ll << 20;
+    return MAP_OK;
+}
+
+static void prof_clear(map_t *m) {
+    for (cudaEvent_t e : m->prof_ev) cudaEventDestroy(e);
+    m->prof_ev.clear();
+    if (m->prof_stats) cudaFree(m->prof_stats);
+    m->prof_stats = nullptr;
+    m->prof_cap = m->prof_n = 0;
+}
+
+static void free_all(map_t *m) {
+    prof_clear(m);
+    void *ptrs[] = {m->md.keys, m->md.vals, m->md.stamp, m->md.dstamp, m->md.dw32, m->md.dw16, m->md.lp32,
+                    m->md.lp16, m->md.label, m->md.slot_key, m->md.seg, m->md.av, m->md.ak, m->md.at,
+                    m->av_alt, m->ak_alt, m->at_alt, m->st, m->fd.win, m->fd.pix, m->fd.logL, m->fd.sem_ok,
+                    m->fd.touched, m->fd.dirty, m->fd.ctr, m->gb.voff, m->gb.toff, m->gb.bsum_v, m->gb.bsum_t,
+                    m->gb.totals, m->stage_pts, m->stage_lab, m->stage_probs, m->out_pos, m->out_col,
+                    m->out_keys, m->out_tri, m->out_anchor, m->gn_T, m->gn_acc, m->pal_dev};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (m->h_ctr) cudaFreeHost(m->h_ctr);
+    if (m->h_st) cudaFreeHost(m->h_st);
+    if (m->h_totals) cudaFreeHost(m->h_totals);
+    if (m->ev_stats) cudaEventDestroy(m->ev_stats);
+}
+
+template <typename T>
+static cudaError_t dalloc(T **p, size_t count) {
+    return cudaMalloc((void **)p, count * sizeof(T) + 16);
+}
+
+extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
+    map_t *m = nullptr;
+    if (!cfg_in || !out) return fail(nullptr, MAP_ERR_ARG, "null argument");
+    const map_config &c = *cfg_in;
+    if (!(c.voxel_size > 0.0) || !(c.truncation > 0.0) || c.truncation > 15.0 * c.voxel_size)
+        return fail(nullptr, MAP_ERR_ARG, "need 0 < truncation <= 15 voxel_size");
+    if (c.n_classes < 2 || c.n_classes > 64) return fail(nullptr, MAP_ERR_ARG, "n_classes must be in [2, 64]");
+    if (c.weight_mode < 0 || c.weight_mode > 1 || c.storage < 0 || c.storage > 1)
+        return fail(nullptr, MAP_ERR_ARG, "bad weight_mode or storage");
+    if (!(c.p_hit > 0.0 && c.p_hit < 1.0) || !(c.lik_floor > 0.0))
+        return fail(nullptr, MAP_ERR_ARG, "need 0 < p_hit < 1 and lik_floor > 0");
+    if (c.max_blocks < 1 || c.max_blocks > (1ll << 24) || c.hash_capacity < 2 || c.max_points < 1 ||
+        c.max_pixels < 1 || c.max_points > (1ll << 31) - 1 || c.mesh_vertex_capacity < 1 ||
+        c.mesh_triangle_capacity < 1 || c.mesh_vertex_capacity > (1ll << 31) - 1 ||
+        c.mesh_triangle_capacity > (1ll << 31) - 1)
+        return fail(nullptr, MAP_ERR_ARG, "capacity out of range");
+    if (map_mc_table(nullptr) != 0) return fail(nullptr, MAP_ERR_STATE, "marching-cubes table generation failed");
+
+    m = new map_t();
+    m->cfg = c;
+    m->C = c.n_classes;
+    uint64_t cap = 1;
+    while (cap < (uint64_t)c.hash_capacity) cap <<= 1;
+    if ((long long)cap < 2 * c.max_blocks) {
+        while ((long long)cap < 2 * c.max_blocks) cap <<= 1;
+    }
+    m->cfg.hash_capacity = (int64_t)cap;
+    const long long nb = c.max_blocks, nvox = nb * BV;
+    MapDev &md = m->md;
+    md.mask = cap - 1;
+    md.max_blocks = (int)nb;
+    md.C = c.n_classes;
+    md.storage = c.storage;
+    md.nu = (float)c.voxel_size;
+    md.av_cap = c.mesh_vertex_capacity;
+    md.at_cap = c.mesh_triangle_capacity;
+    cudaError_t e = cudaSuccess;
+#define ALLOC(p, n)                                                                    \
+    do {                                                                               \
+        e = dalloc(&(p), (size_t)(n));                                                 \
+        if (e != cudaSuccess) {                                                        \
+            std::string msg = std::string("device allocation failed: ") + #p;         \
+            free_all(m);                                                               \
+            delete m;                                                                  \
+            return fail(nullptr, MAP_ERR_NOMEM, msg);                                  \
+        }                                                                              \
+    } while (0)
+    ALLOC(md.keys, cap);
+    ALLOC(md.vals, cap);
+    ALLOC(md.stamp, cap);
+    ALLOC(md.dstamp, cap);
+    if (c.storage == 0) {
+        ALLOC(md.dw32, nvox);
+        ALLOC(md.lp32, nvox * c.n_classes);
+    } else {
+        ALLOC(md.dw16, nvox);
+        ALLOC(md.lp16, nvox * c.n_classes);
+    }
+    ALLOC(md.label, nvox);
+    ALLOC(md.slot_key, nb);
+    ALLOC(md.seg, nb);
+    ALLOC(md.av, c.mesh_vertex_capacity);
+    ALLOC(md.ak, c.mesh_vertex_capacity);
+    ALLOC(md.at, c.mesh_triangle_capacity);
+    ALLOC(m->av_alt, c.mesh_vertex_capacity);
+    ALLOC(m->ak_alt, c.mesh_vertex_capacity);
+    ALLOC(m->at_alt, c.mesh_triangle_capacity);
+    ALLOC(m->st, 1);
+    md.st = m->st;
+    FrameDev &fd = m->fd;
+    ALLOC(fd.win, c.max_pixels);
+    ALLOC(fd.pix, c.max_pixels);
+    ALLOC(fd.logL, c.max_pixels * c.n_classes);
+    ALLOC(fd.sem_ok, c.max_pixels);
+    ALLOC(fd.touched, nb);
+    ALLOC(fd.dirty, nb);
+    ALLOC(fd.ctr, CT_COUNT);
+    m->nchunks = (int)((nb + 1023) / 1024);
+    ALLOC(m->gb.voff, nb);
+    ALLOC(m->gb.toff, nb);
+    ALLOC(m->gb.bsum_v, m->nchunks);
+    ALLOC(m->gb.bsum_t, m->nchunks);
+    ALLOC(m->gb.totals, 2);
+    ALLOC(m->gn_T, 16);
+    ALLOC(m->gn_acc, 32);
+    ALLOC(m->pal_dev, 256);
+#undef ALLOC
+    if (cudaMallocHost(&m->h_ctr, CT_COUNT * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&m->h_st, sizeof(DevState)) != cudaSuccess ||
+        cudaMallocHost(&m->h_totals, 2 * sizeof(long long)) != cudaSuccess) {
+        free_all(m);
+        delete m;
+        return fail(nullptr, MAP_ERR_NOMEM, "pinned host allocation failed");
+    }
+    std::memset(m->h_ctr, 0, CT_COUNT * sizeof(unsigned long long));
+    std::memset(m->h_st, 0, sizeof(DevState));
+    cudaEventCreateWithFlags(&m->ev_stats, cudaEventDisableTiming);
+
+    cudaStream_t s = 0;
+    cudaMemsetAsync(md.keys, 0xFF, cap * sizeof(uint64_t), s);
+    cudaMemsetAsync(md.vals, 0xFF, cap * sizeof(int), s);
+    cudaMemsetAsync(md.stamp, 0xFF, cap * sizeof(int), s);
+    cudaMemsetAsync(md.dstamp, 0xFF, cap * sizeof(int), s);
+    cudaMemsetAsync(m->st, 0, sizeof(DevState), s);
+    cudaMemsetAsync(fd.ctr, 0, CT_COUNT * sizeof(unsigned long long), s);
+    cudaMemsetAsync(m->gn_acc, 0, 32 * sizeof(double), s);
+    launch_init_pool(md, s);
+    // tables
+    std::vector<int8_t> tri(256 * MAP_MC_MAXTRI * 3);
+    map_mc_table(tri.data());
+    std::vector<uint8_t> ntri(256, 0);
+    for (int cs = 0; cs < 256; ++cs)
+        for (int j = 0; j < MAP_MC_MAXTRI; ++j)
+            if (tri[(cs * MAP_MC_MAXTRI + j) * 3] >= 0) ntri[cs] = (uint8_t)(j + 1);
+    map_palette(c.n_classes, m->palette);
+    {
+        std::vector<uchar4> pal(256, make_uchar4(0, 0, 0, 0));
+        for (int l = 0; l < c.n_classes; ++l)
+            pal[l] = make_uchar4(m->palette[3 * l], m->palette[3 * l + 1], m->palette[3 * l + 2], 0);
+        cudaMemcpy(m->pal_dev, pal.data(), 256 * sizeof(uchar4), cudaMemcpyHostToDevice);
+    }
+    if (mesh_upload_tables(tri.data(), ntri.data()) != 0) {
+        free_all(m);
+        delete m;
+        return fail(nullptr, MAP_ERR_CUDA, "marching-cubes table upload failed");
+    }
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    m->grid_integrate = sms * integrate_blocks_per_sm(c.storage, c.n_classes);
+    m->grid_mesh = sms * mesh_blocks_per_sm();
+    m->grid_dirty = sms * 4;
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        std::string msg = std::string("map initialisation failed: ") + cudaGetErrorString(e);
+        free_all(m);
+        delete m;
+        return fail(nullptr, MAP_ERR_CUDA, msg);
+    }
+    *out = m;
+    return MAP_OK;
+}
+
+extern "C" map_status map_destroy(map_t *m) {
+    if (!m) return fail(nullptr, MAP_ERR_ARG, "null map");
+    cudaDeviceSynchronize();
+    free_all(m);
+    delete m;
+    return MAP_OK;
+}
+
+static map_status make_scan_const(map_t *m, const lidar_intrinsics *L, int64_t n, const double *T, int has_probs,
+                                  ScanConst &sc) {
+    if (!L || !T) return fail(m, MAP_ERR_ARG, "null intrinsics or pose");
+    if (L->H < 2 || L->W < 1 || (long long)L->H * L->W > m->cfg.max_pixels)
+        return fail(m, MAP_ERR_ARG, "H * W out of range (H >= 2, H * W <= max_pixels)");
+    if (n < 0 || n > m->cfg.max_points) return fail(m, MAP_ERR_ARG, "n out of range (<= max_points)");
+    if (!(L->fov_up > L->fov_down) || !(L->r_max > L->r_min) || !(L->r_min >= 0.0))
+        return fail(m, MAP_ERR_ARG, "need fov_up > fov_down and 0 <= r_min < r_max");
+    double R[9], t[3];
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) R[3 * r + c] = T[4 * r + c];
+        t[r] = T[4 * r + 3];
+    }
+    for (int i = 0; i < 16; ++i)
+        if (!std::isfinite(T[i])) return fail(m, MAP_ERR_BAD_POSE, "non-finite pose");
+    // R^T R = I, det R = +1, last row (0, 0, 0, 1)
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += R[3 * k + a] * R[3 * k + b];
+            if (std::fabs(s - (a == b ? 1.0 : 0.0)) > 1e-6) return fail(m, MAP_ERR_BAD_POSE, "rotation not orthonormal");
+        }
+    const double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
+                       R[2] * (R[3] * R[7] - R[4] * R[6]);
+    if (det < 0.0 || T[12] != 0.0 || T[13] != 0.0 || T[14] != 0.0 || T[15] != 1.0)
+        return fail(m, MAP_ERR_BAD_POSE, "not a proper rigid transform");
+    const double nu = m->cfg.voxel_size, tau = m->cfg.truncation;
+    const double dtheta = (L->fov_up - L->fov_down) / (L->H - 1);
+    std::memset(&sc, 0, sizeof(sc));
+    sc.H = L->H;
+    sc.W = L->W;
+    sc.C = m->C;
+    sc.n = (int)n;
+    sc.inv_dphi = (float)(L->W / (2.0 * M_PI));
+    sc.inv_dtheta = (float)(1.0 / dtheta);
+    sc.theta0 = (float)(M_PI / 2.0 - L->fov_up);
+    sc.r_min = (float)L->r_min;
+    sc.r_max = (float)L->r_max;
+    for (int i = 0; i < 9; ++i) sc.Rv[i] = (float)(R[i] / nu);
+    for (int k = 0; k < 3; ++k) sc.tv[k] = (float)(t[k] / nu + 0.5);
+    sc.tau = (float)tau;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) sc.Rt[3 * r + c] = (float)R[3 * c + r];
+    for (int k = 0; k < 3; ++k) {
+        const double tv = t[k] / nu;
+        const double fl = std::floor(tv);
+        const double f = tv - fl;
+        sc.k[k] = (int)fl;
+        sc.fhi[k] = (float)f;
+        sc.flo[k] = (float)(f - (double)sc.fhi[k]);
+    }
+    const double nu2 = nu * nu;
+    sc.nu = (float)nu;
+    sc.nu2hi = (float)nu2;
+    sc.nu2lo = (float)(nu2 - (double)sc.nu2hi);
+    sc.log_phit = (float)std::log(m->cfg.p_hit);
+    sc.log_pmiss = (float)std::log((1.0 - m->cfg.p_hit) / (m->C - 1));
+    sc.lik_floor = (float)m->cfg.lik_floor;
+    sc.logp_floor = (float)m->cfg.logp_floor;
+    sc.weight_mode = m->cfg.weight_mode;
+    sc.frame = m->frame;
+    sc.has_probs = has_probs;
+    return MAP_OK;
+}
+
+// Refresh the host's view of the device counters when the last async copy is done.
+static void poll_stats(map_t *m) {
+    if (m->stats_pending && cudaEventQuery(m->ev_stats) == cudaSuccess) {
+        m->known_arena_v = m->h_st->arena_v;
+        m->known_arena_t = m->h_st->arena_t;
+        m->stats_pending = false;
+    }
+}
+
+static map_status compact_arena(map_t *m, cudaStream_t s) {
+    m->launches += 4;
+    launch_seg_scan(m->md, m->gb, m->md.max_blocks, s);
+    launch_seg_gather(m->md, m->gb, m->md.max_blocks, 0, m->av_alt, m->ak_alt, m->at_alt, nullptr, nullptr, nullptr,
+                      nullptr, nullptr, s);
+    launch_set_cursors(m->md, m->gb, s);
+    std::swap(m->md.av, m->av_alt);
+    std::swap(m->md.ak, m->ak_alt);
+    std::swap(m->md.at, m->at_alt);
+    m->known_arena_v = 0;
+    m->known_arena_t = 0;
+    return launch_check(m, "arena compaction");
+}
+
+static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pts, const int32_t *labels,
+                            const float *probs, int64_t n, const double *T, cudaStream_t s) {
+    ScanConst sc;
+    map_status st = make_scan_const(m, L, n, T, probs != nullptr, sc);
+    if (st != MAP_OK) return st;
+    poll_stats(m);
+    if (m->known_arena_v * 2 > (unsigned long long)m->md.av_cap ||
+        m->known_arena_t * 2 > (unsigned long long)m->md.at_cap) {
+        st = compact_arena(m, s);
+        if (st != MAP_OK) return st;
+    }
+    const long long np = (long long)L->H * L->W;
+    cudaEvent_t *ev = nullptr;
+    unsigned long long *ev_stats = nullptr;
+    if (m->prof_n < m->prof_cap) {
+        ev_stats = m->prof_stats + (size_t)m->prof_n * CT_COUNT;
+        ev = &m->prof_ev[(size_t)m->prof_n++ * (MAP_PHASE_COUNT + 1)];
+    }
+    if (ev) CU(cudaEventRecord(ev[0], s));
+    CU(cudaMemsetAsync(m->fd.win, 0xFF, np * sizeof(unsigned long long), s));
+    CU(cudaMemsetAsync(m->fd.ctr, 0, CT_COUNT * sizeof(unsigned long long), s));
+    if (ev) CU(cudaEventRecord(ev[1], s));
+    launch_range_image(pts, sc, m->fd, s);
+    if (ev) CU(cudaEventRecord(ev[2], s));
+    launch_pixels(pts, labels, probs, sc, m->fd, s);
+    if (ev) CU(cudaEventRecord(ev[3], s));
+    launch_alloc(pts, sc, m->md, m->fd, s);
+    if (ev) CU(cudaEventRecord(ev[4], s));
+    launch_integrate(sc, m->md, m->fd, m->grid_integrate, s);
+    if (ev) CU(cudaEventRecord(ev[5], s));
+    launch_dirty(sc, m->md, m->fd, m->grid_dirty, s);
+    if (ev) CU(cudaEventRecord(ev[6], s));
+    launch_mesh(m->md, m->fd, m->pal_dev, m->grid_mesh, s);
+    if (ev) CU(cudaEventRecord(ev[7], s));
+    m->launches += 7;
+    if (ev_stats)
+        CU(cudaMemcpyAsync(ev_stats, m->fd.ctr, CT_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+    st = launch_check(m, "integrate_scan kernels");
+    if (st != MAP_OK) return st;
+    CU(cudaMemcpyAsync(m->h_ctr, m->fd.ctr, CT_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(m->h_st, m->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CU(cudaEventRecord(m->ev_stats, s));
+    m->stats_pending = true;
+    m->frame++;
+    return MAP_OK;
+}
+
+extern "C" map_status integrate_scan(map_t *m, const lidar_intrinsics *L, const float *points_dev,
+                                     const int32_t *labels_dev, const float *probs_dev, int64_t n,
+                                     const double T_world_lidar[16], void *stream) {
+    if (!m) return fail(nullptr, MAP_ERR_ARG, "null map");
+    if (n > 0 && (!points_dev || ((labels_dev == nullptr) == (probs_dev == nullptr))))
+        return fail(m, MAP_ERR_ARG, "need points and exactly one of labels / probs");
+    return run_frame(m, L, points_dev, labels_dev, probs_dev, n, T_world_lidar, (cudaStream_t)stream);
+}
+
+extern "C" map_status integrate_scan_host(map_t *m, const lidar_intrinsics *L, const float *points_host,
+                                          const int32_t *labels_host, const float *probs_host, int64_t n,
+                                          const double T_world_lidar[16], void *stream) {
+    if (!m) return fail(nullptr, MAP_ERR_ARG, "null map");
+    if (n > 0 && (!points_host || ((labels_host == nullptr) == (probs_host == nullptr))))
+        return fail(m, MAP_ERR_ARG, "need points and exactly one of labels / probs");
+    if (n < 0 || n > m->cfg.max_points) return fail(m, MAP_ERR_ARG, "n out of range (<= max_points)");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long cap = m->cfg.max_points;
+    if (!m->stage_pts) CU(cudaMalloc(&m->stage_pts, cap * 3 * sizeof(float)));
+    if (labels_host && !m->stage_lab) CU(cudaMalloc(&m->stage_lab, cap * sizeof(int32_t)));
+    if (probs_host && !m->stage_probs) CU(cudaMalloc(&m->stage_probs, cap * m->C * sizeof(float)));
+    if (n > 0) {
+        CU(cudaMemcpyAsync(m->stage_pts, points_host, n * 3 * sizeof(float), cudaMemcpyHostToDevice, s));
+        if (labels_host)
+            CU(cudaMemcpyAsync(m->stage_lab, labels_host, n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        else
+            CU(cudaMemcpyAsync(m->stage_probs, probs_host, n * m->C * sizeof(float), cudaMemcpyHostToDevice, s));
+    }
+    return run_frame(m, L, m->stage_pts, labels_host ? m->stage_lab : nullptr, probs_host ? m->stage_probs : nullptr,
+                     n, T_world_lidar, s);
+}
+
+extern "C" map_status map_remesh_all(map_t *m, void *stream) {
+    if (!m) return fail(nullptr, MAP_ERR_ARG, "null map");
+    cudaStream_t s = (cudaStream_t)stream;
+    map_status st = compact_arena(m, s);
+    if (st != MAP_OK) return st;
+    CU(cudaMemsetAsync(m->fd.ctr, 0, CT_COUNT * sizeof(unsigned long long), s));
+    launch_list_all(m->md, m->fd, m->frame, s);
+    launch_mesh(m->md, m->fd, m->pal_dev, m->grid_mesh, s);
+    m->launches += 2;
+    st = launch_check(m, "map_remesh_all");
+    if (st != MAP_OK) return st;
+    CU(cudaMemcpyAsync(m->h_st, m->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CU(cudaEventRecord(m->ev_stats, s));
+    m->stats_pending = true;
+    return MAP_OK;
+}
+
+static map_status device_errors(map_t *m) {
+    if (m->h_st->err & ERR_TIMEOUT) return fail(m, MAP_ERR_TIMEOUT, "a device-side wait gave up");
+    if (m->h_st->err) {
+        char buf[128];
+        std::snprintf(buf, sizeof buf, "device capacity exceeded (error bits 0x%x)", m->h_st->err);
+        return fail(m, MAP_ERR_CAPACITY, buf);
+    }
+    return MAP_OK;
+}
+
+extern "C" map_status map_sync(map_t *m, void *stream) {
+    if (!m) return fail(nullptr, MAP_ERR_ARG, "null map");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaMemcpyAsync(m->h_st, m->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    m->known_arena_v = m->h_st->arena_v;
+    m->known_arena_t = m->h_st->arena_t;
+    m->stats_pending = false;
+    return device_errors(m);
+}
+
+extern "C" map_status map_get_frame_stats(map_t *m, int64_t *out, void *stream) {
+    if (!m || !out) return fail(m, MAP_ERR_ARG, "null argument");
+    map_status st = map_sync(m, stream);
+    for (int i = 0; i < MAP_STAT_COUNT; ++i) out[i] = 0;
+    for (int i = 0; i < CT_MT + 1; ++i) out[i] = (int64_t)m->h_ctr[i];
+    out[MAP_STAT_TOTAL_BLOCKS] = (int64_t)std::min<unsigned long long>(m->h_st->pool_count, m->md.max_blocks);
+    out[MAP_STAT_ERROR_BITS] = (int64_t)m->h_st->err;
+    out[MAP_STAT_KERNEL_LAUNCHES] = (int64_t)m->launches;
+    return st;
+}
+
+extern "C" map_status extract_mesh(map_t *m, mesh_view *out, void *stream) {
+    if (!m || !out) return fail(m, MAP_ERR_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_seg_scan(m->md, m->gb, m->md.max_blocks, s);
+    CU(cudaMemcpyAsync(m->h_totals, m->gb.totals, 2 * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    const long long nv = m->h_totals[0], nt = m->h_totals[1];
+    if (nv > m->out_vcap) {
+        if (m->out_pos) cudaFree(m->out_pos);
+        if (m->out_col) cudaFree(m->out_col);
+        if (m->out_keys) cudaFree(m->out_keys);
+        m->out_pos = nullptr;
+        m->out_col = nullptr;
+        m->out_keys = nullptr;
+        m->out_vcap = 0;
+        CU(cudaMalloc(&m->out_pos, nv * 3 * sizeof(float) + 16));
+        CU(cudaMalloc(&m->out_col, nv * 4 + 16));
+        CU(cudaMalloc(&m->out_keys, nv * sizeof(int64_t) + 16));
+        m->out_vcap = nv;
+    }
+    if (nt > m->out_tcap) {
+        if (m->out_tri) cudaFree(m->out_tri);
+        if (m->out_anchor) cudaFree(m->out_anchor);
+        m->out_tri = nullptr;
+        m->out_anchor = nullptr;
+        m->out_tcap = 0;
+        CU(cudaMalloc(&m->out_tri, nt * 3 * sizeof(int32_t) + 16));
+        CU(cudaMalloc(&m->out_anchor, nt * 3 * sizeof(int32_t) + 16));
+        m->out_tcap = nt;
+    }
+    launch_seg_gather(m->md, m->gb, m->md.max_blocks, 1, nullptr, nullptr, nullptr, m->out_pos, m->out_col,
+                      m->out_keys, m->out_tri, m->out_anchor, s);
+    map_status st = launch_check(m, "extract_mesh");
+    if (st != MAP_OK) return st;
+    out->n_vertices = nv;
+    out->n_triangles = nt;
+    out->positions = m->out_pos;
+    out->colors = m->out_col;
+    out->vertex_keys = m->out_keys;
+    out->triangles = m->out_tri;
+    out->triangle_anchors = m->out_anchor;
+    return MAP_OK;
+}
+
+extern "C" map_status query_sdf(map_t *m, const float *xyz_dev, int64_t n, float *sdf_dev, uint8_t *valid_dev,
+                                void *stream) {
+    if (!m || n < 0 || (n > 0 && (!xyz_dev || !sdf_dev))) return fail(m, MAP_ERR_ARG, "bad query arguments");
+    launch_query(m->md, xyz_dev, n, sdf_dev, valid_dev, (cudaStream_t)stream);
+    return launch_check(m, "query_sdf");
+}
+
+extern "C" map_status query_sdf_backward(map_t *m, const float *xyz_dev, const float *grad_sdf_dev, int64_t n,
+                                         float *grad_xyz_dev, double *pose_grad_dev, void *stream) {
+    if (!m || n < 0 || (n > 0 && (!xyz_dev || !grad_sdf_dev || !grad_xyz_dev)))
+        return fail(m, MAP_ERR_ARG, "bad backward arguments");
+    launch_query_bwd(m->md, xyz_dev, grad_sdf_dev, n, grad_xyz_dev, pose_grad_dev, (cudaStream_t)stream);
+    return launch_check(m, "query_sdf_backward");
+}
+
+extern "C" map_status map_align_scan(map_t *m, const float *points_dev, int64_t n, const double T0[16], int32_t iters,
+                                     double T_out[16], void *stream) {
+    if (!m || n < 0 || !T0 || !T_out || iters < 0 || (n > 0 && !points_dev))
+        return fail(m, MAP_ERR_ARG, "bad alignment arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaMemcpyAsync(m->gn_T, T0, 16 * sizeof(double), cudaMemcpyHostToDevice, s));
+    CU(cudaMemsetAsync(m->gn_acc, 0, 32 * sizeof(double), s));
+    for (int it = 0; it < iters; ++it) {
+        launch_gn_terms(m->md, points_dev, n, m->gn_T, m->gn_acc, s);
+        launch_gn_step(m->gn_T, m->gn_acc, s);
+    }
+    map_status st = launch_check(m, "map_align_scan");
+    if (st != MAP_OK) return st;
+    CU(cudaMemcpyAsync(T_out, m->gn_T, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return MAP_OK;
+}
+
+extern "C" map_status map_get_blocks(map_t *m, int32_t *coords_host, int64_t cap, int64_t *count) {
+    if (!m || !count || cap < 0 || (cap > 0 && !coords_host)) return fail(m, MAP_ERR_ARG, "bad arguments");
+    unsigned long long *d_cnt = nullptr;
+    int32_t *d_coords = nullptr;
+    CU(cudaMalloc(&d_cnt, sizeof(unsigned long long)));
+    CU(cudaMemset(d_cnt, 0, sizeof(unsigned long long)));
+    CU(cudaMalloc(&d_coords, (size_t)m->md.max_blocks * 3 * sizeof(int32_t)));
+    launch_collect_blocks(m->md, d_coords, d_cnt, 0);
+    unsigned long long cnt = 0;
+    cudaError_t e = cudaMemcpy(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && cap > 0)
+        e = cudaMemcpy(coords_host, d_coords, (size_t)std::min<long long>(cap, (long long)cnt) * 3 * sizeof(int32_t),
+                       cudaMemcpyDeviceToHost);
+    cudaFree(d_cnt);
+    cudaFree(d_coords);
+    if (e != cudaSuccess) return fail(m, MAP_ERR_CUDA, cudaGetErrorString(e));
+    *count = (int64_t)cnt;
+    return MAP_OK;
+}
+
+extern "C" map_status map_read_blocks(map_t *m, const int32_t *coords, int64_t n, float *D, float *W, float *logP,
+                                      uint8_t *label, uint8_t *found) {
+    if (!m || n < 0 || (n > 0 && !coords)) return fail(m, MAP_ERR_ARG, "bad arguments");
+    if (n == 0) return MAP_OK;
+    std::vector<uint64_t> keys(n);
+    for (int64_t i = 0; i < n; ++i) keys[i] = pack_block(coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]);
+    uint64_t *dk = nullptr;
+    float *dD = nullptr, *dW = nullptr, *dL = nullptr;
+    uint8_t *dlab = nullptr, *dfound = nullptr;
+    const size_t nv = (size_t)n * BV;
+    cudaError_t e = cudaMalloc(&dk, n * sizeof(uint64_t));
+    if (e == cudaSuccess && D) e = cudaMalloc(&dD, nv * sizeof(float));
+    if (e == cudaSuccess && W) e = cudaMalloc(&dW, nv * sizeof(float));
+    if (e == cudaSuccess && logP) e = cudaMalloc(&dL, nv * m->C * sizeof(float));
+    if (e == cudaSuccess && label) e = cudaMalloc(&dlab, nv);
+    if (e == cudaSuccess && found) e = cudaMalloc(&dfound, n);
+    if (e == cudaSuccess) e = cudaMemcpy(dk, keys.data(), n * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        for (int64_t off = 0; off < n; off += 65535) {
+            const int cnt = (int)std::min<int64_t>(65535, n - off);
+            launch_read_blocks(m->md, dk + off, cnt, dD ? dD + off * BV : nullptr, dW ? dW + off * BV : nullptr,
+                               dL ? dL + off * BV * m->C : nullptr, dlab ? dlab + off * BV : nullptr,
+                               dfound ? dfound + off : nullptr, 0);
+        }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && D) e = cudaMemcpy(D, dD, nv * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && W) e = cudaMemcpy(W, dW, nv * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && logP) e = cudaMemcpy(logP, dL, nv * m->C * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && label) e = cudaMemcpy(label, dlab, nv, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && found) e = cudaMemcpy(found, dfound, n, cudaMemcpyDeviceToHost);
+    void *ptrs[] = {dk, dD, dW, dL, dlab, dfound};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (e != cudaSuccess) return fail(m, MAP_ERR_CUDA, cudaGetErrorString(e));
+    return MAP_OK;
+}
+
+extern "C" map_status map_write_blocks(map_t *m, const int32_t *coords, int64_t n, const float *D, const float *W,
+                                       const float *logP) {
+    if (!m || n < 0 || (n > 0 && (!coords || !D || !W))) return fail(m, MAP_ERR_ARG, "bad arguments");
+    float *dD = nullptr, *dW = nullptr, *dL = nullptr;
+    const size_t nv = (size_t)n * BV;
+    cudaError_t e = cudaMalloc(&dD, nv * sizeof(float) + 16);
+    if (e == cudaSuccess) e = cudaMalloc(&dW, nv * sizeof(float) + 16);
+    if (e == cudaSuccess && logP) e = cudaMalloc(&dL, nv * m->C * sizeof(float) + 16);
+    if (e == cudaSuccess) e = cudaMemcpy(dD, D, nv * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dW, W, nv * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && logP) e = cudaMemcpy(dL, logP, nv * m->C * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        for (int64_t i = 0; i < n; ++i)
+            launch_write_block(m->md, pack_block(coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]), dD + i * BV,
+                               dW + i * BV, dL ? dL + i * BV * m->C : nullptr, 0);
+        e = cudaDeviceSynchronize();
+    }
+    if (dD) cudaFree(dD);
+    if (dW) cudaFree(dW);
+    if (dL) cudaFree(dL);
+    if (e != cudaSuccess) return fail(m, MAP_ERR_CUDA, cudaGetErrorString(e));
+    cudaMemcpy(m->h_st, m->st, sizeof(DevState), cudaMemcpyDeviceToHost);
+    return device_errors(m);
+}
+
+extern "C" map_status map_profile_begin(map_t *m, int32_t max_frames) {
+    if (!m || max_frames < 0) return fail(m, MAP_ERR_ARG, "bad arguments");
+    prof_clear(m);
+    m->prof_ev.resize((size_t)max_frames * (MAP_PHASE_COUNT + 1));
+    for (auto &e : m->prof_ev) CU(cudaEventCreate(&e));
+    if (max_frames > 0) {
+        CU(cudaMalloc(&m->prof_stats, (size_t)max_frames * CT_COUNT * sizeof(unsigned long long)));
+        CU(cudaMemset(m->prof_stats, 0, (size_t)max_frames * CT_COUNT * sizeof(unsigned long long)));
+    }
+    m->prof_cap = max_frames;
+    m->prof_n = 0;
+    return MAP_OK;
+}
+
+extern "C" map_status map_profile_end(map_t *m, float *ms_out, int64_t *stats_out, int32_t *n_frames) {
+    if (!m || !n_frames) return fail(m, MAP_ERR_ARG, "bad arguments");
+    const int n = m->prof_n;
+    for (int f = 0; f < n; ++f) {
+        cudaEvent_t *ev = &m->prof_ev[(size_t)f * (MAP_PHASE_COUNT + 1)];
+        CU(cudaEventSynchronize(ev[MAP_PHASE_COUNT]));
+        for (int ph = 0; ph < MAP_PHASE_COUNT; ++ph) {
+            float ms = 0.f;
+            CU(cudaEventElapsedTime(&ms, ev[ph], ev[ph + 1]));
+            if (ms_out) ms_out[(size_t)f * MAP_PHASE_COUNT + ph] = ms;
+        }
+    }
+    if (stats_out && n > 0)
+        CU(cudaMemcpy(stats_out, m->prof_stats, (size_t)n * CT_COUNT * sizeof(unsigned long long),
+                      cudaMemcpyDeviceToHost));
+    *n_frames = n;
+    prof_clear(m);
+    return MAP_OK;
+}
+
+extern "C" const char *map_last_error(map_t *m) { return m ? m->err.c_str() : g_err.c_str(); }

@@ -1,0 +1,223 @@
+"""CUDA path vs FP64 oracle, element by element, through the C ABI.
+
+Workloads are the seeded synthetic scans of ``synth`` (16 x 1024 straight
+drive with hard labels; 64 x 2048 loop with probability vectors), plus
+edge cases: empty scans, ragged point counts, all-invalid points, capacity
+limits and bad poses.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+from tests.gpu_compare import compare_blocks, compare_meshes  # noqa: E402
+
+
+def _lib():
+    import paper_2412_00291_b300 as p
+    return p
+
+
+def _lidar(p, L):
+    return p.lidar_intrinsics(L.H, L.W, L.fov_up, L.fov_down, L.r_min, L.r_max)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _sorted(c):
+    c = np.asarray(c).reshape(-1, 3)
+    return c[np.lexsort((c[:, 2], c[:, 1], c[:, 0]))]
+
+
+def _mesh_np(m):
+    return {k: v.cpu().numpy() for k, v in m.items()}
+
+
+@pytest.fixture(scope="module")
+def line16_run():
+    p = _lib()
+    w = synth.line16()
+    frames = list(synth.sequence(w))
+    gm = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=32768, hash_capacity=1 << 16,
+                        max_points=32768, max_pixels=32768, mesh_vertex_capacity=1 << 22,
+                        mesh_triangle_capacity=1 << 23)
+    om = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    L = _lidar(p, w.lidar)
+    per_frame = []
+    for k, f in enumerate(frames):
+        gm.integrate(L, _dev(f.points), f.T, labels=_dev(f.labels))
+        gs = gm.stats()
+        os_ = om.integrate(w.lidar, f.points, f.T, labels=f.labels)
+        per_frame.append((gs, os_, _sorted(gm.blocks()), _sorted(om.alloc_blocks())))
+    return dict(p=p, w=w, gm=gm, om=om, frames=frames, per_frame=per_frame)
+
+
+def test_line16_counts_and_block_sets(line16_run):
+    for k, (gs, os_, gb, ob) in enumerate(line16_run["per_frame"]):
+        assert gs["error_bits"] == 0
+        assert os_["ambiguous_points"] == 0
+        for key in ("valid_points", "pixel_points", "touched_blocks", "new_blocks"):
+            assert gs[key] == os_[key], (k, key, gs[key], os_[key])
+        np.testing.assert_array_equal(gb, ob)          # allocated block set, bit-exact
+        # updated voxels agree up to the oracle's ambiguous projections
+        assert abs(gs["voxels_updated"] - os_["voxels_updated"]) <= max(10, os_["taint_events"])
+        assert abs(gs["voxels_semantic"] - os_["voxels_semantic"]) <= max(10, os_["taint_events"])
+
+
+def test_line16_voxels(line16_run):
+    r = line16_run
+    w = r["w"]
+    coords = r["om"].alloc_blocks()
+    rep = compare_blocks(r["gm"], r["om"], coords, w.voxel_size, w.frames, w.n_classes)
+    print("line16 voxels:", rep)
+    assert rep["tainted_metric"] < 0.05 * rep["observed"]
+    assert rep["label_checked"] > 0.5 * rep["semantic"]
+
+
+def test_line16_mesh_and_incremental(line16_run):
+    r = line16_run
+    gm, om = r["gm"], r["om"]
+    inc = _mesh_np(gm.mesh())
+    rep = compare_meshes(inc, om.mesh(), om, r["w"].voxel_size)
+    print("line16 mesh:", rep)
+    assert rep["gpu_tris"] > 10000
+    # incremental meshing equals meshing every block from scratch
+    gm.remesh_all()
+    full = _mesh_np(gm.mesh())
+
+    def canon(m):
+        k = m["vertex_keys"]
+        t = k[m["triangles"]]
+        tri = sorted(map(tuple, np.concatenate([t, m["triangle_anchors"]], axis=1).tolist()))
+        v = sorted(zip(k.tolist(), map(tuple, m["positions"].tolist()), map(tuple, m["colors"].tolist())))
+        return tri, v
+    assert canon(inc) == canon(full)
+
+
+def test_edge_cases_empty_ragged_invalid():
+    p = _lib()
+    w = synth.line16()
+    f = next(iter(synth.sequence(w, 1)))
+    L = _lidar(p, w.lidar)
+    gm = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=16384, hash_capacity=1 << 15,
+                        max_points=32768, max_pixels=32768, mesh_vertex_capacity=1 << 21,
+                        mesh_triangle_capacity=1 << 22)
+    om = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    # empty scan
+    gm.integrate(L, torch.zeros((0, 3), dtype=torch.float32, device="cuda"), f.T,
+                 labels=torch.zeros(0, dtype=torch.int32, device="cuda"))
+    s = gm.stats()
+    assert s["valid_points"] == 0 and s["touched_blocks"] == 0 and s["total_blocks"] == 0
+    # all points invalid: NaN, too near, too far
+    bad = np.full((300, 3), np.nan, np.float32)
+    bad[100:200] = [0.1, 0.0, 0.0]
+    bad[200:] = [500.0, 0.0, 0.0]
+    gm.integrate(L, _dev(bad), f.T, labels=_dev(np.zeros(300, np.int32)))
+    assert gm.stats()["valid_points"] == 0
+    # ragged count (not a multiple of the block size), labels out of range ignored
+    n = 16384 - 37
+    lab = f.labels[:n].copy()
+    lab[::97] = 99
+    gm.integrate(L, _dev(f.points[:n]), f.T, labels=_dev(lab))
+    om.integrate(w.lidar, f.points[:n], f.T, labels=lab)
+    gs, os_ = gm.stats(), om.stats()
+    for key in ("valid_points", "pixel_points", "touched_blocks", "new_blocks"):
+        assert gs[key] == os_[key]
+    np.testing.assert_array_equal(_sorted(gm.blocks()), _sorted(om.alloc_blocks()))
+    rep = compare_blocks(gm, om, om.alloc_blocks(), w.voxel_size, 1, w.n_classes)
+    assert rep["observed"] > 10000
+
+
+def test_errors_bad_pose_args_capacity():
+    p = _lib()
+    w = synth.line16()
+    f = next(iter(synth.sequence(w, 1)))
+    L = _lidar(p, w.lidar)
+    gm = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=64, hash_capacity=256,
+                        max_points=32768, max_pixels=32768, mesh_vertex_capacity=1 << 16,
+                        mesh_triangle_capacity=1 << 16)
+    pts, lab = _dev(f.points), _dev(f.labels)
+    T = f.T.copy()
+    T[0, 0] *= 1.01
+    with pytest.raises(p.MapError) as e:
+        gm.integrate(L, pts, T, labels=lab)
+    assert e.value.status == 4
+    with pytest.raises(p.MapError) as e:
+        gm.integrate(L, pts, f.T, labels=lab, probs=torch.zeros((len(pts), 20), device="cuda"))
+    assert e.value.status == 1
+    big = p.lidar_intrinsics(512, 1024, 0.3, -0.3)
+    with pytest.raises(p.MapError) as e:
+        gm.integrate(big, pts, f.T, labels=lab)
+    assert e.value.status == 1
+    # the pool holds 64 blocks: the scan needs more -> latched capacity error, no fault
+    gm.integrate(L, pts, f.T, labels=lab)
+    s = gm.stats(check=False)
+    assert s["error_bits"] & 1
+    with pytest.raises(p.MapError) as e:
+        gm.sync()
+    assert e.value.status == 3
+    assert s["total_blocks"] == 64
+
+
+@pytest.mark.slow
+def test_loop64_full_size_sampled():
+    """The 200-scan 64 x 2048 workload at full size, in the benchmark's launch configuration.
+
+    The GPU integrates all 200 scans; the oracle recomputes the complete
+    allocated block set (integer work) and, for a seeded sample of blocks
+    drawn from its own set plus their +x/+y/+z neighbours, every voxel value.
+    """
+    p = _lib()
+    w = synth.loop64()
+    L = _lidar(p, w.lidar)
+    gm = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes)
+    scene = synth.make_scene(w)
+    Ts = synth.trajectory(w)
+    om = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    # sample: blocks of an oracle-only allocation pass over the first 3 scans
+    probe = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    probe.set_track(np.zeros((0, 3), np.int32))
+    fr = None
+    for k in range(3):
+        fr = synth.make_frame(w, scene, Ts[k], k, out=fr)
+        probe.integrate(w.lidar, fr.points, fr.T, probs=fr.probs)
+    cand = probe.alloc_blocks()
+    rng = np.random.default_rng(2024)
+    base = cand[rng.choice(len(cand), size=48, replace=False)]
+    track = np.unique(np.concatenate([base + np.array([dx, dy, dz]) for dx in (0, 1) for dy in (0, 1)
+                                      for dz in (0, 1)]), axis=0)
+    om.set_track(track)
+    fr = None
+    for k in range(w.frames):
+        fr = synth.make_frame(w, scene, Ts[k], k, out=fr)
+        gm.integrate(L, _dev(fr.points), fr.T, probs=_dev(fr.probs))
+        om.integrate(w.lidar, fr.points, fr.T, probs=fr.probs, nthreads=0)
+        if k in (0, 99, w.frames - 1):
+            gs, os_ = gm.stats(), om.stats()
+            for key in ("valid_points", "pixel_points", "touched_blocks", "new_blocks"):
+                assert gs[key] == os_[key], (k, key)
+    np.testing.assert_array_equal(_sorted(gm.blocks()), _sorted(om.alloc_blocks()))
+    have = np.array([b for b in track if om.read_block(b) is not None])
+    rep = compare_blocks(gm, om, have, w.voxel_size, w.frames, w.n_classes)
+    print("loop64 sampled voxels:", rep)
+    assert rep["observed"] > 5000
+    # mesh segments of the sampled base blocks (their cubes only need the tracked neighbours)
+    full = _mesh_np(gm.mesh())
+    anc_blk = np.floor_divide(full["triangle_anchors"], 8)
+    keep = np.zeros(len(anc_blk), bool)
+    base_set = {tuple(b) for b in base if om.read_block(b) is not None}
+    for i, b in enumerate(map(tuple, anc_blk.tolist())):
+        keep[i] = b in base_set
+    sub_t = full["triangles"][keep]
+    used = np.unique(sub_t)
+    remap = np.full(len(full["vertex_keys"]), -1, np.int64)
+    remap[used] = np.arange(len(used))
+    sub = dict(vertex_keys=full["vertex_keys"][used], positions=full["positions"][used],
+               colors=full["colors"][used], triangles=remap[sub_t], triangle_anchors=full["triangle_anchors"][keep])
+    mrep = compare_meshes(sub, om.mesh(np.array(sorted(base_set))), om, w.voxel_size)
+    print("loop64 sampled mesh:", mrep)

@@ -1,0 +1,131 @@
+"""query_sdf forward/backward, pose gradient and Gauss-Newton alignment vs the oracle.
+
+Both maps hold the same seeded field (written through the C ABI and the
+oracle's block writer, values exactly representable in FP32 or FP16), so
+any difference comes from the query arithmetic alone.
+
+Tolerances: sdf |d| <= 2e-6 m (FP32 interpolation of |D| <= 1 m fields near
+the origin); dD/dx relative 1e-4; pose gradient relative 1e-4 (acceptance
+rule); aligned pose within 1e-4 m / 1e-4 rad of the oracle's FP64 run.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+from tests.fields import block_voxels, blocks_covering, random_rotation  # noqa: E402
+
+
+def _P():
+    import paper_2412_00291_b300 as P
+    return P
+
+
+def _twin(field, blocks, nu, storage=0, n_classes=2):
+    P = _P()
+    g = P.SemanticTSDF(nu, 3 * nu, n_classes, storage=storage, max_blocks=max(4096, 2 * len(blocks)),
+                       hash_capacity=1 << 16, max_points=1 << 18, max_pixels=1 << 12, mesh_vertex_capacity=1 << 20,
+                       mesh_triangle_capacity=1 << 20)
+    o = oracle.OracleMap(nu, 3 * nu, n_classes)
+    cast = np.float16 if storage else np.float32
+    D = np.stack([field(block_voxels(b) * nu) for b in blocks]).astype(cast).astype(np.float32)
+    W = np.ones_like(D)
+    g.write_blocks(blocks, D, W)
+    for b, d in zip(blocks, D):
+        o.write_block(b, d.astype(np.float64), np.ones(512))
+    return g, o
+
+
+def _sphere(c, R):
+    return lambda x: R - np.linalg.norm(x - c, axis=1)
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_query_forward_backward(storage):
+    rng = np.random.default_rng(31)
+    nu = 0.1
+    blocks = blocks_covering([-1.6] * 3, [1.6] * 3, nu)
+    g, o = _twin(_sphere(np.zeros(3), 1.0), blocks, nu, storage)
+    x = rng.uniform(-1.7, 1.7, size=(20000, 3)).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    sdf, valid = g.query(xd)
+    osdf, ovalid, ograd = o.query(x.astype(np.float64))
+    np.testing.assert_array_equal(valid.cpu().numpy(), ovalid)
+    assert ovalid.mean() > 0.5 and (~ovalid).sum() > 100
+    s = sdf.cpu().numpy()
+    assert np.all(np.isnan(s[~ovalid]))
+    np.testing.assert_allclose(s[ovalid], osdf[ovalid], atol=2e-6, rtol=0)
+    P = _P()
+    gs = torch.from_numpy(rng.normal(size=len(x)).astype(np.float32)).cuda()
+    gx = P.query_sdf_backward(g.h, xd, gs).cpu().numpy()
+    want = ograd * gs.cpu().numpy()[:, None]
+    np.testing.assert_allclose(gx[ovalid], want[ovalid], atol=1e-4 * np.abs(want).max(), rtol=1e-4)
+    assert np.all(gx[~ovalid] == 0)
+    # autograd Function gives the same gradient
+    xr = xd.clone().requires_grad_(True)
+    sd, vd = P.QuerySDF.apply(xr, g)
+    (torch.nan_to_num(sd) * gs).sum().backward()
+    np.testing.assert_allclose(xr.grad.cpu().numpy(), gx, rtol=0, atol=0)
+
+
+def test_pose_gradient_matches_oracle_and_fd():
+    rng = np.random.default_rng(32)
+    nu = 0.1
+    blocks = blocks_covering([-2.0] * 3, [2.0] * 3, nu)
+    g, o = _twin(_sphere(np.array([0.1, -0.2, 0.05]), 1.2), blocks, nu)
+    P = _P()
+    pts = (rng.normal(size=(5000, 3)) * 0.3 + rng.normal(size=(5000, 3)) / 1.0).astype(np.float32)
+    pts /= np.linalg.norm(pts, axis=1, keepdims=True)
+    pts *= rng.uniform(0.9, 1.5, size=(len(pts), 1)).astype(np.float32)
+    T = synth.pose(random_rotation(rng), [0.03, -0.02, 0.01])
+    # world points of the scan under T (FP32, as a user would pass them)
+    xw = (pts.astype(np.float64) @ T[:3, :3].T + T[:3, 3]).astype(np.float32)
+    xd = torch.from_numpy(xw).cuda()
+    sdf, valid = g.query(xd)
+    grad_sdf = torch.where(valid, 2.0 * torch.nan_to_num(sdf), torch.zeros_like(sdf))
+    pg = P.pose_gradient(g, xd, grad_sdf).cpu().numpy()
+    ref = o.pose_terms(xw.astype(np.float64).astype(np.float32), np.eye(4))
+    np.testing.assert_allclose(pg, ref["dL"], rtol=1e-4, atol=1e-6 * np.abs(ref["dL"]).max())
+    # and against FP64 central differences of the oracle loss (h = 1e-4)
+    h = 1e-4
+    for j in range(6):
+        xi = np.zeros(6)
+        xi[j] = h
+        lp = o.pose_terms(xw, oracle.se3_exp(xi))["loss"]
+        lm = o.pose_terms(xw, oracle.se3_exp(-xi))["loss"]
+        fd = (lp - lm) / (2 * h)
+        assert pg[j] == pytest.approx(fd, rel=1e-3, abs=1e-3 * np.abs(ref["dL"]).max())
+
+
+def _room_points(rng, size, o, n):
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    with np.errstate(divide="ignore"):
+        t = np.where(d > 0, (np.asarray(size) - o) / d, -o / d)
+    return o + d * t.min(axis=1, keepdims=True)
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_gauss_newton_alignment(storage):
+    rng = np.random.default_rng(33)
+    nu = 0.1
+    size = np.array([6.0, 5.0, 4.0])
+    blocks = blocks_covering([-0.6] * 3, size + 0.6, nu)
+    g, o = _twin(lambda x: np.minimum(x, size - x).min(axis=1), blocks, nu, storage)
+    T_true = synth.pose(synth.rot_rpy(0.02, -0.03, 0.4), [2.8, 2.2, 1.6])
+    pw = _room_points(rng, size, T_true[:3, 3], 20000)
+    pl = ((pw - T_true[:3, 3]) @ T_true[:3, :3]).astype(np.float32)
+    xi = np.concatenate([rng.normal(size=3), rng.normal(size=3)])
+    xi[:3] *= 0.1 / np.linalg.norm(xi[:3])
+    xi[3:] *= math.radians(2.0) / np.linalg.norm(xi[3:])
+    T0 = oracle.se3_exp(xi) @ T_true
+    Tg = g.align(torch.from_numpy(pl).cuda(), T0, iters=20)
+    To = o.align(pl, T0, iters=20)
+    assert np.abs(Tg[:3, 3] - To[:3, 3]).max() < (1e-4 if storage == 0 else 1e-3)
+    assert np.abs(Tg[:3, :3] - To[:3, :3]).max() < (1e-4 if storage == 0 else 1e-3)
+    assert np.abs(Tg[:3, 3] - T_true[:3, 3]).max() < 3e-3
