@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512)
+    ap.add_argument("--max-blocks", type=int, default=0, help="pool size override (profiling runs)")
+    ap.add_argument("--mesh-cap", type=int, default=0, help="mesh arena vertex capacity override")
     return ap.parse_args()
 
 
@@ -98,57 +100,81 @@ def algorithmic_bytes(st, n_points, H, W, C, s):
 
 
 class ClockSampler:
-    """Samples SM clock and throttle reasons via NVML in a background thread."""
+    """SM clock and throttle reasons during the timed region, sampled in a background thread.
+
+    NVML is addressed by the CUDA device's UUID (NVML indices ignore
+    CUDA_VISIBLE_DEVICES); when NVML is unusable, nvidia-smi is polled instead.
+    """
 
     REASONS = {"gpu_idle": 0x1, "applications_clocks_setting": 0x2, "sw_power_cap": 0x4, "hw_slowdown": 0x8,
                "sync_boost": 0x10, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
                "hw_power_brake_slowdown": 0x80, "display_clock_setting": 0x100}
 
-    def __init__(self, index, period=0.005):
-        self.samples, self.reasons = [], 0
-        self.period, self.ok = period, False
+    def __init__(self, device_index, period=0.005):
+        self.samples, self.reasons, self.err = [], 0, None
+        self.period, self.mode = period, None
+        self.max_mhz = None
         self.stop_ev = threading.Event()
         try:
             import pynvml
+            import torch
             pynvml.nvmlInit()
             self.nv = pynvml
-            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            try:
+                self.h = pynvml.nvmlDeviceGetHandleByUUID("GPU-" + uuid)
+            except Exception:
+                self.h = pynvml.nvmlDeviceGetHandleByUUID(uuid)
             self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
-            self.ok = True
-        except Exception as e:   # pragma: no cover
-            self.err = str(e)
+            self.mode = "nvml"
+        except Exception as e:
+            self.err = f"nvml: {e}"
+            self.mode = "smi"
+            self.smi_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(device_index)).split(",")[device_index]
+
+    def _reasons_nvml(self):
+        nv = self.nv
+        for fn in ("nvmlDeviceGetCurrentClocksEventReasons", "nvmlDeviceGetCurrentClocksThrottleReasons"):
+            if hasattr(nv, fn):
+                return int(getattr(nv, fn)(self.h))
+        return 0
 
     def _run(self):
-        nv = self.nv
+        import subprocess
         while not self.stop_ev.is_set():
             try:
-                self.samples.append(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM))
-                try:
-                    r = nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
-                except AttributeError:
-                    r = nv.nvmlDeviceGetCurrentClocksThrottleReasons(self.h)
-                self.reasons |= int(r)
-            except Exception:
-                pass
-            time.sleep(self.period)
+                if self.mode == "nvml":
+                    self.samples.append(self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM))
+                    self.reasons |= self._reasons_nvml()
+                    time.sleep(self.period)
+                else:
+                    q = "clocks.sm,clocks.max.sm,clocks_event_reasons.active"
+                    out = subprocess.run(["nvidia-smi", "-i", self.smi_index, f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                         timeout=5).stdout.strip().split(",")
+                    self.samples.append(float(out[0]))
+                    self.max_mhz = float(out[1])
+                    self.reasons |= int(out[2].strip(), 16)
+            except Exception as e:
+                self.err = str(e)
+                time.sleep(0.05)
 
     def __enter__(self):
-        if self.ok:
-            self.t = threading.Thread(target=self._run, daemon=True)
-            self.t.start()
+        self.t = threading.Thread(target=self._run, daemon=True)
+        self.t.start()
         return self
 
     def __exit__(self, *a):
-        if self.ok:
-            self.stop_ev.set()
-            self.t.join()
+        self.stop_ev.set()
+        self.t.join()
 
     def summary(self):
-        if not self.ok:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvml unavailable"]}
         names = [k for k, v in self.REASONS.items() if self.reasons & v and k != "gpu_idle"]
-        return {"sm_mhz": float(np.median(self.samples)) if self.samples else None, "sm_max_mhz": self.max_mhz,
-                "reasons": names, "samples": len(self.samples)}
+        out = {"sm_mhz": float(np.median(self.samples)) if self.samples else None, "sm_max_mhz": self.max_mhz,
+               "reasons": names, "samples": len(self.samples), "source": self.mode}
+        if self.err:
+            out["note"] = self.err[:200]
+        return out
 
 
 def measured_peaks():
@@ -262,7 +288,14 @@ def run_ours(args, rank, world, local_rank):
     t_gen = time.perf_counter() - t_gen
     storage = 0 if args.storage == "fp32" else 1
     s_bytes = 4 if storage == 0 else 2
-    tsdf = P.SemanticTSDF(w.voxel_size, w.truncation, C, storage=storage)
+    cfg = {}
+    if args.max_blocks:
+        cfg["max_blocks"] = args.max_blocks
+        cfg["hash_capacity"] = 4 * args.max_blocks
+    if args.mesh_cap:
+        cfg["mesh_vertex_capacity"] = args.mesh_cap
+        cfg["mesh_triangle_capacity"] = 2 * args.mesh_cap
+    tsdf = P.SemanticTSDF(w.voxel_size, w.truncation, C, storage=storage, **cfg)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(args.flush_mb << 20, dtype=torch.uint8, device=dev)
 
@@ -325,7 +358,8 @@ def run_ours(args, rank, world, local_rank):
     # --- end to end through the host-buffer entry point ----------------------
     e2e = None
     if not args.no_e2e:
-        tsdf2 = P.SemanticTSDF(w.voxel_size, w.truncation, C, storage=storage)
+        tsdf.close()
+        tsdf2 = P.SemanticTSDF(w.voxel_size, w.truncation, C, storage=storage, **cfg)
         for k in range(args.warmup):
             hp, hq = host[k]
             tsdf2.integrate_host(lid, hp, Ts[k], **({"probs": hq} if pr_d else {"labels": hq}))
@@ -376,7 +410,6 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
-    tsdf.close()
 
 
 def main():

@@ -18,16 +18,30 @@ namespace stsdf {
 static int8_t *h_tri_dev = nullptr;      // [256][MC_MAXTRI][3] cube-edge ids
 static uint8_t *h_ntri_dev = nullptr;    // [256] triangles per case
 
-__global__ void __launch_bounds__(256) k_mesh(MapDev md, FrameDev fd, const int8_t *__restrict__ ttri,
-                                              const uint8_t *__restrict__ tntri, const uchar4 *__restrict__ tpal) {
+constexpr int EDGE_WORDS = (MC_EDGES + 31) / 32;   // 61 words of lattice-edge bits per block
+
+// Local index of the lattice edge that cube edge ce of the cube anchored at
+// (ax, ay, az) lies on: axis * 648 + a + 8 (b + 9 c), with a the coordinate
+// along the axis and b, c the coordinates along the next two axes cyclically.
+__device__ __forceinline__ int cube_edge_index(int ce, int ax, int ay, int az) {
+    const int axis = ce >> 2;
+    const int pa = axis == 0 ? ax : (axis == 1 ? ay : az);
+    const int pb = (axis == 0 ? ay : (axis == 1 ? az : ax)) + (ce & 1);
+    const int pc = (axis == 0 ? az : (axis == 1 ? ax : ay)) + ((ce >> 1) & 1);
+    return axis * 648 + pa + 8 * (pb + 9 * pc);
+}
+
+__global__ void __launch_bounds__(256, 6) k_mesh(MapDev md, FrameDev fd, const int8_t *__restrict__ ttri,
+                                                 const uint8_t *__restrict__ tntri, const uchar4 *__restrict__ tpal) {
     __shared__ int8_t s_tri[256 * MC_MAXTRI * 3];
     __shared__ uint8_t s_ntri[256];
     __shared__ uchar4 s_pal[256];
     __shared__ float sD[729];
-    __shared__ uint8_t sOk[729];
+    __shared__ uint8_t sF[729];        // bit 0: observed (W > 0), bit 1: inside (D < 0)
     __shared__ uint8_t sLab[729];
-    __shared__ uint16_t sCase[512];
-    __shared__ int16_t sVid[MC_EDGES];
+    __shared__ uint8_t sCase[512];
+    __shared__ unsigned sEdge[EDGE_WORDS];
+    __shared__ int sWordOff[EDGE_WORDS];
     __shared__ int s_nb[8];
     __shared__ int s_warp[8];
     __shared__ long long s_hdr[2];
@@ -40,162 +54,160 @@ __global__ void __launch_bounds__(256) k_mesh(MapDev md, FrameDev fd, const int8
     unsigned long long nd = *(volatile unsigned long long *)&fd.ctr[CT_DIRTY];
     if (nd > (unsigned long long)md.max_blocks) nd = md.max_blocks;
     long long n_v = 0, n_t = 0;
+    const bool f32 = md.storage == 0;
     __syncthreads();
     for (unsigned long long li = blockIdx.x; li < nd; li += gridDim.x) {
         const int h = fd.dirty[li];
         const int slot = md.vals[h];
         int bx, by, bz;
         unpack_block(md.keys[h], bx, by, bz);
-        if (tid < 8) {
-            int s = slot;
-            if (tid) {
-                const int hh =
-                    hash_find(md.keys, md.mask, pack_block(bx + (tid & 1), by + ((tid >> 1) & 1), bz + (tid >> 2)));
-                s = hh < 0 ? -1 : md.vals[hh];
-            }
-            s_nb[tid] = s;
+        // neighbour slots (lanes 1..7 of warp 0) overlap with the block's own 512 voxels
+        if (tid >= 1 && tid < 8) {
+            const int hh =
+                hash_find(md.keys, md.mask, pack_block(bx + (tid & 1), by + ((tid >> 1) & 1), bz + (tid >> 2)));
+            s_nb[tid] = hh < 0 ? -1 : md.vals[hh];
+        }
+        if (tid < EDGE_WORDS) sEdge[tid] = 0u;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int v = tid + 256 * q;
+            const int r = (v & 7) + 9 * (((v >> 3) & 7) + 9 * (v >> 6));
+            const long long vox = (long long)slot * BV + v;
+            const float2 dw = f32 ? md.dw32[vox] : __half22float2(md.dw16[vox]);
+            sD[r] = dw.x;
+            sF[r] = (dw.y > 0.f ? 1 : 0) | (dw.x < 0.f ? 2 : 0);
+            sLab[r] = md.label[vox];
         }
         __syncthreads();
+        // the +x / +y / +z faces, edges and corner from the upper neighbours
         for (int r = tid; r < 729; r += blockDim.x) {
             const int x = r % 9, y = (r / 9) % 9, z = r / 81;
-            const int s = s_nb[(x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2)];
+            const int nbi = (x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2);
+            if (nbi == 0) continue;
+            const int s = s_nb[nbi];
             float D = 0.f;
-            uint8_t ok = 0, lab = 0;
+            uint8_t f = 0, lab = 0;
             if (s >= 0) {
                 const long long vox = (long long)s * BV + (x & 7) + 8 * (y & 7) + 64 * (z & 7);
-                const float2 dw = md.storage == 0 ? md.dw32[vox] : __half22float2(md.dw16[vox]);
+                const float2 dw = f32 ? md.dw32[vox] : __half22float2(md.dw16[vox]);
                 D = dw.x;
-                ok = dw.y > 0.f;
+                f = (dw.y > 0.f ? 1 : 0) | (dw.x < 0.f ? 2 : 0);
                 lab = md.label[vox];
             }
             sD[r] = D;
-            sOk[r] = ok;
+            sF[r] = f;
             sLab[r] = lab;
         }
         __syncthreads();
-        // cubes 2t, 2t+1: validity, case, triangle count
+        // cubes 2t, 2t+1: validity, case, triangle count; mark their crossing edges
         int nt_q[2];
         int cnt_t = 0;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int a = 2 * tid + q;
             const int ax = a & 7, ay = (a >> 3) & 7, az = a >> 6;
-            bool valid = true;
-            int cs = 0;
+            const int r0 = ax + 9 * (ay + 9 * az);
+            int ok = 1, cs = 0;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                const int r = (ax + (c & 1)) + 9 * ((ay + ((c >> 1) & 1)) + 9 * (az + (c >> 2)));
-                valid = valid && sOk[r];
-                cs |= (sD[r] < 0.f ? 1 : 0) << c;
+                const int f = sF[r0 + (c & 1) + 9 * ((c >> 1) & 1) + 81 * (c >> 2)];
+                ok &= f;
+                cs |= ((f >> 1) & 1) << c;
             }
-            const int nt = valid ? s_ntri[cs] : 0;
-            sCase[a] = valid ? (uint16_t)(0x100 | cs) : (uint16_t)0;
+            const int nt = ok ? s_ntri[cs] : 0;
+            sCase[a] = (uint8_t)cs;
             nt_q[q] = nt;
             cnt_t += nt;
+            if (nt) {
+#pragma unroll
+                for (int ce = 0; ce < 12; ++ce) {
+                    const int axis = ce >> 2, a1 = axis == 2 ? 0 : axis + 1, a2 = axis == 0 ? 2 : axis - 1;
+                    const int clo = ((ce & 1) << a1) | (((ce >> 1) & 1) << a2);
+                    if (((cs >> clo) ^ (cs >> (clo | (1 << axis)))) & 1) {
+                        const int e = cube_edge_index(ce, ax, ay, az);
+                        atomicOr(&sEdge[e >> 5], 1u << (e & 31));
+                    }
+                }
+            }
         }
         int tot_t;
         const int toff = block_exclusive_scan(cnt_t, s_warp, tot_t);
-        // lattice edges 8t .. 8t+7: crossing and used by a meshed cube of this block
-        unsigned flags = 0;
-        int cnt_v = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int e = 8 * tid + q;
-            if (e >= MC_EDGES) break;
-            const int axis = e / 648, rem = e % 648;
-            const int a1 = (axis + 1) % 3, a2 = (axis + 2) % 3;
-            int p[3];
-            p[axis] = rem & 7;
-            p[a1] = (rem >> 3) % 9;
-            p[a2] = (rem >> 3) / 9;
-            const int r0 = p[0] + 9 * (p[1] + 9 * p[2]);
-            const int r1 = r0 + (axis == 0 ? 1 : (axis == 1 ? 9 : 81));
-            if (!(sOk[r0] && sOk[r1] && ((sD[r0] < 0.f) != (sD[r1] < 0.f)))) continue;
-            bool used = false;
-#pragma unroll
-            for (int d = 0; d < 4; ++d) {
-                int an[3] = {p[0], p[1], p[2]};
-                an[a1] -= d & 1;
-                an[a2] -= d >> 1;
-                if (an[a1] < 0 || an[a1] > 7 || an[a2] < 0 || an[a2] > 7) continue;
-                if (sCase[an[0] + 8 * an[1] + 64 * an[2]] & 0x100) used = true;
+        if (tot_t == 0) {
+            // nothing to mesh: drop the block's old segment
+            if (tid == 0) {
+                const int4 old = md.seg[slot];
+                if (old.y | old.w) md.seg[slot] = make_int4(0, 0, 0, 0);
             }
-            if (used) {
-                flags |= 1u << q;
-                ++cnt_v;
-            }
+            continue;   // tot_t is uniform; the scan's barriers protect shared memory reuse
         }
+        // vertex numbering: popcount prefix over the edge bitmap
+        const int wc = tid < EDGE_WORDS ? __popc(sEdge[tid]) : 0;
         int tot_v;
-        const int voff = block_exclusive_scan(cnt_v, s_warp, tot_v);
-        {
-            int k = voff;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int e = 8 * tid + q;
-                if (e < MC_EDGES) sVid[e] = ((flags >> q) & 1) ? (int16_t)(k++) : (int16_t)-1;
-            }
-        }
+        const int woff = block_exclusive_scan(wc, s_warp, tot_v);
+        if (tid < EDGE_WORDS) sWordOff[tid] = woff;
+        // reserve arena space: vertex and triangle cursors advanced by two warps at once
+        if (tid == 0) s_hdr[0] = (long long)atomicAdd(&md.st->arena_v, (unsigned long long)tot_v);
+        if (tid == 32) s_hdr[1] = (long long)atomicAdd(&md.st->arena_t, (unsigned long long)tot_t);
+        __syncthreads();
+        const bool fits = s_hdr[0] + tot_v <= md.av_cap && s_hdr[1] + tot_t <= md.at_cap;
         if (tid == 0) {
-            const unsigned long long vo = atomicAdd(&md.st->arena_v, (unsigned long long)tot_v);
-            const unsigned long long to = atomicAdd(&md.st->arena_t, (unsigned long long)tot_t);
-            if (vo + tot_v > (unsigned long long)md.av_cap || to + tot_t > (unsigned long long)md.at_cap) {
+            if (fits) {
+                md.seg[slot] = make_int4((int)s_hdr[0], tot_v, (int)s_hdr[1], tot_t);
+            } else {
                 atomicOr(&md.st->err, ERR_ARENA_FULL);
                 md.seg[slot] = make_int4(0, 0, 0, 0);
-                s_hdr[0] = -1;
-            } else {
-                md.seg[slot] = make_int4((int)vo, tot_v, (int)to, tot_t);
-                s_hdr[0] = (long long)vo;
-                s_hdr[1] = (long long)to;
             }
             n_v += tot_v;
             n_t += tot_t;
         }
-        __syncthreads();
-        if (s_hdr[0] >= 0) {
+        if (fits) {
             const long long vo = s_hdr[0], to = s_hdr[1];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                if (!((flags >> q) & 1)) continue;
-                const int e = 8 * tid + q;
-                const int axis = e / 648, rem = e % 648;
-                const int a1 = (axis + 1) % 3, a2 = (axis + 2) % 3;
-                int p[3];
-                p[axis] = rem & 7;
-                p[a1] = (rem >> 3) % 9;
-                p[a2] = (rem >> 3) / 9;
-                const int r0 = p[0] + 9 * (p[1] + 9 * p[2]);
-                const int r1 = r0 + (axis == 0 ? 1 : (axis == 1 ? 9 : 81));
-                const float D0 = sD[r0], D1 = sD[r1];
-                const float t = D0 / (D0 - D1);
-                const int g[3] = {8 * bx + p[0], 8 * by + p[1], 8 * bz + p[2]};
-                float pos[3];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) pos[k] = md.nu * (float)g[k];
-                pos[axis] = md.nu * ((float)g[axis] + t);
-                const int lab = fabsf(D1) < fabsf(D0) ? sLab[r1] : sLab[r0];
-                const uchar4 col = s_pal[lab];
-                const unsigned packed = (unsigned)col.x | ((unsigned)col.y << 8) | ((unsigned)col.z << 16) |
-                                        ((unsigned)lab << 24);
-                const long long o = vo + sVid[e];
-                md.av[o] = make_float4(pos[0], pos[1], pos[2], __uint_as_float(packed));
-                md.ak[o] = edge_key(g[0], g[1], g[2], axis);
+            // vertices of the marked edges 8t .. 8t+7 (one byte of one bitmap word)
+            const int w = tid >> 2;
+            if (w < EDGE_WORDS) {
+                const unsigned word = sEdge[w];
+                unsigned bits = (word >> ((tid & 3) * 8)) & 0xffu;
+                while (bits) {
+                    const int q = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const int e = 8 * tid + q;
+                    const int vid = sWordOff[w] + __popc(word & ((1u << (e & 31)) - 1u));
+                    const int axis = e / 648, rem = e - 648 * axis;
+                    const int ca = rem & 7, cb = (rem >> 3) % 9, cc = (rem >> 3) / 9;
+                    const int x = axis == 0 ? ca : (axis == 1 ? cc : cb);
+                    const int y = axis == 0 ? cb : (axis == 1 ? ca : cc);
+                    const int z = axis == 0 ? cc : (axis == 1 ? cb : ca);
+                    const int r0 = x + 9 * (y + 9 * z);
+                    const int r1 = r0 + (axis == 0 ? 1 : (axis == 1 ? 9 : 81));
+                    const float D0 = sD[r0], D1 = sD[r1];
+                    const float t = D0 / (D0 - D1);
+                    const int gx = 8 * bx + x, gy = 8 * by + y, gz = 8 * bz + z;
+                    float px = md.nu * (float)gx, py = md.nu * (float)gy, pz = md.nu * (float)gz;
+                    if (axis == 0) px = md.nu * ((float)gx + t);
+                    else if (axis == 1) py = md.nu * ((float)gy + t);
+                    else pz = md.nu * ((float)gz + t);
+                    const int lab = fabsf(D1) < fabsf(D0) ? sLab[r1] : sLab[r0];
+                    const uchar4 col = s_pal[lab];
+                    const unsigned packed = (unsigned)col.x | ((unsigned)col.y << 8) | ((unsigned)col.z << 16) |
+                                            ((unsigned)lab << 24);
+                    md.av[vo + vid] = make_float4(px, py, pz, __uint_as_float(packed));
+                    md.ak[vo + vid] = edge_key(gx, gy, gz, axis);
+                }
             }
             long long tb = to + toff;
-#pragma unroll
+#pragma unroll 1
             for (int q = 0; q < 2; ++q) {
                 const int a = 2 * tid + q;
                 const int nt = nt_q[q];
                 if (nt == 0) continue;
-                const int cs = sCase[a] & 0xff;
-                const int an[3] = {a & 7, (a >> 3) & 7, a >> 6};
+                const int cs = sCase[a];
+                const int ax = a & 7, ay = (a >> 3) & 7, az = a >> 6;
                 for (int j = 0; j < nt; ++j) {
                     int vid[3];
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
-                        const int ce = s_tri[(cs * MC_MAXTRI + j) * 3 + k];
-                        const int axis = ce >> 2, a1 = (axis + 1) % 3, a2 = (axis + 2) % 3;
-                        const int pa = an[axis], pb = an[a1] + (ce & 1), pc = an[a2] + ((ce >> 1) & 1);
-                        vid[k] = sVid[axis * 648 + pa + 8 * (pb + 9 * pc)];
+                        const int e = cube_edge_index(s_tri[(cs * MC_MAXTRI + j) * 3 + k], ax, ay, az);
+                        vid[k] = sWordOff[e >> 5] + __popc(sEdge[e >> 5] & ((1u << (e & 31)) - 1u));
                     }
                     md.at[tb + j] = make_ushort4((unsigned short)vid[0], (unsigned short)vid[1],
                                                  (unsigned short)vid[2], (unsigned short)a);

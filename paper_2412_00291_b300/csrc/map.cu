@@ -27,9 +27,18 @@ struct map_t {
     unsigned long long *h_ctr = nullptr;
     DevState *h_st = nullptr;
     long long *h_totals = nullptr;
-    cudaEvent_t ev_stats = nullptr;
-    bool stats_pending = false;
+    // Ring of per-frame device-state copies: bounds how far the host runs ahead
+    // (at most RING frames in flight) and gives it a view of the mesh-arena
+    // cursor that is at most RING frames old.
+    static constexpr int RING = 8;
+    DevState *h_ring = nullptr;
+    cudaEvent_t ev_ring[RING] = {};
+    long long ring_frame[RING] = {};
+    int ring_epoch[RING] = {};
+    int epoch = 0;                  // bumped by every compaction
     unsigned long long known_arena_v = 0, known_arena_t = 0;
+    long long known_frame = -1;
+    unsigned long long max_append_v = 0, max_append_t = 0;
     // staging for host inputs
     float *stage_pts = nullptr;
     int32_t *stage_lab = nullptr;
@@ -118,7 +127,9 @@ static void free_all(map_t *m) {
     if (m->h_ctr) cudaFreeHost(m->h_ctr);
     if (m->h_st) cudaFreeHost(m->h_st);
     if (m->h_totals) cudaFreeHost(m->h_totals);
-    if (m->ev_stats) cudaEventDestroy(m->ev_stats);
+    if (m->h_ring) cudaFreeHost(m->h_ring);
+    for (auto &e : m->ev_ring)
+        if (e) cudaEventDestroy(e);
 }
 
 template <typename T>
@@ -215,14 +226,17 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
 #undef ALLOC
     if (cudaMallocHost(&m->h_ctr, CT_COUNT * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&m->h_st, sizeof(DevState)) != cudaSuccess ||
-        cudaMallocHost(&m->h_totals, 2 * sizeof(long long)) != cudaSuccess) {
+        cudaMallocHost(&m->h_totals, 2 * sizeof(long long)) != cudaSuccess ||
+        cudaMallocHost(&m->h_ring, map_t::RING * sizeof(DevState)) != cudaSuccess) {
         free_all(m);
         delete m;
         return fail(nullptr, MAP_ERR_NOMEM, "pinned host allocation failed");
     }
     std::memset(m->h_ctr, 0, CT_COUNT * sizeof(unsigned long long));
     std::memset(m->h_st, 0, sizeof(DevState));
-    cudaEventCreateWithFlags(&m->ev_stats, cudaEventDisableTiming);
+    std::memset(m->h_ring, 0, map_t::RING * sizeof(DevState));
+    for (auto &e : m->ev_ring) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    for (int i = 0; i < map_t::RING; ++i) m->ring_frame[i] = -1;
 
     cudaStream_t s = 0;
     cudaMemsetAsync(md.keys, 0xFF, cap * sizeof(uint64_t), s);
@@ -343,13 +357,40 @@ static map_status make_scan_const(map_t *m, const lidar_intrinsics *L, int64_t n
     return MAP_OK;
 }
 
-// Refresh the host's view of the device counters when the last async copy is done.
-static void poll_stats(map_t *m) {
-    if (m->stats_pending && cudaEventQuery(m->ev_stats) == cudaSuccess) {
-        m->known_arena_v = m->h_st->arena_v;
-        m->known_arena_t = m->h_st->arena_t;
-        m->stats_pending = false;
+// Fold a completed ring entry into the host's view of the arena cursors.
+static void absorb(map_t *m, int slot) {
+    if (m->ring_frame[slot] < 0 || m->ring_epoch[slot] != m->epoch) return;
+    const DevState &d = m->h_ring[slot];
+    if (m->ring_frame[slot] > m->known_frame) {
+        if (m->known_frame >= 0 && d.arena_v >= m->known_arena_v && d.arena_t >= m->known_arena_t) {
+            const long long df = m->ring_frame[slot] - m->known_frame;
+            m->max_append_v = std::max(m->max_append_v, (d.arena_v - m->known_arena_v) / df);
+            m->max_append_t = std::max(m->max_append_t, (d.arena_t - m->known_arena_t) / df);
+        }
+        m->known_arena_v = d.arena_v;
+        m->known_arena_t = d.arena_t;
+        m->known_frame = m->ring_frame[slot];
     }
+}
+
+// Before frame f: wait for frame f - RING's copy (frames-in-flight bound) and
+// read every completed copy.
+static void poll_stats(map_t *m) {
+    const int slot = m->frame % map_t::RING;
+    if (m->ring_frame[slot] >= 0) {
+        cudaEventSynchronize(m->ev_ring[slot]);
+        absorb(m, slot);
+    }
+    for (int i = 0; i < map_t::RING; ++i)
+        if (m->ring_frame[i] >= 0 && cudaEventQuery(m->ev_ring[i]) == cudaSuccess) absorb(m, i);
+}
+
+// Compact when the cursor could pass 3/4 of capacity before the host sees it again.
+static bool need_compaction(const map_t *m) {
+    const unsigned long long lag = (unsigned long long)(m->frame - m->known_frame) + 1;
+    const unsigned long long est_v = m->known_arena_v + lag * m->max_append_v;
+    const unsigned long long est_t = m->known_arena_t + lag * m->max_append_t;
+    return 4 * est_v > 3 * (unsigned long long)m->md.av_cap || 4 * est_t > 3 * (unsigned long long)m->md.at_cap;
 }
 
 static map_status compact_arena(map_t *m, cudaStream_t s) {
@@ -361,8 +402,11 @@ static map_status compact_arena(map_t *m, cudaStream_t s) {
     std::swap(m->md.av, m->av_alt);
     std::swap(m->md.ak, m->ak_alt);
     std::swap(m->md.at, m->at_alt);
+    // readings taken before this point describe the old arena
+    m->epoch++;
     m->known_arena_v = 0;
     m->known_arena_t = 0;
+    m->known_frame = m->frame - 1;
     return launch_check(m, "arena compaction");
 }
 
@@ -372,8 +416,7 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     map_status st = make_scan_const(m, L, n, T, probs != nullptr, sc);
     if (st != MAP_OK) return st;
     poll_stats(m);
-    if (m->known_arena_v * 2 > (unsigned long long)m->md.av_cap ||
-        m->known_arena_t * 2 > (unsigned long long)m->md.at_cap) {
+    if (need_compaction(m)) {
         st = compact_arena(m, s);
         if (st != MAP_OK) return st;
     }
@@ -406,9 +449,11 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     st = launch_check(m, "integrate_scan kernels");
     if (st != MAP_OK) return st;
     CU(cudaMemcpyAsync(m->h_ctr, m->fd.ctr, CT_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(m->h_st, m->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-    CU(cudaEventRecord(m->ev_stats, s));
-    m->stats_pending = true;
+    const int slot = m->frame % map_t::RING;
+    CU(cudaMemcpyAsync(&m->h_ring[slot], m->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CU(cudaEventRecord(m->ev_ring[slot], s));
+    m->ring_frame[slot] = m->frame;
+    m->ring_epoch[slot] = m->epoch;
     m->frame++;
     return MAP_OK;
 }
@@ -456,9 +501,6 @@ extern "C" map_status map_remesh_all(map_t *m, void *stream) {
     m->launches += 2;
     st = launch_check(m, "map_remesh_all");
     if (st != MAP_OK) return st;
-    CU(cudaMemcpyAsync(m->h_st, m->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-    CU(cudaEventRecord(m->ev_stats, s));
-    m->stats_pending = true;
     return MAP_OK;
 }
 
@@ -479,7 +521,7 @@ extern "C" map_status map_sync(map_t *m, void *stream) {
     CU(cudaStreamSynchronize(s));
     m->known_arena_v = m->h_st->arena_v;
     m->known_arena_t = m->h_st->arena_t;
-    m->stats_pending = false;
+    m->known_frame = m->frame - 1;
     return device_errors(m);
 }
 

@@ -3,8 +3,10 @@
 Stated bound for D: each update rounds the stored D once (at most half an
 FP16 ulp, 2^-11 |D| <= 2^-11 tau) and earlier rounding errors are carried
 with weight W / (W + w) < 1, so after K updates |dD| <= K 2^-11 tau (plus
-the FP32 path's 1e-4 nu).  W: each store is relative 2^-11, so
-|dW| <= K 2^-11 W.  Labels must agree wherever the oracle's top-two gap
+the FP32 path's 1e-4 nu).  W: each store rounds to half an ulp, relative
+2^-11 for normal values and absolute 2^-25 in the subnormal range below
+2^-14 (tiny weights of voxels observed at psi close to -tau), so
+|dW| <= K (2^-11 W + 2^-25).  Labels must agree wherever the oracle's top-two gap
 exceeds 2e-2 (FP16 log-probabilities near -30 have a 2^-6 grid).  Measured
 errors are printed and must sit well inside these bounds.
 """
@@ -47,15 +49,16 @@ def test_fp16_storage_line16():
         assert np.array_equal(a["W"][i][clean] > 0, o["W"][clean] > 0)
         dD16.append(np.abs(a["D"][i] - o["D"])[obs])
         dD32.append(np.abs(a["D"][i] - b["D"][i])[obs])
-        dW16.append((np.abs(a["W"][i] - o["W"]) / np.maximum(o["W"], 1e-30))[obs])
+        dW16.append((np.abs(a["W"][i] - o["W"]) / (2.0 ** -11 * o["W"] + 2.0 ** -25))[obs])
         sure = obs & (o["gap"] > 2e-2)
         agree += int((a["label"][i][sure] == o["label"][sure]).sum())
         checked += int(sure.sum())
     dD16, dD32, dW16 = map(np.concatenate, (dD16, dD32, dW16))
     bound_D = K * 2.0 ** -11 * w.truncation + 1e-4 * w.voxel_size
     print(f"fp16: max|dD| vs FP64 {dD16.max():.3e} (p99 {np.percentile(dD16, 99):.3e}), vs FP32 {dD32.max():.3e}; "
-          f"bound {bound_D:.3e}; max rel dW {dW16.max():.3e}; label agreement {agree}/{checked}")
+          f"bound {bound_D:.3e}; max dW in units of the per-store bound {dW16.max():.2f}; "
+          f"label agreement {agree}/{checked}")
     assert dD16.max() <= bound_D
-    assert dW16.max() <= K * 2.0 ** -11
+    assert dW16.max() <= K
     assert agree == checked
     assert dD16.max() < 1e-3 * w.truncation * K
