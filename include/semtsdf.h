@@ -154,6 +154,27 @@ map_status integrate_scan_host(map_t *map, const lidar_intrinsics *lidar, const 
  * arrays owned by the map).  Synchronises `stream` to learn the sizes. */
 map_status extract_mesh(map_t *map, mesh_view *out, void *stream);
 
+/* extract_mesh for callers that cannot allocate device memory (a real-time
+ * loop that must not block on cudaMalloc, or a host framework that gives the
+ * library only memory it reserved up front).  The paper has no counterpart;
+ * this is an integration aid.  Same result as extract_mesh, written into the
+ * caller's device buffers:
+ *   positions[vertex_capacity][3] float32, colors[vertex_capacity][4] uint8,
+ *   vertex_keys[vertex_capacity] int64, triangles[triangle_capacity][3] int32
+ *   (indices into these vertex arrays), triangle_anchors[triangle_capacity][3].
+ * *n_vertices / *n_triangles receive the mesh size; when it exceeds either
+ * capacity nothing is written and MAP_ERR_CAPACITY is returned (call again
+ * with larger buffers).  Allocates nothing: its scan scratch is one static
+ * device array of 2^19 block slots (8.4 MB, kept by every GPU that loads the
+ * library until exit); maps whose pool exceeds 2^19 blocks get MAP_ERR_ARG.
+ * The first call on a device looks up that array's device address, so make
+ * it before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU (different streams or threads) race.  Synchronises
+ * `stream` to learn the mesh size. */
+map_status extract_mesh_noalloc(map_t *map, float *positions, uint8_t *colors, int64_t *vertex_keys,
+                                int32_t *triangles, int32_t *triangle_anchors, int64_t vertex_capacity,
+                                int64_t triangle_capacity, int64_t *n_vertices, int64_t *n_triangles, void *stream);
+
 /* Re-mesh every allocated block from scratch (replacing the incremental
  * segments); used to check that incremental meshing equals a full pass. */
 map_status map_remesh_all(map_t *map, void *stream);

@@ -63,6 +63,7 @@ _SIGS = {
     "integrate_scan_host": ([P, P, P, P, P, I64, P, P], I32),
     "extract_mesh": ([P, P, P], I32),
     "map_remesh_all": ([P, P], I32),
+    "extract_mesh_noalloc": ([P, P, P, P, P, P, I64, I64, P, P, P], I32),
     "query_sdf": ([P, P, I64, P, P, P], I32),
     "query_sdf_backward": ([P, P, P, I64, P, P, P], I32),
     "map_align_scan": ([P, P, I64, P, I32, P, P], I32),
@@ -203,6 +204,25 @@ def extract_mesh(h, stream=None, copy=True) -> dict:
     if copy:
         out = {k: v.clone() for k, v in out.items()}
     return out
+
+
+def extract_mesh_noalloc(h, positions, colors, vertex_keys, triangles, triangle_anchors, stream=None):
+    """extract_mesh into caller-owned CUDA tensors; the library allocates nothing.
+
+    positions [V, 3] float32, colors [V, 4] uint8, vertex_keys [V] int64,
+    triangles [T, 3] int32, triangle_anchors [T, 3] int32, with V and T the
+    capacities.  Returns (n_vertices, n_triangles); raises MapError
+    (MAP_ERR_CAPACITY, sizes in the message) when the mesh does not fit.
+    """
+    nv, nt = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.extract_mesh_noalloc(h, _dev_ptr(positions, torch.float32, "positions", 3),
+                                     _dev_ptr(colors, torch.uint8, "colors", 4),
+                                     _dev_ptr(vertex_keys, torch.int64, "vertex_keys"),
+                                     _dev_ptr(triangles, torch.int32, "triangles", 3),
+                                     _dev_ptr(triangle_anchors, torch.int32, "triangle_anchors", 3),
+                                     int(positions.shape[0]), int(triangles.shape[0]), ctypes.byref(nv),
+                                     ctypes.byref(nt), _stream(stream)), h)
+    return nv.value, nt.value
 
 
 def map_remesh_all(h, stream=None):

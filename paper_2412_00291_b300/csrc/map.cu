@@ -731,3 +731,9 @@ extern "C" map_status map_profile_end(map_t *m, float *ms_out, int64_t *stats_ou
 }
 
 extern "C" const char *map_last_error(map_t *m) { return m ? m->err.c_str() : g_err.c_str(); }
+
+// Internal accessors for translation units that add entry points around a map.
+namespace stsdf {
+const MapDev *map_device_view(const map_t *m) { return &m->md; }
+void map_set_error(map_t *m, const char *msg) { m->err = msg; }
+}  // namespace stsdf
