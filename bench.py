@@ -37,9 +37,9 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-PHASES = ("reset", "range_image", "pixels", "alloc", "integrate", "dirty", "mesh")
-KERNEL_FILES = {"range_image": "k_scan.cu", "pixels": "k_scan.cu", "alloc": "k_alloc.cu",
-                "integrate": "k_integrate.cu", "dirty": "k_alloc.cu", "mesh": "k_mesh.cu"}
+PHASES = ("reset", "points", "pixels", "tsdf", "semantic", "mesh")
+KERNEL_FILES = {"points": "k_alloc.cu", "pixels": "k_scan.cu", "tsdf": "k_integrate.cu",
+                "semantic": "k_integrate.cu", "mesh": "k_mesh.cu"}
 
 
 def parse():
@@ -77,25 +77,28 @@ def frames_for(w, n, nthreads=0):
 # algorithmic bytes per kernel (HBM traffic the method must do), per frame
 # --------------------------------------------------------------------------
 def algorithmic_bytes(st, n_points, H, W, C, s):
-    """st: per-frame counters (MAP_STAT_* order); s: bytes per stored scalar (4 FP32, 2 FP16).
+    """HBM bytes each kernel of one scan must move, from that scan's counters.
 
-    integrate: each updated voxel reads and writes {D, W} (2 s each way); each
-      semantically updated voxel reads and writes C log-probabilities and
-      writes its label byte; plus a 16-byte work-list/hash record per touched block.
-    mesh: per re-meshed block, {D, W} + label of its 9^3 staged voxels, its
-      segment record, and the emitted vertices (16 B + 8 B key) and triangles (8 B).
-    range_image: the points (12 B each).  pixels: the winners' probability rows
-      (C * 4 B), the per-pixel outputs.  alloc: the points again.
+    st: per-scan counters (MAP_STAT_* order); s: bytes per stored scalar (4 FP32, 2 FP16).
+    points:   the points (12 B each); winners and hash probes stay in L2.
+    pixels:   winner probability rows (4C B) read, log-likelihood rows (4C B),
+              pixel records (16 B) and flags (1 B) written, per pixel.
+    tsdf:     {D, W} read and written (2 x 2s B) per updated voxel, an 8 B
+              list entry per semantic voxel, a 16 B work record per touched block.
+    semantic: C log-probabilities read and written (2 C s B), the label byte
+              and the 8 B list entry per semantically updated voxel.
+    mesh:     {D, W} + label (2s + 1 B) of the 512 own voxels and the segment
+              record (16 B) per re-meshed block, 24 B per vertex and 8 B per
+              triangle emitted (neighbour faces are re-reads).
     """
     upd, sem, touched, dirty, mv, mt = st[4], st[5], st[2], st[6], st[7], st[8]
     return {
-        "integrate": upd * 2 * (2 * s) + sem * (2 * C * s + 1) + touched * 16,
-        "mesh": dirty * (729 * (2 * s + 1) + 16) + mv * 24 + mt * 8,
-        "range_image": n_points * 12,
-        "pixels": H * W * (C * 4 + 16 + 1) + H * W * C * 4,
-        "alloc": n_points * 12,
-        "dirty": touched * 8 * 12,
         "reset": H * W * 8,
+        "points": n_points * 12,
+        "pixels": H * W * (8 * C + 17),
+        "tsdf": upd * 2 * (2 * s) + sem * 8 + touched * 16,
+        "semantic": sem * (2 * C * s + 1 + 8),
+        "mesh": dirty * (512 * (2 * s + 1) + 16) + mv * 24 + mt * 8,
     }
 
 

@@ -74,7 +74,7 @@ typedef struct {
     double lik_floor;         /* lower bound of probability-vector entries (1e-6)        */
     int32_t storage;          /* 0: FP32 {D, W} and log-probabilities; 1: FP16 storage   */
     int32_t reserved0;
-    int64_t max_blocks;       /* block pool size (8^3 voxels each)                        */
+    int64_t max_blocks;       /* block pool size (8^3 voxels each), at most 2^22             */
     int64_t hash_capacity;    /* hash slots, rounded up to a power of two                 */
     int64_t max_points;       /* largest scan accepted by integrate_scan                  */
     int64_t max_pixels;       /* largest H * W accepted                                    */
@@ -228,16 +228,15 @@ map_status map_write_blocks(map_t *map, const int32_t *coords_host, int64_t n, c
 
 /* ---- phase profiling (CUDA events on the caller's stream) ---- */
 
-/* Phases of one integrate_scan, in launch order. */
+/* Phases of one integrate_scan, in launch order (one kernel each, after the resets). */
 enum {
-    MAP_PHASE_RESET = 0,      /* range-image and counter resets                  */
-    MAP_PHASE_RANGE = 1,      /* range image (Sec. III-C.1)                       */
-    MAP_PHASE_PIXELS = 2,     /* per-pixel range pair and class log-likelihood    */
-    MAP_PHASE_ALLOC = 3,      /* band allocation, hash insert, touched list       */
-    MAP_PHASE_INTEGRATE = 4,  /* projective TSDF + Bayesian fusion                */
-    MAP_PHASE_DIRTY = 5,      /* blocks to re-mesh                                */
-    MAP_PHASE_MESH = 6,       /* incremental marching cubes                       */
-    MAP_PHASE_COUNT = 7
+    MAP_PHASE_RESET = 0,      /* range-image and counter resets                               */
+    MAP_PHASE_POINTS = 1,     /* per point: range-image winner (Sec. III-C.1), band allocation */
+    MAP_PHASE_PIXELS = 2,     /* per pixel: range pair and class log-likelihood               */
+    MAP_PHASE_TSDF = 3,       /* projective TSDF update (Sec. III-C.2), re-mesh queue          */
+    MAP_PHASE_SEMANTIC = 4,   /* Bayesian class fusion (Eq. bayesian_filter)                  */
+    MAP_PHASE_MESH = 5,       /* incremental marching cubes                                   */
+    MAP_PHASE_COUNT = 6
 };
 
 /* Start recording per-phase events for up to max_frames subsequent

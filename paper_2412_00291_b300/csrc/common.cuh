@@ -33,14 +33,28 @@ enum : int {
     CT_COUNT = 16
 };
 
+// The mesh arena is split into ARENA_PARTS partitions with their own append
+// cursors, so that concurrent meshing warps do not all contend for one atomic.
+constexpr int ARENA_PARTS = 16;
+
 // Persistent device scalars of a map.
 struct DevState {
-    unsigned long long pool_count;   // blocks allocated so far
-    unsigned long long arena_v;      // append cursors of the mesh arena
-    unsigned long long arena_t;
-    unsigned int err;                // latched ERR_* bits
+    unsigned long long pool_count;               // blocks allocated so far
+    unsigned long long arena_v[ARENA_PARTS];     // vertex append cursor of each partition
+    unsigned long long arena_t[ARENA_PARTS];     // triangle append cursor of each partition
+    unsigned long long arena_v_base[ARENA_PARTS], arena_v_end[ARENA_PARTS];
+    unsigned long long arena_t_base[ARENA_PARTS], arena_t_end[ARENA_PARTS];
+    unsigned int err;                            // latched ERR_* bits
     unsigned int pad;
 };
+
+// Partition p of [live, cap): base and end.
+__host__ __device__ inline void arena_partition(unsigned long long live, unsigned long long cap, int p,
+                                                unsigned long long &base, unsigned long long &end) {
+    const unsigned long long free_ = cap > live ? cap - live : 0;
+    base = live + free_ / ARENA_PARTS * p;
+    end = p == ARENA_PARTS - 1 ? cap : live + free_ / ARENA_PARTS * (p + 1);
+}
 
 // Block key: 21 bits per block coordinate, biased by 2^20.
 __host__ __device__ inline uint64_t pack_block(int x, int y, int z) {
@@ -73,7 +87,7 @@ struct ScanConst {
     float inv_dphi, inv_dtheta, theta0;
     float r_min, r_max;
     // band endpoints, IEEE single precision recipe: R / nu and t / nu + 1/2
-    float Rv[9], tv[3], tau;
+    float Rv[9], tv[3], tau, inv_2tau;
     // world-to-LiDAR rotation R^T (row-major), used to find a voxel's pixel
     float Rt[9];
     // sensor position in voxel units = k + (fhi + flo), k integer, 0 <= f < 1
@@ -84,6 +98,7 @@ struct ScanConst {
     int weight_mode;
     int frame;
     int has_probs;
+    int probs_vec4;       // probability rows can be read as float4 (C % 4 == 0, 16-byte aligned)
 };
 
 // Device pointers of one map.
@@ -91,17 +106,20 @@ struct MapDev {
     uint64_t *keys;      // [cap] block keys, EMPTY_KEY when free
     int *vals;           // [cap] pool slot of the key (-1: pool was full)
     int *stamp;          // [cap] last frame the block was touched
-    int *dstamp;         // [cap] last frame the block was queued for meshing
+    int *dstamp_slot;    // [slot] last frame the block was queued for meshing
     uint64_t mask;       // cap - 1
     int max_blocks;
     int C;
     int storage;         // 0 FP32, 1 FP16
     float2 *dw32;        // [slot][512] {D, W}
     __half2 *dw16;
-    float *lp32;         // [slot][C][512] log-probabilities, class-major
+    float *lp32;         // [slot][512][CP] log-probabilities, one padded record per voxel
     __half *lp16;
+    int CP;              // record stride in elements: C rounded up to whole 32-byte sectors
     uint8_t *label;      // [slot][512] most probable class
     uint64_t *slot_key;  // [slot] block key owning the pool slot
+    int *slot_frame;     // [slot] frame in which the slot was allocated
+    int *nbr;            // [slot][16] slots of the blocks b + e_o (o = 1..7) and b - e_o (8 + o), -1 if none
     int4 *seg;           // [slot] mesh segment: vertex offset, count, triangle offset, count
     float4 *av;          // mesh arena: vertex {x, y, z, rgb|label bits}
     int64_t *ak;         // mesh arena: vertex edge keys
@@ -118,7 +136,9 @@ struct FrameDev {
     float *logL;               // [H*W][C] per-pixel class log-likelihood
     uint8_t *sem_ok;           // [H*W] 1 when the pixel carries a class likelihood
     int *touched;              // [max_blocks] hash slots of U_k
-    int *dirty;                // [max_blocks] hash slots to re-mesh
+    int *dirty;                // [max_blocks] pool slots to re-mesh
+    int2 *sem_list;            // [sem_cap] {pool voxel index, pixel} awaiting the class update
+    long long sem_cap;
     unsigned long long *ctr;   // [CT_COUNT]
 };
 
@@ -148,12 +168,28 @@ __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, f
     pl = __fsub_rn(e, __fsub_rn(ph, p));
 }
 
+// Offset of class c of pool voxel vox (= slot * 512 + voxel index) in the log-probability array.
+__host__ __device__ inline long long lp_index(const MapDev &md, long long vox, int c) {
+    return vox * md.CP + c;
+}
+
 // Range of a point exactly as the allocation recipe defines it.
 __device__ __forceinline__ float range_f32(float x, float y, float z) {
     float s = __fmul_rn(x, x);
     s = __fadd_rn(s, __fmul_rn(y, y));
     s = __fadd_rn(s, __fmul_rn(z, z));
     return __fsqrt_rn(s);
+}
+
+// Pixel of a valid LiDAR-frame point (Sec. III-C.1), -1 when its beam row is outside [0, H).
+__device__ __forceinline__ int point_pixel(const ScanConst &sc, float x, float y, float z, float l) {
+    const float uc = (PI_F - atan2f(y, x)) * sc.inv_dphi;
+    const float vc = (acosf(fminf(fmaxf(z / l, -1.f), 1.f)) - sc.theta0) * sc.inv_dtheta;
+    int u = (int)floorf(uc + 0.5f);
+    const int v = (int)floorf(vc + 0.5f);
+    if (u >= sc.W) u -= sc.W;
+    if (u < 0) u += sc.W;
+    return (v >= 0 && v < sc.H) ? v * sc.W + u : -1;
 }
 
 __device__ __forceinline__ int hash_find(const uint64_t *__restrict__ keys, uint64_t mask, uint64_t key) {
@@ -165,6 +201,22 @@ __device__ __forceinline__ int hash_find(const uint64_t *__restrict__ keys, uint
         h = (h + 1) & mask;
     }
     return -1;
+}
+
+// Neighbour links of block `key` (pool slot s) with its 14 face/edge/corner
+// neighbours b +- e_o, both directions; every block is in the hash already.
+__device__ __forceinline__ void link_block(const MapDev &md, uint64_t key, int s, int o) {
+    int x, y, z;
+    unpack_block(key, x, y, z);
+    const int dx = o & 1, dy = (o >> 1) & 1, dz = o >> 2;
+    const int hp = hash_find(md.keys, md.mask, pack_block(x + dx, y + dy, z + dz));
+    const int np = hp < 0 ? -1 : md.vals[hp];
+    md.nbr[s * 16 + o] = np;
+    if (np >= 0) md.nbr[np * 16 + 8 + o] = s;
+    const int hm = hash_find(md.keys, md.mask, pack_block(x - dx, y - dy, z - dz));
+    const int nm = hm < 0 ? -1 : md.vals[hm];
+    md.nbr[s * 16 + 8 + o] = nm;
+    if (nm >= 0) md.nbr[nm * 16 + o] = s;
 }
 
 // Block-wide exclusive scan of one int per thread (blockDim.x multiple of 32, <= 1024).
@@ -192,6 +244,19 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *s_warp, int &tot
     total = s_warp[nw - 1];
     __syncthreads();
     return base + x - v;
+}
+
+// Exclusive scan over the 32 lanes of a warp; total returned in every lane.
+__device__ __forceinline__ int warp_exclusive_scan(int v, int &total) {
+    const int lane = threadIdx.x & 31;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
 }
 
 // sum over the block, result valid in every thread

@@ -1,6 +1,6 @@
-// Block allocation along each point's truncation band, the touched-block list
-// U_k and the list of blocks to re-mesh; plus pool initialisation and the
-// block read/write helpers.
+// Per-point work of a scan (range-image winners and block allocation along
+// each point's truncation band, the touched-block list U_k); plus pool
+// initialisation and the block read/write helpers.
 //
 // Band of a valid point (range r in [r_min, r_max]): the world segment
 // [p - tau d, p + tau d] (start clipped to the sensor when r < tau), d the
@@ -119,16 +119,33 @@ __device__ int hash_insert(const MapDev &md, uint64_t key, int &is_new) {
     return -1;
 }
 
-__global__ void __launch_bounds__(256) k_alloc(const float *__restrict__ pts, ScanConst sc, MapDev md, FrameDev fd) {
+// One thread per point: validity, the range-image winner of its pixel
+// (u = round((pi - atan2(y, x)) / dphi) mod W, v = round((acos(z / r) -
+// theta0) / dtheta); nearest point wins, equal ranges the lower index, by one
+// 64-bit atomicMin on (range bits << 32 | index)), and the blocks of its band.
+__global__ void __launch_bounds__(256) k_points(const float *__restrict__ pts, ScanConst sc, MapDev md, FrameDev fd) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int nb = 0;
+    int nb = 0, valid = 0, inpix = 0;
     int blocks[MAX_BAND_BLOCKS][3];
     if (i < sc.n) {
         const float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
         if (isfinite(x) && isfinite(y) && isfinite(z)) {
             const float l = range_f32(x, y, z);
-            if (l >= sc.r_min && l <= sc.r_max && l > 0.f) nb = band_blocks(sc, x, y, z, l, blocks);
+            if (l >= sc.r_min && l <= sc.r_max && l > 0.f) {
+                valid = 1;
+                const int p = point_pixel(sc, x, y, z, l);
+                if (p >= 0) {
+                    inpix = 1;
+                    atomicMin(&fd.win[p], ((unsigned long long)__float_as_uint(l) << 32) | (unsigned)i);
+                }
+                nb = band_blocks(sc, x, y, z, l, blocks);
+            }
         }
+    }
+    const unsigned mv = __ballot_sync(0xffffffffu, valid), mp = __ballot_sync(0xffffffffu, inpix);
+    if ((threadIdx.x & 31) == 0 && (mv | mp)) {
+        atomicAdd(&fd.ctr[CT_VALID], (unsigned long long)__popc(mv));
+        atomicAdd(&fd.ctr[CT_PIXEL], (unsigned long long)__popc(mp));
     }
     int n_new = 0;
     for (int j = 0; j < nb; ++j) {
@@ -139,7 +156,10 @@ __global__ void __launch_bounds__(256) k_alloc(const float *__restrict__ pts, Sc
         if (is_new) {
             ++n_new;
             const int s = md.vals[h];
-            if (s >= 0) md.slot_key[s] = key;
+            if (s >= 0) {
+                md.slot_key[s] = key;
+                md.slot_frame[s] = sc.frame;
+            }
         }
         if (atomicExch(&md.stamp[h], sc.frame) != sc.frame) {
             const unsigned long long idx = atomicAdd(&fd.ctr[CT_TOUCHED], 1ull);
@@ -151,38 +171,25 @@ __global__ void __launch_bounds__(256) k_alloc(const float *__restrict__ pts, Sc
     if ((threadIdx.x & 31) == 0 && n_new) atomicAdd(&fd.ctr[CT_NEW], (unsigned long long)n_new);
 }
 
-// Blocks to re-mesh: every touched block b and its neighbours b - e,
-// e in {0,1}^3 \ 0 (their cubes reach into b), when allocated.
-__global__ void __launch_bounds__(256) k_dirty(ScanConst sc, MapDev md, FrameDev fd) {
-    unsigned long long nt = *(volatile unsigned long long *)&fd.ctr[CT_TOUCHED];
-    if (nt > (unsigned long long)md.max_blocks) nt = md.max_blocks;
-    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < nt * 8;
-         e += (unsigned long long)gridDim.x * blockDim.x) {
-        const int h = fd.touched[e >> 3];
-        const int o = (int)(e & 7);
-        int hh = h;
-        if (o) {
-            int x, y, z;
-            unpack_block(md.keys[h], x, y, z);
-            hh = hash_find(md.keys, md.mask, pack_block(x - (o & 1), y - ((o >> 1) & 1), z - ((o >> 2) & 1)));
-            if (hh < 0) continue;
-        }
-        if (md.vals[hh] < 0) continue;
-        if (atomicExch(&md.dstamp[hh], sc.frame) != sc.frame) {
-            const unsigned long long idx = atomicAdd(&fd.ctr[CT_DIRTY], 1ull);
-            if (idx < (unsigned long long)md.max_blocks) fd.dirty[idx] = hh;
-            else atomicOr(&md.st->err, ERR_LIST_FULL);
-        }
+// Link every allocated block (after host-side writes).
+__global__ void k_link_all(MapDev md) {
+    unsigned long long pc = md.st->pool_count;
+    if (pc > (unsigned long long)md.max_blocks) pc = md.max_blocks;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)pc * 7;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(e / 7), o = 1 + (int)(e % 7);
+        link_block(md, md.slot_key[s], s, o);
     }
 }
 
-// Every allocated block into the dirty list (full re-mesh).
+// Every allocated block into the re-mesh list (full re-mesh).
 __global__ void k_list_all(MapDev md, FrameDev fd) {
-    for (unsigned long long h = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; h <= md.mask;
-         h += (unsigned long long)gridDim.x * blockDim.x) {
-        if (md.keys[h] == EMPTY_KEY || md.vals[h] < 0) continue;
+    unsigned long long pc = md.st->pool_count;
+    if (pc > (unsigned long long)md.max_blocks) pc = md.max_blocks;
+    for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; s < pc;
+         s += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long idx = atomicAdd(&fd.ctr[CT_DIRTY], 1ull);
-        if (idx < (unsigned long long)md.max_blocks) fd.dirty[idx] = (int)h;
+        if (idx < (unsigned long long)md.max_blocks) fd.dirty[idx] = (int)s;
     }
 }
 
@@ -196,10 +203,11 @@ __global__ void k_init_pool(MapDev md) {
         else md.dw16[i] = __floats2half2_rn(0.f, 0.f);
         md.label[i] = 0;
         const long long slot = i / BV, v = i - slot * BV;
-        for (int c = 0; c < md.C; ++c) {
-            const long long j = (slot * md.C + c) * BV + v;
-            if (md.storage == 0) md.lp32[j] = lp0;
-            else md.lp16[j] = __float2half_rn(lp0);
+        for (int c = 0; c < md.CP; ++c) {
+            const long long j = lp_index(md, i, c);
+            const float val = c < md.C ? lp0 : 0.f;   // padding of the record stays zero
+            if (md.storage == 0) md.lp32[j] = val;
+            else md.lp16[j] = __float2half_rn(val);
         }
         if (v == 0) md.seg[slot] = make_int4(0, 0, 0, 0);
     }
@@ -212,7 +220,10 @@ __global__ void k_write_block(MapDev md, uint64_t key, const float *D, const flo
         int is_new = 0;
         const int h = hash_insert(md, key, is_new);
         s_slot = h < 0 ? -1 : md.vals[h];
-        if (s_slot >= 0) md.slot_key[s_slot] = key;
+        if (s_slot >= 0) {
+            md.slot_key[s_slot] = key;
+            if (is_new) md.slot_frame[s_slot] = -2;
+        }
     }
     __syncthreads();
     const int slot = s_slot;
@@ -225,7 +236,7 @@ __global__ void k_write_block(MapDev md, uint64_t key, const float *D, const flo
         float bv = -INFINITY;
         for (int c = 0; c < md.C; ++c) {
             const float lp = logP ? logP[c * BV + v] : -logf((float)md.C);
-            const long long j = ((long long)slot * md.C + c) * BV + v;
+            const long long j = lp_index(md, vox, c);
             if (md.storage == 0) md.lp32[j] = lp;
             else md.lp16[j] = __float2half_rn(lp);
             const float stored = md.storage == 0 ? lp : __half2float(__float2half_rn(lp));
@@ -274,7 +285,7 @@ __global__ void k_read_blocks(MapDev md, const uint64_t *keys, int n, float *D, 
             for (int c = 0; c < md.C; ++c) {
                 float lp = -logf((float)md.C);
                 if (slot >= 0) {
-                    const long long j = ((long long)slot * md.C + c) * BV + v;
+                    const long long j = lp_index(md, (long long)slot * BV + v, c);
                     lp = md.storage == 0 ? md.lp32[j] : __half2float(md.lp16[j]);
                 }
                 logP[((long long)b * md.C + c) * BV + v] = lp;
@@ -299,17 +310,15 @@ __global__ void k_collect_blocks(MapDev md, int32_t *coords, unsigned long long 
     }
 }
 
-void launch_alloc(const float *pts, const ScanConst &sc, const MapDev &md, const FrameDev &fd, cudaStream_t s) {
+void launch_points(const float *pts, const ScanConst &sc, const MapDev &md, const FrameDev &fd, cudaStream_t s) {
     if (sc.n <= 0) return;
-    k_alloc<<<(unsigned)((sc.n + 255) / 256), 256, 0, s>>>(pts, sc, md, fd);
-}
-void launch_dirty(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s) {
-    k_dirty<<<grid, 256, 0, s>>>(sc, md, fd);
+    k_points<<<(unsigned)((sc.n + 255) / 256), 256, 0, s>>>(pts, sc, md, fd);
 }
 void launch_list_all(const MapDev &md, const FrameDev &fd, int, cudaStream_t s) {
     k_list_all<<<1024, 256, 0, s>>>(md, fd);
 }
 void launch_init_pool(const MapDev &md, cudaStream_t s) { k_init_pool<<<2048, 256, 0, s>>>(md); }
+void launch_link_all(const MapDev &md, cudaStream_t s) { k_link_all<<<1024, 256, 0, s>>>(md); }
 void launch_write_block(const MapDev &md, uint64_t key, const float *D, const float *W, const float *logP,
                         cudaStream_t s) {
     k_write_block<<<1, 256, 0, s>>>(md, key, D, W, logP);

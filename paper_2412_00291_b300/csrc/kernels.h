@@ -5,16 +5,15 @@
 
 namespace stsdf {
 
-// k_scan.cu: measurement preprocessing (Sec. III-C.1)
-void launch_range_image(const float *pts, const ScanConst &sc, const FrameDev &fd, cudaStream_t s);
+// k_scan.cu: per-pixel table of the range image (Sec. III-C.1)
 void launch_pixels(const float *pts, const int32_t *labels, const float *probs, const ScanConst &sc,
                    const FrameDev &fd, cudaStream_t s);
 
-// k_alloc.cu: band allocation, touched and dirty lists
-void launch_alloc(const float *pts, const ScanConst &sc, const MapDev &md, const FrameDev &fd, cudaStream_t s);
-void launch_dirty(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s);
+// k_alloc.cu: per-point range-image winners and band allocation (touched list)
+void launch_points(const float *pts, const ScanConst &sc, const MapDev &md, const FrameDev &fd, cudaStream_t s);
 void launch_list_all(const MapDev &md, const FrameDev &fd, int frame, cudaStream_t s);
 void launch_init_pool(const MapDev &md, cudaStream_t s);
+void launch_link_all(const MapDev &md, cudaStream_t s);
 void launch_write_block(const MapDev &md, uint64_t key, const float *D, const float *W, const float *logP,
                         cudaStream_t s);
 void launch_read_blocks(const MapDev &md, const uint64_t *keys, int n, float *D, float *W, float *logP,
@@ -23,7 +22,9 @@ void launch_collect_blocks(const MapDev &md, int32_t *coords, unsigned long long
 
 // k_integrate.cu: projective TSDF + Bayesian semantic fusion (Sec. III-C.2, III-C.3)
 void launch_integrate(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s);
+void launch_semantic(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s);
 int integrate_blocks_per_sm(int storage, int C);
+int semantic_blocks_per_sm(int storage, int C);
 
 // k_mesh.cu: incremental marching cubes and mesh gathering
 int mesh_upload_tables(const int8_t *tri, const uint8_t *ntri);

@@ -36,9 +36,9 @@ struct map_t {
     long long ring_frame[RING] = {};
     int ring_epoch[RING] = {};
     int epoch = 0;                  // bumped by every compaction
-    unsigned long long known_arena_v = 0, known_arena_t = 0;
+    double known_fill = 0.0;         // largest used fraction of any arena partition
     long long known_frame = -1;
-    unsigned long long max_append_v = 0, max_append_t = 0;
+    double max_append = 0.0;         // largest per-frame growth of that fraction
     // staging for host inputs
     float *stage_pts = nullptr;
     int32_t *stage_lab = nullptr;
@@ -56,7 +56,7 @@ struct map_t {
     // alignment scratch
     double *gn_T = nullptr, *gn_acc = nullptr;
     int frame = 0;
-    int grid_integrate = 0, grid_mesh = 0, grid_dirty = 0;
+    int grid_integrate = 0, grid_mesh = 0, grid_semantic = 0;
     // phase profiling: (MAP_PHASE_COUNT + 1) events per recorded frame
     std::vector<cudaEvent_t> prof_ev;
     int prof_cap = 0, prof_n = 0;
@@ -116,10 +116,10 @@ static void prof_clear(map_t *m) {
 
 static void free_all(map_t *m) {
     prof_clear(m);
-    void *ptrs[] = {m->md.keys, m->md.vals, m->md.stamp, m->md.dstamp, m->md.dw32, m->md.dw16, m->md.lp32,
-                    m->md.lp16, m->md.label, m->md.slot_key, m->md.seg, m->md.av, m->md.ak, m->md.at,
+    void *ptrs[] = {m->md.keys, m->md.vals, m->md.stamp, m->md.dstamp_slot, m->md.dw32, m->md.dw16, m->md.lp32,
+                    m->md.lp16, m->md.label, m->md.slot_key, m->md.slot_frame, m->md.nbr, m->md.seg, m->md.av, m->md.ak, m->md.at,
                     m->av_alt, m->ak_alt, m->at_alt, m->st, m->fd.win, m->fd.pix, m->fd.logL, m->fd.sem_ok,
-                    m->fd.touched, m->fd.dirty, m->fd.ctr, m->gb.voff, m->gb.toff, m->gb.bsum_v, m->gb.bsum_t,
+                    m->fd.touched, m->fd.dirty, m->fd.sem_list, m->fd.ctr, m->gb.voff, m->gb.toff, m->gb.bsum_v, m->gb.bsum_t,
                     m->gb.totals, m->stage_pts, m->stage_lab, m->stage_probs, m->out_pos, m->out_col,
                     m->out_keys, m->out_tri, m->out_anchor, m->gn_T, m->gn_acc, m->pal_dev};
     for (void *p : ptrs)
@@ -148,7 +148,7 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
         return fail(nullptr, MAP_ERR_ARG, "bad weight_mode or storage");
     if (!(c.p_hit > 0.0 && c.p_hit < 1.0) || !(c.lik_floor > 0.0))
         return fail(nullptr, MAP_ERR_ARG, "need 0 < p_hit < 1 and lik_floor > 0");
-    if (c.max_blocks < 1 || c.max_blocks > (1ll << 24) || c.hash_capacity < 2 || c.max_points < 1 ||
+    if (c.max_blocks < 1 || c.max_blocks > (1ll << 22) || c.hash_capacity < 2 || c.max_points < 1 ||
         c.max_pixels < 1 || c.max_points > (1ll << 31) - 1 || c.mesh_vertex_capacity < 1 ||
         c.mesh_triangle_capacity < 1 || c.mesh_vertex_capacity > (1ll << 31) - 1 ||
         c.mesh_triangle_capacity > (1ll << 31) - 1)
@@ -170,6 +170,11 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     md.max_blocks = (int)nb;
     md.C = c.n_classes;
     md.storage = c.storage;
+    {
+        // log-probability record per voxel padded to whole 32-byte sectors
+        const int per_sector = c.storage == 0 ? 8 : 16;
+        md.CP = ((c.n_classes + per_sector - 1) / per_sector) * per_sector;
+    }
     md.nu = (float)c.voxel_size;
     md.av_cap = c.mesh_vertex_capacity;
     md.at_cap = c.mesh_triangle_capacity;
@@ -187,16 +192,18 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     ALLOC(md.keys, cap);
     ALLOC(md.vals, cap);
     ALLOC(md.stamp, cap);
-    ALLOC(md.dstamp, cap);
+    ALLOC(md.dstamp_slot, nb);
     if (c.storage == 0) {
         ALLOC(md.dw32, nvox);
-        ALLOC(md.lp32, nvox * c.n_classes);
+        ALLOC(md.lp32, nvox * md.CP);
     } else {
         ALLOC(md.dw16, nvox);
-        ALLOC(md.lp16, nvox * c.n_classes);
+        ALLOC(md.lp16, nvox * md.CP);
     }
     ALLOC(md.label, nvox);
     ALLOC(md.slot_key, nb);
+    ALLOC(md.slot_frame, nb);
+    ALLOC(md.nbr, nb * 16);
     ALLOC(md.seg, nb);
     ALLOC(md.av, c.mesh_vertex_capacity);
     ALLOC(md.ak, c.mesh_vertex_capacity);
@@ -213,6 +220,8 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     ALLOC(fd.sem_ok, c.max_pixels);
     ALLOC(fd.touched, nb);
     ALLOC(fd.dirty, nb);
+    fd.sem_cap = std::min<long long>(nvox, 1ll << 25);
+    ALLOC(fd.sem_list, fd.sem_cap);
     ALLOC(fd.ctr, CT_COUNT);
     m->nchunks = (int)((nb + 1023) / 1024);
     ALLOC(m->gb.voff, nb);
@@ -242,8 +251,20 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     cudaMemsetAsync(md.keys, 0xFF, cap * sizeof(uint64_t), s);
     cudaMemsetAsync(md.vals, 0xFF, cap * sizeof(int), s);
     cudaMemsetAsync(md.stamp, 0xFF, cap * sizeof(int), s);
-    cudaMemsetAsync(md.dstamp, 0xFF, cap * sizeof(int), s);
-    cudaMemsetAsync(m->st, 0, sizeof(DevState), s);
+    cudaMemsetAsync(md.dstamp_slot, 0xFF, nb * sizeof(int), s);
+    cudaMemsetAsync(md.slot_frame, 0xFF, nb * sizeof(int), s);
+    cudaMemsetAsync(md.nbr, 0xFF, nb * 16 * sizeof(int), s);
+    {
+        DevState init;
+        std::memset(&init, 0, sizeof(init));
+        for (int p = 0; p < ARENA_PARTS; ++p) {
+            arena_partition(0, (unsigned long long)c.mesh_vertex_capacity, p, init.arena_v_base[p], init.arena_v_end[p]);
+            arena_partition(0, (unsigned long long)c.mesh_triangle_capacity, p, init.arena_t_base[p], init.arena_t_end[p]);
+            init.arena_v[p] = init.arena_v_base[p];
+            init.arena_t[p] = init.arena_t_base[p];
+        }
+        cudaMemcpy(m->st, &init, sizeof(init), cudaMemcpyHostToDevice);
+    }
     cudaMemsetAsync(fd.ctr, 0, CT_COUNT * sizeof(unsigned long long), s);
     cudaMemsetAsync(m->gn_acc, 0, 32 * sizeof(double), s);
     launch_init_pool(md, s);
@@ -270,8 +291,8 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     m->grid_integrate = sms * integrate_blocks_per_sm(c.storage, c.n_classes);
+    m->grid_semantic = 4 * sms * semantic_blocks_per_sm(c.storage, c.n_classes);
     m->grid_mesh = sms * mesh_blocks_per_sm();
-    m->grid_dirty = sms * 4;
     e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -333,6 +354,7 @@ static map_status make_scan_const(map_t *m, const lidar_intrinsics *L, int64_t n
     for (int i = 0; i < 9; ++i) sc.Rv[i] = (float)(R[i] / nu);
     for (int k = 0; k < 3; ++k) sc.tv[k] = (float)(t[k] / nu + 0.5);
     sc.tau = (float)tau;
+    sc.inv_2tau = (float)(1.0 / (2.0 * tau));
     for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c) sc.Rt[3 * r + c] = (float)R[3 * c + r];
     for (int k = 0; k < 3; ++k) {
@@ -354,21 +376,30 @@ static map_status make_scan_const(map_t *m, const lidar_intrinsics *L, int64_t n
     sc.weight_mode = m->cfg.weight_mode;
     sc.frame = m->frame;
     sc.has_probs = has_probs;
+    sc.probs_vec4 = 0;
     return MAP_OK;
 }
 
-// Fold a completed ring entry into the host's view of the arena cursors.
+// Largest used fraction of any mesh-arena partition in a device-state copy.
+static double arena_fill(const DevState &d) {
+    double f = 0.0;
+    for (int p = 0; p < ARENA_PARTS; ++p) {
+        const double sv = (double)(d.arena_v_end[p] - d.arena_v_base[p]);
+        const double st = (double)(d.arena_t_end[p] - d.arena_t_base[p]);
+        if (sv > 0) f = std::max(f, (double)(d.arena_v[p] - d.arena_v_base[p]) / sv);
+        if (st > 0) f = std::max(f, (double)(d.arena_t[p] - d.arena_t_base[p]) / st);
+    }
+    return f;
+}
+
+// Fold a completed ring entry into the host's view of the arena fill.
 static void absorb(map_t *m, int slot) {
     if (m->ring_frame[slot] < 0 || m->ring_epoch[slot] != m->epoch) return;
-    const DevState &d = m->h_ring[slot];
     if (m->ring_frame[slot] > m->known_frame) {
-        if (m->known_frame >= 0 && d.arena_v >= m->known_arena_v && d.arena_t >= m->known_arena_t) {
-            const long long df = m->ring_frame[slot] - m->known_frame;
-            m->max_append_v = std::max(m->max_append_v, (d.arena_v - m->known_arena_v) / df);
-            m->max_append_t = std::max(m->max_append_t, (d.arena_t - m->known_arena_t) / df);
-        }
-        m->known_arena_v = d.arena_v;
-        m->known_arena_t = d.arena_t;
+        const double f = arena_fill(m->h_ring[slot]);
+        if (m->known_frame >= 0 && f >= m->known_fill)
+            m->max_append = std::max(m->max_append, (f - m->known_fill) / (double)(m->ring_frame[slot] - m->known_frame));
+        m->known_fill = f;
         m->known_frame = m->ring_frame[slot];
     }
 }
@@ -385,12 +416,11 @@ static void poll_stats(map_t *m) {
         if (m->ring_frame[i] >= 0 && cudaEventQuery(m->ev_ring[i]) == cudaSuccess) absorb(m, i);
 }
 
-// Compact when the cursor could pass 3/4 of capacity before the host sees it again.
+// Compact when a partition could pass 3/4 of its space before the host sees it
+// again (per-partition growth estimated at twice the largest seen).
 static bool need_compaction(const map_t *m) {
-    const unsigned long long lag = (unsigned long long)(m->frame - m->known_frame) + 1;
-    const unsigned long long est_v = m->known_arena_v + lag * m->max_append_v;
-    const unsigned long long est_t = m->known_arena_t + lag * m->max_append_t;
-    return 4 * est_v > 3 * (unsigned long long)m->md.av_cap || 4 * est_t > 3 * (unsigned long long)m->md.at_cap;
+    const double lag = (double)(m->frame - m->known_frame) + 1.0;
+    return m->known_fill + 2.0 * lag * m->max_append > 0.75;
 }
 
 static map_status compact_arena(map_t *m, cudaStream_t s) {
@@ -404,8 +434,7 @@ static map_status compact_arena(map_t *m, cudaStream_t s) {
     std::swap(m->md.at, m->at_alt);
     // readings taken before this point describe the old arena
     m->epoch++;
-    m->known_arena_v = 0;
-    m->known_arena_t = 0;
+    m->known_fill = 0.0;
     m->known_frame = m->frame - 1;
     return launch_check(m, "arena compaction");
 }
@@ -415,6 +444,7 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     ScanConst sc;
     map_status st = make_scan_const(m, L, n, T, probs != nullptr, sc);
     if (st != MAP_OK) return st;
+    sc.probs_vec4 = probs && (m->C % 4 == 0) && (((uintptr_t)probs & 15) == 0);
     poll_stats(m);
     if (need_compaction(m)) {
         st = compact_arena(m, s);
@@ -431,19 +461,17 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     CU(cudaMemsetAsync(m->fd.win, 0xFF, np * sizeof(unsigned long long), s));
     CU(cudaMemsetAsync(m->fd.ctr, 0, CT_COUNT * sizeof(unsigned long long), s));
     if (ev) CU(cudaEventRecord(ev[1], s));
-    launch_range_image(pts, sc, m->fd, s);
+    launch_points(pts, sc, m->md, m->fd, s);
     if (ev) CU(cudaEventRecord(ev[2], s));
     launch_pixels(pts, labels, probs, sc, m->fd, s);
     if (ev) CU(cudaEventRecord(ev[3], s));
-    launch_alloc(pts, sc, m->md, m->fd, s);
-    if (ev) CU(cudaEventRecord(ev[4], s));
     launch_integrate(sc, m->md, m->fd, m->grid_integrate, s);
+    if (ev) CU(cudaEventRecord(ev[4], s));
+    launch_semantic(sc, m->md, m->fd, m->grid_semantic, s);
     if (ev) CU(cudaEventRecord(ev[5], s));
-    launch_dirty(sc, m->md, m->fd, m->grid_dirty, s);
-    if (ev) CU(cudaEventRecord(ev[6], s));
     launch_mesh(m->md, m->fd, m->pal_dev, m->grid_mesh, s);
-    if (ev) CU(cudaEventRecord(ev[7], s));
-    m->launches += 7;
+    if (ev) CU(cudaEventRecord(ev[6], s));
+    m->launches += 5;
     if (ev_stats)
         CU(cudaMemcpyAsync(ev_stats, m->fd.ctr, CT_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
     st = launch_check(m, "integrate_scan kernels");
@@ -519,8 +547,7 @@ extern "C" map_status map_sync(map_t *m, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaMemcpyAsync(m->h_st, m->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    m->known_arena_v = m->h_st->arena_v;
-    m->known_arena_t = m->h_st->arena_t;
+    m->known_fill = arena_fill(*m->h_st);
     m->known_frame = m->frame - 1;
     return device_errors(m);
 }
@@ -686,6 +713,7 @@ extern "C" map_status map_write_blocks(map_t *m, const int32_t *coords, int64_t 
         for (int64_t i = 0; i < n; ++i)
             launch_write_block(m->md, pack_block(coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]), dD + i * BV,
                                dW + i * BV, dL ? dL + i * BV * m->C : nullptr, 0);
+        launch_link_all(m->md, 0);
         e = cudaDeviceSynchronize();
     }
     if (dD) cudaFree(dD);
