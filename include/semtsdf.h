@@ -200,6 +200,60 @@ map_status query_sdf_backward(map_t *map, const float *xyz_dev, const float *gra
 map_status map_align_scan(map_t *map, const float *points_dev, int64_t n, const double T0[16], int32_t iters,
                           double T_out[16], void *stream);
 
+/* ---- batched persistent integration (many maps, one launch) ---- */
+
+/* One map's scan in a batch step (same meaning as the integrate_scan arguments). */
+typedef struct {
+    map_t *map;
+    lidar_intrinsics lidar;
+    const float *points_dev;
+    const int32_t *labels_dev;
+    const float *probs_dev;
+    int64_t n;
+    double T_world_lidar[16];
+} scan_desc;
+
+typedef struct map_batch_t map_batch_t;
+
+enum {
+    MAP_BATCH_GRAPH = 1,     /* replay the launch from a CUDA graph (one per launch configuration) */
+    MAP_BATCH_AUTOTUNE = 2   /* time each launch configuration on the first steps, keep the fastest */
+};
+
+/* Group 1..48 maps (each used by this batch only while it exists).  The batch
+ * kernel needs cooperative launch support; MAP_ERR_STATE otherwise. */
+map_status map_batch_create(map_t *const *maps, int32_t n_maps, int32_t flags, map_batch_t **out);
+map_status map_batch_destroy(map_batch_t *batch);
+
+/* Fuse scans[i] into the batch's i-th map for every i, in ONE cooperative
+ * persistent kernel launch (Sec. III-C per map: range image, band
+ * allocation, projective TSDF, Bayesian class fusion, incremental marching
+ * cubes), with grid-wide barriers between the phases instead of host round
+ * trips.  Results are identical to n_maps integrate_scan calls.  With
+ * MAP_BATCH_AUTOTUNE the first 3 x 6 steps rotate through six launch
+ * configurations (threads per block 128/256 x items per thread 1/2/4) and the
+ * fastest median is kept.  Waits for the previous batch step (at most one in
+ * flight); errors of the previous step (MAP_ERR_TIMEOUT when a barrier wait
+ * ran out, MAP_ERR_CAPACITY) are returned by the next call or map_batch_sync. */
+map_status map_batch_integrate(map_batch_t *batch, const scan_desc *scans, void *stream);
+
+/* Wait for the step in flight and report its errors. */
+map_status map_batch_sync(map_batch_t *batch, void *stream);
+
+/* The launch configuration in use (0 while still tuning). */
+map_status map_batch_config(map_batch_t *batch, int32_t *threads_per_block, int32_t *items_per_thread,
+                            int32_t *tuned);
+
+/* Fix the launch configuration (0..5; -1 = tune). */
+map_status map_batch_set_config(map_batch_t *batch, int32_t config_index);
+
+/* Failure test hook: the next batch launch lets one CTA leave at once, so
+ * the first grid barrier cannot complete; every other CTA gives up after
+ * spin_limit polls and the step reports MAP_ERR_TIMEOUT. */
+map_status map_batch_test_timeout(map_batch_t *batch, uint64_t spin_limit);
+
+const char *map_batch_last_error(map_batch_t *batch);
+
 /* ---- host-side inspection and checkpoint helpers (synchronising) ---- */
 
 /* Wait for the map's work on `stream` and report latched device errors. */

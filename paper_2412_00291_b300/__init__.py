@@ -55,6 +55,15 @@ class MeshView(ctypes.Structure):
                 ("vertex_keys", P), ("triangles", P), ("triangle_anchors", P)]
 
 
+class ScanDesc(ctypes.Structure):
+    _fields_ = [("map", P), ("lidar", LidarIntrinsics), ("points_dev", P), ("labels_dev", P), ("probs_dev", P),
+                ("n", I64), ("T_world_lidar", D * 16)]
+
+
+MAP_BATCH_GRAPH = 1
+MAP_BATCH_AUTOTUNE = 2
+BATCH_MAX = 48
+
 _SIGS = {
     "map_config_default": ([P], I32),
     "map_create": ([P, P], I32),
@@ -77,6 +86,14 @@ _SIGS = {
     "map_profile_end": ([P, P, P, P], I32),
     "map_mc_table": ([P], I32),
     "map_palette": ([I32, P], I32),
+    "map_batch_create": ([P, I32, I32, P], I32),
+    "map_batch_destroy": ([P], I32),
+    "map_batch_integrate": ([P, P, P], I32),
+    "map_batch_sync": ([P, P], I32),
+    "map_batch_config": ([P, P, P, P], I32),
+    "map_batch_set_config": ([P, I32], I32),
+    "map_batch_test_timeout": ([P, ctypes.c_uint64], I32),
+    "map_batch_last_error": ([P], ctypes.c_char_p),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -93,6 +110,12 @@ class MapError(RuntimeError):
 def _check(status, handle=None):
     if status != 0:
         msg = _lib.map_last_error(handle)
+        raise MapError(status, msg.decode() if msg else "")
+
+
+def _bcheck(status, batch=None):
+    if status != 0:
+        msg = _lib.map_batch_last_error(batch)
         raise MapError(status, msg.decode() if msg else "")
 
 
@@ -162,6 +185,8 @@ def integrate_scan(h, lidar: LidarIntrinsics, points, T_world_lidar, labels=None
 
 def integrate_scan_host(h, lidar: LidarIntrinsics, points, T_world_lidar, labels=None, probs=None, stream=None):
     """Host (ideally pinned) buffers: numpy arrays or CPU tensors."""
+    keep = []
+
     def hp(a, dtype):
         if a is None:
             return None
@@ -169,7 +194,9 @@ def integrate_scan_host(h, lidar: LidarIntrinsics, points, T_world_lidar, labels
             if a.is_cuda or a.dtype != dtype or not a.is_contiguous():
                 raise TypeError("host tensor expected")
             return ctypes.c_void_p(a.data_ptr())
-        return _np_ptr(np.ascontiguousarray(a))
+        a = np.ascontiguousarray(a)
+        keep.append(a)
+        return _np_ptr(a)
     n = int(points.shape[0])
     _, Tp = _pose(T_world_lidar)
     _check(_lib.integrate_scan_host(h, ctypes.byref(lidar), hp(points, torch.float32), hp(labels, torch.int32),
@@ -317,6 +344,57 @@ def map_profile_end(h, max_frames):
     n = ctypes.c_int32()
     _check(_lib.map_profile_end(h, _np_ptr(out), _np_ptr(st), ctypes.byref(n)), h)
     return out[:n.value], st[:n.value]
+
+
+def map_batch_create(handles, flags=MAP_BATCH_GRAPH | MAP_BATCH_AUTOTUNE):
+    arr = (P * len(handles))(*[hh.value if isinstance(hh, ctypes.c_void_p) else hh for hh in handles])
+    b = ctypes.c_void_p()
+    _bcheck(_lib.map_batch_create(arr, len(handles), int(flags), ctypes.byref(b)))
+    return b
+
+
+def map_batch_destroy(b):
+    _bcheck(_lib.map_batch_destroy(b))
+
+
+def map_batch_integrate(b, handles, lidars, points, poses, labels=None, probs=None, stream=None):
+    """One cooperative launch fuses points[i] (pose poses[i]) into handles[i] for every i."""
+    n = len(handles)
+    descs = (ScanDesc * n)()
+    for i in range(n):
+        pts = points[i]
+        lab = None if labels is None else labels[i]
+        pr = None if probs is None else probs[i]
+        C = None if pr is None else int(pr.shape[1])
+        d = descs[i]
+        d.map = handles[i].value if isinstance(handles[i], ctypes.c_void_p) else handles[i]
+        d.lidar = lidars[i]
+        d.points_dev = _dev_ptr(pts, torch.float32, "points", 3)
+        d.labels_dev = _dev_ptr(lab, torch.int32, "labels")
+        d.probs_dev = _dev_ptr(pr, torch.float32, "probs", C)
+        d.n = 0 if pts is None else int(pts.shape[0])
+        T = np.asarray(poses[i], dtype=np.float64).reshape(16)
+        for k in range(16):
+            d.T_world_lidar[k] = float(T[k])
+    _bcheck(_lib.map_batch_integrate(b, descs, _stream(stream)), b)
+
+
+def map_batch_sync(b, stream=None):
+    _bcheck(_lib.map_batch_sync(b, _stream(stream)), b)
+
+
+def map_batch_config(b) -> dict:
+    t, v, tuned = I32(), I32(), I32()
+    _bcheck(_lib.map_batch_config(b, ctypes.byref(t), ctypes.byref(v), ctypes.byref(tuned)), b)
+    return {"threads_per_block": t.value, "items_per_thread": v.value, "tuned": bool(tuned.value)}
+
+
+def map_batch_set_config(b, index):
+    _bcheck(_lib.map_batch_set_config(b, int(index)), b)
+
+
+def map_batch_test_timeout(b, spin_limit):
+    _bcheck(_lib.map_batch_test_timeout(b, int(spin_limit)), b)
 
 
 def map_last_error(h=None) -> str:

@@ -1,0 +1,782 @@
+// Device bodies of the per-frame pipeline, shared by the single-map kernels
+// (k_alloc.cu, k_scan.cu, k_integrate.cu, k_mesh.cu) and the batched
+// persistent kernel (k_batch.cu).  Each body processes one work item: a point,
+// a pixel, a touched block (one warp), a class-update entry, a block to
+// re-mesh (one warp).
+#pragma once
+
+#include "kernels.h"
+
+namespace stsdf {
+
+// Blocks met by the band of one point, in path order; returns their count.
+__device__ __forceinline__ int band_blocks(const ScanConst &sc, float x0, float x1, float x2, float l, int (*out)[3]) {
+    const float q = __fdiv_rn(sc.tau, l);
+    float f0 = __fsub_rn(1.f, q);
+    if (f0 < 0.f) f0 = 0.f;
+    const float f1 = __fadd_rn(1.f, q);
+    float e0[3], e1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float s = __fmul_rn(sc.Rv[3 * k], x0);
+        s = __fadd_rn(s, __fmul_rn(sc.Rv[3 * k + 1], x1));
+        s = __fadd_rn(s, __fmul_rn(sc.Rv[3 * k + 2], x2));
+        e0[k] = __fadd_rn(sc.tv[k], __fmul_rn(s, f0));
+        e1[k] = __fadd_rn(sc.tv[k], __fmul_rn(s, f1));
+    }
+    // crossing events: parameter, kind (0: entered at t, 1: left after t), axis, step
+    float et[3 * MAX_AXIS_CROSS];
+    int einfo[3 * MAX_AXIS_CROSS];
+    int ne = 0;
+    int cur[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int b0 = (int)floorf(__fmul_rn(e0[k], 0.125f));
+        const int b1 = (int)floorf(__fmul_rn(e1[k], 0.125f));
+        cur[k] = b0;
+        const float d = __fsub_rn(e1[k], e0[k]);
+        if (b1 > b0) {
+            for (int b = b0 + 1, c = 0; b <= b1 && c < MAX_AXIS_CROSS; ++b, ++c) {
+                et[ne] = __fdiv_rn(__fsub_rn((float)(8 * b), e0[k]), d);
+                einfo[ne++] = (0 << 4) | (k << 1) | 1;
+            }
+        } else if (b1 < b0) {
+            for (int b = b0, c = 0; b > b1 && c < MAX_AXIS_CROSS; --b, ++c) {
+                et[ne] = __fdiv_rn(__fsub_rn((float)(8 * b), e0[k]), d);
+                einfo[ne++] = (1 << 4) | (k << 1) | 0;
+            }
+        }
+    }
+    // insertion sort by (t, kind)
+    for (int i = 1; i < ne; ++i) {
+        float t = et[i];
+        int inf = einfo[i];
+        int j = i - 1;
+        while (j >= 0 && (et[j] > t || (et[j] == t && (einfo[j] >> 4) > (inf >> 4)))) {
+            et[j + 1] = et[j];
+            einfo[j + 1] = einfo[j];
+            --j;
+        }
+        et[j + 1] = t;
+        einfo[j + 1] = inf;
+    }
+    int nb = 0;
+    out[nb][0] = cur[0];
+    out[nb][1] = cur[1];
+    out[nb][2] = cur[2];
+    ++nb;
+    for (int i = 0; i < ne;) {
+        int j = i;
+        while (j < ne && et[j] == et[i] && (einfo[j] >> 4) == (einfo[i] >> 4)) {
+            const int ax = (einfo[j] >> 1) & 3;
+            cur[ax] += (einfo[j] & 1) ? 1 : -1;
+            ++j;
+        }
+        out[nb][0] = cur[0];
+        out[nb][1] = cur[1];
+        out[nb][2] = cur[2];
+        ++nb;
+        i = j;
+    }
+    return nb;
+}
+
+// Find or insert a block key; lock-free (compare-and-swap on the key slot).
+// The inserting thread takes the next pool slot; readers of vals[] run in
+// later kernels only, so no thread waits on another.
+__device__ __forceinline__ int hash_insert(const MapDev &md, uint64_t key, int &is_new) {
+    uint64_t h = fmix64(key) & md.mask;
+    for (int p = 0; p < MAX_PROBES; ++p) {
+        const uint64_t k = md.keys[h];
+        if (k == key) {
+            is_new = 0;
+            return (int)h;
+        }
+        if (k == EMPTY_KEY) {
+            const uint64_t old = atomicCAS((unsigned long long *)&md.keys[h], EMPTY_KEY, key);
+            if (old == EMPTY_KEY) {
+                const unsigned long long s = atomicAdd(&md.st->pool_count, 1ull);
+                if (s < (unsigned long long)md.max_blocks) {
+                    md.vals[h] = (int)s;
+                } else {
+                    md.vals[h] = -1;
+                    atomicOr(&md.st->err, ERR_POOL_FULL);
+                }
+                is_new = 1;
+                return (int)h;
+            }
+            if (old == key) {
+                is_new = 0;
+                return (int)h;
+            }
+        }
+        h = (h + 1) & md.mask;
+    }
+    atomicOr(&md.st->err, ERR_HASH_PROBES);
+    return -1;
+}
+
+// One thread per point: validity, the range-image winner of its pixel
+// (u = round((pi - atan2(y, x)) / dphi) mod W, v = round((acos(z / r) -
+// theta0) / dtheta); nearest point wins, equal ranges the lower index, by one
+// 64-bit atomicMin on (range bits << 32 | index)), and the blocks of its band.
+__device__ __forceinline__ void points_item(const float *__restrict__ pts, const ScanConst &sc, const MapDev &md,
+                                            const FrameDev &fd, long long i) {
+    int nb = 0, valid = 0, inpix = 0;
+    int blocks[MAX_BAND_BLOCKS][3];
+    if (i < sc.n) {
+        const float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+        if (isfinite(x) && isfinite(y) && isfinite(z)) {
+            const float l = range_f32(x, y, z);
+            if (l >= sc.r_min && l <= sc.r_max && l > 0.f) {
+                valid = 1;
+                const int p = point_pixel(sc, x, y, z, l);
+                if (p >= 0) {
+                    inpix = 1;
+                    atomicMin(&fd.win[p], ((unsigned long long)__float_as_uint(l) << 32) | (unsigned)i);
+                }
+                nb = band_blocks(sc, x, y, z, l, blocks);
+            }
+        }
+    }
+    const unsigned mv = __ballot_sync(0xffffffffu, valid), mp = __ballot_sync(0xffffffffu, inpix);
+    if ((threadIdx.x & 31) == 0 && (mv | mp)) {
+        atomicAdd(&fd.ctr[CT_VALID], (unsigned long long)__popc(mv));
+        atomicAdd(&fd.ctr[CT_PIXEL], (unsigned long long)__popc(mp));
+    }
+    int n_new = 0;
+    for (int j = 0; j < nb; ++j) {
+        const uint64_t key = pack_block(blocks[j][0], blocks[j][1], blocks[j][2]);
+        int is_new = 0;
+        const int h = hash_insert(md, key, is_new);
+        if (h < 0) continue;
+        if (is_new) {
+            ++n_new;
+            const int s = md.vals[h];
+            if (s >= 0) {
+                md.slot_key[s] = key;
+                md.slot_frame[s] = sc.frame;
+            }
+        }
+        if (atomicExch(&md.stamp[h], sc.frame) != sc.frame) {
+            const unsigned long long idx = atomicAdd(&fd.ctr[CT_TOUCHED], 1ull);
+            if (idx < (unsigned long long)md.max_blocks) fd.touched[idx] = h;
+            else atomicOr(&md.st->err, ERR_LIST_FULL);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) n_new += __shfl_xor_sync(0xffffffffu, n_new, o);
+    if ((threadIdx.x & 31) == 0 && n_new) atomicAdd(&fd.ctr[CT_NEW], (unsigned long long)n_new);
+}
+
+// Per pixel: the winner's range r, r^2 as an exact float pair, its index, and
+// its class log-likelihood row log P(O = l | I_k) of Eq. (bayesian_filter)
+// (or no likelihood when the winner carries no valid label).
+__device__ __forceinline__ void pixel_item(const float *__restrict__ pts, const int32_t *__restrict__ labels,
+                                           const float *__restrict__ probs, const ScanConst &sc, const FrameDev &fd,
+                                           int p) {
+    if (p >= sc.H * sc.W) return;
+    const unsigned long long key = fd.win[p];
+    if (key == ~0ull) {
+        fd.pix[p] = make_float4(-1.f, 0.f, 0.f, __int_as_float(-1));
+        fd.sem_ok[p] = 0;
+        return;
+    }
+    const int idx = (int)(key & 0xffffffffu);
+    const float r = __uint_as_float((unsigned)(key >> 32));
+    const float x = pts[3 * idx], y = pts[3 * idx + 1], z = pts[3 * idx + 2];
+    float a, ae, b, be, c, ce, sh, sl;
+    two_prod(x, x, a, ae);
+    two_prod(y, y, b, be);
+    two_prod(z, z, c, ce);
+    df_add(a, ae, b, be, sh, sl);
+    df_add(sh, sl, c, ce, sh, sl);
+    fd.pix[p] = make_float4(r, sh, sl, __int_as_float(idx));
+    const int C = sc.C;
+    float *out = fd.logL + (long long)p * C;
+    if (sc.has_probs) {
+        const float *q = probs + (long long)idx * C;
+        if (sc.probs_vec4) {
+            for (int cc = 0; cc < C; cc += 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(q + cc);
+                *reinterpret_cast<float4 *>(out + cc) =
+                    make_float4(logf(fmaxf(v.x, sc.lik_floor)), logf(fmaxf(v.y, sc.lik_floor)),
+                                logf(fmaxf(v.z, sc.lik_floor)), logf(fmaxf(v.w, sc.lik_floor)));
+            }
+        } else {
+            for (int cc = 0; cc < C; ++cc) out[cc] = logf(fmaxf(q[cc], sc.lik_floor));
+        }
+        fd.sem_ok[p] = 1;
+    } else {
+        const int l = labels[idx];
+        const int ok = (l >= 0 && l < C);
+        if (ok)
+            for (int cc = 0; cc < C; ++cc) out[cc] = (cc == l) ? sc.log_phit : sc.log_pmiss;
+        fd.sem_ok[p] = (uint8_t)ok;
+    }
+}
+
+template <bool F16>
+__device__ __forceinline__ float2 load_dw(const MapDev &md, long long vox) {
+    if (F16) return __half22float2(md.dw16[vox]);
+    return md.dw32[vox];
+}
+template <bool F16>
+__device__ __forceinline__ void store_dw(const MapDev &md, long long vox, float D, float W) {
+    if (F16) md.dw16[vox] = __floats2half2_rn(D, W);
+    else md.dw32[vox] = make_float2(D, W);
+}
+template <bool F16>
+__device__ __forceinline__ float load_lp(const MapDev &md, long long j) {
+    if (F16) return __half2float(md.lp16[j]);
+    return md.lp32[j];
+}
+template <bool F16>
+__device__ __forceinline__ void store_lp(const MapDev &md, long long j, float v) {
+    if (F16) md.lp16[j] = __float2half_rn(v);
+    else md.lp32[j] = v;
+}
+
+// Projective TSDF update of every voxel of the touched blocks, one warp per
+// block (16 voxels per lane, no block-wide barriers).  Voxels that also need
+// the class update (|psi| <= tau, pixel with a likelihood) are appended to a
+// compact list (voxel, pixel), warp-aggregated so that the list keeps voxel
+// order within each warp.  Each block also queues itself and its lower
+// neighbours for re-meshing, and a block allocated in this frame links
+// itself with its neighbours.
+// Offsets o (bit o, e_o = (o & 1, o >> 1 & 1, o >> 2)) whose lower neighbour
+// b - e_o reads a voxel of b: those with e_o inside the set Z of axes on which
+// the voxel sits at local coordinate 0.  Byte Z of the table is that set of o.
+constexpr unsigned long long remesh_table() {
+    unsigned long long t = 0;
+    for (int z = 0; z < 8; ++z)
+        for (int o = 0; o < 8; ++o)
+            if ((o & ~z) == 0) t |= 1ull << (8 * z + o);
+    return t;
+}
+constexpr unsigned long long REMESH_TABLE = remesh_table();
+static_assert(REMESH_TABLE == 0xFF5533110F050301ull, "re-mesh offset table");
+
+__device__ __forceinline__ unsigned remesh_offsets(int vi) {
+    const int z = ((vi & 7) == 0 ? 1 : 0) | (((vi >> 3) & 7) == 0 ? 2 : 0) | ((vi >> 6) == 0 ? 4 : 0);
+    return (unsigned)(REMESH_TABLE >> (8 * z)) & 0xffu;
+}
+
+// One voxel of the block: pixel, projective psi, running-average update,
+// and the class-update list entry.
+template <bool F16>
+__device__ __forceinline__ void tsdf_voxel(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int slot,
+                                           int bx, int by, int bz, int vi, long long &n_upd, unsigned &remesh,
+                                           int2 *wbuf, int &wcount) {
+    const int lane = threadIdx.x & 31;
+    const float tau = sc.tau;
+    const int lx = vi & 7, ly = (vi >> 3) & 7, lz = vi >> 6;
+    // offset from the sensor in voxel units: exact integer part minus the fraction's high part
+    const float m0 = (float)(8 * bx + lx - sc.k[0]), m1 = (float)(8 * by + ly - sc.k[1]),
+                m2 = (float)(8 * bz + lz - sc.k[2]);
+    const float s0 = m0 - sc.fhi[0], s1 = m1 - sc.fhi[1], s2 = m2 - sc.fhi[2];
+    // direction in the LiDAR frame (scale-free) -> pixel (Sec. III-C.1)
+    const float x0 = sc.Rt[0] * s0 + sc.Rt[1] * s1 + sc.Rt[2] * s2;
+    const float x1 = sc.Rt[3] * s0 + sc.Rt[4] * s1 + sc.Rt[5] * s2;
+    const float x2 = sc.Rt[6] * s0 + sc.Rt[7] * s1 + sc.Rt[8] * s2;
+    const float rr2 = x0 * x0 + x1 * x1 + x2 * x2;
+    bool upd = false, sem = false;
+    int p = 0;
+    if (rr2 > 0.f) {
+        const float irr = rsqrtf(rr2);
+        const float uc = (PI_F - atan2f(x1, x0)) * sc.inv_dphi;
+        const float vc = (acosf(fminf(fmaxf(x2 * irr, -1.f), 1.f)) - sc.theta0) * sc.inv_dtheta;
+        int u = (int)floorf(uc + 0.5f);
+        const int v = (int)floorf(vc + 0.5f);
+        if (u >= sc.W) u -= sc.W;
+        if (u < 0) u += sc.W;
+        if (v >= 0 && v < sc.H) {
+            p = v * sc.W + u;
+            const float4 px = fd.pix[p];
+            if (__float_as_int(px.w) >= 0) {
+                // plain FP32 psi is within ~1e-5 m of the exact value; away from +-tau it
+                // decides the update exactly: beyond +tau (+1 mm) sdf = tau and w = 1, below
+                // -tau (-1 mm) nothing; only the band in between needs the float-pair psi
+                float psi = px.x - sc.nu * (rr2 * irr);
+                float sdf = tau, w = 1.f;
+                upd = psi >= -tau - 1e-3f;
+                if (upd && psi <= tau + 1e-3f) {
+                    float e0, e1, e2, t0, t1, t2;
+                    two_sum(m0, -sc.fhi[0], t0, e0);
+                    two_sum(m1, -sc.fhi[1], t1, e1);
+                    two_sum(m2, -sc.fhi[2], t2, e2);
+                    e0 = __fsub_rn(e0, sc.flo[0]);
+                    e1 = __fsub_rn(e1, sc.flo[1]);
+                    e2 = __fsub_rn(e2, sc.flo[2]);
+                    // rho^2 in voxel units, then metres^2, as float pairs; psi = (r^2 - rho^2) / (r + rho)
+                    float a, ae, b, be, c, ce, qh, ql, mh, ml, dh, dl;
+                    two_prod(t0, t0, a, ae);
+                    two_prod(t1, t1, b, be);
+                    two_prod(t2, t2, c, ce);
+                    ae = __fmaf_rn(2.f * t0, e0, ae);
+                    be = __fmaf_rn(2.f * t1, e1, be);
+                    ce = __fmaf_rn(2.f * t2, e2, ce);
+                    df_add(a, ae, b, be, qh, ql);
+                    df_add(qh, ql, c, ce, qh, ql);
+                    df_mul(qh, ql, sc.nu2hi, sc.nu2lo, mh, ml);
+                    df_add(px.y, px.z, -mh, -ml, dh, dl);
+                    psi = __fdividef(dh + dl, px.x + mh * rsqrtf(mh));
+                    sdf = fminf(psi, tau);
+                    if (sc.weight_mode == 0) w = fminf(fmaxf((psi + tau) * sc.inv_2tau, 0.f), 1.f);
+                    upd = psi >= -tau && w > 0.f;
+                    sem = upd && fabsf(psi) <= tau && fd.sem_ok[p];
+                }
+                if (upd) {
+                    const long long vox = (long long)slot * BV + vi;
+                    const float2 dw = load_dw<F16>(md, vox);
+                    const float Wn = dw.y + w;
+                    store_dw<F16>(md, vox, __fdividef(dw.y * dw.x + w * sdf, Wn), Wn);
+                    ++n_upd;
+                    remesh |= remesh_offsets(vi);
+                }
+            }
+        }
+    }
+    // class-update entries collect in the warp's shared buffer (one global append per block)
+    const unsigned mk = __ballot_sync(0xffffffffu, sem);
+    if (sem) wbuf[wcount + __popc(mk & ((1u << lane) - 1u))] = make_int2(slot * BV + vi, p);
+    wcount += __popc(mk);
+}
+
+// One touched block (hash slot h), processed by one warp.
+template <bool F16>
+__device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int h,
+                                                int2 *wbuf, long long &n_upd) {
+    const int lane = threadIdx.x & 31;
+    const int slot = md.vals[h];
+    if (slot < 0) return;
+    const uint64_t key = md.keys[h];
+    int bx, by, bz;
+    unpack_block(key, bx, by, bz);
+    // a block allocated in this frame links itself with its neighbours
+    if (lane >= 8 && lane < 15 && md.slot_frame[slot] == sc.frame) link_block(md, key, slot, lane - 7);
+    unsigned remesh = 0;
+    int wcount = 0;
+#pragma unroll 1
+    for (int vi = lane; vi < BV; vi += 32)
+        tsdf_voxel<F16>(sc, md, fd, slot, bx, by, bz, vi, n_upd, remesh, wbuf, wcount);
+    __syncwarp();
+    // one append of the block's class-update entries
+    if (wcount) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&fd.ctr[CT_SEM], (unsigned long long)wcount);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (int i = lane; i < wcount; i += 32) {
+            if (base + i < (unsigned long long)fd.sem_cap) fd.sem_list[base + i] = wbuf[i];
+            else atomicOr(&md.st->err, ERR_LIST_FULL);
+        }
+    }
+    // queue for re-meshing this block (if any voxel changed) and each lower
+    // neighbour b - e whose cubes read a changed voxel of b, once per frame each
+    // (the block's own links: set before, or just above by this warp)
+    remesh = __reduce_or_sync(0xffffffffu, remesh);
+    bool q = false;
+    int hs = -1;
+    if (lane < 8 && ((remesh >> lane) & 1u)) {
+        hs = lane == 0 ? slot : md.nbr[slot * 16 + 8 + lane];
+        q = hs >= 0 && atomicExch(&md.dstamp_slot[hs], sc.frame) != sc.frame;
+    }
+    const unsigned mq = __ballot_sync(0xffffffffu, q);
+    if (mq) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&fd.ctr[CT_DIRTY], (unsigned long long)__popc(mq));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (q) {
+            const unsigned long long idx = base + __popc(mq & ((1u << lane) - 1u));
+            if (idx < (unsigned long long)md.max_blocks) fd.dirty[idx] = hs;
+            else atomicOr(&md.st->err, ERR_LIST_FULL);
+        }
+    }
+    __syncwarp();
+}
+
+// Recursive Bayesian class update (Eq. bayesian_filter) of the listed voxels,
+// one voxel per thread: logP_c += log L_c, renormalise by logsumexp, floor,
+// and refresh the voxel's argmax label.  A voxel's classes form one record of
+// whole 32-byte sectors (FP32: 24 floats, FP16: 32 halves for 20 classes),
+// read and written with vector accesses, padding included.
+template <bool F16, int NC>
+__device__ __forceinline__ void load_record(const MapDev &md, long long vox, float *av) {
+    if (F16) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(md.lp16 + lp_index(md, vox, 0));
+#pragma unroll
+        for (int j = 0; j < NC / 8; ++j) {
+            const uint4 u = q[j];
+            const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+            const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+            const float2 c = __half22float2(*reinterpret_cast<const __half2 *>(&u.z));
+            const float2 d = __half22float2(*reinterpret_cast<const __half2 *>(&u.w));
+            av[8 * j] = a.x; av[8 * j + 1] = a.y; av[8 * j + 2] = b.x; av[8 * j + 3] = b.y;
+            av[8 * j + 4] = c.x; av[8 * j + 5] = c.y; av[8 * j + 6] = d.x; av[8 * j + 7] = d.y;
+        }
+#pragma unroll
+        for (int cc = (NC / 8) * 8; cc < NC; ++cc) av[cc] = __half2float(md.lp16[lp_index(md, vox, cc)]);
+    } else {
+        const float4 *q = reinterpret_cast<const float4 *>(md.lp32 + lp_index(md, vox, 0));
+#pragma unroll
+        for (int j = 0; j < NC / 4; ++j) {
+            const float4 v = q[j];
+            av[4 * j] = v.x; av[4 * j + 1] = v.y; av[4 * j + 2] = v.z; av[4 * j + 3] = v.w;
+        }
+#pragma unroll
+        for (int cc = (NC / 4) * 4; cc < NC; ++cc) av[cc] = md.lp32[lp_index(md, vox, cc)];
+    }
+}
+
+// Store a full padded record (NCP elements, zeros beyond NC) so that every
+// written sector is written whole.
+template <bool F16, int NC, int NCP>
+__device__ __forceinline__ void store_record(const MapDev &md, long long vox, const float *nv) {
+    if (F16) {
+        uint4 *q = reinterpret_cast<uint4 *>(md.lp16 + lp_index(md, vox, 0));
+#pragma unroll
+        for (int j = 0; j < NCP / 8; ++j) {
+            float f[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) f[k] = (8 * j + k < NC) ? nv[8 * j + k] : 0.f;
+            uint4 u;
+            __half2 h0 = __floats2half2_rn(f[0], f[1]), h1 = __floats2half2_rn(f[2], f[3]);
+            __half2 h2 = __floats2half2_rn(f[4], f[5]), h3 = __floats2half2_rn(f[6], f[7]);
+            u.x = *reinterpret_cast<unsigned *>(&h0);
+            u.y = *reinterpret_cast<unsigned *>(&h1);
+            u.z = *reinterpret_cast<unsigned *>(&h2);
+            u.w = *reinterpret_cast<unsigned *>(&h3);
+            q[j] = u;
+        }
+    } else {
+        float4 *q = reinterpret_cast<float4 *>(md.lp32 + lp_index(md, vox, 0));
+#pragma unroll
+        for (int j = 0; j < NCP / 4; ++j) {
+            float f[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[k] = (4 * j + k < NC) ? nv[4 * j + k] : 0.f;
+            q[j] = make_float4(f[0], f[1], f[2], f[3]);
+        }
+    }
+}
+
+template <bool F16, int NC>
+__device__ __forceinline__ void semantic_item(const ScanConst &sc, const MapDev &md, const FrameDev &fd,
+                                              unsigned long long e) {
+    constexpr int MAXC_RT = 64;
+    // padded record length for the compile-time class count (32-byte sectors)
+    constexpr int NCP = NC > 0 ? (F16 ? ((NC + 15) / 16) * 16 : ((NC + 7) / 8) * 8) : 1;
+    const int C = NC > 0 ? NC : sc.C;
+    const int2 ent = fd.sem_list[e];
+    const long long vox = ent.x;
+    const float *lrow = fd.logL + (long long)ent.y * C;
+    float m = -INFINITY;
+    if (NC > 0) {
+        float av[NC > 0 ? NC : 1];
+        load_record<F16, (NC > 0 ? NC : 1)>(md, vox, av);
+        if (NC % 4 == 0) {
+#pragma unroll
+            for (int cc = 0; cc < (NC > 0 ? NC : 1); cc += 4) {
+                const float4 l4 = *reinterpret_cast<const float4 *>(lrow + cc);
+                av[cc] += l4.x;
+                av[cc + 1] += l4.y;
+                av[cc + 2] += l4.z;
+                av[cc + 3] += l4.w;
+            }
+        } else {
+#pragma unroll
+            for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) av[cc] += lrow[cc];
+        }
+#pragma unroll
+        for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) m = fmaxf(m, av[cc]);
+        float ssum = 0.f;
+#pragma unroll
+        for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) ssum += expf(av[cc] - m);
+        const float lse = m + logf(ssum);
+        int best = 0;
+        float bv = -INFINITY;
+#pragma unroll
+        for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) {
+            av[cc] = fmaxf(av[cc] - lse, sc.logp_floor);
+            const float stored = F16 ? __half2float(__float2half_rn(av[cc])) : av[cc];
+            if (stored > bv) {
+                bv = stored;
+                best = cc;
+            }
+        }
+        store_record<F16, (NC > 0 ? NC : 1), NCP>(md, vox, av);
+        md.label[vox] = (uint8_t)best;
+    } else {
+        float av[MAXC_RT];
+        for (int cc = 0; cc < C; ++cc) {
+            av[cc] = load_lp<F16>(md, lp_index(md, vox, cc)) + lrow[cc];
+            m = fmaxf(m, av[cc]);
+        }
+        float ssum = 0.f;
+        for (int cc = 0; cc < C; ++cc) ssum += expf(av[cc] - m);
+        const float lse = m + logf(ssum);
+        int best = 0;
+        float bv = -INFINITY;
+        for (int cc = 0; cc < C; ++cc) {
+            const float nv = fmaxf(av[cc] - lse, sc.logp_floor);
+            store_lp<F16>(md, lp_index(md, vox, cc), nv);
+            const float stored = F16 ? __half2float(__float2half_rn(nv)) : nv;
+            if (stored > bv) {
+                bv = stored;
+                best = cc;
+            }
+        }
+        md.label[vox] = (uint8_t)best;
+    }
+}
+
+constexpr int EDGE_WORDS = (MC_EDGES + 31) / 32;   // 61 words of lattice-edge bits per block
+constexpr int MESH_WARPS = 8;                       // warps (blocks in flight) per CTA
+
+// Local index of the lattice edge that cube edge ce of the cube anchored at
+// (ax, ay, az) lies on: axis * 648 + a + 8 (b + 9 c), with a the coordinate
+// along the axis and b, c the coordinates along the next two axes cyclically.
+__device__ __forceinline__ int cube_edge_index(int ce, int ax, int ay, int az) {
+    const int axis = ce >> 2;
+    const int pa = axis == 0 ? ax : (axis == 1 ? ay : az);
+    const int pb = (axis == 0 ? ay : (axis == 1 ? az : ax)) + (ce & 1);
+    const int pc = (axis == 0 ? az : (axis == 1 ? ax : ay)) + ((ce >> 1) & 1);
+    return axis * 648 + pa + 8 * (pb + 9 * pc);
+}
+
+// Per-warp staging of one block: the 9^3 region (block + upper faces).
+struct MeshWarpSmem {
+    float D[729];
+    uint32_t rowm[81];        // per (y, z) row of 9 voxels: bits 0..8 observed, bits 16..24 D < 0
+    unsigned edge[64];        // lattice-edge bitmap (61 words used)
+    int woff[64];             // vertex number of each word's first set bit
+    int nb[8];                // slots of this block (0) and its 7 upper neighbours, -1 if none
+    uint8_t F[729];           // bit 0 observed (W > 0), bit 1 D < 0
+    uint8_t lab[729];
+    uint8_t cs[512];          // cube case
+};
+
+struct MeshCtaSmem {
+    int8_t tri[256 * MC_MAXTRI * 3];
+    uint8_t ntri[256];
+    uchar4 pal[256];
+    MeshWarpSmem w[MESH_WARPS];
+};
+
+__device__ __forceinline__ int face_pos(int j, int &nbi) {
+    // the 217 voxels of the region outside the block: x = 8 face, then y = 8, then z = 8
+    int x, y, z;
+    if (j < 81) {
+        x = 8; y = j % 9; z = j / 9;
+    } else if (j < 153) {
+        const int k = j - 81;
+        x = k & 7; y = 8; z = k >> 3;
+    } else {
+        const int k = j - 153;
+        x = k & 7; y = k >> 3; z = 8;
+    }
+    nbi = (x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2);
+    return x + 9 * (y + 9 * z);
+}
+
+// One block to re-mesh (pool slot `slot`), processed by one warp with its
+// staging area W; `part` selects the mesh-arena partition.
+__device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev &fd, const int8_t *__restrict__ tri,
+                                                const uint8_t *__restrict__ ntri, const uchar4 *__restrict__ pal,
+                                                MeshWarpSmem &W, int slot, int part, long long &n_v, long long &n_t) {
+    const int lane = threadIdx.x & 31;
+    const bool f32 = md.storage == 0;
+    int bx, by, bz;
+    unpack_block(md.slot_key[slot], bx, by, bz);
+    // slots of the 7 upper neighbours, from the per-slot links
+    if (lane < 8) W.nb[lane] = lane == 0 ? slot : md.nbr[slot * 16 + lane];
+    int seen = 0;   // bit 0: an observed voxel with D < 0, bit 1: one with D >= 0
+#pragma unroll 4
+    for (int v = lane; v < BV; v += 32) {
+        const int r = (v & 7) + 9 * (((v >> 3) & 7) + 9 * (v >> 6));
+        const long long vox = (long long)slot * BV + v;
+        const float2 dw = f32 ? md.dw32[vox] : __half22float2(md.dw16[vox]);
+        const int f = (dw.y > 0.f ? 1 : 0) | (dw.x < 0.f ? 2 : 0);
+        W.D[r] = dw.x;
+        W.F[r] = (uint8_t)f;
+        W.lab[r] = md.label[vox];
+        if (f & 1) seen |= (f & 2) ? 1 : 2;
+    }
+    __syncwarp();
+#pragma unroll 2
+    for (int j = lane; j < 217; j += 32) {
+        int nbi;
+        const int r = face_pos(j, nbi);
+        const int s = W.nb[nbi];
+        float D = 0.f;
+        int f = 0;
+        uint8_t lab = 0;
+        if (s >= 0) {
+            const int x = r % 9, y = (r / 9) % 9, z = r / 81;
+            const long long vox = (long long)s * BV + (x & 7) + 8 * (y & 7) + 64 * (z & 7);
+            const float2 dw = f32 ? md.dw32[vox] : __half22float2(md.dw16[vox]);
+            D = dw.x;
+            f = (dw.y > 0.f ? 1 : 0) | (dw.x < 0.f ? 2 : 0);
+            lab = md.label[vox];
+        }
+        W.D[r] = D;
+        W.F[r] = (uint8_t)f;
+        W.lab[r] = lab;
+        if (f & 1) seen |= (f & 2) ? 1 : 2;
+    }
+    const bool any_neg = __any_sync(0xffffffffu, seen & 1), any_pos = __any_sync(0xffffffffu, seen & 2);
+    if (!(any_neg && any_pos)) {
+        // no sign change among observed voxels: no cube can cross; drop the old segment
+        if (lane == 0) {
+            const int4 old = md.seg[slot];
+            if (old.y | old.w) md.seg[slot] = make_int4(0, 0, 0, 0);
+        }
+        __syncwarp();
+        return;
+    }
+    __syncwarp();
+    // packed row masks of the 81 (y, z) rows
+    for (int rw = lane; rw < 81; rw += 32) {
+        uint32_t m = 0;
+#pragma unroll
+        for (int x = 0; x < 9; ++x) {
+            const uint32_t f = W.F[x + 9 * rw];
+            m |= ((f & 1u) << x) | (((f >> 1) & 1u) << (16 + x));
+        }
+        W.rowm[rw] = m;
+    }
+    for (int k = lane; k < 64; k += 32) W.edge[k] = 0u;
+    __syncwarp();
+    // cube rows (ay, az) = lane and lane + 32: eight cubes along x from four row masks
+    int cnt_t = 0;
+#pragma unroll 1
+    for (int q = 0; q < 2; ++q) {
+        const int cr = lane + 32 * q, ay = cr & 7, az = cr >> 3;
+        const uint32_t m00 = W.rowm[ay + 9 * az], m10 = W.rowm[ay + 1 + 9 * az];
+        const uint32_t m01 = W.rowm[ay + 9 * (az + 1)], m11 = W.rowm[ay + 1 + 9 * (az + 1)];
+        const uint32_t okm = m00 & m10 & m01 & m11;
+#pragma unroll 1
+        for (int ax = 0; ax < 8; ++ax) {
+            const bool ok = ((okm >> ax) & 3u) == 3u;
+            const int cs = (int)(((m00 >> (16 + ax)) & 3u) | (((m10 >> (16 + ax)) & 3u) << 2) |
+                                 (((m01 >> (16 + ax)) & 3u) << 4) | (((m11 >> (16 + ax)) & 3u) << 6));
+            const int nt = ok ? ntri[cs] : 0;
+            W.cs[ax + 8 * cr] = (uint8_t)(nt ? cs : 0);
+            cnt_t += nt;
+            if (nt) {
+#pragma unroll
+                for (int ce = 0; ce < 12; ++ce) {
+                    const int axis = ce >> 2, a1 = axis == 2 ? 0 : axis + 1, a2 = axis == 0 ? 2 : axis - 1;
+                    const int clo = ((ce & 1) << a1) | (((ce >> 1) & 1) << a2);
+                    if (((cs >> clo) ^ (cs >> (clo | (1 << axis)))) & 1) {
+                        const int e = cube_edge_index(ce, ax, ay, az);
+                        atomicOr(&W.edge[e >> 5], 1u << (e & 31));
+                    }
+                }
+            }
+        }
+    }
+    int tot_t;
+    const int toff = warp_exclusive_scan(cnt_t, tot_t);
+    if (tot_t == 0) {
+        if (lane == 0) {
+            const int4 old = md.seg[slot];
+            if (old.y | old.w) md.seg[slot] = make_int4(0, 0, 0, 0);
+        }
+        __syncwarp();
+        return;
+    }
+    __syncwarp();
+    // vertex numbering: popcount prefix over the bitmap (words lane, lane + 32)
+    const int c0 = __popc(W.edge[lane]), c1 = lane + 32 < EDGE_WORDS ? __popc(W.edge[lane + 32]) : 0;
+    int tot_lo, tot_v;
+    const int off_lo = warp_exclusive_scan(c0, tot_lo);
+    const int off_hi = warp_exclusive_scan(c1, tot_v);
+    W.woff[lane] = off_lo;
+    W.woff[lane + 32] = tot_lo + off_hi;
+    tot_v += tot_lo;
+    // reserve arena space in this warp's partition (two lanes, two cursors)
+    unsigned long long res = 0, lim = 0;
+    if (lane == 0) {
+        res = atomicAdd(&md.st->arena_v[part], (unsigned long long)tot_v);
+        lim = md.st->arena_v_end[part];
+    }
+    if (lane == 1) {
+        res = atomicAdd(&md.st->arena_t[part], (unsigned long long)tot_t);
+        lim = md.st->arena_t_end[part];
+    }
+    const long long vo = (long long)__shfl_sync(0xffffffffu, res, 0);
+    const long long to = (long long)__shfl_sync(0xffffffffu, res, 1);
+    const bool fits = (unsigned long long)vo + tot_v <= __shfl_sync(0xffffffffu, lim, 0) &&
+                      (unsigned long long)to + tot_t <= __shfl_sync(0xffffffffu, lim, 1);
+    if (lane == 0) {
+        if (fits) {
+            md.seg[slot] = make_int4((int)vo, tot_v, (int)to, tot_t);
+        } else {
+            atomicOr(&md.st->err, ERR_ARENA_FULL);
+            md.seg[slot] = make_int4(0, 0, 0, 0);
+        }
+        n_v += tot_v;
+        n_t += tot_t;
+    }
+    __syncwarp();
+    if (fits) {
+        // vertices: bytes b = lane + 32 k of the bitmap, edges 8 b .. 8 b + 7
+        for (int b = lane; b < 4 * EDGE_WORDS; b += 32) {
+            const unsigned word = W.edge[b >> 2];
+            unsigned bits = (word >> ((b & 3) * 8)) & 0xffu;
+            while (bits) {
+                const int q = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int e = 8 * b + q;
+                const int vid = W.woff[b >> 2] + __popc(word & ((1u << (e & 31)) - 1u));
+                const int axis = e / 648, rem = e - 648 * axis;
+                const int ca = rem & 7, cb = (rem >> 3) % 9, cc = (rem >> 3) / 9;
+                const int x = axis == 0 ? ca : (axis == 1 ? cc : cb);
+                const int y = axis == 0 ? cb : (axis == 1 ? ca : cc);
+                const int z = axis == 0 ? cc : (axis == 1 ? cb : ca);
+                const int r0 = x + 9 * (y + 9 * z);
+                const int r1 = r0 + (axis == 0 ? 1 : (axis == 1 ? 9 : 81));
+                const float D0 = W.D[r0], D1 = W.D[r1];
+                const float t = D0 / (D0 - D1);
+                const int gx = 8 * bx + x, gy = 8 * by + y, gz = 8 * bz + z;
+                float px = md.nu * (float)gx, py = md.nu * (float)gy, pz = md.nu * (float)gz;
+                if (axis == 0) px = md.nu * ((float)gx + t);
+                else if (axis == 1) py = md.nu * ((float)gy + t);
+                else pz = md.nu * ((float)gz + t);
+                // label of the endpoint nearer the surface (lower endpoint on ties)
+                const int lab = fabsf(D1) < fabsf(D0) ? W.lab[r1] : W.lab[r0];
+                const uchar4 col = pal[lab];
+                const unsigned packed = (unsigned)col.x | ((unsigned)col.y << 8) | ((unsigned)col.z << 16) |
+                                        ((unsigned)lab << 24);
+                md.av[vo + vid] = make_float4(px, py, pz, __uint_as_float(packed));
+                md.ak[vo + vid] = edge_key(gx, gy, gz, axis);
+            }
+        }
+        // triangles of this lane's cubes, in counting order
+        long long tb = to + toff;
+#pragma unroll 1
+        for (int q = 0; q < 2; ++q) {
+            const int cr = lane + 32 * q, ay = cr & 7, az = cr >> 3;
+#pragma unroll 1
+            for (int ax = 0; ax < 8; ++ax) {
+                const int a = ax + 8 * cr;
+                const int cs = W.cs[a];
+                const int nt = cs ? ntri[cs] : 0;
+                for (int j = 0; j < nt; ++j) {
+                    int vid[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const int e = cube_edge_index(tri[(cs * MC_MAXTRI + j) * 3 + k], ax, ay, az);
+                        vid[k] = W.woff[e >> 5] + __popc(W.edge[e >> 5] & ((1u << (e & 31)) - 1u));
+                    }
+                    md.at[tb + j] = make_ushort4((unsigned short)vid[0], (unsigned short)vid[1],
+                                                 (unsigned short)vid[2], (unsigned short)a);
+                }
+                tb += nt;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+}  // namespace stsdf

@@ -8,167 +8,12 @@
 // [8b, 8b + 8) on every axis.  Endpoints and crossing parameters follow a
 // fixed IEEE single-precision recipe (correctly rounded intrinsics, no
 // contraction), which makes the allocated block set reproducible bit for bit.
-#include "kernels.h"
+#include "frame_bodies.cuh"
 
 namespace stsdf {
 
-// Blocks met by the band of one point, in path order; returns their count.
-__device__ int band_blocks(const ScanConst &sc, float x0, float x1, float x2, float l, int (*out)[3]) {
-    const float q = __fdiv_rn(sc.tau, l);
-    float f0 = __fsub_rn(1.f, q);
-    if (f0 < 0.f) f0 = 0.f;
-    const float f1 = __fadd_rn(1.f, q);
-    float e0[3], e1[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        float s = __fmul_rn(sc.Rv[3 * k], x0);
-        s = __fadd_rn(s, __fmul_rn(sc.Rv[3 * k + 1], x1));
-        s = __fadd_rn(s, __fmul_rn(sc.Rv[3 * k + 2], x2));
-        e0[k] = __fadd_rn(sc.tv[k], __fmul_rn(s, f0));
-        e1[k] = __fadd_rn(sc.tv[k], __fmul_rn(s, f1));
-    }
-    // crossing events: parameter, kind (0: entered at t, 1: left after t), axis, step
-    float et[3 * MAX_AXIS_CROSS];
-    int einfo[3 * MAX_AXIS_CROSS];
-    int ne = 0;
-    int cur[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int b0 = (int)floorf(__fmul_rn(e0[k], 0.125f));
-        const int b1 = (int)floorf(__fmul_rn(e1[k], 0.125f));
-        cur[k] = b0;
-        const float d = __fsub_rn(e1[k], e0[k]);
-        if (b1 > b0) {
-            for (int b = b0 + 1, c = 0; b <= b1 && c < MAX_AXIS_CROSS; ++b, ++c) {
-                et[ne] = __fdiv_rn(__fsub_rn((float)(8 * b), e0[k]), d);
-                einfo[ne++] = (0 << 4) | (k << 1) | 1;
-            }
-        } else if (b1 < b0) {
-            for (int b = b0, c = 0; b > b1 && c < MAX_AXIS_CROSS; --b, ++c) {
-                et[ne] = __fdiv_rn(__fsub_rn((float)(8 * b), e0[k]), d);
-                einfo[ne++] = (1 << 4) | (k << 1) | 0;
-            }
-        }
-    }
-    // insertion sort by (t, kind)
-    for (int i = 1; i < ne; ++i) {
-        float t = et[i];
-        int inf = einfo[i];
-        int j = i - 1;
-        while (j >= 0 && (et[j] > t || (et[j] == t && (einfo[j] >> 4) > (inf >> 4)))) {
-            et[j + 1] = et[j];
-            einfo[j + 1] = einfo[j];
-            --j;
-        }
-        et[j + 1] = t;
-        einfo[j + 1] = inf;
-    }
-    int nb = 0;
-    out[nb][0] = cur[0];
-    out[nb][1] = cur[1];
-    out[nb][2] = cur[2];
-    ++nb;
-    for (int i = 0; i < ne;) {
-        int j = i;
-        while (j < ne && et[j] == et[i] && (einfo[j] >> 4) == (einfo[i] >> 4)) {
-            const int ax = (einfo[j] >> 1) & 3;
-            cur[ax] += (einfo[j] & 1) ? 1 : -1;
-            ++j;
-        }
-        out[nb][0] = cur[0];
-        out[nb][1] = cur[1];
-        out[nb][2] = cur[2];
-        ++nb;
-        i = j;
-    }
-    return nb;
-}
-
-// Find or insert a block key; lock-free (compare-and-swap on the key slot).
-// The inserting thread takes the next pool slot; readers of vals[] run in
-// later kernels only, so no thread waits on another.
-__device__ int hash_insert(const MapDev &md, uint64_t key, int &is_new) {
-    uint64_t h = fmix64(key) & md.mask;
-    for (int p = 0; p < MAX_PROBES; ++p) {
-        const uint64_t k = md.keys[h];
-        if (k == key) {
-            is_new = 0;
-            return (int)h;
-        }
-        if (k == EMPTY_KEY) {
-            const uint64_t old = atomicCAS((unsigned long long *)&md.keys[h], EMPTY_KEY, key);
-            if (old == EMPTY_KEY) {
-                const unsigned long long s = atomicAdd(&md.st->pool_count, 1ull);
-                if (s < (unsigned long long)md.max_blocks) {
-                    md.vals[h] = (int)s;
-                } else {
-                    md.vals[h] = -1;
-                    atomicOr(&md.st->err, ERR_POOL_FULL);
-                }
-                is_new = 1;
-                return (int)h;
-            }
-            if (old == key) {
-                is_new = 0;
-                return (int)h;
-            }
-        }
-        h = (h + 1) & md.mask;
-    }
-    atomicOr(&md.st->err, ERR_HASH_PROBES);
-    return -1;
-}
-
-// One thread per point: validity, the range-image winner of its pixel
-// (u = round((pi - atan2(y, x)) / dphi) mod W, v = round((acos(z / r) -
-// theta0) / dtheta); nearest point wins, equal ranges the lower index, by one
-// 64-bit atomicMin on (range bits << 32 | index)), and the blocks of its band.
 __global__ void __launch_bounds__(256) k_points(const float *__restrict__ pts, ScanConst sc, MapDev md, FrameDev fd) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int nb = 0, valid = 0, inpix = 0;
-    int blocks[MAX_BAND_BLOCKS][3];
-    if (i < sc.n) {
-        const float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
-        if (isfinite(x) && isfinite(y) && isfinite(z)) {
-            const float l = range_f32(x, y, z);
-            if (l >= sc.r_min && l <= sc.r_max && l > 0.f) {
-                valid = 1;
-                const int p = point_pixel(sc, x, y, z, l);
-                if (p >= 0) {
-                    inpix = 1;
-                    atomicMin(&fd.win[p], ((unsigned long long)__float_as_uint(l) << 32) | (unsigned)i);
-                }
-                nb = band_blocks(sc, x, y, z, l, blocks);
-            }
-        }
-    }
-    const unsigned mv = __ballot_sync(0xffffffffu, valid), mp = __ballot_sync(0xffffffffu, inpix);
-    if ((threadIdx.x & 31) == 0 && (mv | mp)) {
-        atomicAdd(&fd.ctr[CT_VALID], (unsigned long long)__popc(mv));
-        atomicAdd(&fd.ctr[CT_PIXEL], (unsigned long long)__popc(mp));
-    }
-    int n_new = 0;
-    for (int j = 0; j < nb; ++j) {
-        const uint64_t key = pack_block(blocks[j][0], blocks[j][1], blocks[j][2]);
-        int is_new = 0;
-        const int h = hash_insert(md, key, is_new);
-        if (h < 0) continue;
-        if (is_new) {
-            ++n_new;
-            const int s = md.vals[h];
-            if (s >= 0) {
-                md.slot_key[s] = key;
-                md.slot_frame[s] = sc.frame;
-            }
-        }
-        if (atomicExch(&md.stamp[h], sc.frame) != sc.frame) {
-            const unsigned long long idx = atomicAdd(&fd.ctr[CT_TOUCHED], 1ull);
-            if (idx < (unsigned long long)md.max_blocks) fd.touched[idx] = h;
-            else atomicOr(&md.st->err, ERR_LIST_FULL);
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) n_new += __shfl_xor_sync(0xffffffffu, n_new, o);
-    if ((threadIdx.x & 31) == 0 && n_new) atomicAdd(&fd.ctr[CT_NEW], (unsigned long long)n_new);
+    points_item(pts, sc, md, fd, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Link every allocated block (after host-side writes).

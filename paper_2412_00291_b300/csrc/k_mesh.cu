@@ -12,62 +12,14 @@
 // each per block.
 // Each vertex carries the most probable class of the edge endpoint nearer
 // the surface (lower endpoint on ties) and that class's palette colour.
-#include "kernels.h"
+#include "batch.h"
+#include "frame_bodies.cuh"
 
 namespace stsdf {
 
 // generated case table, shared by every map of the process
 static int8_t *h_tri_dev = nullptr;      // [256][MC_MAXTRI][3] cube-edge ids
 static uint8_t *h_ntri_dev = nullptr;    // [256] triangles per case
-
-constexpr int EDGE_WORDS = (MC_EDGES + 31) / 32;   // 61 words of lattice-edge bits per block
-constexpr int MESH_WARPS = 8;                       // warps (blocks in flight) per CTA
-
-// Local index of the lattice edge that cube edge ce of the cube anchored at
-// (ax, ay, az) lies on: axis * 648 + a + 8 (b + 9 c), with a the coordinate
-// along the axis and b, c the coordinates along the next two axes cyclically.
-__device__ __forceinline__ int cube_edge_index(int ce, int ax, int ay, int az) {
-    const int axis = ce >> 2;
-    const int pa = axis == 0 ? ax : (axis == 1 ? ay : az);
-    const int pb = (axis == 0 ? ay : (axis == 1 ? az : ax)) + (ce & 1);
-    const int pc = (axis == 0 ? az : (axis == 1 ? ax : ay)) + ((ce >> 1) & 1);
-    return axis * 648 + pa + 8 * (pb + 9 * pc);
-}
-
-// Per-warp staging of one block: the 9^3 region (block + upper faces).
-struct MeshWarpSmem {
-    float D[729];
-    uint32_t rowm[81];        // per (y, z) row of 9 voxels: bits 0..8 observed, bits 16..24 D < 0
-    unsigned edge[64];        // lattice-edge bitmap (61 words used)
-    int woff[64];             // vertex number of each word's first set bit
-    int nb[8];                // slots of this block (0) and its 7 upper neighbours, -1 if none
-    uint8_t F[729];           // bit 0 observed (W > 0), bit 1 D < 0
-    uint8_t lab[729];
-    uint8_t cs[512];          // cube case
-};
-
-struct MeshCtaSmem {
-    int8_t tri[256 * MC_MAXTRI * 3];
-    uint8_t ntri[256];
-    uchar4 pal[256];
-    MeshWarpSmem w[MESH_WARPS];
-};
-
-__device__ __forceinline__ int face_pos(int j, int &nbi) {
-    // the 217 voxels of the region outside the block: x = 8 face, then y = 8, then z = 8
-    int x, y, z;
-    if (j < 81) {
-        x = 8; y = j % 9; z = j / 9;
-    } else if (j < 153) {
-        const int k = j - 81;
-        x = k & 7; y = 8; z = k >> 3;
-    } else {
-        const int k = j - 153;
-        x = k & 7; y = k >> 3; z = 8;
-    }
-    nbi = (x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2);
-    return x + 9 * (y + 9 * z);
-}
 
 __global__ void __launch_bounds__(32 * MESH_WARPS) k_mesh(MapDev md, FrameDev fd, const int8_t *__restrict__ ttri,
                                                            const uint8_t *__restrict__ tntri,
@@ -81,208 +33,13 @@ __global__ void __launch_bounds__(32 * MESH_WARPS) k_mesh(MapDev md, FrameDev fd
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    MeshWarpSmem &W = S.w[wid];
     unsigned long long nd = *(volatile unsigned long long *)&fd.ctr[CT_DIRTY];
     if (nd > (unsigned long long)md.max_blocks) nd = md.max_blocks;
     const long long nwarps = (long long)gridDim.x * MESH_WARPS;
+    const int part = (int)((blockIdx.x * MESH_WARPS + wid) % ARENA_PARTS);
     long long n_v = 0, n_t = 0;
-    const bool f32 = md.storage == 0;
-    for (long long li = (long long)blockIdx.x * MESH_WARPS + wid; li < (long long)nd; li += nwarps) {
-        const int slot = fd.dirty[li];
-        int bx, by, bz;
-        unpack_block(md.slot_key[slot], bx, by, bz);
-        // slots of the 7 upper neighbours, from the per-slot links
-        if (lane < 8) W.nb[lane] = lane == 0 ? slot : md.nbr[slot * 16 + lane];
-        int seen = 0;   // bit 0: an observed voxel with D < 0, bit 1: one with D >= 0
-#pragma unroll 4
-        for (int v = lane; v < BV; v += 32) {
-            const int r = (v & 7) + 9 * (((v >> 3) & 7) + 9 * (v >> 6));
-            const long long vox = (long long)slot * BV + v;
-            const float2 dw = f32 ? md.dw32[vox] : __half22float2(md.dw16[vox]);
-            const int f = (dw.y > 0.f ? 1 : 0) | (dw.x < 0.f ? 2 : 0);
-            W.D[r] = dw.x;
-            W.F[r] = (uint8_t)f;
-            W.lab[r] = md.label[vox];
-            if (f & 1) seen |= (f & 2) ? 1 : 2;
-        }
-        __syncwarp();
-#pragma unroll 2
-        for (int j = lane; j < 217; j += 32) {
-            int nbi;
-            const int r = face_pos(j, nbi);
-            const int s = W.nb[nbi];
-            float D = 0.f;
-            int f = 0;
-            uint8_t lab = 0;
-            if (s >= 0) {
-                const int x = r % 9, y = (r / 9) % 9, z = r / 81;
-                const long long vox = (long long)s * BV + (x & 7) + 8 * (y & 7) + 64 * (z & 7);
-                const float2 dw = f32 ? md.dw32[vox] : __half22float2(md.dw16[vox]);
-                D = dw.x;
-                f = (dw.y > 0.f ? 1 : 0) | (dw.x < 0.f ? 2 : 0);
-                lab = md.label[vox];
-            }
-            W.D[r] = D;
-            W.F[r] = (uint8_t)f;
-            W.lab[r] = lab;
-            if (f & 1) seen |= (f & 2) ? 1 : 2;
-        }
-        const bool any_neg = __any_sync(0xffffffffu, seen & 1), any_pos = __any_sync(0xffffffffu, seen & 2);
-        if (!(any_neg && any_pos)) {
-            // no sign change among observed voxels: no cube can cross; drop the old segment
-            if (lane == 0) {
-                const int4 old = md.seg[slot];
-                if (old.y | old.w) md.seg[slot] = make_int4(0, 0, 0, 0);
-            }
-            __syncwarp();
-            continue;
-        }
-        __syncwarp();
-        // packed row masks of the 81 (y, z) rows
-        for (int rw = lane; rw < 81; rw += 32) {
-            uint32_t m = 0;
-#pragma unroll
-            for (int x = 0; x < 9; ++x) {
-                const uint32_t f = W.F[x + 9 * rw];
-                m |= ((f & 1u) << x) | (((f >> 1) & 1u) << (16 + x));
-            }
-            W.rowm[rw] = m;
-        }
-        for (int k = lane; k < 64; k += 32) W.edge[k] = 0u;
-        __syncwarp();
-        // cube rows (ay, az) = lane and lane + 32: eight cubes along x from four row masks
-        int cnt_t = 0;
-#pragma unroll 1
-        for (int q = 0; q < 2; ++q) {
-            const int cr = lane + 32 * q, ay = cr & 7, az = cr >> 3;
-            const uint32_t m00 = W.rowm[ay + 9 * az], m10 = W.rowm[ay + 1 + 9 * az];
-            const uint32_t m01 = W.rowm[ay + 9 * (az + 1)], m11 = W.rowm[ay + 1 + 9 * (az + 1)];
-            const uint32_t okm = m00 & m10 & m01 & m11;
-#pragma unroll 1
-            for (int ax = 0; ax < 8; ++ax) {
-                const bool ok = ((okm >> ax) & 3u) == 3u;
-                const int cs = (int)(((m00 >> (16 + ax)) & 3u) | (((m10 >> (16 + ax)) & 3u) << 2) |
-                                     (((m01 >> (16 + ax)) & 3u) << 4) | (((m11 >> (16 + ax)) & 3u) << 6));
-                const int nt = ok ? S.ntri[cs] : 0;
-                W.cs[ax + 8 * cr] = (uint8_t)(nt ? cs : 0);
-                cnt_t += nt;
-                if (nt) {
-#pragma unroll
-                    for (int ce = 0; ce < 12; ++ce) {
-                        const int axis = ce >> 2, a1 = axis == 2 ? 0 : axis + 1, a2 = axis == 0 ? 2 : axis - 1;
-                        const int clo = ((ce & 1) << a1) | (((ce >> 1) & 1) << a2);
-                        if (((cs >> clo) ^ (cs >> (clo | (1 << axis)))) & 1) {
-                            const int e = cube_edge_index(ce, ax, ay, az);
-                            atomicOr(&W.edge[e >> 5], 1u << (e & 31));
-                        }
-                    }
-                }
-            }
-        }
-        int tot_t;
-        const int toff = warp_exclusive_scan(cnt_t, tot_t);
-        if (tot_t == 0) {
-            if (lane == 0) {
-                const int4 old = md.seg[slot];
-                if (old.y | old.w) md.seg[slot] = make_int4(0, 0, 0, 0);
-            }
-            __syncwarp();
-            continue;
-        }
-        __syncwarp();
-        // vertex numbering: popcount prefix over the bitmap (words lane, lane + 32)
-        const int c0 = __popc(W.edge[lane]), c1 = lane + 32 < EDGE_WORDS ? __popc(W.edge[lane + 32]) : 0;
-        int tot_lo, tot_v;
-        const int off_lo = warp_exclusive_scan(c0, tot_lo);
-        const int off_hi = warp_exclusive_scan(c1, tot_v);
-        W.woff[lane] = off_lo;
-        W.woff[lane + 32] = tot_lo + off_hi;
-        tot_v += tot_lo;
-        // reserve arena space in this warp's partition (two lanes, two cursors)
-        const int part = (int)((blockIdx.x * MESH_WARPS + wid) % ARENA_PARTS);
-        unsigned long long res = 0, lim = 0;
-        if (lane == 0) {
-            res = atomicAdd(&md.st->arena_v[part], (unsigned long long)tot_v);
-            lim = md.st->arena_v_end[part];
-        }
-        if (lane == 1) {
-            res = atomicAdd(&md.st->arena_t[part], (unsigned long long)tot_t);
-            lim = md.st->arena_t_end[part];
-        }
-        const long long vo = (long long)__shfl_sync(0xffffffffu, res, 0);
-        const long long to = (long long)__shfl_sync(0xffffffffu, res, 1);
-        const bool fits = (unsigned long long)vo + tot_v <= __shfl_sync(0xffffffffu, lim, 0) &&
-                          (unsigned long long)to + tot_t <= __shfl_sync(0xffffffffu, lim, 1);
-        if (lane == 0) {
-            if (fits) {
-                md.seg[slot] = make_int4((int)vo, tot_v, (int)to, tot_t);
-            } else {
-                atomicOr(&md.st->err, ERR_ARENA_FULL);
-                md.seg[slot] = make_int4(0, 0, 0, 0);
-            }
-            n_v += tot_v;
-            n_t += tot_t;
-        }
-        __syncwarp();
-        if (fits) {
-            // vertices: bytes b = lane + 32 k of the bitmap, edges 8 b .. 8 b + 7
-            for (int b = lane; b < 4 * EDGE_WORDS; b += 32) {
-                const unsigned word = W.edge[b >> 2];
-                unsigned bits = (word >> ((b & 3) * 8)) & 0xffu;
-                while (bits) {
-                    const int q = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const int e = 8 * b + q;
-                    const int vid = W.woff[b >> 2] + __popc(word & ((1u << (e & 31)) - 1u));
-                    const int axis = e / 648, rem = e - 648 * axis;
-                    const int ca = rem & 7, cb = (rem >> 3) % 9, cc = (rem >> 3) / 9;
-                    const int x = axis == 0 ? ca : (axis == 1 ? cc : cb);
-                    const int y = axis == 0 ? cb : (axis == 1 ? ca : cc);
-                    const int z = axis == 0 ? cc : (axis == 1 ? cb : ca);
-                    const int r0 = x + 9 * (y + 9 * z);
-                    const int r1 = r0 + (axis == 0 ? 1 : (axis == 1 ? 9 : 81));
-                    const float D0 = W.D[r0], D1 = W.D[r1];
-                    const float t = D0 / (D0 - D1);
-                    const int gx = 8 * bx + x, gy = 8 * by + y, gz = 8 * bz + z;
-                    float px = md.nu * (float)gx, py = md.nu * (float)gy, pz = md.nu * (float)gz;
-                    if (axis == 0) px = md.nu * ((float)gx + t);
-                    else if (axis == 1) py = md.nu * ((float)gy + t);
-                    else pz = md.nu * ((float)gz + t);
-                    // label of the endpoint nearer the surface (lower endpoint on ties)
-                    const int lab = fabsf(D1) < fabsf(D0) ? W.lab[r1] : W.lab[r0];
-                    const uchar4 col = S.pal[lab];
-                    const unsigned packed = (unsigned)col.x | ((unsigned)col.y << 8) | ((unsigned)col.z << 16) |
-                                            ((unsigned)lab << 24);
-                    md.av[vo + vid] = make_float4(px, py, pz, __uint_as_float(packed));
-                    md.ak[vo + vid] = edge_key(gx, gy, gz, axis);
-                }
-            }
-            // triangles of this lane's cubes, in counting order
-            long long tb = to + toff;
-#pragma unroll 1
-            for (int q = 0; q < 2; ++q) {
-                const int cr = lane + 32 * q, ay = cr & 7, az = cr >> 3;
-#pragma unroll 1
-                for (int ax = 0; ax < 8; ++ax) {
-                    const int a = ax + 8 * cr;
-                    const int cs = W.cs[a];
-                    const int nt = cs ? S.ntri[cs] : 0;
-                    for (int j = 0; j < nt; ++j) {
-                        int vid[3];
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const int e = cube_edge_index(S.tri[(cs * MC_MAXTRI + j) * 3 + k], ax, ay, az);
-                            vid[k] = W.woff[e >> 5] + __popc(W.edge[e >> 5] & ((1u << (e & 31)) - 1u));
-                        }
-                        md.at[tb + j] = make_ushort4((unsigned short)vid[0], (unsigned short)vid[1],
-                                                     (unsigned short)vid[2], (unsigned short)a);
-                    }
-                    tb += nt;
-                }
-            }
-        }
-        __syncwarp();
-    }
+    for (long long li = (long long)blockIdx.x * MESH_WARPS + wid; li < (long long)nd; li += nwarps)
+        mesh_block_warp(md, fd, S.tri, S.ntri, S.pal, S.w[wid], fd.dirty[li], part, n_v, n_t);
     if (lane == 0) {
         if (n_v) atomicAdd(&fd.ctr[CT_MV], (unsigned long long)n_v);
         if (n_t) atomicAdd(&fd.ctr[CT_MT], (unsigned long long)n_t);
@@ -298,6 +55,9 @@ int mesh_upload_tables(const int8_t *tri, const uint8_t *ntri) {
     }
     return 0;
 }
+
+const int8_t *mesh_table_tri() { return h_tri_dev; }
+const uint8_t *mesh_table_ntri() { return h_ntri_dev; }
 
 int mesh_blocks_per_sm() {
     const int bytes = (int)sizeof(MeshCtaSmem);

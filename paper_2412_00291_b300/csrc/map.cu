@@ -6,7 +6,10 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
+
 #include "../../include/semtsdf.h"
+#include "batch.h"
 #include "kernels.h"
 
 using namespace stsdf;
@@ -759,6 +762,284 @@ extern "C" map_status map_profile_end(map_t *m, float *ms_out, int64_t *stats_ou
 }
 
 extern "C" const char *map_last_error(map_t *m) { return m ? m->err.c_str() : g_err.c_str(); }
+
+// ===========================================================================
+// Batched persistent integration (one cooperative launch for many maps)
+// ===========================================================================
+struct map_batch_t {
+    std::vector<map_t *> maps;
+    int flags = 0;
+    BatchCtl *ctl = nullptr;          // device
+    BatchState *out_dev = nullptr;    // device
+    BatchState *out_host = nullptr;   // pinned
+    int grid[kNumBatchConfigs] = {};
+    cudaGraph_t graph[kNumBatchConfigs] = {};
+    cudaGraphExec_t exec[kNumBatchConfigs] = {};
+    cudaGraphNode_t knode[kNumBatchConfigs] = {};
+    int fixed_cfg = -1;               // set by map_batch_set_config
+    int chosen = -1;                  // autotuner's choice
+    int trials = 3;                   // timed steps per configuration
+    std::vector<float> samples[kNumBatchConfigs];
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_done = nullptr;
+    cudaStream_t cap = nullptr;       // private stream the graphs are captured on (never executes work)
+    int pending_cfg = -1;             // configuration of the step in flight (timed when tuning)
+    bool pending = false;
+    unsigned long long fault_spin = 0;   // test hook: next launch lets CTA 0 leave at once
+    BatchArgs args;                      // host staging of the kernel parameters
+    std::string err;
+};
+
+static map_status bfail(map_batch_t *b, map_status st, const std::string &msg) {
+    if (b) b->err = msg;
+    g_err = msg;
+    return st;
+}
+
+#define BCU(call)                                                                                    \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return bfail(b, MAP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+    } while (0)
+
+extern "C" map_status map_batch_create(map_t *const *maps, int32_t n_maps, int32_t flags, map_batch_t **out) {
+    map_batch_t *b = nullptr;
+    if (!maps || !out || n_maps < 1 || n_maps > BATCH_MAX)
+        return bfail(nullptr, MAP_ERR_ARG, "need 1 <= n_maps <= 48 and non-null pointers");
+    for (int i = 0; i < n_maps; ++i)
+        if (!maps[i]) return bfail(nullptr, MAP_ERR_ARG, "null map in batch");
+    int coop = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!coop) return bfail(nullptr, MAP_ERR_STATE, "device does not support cooperative launches");
+    b = new map_batch_t();
+    b->maps.assign(maps, maps + n_maps);
+    b->flags = flags;
+    for (int c = 0; c < kNumBatchConfigs; ++c) {
+        int bps = 0;
+        cudaError_t e = batch_occupancy(c, bps);
+        if (e != cudaSuccess || bps < 1) {
+            delete b;
+            return bfail(nullptr, MAP_ERR_CUDA, std::string("batch kernel occupancy: ") + cudaGetErrorString(e));
+        }
+        b->grid[c] = bps * sms;
+    }
+    if (cudaMalloc(&b->ctl, sizeof(BatchCtl)) != cudaSuccess ||
+        cudaMalloc(&b->out_dev, BATCH_MAX * sizeof(BatchState)) != cudaSuccess ||
+        cudaMallocHost(&b->out_host, BATCH_MAX * sizeof(BatchState)) != cudaSuccess) {
+        delete b;
+        return bfail(nullptr, MAP_ERR_NOMEM, "batch allocation failed");
+    }
+    cudaEventCreate(&b->ev_a);
+    cudaEventCreate(&b->ev_b);
+    cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming);
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        map_batch_destroy(b);
+        return bfail(nullptr, MAP_ERR_CUDA, "batch capture stream");
+    }
+    if (!(flags & MAP_BATCH_AUTOTUNE)) b->fixed_cfg = kNumBatchConfigs - 2;   // 8 warps, 2 items per thread
+    *out = b;
+    return MAP_OK;
+}
+
+extern "C" map_status map_batch_destroy(map_batch_t *b) {
+    if (!b) return bfail(nullptr, MAP_ERR_ARG, "null batch");
+    cudaDeviceSynchronize();
+    for (int c = 0; c < kNumBatchConfigs; ++c) {
+        if (b->exec[c]) cudaGraphExecDestroy(b->exec[c]);
+        if (b->graph[c]) cudaGraphDestroy(b->graph[c]);
+    }
+    if (b->ctl) cudaFree(b->ctl);
+    if (b->out_dev) cudaFree(b->out_dev);
+    if (b->out_host) cudaFreeHost(b->out_host);
+    if (b->ev_a) cudaEventDestroy(b->ev_a);
+    if (b->ev_b) cudaEventDestroy(b->ev_b);
+    if (b->ev_done) cudaEventDestroy(b->ev_done);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return MAP_OK;
+}
+
+// Wait for the step in flight and fold its per-map results into the maps.
+static map_status batch_retire(map_batch_t *b) {
+    if (!b->pending) return MAP_OK;
+    BCU(cudaEventSynchronize(b->ev_done));
+    b->pending = false;
+    const int timed_cfg = b->pending_cfg;
+    b->pending_cfg = -1;
+    BatchCtl ctl;
+    BCU(cudaMemcpy(&ctl, b->ctl, sizeof(ctl), cudaMemcpyDeviceToHost));
+    // a step that timed out wrote no results; the maps keep their last readings
+    if (ctl.err & ERR_TIMEOUT) return bfail(b, MAP_ERR_TIMEOUT, "batch launch: a grid barrier timed out");
+    if (timed_cfg >= 0) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, b->ev_a, b->ev_b) == cudaSuccess) b->samples[timed_cfg].push_back(ms);
+    }
+    for (size_t i = 0; i < b->maps.size(); ++i) {
+        map_t *m = b->maps[i];
+        *m->h_st = b->out_host[i].st;
+        std::memcpy(m->h_ctr, b->out_host[i].ctr, sizeof(b->out_host[i].ctr));
+        const double f = arena_fill(*m->h_st);
+        if (m->known_frame >= 0 && m->frame - 1 > m->known_frame && f >= m->known_fill)
+            m->max_append = std::max(m->max_append, (f - m->known_fill) / (double)(m->frame - 1 - m->known_frame));
+        m->known_fill = f;
+        m->known_frame = m->frame - 1;
+    }
+    return MAP_OK;
+}
+
+static int batch_pick_config(map_batch_t *b) {
+    if (b->fixed_cfg >= 0) return b->fixed_cfg;
+    if (b->chosen >= 0) return b->chosen;
+    int best = -1, fewest = 1 << 30;
+    for (int c = 0; c < kNumBatchConfigs; ++c)
+        if ((int)b->samples[c].size() < fewest) {
+            fewest = (int)b->samples[c].size();
+            best = c;
+        }
+    if (fewest < b->trials) return best;
+    // every configuration timed: keep the one with the lowest median step time
+    float best_ms = 1e30f;
+    for (int c = 0; c < kNumBatchConfigs; ++c) {
+        std::vector<float> v = b->samples[c];
+        std::sort(v.begin(), v.end());
+        const float med = v[v.size() / 2];
+        if (med < best_ms) {
+            best_ms = med;
+            b->chosen = c;
+        }
+    }
+    return b->chosen;
+}
+
+extern "C" map_status map_batch_integrate(map_batch_t *b, const scan_desc *scans, void *stream) {
+    if (!b || !scans) return bfail(b, MAP_ERR_ARG, "null batch or scans");
+    cudaStream_t s = (cudaStream_t)stream;
+    map_status st = batch_retire(b);
+    if (st != MAP_OK) return st;
+    BatchArgs &args = b->args;   // copied into the launch (or the graph node) by the calls below
+    std::memset(&args, 0, sizeof(args));
+    const int n = (int)b->maps.size();
+    for (int i = 0; i < n; ++i) {
+        map_t *m = b->maps[i];
+        const scan_desc &d = scans[i];
+        if (d.map != m) return bfail(b, MAP_ERR_ARG, "scans[i].map must be the batch's i-th map");
+        if (d.n > 0 && (!d.points_dev || ((d.labels_dev == nullptr) == (d.probs_dev == nullptr))))
+            return bfail(b, MAP_ERR_ARG, "need points and exactly one of labels / probs");
+        ScanConst sc;
+        st = make_scan_const(m, &d.lidar, d.n, d.T_world_lidar, d.probs_dev != nullptr, sc);
+        if (st != MAP_OK) return bfail(b, st, m->err);
+        sc.probs_vec4 = d.probs_dev && (m->C % 4 == 0) && (((uintptr_t)d.probs_dev & 15) == 0);
+        if (need_compaction(m)) {
+            st = compact_arena(m, s);
+            if (st != MAP_OK) return bfail(b, st, m->err);
+        }
+        BatchItem &it = args.it[i];
+        it.sc = sc;
+        it.md = m->md;
+        it.fd = m->fd;
+        it.pts = d.points_dev;
+        it.labels = d.labels_dev;
+        it.probs = d.probs_dev;
+        it.pal = m->pal_dev;
+    }
+    args.n = n;
+    args.ctl = b->ctl;
+    args.out = b->out_dev;
+    args.tri = mesh_table_tri();
+    args.ntri = mesh_table_ntri();
+    args.fault_skip_cta0 = b->fault_spin ? 1 : 0;
+    args.spin_limit = b->fault_spin;
+    b->fault_spin = 0;
+    const int cfg = batch_pick_config(b);
+    const bool timing = b->fixed_cfg < 0 && b->chosen < 0;
+    if (timing) BCU(cudaEventRecord(b->ev_a, s));
+    if (b->flags & MAP_BATCH_GRAPH) {
+        if (!b->exec[cfg]) {
+            // capture barrier reset + launch + result copy once per configuration, on the
+            // private stream (the caller's stream may be the legacy default stream)
+            BCU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e0 = cudaMemsetAsync(b->ctl, 0, sizeof(BatchCtl), b->cap);
+            cudaError_t e = launch_batch(cfg, b->grid[cfg], args, b->cap);
+            cudaError_t e2 = cudaMemcpyAsync(b->out_host, b->out_dev, BATCH_MAX * sizeof(BatchState),
+                                             cudaMemcpyDeviceToHost, b->cap);
+            BCU(cudaStreamEndCapture(b->cap, &b->graph[cfg]));
+            BCU(e0);
+            BCU(e);
+            BCU(e2);
+            size_t nn = 0;
+            BCU(cudaGraphGetNodes(b->graph[cfg], nullptr, &nn));
+            std::vector<cudaGraphNode_t> nodes(nn);
+            BCU(cudaGraphGetNodes(b->graph[cfg], nodes.data(), &nn));
+            for (auto nd : nodes) {
+                cudaGraphNodeType t;
+                cudaGraphNodeGetType(nd, &t);
+                if (t == cudaGraphNodeTypeKernel) b->knode[cfg] = nd;
+            }
+            BCU(cudaGraphInstantiate(&b->exec[cfg], b->graph[cfg], 0));
+        } else {
+            cudaKernelNodeParams kp;
+            BCU(cudaGraphKernelNodeGetParams(b->knode[cfg], &kp));
+            void *params[] = {(void *)&args};
+            kp.kernelParams = params;
+            kp.extra = nullptr;
+            BCU(cudaGraphExecKernelNodeSetParams(b->exec[cfg], b->knode[cfg], &kp));
+        }
+        BCU(cudaGraphLaunch(b->exec[cfg], s));
+    } else {
+        BCU(cudaMemsetAsync(b->ctl, 0, sizeof(BatchCtl), s));
+        BCU(launch_batch(cfg, b->grid[cfg], args, s));
+        BCU(cudaMemcpyAsync(b->out_host, b->out_dev, n * sizeof(BatchState), cudaMemcpyDeviceToHost, s));
+    }
+    if (timing) {
+        BCU(cudaEventRecord(b->ev_b, s));
+        b->pending_cfg = cfg;
+    }
+    BCU(cudaEventRecord(b->ev_done, s));
+    b->pending = true;
+    for (map_t *m : b->maps) {
+        m->frame++;
+        m->launches += 1;
+    }
+    return MAP_OK;
+}
+
+extern "C" map_status map_batch_sync(map_batch_t *b, void *stream) {
+    if (!b) return bfail(nullptr, MAP_ERR_ARG, "null batch");
+    map_status st = batch_retire(b);
+    if (st != MAP_OK) return st;
+    for (map_t *m : b->maps) {
+        st = device_errors(m);
+        if (st != MAP_OK) return bfail(b, st, m->err);
+    }
+    (void)stream;
+    return MAP_OK;
+}
+
+extern "C" map_status map_batch_config(map_batch_t *b, int32_t *threads_per_block, int32_t *items_per_thread,
+                                       int32_t *tuned) {
+    if (!b) return bfail(nullptr, MAP_ERR_ARG, "null batch");
+    const int c = b->fixed_cfg >= 0 ? b->fixed_cfg : b->chosen;
+    if (threads_per_block) *threads_per_block = c >= 0 ? 32 * kBatchConfigs[c].warps : 0;
+    if (items_per_thread) *items_per_thread = c >= 0 ? kBatchConfigs[c].vpt : 0;
+    if (tuned) *tuned = b->fixed_cfg < 0 && b->chosen >= 0;
+    return MAP_OK;
+}
+
+extern "C" map_status map_batch_set_config(map_batch_t *b, int32_t cfg) {
+    if (!b || cfg < -1 || cfg >= kNumBatchConfigs) return bfail(b, MAP_ERR_ARG, "bad configuration index");
+    b->fixed_cfg = cfg;
+    return MAP_OK;
+}
+
+extern "C" map_status map_batch_test_timeout(map_batch_t *b, uint64_t spin_limit) {
+    if (!b || spin_limit == 0) return bfail(b, MAP_ERR_ARG, "need a batch and a positive spin limit");
+    b->fault_spin = spin_limit;
+    return MAP_OK;
+}
+
+extern "C" const char *map_batch_last_error(map_batch_t *b) { return b ? b->err.c_str() : g_err.c_str(); }
 
 // Internal accessors for translation units that add entry points around a map.
 namespace stsdf {
