@@ -132,9 +132,8 @@ struct MapDev {
 // Per-frame scratch of one map.
 struct FrameDev {
     unsigned long long *win;   // [H*W] (float bits of range << 32) | point index
-    float4 *pix;               // [H*W] {r, r^2 hi, r^2 lo, winner index bits (-1: none)}
+    float4 *pix;               // [H*W] {r, r^2 hi, r^2 lo, flag bits: -1 no return, 0 no class likelihood, 1 likelihood}
     float *logL;               // [H*W][C] per-pixel class log-likelihood
-    uint8_t *sem_ok;           // [H*W] 1 when the pixel carries a class likelihood
     int *touched;              // [max_blocks] hash slots of U_k
     int *dirty;                // [max_blocks] pool slots to re-mesh
     int2 *sem_list;            // [sem_cap] {pool voxel index, pixel} awaiting the class update

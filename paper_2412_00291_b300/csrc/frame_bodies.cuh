@@ -145,8 +145,14 @@ __device__ __forceinline__ void points_item(const float *__restrict__ pts, const
         atomicAdd(&fd.ctr[CT_PIXEL], (unsigned long long)__popc(mp));
     }
     int n_new = 0;
-    for (int j = 0; j < nb; ++j) {
-        const uint64_t key = pack_block(blocks[j][0], blocks[j][1], blocks[j][2]);
+    // step j of every lane's band together: lanes holding the same block (neighbouring
+    // points of a beam) leave it to the lowest of them, which spares repeated probes
+    // and same-address atomics
+    const int nb_max = __reduce_max_sync(0xffffffffu, (unsigned)nb);
+    for (int j = 0; j < nb_max; ++j) {
+        const uint64_t key = j < nb ? pack_block(blocks[j][0], blocks[j][1], blocks[j][2]) : EMPTY_KEY;
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        if (j >= nb || __ffs(grp) - 1 != (int)(threadIdx.x & 31)) continue;
         int is_new = 0;
         const int h = hash_insert(md, key, is_new);
         if (h < 0) continue;
@@ -168,8 +174,9 @@ __device__ __forceinline__ void points_item(const float *__restrict__ pts, const
     if ((threadIdx.x & 31) == 0 && n_new) atomicAdd(&fd.ctr[CT_NEW], (unsigned long long)n_new);
 }
 
-// Per pixel: the winner's range r, r^2 as an exact float pair, its index, and
-// its class log-likelihood row log P(O = l | I_k) of Eq. (bayesian_filter)
+// Per pixel: the winner's range r, r^2 as an exact float pair, a flag (-1 no
+// return, 0 a return without class likelihood, 1 with one), and its class
+// log-likelihood row log P(O = l | I_k) of Eq. (bayesian_filter)
 // (or no likelihood when the winner carries no valid label).
 __device__ __forceinline__ void pixel_item(const float *__restrict__ pts, const int32_t *__restrict__ labels,
                                            const float *__restrict__ probs, const ScanConst &sc, const FrameDev &fd,
@@ -178,7 +185,6 @@ __device__ __forceinline__ void pixel_item(const float *__restrict__ pts, const 
     const unsigned long long key = fd.win[p];
     if (key == ~0ull) {
         fd.pix[p] = make_float4(-1.f, 0.f, 0.f, __int_as_float(-1));
-        fd.sem_ok[p] = 0;
         return;
     }
     const int idx = (int)(key & 0xffffffffu);
@@ -190,8 +196,8 @@ __device__ __forceinline__ void pixel_item(const float *__restrict__ pts, const 
     two_prod(z, z, c, ce);
     df_add(a, ae, b, be, sh, sl);
     df_add(sh, sl, c, ce, sh, sl);
-    fd.pix[p] = make_float4(r, sh, sl, __int_as_float(idx));
     const int C = sc.C;
+    int has_lik = 1;
     float *out = fd.logL + (long long)p * C;
     if (sc.has_probs) {
         const float *q = probs + (long long)idx * C;
@@ -205,14 +211,13 @@ __device__ __forceinline__ void pixel_item(const float *__restrict__ pts, const 
         } else {
             for (int cc = 0; cc < C; ++cc) out[cc] = logf(fmaxf(q[cc], sc.lik_floor));
         }
-        fd.sem_ok[p] = 1;
     } else {
         const int l = labels[idx];
-        const int ok = (l >= 0 && l < C);
-        if (ok)
+        has_lik = (l >= 0 && l < C);
+        if (has_lik)
             for (int cc = 0; cc < C; ++cc) out[cc] = (cc == l) ? sc.log_phit : sc.log_pmiss;
-        fd.sem_ok[p] = (uint8_t)ok;
     }
+    fd.pix[p] = make_float4(r, sh, sl, __int_as_float(has_lik));
 }
 
 template <bool F16>
@@ -261,84 +266,88 @@ __device__ __forceinline__ unsigned remesh_offsets(int vi) {
     return (unsigned)(REMESH_TABLE >> (8 * z)) & 0xffu;
 }
 
-// One voxel of the block: pixel, projective psi, running-average update,
-// and the class-update list entry.
-template <bool F16>
-__device__ __forceinline__ void tsdf_voxel(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int slot,
-                                           int bx, int by, int bz, int vi, long long &n_upd, unsigned &remesh,
-                                           int2 *wbuf, int &wcount) {
-    const int lane = threadIdx.x & 31;
-    const float tau = sc.tau;
+// Pixel of voxel vi of block (bx, by, bz) (Sec. III-C.1), or -1 outside the
+// image; also returns the voxel's offset from the sensor in voxel units
+// (exact integer part minus the fraction's high part, m) and |x_l|^2 (rr2)
+// and its reciprocal square root (irr) in those units.
+__device__ __forceinline__ int tsdf_pixel(const ScanConst &sc, int bx, int by, int bz, int vi, float &m0, float &m1,
+                                          float &m2, float &rr2, float &irr) {
     const int lx = vi & 7, ly = (vi >> 3) & 7, lz = vi >> 6;
-    // offset from the sensor in voxel units: exact integer part minus the fraction's high part
-    const float m0 = (float)(8 * bx + lx - sc.k[0]), m1 = (float)(8 * by + ly - sc.k[1]),
-                m2 = (float)(8 * bz + lz - sc.k[2]);
+    m0 = (float)(8 * bx + lx - sc.k[0]);
+    m1 = (float)(8 * by + ly - sc.k[1]);
+    m2 = (float)(8 * bz + lz - sc.k[2]);
     const float s0 = m0 - sc.fhi[0], s1 = m1 - sc.fhi[1], s2 = m2 - sc.fhi[2];
-    // direction in the LiDAR frame (scale-free) -> pixel (Sec. III-C.1)
+    // direction in the LiDAR frame (scale-free) -> pixel
     const float x0 = sc.Rt[0] * s0 + sc.Rt[1] * s1 + sc.Rt[2] * s2;
     const float x1 = sc.Rt[3] * s0 + sc.Rt[4] * s1 + sc.Rt[5] * s2;
     const float x2 = sc.Rt[6] * s0 + sc.Rt[7] * s1 + sc.Rt[8] * s2;
-    const float rr2 = x0 * x0 + x1 * x1 + x2 * x2;
-    bool upd = false, sem = false;
-    int p = 0;
-    if (rr2 > 0.f) {
-        const float irr = rsqrtf(rr2);
-        const float uc = (PI_F - atan2f(x1, x0)) * sc.inv_dphi;
-        const float vc = (acosf(fminf(fmaxf(x2 * irr, -1.f), 1.f)) - sc.theta0) * sc.inv_dtheta;
-        int u = (int)floorf(uc + 0.5f);
-        const int v = (int)floorf(vc + 0.5f);
-        if (u >= sc.W) u -= sc.W;
-        if (u < 0) u += sc.W;
-        if (v >= 0 && v < sc.H) {
-            p = v * sc.W + u;
-            const float4 px = fd.pix[p];
-            if (__float_as_int(px.w) >= 0) {
-                // plain FP32 psi is within ~1e-5 m of the exact value; away from +-tau it
-                // decides the update exactly: beyond +tau (+1 mm) sdf = tau and w = 1, below
-                // -tau (-1 mm) nothing; only the band in between needs the float-pair psi
-                float psi = px.x - sc.nu * (rr2 * irr);
-                float sdf = tau, w = 1.f;
-                upd = psi >= -tau - 1e-3f;
-                if (upd && psi <= tau + 1e-3f) {
-                    float e0, e1, e2, t0, t1, t2;
-                    two_sum(m0, -sc.fhi[0], t0, e0);
-                    two_sum(m1, -sc.fhi[1], t1, e1);
-                    two_sum(m2, -sc.fhi[2], t2, e2);
-                    e0 = __fsub_rn(e0, sc.flo[0]);
-                    e1 = __fsub_rn(e1, sc.flo[1]);
-                    e2 = __fsub_rn(e2, sc.flo[2]);
-                    // rho^2 in voxel units, then metres^2, as float pairs; psi = (r^2 - rho^2) / (r + rho)
-                    float a, ae, b, be, c, ce, qh, ql, mh, ml, dh, dl;
-                    two_prod(t0, t0, a, ae);
-                    two_prod(t1, t1, b, be);
-                    two_prod(t2, t2, c, ce);
-                    ae = __fmaf_rn(2.f * t0, e0, ae);
-                    be = __fmaf_rn(2.f * t1, e1, be);
-                    ce = __fmaf_rn(2.f * t2, e2, ce);
-                    df_add(a, ae, b, be, qh, ql);
-                    df_add(qh, ql, c, ce, qh, ql);
-                    df_mul(qh, ql, sc.nu2hi, sc.nu2lo, mh, ml);
-                    df_add(px.y, px.z, -mh, -ml, dh, dl);
-                    psi = __fdividef(dh + dl, px.x + mh * rsqrtf(mh));
-                    sdf = fminf(psi, tau);
-                    if (sc.weight_mode == 0) w = fminf(fmaxf((psi + tau) * sc.inv_2tau, 0.f), 1.f);
-                    upd = psi >= -tau && w > 0.f;
-                    sem = upd && fabsf(psi) <= tau && fd.sem_ok[p];
-                }
-                if (upd) {
-                    const long long vox = (long long)slot * BV + vi;
-                    const float2 dw = load_dw<F16>(md, vox);
-                    const float Wn = dw.y + w;
-                    store_dw<F16>(md, vox, __fdividef(dw.y * dw.x + w * sdf, Wn), Wn);
-                    ++n_upd;
-                    remesh |= remesh_offsets(vi);
-                }
-            }
-        }
+    rr2 = x0 * x0 + x1 * x1 + x2 * x2;
+    irr = 0.f;
+    if (!(rr2 > 0.f)) return -1;
+    irr = rsqrtf(rr2);
+    const float uc = (PI_F - atan2f(x1, x0)) * sc.inv_dphi;
+    const float vc = (acosf(fminf(fmaxf(x2 * irr, -1.f), 1.f)) - sc.theta0) * sc.inv_dtheta;
+    int u = (int)floorf(uc + 0.5f);
+    const int v = (int)floorf(vc + 0.5f);
+    if (u >= sc.W) u -= sc.W;
+    if (u < 0) u += sc.W;
+    return (v >= 0 && v < sc.H) ? v * sc.W + u : -1;
+}
+
+// Projective psi and the running-average update of one voxel given its pixel
+// record px (Sec. III-C.2) and its stored {D, W} (read ahead by the caller).
+// Returns true when the voxel also takes the class update.
+template <bool F16>
+__device__ __forceinline__ bool tsdf_update(const ScanConst &sc, const MapDev &md, long long vox, int vi, int p,
+                                            float4 px, float2 dw, float m0, float m1, float m2, float rr2, float irr,
+                                            long long &n_upd, unsigned &remesh) {
+    if (p < 0 || __float_as_int(px.w) < 0) return false;
+    const float tau = sc.tau;
+    // plain FP32 psi is within ~1e-5 m of the exact value; away from +-tau it
+    // decides the update exactly: beyond +tau (+1 mm) sdf = tau and w = 1, below
+    // -tau (-1 mm) nothing; only the band in between needs the float-pair psi
+    float psi = px.x - sc.nu * (rr2 * irr);
+    float sdf = tau, w = 1.f;
+    bool upd = psi >= -tau - 1e-3f, sem = false;
+    if (upd && psi <= tau + 1e-3f) {
+        float e0, e1, e2, t0, t1, t2;
+        two_sum(m0, -sc.fhi[0], t0, e0);
+        two_sum(m1, -sc.fhi[1], t1, e1);
+        two_sum(m2, -sc.fhi[2], t2, e2);
+        e0 = __fsub_rn(e0, sc.flo[0]);
+        e1 = __fsub_rn(e1, sc.flo[1]);
+        e2 = __fsub_rn(e2, sc.flo[2]);
+        // rho^2 in voxel units, then metres^2, as float pairs; psi = (r^2 - rho^2) / (r + rho)
+        float a, ae, b, be, c, ce, qh, ql, mh, ml, dh, dl;
+        two_prod(t0, t0, a, ae);
+        two_prod(t1, t1, b, be);
+        two_prod(t2, t2, c, ce);
+        ae = __fmaf_rn(2.f * t0, e0, ae);
+        be = __fmaf_rn(2.f * t1, e1, be);
+        ce = __fmaf_rn(2.f * t2, e2, ce);
+        df_add(a, ae, b, be, qh, ql);
+        df_add(qh, ql, c, ce, qh, ql);
+        df_mul(qh, ql, sc.nu2hi, sc.nu2lo, mh, ml);
+        df_add(px.y, px.z, -mh, -ml, dh, dl);
+        psi = __fdividef(dh + dl, px.x + mh * rsqrtf(mh));
+        sdf = fminf(psi, tau);
+        if (sc.weight_mode == 0) w = fminf(fmaxf((psi + tau) * sc.inv_2tau, 0.f), 1.f);
+        upd = psi >= -tau && w > 0.f;
+        sem = upd && fabsf(psi) <= tau && __float_as_int(px.w) == 1;
     }
-    // class-update entries collect in the warp's shared buffer (one global append per block)
+    if (upd) {
+        const float Wn = dw.y + w;
+        store_dw<F16>(md, vox, __fdividef(dw.y * dw.x + w * sdf, Wn), Wn);
+        ++n_upd;
+        remesh |= remesh_offsets(vi);
+    }
+    return sem;
+}
+
+// Class-update entries collect in the warp's shared buffer (one global append per block).
+__device__ __forceinline__ void tsdf_list(bool sem, int vox, int p, int2 *wbuf, int &wcount) {
     const unsigned mk = __ballot_sync(0xffffffffu, sem);
-    if (sem) wbuf[wcount + __popc(mk & ((1u << lane) - 1u))] = make_int2(slot * BV + vi, p);
+    if (sem) wbuf[wcount + __popc(mk & ((1u << (threadIdx.x & 31)) - 1u))] = make_int2(vox, p);
     wcount += __popc(mk);
 }
 
@@ -356,9 +365,22 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
     if (lane >= 8 && lane < 15 && md.slot_frame[slot] == sc.frame) link_block(md, key, slot, lane - 7);
     unsigned remesh = 0;
     int wcount = 0;
+    // voxels vi and vi + 32 per step: both {D, W} reads are issued before the
+    // projections and both pixel reads before either update, so that their
+    // latencies overlap
 #pragma unroll 1
-    for (int vi = lane; vi < BV; vi += 32)
-        tsdf_voxel<F16>(sc, md, fd, slot, bx, by, bz, vi, n_upd, remesh, wbuf, wcount);
+    for (int vi = lane; vi < BV; vi += 64) {
+        const long long va = (long long)slot * BV + vi, vb = va + 32;
+        const float2 dwa = load_dw<F16>(md, va), dwb = load_dw<F16>(md, vb);
+        float ma0, ma1, ma2, ra, ia, mb0, mb1, mb2, rb, ib;
+        const int pa = tsdf_pixel(sc, bx, by, bz, vi, ma0, ma1, ma2, ra, ia);
+        const int pb = tsdf_pixel(sc, bx, by, bz, vi + 32, mb0, mb1, mb2, rb, ib);
+        const float4 pxa = fd.pix[pa < 0 ? 0 : pa], pxb = fd.pix[pb < 0 ? 0 : pb];
+        const bool sa = tsdf_update<F16>(sc, md, va, vi, pa, pxa, dwa, ma0, ma1, ma2, ra, ia, n_upd, remesh);
+        const bool sb = tsdf_update<F16>(sc, md, vb, vi + 32, pb, pxb, dwb, mb0, mb1, mb2, rb, ib, n_upd, remesh);
+        tsdf_list(sa, slot * BV + vi, pa, wbuf, wcount);
+        tsdf_list(sb, slot * BV + vi + 32, pb, wbuf, wcount);
+    }
     __syncwarp();
     // one append of the block's class-update entries
     if (wcount) {
@@ -529,30 +551,24 @@ __device__ __forceinline__ void semantic_item(const ScanConst &sc, const MapDev 
     }
 }
 
-constexpr int EDGE_WORDS = (MC_EDGES + 31) / 32;   // 61 words of lattice-edge bits per block
-constexpr int MESH_WARPS = 8;                       // warps (blocks in flight) per CTA
+constexpr int MESH_WARPS = 8;   // warps (blocks in flight) per CTA
 
-// Local index of the lattice edge that cube edge ce of the cube anchored at
-// (ax, ay, az) lies on: axis * 648 + a + 8 (b + 9 c), with a the coordinate
-// along the axis and b, c the coordinates along the next two axes cyclically.
-__device__ __forceinline__ int cube_edge_index(int ce, int ax, int ay, int az) {
-    const int axis = ce >> 2;
-    const int pa = axis == 0 ? ax : (axis == 1 ? ay : az);
-    const int pb = (axis == 0 ? ay : (axis == 1 ? az : ax)) + (ce & 1);
-    const int pc = (axis == 0 ? az : (axis == 1 ? ax : ay)) + ((ce >> 1) & 1);
-    return axis * 648 + pa + 8 * (pb + 9 * pc);
-}
-
-// Per-warp staging of one block: the 9^3 region (block + upper faces).
+// Per-warp staging of one block: the 9^3 region (block + upper faces) and
+// the bit masks the extraction works on.  Voxel rows run along x and are
+// indexed rw = y + 9 z; cube rows are indexed cy + 8 cz.
 struct MeshWarpSmem {
     float D[729];
-    uint32_t rowm[81];        // per (y, z) row of 9 voxels: bits 0..8 observed, bits 16..24 D < 0
-    unsigned edge[64];        // lattice-edge bitmap (61 words used)
-    int woff[64];             // vertex number of each word's first set bit
-    int nb[8];                // slots of this block (0) and its 7 upper neighbours, -1 if none
-    uint8_t F[729];           // bit 0 observed (W > 0), bit 1 D < 0
+    uint32_t rowm[81];    // per voxel row: bits 0..8 observed (x = 0..8), bits 16..24 D < 0
+    uint32_t ew[81];      // per voxel row: lattice edges that carry a vertex, from voxel (x, y, z):
+                          // bits 0..7 +x edges (x = 0..7), 8..16 +y edges, 17..25 +z edges (x = 0..8)
+    uint16_t woff[82];    // number of the first vertex of each row
+    uint8_t okc[64];      // per cube row: cubes whose eight corners are observed (bit = ax)
+    int nb[8];            // slots of this block (0) and its 7 upper neighbours, -1 if none
+    union {
+        uint8_t F[729];   // while staging: bit 0 observed (W > 0), bit 1 D < 0
+        uint16_t mc[512]; // then: the cubes that emit triangles (ax + 8 (ay + 8 az)), in order
+    } u;
     uint8_t lab[729];
-    uint8_t cs[512];          // cube case
 };
 
 struct MeshCtaSmem {
@@ -578,8 +594,54 @@ __device__ __forceinline__ int face_pos(int j, int &nbi) {
     return x + 9 * (y + 9 * z);
 }
 
+// Bit position of the k-th (from 0) set bit of w; requires k < popc(w).
+__device__ __forceinline__ int nth_set_bit(uint32_t w, int k) {
+    int pos = 0, c = __popc(w & 0xffffu);
+    if (k >= c) { k -= c; w >>= 16; pos += 16; }
+    c = __popc(w & 0xffu);
+    if (k >= c) { k -= c; w >>= 8; pos += 8; }
+    c = __popc(w & 0xfu);
+    if (k >= c) { k -= c; w >>= 4; pos += 4; }
+    c = __popc(w & 0x3u);
+    if (k >= c) { k -= c; w >>= 2; pos += 2; }
+    return pos + (k >= (int)(w & 1u) ? 1 : 0);
+}
+
+// Case of cube a = ax + 8 (ay + 8 az): bit cx + 2 cy + 4 cz set when corner
+// (ax + cx, ay + cy, az + cz) has D < 0.
+__device__ __forceinline__ int cube_case(const uint32_t *rowm, int a) {
+    const int ax = a & 7, r = ((a >> 3) & 7) + 9 * (a >> 6), sh = 16 + ax;
+    return (int)(((rowm[r] >> sh) & 3u) | (((rowm[r + 1] >> sh) & 3u) << 2) | (((rowm[r + 9] >> sh) & 3u) << 4) |
+                 (((rowm[r + 10] >> sh) & 3u) << 6));
+}
+
+// Vertex number of cube edge ce (axis ce >> 2, offsets ce & 1 and (ce >> 1) & 1
+// along the next two axes, cyclically) of the cube anchored at (ax, ay, az).
+__device__ __forceinline__ int cube_edge_vertex(const MeshWarpSmem &W, int ce, int ax, int ay, int az) {
+    const int axis = ce >> 2, o1 = ce & 1, o2 = (ce >> 1) & 1;
+    int rw, bit;
+    if (axis == 0) {
+        rw = ay + o1 + 9 * (az + o2);
+        bit = ax;
+    } else if (axis == 1) {
+        rw = ay + 9 * (az + o1);
+        bit = 8 + ax + o2;
+    } else {
+        rw = ay + o2 + 9 * az;
+        bit = 17 + ax + o1;
+    }
+    return W.woff[rw] + __popc(W.ew[rw] & ((1u << bit) - 1u));
+}
+
 // One block to re-mesh (pool slot `slot`), processed by one warp with its
 // staging area W; `part` selects the mesh-arena partition.
+//
+// A cube emits triangles when its eight corners are observed and not all on
+// one side of the surface; a lattice edge carries a vertex when its two
+// voxels are observed with opposite signs and one of its (up to four) cubes
+// has all corners observed.  Both are evaluated for whole rows at once with
+// bit operations on the row masks; vertices and emitting cubes are then
+// numbered by prefix counts and emitted one per lane.
 __device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev &fd, const int8_t *__restrict__ tri,
                                                 const uint8_t *__restrict__ ntri, const uchar4 *__restrict__ pal,
                                                 MeshWarpSmem &W, int slot, int part, long long &n_v, long long &n_t) {
@@ -597,7 +659,7 @@ __device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev
         const float2 dw = f32 ? md.dw32[vox] : __half22float2(md.dw16[vox]);
         const int f = (dw.y > 0.f ? 1 : 0) | (dw.x < 0.f ? 2 : 0);
         W.D[r] = dw.x;
-        W.F[r] = (uint8_t)f;
+        W.u.F[r] = (uint8_t)f;
         W.lab[r] = md.label[vox];
         if (f & 1) seen |= (f & 2) ? 1 : 2;
     }
@@ -619,65 +681,47 @@ __device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev
             lab = md.label[vox];
         }
         W.D[r] = D;
-        W.F[r] = (uint8_t)f;
+        W.u.F[r] = (uint8_t)f;
         W.lab[r] = lab;
         if (f & 1) seen |= (f & 2) ? 1 : 2;
     }
     const bool any_neg = __any_sync(0xffffffffu, seen & 1), any_pos = __any_sync(0xffffffffu, seen & 2);
-    if (!(any_neg && any_pos)) {
-        // no sign change among observed voxels: no cube can cross; drop the old segment
-        if (lane == 0) {
-            const int4 old = md.seg[slot];
-            if (old.y | old.w) md.seg[slot] = make_int4(0, 0, 0, 0);
-        }
+    int tot_m = 0;
+    if (any_neg && any_pos) {
         __syncwarp();
-        return;
-    }
-    __syncwarp();
-    // packed row masks of the 81 (y, z) rows
-    for (int rw = lane; rw < 81; rw += 32) {
-        uint32_t m = 0;
+        // row masks of the 81 voxel rows
+        for (int rw = lane; rw < 81; rw += 32) {
+            uint32_t m = 0;
 #pragma unroll
-        for (int x = 0; x < 9; ++x) {
-            const uint32_t f = W.F[x + 9 * rw];
-            m |= ((f & 1u) << x) | (((f >> 1) & 1u) << (16 + x));
-        }
-        W.rowm[rw] = m;
-    }
-    for (int k = lane; k < 64; k += 32) W.edge[k] = 0u;
-    __syncwarp();
-    // cube rows (ay, az) = lane and lane + 32: eight cubes along x from four row masks
-    int cnt_t = 0;
-#pragma unroll 1
-    for (int q = 0; q < 2; ++q) {
-        const int cr = lane + 32 * q, ay = cr & 7, az = cr >> 3;
-        const uint32_t m00 = W.rowm[ay + 9 * az], m10 = W.rowm[ay + 1 + 9 * az];
-        const uint32_t m01 = W.rowm[ay + 9 * (az + 1)], m11 = W.rowm[ay + 1 + 9 * (az + 1)];
-        const uint32_t okm = m00 & m10 & m01 & m11;
-#pragma unroll 1
-        for (int ax = 0; ax < 8; ++ax) {
-            const bool ok = ((okm >> ax) & 3u) == 3u;
-            const int cs = (int)(((m00 >> (16 + ax)) & 3u) | (((m10 >> (16 + ax)) & 3u) << 2) |
-                                 (((m01 >> (16 + ax)) & 3u) << 4) | (((m11 >> (16 + ax)) & 3u) << 6));
-            const int nt = ok ? ntri[cs] : 0;
-            W.cs[ax + 8 * cr] = (uint8_t)(nt ? cs : 0);
-            cnt_t += nt;
-            if (nt) {
-#pragma unroll
-                for (int ce = 0; ce < 12; ++ce) {
-                    const int axis = ce >> 2, a1 = axis == 2 ? 0 : axis + 1, a2 = axis == 0 ? 2 : axis - 1;
-                    const int clo = ((ce & 1) << a1) | (((ce >> 1) & 1) << a2);
-                    if (((cs >> clo) ^ (cs >> (clo | (1 << axis)))) & 1) {
-                        const int e = cube_edge_index(ce, ax, ay, az);
-                        atomicOr(&W.edge[e >> 5], 1u << (e & 31));
-                    }
-                }
+            for (int x = 0; x < 9; ++x) {
+                const uint32_t f = W.u.F[x + 9 * rw];
+                m |= ((f & 1u) << x) | (((f >> 1) & 1u) << (16 + x));
             }
+            W.rowm[rw] = m;
+        }
+        __syncwarp();
+        // cube rows 2 lane and 2 lane + 1: observed cubes, and the emitting ones among them
+        uint32_t mixl = 0;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int cr = 2 * lane + q, r = (cr & 7) + 9 * (cr >> 3);
+            const uint32_t m00 = W.rowm[r], m10 = W.rowm[r + 1], m01 = W.rowm[r + 9], m11 = W.rowm[r + 10];
+            const uint32_t o = m00 & m10 & m01 & m11;
+            const uint32_t ok = o & (o >> 1) & 0xffu;
+            const uint32_t na = o >> 16, nn = (m00 | m10 | m01 | m11) >> 16;
+            W.okc[cr] = (uint8_t)ok;
+            mixl |= (ok & (nn | (nn >> 1)) & ~(na & (na >> 1)) & 0xffu) << (8 * q);
+        }
+        const int moff = warp_exclusive_scan(__popc(mixl), tot_m);
+        // the staging flags are dead: list the emitting cubes in their place (cube 16 lane + b)
+        for (int o = moff; mixl; ++o) {
+            const int b = __ffs(mixl) - 1;
+            mixl &= mixl - 1u;
+            W.u.mc[o] = (uint16_t)(16 * lane + b);
         }
     }
-    int tot_t;
-    const int toff = warp_exclusive_scan(cnt_t, tot_t);
-    if (tot_t == 0) {
+    if (tot_m == 0) {
+        // no cube can emit: drop the old segment
         if (lane == 0) {
             const int4 old = md.seg[slot];
             if (old.y | old.w) md.seg[slot] = make_int4(0, 0, 0, 0);
@@ -686,14 +730,46 @@ __device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev
         return;
     }
     __syncwarp();
-    // vertex numbering: popcount prefix over the bitmap (words lane, lane + 32)
-    const int c0 = __popc(W.edge[lane]), c1 = lane + 32 < EDGE_WORDS ? __popc(W.edge[lane + 32]) : 0;
-    int tot_lo, tot_v;
-    const int off_lo = warp_exclusive_scan(c0, tot_lo);
-    const int off_hi = warp_exclusive_scan(c1, tot_v);
-    W.woff[lane] = off_lo;
-    W.woff[lane + 32] = tot_lo + off_hi;
-    tot_v += tot_lo;
+    // lattice edges with a vertex, row by row
+    for (int rw = lane; rw < 81; rw += 32) {
+        const int y = rw % 9, z = rw / 9;
+        const uint32_t m = W.rowm[rw];
+        const uint32_t obs = m & 0x1ffu, neg = (m >> 16) & 0x1ffu;
+        // observed cubes of the cube rows (y - 1 | y, z - 1 | z) around this voxel row
+        const uint32_t c00 = (y > 0 && z > 0) ? W.okc[(y - 1) + 8 * (z - 1)] : 0u;
+        const uint32_t c10 = (y < 8 && z > 0) ? W.okc[y + 8 * (z - 1)] : 0u;
+        const uint32_t c01 = (y > 0 && z < 8) ? W.okc[(y - 1) + 8 * z] : 0u;
+        const uint32_t c11 = (y < 8 && z < 8) ? W.okc[y + 8 * z] : 0u;
+        uint32_t e = (neg ^ (neg >> 1)) & obs & (obs >> 1) & (c00 | c10 | c01 | c11) & 0xffu;
+        if (y < 8) {
+            const uint32_t m2 = W.rowm[rw + 1], c = c10 | c11;
+            e |= ((neg ^ (m2 >> 16)) & obs & m2 & (c | (c << 1)) & 0x1ffu) << 8;
+        }
+        if (z < 8) {
+            const uint32_t m3 = W.rowm[rw + 9], c = c01 | c11;
+            e |= ((neg ^ (m3 >> 16)) & obs & m3 & (c | (c << 1)) & 0x1ffu) << 17;
+        }
+        W.ew[rw] = e;
+    }
+    __syncwarp();
+    // vertex numbering: rows 3 lane .. 3 lane + 2
+    int c0 = 0, c1 = 0, c2 = 0;
+    if (lane < 27) {
+        c0 = __popc(W.ew[3 * lane]);
+        c1 = __popc(W.ew[3 * lane + 1]);
+        c2 = __popc(W.ew[3 * lane + 2]);
+    }
+    int tot_v;
+    const int voff = warp_exclusive_scan(c0 + c1 + c2, tot_v);
+    if (lane < 27) {
+        W.woff[3 * lane] = (uint16_t)voff;
+        W.woff[3 * lane + 1] = (uint16_t)(voff + c0);
+        W.woff[3 * lane + 2] = (uint16_t)(voff + c0 + c1);
+    }
+    // triangle count of the emitting cubes
+    int cnt_t = 0;
+    for (int i = lane; i < tot_m; i += 32) cnt_t += ntri[cube_case(W.rowm, W.u.mc[i])];
+    const int tot_t = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt_t);
     // reserve arena space in this warp's partition (two lanes, two cursors)
     unsigned long long res = 0, lim = 0;
     if (lane == 0) {
@@ -720,60 +796,54 @@ __device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev
     }
     __syncwarp();
     if (fits) {
-        // vertices: bytes b = lane + 32 k of the bitmap, edges 8 b .. 8 b + 7
-        for (int b = lane; b < 4 * EDGE_WORDS; b += 32) {
-            const unsigned word = W.edge[b >> 2];
-            unsigned bits = (word >> ((b & 3) * 8)) & 0xffu;
-            while (bits) {
-                const int q = __ffs(bits) - 1;
-                bits &= bits - 1;
-                const int e = 8 * b + q;
-                const int vid = W.woff[b >> 2] + __popc(word & ((1u << (e & 31)) - 1u));
-                const int axis = e / 648, rem = e - 648 * axis;
-                const int ca = rem & 7, cb = (rem >> 3) % 9, cc = (rem >> 3) / 9;
-                const int x = axis == 0 ? ca : (axis == 1 ? cc : cb);
-                const int y = axis == 0 ? cb : (axis == 1 ? ca : cc);
-                const int z = axis == 0 ? cc : (axis == 1 ? cb : ca);
-                const int r0 = x + 9 * (y + 9 * z);
-                const int r1 = r0 + (axis == 0 ? 1 : (axis == 1 ? 9 : 81));
-                const float D0 = W.D[r0], D1 = W.D[r1];
-                const float t = D0 / (D0 - D1);
-                const int gx = 8 * bx + x, gy = 8 * by + y, gz = 8 * bz + z;
-                float px = md.nu * (float)gx, py = md.nu * (float)gy, pz = md.nu * (float)gz;
-                if (axis == 0) px = md.nu * ((float)gx + t);
-                else if (axis == 1) py = md.nu * ((float)gy + t);
-                else pz = md.nu * ((float)gz + t);
-                // label of the endpoint nearer the surface (lower endpoint on ties)
-                const int lab = fabsf(D1) < fabsf(D0) ? W.lab[r1] : W.lab[r0];
-                const uchar4 col = pal[lab];
-                const unsigned packed = (unsigned)col.x | ((unsigned)col.y << 8) | ((unsigned)col.z << 16) |
-                                        ((unsigned)lab << 24);
-                md.av[vo + vid] = make_float4(px, py, pz, __uint_as_float(packed));
-                md.ak[vo + vid] = edge_key(gx, gy, gz, axis);
-            }
-        }
-        // triangles of this lane's cubes, in counting order
-        long long tb = to + toff;
-#pragma unroll 1
-        for (int q = 0; q < 2; ++q) {
-            const int cr = lane + 32 * q, ay = cr & 7, az = cr >> 3;
-#pragma unroll 1
-            for (int ax = 0; ax < 8; ++ax) {
-                const int a = ax + 8 * cr;
-                const int cs = W.cs[a];
-                const int nt = cs ? ntri[cs] : 0;
-                for (int j = 0; j < nt; ++j) {
-                    int vid[3];
+        // vertices, one per lane
+        for (int vid = lane; vid < tot_v; vid += 32) {
+            int rw = 0;
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const int e = cube_edge_index(tri[(cs * MC_MAXTRI + j) * 3 + k], ax, ay, az);
-                        vid[k] = W.woff[e >> 5] + __popc(W.edge[e >> 5] & ((1u << (e & 31)) - 1u));
-                    }
-                    md.at[tb + j] = make_ushort4((unsigned short)vid[0], (unsigned short)vid[1],
-                                                 (unsigned short)vid[2], (unsigned short)a);
-                }
-                tb += nt;
+            for (int st = 64; st > 0; st >>= 1)
+                if (rw + st <= 80 && W.woff[rw + st] <= vid) rw += st;
+            const int q = nth_set_bit(W.ew[rw], vid - W.woff[rw]);
+            const int axis = q < 8 ? 0 : (q < 17 ? 1 : 2);
+            const int x = q - (axis == 0 ? 0 : (axis == 1 ? 8 : 17)), y = rw % 9, z = rw / 9;
+            const int r0 = x + 9 * rw;
+            const int r1 = r0 + (axis == 0 ? 1 : (axis == 1 ? 9 : 81));
+            const float D0 = W.D[r0], D1 = W.D[r1];
+            const float t = D0 / (D0 - D1);
+            const int gx = 8 * bx + x, gy = 8 * by + y, gz = 8 * bz + z;
+            float px = md.nu * (float)gx, py = md.nu * (float)gy, pz = md.nu * (float)gz;
+            if (axis == 0) px = md.nu * ((float)gx + t);
+            else if (axis == 1) py = md.nu * ((float)gy + t);
+            else pz = md.nu * ((float)gz + t);
+            // label of the endpoint nearer the surface (lower endpoint on ties)
+            const int lab = fabsf(D1) < fabsf(D0) ? W.lab[r1] : W.lab[r0];
+            const uchar4 col = pal[lab];
+            const unsigned packed = (unsigned)col.x | ((unsigned)col.y << 8) | ((unsigned)col.z << 16) |
+                                    ((unsigned)lab << 24);
+            md.av[vo + vid] = make_float4(px, py, pz, __uint_as_float(packed));
+            md.ak[vo + vid] = edge_key(gx, gy, gz, axis);
+        }
+        // triangles: one emitting cube per lane, in list order
+        long long tb = to;
+        for (int i0 = 0; i0 < tot_m; i0 += 32) {
+            const int i = i0 + lane;
+            int a = 0, cs = 0, nt = 0;
+            if (i < tot_m) {
+                a = W.u.mc[i];
+                cs = cube_case(W.rowm, a);
+                nt = ntri[cs];
             }
+            int round_t;
+            const int off = warp_exclusive_scan(nt, round_t);
+            const int ax = a & 7, ay = (a >> 3) & 7, az = a >> 6;
+            for (int j = 0; j < nt; ++j) {
+                const int8_t *tj = tri + (cs * MC_MAXTRI + j) * 3;
+                const int v0 = cube_edge_vertex(W, tj[0], ax, ay, az);
+                const int v1 = cube_edge_vertex(W, tj[1], ax, ay, az);
+                const int v2 = cube_edge_vertex(W, tj[2], ax, ay, az);
+                md.at[tb + off + j] = make_ushort4((unsigned short)v0, (unsigned short)v1, (unsigned short)v2,
+                                                   (unsigned short)a);
+            }
+            tb += round_t;
         }
     }
     __syncwarp();

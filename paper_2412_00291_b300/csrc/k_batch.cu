@@ -74,7 +74,7 @@ struct BatchSmem {
 };
 
 template <int WARPS, int VPT>
-__global__ void __launch_bounds__(32 * WARPS, 16 / WARPS) k_batch(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch(const __grid_constant__ BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BatchSmem<WARPS> &S = *reinterpret_cast<BatchSmem<WARPS> *>(smem_raw);
     BatchCtl *ctl = a.ctl;

@@ -23,7 +23,7 @@
 namespace stsdf {
 
 template <bool F16>
-__global__ void __launch_bounds__(256, 6) k_tsdf(ScanConst sc, MapDev md, FrameDev fd) {
+__global__ void __launch_bounds__(256, 4) k_tsdf(ScanConst sc, MapDev md, FrameDev fd) {
     __shared__ int2 s_buf[8][BV];   // per-warp class-update entries of the current block
     const int lane = threadIdx.x & 31;
     int2 *wbuf = s_buf[threadIdx.x >> 5];

@@ -121,7 +121,7 @@ static void free_all(map_t *m) {
     prof_clear(m);
     void *ptrs[] = {m->md.keys, m->md.vals, m->md.stamp, m->md.dstamp_slot, m->md.dw32, m->md.dw16, m->md.lp32,
                     m->md.lp16, m->md.label, m->md.slot_key, m->md.slot_frame, m->md.nbr, m->md.seg, m->md.av, m->md.ak, m->md.at,
-                    m->av_alt, m->ak_alt, m->at_alt, m->st, m->fd.win, m->fd.pix, m->fd.logL, m->fd.sem_ok,
+                    m->av_alt, m->ak_alt, m->at_alt, m->st, m->fd.win, m->fd.pix, m->fd.logL,
                     m->fd.touched, m->fd.dirty, m->fd.sem_list, m->fd.ctr, m->gb.voff, m->gb.toff, m->gb.bsum_v, m->gb.bsum_t,
                     m->gb.totals, m->stage_pts, m->stage_lab, m->stage_probs, m->out_pos, m->out_col,
                     m->out_keys, m->out_tri, m->out_anchor, m->gn_T, m->gn_acc, m->pal_dev};
@@ -220,7 +220,6 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     ALLOC(fd.win, c.max_pixels);
     ALLOC(fd.pix, c.max_pixels);
     ALLOC(fd.logL, c.max_pixels * c.n_classes);
-    ALLOC(fd.sem_ok, c.max_pixels);
     ALLOC(fd.touched, nb);
     ALLOC(fd.dirty, nb);
     fd.sem_cap = std::min<long long>(nvox, 1ll << 25);

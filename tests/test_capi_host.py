@@ -66,6 +66,28 @@ def test_mc_table_matches_oracle_face_walk():
         assert got == want, cs
 
 
+def test_mc_table_uses_exactly_the_crossing_edges():
+    """Every case with corners on both sides emits triangles, and its triangles use exactly the
+    cube edges whose endpoints differ in sign (the mesh kernel marks vertex edges by sign
+    changes next to fully observed cubes and relies on this)."""
+    import paper_2412_00291_b300 as p
+    table = p.map_mc_table()
+    for cs in range(256):
+        crossing = set()
+        for ce in range(12):
+            axis, d1, d2 = ce >> 2, ce & 1, (ce >> 1) & 1
+            off = [0, 0, 0]
+            off[(axis + 1) % 3] = d1
+            off[(axis + 2) % 3] = d2
+            c0 = off[0] + 2 * off[1] + 4 * off[2]
+            c1 = c0 + (1 << axis)
+            if ((cs >> c0) ^ (cs >> c1)) & 1:
+                crossing.add(ce)
+        used = {int(ce) for j in range(p.MC_MAXTRI) if table[cs, j, 0] >= 0 for ce in table[cs, j]}
+        assert used == crossing, cs
+        assert (len(used) > 0) == (cs not in (0, 255))
+
+
 def test_palette_matches_oracle():
     import paper_2412_00291_b300 as p
     for C in (2, 7, 20, 64):
