@@ -37,9 +37,8 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-PHASES = ("reset", "points", "pixels", "tsdf", "semantic", "mesh")
-KERNEL_FILES = {"points": "k_alloc.cu", "pixels": "k_scan.cu", "tsdf": "k_integrate.cu",
-                "semantic": "k_integrate.cu", "mesh": "k_mesh.cu"}
+PHASES = ("reset", "points", "tsdf", "semantic", "mesh")
+KERNEL_FILES = {"points": "k_alloc.cu", "tsdf": "k_integrate.cu", "semantic": "k_integrate.cu", "mesh": "k_mesh.cu"}
 
 
 def parse():
@@ -81,12 +80,12 @@ def algorithmic_bytes(st, n_points, H, W, C, s):
 
     st: per-scan counters (MAP_STAT_* order); s: bytes per stored scalar (4 FP32, 2 FP16).
     points:   the points (12 B each); winners and hash probes stay in L2.
-    pixels:   winner probability rows (4C B) read, log-likelihood rows (4C B),
-              pixel records (16 B) and flags (1 B) written, per pixel.
     tsdf:     {D, W} read and written (2 x 2s B) per updated voxel, an 8 B
-              list entry per semantic voxel, a 16 B work record per touched block.
+              list entry per semantic voxel, a 16 B work record per touched block
+              (range-image winners and winner points are L2 reads).
     semantic: C log-probabilities read and written (2 C s B), the label byte
-              and the 8 B list entry per semantically updated voxel.
+              and the 8 B list entry per semantically updated voxel (the
+              winners' class inputs are L2 reads).
     mesh:     {D, W} + label (2s + 1 B) of the 512 own voxels and the segment
               record (16 B) per re-meshed block, 24 B per vertex and 8 B per
               triangle emitted (neighbour faces are re-reads).
@@ -95,7 +94,6 @@ def algorithmic_bytes(st, n_points, H, W, C, s):
     return {
         "reset": H * W * 8,
         "points": n_points * 12,
-        "pixels": H * W * (8 * C + 17),
         "tsdf": upd * 2 * (2 * s) + sem * 8 + touched * 16,
         "semantic": sem * (2 * C * s + 1 + 8),
         "mesh": dirty * (512 * (2 * s + 1) + 16) + mv * 24 + mt * 8,

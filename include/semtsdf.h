@@ -286,11 +286,10 @@ map_status map_write_blocks(map_t *map, const int32_t *coords_host, int64_t n, c
 enum {
     MAP_PHASE_RESET = 0,      /* range-image and counter resets                               */
     MAP_PHASE_POINTS = 1,     /* per point: range-image winner (Sec. III-C.1), band allocation */
-    MAP_PHASE_PIXELS = 2,     /* per pixel: range pair and class log-likelihood               */
-    MAP_PHASE_TSDF = 3,       /* projective TSDF update (Sec. III-C.2), re-mesh queue          */
-    MAP_PHASE_SEMANTIC = 4,   /* Bayesian class fusion (Eq. bayesian_filter)                  */
-    MAP_PHASE_MESH = 5,       /* incremental marching cubes                                   */
-    MAP_PHASE_COUNT = 6
+    MAP_PHASE_TSDF = 2,       /* projective TSDF update (Sec. III-C.2), re-mesh queue          */
+    MAP_PHASE_SEMANTIC = 3,   /* Bayesian class fusion (Eq. bayesian_filter)                  */
+    MAP_PHASE_MESH = 4,       /* incremental marching cubes                                   */
+    MAP_PHASE_COUNT = 5
 };
 
 /* Start recording per-phase events for up to max_frames subsequent

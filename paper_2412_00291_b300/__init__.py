@@ -330,7 +330,7 @@ def map_write_blocks(h, coords, D, W, logP=None):
     _check(_lib.map_write_blocks(h, _np_ptr(c), len(c), _np_ptr(D), _np_ptr(W), _np_ptr(lp)), h)
 
 
-PHASES = ("reset", "points", "pixels", "tsdf", "semantic", "mesh")
+PHASES = ("reset", "points", "tsdf", "semantic", "mesh")
 
 
 def map_profile_begin(h, max_frames):
@@ -338,7 +338,7 @@ def map_profile_begin(h, max_frames):
 
 
 def map_profile_end(h, max_frames):
-    """Phase durations [frames, 6] (ms, see PHASES) and per-frame counters [frames, 16]."""
+    """Phase durations [frames, 5] (ms, see PHASES) and per-frame counters [frames, 16]."""
     out = np.zeros((max(int(max_frames), 1), len(PHASES)), np.float32)
     st = np.zeros((max(int(max_frames), 1), 16), np.int64)
     n = ctypes.c_int32()

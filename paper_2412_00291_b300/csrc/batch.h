@@ -12,9 +12,6 @@ struct BatchItem {
     ScanConst sc;
     MapDev md;
     FrameDev fd;
-    const float *pts;
-    const int32_t *labels;
-    const float *probs;
     const uchar4 *pal;
 };
 

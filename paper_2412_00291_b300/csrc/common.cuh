@@ -99,6 +99,10 @@ struct ScanConst {
     int frame;
     int has_probs;
     int probs_vec4;       // probability rows can be read as float4 (C % 4 == 0, 16-byte aligned)
+    // the scan: points [n][3], and per point a label [n] or class probabilities [n][C]
+    const float *pts;
+    const int32_t *labels;
+    const float *probs;
 };
 
 // Device pointers of one map.
@@ -131,12 +135,10 @@ struct MapDev {
 
 // Per-frame scratch of one map.
 struct FrameDev {
-    unsigned long long *win;   // [H*W] (float bits of range << 32) | point index
-    float4 *pix;               // [H*W] {r, r^2 hi, r^2 lo, flag bits: -1 no return, 0 no class likelihood, 1 likelihood}
-    float *logL;               // [H*W][C] per-pixel class log-likelihood
+    unsigned long long *win;   // [H*W] range-image winner: (float bits of range << 32) | point index, ~0 if none
     int *touched;              // [max_blocks] hash slots of U_k
     int *dirty;                // [max_blocks] pool slots to re-mesh
-    int2 *sem_list;            // [sem_cap] {pool voxel index, pixel} awaiting the class update
+    int2 *sem_list;            // [sem_cap] {pool voxel index, winner point index} awaiting the class update
     long long sem_cap;
     unsigned long long *ctr;   // [CT_COUNT]
 };
@@ -269,6 +271,27 @@ __device__ __forceinline__ long long block_sum(long long v, long long *s_tmp) {
     for (int i = 0; i < nw; ++i) t += s_tmp[i];
     __syncthreads();
     return t;
+}
+
+// Per-CTA totals of per-thread statistics, added to the frame counters by
+// thread 0 (one atomic per counter and CTA instead of one per warp: the
+// counters share a cache line, whose atomics the L2 serialises).
+template <int N>
+__device__ __forceinline__ void cta_count(unsigned long long *ctr, const int (&idx)[N], long long (&v)[N]) {
+    __shared__ long long s_part[N][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        if (lane == 0) s_part[k][wid] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < N) {
+        long long t = 0;
+        for (int i = 0; i < nw; ++i) t += s_part[threadIdx.x][i];
+        if (t) atomicAdd(&ctr[idx[threadIdx.x]], (unsigned long long)t);
+    }
 }
 
 }  // namespace stsdf

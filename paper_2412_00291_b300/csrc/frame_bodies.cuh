@@ -120,8 +120,10 @@ __device__ __forceinline__ int hash_insert(const MapDev &md, uint64_t key, int &
 // (u = round((pi - atan2(y, x)) / dphi) mod W, v = round((acos(z / r) -
 // theta0) / dtheta); nearest point wins, equal ranges the lower index, by one
 // 64-bit atomicMin on (range bits << 32 | index)), and the blocks of its band.
+// The point's statistics (valid, in a pixel, blocks it inserted) are added
+// to `cnt`; the caller forms the totals.
 __device__ __forceinline__ void points_item(const float *__restrict__ pts, const ScanConst &sc, const MapDev &md,
-                                            const FrameDev &fd, long long i) {
+                                            const FrameDev &fd, long long i, long long (&cnt)[3]) {
     int nb = 0, valid = 0, inpix = 0;
     int blocks[MAX_BAND_BLOCKS][3];
     if (i < sc.n) {
@@ -139,85 +141,71 @@ __device__ __forceinline__ void points_item(const float *__restrict__ pts, const
             }
         }
     }
-    const unsigned mv = __ballot_sync(0xffffffffu, valid), mp = __ballot_sync(0xffffffffu, inpix);
-    if ((threadIdx.x & 31) == 0 && (mv | mp)) {
-        atomicAdd(&fd.ctr[CT_VALID], (unsigned long long)__popc(mv));
-        atomicAdd(&fd.ctr[CT_PIXEL], (unsigned long long)__popc(mp));
-    }
+    cnt[0] += valid;
+    cnt[1] += inpix;
     int n_new = 0;
-    // step j of every lane's band together: lanes holding the same block (neighbouring
-    // points of a beam) leave it to the lowest of them, which spares repeated probes
-    // and same-address atomics
+    const int lane = threadIdx.x & 31;
+    // Four band steps of every lane at a time.  Lanes holding the same block in
+    // one step (neighbouring points of a beam) leave it to the lowest of them;
+    // the owners' first hash probes, then their frame-stamp exchanges, are all
+    // in flight together, and the blocks first touched in this frame are
+    // appended to U_k with one counter update per warp.
     const int nb_max = __reduce_max_sync(0xffffffffu, (unsigned)nb);
-    for (int j = 0; j < nb_max; ++j) {
-        const uint64_t key = j < nb ? pack_block(blocks[j][0], blocks[j][1], blocks[j][2]) : EMPTY_KEY;
-        const unsigned grp = __match_any_sync(0xffffffffu, key);
-        if (j >= nb || __ffs(grp) - 1 != (int)(threadIdx.x & 31)) continue;
-        int is_new = 0;
-        const int h = hash_insert(md, key, is_new);
-        if (h < 0) continue;
-        if (is_new) {
-            ++n_new;
-            const int s = md.vals[h];
-            if (s >= 0) {
-                md.slot_key[s] = key;
-                md.slot_frame[s] = sc.frame;
+    for (int j0 = 0; j0 < nb_max; j0 += 4) {
+        uint64_t key[4];
+        bool own[4];
+        int h[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + q;
+            key[q] = j < nb ? pack_block(blocks[j][0], blocks[j][1], blocks[j][2]) : EMPTY_KEY;
+            const unsigned grp = __match_any_sync(0xffffffffu, key[q]);
+            own[q] = j < nb && __ffs(grp) - 1 == lane;
+        }
+        uint64_t probe[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            h[q] = (int)(fmix64(key[q]) & md.mask);
+            probe[q] = own[q] ? md.keys[h[q]] : key[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (own[q] && probe[q] != key[q]) {
+                // not at its home slot: the full find-or-insert
+                int is_new = 0;
+                h[q] = hash_insert(md, key[q], is_new);
+                if (h[q] >= 0 && is_new) {
+                    ++n_new;
+                    const int sl = md.vals[h[q]];
+                    if (sl >= 0) {
+                        md.slot_key[sl] = key[q];
+                        md.slot_frame[sl] = sc.frame;
+                    }
+                }
             }
         }
-        if (atomicExch(&md.stamp[h], sc.frame) != sc.frame) {
-            const unsigned long long idx = atomicAdd(&fd.ctr[CT_TOUCHED], 1ull);
-            if (idx < (unsigned long long)md.max_blocks) fd.touched[idx] = h;
-            else atomicOr(&md.st->err, ERR_LIST_FULL);
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) n_new += __shfl_xor_sync(0xffffffffu, n_new, o);
-    if ((threadIdx.x & 31) == 0 && n_new) atomicAdd(&fd.ctr[CT_NEW], (unsigned long long)n_new);
-}
-
-// Per pixel: the winner's range r, r^2 as an exact float pair, a flag (-1 no
-// return, 0 a return without class likelihood, 1 with one), and its class
-// log-likelihood row log P(O = l | I_k) of Eq. (bayesian_filter)
-// (or no likelihood when the winner carries no valid label).
-__device__ __forceinline__ void pixel_item(const float *__restrict__ pts, const int32_t *__restrict__ labels,
-                                           const float *__restrict__ probs, const ScanConst &sc, const FrameDev &fd,
-                                           int p) {
-    if (p >= sc.H * sc.W) return;
-    const unsigned long long key = fd.win[p];
-    if (key == ~0ull) {
-        fd.pix[p] = make_float4(-1.f, 0.f, 0.f, __int_as_float(-1));
-        return;
-    }
-    const int idx = (int)(key & 0xffffffffu);
-    const float r = __uint_as_float((unsigned)(key >> 32));
-    const float x = pts[3 * idx], y = pts[3 * idx + 1], z = pts[3 * idx + 2];
-    float a, ae, b, be, c, ce, sh, sl;
-    two_prod(x, x, a, ae);
-    two_prod(y, y, b, be);
-    two_prod(z, z, c, ce);
-    df_add(a, ae, b, be, sh, sl);
-    df_add(sh, sl, c, ce, sh, sl);
-    const int C = sc.C;
-    int has_lik = 1;
-    float *out = fd.logL + (long long)p * C;
-    if (sc.has_probs) {
-        const float *q = probs + (long long)idx * C;
-        if (sc.probs_vec4) {
-            for (int cc = 0; cc < C; cc += 4) {
-                const float4 v = *reinterpret_cast<const float4 *>(q + cc);
-                *reinterpret_cast<float4 *>(out + cc) =
-                    make_float4(logf(fmaxf(v.x, sc.lik_floor)), logf(fmaxf(v.y, sc.lik_floor)),
-                                logf(fmaxf(v.z, sc.lik_floor)), logf(fmaxf(v.w, sc.lik_floor)));
+        bool first[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            first[q] = own[q] && h[q] >= 0 && atomicExch(&md.stamp[h[q]], sc.frame) != sc.frame;
+        const int cnt = (int)first[0] + (int)first[1] + (int)first[2] + (int)first[3];
+        int tot;
+        int off = warp_exclusive_scan(cnt, tot);
+        if (tot) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&fd.ctr[CT_TOUCHED], (unsigned long long)tot);
+            base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (first[q]) {
+                    const unsigned long long idx = base + off++;
+                    if (idx < (unsigned long long)md.max_blocks) fd.touched[idx] = h[q];
+                    else atomicOr(&md.st->err, ERR_LIST_FULL);
+                }
             }
-        } else {
-            for (int cc = 0; cc < C; ++cc) out[cc] = logf(fmaxf(q[cc], sc.lik_floor));
         }
-    } else {
-        const int l = labels[idx];
-        has_lik = (l >= 0 && l < C);
-        if (has_lik)
-            for (int cc = 0; cc < C; ++cc) out[cc] = (cc == l) ? sc.log_phit : sc.log_pmiss;
     }
-    fd.pix[p] = make_float4(r, sh, sl, __int_as_float(has_lik));
+    cnt[2] += n_new;
 }
 
 template <bool F16>
@@ -294,22 +282,35 @@ __device__ __forceinline__ int tsdf_pixel(const ScanConst &sc, int bx, int by, i
     return (v >= 0 && v < sc.H) ? v * sc.W + u : -1;
 }
 
-// Projective psi and the running-average update of one voxel given its pixel
-// record px (Sec. III-C.2) and its stored {D, W} (read ahead by the caller).
-// Returns true when the voxel also takes the class update.
+// Projective psi and the running-average update of one voxel whose pixel's
+// range-image winner is `win` (range bits << 32 | point index, ~0 when the
+// pixel has no return) (Sec. III-C.2), given the voxel's stored {D, W} (read
+// ahead by the caller).  Returns true when the voxel also takes the class
+// update, with the winner's point index in `idx`.
 template <bool F16>
 __device__ __forceinline__ bool tsdf_update(const ScanConst &sc, const MapDev &md, long long vox, int vi, int p,
-                                            float4 px, float2 dw, float m0, float m1, float m2, float rr2, float irr,
-                                            long long &n_upd, unsigned &remesh) {
-    if (p < 0 || __float_as_int(px.w) < 0) return false;
+                                            unsigned long long win, float2 dw, float m0, float m1, float m2,
+                                            float rr2, float irr, long long &n_upd, unsigned &remesh, int &idx) {
+    if (p < 0 || win == ~0ull) return false;
     const float tau = sc.tau;
+    const float r = __uint_as_float((unsigned)(win >> 32));
     // plain FP32 psi is within ~1e-5 m of the exact value; away from +-tau it
     // decides the update exactly: beyond +tau (+1 mm) sdf = tau and w = 1, below
     // -tau (-1 mm) nothing; only the band in between needs the float-pair psi
-    float psi = px.x - sc.nu * (rr2 * irr);
+    float psi = r - sc.nu * (rr2 * irr);
     float sdf = tau, w = 1.f;
     bool upd = psi >= -tau - 1e-3f, sem = false;
     if (upd && psi <= tau + 1e-3f) {
+        // r^2 of the winner as an exact float pair, from its coordinates
+        idx = (int)(win & 0xffffffffu);
+        const float x = sc.pts[3 * (long long)idx], y = sc.pts[3 * (long long)idx + 1],
+                    z = sc.pts[3 * (long long)idx + 2];
+        float a, ae, b, be, c, ce, rh, rl;
+        two_prod(x, x, a, ae);
+        two_prod(y, y, b, be);
+        two_prod(z, z, c, ce);
+        df_add(a, ae, b, be, rh, rl);
+        df_add(rh, rl, c, ce, rh, rl);
         float e0, e1, e2, t0, t1, t2;
         two_sum(m0, -sc.fhi[0], t0, e0);
         two_sum(m1, -sc.fhi[1], t1, e1);
@@ -318,7 +319,7 @@ __device__ __forceinline__ bool tsdf_update(const ScanConst &sc, const MapDev &m
         e1 = __fsub_rn(e1, sc.flo[1]);
         e2 = __fsub_rn(e2, sc.flo[2]);
         // rho^2 in voxel units, then metres^2, as float pairs; psi = (r^2 - rho^2) / (r + rho)
-        float a, ae, b, be, c, ce, qh, ql, mh, ml, dh, dl;
+        float qh, ql, mh, ml, dh, dl;
         two_prod(t0, t0, a, ae);
         two_prod(t1, t1, b, be);
         two_prod(t2, t2, c, ce);
@@ -328,12 +329,20 @@ __device__ __forceinline__ bool tsdf_update(const ScanConst &sc, const MapDev &m
         df_add(a, ae, b, be, qh, ql);
         df_add(qh, ql, c, ce, qh, ql);
         df_mul(qh, ql, sc.nu2hi, sc.nu2lo, mh, ml);
-        df_add(px.y, px.z, -mh, -ml, dh, dl);
-        psi = __fdividef(dh + dl, px.x + mh * rsqrtf(mh));
+        df_add(rh, rl, -mh, -ml, dh, dl);
+        psi = __fdividef(dh + dl, r + mh * rsqrtf(mh));
         sdf = fminf(psi, tau);
         if (sc.weight_mode == 0) w = fminf(fmaxf((psi + tau) * sc.inv_2tau, 0.f), 1.f);
         upd = psi >= -tau && w > 0.f;
-        sem = upd && fabsf(psi) <= tau && __float_as_int(px.w) == 1;
+        if (upd && fabsf(psi) <= tau) {
+            // the winner carries a class likelihood: a probability row, or a label in range
+            if (sc.has_probs) {
+                sem = true;
+            } else {
+                const int l = sc.labels[idx];
+                sem = l >= 0 && l < sc.C;
+            }
+        }
     }
     if (upd) {
         const float Wn = dw.y + w;
@@ -344,10 +353,11 @@ __device__ __forceinline__ bool tsdf_update(const ScanConst &sc, const MapDev &m
     return sem;
 }
 
-// Class-update entries collect in the warp's shared buffer (one global append per block).
-__device__ __forceinline__ void tsdf_list(bool sem, int vox, int p, int2 *wbuf, int &wcount) {
+// Class-update entries {voxel, winner point} collect in the warp's shared
+// buffer (one global append per block).
+__device__ __forceinline__ void tsdf_list(bool sem, int vox, int idx, int2 *wbuf, int &wcount) {
     const unsigned mk = __ballot_sync(0xffffffffu, sem);
-    if (sem) wbuf[wcount + __popc(mk & ((1u << (threadIdx.x & 31)) - 1u))] = make_int2(vox, p);
+    if (sem) wbuf[wcount + __popc(mk & ((1u << (threadIdx.x & 31)) - 1u))] = make_int2(vox, idx);
     wcount += __popc(mk);
 }
 
@@ -375,11 +385,12 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
         float ma0, ma1, ma2, ra, ia, mb0, mb1, mb2, rb, ib;
         const int pa = tsdf_pixel(sc, bx, by, bz, vi, ma0, ma1, ma2, ra, ia);
         const int pb = tsdf_pixel(sc, bx, by, bz, vi + 32, mb0, mb1, mb2, rb, ib);
-        const float4 pxa = fd.pix[pa < 0 ? 0 : pa], pxb = fd.pix[pb < 0 ? 0 : pb];
-        const bool sa = tsdf_update<F16>(sc, md, va, vi, pa, pxa, dwa, ma0, ma1, ma2, ra, ia, n_upd, remesh);
-        const bool sb = tsdf_update<F16>(sc, md, vb, vi + 32, pb, pxb, dwb, mb0, mb1, mb2, rb, ib, n_upd, remesh);
-        tsdf_list(sa, slot * BV + vi, pa, wbuf, wcount);
-        tsdf_list(sb, slot * BV + vi + 32, pb, wbuf, wcount);
+        const unsigned long long wa = fd.win[pa < 0 ? 0 : pa], wb = fd.win[pb < 0 ? 0 : pb];
+        int ka = 0, kb = 0;
+        const bool sa = tsdf_update<F16>(sc, md, va, vi, pa, wa, dwa, ma0, ma1, ma2, ra, ia, n_upd, remesh, ka);
+        const bool sb = tsdf_update<F16>(sc, md, vb, vi + 32, pb, wb, dwb, mb0, mb1, mb2, rb, ib, n_upd, remesh, kb);
+        tsdf_list(sa, slot * BV + vi, ka, wbuf, wcount);
+        tsdf_list(sb, slot * BV + vi + 32, kb, wbuf, wcount);
     }
     __syncwarp();
     // one append of the block's class-update entries
@@ -490,23 +501,30 @@ __device__ __forceinline__ void semantic_item(const ScanConst &sc, const MapDev 
     const int C = NC > 0 ? NC : sc.C;
     const int2 ent = fd.sem_list[e];
     const long long vox = ent.x;
-    const float *lrow = fd.logL + (long long)ent.y * C;
+    const long long idx = ent.y;   // the pixel's winner point: log P(O = l | I_k) from its input
     float m = -INFINITY;
     if (NC > 0) {
         float av[NC > 0 ? NC : 1];
         load_record<F16, (NC > 0 ? NC : 1)>(md, vox, av);
-        if (NC % 4 == 0) {
+        if (sc.has_probs) {
+            const float *q = sc.probs + idx * C;
+            if (NC % 4 == 0 && sc.probs_vec4) {
 #pragma unroll
-            for (int cc = 0; cc < (NC > 0 ? NC : 1); cc += 4) {
-                const float4 l4 = *reinterpret_cast<const float4 *>(lrow + cc);
-                av[cc] += l4.x;
-                av[cc + 1] += l4.y;
-                av[cc + 2] += l4.z;
-                av[cc + 3] += l4.w;
+                for (int cc = 0; cc < (NC > 0 ? NC : 1); cc += 4) {
+                    const float4 v = *reinterpret_cast<const float4 *>(q + cc);
+                    av[cc] += logf(fmaxf(v.x, sc.lik_floor));
+                    av[cc + 1] += logf(fmaxf(v.y, sc.lik_floor));
+                    av[cc + 2] += logf(fmaxf(v.z, sc.lik_floor));
+                    av[cc + 3] += logf(fmaxf(v.w, sc.lik_floor));
+                }
+            } else {
+#pragma unroll
+                for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) av[cc] += logf(fmaxf(q[cc], sc.lik_floor));
             }
         } else {
+            const int l = sc.labels[idx];
 #pragma unroll
-            for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) av[cc] += lrow[cc];
+            for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) av[cc] += cc == l ? sc.log_phit : sc.log_pmiss;
         }
 #pragma unroll
         for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) m = fmaxf(m, av[cc]);
@@ -529,8 +547,11 @@ __device__ __forceinline__ void semantic_item(const ScanConst &sc, const MapDev 
         md.label[vox] = (uint8_t)best;
     } else {
         float av[MAXC_RT];
+        const float *q = sc.probs + idx * C;
+        const int l = sc.has_probs ? -1 : sc.labels[idx];
         for (int cc = 0; cc < C; ++cc) {
-            av[cc] = load_lp<F16>(md, lp_index(md, vox, cc)) + lrow[cc];
+            const float lik = sc.has_probs ? logf(fmaxf(q[cc], sc.lik_floor)) : (cc == l ? sc.log_phit : sc.log_pmiss);
+            av[cc] = load_lp<F16>(md, lp_index(md, vox, cc)) + lik;
             m = fmaxf(m, av[cc]);
         }
         float ssum = 0.f;

@@ -13,7 +13,9 @@
 namespace stsdf {
 
 __global__ void __launch_bounds__(256) k_points(const float *__restrict__ pts, ScanConst sc, MapDev md, FrameDev fd) {
-    points_item(pts, sc, md, fd, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    long long cnt[3] = {0, 0, 0};
+    points_item(pts, sc, md, fd, (long long)blockIdx.x * blockDim.x + threadIdx.x, cnt);
+    cta_count<3>(fd.ctr, {CT_VALID, CT_PIXEL, CT_NEW}, cnt);
 }
 
 // Link every allocated block (after host-side writes).

@@ -2,7 +2,7 @@
 // each of up to BATCH_MAX maps (uneven scan sizes, voxel sizes and storage).
 //
 // The kernel runs the per-frame phases back to back for all maps at once:
-//   reset -> points -> pixels -> TSDF -> class update -> re-meshing,
+//   reset -> points -> TSDF -> class update -> re-meshing,
 // separated by a grid-wide barrier.  Inside a phase, a flattened work index
 // is mapped to (map, item) through prefix sums over the maps' item counts
 // (each map's range padded to a multiple of 32, so that warp-level votes
@@ -111,19 +111,20 @@ __global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch(const __grid_c
             const long long wb = base + (long long)k * nthreads;   // warp-uniform
             if (wb >= S.pre[n]) break;
             const int i = find_map(S.pre, n, wb);
-            points_item(a.it[i].pts, a.it[i].sc, a.it[i].md, a.it[i].fd, wb - S.pre[i] + lane);
+            long long cnt[3] = {0, 0, 0};
+            points_item(a.it[i].sc.pts, a.it[i].sc, a.it[i].md, a.it[i].fd, wb - S.pre[i] + lane, cnt);
+            // the warp's items all belong to map i: one add per counter and warp
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) cnt[c] += __shfl_xor_sync(0xffffffffu, cnt[c], o);
+            }
+            if (lane == 0) {
+                if (cnt[0]) atomicAdd(&a.it[i].fd.ctr[CT_VALID], (unsigned long long)cnt[0]);
+                if (cnt[1]) atomicAdd(&a.it[i].fd.ctr[CT_PIXEL], (unsigned long long)cnt[1]);
+                if (cnt[2]) atomicAdd(&a.it[i].fd.ctr[CT_NEW], (unsigned long long)cnt[2]);
+            }
         }
-    }
-    if (!grid_sync(ctl, limit, gen)) return;
-
-    // ---- pixels: range pair and class log-likelihood --------------------------
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < n; ++i) S.pre[i + 1] = S.pre[i] + (long long)a.it[i].sc.H * a.it[i].sc.W;
-    }
-    __syncthreads();
-    for (long long e = tid; e < S.pre[n]; e += nthreads) {
-        const int i = find_map(S.pre, n, e);
-        pixel_item(a.it[i].pts, a.it[i].labels, a.it[i].probs, a.it[i].sc, a.it[i].fd, (int)(e - S.pre[i]));
     }
     if (!grid_sync(ctl, limit, gen)) return;
 

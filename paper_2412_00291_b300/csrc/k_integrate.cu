@@ -25,7 +25,6 @@ namespace stsdf {
 template <bool F16>
 __global__ void __launch_bounds__(256, 4) k_tsdf(ScanConst sc, MapDev md, FrameDev fd) {
     __shared__ int2 s_buf[8][BV];   // per-warp class-update entries of the current block
-    const int lane = threadIdx.x & 31;
     int2 *wbuf = s_buf[threadIdx.x >> 5];
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -33,9 +32,8 @@ __global__ void __launch_bounds__(256, 4) k_tsdf(ScanConst sc, MapDev md, FrameD
     unsigned long long nt = *(volatile unsigned long long *)&fd.ctr[CT_TOUCHED];
     if (nt > (unsigned long long)md.max_blocks) nt = md.max_blocks;
     for (long long li = warp; li < (long long)nt; li += nwarps) tsdf_block_warp<F16>(sc, md, fd, fd.touched[li], wbuf, n_upd);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) n_upd += __shfl_xor_sync(0xffffffffu, n_upd, o);
-    if (lane == 0 && n_upd) atomicAdd(&fd.ctr[CT_UPD], (unsigned long long)n_upd);
+    long long cnt[1] = {n_upd};
+    cta_count<1>(fd.ctr, {CT_UPD}, cnt);
 }
 
 template <bool F16, int NC>

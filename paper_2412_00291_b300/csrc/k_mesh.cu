@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(32 * MESH_WARPS) k_mesh(MapDev md, FrameDev fd
         S.pal[i] = tpal[i];
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int wid = threadIdx.x >> 5;
     unsigned long long nd = *(volatile unsigned long long *)&fd.ctr[CT_DIRTY];
     if (nd > (unsigned long long)md.max_blocks) nd = md.max_blocks;
     const long long nwarps = (long long)gridDim.x * MESH_WARPS;
@@ -40,10 +40,8 @@ __global__ void __launch_bounds__(32 * MESH_WARPS) k_mesh(MapDev md, FrameDev fd
     long long n_v = 0, n_t = 0;
     for (long long li = (long long)blockIdx.x * MESH_WARPS + wid; li < (long long)nd; li += nwarps)
         mesh_block_warp(md, fd, S.tri, S.ntri, S.pal, S.w[wid], fd.dirty[li], part, n_v, n_t);
-    if (lane == 0) {
-        if (n_v) atomicAdd(&fd.ctr[CT_MV], (unsigned long long)n_v);
-        if (n_t) atomicAdd(&fd.ctr[CT_MT], (unsigned long long)n_t);
-    }
+    long long cnt[2] = {n_v, n_t};
+    cta_count<2>(fd.ctr, {CT_MV, CT_MT}, cnt);
 }
 
 int mesh_upload_tables(const int8_t *tri, const uint8_t *ntri) {

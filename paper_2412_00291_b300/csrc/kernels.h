@@ -5,10 +5,6 @@
 
 namespace stsdf {
 
-// k_scan.cu: per-pixel table of the range image (Sec. III-C.1)
-void launch_pixels(const float *pts, const int32_t *labels, const float *probs, const ScanConst &sc,
-                   const FrameDev &fd, cudaStream_t s);
-
 // k_alloc.cu: per-point range-image winners and band allocation (touched list)
 void launch_points(const float *pts, const ScanConst &sc, const MapDev &md, const FrameDev &fd, cudaStream_t s);
 void launch_list_all(const MapDev &md, const FrameDev &fd, int frame, cudaStream_t s);

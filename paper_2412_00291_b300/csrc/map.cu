@@ -121,7 +121,7 @@ static void free_all(map_t *m) {
     prof_clear(m);
     void *ptrs[] = {m->md.keys, m->md.vals, m->md.stamp, m->md.dstamp_slot, m->md.dw32, m->md.dw16, m->md.lp32,
                     m->md.lp16, m->md.label, m->md.slot_key, m->md.slot_frame, m->md.nbr, m->md.seg, m->md.av, m->md.ak, m->md.at,
-                    m->av_alt, m->ak_alt, m->at_alt, m->st, m->fd.win, m->fd.pix, m->fd.logL,
+                    m->av_alt, m->ak_alt, m->at_alt, m->st, m->fd.win,
                     m->fd.touched, m->fd.dirty, m->fd.sem_list, m->fd.ctr, m->gb.voff, m->gb.toff, m->gb.bsum_v, m->gb.bsum_t,
                     m->gb.totals, m->stage_pts, m->stage_lab, m->stage_probs, m->out_pos, m->out_col,
                     m->out_keys, m->out_tri, m->out_anchor, m->gn_T, m->gn_acc, m->pal_dev};
@@ -218,8 +218,6 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     md.st = m->st;
     FrameDev &fd = m->fd;
     ALLOC(fd.win, c.max_pixels);
-    ALLOC(fd.pix, c.max_pixels);
-    ALLOC(fd.logL, c.max_pixels * c.n_classes);
     ALLOC(fd.touched, nb);
     ALLOC(fd.dirty, nb);
     fd.sem_cap = std::min<long long>(nvox, 1ll << 25);
@@ -446,6 +444,9 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     ScanConst sc;
     map_status st = make_scan_const(m, L, n, T, probs != nullptr, sc);
     if (st != MAP_OK) return st;
+    sc.pts = pts;
+    sc.labels = labels;
+    sc.probs = probs;
     sc.probs_vec4 = probs && (m->C % 4 == 0) && (((uintptr_t)probs & 15) == 0);
     poll_stats(m);
     if (need_compaction(m)) {
@@ -465,15 +466,13 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     if (ev) CU(cudaEventRecord(ev[1], s));
     launch_points(pts, sc, m->md, m->fd, s);
     if (ev) CU(cudaEventRecord(ev[2], s));
-    launch_pixels(pts, labels, probs, sc, m->fd, s);
-    if (ev) CU(cudaEventRecord(ev[3], s));
     launch_integrate(sc, m->md, m->fd, m->grid_integrate, s);
-    if (ev) CU(cudaEventRecord(ev[4], s));
+    if (ev) CU(cudaEventRecord(ev[3], s));
     launch_semantic(sc, m->md, m->fd, m->grid_semantic, s);
-    if (ev) CU(cudaEventRecord(ev[5], s));
+    if (ev) CU(cudaEventRecord(ev[4], s));
     launch_mesh(m->md, m->fd, m->pal_dev, m->grid_mesh, s);
-    if (ev) CU(cudaEventRecord(ev[6], s));
-    m->launches += 5;
+    if (ev) CU(cudaEventRecord(ev[5], s));
+    m->launches += 4;
     if (ev_stats)
         CU(cudaMemcpyAsync(ev_stats, m->fd.ctr, CT_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
     st = launch_check(m, "integrate_scan kernels");
@@ -938,9 +937,9 @@ extern "C" map_status map_batch_integrate(map_batch_t *b, const scan_desc *scans
         it.sc = sc;
         it.md = m->md;
         it.fd = m->fd;
-        it.pts = d.points_dev;
-        it.labels = d.labels_dev;
-        it.probs = d.probs_dev;
+        it.sc.pts = d.points_dev;
+        it.sc.labels = d.labels_dev;
+        it.sc.probs = d.probs_dev;
         it.pal = m->pal_dev;
     }
     args.n = n;
