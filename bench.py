@@ -47,13 +47,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=195)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["loop64", "line16", "streams32"], default="loop64")
+    ap.add_argument("--workload", choices=["loop64", "line16", "streams32", "align1km"], default="loop64")
     ap.add_argument("--storage", choices=["fp32", "fp16"], default="fp32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--max-blocks", type=int, default=0, help="pool size override (profiling runs)")
     ap.add_argument("--mesh-cap", type=int, default=0, help="mesh arena vertex capacity override")
+    ap.add_argument("--no-fp16-report", action="store_true", help="skip the FP16-vs-FP32 comparison")
     return ap.parse_args()
 
 
@@ -198,6 +199,44 @@ def traffic_record(kernel):
     if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec.get("source_sha"):
         return None
     return rec
+
+
+def fp16_report(P, w, lid, m16, make_step, n_frames, cfg, dev):
+    """Precision form vs plain: the FP16-storage map after n_frames scans against an FP32-storage
+    map fed the same scans: per-voxel TSDF error, weight error, label agreement and mesh vertex
+    error (vertices matched by edge key), with the stated FP16 bound n_frames * 2^-11 * tau."""
+    import torch
+    m32 = P.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, storage=0, **cfg)
+    step = make_step(m32)
+    for k in range(n_frames):
+        step(k)
+    torch.cuda.synchronize()
+    b16 = m16.blocks()
+    b32 = m32.blocks()
+    s16 = {tuple(b) for b in b16.tolist()}
+    same_blocks = s16 == {tuple(b) for b in b32.tolist()}
+    sel = b32[:: max(1, len(b32) // 20000)]
+    r32 = m32.read_blocks(sel, want_logp=False)
+    r16 = m16.read_blocks(sel, want_logp=False)
+    obs = (r32["W"] > 0) & (r16["W"] > 0)
+    dD = np.abs(r16["D"] - r32["D"])[obs]
+    dW = (np.abs(r16["W"] - r32["W"]) / np.maximum(r32["W"], 1e-30))[obs]
+    lab = (r16["label"] == r32["label"])[obs]
+    g16 = {k: v.cpu().numpy() for k, v in m16.mesh().items()}
+    g32 = {k: v.cpu().numpy() for k, v in m32.mesh().items()}
+    k16, i16 = np.unique(g16["vertex_keys"], return_index=True)
+    k32, i32 = np.unique(g32["vertex_keys"], return_index=True)
+    common, a, b = np.intersect1d(k16, k32, return_indices=True)
+    dp = np.abs(g16["positions"][i16[a]] - g32["positions"][i32[b]]).max(axis=1) if len(common) else np.zeros(1)
+    m32.close()
+    return {"scans": n_frames, "block_sets_equal": bool(same_blocks), "voxels_compared": int(obs.sum()),
+            "max_abs_dD_m": float(dD.max(initial=0)), "mean_abs_dD_m": float(dD.mean()) if dD.size else 0.0,
+            "p99_abs_dD_m": float(np.percentile(dD, 99)) if dD.size else 0.0,
+            "stated_bound_m": n_frames * 2.0 ** -11 * w.truncation,
+            "max_rel_dW": float(dW.max(initial=0)), "label_agreement": float(lab.mean()) if lab.size else 1.0,
+            "mesh_vertices_fp16": int(len(k16)), "mesh_vertices_fp32": int(len(k32)),
+            "mesh_vertices_matched": int(len(common)), "mesh_vertex_max_err_m": float(dp.max(initial=0)),
+            "mesh_vertex_p99_err_m": float(np.percentile(dp, 99)) if len(common) else 0.0}
 
 
 def cpu_baseline(w, budget_s=15.0, max_frames=8, col_stride=1):
@@ -350,6 +389,9 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     phase_ms, fstats = P.map_profile_end(tsdf.h, args.steps)
     prof_total_ms = float(phase_ms.sum())
+    fp16 = None
+    if storage == 1 and not args.no_fp16_report:
+        fp16 = fp16_report(P, w, lid, tsdf, make_step, args.warmup + args.steps, cfg, dev)
     n_points = L.H * L.W
     value = world * args.steps * n_points / (total_ms * 1e-3)
     # --- roofline of the dominant kernel ------------------------------------
@@ -423,6 +465,7 @@ def run_ours(args, rank, world, local_rank):
         "kernels_note": "per-kernel times from a second pass over the same scans with CUDA events between "
                         f"the kernels ({prof_total_ms / args.steps:.4f} ms/scan with those events)",
         "cpu_baseline": cpu,
+        "fp16_vs_fp32": fp16,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clocks,
@@ -565,6 +608,163 @@ def run_batch(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def _rot_err_deg(Ra, Rb):
+    c = (np.trace(Ra.T @ Rb) - 1.0) / 2.0
+    return math.degrees(math.acos(max(-1.0, min(1.0, c))))
+
+
+def run_align(args, rank, world, local_rank):
+    """Differentiable form: scan-to-map alignment on a 1 km x 1 km map (FP16 storage).
+
+    The map is built by fusing the 480 scans of the drive.  Then `steps` scans (after `warmup`
+    untimed ones), spread along the drive, are aligned from a pose perturbed by 0.5 m along a
+    random direction and 5 deg about a random axis: 20 Gauss-Newton iterations of
+    sum query_sdf^2 over the scan's 131,072 points, all on the device (map_align_scan), timed
+    per scan with CUDA events on the launching stream.  On one scan the analytic pose gradient
+    is checked against FP64 central differences (h = 1e-4) of the oracle's loss evaluated on
+    the map blocks around 4,096 sampled points, copied from the device."""
+    import torch
+    import oracle
+    import paper_2412_00291_b300 as P
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.drive1km(seed=5 + 100 * rank)
+    L = w.lidar
+    lid = P.lidar_intrinsics(L.H, L.W, L.fov_up, L.fov_down, L.r_min, L.r_max)
+    m = P.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, storage=1, max_blocks=1 << 20,
+                       hash_capacity=1 << 22, mesh_vertex_capacity=64 << 20, mesh_triangle_capacity=128 << 20)
+    scene = synth.make_scene(w)
+    Ts = synth.trajectory(w, w.frames)
+    t0 = time.perf_counter()
+    frames_keep = {}
+    n_align = min(args.warmup + args.steps, 40)
+    pick = [int(40 + i * (w.frames - 80) / max(1, n_align - 1)) for i in range(n_align)]
+    for k in range(w.frames):
+        f = synth.make_frame(w, scene, Ts[k], k)
+        m.integrate(lid, torch.from_numpy(f.points).to(dev), f.T, labels=torch.from_numpy(f.labels).to(dev))
+        if k in pick:
+            ok = np.isfinite(f.points).all(axis=1)
+            frames_keep[k] = (f.points[ok].copy(), f.T.copy())
+    st = m.stats()
+    build_s = time.perf_counter() - t0
+    rng = np.random.default_rng([w.seed, 17])
+    stream = torch.cuda.current_stream(dev)
+    times, terr, rerr, terr0 = [], [], [], []
+    grad_check = None
+    with ClockSampler(local_rank) as clk:
+        for i, k in enumerate(pick):
+            pts, T = frames_keep[k]
+            d = rng.normal(size=3)
+            d /= np.linalg.norm(d)
+            a = rng.normal(size=3)
+            a /= np.linalg.norm(a)
+            # perturbation in the sensor frame: 0.5 m translation, 5 deg rotation about the sensor
+            dT = np.eye(4)
+            dT[:3, :3] = oracle.se3_exp(np.concatenate([np.zeros(3), math.radians(5.0) * a]))[:3, :3]
+            dT[:3, 3] = 0.5 * d
+            T0 = T @ dT
+            pd = torch.from_numpy(pts).to(dev)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Tout = m.align(pd, T0, iters=20)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+                terr.append(float(np.linalg.norm(Tout[:3, 3] - T[:3, 3])))
+                rerr.append(_rot_err_deg(Tout[:3, :3], T[:3, :3]))
+                terr0.append(float(np.linalg.norm(T0[:3, 3] - T[:3, 3])))
+            if grad_check is None:
+                grad_check = _align_grad_check(P, oracle, m, w, pts, T0, dev, rng)
+    if rank != 0:
+        return
+    n_pts = int(np.mean([len(frames_keep[k][0]) for k in pick]))
+    ms = float(np.mean(times))
+    line = {
+        "metric": "scan-to-map alignment time, 20 Gauss-Newton iterations (64x2048 scan, 1 km map)",
+        "value": ms, "unit": "ms/scan", "n_gpus": world, "steps": len(times), "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "fp16-storage/fp32-math (fp64 6x6 solve)", "data": "synthetic",
+        "config": {"workload": w.name, "points_per_scan_mean": n_pts, "map_blocks": st["total_blocks"],
+                   "map_voxels": st["total_blocks"] * 512, "map_build_s": build_s,
+                   "perturbation": "0.5 m along a random direction, 5 deg about a random axis",
+                   "iterations": 20, "timing": "CUDA events around each map_align_scan call (it synchronises)"},
+        "points_iterations_per_s": n_pts * 20 / (ms * 1e-3),
+        "final_translation_error_m": {"median": float(np.median(terr)), "max": float(np.max(terr))},
+        "final_rotation_error_deg": {"median": float(np.median(rerr)), "max": float(np.max(rerr))},
+        "initial_translation_error_m": float(np.median(terr0)),
+        "pose_gradient_check": grad_check,
+        "gpu_launches": None, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _align_grad_check(P, oracle, m, w, pts, T, dev, rng, n=4096, h=1e-4):
+    """Analytic pose gradient (hand-written backward) vs the oracle's FP64 analytic gradient and
+    FP64 central differences (h = 1e-4) of its loss, on a copy of the map blocks around n sampled
+    points.  Rotations are taken about the points' centroid c (rotating about the far-away world
+    origin would move the points by centimetres); the gradient about the origin converts as
+    g_phi(c) = g_phi - c x g_rho.  Only points valid at the pose and at all 12 perturbed poses
+    and inside the same interpolation cell at all of them enter the loss, so that it is smooth
+    (the trilinear field's gradient jumps across cell faces)."""
+    import torch
+    nu = w.voxel_size
+    sel = rng.choice(len(pts), size=min(n, len(pts)), replace=False)
+    p = pts[sel]
+    xw = (p.astype(np.float64) @ T[:3, :3].T + T[:3, 3]).astype(np.float32)
+    x = xw.astype(np.float64)
+    c = x.mean(axis=0)
+    # blocks holding every voxel within 3 voxels of a sampled point
+    v = np.floor(x / nu)
+    offs = np.array([[i, j, k] for i in (-3, 0, 3) for j in (-3, 0, 3) for k in (-3, 0, 3)])
+    blocks = np.unique(np.floor((v[:, None, :] + offs[None]) / 8.0).reshape(-1, 3).astype(np.int64), axis=0)
+    rb = m.read_blocks(blocks.astype(np.int32), want_logp=False)
+    o = oracle.OracleMap(nu, w.truncation, 2)
+    for b, f, D, W in zip(blocks, rb["found"], rb["D"], rb["W"]):
+        if f:
+            o.write_block(b.astype(np.int32), D.astype(np.float64), W.astype(np.float64))
+
+    def moved(j, sgn):
+        if j < 3:
+            y = x.copy()
+            y[:, j] += sgn * h
+            return y
+        e = np.zeros(6)
+        e[j] = sgn * h
+        R = oracle.se3_exp(e)[:3, :3]
+        return (x - c) @ R.T + c
+
+    base_sdf, base_ok, base_grad = o.query(x)
+    ok = base_ok.copy()
+    cell = np.floor(x / nu)
+    sides = {}
+    for j in range(6):
+        for sgn in (1, -1):
+            y = moved(j, sgn)
+            sd, vv, _ = o.query(y)
+            sides[(j, sgn)] = sd
+            # valid, and inside the same interpolation cell (the trilinear field is smooth there)
+            ok &= vv & np.all(np.floor(y / nu) == cell, axis=1)
+    fd = np.array([(np.sum(sides[(j, 1)][ok] ** 2) - np.sum(sides[(j, -1)][ok] ** 2)) / (2 * h) for j in range(6)])
+    # oracle analytic gradient on the same points (rotation about c)
+    gx = 2.0 * base_sdf[ok, None] * base_grad[ok]
+    ref = np.concatenate([gx.sum(axis=0), np.cross(x[ok] - c, gx).sum(axis=0)])
+    # device: backward with dL/dsdf = 2 sdf on the same points, pose gradient about the origin
+    xd = torch.from_numpy(xw).to(dev)
+    sdf, valid = m.query(xd)
+    okd = torch.from_numpy(ok).to(dev)
+    g = torch.where(okd & valid, 2.0 * torch.nan_to_num(sdf), torch.zeros_like(sdf))
+    pg = P.pose_gradient(m, xd, g).cpu().numpy().astype(np.float64)
+    pg_c = np.concatenate([pg[:3], pg[3:] - np.cross(c, pg[:3])])
+    scale = float(np.abs(ref).max())
+    return {"points": int(len(sel)), "points_in_loss": int(ok.sum()), "blocks_copied": int(rb["found"].sum()),
+            "max_rel_err_vs_oracle_fp64": float(np.max(np.abs(pg_c - ref)) / scale),
+            "max_rel_err_vs_central_diff": float(np.max(np.abs(pg_c - fd)) / scale),
+            "oracle_analytic_vs_central_diff": float(np.max(np.abs(ref - fd)) / scale), "h": h,
+            "rotation_centre": "centroid of the sampled points"}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -579,6 +779,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "streams32":
         run_batch(args, rank, world, local_rank)
+    elif args.workload == "align1km":
+        run_align(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1 and args.impl == "ours":

@@ -11,6 +11,10 @@
 namespace stsdf {
 
 // g: position in voxel units relative to integer offset k (g_true = k + g).
+// The 8 corners lie in at most 2 blocks per axis.  The slots of those blocks
+// are found with every first hash probe in flight at once (a longer probe
+// sequence only for a key not at its home slot), then all 8 voxels are read
+// at once: three dependent memory steps per query.
 __device__ __forceinline__ bool trilinear(const MapDev &md, const int k[3], const float g[3], float &D,
                                           float dg[3]) {
     int v0[3];
@@ -21,29 +25,48 @@ __device__ __forceinline__ bool trilinear(const MapDev &md, const int k[3], cons
         v0[a] = (int)fl + k[a];
         f[a] = g[a] - fl;
     }
-    uint64_t ck[8];
-    int cs[8];
-    int nc = 0;
-    float Dc[8];
+    // block coordinates of the lower / upper corner along each axis
+    const int b0[3] = {v0[0] >> 3, v0[1] >> 3, v0[2] >> 3};
+    const int b1[3] = {(v0[0] + 1) >> 3, (v0[1] + 1) >> 3, (v0[2] + 1) >> 3};
+    // block j = (jx, jy, jz) in {0,1}^3, needed only where the axis crosses
+    uint64_t key[8];
+    uint64_t hh[8];
+    uint64_t first[8];
+    bool need[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int jx = j & 1, jy = (j >> 1) & 1, jz = j >> 2;
+        need[j] = (!jx || b1[0] != b0[0]) && (!jy || b1[1] != b0[1]) && (!jz || b1[2] != b0[2]);
+        key[j] = pack_block(jx ? b1[0] : b0[0], jy ? b1[1] : b0[1], jz ? b1[2] : b0[2]);
+        hh[j] = fmix64(key[j]) & md.mask;
+        first[j] = need[j] ? md.keys[hh[j]] : key[j];
+    }
+    int slot[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        int h = (int)hh[j];
+        if (need[j] && first[j] != key[j]) h = first[j] == EMPTY_KEY ? -1 : hash_find(md.keys, md.mask, key[j]);
+        slot[j] = need[j] ? (h < 0 ? -1 : md.vals[h]) : 0;
+    }
+    float2 dw[8];
+    bool ok = true;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int vx = v0[0] + (c & 1), vy = v0[1] + ((c >> 1) & 1), vz = v0[2] + (c >> 2);
-        const uint64_t key = pack_block(vx >> 3, vy >> 3, vz >> 3);
-        int slot = -2;
-        for (int j = 0; j < nc; ++j)
-            if (ck[j] == key) slot = cs[j];
-        if (slot == -2) {
-            const int h = hash_find(md.keys, md.mask, key);
-            slot = h < 0 ? -1 : md.vals[h];
-            ck[nc] = key;
-            cs[nc] = slot;
-            ++nc;
-        }
-        if (slot < 0) return false;
-        const long long vox = (long long)slot * BV + (vx & 7) + 8 * (vy & 7) + 64 * (vz & 7);
-        const float2 dw = md.storage == 0 ? md.dw32[vox] : __half22float2(md.dw16[vox]);
-        if (!(dw.y > 0.f)) return false;
-        Dc[c] = dw.x;
+        // block of this corner: index j with jx set only when the corner sits in the upper block
+        const int j = ((vx >> 3) != b0[0] ? 1 : 0) | ((vy >> 3) != b0[1] ? 2 : 0) | ((vz >> 3) != b0[2] ? 4 : 0);
+        const int sl = slot[j];
+        ok = ok && sl >= 0;
+        const long long vox = (long long)(sl < 0 ? 0 : sl) * BV + (vx & 7) + 8 * (vy & 7) + 64 * (vz & 7);
+        dw[c] = sl < 0 ? make_float2(0.f, 0.f)
+                       : (md.storage == 0 ? md.dw32[vox] : __half22float2(md.dw16[vox]));
+    }
+    if (!ok) return false;
+    float Dc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        if (!(dw[c].y > 0.f)) return false;
+        Dc[c] = dw[c].x;
     }
     float s = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
 #pragma unroll
@@ -132,15 +155,18 @@ __global__ void __launch_bounds__(256) k_query_bwd(MapDev md, const float *__res
     }
 }
 
-// Gauss-Newton accumulation: acc[0..20] upper triangle of H = sum J^T J,
-// acc[21..26] g = sum J^T D, acc[27] loss sum D^2, acc[28] valid count.
+// Gauss-Newton accumulation: per CTA b, acc[32 b + 0..20] upper triangle of
+// H = sum J^T J, acc[32 b + 21..26] g = sum J^T D, acc[32 b + 27] loss sum
+// D^2, acc[32 b + 28] valid count (plain stores, no atomics; k_gn_step sums
+// the CTAs' rows in a fixed order).
 constexpr int GN_ACC = 29;
+constexpr int GN_MAX_CTAS = 148 * 8;
 
 __global__ void __launch_bounds__(256) k_gn_terms(MapDev md, const float *__restrict__ pts, long long n,
                                                   const double *__restrict__ T, double *acc) {
     __shared__ float s_c[16];
     __shared__ int s_k[3];
-    __shared__ double s_tmp[8];
+    __shared__ float s_h[8][GN_ACC], s_l[8][GN_ACC];
     if (threadIdx.x == 0) {
         // R / nu and the split t / nu = k + f (k integer)
         for (int r = 0; r < 3; ++r) {
@@ -152,9 +178,11 @@ __global__ void __launch_bounds__(256) k_gn_terms(MapDev md, const float *__rest
         }
     }
     __syncthreads();
-    double a[GN_ACC];
+    // sums as unevaluated float pairs (products exact by TwoProd, sums by TwoSum):
+    // ~48-bit sums on the FP32 pipes (this GPU's FP64 rate is a small fraction)
+    float ah[GN_ACC], al[GN_ACC];
 #pragma unroll
-    for (int j = 0; j < GN_ACC; ++j) a[j] = 0.0;
+    for (int j = 0; j < GN_ACC; ++j) ah[j] = al[j] = 0.f;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float p0 = pts[3 * i], p1 = pts[3 * i + 1], p2 = pts[3 * i + 2];
         if (!(isfinite(p0) && isfinite(p1) && isfinite(p2))) continue;
@@ -170,81 +198,177 @@ __global__ void __launch_bounds__(256) k_gn_terms(MapDev md, const float *__rest
         for (int r = 0; r < 3; ++r) x[r] = md.nu * ((float)s_k[r] + g[r]);
         const float J[6] = {gr[0], gr[1], gr[2], x[1] * gr[2] - x[2] * gr[1], x[2] * gr[0] - x[0] * gr[2],
                             x[0] * gr[1] - x[1] * gr[0]};
+        float ph, pl;
         int q = 0;
 #pragma unroll
         for (int r = 0; r < 6; ++r)
 #pragma unroll
-            for (int c = r; c < 6; ++c) a[q++] += (double)J[r] * (double)J[c];
+            for (int c = r; c < 6; ++c) {
+                two_prod(J[r], J[c], ph, pl);
+                df_add(ah[q], al[q], ph, pl, ah[q], al[q]);
+                ++q;
+            }
 #pragma unroll
-        for (int r = 0; r < 6; ++r) a[21 + r] += (double)J[r] * (double)D;
-        a[27] += (double)D * (double)D;
-        a[28] += 1.0;
+        for (int r = 0; r < 6; ++r) {
+            two_prod(J[r], D, ph, pl);
+            df_add(ah[21 + r], al[21 + r], ph, pl, ah[21 + r], al[21 + r]);
+        }
+        two_prod(D, D, ph, pl);
+        df_add(ah[27], al[27], ph, pl, ah[27], al[27]);
+        df_add(ah[28], al[28], 1.f, 0.f, ah[28], al[28]);
     }
+    // warp sums, then the CTA's row of partial sums (as doubles)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int j = 0; j < GN_ACC; ++j) {
-        const double t = block_sum_d(a[j], s_tmp);
-        if (threadIdx.x == 0 && t != 0.0) atomicAdd(&acc[j], t);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float bh = __shfl_xor_sync(0xffffffffu, ah[j], o), bl = __shfl_xor_sync(0xffffffffu, al[j], o);
+            df_add(ah[j], al[j], bh, bl, ah[j], al[j]);
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < GN_ACC; ++j) {
+            s_h[wid][j] = ah[j];
+            s_l[wid][j] = al[j];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < GN_ACC) {
+        float th = 0.f, tl = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) df_add(th, tl, s_h[w][threadIdx.x], s_l[w][threadIdx.x], th, tl);
+        acc[32 * blockIdx.x + threadIdx.x] = (double)th + (double)tl;
     }
 }
 
-// One thread: solve (H + mu I) d = -g, T <- Exp(d) T, clear the accumulators.
-__global__ void k_gn_step(double *T, double *acc) {
-    double H[6][6], A[6][7];
-    int q = 0;
-    for (int r = 0; r < 6; ++r)
-        for (int c = r; c < 6; ++c) {
-            H[r][c] = acc[q];
-            H[c][r] = acc[q];
-            ++q;
-        }
-    double tr = 0.0;
-    for (int r = 0; r < 6; ++r) tr += H[r][r];
-    const double mu = 1e-6 * (tr / 6.0 + 1e-12);
-    for (int r = 0; r < 6; ++r) {
-        for (int c = 0; c < 6; ++c) A[r][c] = H[r][c] + (r == c ? mu : 0.0);
-        A[r][6] = -acc[21 + r];
+// Rodrigues coefficients A = sin(t)/t, B = (1 - cos(t))/t^2, C = (t - sin(t))/t^3
+// of the SE(3) exponential: their Taylor series in t^2 for t < 0.5 (terms to
+// t^16, truncation below 1e-17), the closed forms otherwise.
+__host__ __device__ constexpr double inv_factorial(int n) { return n <= 1 ? 1.0 : inv_factorial(n - 1) / (double)n; }
+struct RodriguesSeries {
+    double a[9], b[9], c[9];   // (-1)^k / (2k+1)!, (-1)^k / (2k+2)!, (-1)^k / (2k+3)!
+};
+__host__ __device__ constexpr RodriguesSeries rodrigues_series() {
+    RodriguesSeries r{};
+    for (int k = 0; k < 9; ++k) {
+        const double sg = (k & 1) ? -1.0 : 1.0;
+        r.a[k] = sg * inv_factorial(2 * k + 1);
+        r.b[k] = sg * inv_factorial(2 * k + 2);
+        r.c[k] = sg * inv_factorial(2 * k + 3);
     }
+    return r;
+}
+__device__ __forceinline__ void rodrigues_coeffs(double th2, double &A1, double &B1, double &C1) {
+    constexpr RodriguesSeries S = rodrigues_series();
+    if (th2 < 0.25) {
+        // Horner in t^2
+        A1 = S.a[8];
+        B1 = S.b[8];
+        C1 = S.c[8];
+#pragma unroll
+        for (int k = 7; k >= 0; --k) {
+            A1 = fma(A1, th2, S.a[k]);
+            B1 = fma(B1, th2, S.b[k]);
+            C1 = fma(C1, th2, S.c[k]);
+        }
+    } else {
+        const double th = sqrt(th2);
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        A1 = sn / th;
+        B1 = (1.0 - cs) / th2;
+        C1 = (th - sn) / (th2 * th);
+    }
+}
+
+// One CTA: sum the per-CTA rows (fixed order), then one thread solves
+// (H + mu I) d = -g (Cholesky; H is a sum of outer products plus mu I) and
+// applies T <- Exp(d) T.
+__global__ void __launch_bounds__(256) k_gn_step(double *T, const double *acc, int nparts) {
+    __shared__ double s_p[8][32];
+    __shared__ double s_a[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane < GN_ACC) {
+        // rows wid, wid + 8, ... in order; eight loads in flight per step
+        double t = 0.0;
+        for (int b0 = wid; b0 < nparts; b0 += 64) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = b0 + 8 * u < nparts ? acc[32 * (b0 + 8 * u) + lane] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) t += v[u];
+        }
+        s_p[wid][lane] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < GN_ACC) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += s_p[w][threadIdx.x];
+        s_a[threadIdx.x] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double *a = s_a;
+    // H = sum J^T J (upper triangle, row-major in a[0..20]) + mu I, solved by a
+    // Cholesky factorisation held in registers (every index a compile-time constant)
+    double Hm[6][6];
+    {
+        int q = 0;
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+            for (int c = r; c < 6; ++c) {
+                Hm[r][c] = a[q];
+                Hm[c][r] = a[q];
+                ++q;
+            }
+    }
+    double tr = 0.0;
+#pragma unroll
+    for (int r = 0; r < 6; ++r) tr += Hm[r][r];
+    const double mu = 1e-6 * (tr / 6.0 + 1e-12);
+    double Lc[6][6], inv_diag[6];
     bool ok = true;
-    for (int c = 0; c < 6 && ok; ++c) {
-        int piv = c;
-        for (int r = c + 1; r < 6; ++r)
-            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
-        for (int k = 0; k < 7; ++k) {
-            const double t = A[c][k];
-            A[c][k] = A[piv][k];
-            A[piv][k] = t;
-        }
-        if (A[c][c] == 0.0) {
-            ok = false;
-            break;
-        }
-        for (int r = c + 1; r < 6; ++r) {
-            const double f = A[r][c] / A[c][c];
-            for (int k = c; k < 7; ++k) A[r][k] -= f * A[c][k];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            double sum = Hm[i][j] + (i == j ? mu : 0.0);
+#pragma unroll
+            for (int k = 0; k < j; ++k) sum -= Lc[i][k] * Lc[j][k];
+            if (i == j) {
+                ok = ok && sum > 0.0;
+                Lc[i][i] = sqrt(sum > 0.0 ? sum : 1.0);
+                inv_diag[i] = 1.0 / Lc[i][i];
+            } else {
+                Lc[i][j] = sum * inv_diag[j];
+            }
         }
     }
     double d[6] = {0, 0, 0, 0, 0, 0};
     if (ok) {
-        for (int c = 5; c >= 0; --c) {
-            double s = A[c][6];
-            for (int k = c + 1; k < 6; ++k) s -= A[c][k] * d[k];
-            d[c] = s / A[c][c];
+        double y[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            double sum = -a[21 + i];
+#pragma unroll
+            for (int k = 0; k < i; ++k) sum -= Lc[i][k] * y[k];
+            y[i] = sum * inv_diag[i];
+        }
+#pragma unroll
+        for (int i = 5; i >= 0; --i) {
+            double sum = y[i];
+#pragma unroll
+            for (int k = i + 1; k < 6; ++k) sum -= Lc[k][i] * d[k];
+            d[i] = sum * inv_diag[i];
         }
     }
     // Exp(rho, phi): Rodrigues rotation, translation V(phi) rho
     const double *rho = d, *phi = d + 3;
     const double th2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2];
-    const double th = sqrt(th2);
     double A1, B1, C1;
-    if (th < 1e-8) {
-        A1 = 1.0 - th2 / 6.0;
-        B1 = 0.5 - th2 / 24.0;
-        C1 = 1.0 / 6.0 - th2 / 120.0;
-    } else {
-        A1 = sin(th) / th;
-        B1 = (1.0 - cos(th)) / th2;
-        C1 = (th - sin(th)) / (th2 * th);
-    }
+    rodrigues_coeffs(th2, A1, B1, C1);
     const double K[3][3] = {{0, -phi[2], phi[1]}, {phi[2], 0, -phi[0]}, {-phi[1], phi[0], 0}};
     double K2[3][3], R[3][3], V[3][3];
     for (int i = 0; i < 3; ++i)
@@ -266,7 +390,6 @@ __global__ void k_gn_step(double *T, double *acc) {
                         V[r][2] * rho[2];
     }
     for (int r = 0; r < 12; ++r) T[r] = Tn[r];
-    for (int j = 0; j < GN_ACC; ++j) acc[j] = 0.0;
 }
 
 void launch_query(const MapDev &md, const float *xyz, long long m, float *sdf, uint8_t *valid, cudaStream_t s) {
@@ -276,13 +399,18 @@ void launch_query_bwd(const MapDev &md, const float *xyz, const float *gsdf, lon
                       double *pose_grad, cudaStream_t s) {
     if (m > 0) k_query_bwd<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(md, xyz, gsdf, m, gxyz, pose_grad);
 }
+int gn_terms_grid(long long n) {
+    long long grid = (n + 255) / 256;
+    if (grid > GN_MAX_CTAS) grid = GN_MAX_CTAS;
+    if (grid < 1) grid = 1;
+    return (int)grid;
+}
 void launch_gn_terms(const MapDev &md, const float *pts, long long n, const double *T_dev, double *acc,
                      cudaStream_t s) {
-    long long grid = (n + 255) / 256;
-    if (grid > 148 * 8) grid = 148 * 8;
-    if (grid < 1) grid = 1;
-    k_gn_terms<<<(unsigned)grid, 256, 0, s>>>(md, pts, n, T_dev, acc);
+    k_gn_terms<<<gn_terms_grid(n), 256, 0, s>>>(md, pts, n, T_dev, acc);
 }
-void launch_gn_step(double *T_dev, double *acc, cudaStream_t s) { k_gn_step<<<1, 1, 0, s>>>(T_dev, acc); }
+void launch_gn_step(double *T_dev, const double *acc, int nparts, cudaStream_t s) {
+    k_gn_step<<<1, 256, 0, s>>>(T_dev, acc, nparts);
+}
 
 }  // namespace stsdf

@@ -44,6 +44,9 @@ void launch_query_bwd(const MapDev &md, const float *xyz, const float *gsdf, lon
                       double *pose_grad, cudaStream_t s);
 void launch_gn_terms(const MapDev &md, const float *pts, long long n, const double *T_dev, double *acc,
                      cudaStream_t s);
-void launch_gn_step(double *T_dev, double *acc, cudaStream_t s);
+constexpr int GN_ACC_STRIDE = 32;             // doubles per CTA row of Gauss-Newton partial sums
+constexpr int GN_ACC_ROWS = 148 * 8;          // most CTAs of k_gn_terms
+int gn_terms_grid(long long n);
+void launch_gn_step(double *T_dev, const double *acc, int nparts, cudaStream_t s);
 
 }  // namespace stsdf

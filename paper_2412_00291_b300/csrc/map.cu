@@ -230,7 +230,7 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     ALLOC(m->gb.bsum_t, m->nchunks);
     ALLOC(m->gb.totals, 2);
     ALLOC(m->gn_T, 16);
-    ALLOC(m->gn_acc, 32);
+    ALLOC(m->gn_acc, (size_t)GN_ACC_ROWS * GN_ACC_STRIDE);
     ALLOC(m->pal_dev, 256);
 #undef ALLOC
     if (cudaMallocHost(&m->h_ctr, CT_COUNT * sizeof(unsigned long long)) != cudaSuccess ||
@@ -266,7 +266,6 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
         cudaMemcpy(m->st, &init, sizeof(init), cudaMemcpyHostToDevice);
     }
     cudaMemsetAsync(fd.ctr, 0, CT_COUNT * sizeof(unsigned long long), s);
-    cudaMemsetAsync(m->gn_acc, 0, 32 * sizeof(double), s);
     launch_init_pool(md, s);
     // tables
     std::vector<int8_t> tri(256 * MAP_MC_MAXTRI * 3);
@@ -629,10 +628,10 @@ extern "C" map_status map_align_scan(map_t *m, const float *points_dev, int64_t 
         return fail(m, MAP_ERR_ARG, "bad alignment arguments");
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaMemcpyAsync(m->gn_T, T0, 16 * sizeof(double), cudaMemcpyHostToDevice, s));
-    CU(cudaMemsetAsync(m->gn_acc, 0, 32 * sizeof(double), s));
+    const int parts = gn_terms_grid(n);
     for (int it = 0; it < iters; ++it) {
         launch_gn_terms(m->md, points_dev, n, m->gn_T, m->gn_acc, s);
-        launch_gn_step(m->gn_T, m->gn_acc, s);
+        launch_gn_step(m->gn_T, m->gn_acc, parts, s);
     }
     map_status st = launch_check(m, "map_align_scan");
     if (st != MAP_OK) return st;

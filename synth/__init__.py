@@ -232,6 +232,15 @@ def loop64() -> Workload:
                     0.1, 0.3, 20, "probs", "loop", 2, n_prims=2000, extent=200.0)
 
 
+def drive1km(seed: int = 5) -> Workload:
+    """Large map for scan-to-map alignment: the 64 x 2048 scanner (+-22.5 deg, 100 m, sigma 3 cm)
+    on a gently winding 960 m drive through a seeded 1 km x 1 km scene of 50,000 boxes/cylinders
+    (the density of the 200 m loop scene) and 1,000 sloped patches; 480 poses 2 m apart, hard
+    labels, 0.1 m voxels, 0.3 m truncation."""
+    return Workload("scan64x2048_drive1km_v0.1", lidar_deg(64, 2048, 22.5, -22.5, 100.0), 0.03, 480,
+                    0.1, 0.3, 20, "hard", "drive", seed, n_prims=50000, extent=1000.0)
+
+
 def streams32(seed: int = 3, n_streams: int = 32) -> list[Workload]:
     """Independent map streams of uneven size for the batched form (50 frames of each are used).
 
