@@ -188,16 +188,19 @@ def measured_peaks():
 
 
 def traffic_record(kernel):
-    """Per-launch DRAM bytes from the committed ncu summary, if it matches the current source."""
+    """Per-launch DRAM bytes from the committed ncu summary, if it matches the current source
+    (the kernel's file and the shared per-item bodies)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     rec = json.load(open(p)).get(kernel)
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_2412_00291_b300", "csrc", KERNEL_FILES.get(kernel, ""))
-    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec.get("source_sha"):
-        return None
+    csrc = os.path.join(ROOT, "paper_2412_00291_b300", "csrc")
+    for f, key in ((KERNEL_FILES.get(kernel, ""), "source_sha"), ("frame_bodies.cuh", "bodies_sha")):
+        src = os.path.join(csrc, f)
+        if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec.get(key):
+            return None   # the kernel changed since the counters were taken
     return rec
 
 
