@@ -12,7 +12,6 @@ struct BatchItem {
     ScanConst sc;
     MapDev md;
     FrameDev fd;
-    const uchar4 *pal;
 };
 
 // Grid barrier and status of one batch launch (zeroed before each launch).

@@ -121,11 +121,12 @@ struct MapDev {
     __half *lp16;
     int CP;              // record stride in elements: C rounded up to whole 32-byte sectors
     uint8_t *label;      // [slot][512] most probable class
+    const uchar4 *pal;   // [256] class colours (rgb)
     uint64_t *slot_key;  // [slot] block key owning the pool slot
     int *slot_frame;     // [slot] frame in which the slot was allocated
     int *nbr;            // [slot][16] slots of the blocks b + e_o (o = 1..7) and b - e_o (8 + o), -1 if none
     int4 *seg;           // [slot] mesh segment: vertex offset, count, triangle offset, count
-    float4 *av;          // mesh arena: vertex {x, y, z, rgb|label bits}
+    float4 *av;          // mesh arena: vertex {x, y, z, bits of its source pool voxel (class at extraction)}
     int64_t *ak;         // mesh arena: vertex edge keys
     ushort4 *at;         // mesh arena: triangle {i0, i1, i2, cube anchor (local)}
     long long av_cap, at_cap;

@@ -431,7 +431,10 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
 // one voxel per thread: logP_c += log L_c, renormalise by logsumexp, floor,
 // and refresh the voxel's argmax label.  A voxel's classes form one record of
 // whole 32-byte sectors (FP32: 24 floats, FP16: 32 halves for 20 classes),
-// read and written with vector accesses, padding included.
+// read and written with vector accesses, padding included.  The logarithms
+// and exponentials use the MUFU approximations (__logf, __expf): their error,
+// ~1e-6 per term, is two orders below the class log-probability tolerance of
+// the oracle comparison (1e-4 sqrt(K) + 1e-5 after K scans).
 template <bool F16, int NC>
 __device__ __forceinline__ void load_record(const MapDev &md, long long vox, float *av) {
     if (F16) {
@@ -512,14 +515,14 @@ __device__ __forceinline__ void semantic_item(const ScanConst &sc, const MapDev 
 #pragma unroll
                 for (int cc = 0; cc < (NC > 0 ? NC : 1); cc += 4) {
                     const float4 v = *reinterpret_cast<const float4 *>(q + cc);
-                    av[cc] += logf(fmaxf(v.x, sc.lik_floor));
-                    av[cc + 1] += logf(fmaxf(v.y, sc.lik_floor));
-                    av[cc + 2] += logf(fmaxf(v.z, sc.lik_floor));
-                    av[cc + 3] += logf(fmaxf(v.w, sc.lik_floor));
+                    av[cc] += __logf(fmaxf(v.x, sc.lik_floor));
+                    av[cc + 1] += __logf(fmaxf(v.y, sc.lik_floor));
+                    av[cc + 2] += __logf(fmaxf(v.z, sc.lik_floor));
+                    av[cc + 3] += __logf(fmaxf(v.w, sc.lik_floor));
                 }
             } else {
 #pragma unroll
-                for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) av[cc] += logf(fmaxf(q[cc], sc.lik_floor));
+                for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) av[cc] += __logf(fmaxf(q[cc], sc.lik_floor));
             }
         } else {
             const int l = sc.labels[idx];
@@ -530,8 +533,8 @@ __device__ __forceinline__ void semantic_item(const ScanConst &sc, const MapDev 
         for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) m = fmaxf(m, av[cc]);
         float ssum = 0.f;
 #pragma unroll
-        for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) ssum += expf(av[cc] - m);
-        const float lse = m + logf(ssum);
+        for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) ssum += __expf(av[cc] - m);
+        const float lse = m + __logf(ssum);
         int best = 0;
         float bv = -INFINITY;
 #pragma unroll
@@ -550,13 +553,13 @@ __device__ __forceinline__ void semantic_item(const ScanConst &sc, const MapDev 
         const float *q = sc.probs + idx * C;
         const int l = sc.has_probs ? -1 : sc.labels[idx];
         for (int cc = 0; cc < C; ++cc) {
-            const float lik = sc.has_probs ? logf(fmaxf(q[cc], sc.lik_floor)) : (cc == l ? sc.log_phit : sc.log_pmiss);
+            const float lik = sc.has_probs ? __logf(fmaxf(q[cc], sc.lik_floor)) : (cc == l ? sc.log_phit : sc.log_pmiss);
             av[cc] = load_lp<F16>(md, lp_index(md, vox, cc)) + lik;
             m = fmaxf(m, av[cc]);
         }
         float ssum = 0.f;
-        for (int cc = 0; cc < C; ++cc) ssum += expf(av[cc] - m);
-        const float lse = m + logf(ssum);
+        for (int cc = 0; cc < C; ++cc) ssum += __expf(av[cc] - m);
+        const float lse = m + __logf(ssum);
         int best = 0;
         float bv = -INFINITY;
         for (int cc = 0; cc < C; ++cc) {
@@ -586,16 +589,14 @@ struct MeshWarpSmem {
     uint8_t okc[64];      // per cube row: cubes whose eight corners are observed (bit = ax)
     int nb[8];            // slots of this block (0) and its 7 upper neighbours, -1 if none
     union {
-        uint8_t F[729];   // while staging: bit 0 observed (W > 0), bit 1 D < 0
+        uint4 F4[81];     // while staging: per voxel row, 16 bytes, byte x: bit 0 observed (W > 0), bit 1 D < 0
         uint16_t mc[512]; // then: the cubes that emit triangles (ax + 8 (ay + 8 az)), in order
     } u;
-    uint8_t lab[729];
 };
 
 struct MeshCtaSmem {
     int8_t tri[256 * MC_MAXTRI * 3];
     uint8_t ntri[256];
-    uchar4 pal[256];
     MeshWarpSmem w[MESH_WARPS];
 };
 
@@ -664,7 +665,7 @@ __device__ __forceinline__ int cube_edge_vertex(const MeshWarpSmem &W, int ce, i
 // bit operations on the row masks; vertices and emitting cubes are then
 // numbered by prefix counts and emitted one per lane.
 __device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev &fd, const int8_t *__restrict__ tri,
-                                                const uint8_t *__restrict__ ntri, const uchar4 *__restrict__ pal,
+                                                const uint8_t *__restrict__ ntri,
                                                 MeshWarpSmem &W, int slot, int part, long long &n_v, long long &n_t) {
     const int lane = threadIdx.x & 31;
     const bool f32 = md.storage == 0;
@@ -680,8 +681,7 @@ __device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev
         const float2 dw = f32 ? md.dw32[vox] : __half22float2(md.dw16[vox]);
         const int f = (dw.y > 0.f ? 1 : 0) | (dw.x < 0.f ? 2 : 0);
         W.D[r] = dw.x;
-        W.u.F[r] = (uint8_t)f;
-        W.lab[r] = md.label[vox];
+        reinterpret_cast<uint8_t *>(W.u.F4)[(v & 7) + 16 * (((v >> 3) & 7) + 9 * (v >> 6))] = (uint8_t)f;
         if (f & 1) seen |= (f & 2) ? 1 : 2;
     }
     __syncwarp();
@@ -692,18 +692,15 @@ __device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev
         const int s = W.nb[nbi];
         float D = 0.f;
         int f = 0;
-        uint8_t lab = 0;
         if (s >= 0) {
             const int x = r % 9, y = (r / 9) % 9, z = r / 81;
             const long long vox = (long long)s * BV + (x & 7) + 8 * (y & 7) + 64 * (z & 7);
             const float2 dw = f32 ? md.dw32[vox] : __half22float2(md.dw16[vox]);
             D = dw.x;
             f = (dw.y > 0.f ? 1 : 0) | (dw.x < 0.f ? 2 : 0);
-            lab = md.label[vox];
         }
         W.D[r] = D;
-        W.u.F[r] = (uint8_t)f;
-        W.lab[r] = lab;
+        reinterpret_cast<uint8_t *>(W.u.F4)[r % 9 + 16 * (r / 9)] = (uint8_t)f;
         if (f & 1) seen |= (f & 2) ? 1 : 2;
     }
     const bool any_neg = __any_sync(0xffffffffu, seen & 1), any_pos = __any_sync(0xffffffffu, seen & 2);
@@ -711,14 +708,16 @@ __device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev
     if (any_neg && any_pos) {
         __syncwarp();
         // row masks of the 81 voxel rows
+        // (bit 0, resp. 1, of four bytes gathered into 4 bits by one multiply: the
+        // products b_i 2^(8i) 2^(24-7k) land on bit 24 + i for i = k, below bit 20
+        // for i < k without overlapping, and beyond bit 31 for i > k)
         for (int rw = lane; rw < 81; rw += 32) {
-            uint32_t m = 0;
-#pragma unroll
-            for (int x = 0; x < 9; ++x) {
-                const uint32_t f = W.u.F[x + 9 * rw];
-                m |= ((f & 1u) << x) | (((f >> 1) & 1u) << (16 + x));
-            }
-            W.rowm[rw] = m;
+            const uint4 q = W.u.F4[rw];
+            const uint32_t ob = (((q.x & 0x01010101u) * 0x01020408u) >> 24) |
+                                ((((q.y & 0x01010101u) * 0x01020408u) >> 24) << 4) | ((q.z & 1u) << 8);
+            const uint32_t ng = ((((q.x >> 1) & 0x01010101u) * 0x01020408u) >> 24) |
+                                (((((q.y >> 1) & 0x01010101u) * 0x01020408u) >> 24) << 4) | (((q.z >> 1) & 1u) << 8);
+            W.rowm[rw] = ob | (ng << 16);
         }
         __syncwarp();
         // cube rows 2 lane and 2 lane + 1: observed cubes, and the emitting ones among them
@@ -835,11 +834,16 @@ __device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev
             if (axis == 0) px = md.nu * ((float)gx + t);
             else if (axis == 1) py = md.nu * ((float)gy + t);
             else pz = md.nu * ((float)gz + t);
-            // label of the endpoint nearer the surface (lower endpoint on ties)
-            const int lab = fabsf(D1) < fabsf(D0) ? W.lab[r1] : W.lab[r0];
-            const uchar4 col = pal[lab];
-            const unsigned packed = (unsigned)col.x | ((unsigned)col.y << 8) | ((unsigned)col.z << 16) |
-                                    ((unsigned)lab << 24);
+            // the endpoint nearer the surface (lower endpoint on ties) gives the
+            // vertex its class: its pool voxel index is stored, and the label
+            // (and colour) are read when the mesh is extracted.  That is the label
+            // after this scan's class update: a voxel's label changes only in a
+            // scan that also re-meshes every block reading it.
+            const int re = fabsf(D1) < fabsf(D0) ? r1 : r0;
+            const int ex = re % 9, ey = (re / 9) % 9, ez = re / 81;
+            const int es = W.nb[(ex >> 3) | ((ey >> 3) << 1) | ((ez >> 3) << 2)];
+            const unsigned packed =
+                es >= 0 ? (unsigned)es * BV + (ex & 7) + 8 * (ey & 7) + 64 * (ez & 7) : 0xffffffffu;
             md.av[vo + vid] = make_float4(px, py, pz, __uint_as_float(packed));
             md.ak[vo + vid] = edge_key(gx, gy, gz, axis);
         }

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch(const __grid_c
         const int i = find_map(S.pre, n, e);
         const BatchItem &it = a.it[i];
         long long n_v = 0, n_t = 0;
-        mesh_block_warp(it.md, it.fd, S.u.mesh.tri, S.u.mesh.ntri, it.pal, S.u.mesh.w[wid], it.fd.dirty[e - S.pre[i]],
+        mesh_block_warp(it.md, it.fd, S.u.mesh.tri, S.u.mesh.ntri, S.u.mesh.w[wid], it.fd.dirty[e - S.pre[i]],
                         part, n_v, n_t);
         if (lane == 0) {
             if (n_v) atomicAdd(&it.fd.ctr[CT_MV], (unsigned long long)n_v);

@@ -22,15 +22,11 @@ static int8_t *h_tri_dev = nullptr;      // [256][MC_MAXTRI][3] cube-edge ids
 static uint8_t *h_ntri_dev = nullptr;    // [256] triangles per case
 
 __global__ void __launch_bounds__(32 * MESH_WARPS) k_mesh(MapDev md, FrameDev fd, const int8_t *__restrict__ ttri,
-                                                           const uint8_t *__restrict__ tntri,
-                                                           const uchar4 *__restrict__ tpal) {
+                                                           const uint8_t *__restrict__ tntri) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MeshCtaSmem &S = *reinterpret_cast<MeshCtaSmem *>(smem_raw);
     for (int i = threadIdx.x; i < 256 * MC_MAXTRI * 3; i += blockDim.x) S.tri[i] = ttri[i];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
-        S.ntri[i] = tntri[i];
-        S.pal[i] = tpal[i];
-    }
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) S.ntri[i] = tntri[i];
     __syncthreads();
     const int wid = threadIdx.x >> 5;
     unsigned long long nd = *(volatile unsigned long long *)&fd.ctr[CT_DIRTY];
@@ -39,7 +35,7 @@ __global__ void __launch_bounds__(32 * MESH_WARPS) k_mesh(MapDev md, FrameDev fd
     const int part = (int)((blockIdx.x * MESH_WARPS + wid) % ARENA_PARTS);
     long long n_v = 0, n_t = 0;
     for (long long li = (long long)blockIdx.x * MESH_WARPS + wid; li < (long long)nd; li += nwarps)
-        mesh_block_warp(md, fd, S.tri, S.ntri, S.pal, S.w[wid], fd.dirty[li], part, n_v, n_t);
+        mesh_block_warp(md, fd, S.tri, S.ntri, S.w[wid], fd.dirty[li], part, n_v, n_t);
     long long cnt[2] = {n_v, n_t};
     cta_count<2>(fd.ctr, {CT_MV, CT_MT}, cnt);
 }
@@ -65,8 +61,8 @@ int mesh_blocks_per_sm() {
     return n > 0 ? n : 1;
 }
 
-void launch_mesh(const MapDev &md, const FrameDev &fd, const uchar4 *palette, int grid, cudaStream_t s) {
-    k_mesh<<<grid, 32 * MESH_WARPS, sizeof(MeshCtaSmem), s>>>(md, fd, h_tri_dev, h_ntri_dev, palette);
+void launch_mesh(const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s) {
+    k_mesh<<<grid, 32 * MESH_WARPS, sizeof(MeshCtaSmem), s>>>(md, fd, h_tri_dev, h_ntri_dev);
 }
 
 // ---------------------------------------------------------------------------
@@ -180,14 +176,17 @@ __global__ void __launch_bounds__(256) k_seg_gather(MapDev md, GatherBufs g, int
             if (sg.w > 0) unpack_block(md.slot_key[s], bx, by, bz);
             for (int i = lane; i < sg.y; i += 32) {
                 const float4 v = md.av[sg.x + i];
-                const unsigned pk = __float_as_uint(v.w);
+                // class of the vertex's source voxel, and its palette colour
+                const unsigned src = __float_as_uint(v.w);
+                const int lab = src == 0xffffffffu ? 0 : md.label[src];
+                const uchar4 c = md.pal[lab];
                 pos[3 * (ov + i)] = v.x;
                 pos[3 * (ov + i) + 1] = v.y;
                 pos[3 * (ov + i) + 2] = v.z;
-                col[4 * (ov + i)] = pk & 0xff;
-                col[4 * (ov + i) + 1] = (pk >> 8) & 0xff;
-                col[4 * (ov + i) + 2] = (pk >> 16) & 0xff;
-                col[4 * (ov + i) + 3] = (pk >> 24) & 0xff;
+                col[4 * (ov + i)] = c.x;
+                col[4 * (ov + i) + 1] = c.y;
+                col[4 * (ov + i) + 2] = c.z;
+                col[4 * (ov + i) + 3] = (uint8_t)lab;
                 keys[ov + i] = md.ak[sg.x + i];
             }
             for (int i = lane; i < sg.w; i += 32) {

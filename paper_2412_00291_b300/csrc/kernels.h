@@ -24,7 +24,7 @@ int semantic_blocks_per_sm(int storage, int C);
 
 // k_mesh.cu: incremental marching cubes and mesh gathering
 int mesh_upload_tables(const int8_t *tri, const uint8_t *ntri);
-void launch_mesh(const MapDev &md, const FrameDev &fd, const uchar4 *palette, int grid, cudaStream_t s);
+void launch_mesh(const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s);
 int mesh_blocks_per_sm();
 struct GatherBufs {
     long long *voff, *toff;          // [max_blocks] per-slot exclusive offsets within a chunk

@@ -232,6 +232,7 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     ALLOC(m->gn_T, 16);
     ALLOC(m->gn_acc, (size_t)GN_ACC_ROWS * GN_ACC_STRIDE);
     ALLOC(m->pal_dev, 256);
+    md.pal = m->pal_dev;
 #undef ALLOC
     if (cudaMallocHost(&m->h_ctr, CT_COUNT * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&m->h_st, sizeof(DevState)) != cudaSuccess ||
@@ -469,7 +470,7 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     if (ev) CU(cudaEventRecord(ev[3], s));
     launch_semantic(sc, m->md, m->fd, m->grid_semantic, s);
     if (ev) CU(cudaEventRecord(ev[4], s));
-    launch_mesh(m->md, m->fd, m->pal_dev, m->grid_mesh, s);
+    launch_mesh(m->md, m->fd, m->grid_mesh, s);
     if (ev) CU(cudaEventRecord(ev[5], s));
     m->launches += 4;
     if (ev_stats)
@@ -525,7 +526,7 @@ extern "C" map_status map_remesh_all(map_t *m, void *stream) {
     if (st != MAP_OK) return st;
     CU(cudaMemsetAsync(m->fd.ctr, 0, CT_COUNT * sizeof(unsigned long long), s));
     launch_list_all(m->md, m->fd, m->frame, s);
-    launch_mesh(m->md, m->fd, m->pal_dev, m->grid_mesh, s);
+    launch_mesh(m->md, m->fd, m->grid_mesh, s);
     m->launches += 2;
     st = launch_check(m, "map_remesh_all");
     if (st != MAP_OK) return st;
@@ -939,7 +940,6 @@ extern "C" map_status map_batch_integrate(map_batch_t *b, const scan_desc *scans
         it.sc.pts = d.points_dev;
         it.sc.labels = d.labels_dev;
         it.sc.probs = d.probs_dev;
-        it.pal = m->pal_dev;
     }
     args.n = n;
     args.ctl = b->ctl;
