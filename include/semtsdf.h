@@ -282,7 +282,10 @@ map_status map_write_blocks(map_t *map, const int32_t *coords_host, int64_t n, c
 
 /* ---- phase profiling (CUDA events on the caller's stream) ---- */
 
-/* Phases of one integrate_scan, in launch order (one kernel each, after the resets). */
+/* Phases of one integrate_scan, in launch order (one kernel each, after the resets).
+ * The class update and the re-meshing run concurrently (two streams, both
+ * after the TSDF kernel); each reports its own duration, so a scan takes
+ * less than the sum of its phases. */
 enum {
     MAP_PHASE_RESET = 0,      /* range-image and counter resets                               */
     MAP_PHASE_POINTS = 1,     /* per point: range-image winner (Sec. III-C.1), band allocation */

@@ -2,7 +2,7 @@
 // each of up to BATCH_MAX maps (uneven scan sizes, voxel sizes and storage).
 //
 // The kernel runs the per-frame phases back to back for all maps at once:
-//   reset -> points -> TSDF -> class update -> re-meshing,
+//   reset -> points -> TSDF -> class update and re-meshing together,
 // separated by a grid-wide barrier.  Inside a phase, a flattened work index
 // is mapped to (map, item) through prefix sums over the maps' item counts
 // (each map's range padded to a multiple of 32, so that warp-level votes
@@ -71,6 +71,7 @@ struct BatchSmem {
         } mesh;
     } u;
     long long pre[BATCH_MAX + 1];
+    long long pre2[BATCH_MAX + 1];
 };
 
 template <int WARPS, int VPT>
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch(const __grid_c
     // ---- reset: range-image winners and counters ------------------------------
     if (threadIdx.x == 0) {
         S.pre[0] = 0;
+        S.pre2[0] = 0;
         for (int i = 0; i < n; ++i) S.pre[i + 1] = S.pre[i] + (long long)a.it[i].sc.H * a.it[i].sc.W;
     }
     __syncthreads();
@@ -150,12 +152,17 @@ __global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch(const __grid_c
     }
     if (!grid_sync(ctl, limit, gen)) return;
 
-    // ---- class update: one thread per listed voxel -----------------------------
+    // ---- class update and re-meshing (independent: the mesh reads no labels) --
+    for (int k = threadIdx.x; k < 256 * MC_MAXTRI * 3; k += blockDim.x) S.u.mesh.tri[k] = a.tri[k];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) S.u.mesh.ntri[k] = a.ntri[k];
     if (threadIdx.x == 0) {
         for (int i = 0; i < n; ++i) {
             unsigned long long t = *(volatile unsigned long long *)&a.it[i].fd.ctr[CT_SEM];
             if (t > (unsigned long long)a.it[i].fd.sem_cap) t = a.it[i].fd.sem_cap;
             S.pre[i + 1] = S.pre[i] + (long long)t;
+            t = *(volatile unsigned long long *)&a.it[i].fd.ctr[CT_DIRTY];
+            if (t > (unsigned long long)a.it[i].md.max_blocks) t = a.it[i].md.max_blocks;
+            S.pre2[i + 1] = S.pre2[i] + (long long)t;
         }
     }
     __syncthreads();
@@ -176,26 +183,13 @@ __global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch(const __grid_c
             }
         }
     }
-    if (!grid_sync(ctl, limit, gen)) return;
-
-    // ---- re-meshing: one warp per queued block --------------------------------
-    for (int k = threadIdx.x; k < 256 * MC_MAXTRI * 3; k += blockDim.x) S.u.mesh.tri[k] = a.tri[k];
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) S.u.mesh.ntri[k] = a.ntri[k];
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < n; ++i) {
-            unsigned long long t = *(volatile unsigned long long *)&a.it[i].fd.ctr[CT_DIRTY];
-            if (t > (unsigned long long)a.it[i].md.max_blocks) t = a.it[i].md.max_blocks;
-            S.pre[i + 1] = S.pre[i] + (long long)t;
-        }
-    }
-    __syncthreads();
     const int part = (int)(gwarp % ARENA_PARTS);
-    for (long long e = gwarp; e < S.pre[n]; e += nwarps) {
-        const int i = find_map(S.pre, n, e);
+    for (long long e = gwarp; e < S.pre2[n]; e += nwarps) {
+        const int i = find_map(S.pre2, n, e);
         const BatchItem &it = a.it[i];
         long long n_v = 0, n_t = 0;
-        mesh_block_warp(it.md, it.fd, S.u.mesh.tri, S.u.mesh.ntri, S.u.mesh.w[wid], it.fd.dirty[e - S.pre[i]],
-                        part, n_v, n_t);
+        mesh_block_warp(it.md, it.fd, S.u.mesh.tri, S.u.mesh.ntri, S.u.mesh.w[wid], it.fd.dirty[e - S.pre2[i]], part,
+                        n_v, n_t);
         if (lane == 0) {
             if (n_v) atomicAdd(&it.fd.ctr[CT_MV], (unsigned long long)n_v);
             if (n_t) atomicAdd(&it.fd.ctr[CT_MT], (unsigned long long)n_t);

@@ -36,6 +36,10 @@ struct map_t {
     static constexpr int RING = 8;
     DevState *h_ring = nullptr;
     cudaEvent_t ev_ring[RING] = {};
+    // the class update runs on a second stream beside the re-meshing (the mesh
+    // does not read class labels); fork after the TSDF kernel, join before return
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     long long ring_frame[RING] = {};
     int ring_epoch[RING] = {};
     int epoch = 0;                  // bumped by every compaction
@@ -133,6 +137,9 @@ static void free_all(map_t *m) {
     if (m->h_ring) cudaFreeHost(m->h_ring);
     for (auto &e : m->ev_ring)
         if (e) cudaEventDestroy(e);
+    if (m->ev_fork) cudaEventDestroy(m->ev_fork);
+    if (m->ev_join) cudaEventDestroy(m->ev_join);
+    if (m->side) cudaStreamDestroy(m->side);
 }
 
 template <typename T>
@@ -246,6 +253,13 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     std::memset(m->h_st, 0, sizeof(DevState));
     std::memset(m->h_ring, 0, map_t::RING * sizeof(DevState));
     for (auto &e : m->ev_ring) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        free_all(m);
+        delete m;
+        return fail(nullptr, MAP_ERR_CUDA, "stream / event creation failed");
+    }
     for (int i = 0; i < map_t::RING; ++i) m->ring_frame[i] = -1;
 
     cudaStream_t s = 0;
@@ -468,10 +482,15 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     if (ev) CU(cudaEventRecord(ev[2], s));
     launch_integrate(sc, m->md, m->fd, m->grid_integrate, s);
     if (ev) CU(cudaEventRecord(ev[3], s));
-    launch_semantic(sc, m->md, m->fd, m->grid_semantic, s);
-    if (ev) CU(cudaEventRecord(ev[4], s));
+    // class update on the side stream, re-meshing on the caller's, concurrently
+    CU(cudaEventRecord(m->ev_fork, s));
+    CU(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
+    launch_semantic(sc, m->md, m->fd, m->grid_semantic, m->side);
+    if (ev) CU(cudaEventRecord(ev[4], m->side));
     launch_mesh(m->md, m->fd, m->grid_mesh, s);
     if (ev) CU(cudaEventRecord(ev[5], s));
+    CU(cudaEventRecord(m->ev_join, m->side));
+    CU(cudaStreamWaitEvent(s, m->ev_join, 0));
     m->launches += 4;
     if (ev_stats)
         CU(cudaMemcpyAsync(ev_stats, m->fd.ctr, CT_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
@@ -745,9 +764,12 @@ extern "C" map_status map_profile_end(map_t *m, float *ms_out, int64_t *stats_ou
     for (int f = 0; f < n; ++f) {
         cudaEvent_t *ev = &m->prof_ev[(size_t)f * (MAP_PHASE_COUNT + 1)];
         CU(cudaEventSynchronize(ev[MAP_PHASE_COUNT]));
+        CU(cudaEventSynchronize(ev[MAP_PHASE_SEMANTIC + 1]));
         for (int ph = 0; ph < MAP_PHASE_COUNT; ++ph) {
+            // the class update and the re-meshing both start at the end of the TSDF kernel
+            const int from = ph == MAP_PHASE_MESH ? MAP_PHASE_SEMANTIC : ph;
             float ms = 0.f;
-            CU(cudaEventElapsedTime(&ms, ev[ph], ev[ph + 1]));
+            CU(cudaEventElapsedTime(&ms, ev[from], ev[ph + 1]));
             if (ms_out) ms_out[(size_t)f * MAP_PHASE_COUNT + ph] = ms;
         }
     }
