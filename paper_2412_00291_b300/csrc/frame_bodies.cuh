@@ -600,22 +600,6 @@ struct MeshCtaSmem {
     MeshWarpSmem w[MESH_WARPS];
 };
 
-__device__ __forceinline__ int face_pos(int j, int &nbi) {
-    // the 217 voxels of the region outside the block: x = 8 face, then y = 8, then z = 8
-    int x, y, z;
-    if (j < 81) {
-        x = 8; y = j % 9; z = j / 9;
-    } else if (j < 153) {
-        const int k = j - 81;
-        x = k & 7; y = 8; z = k >> 3;
-    } else {
-        const int k = j - 153;
-        x = k & 7; y = k >> 3; z = 8;
-    }
-    nbi = (x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2);
-    return x + 9 * (y + 9 * z);
-}
-
 // Bit position of the k-th (from 0) set bit of w; requires k < popc(w).
 __device__ __forceinline__ int nth_set_bit(uint32_t w, int k) {
     int pos = 0, c = __popc(w & 0xffffu);
@@ -674,34 +658,59 @@ __device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev
     // slots of the 7 upper neighbours, from the per-slot links
     if (lane < 8) W.nb[lane] = lane == 0 ? slot : md.nbr[slot * 16 + lane];
     int seen = 0;   // bit 0: an observed voxel with D < 0, bit 1: one with D >= 0
-#pragma unroll 4
-    for (int v = lane; v < BV; v += 32) {
-        const int r = (v & 7) + 9 * (((v >> 3) & 7) + 9 * (v >> 6));
-        const long long vox = (long long)slot * BV + v;
-        const float2 dw = f32 ? md.dw32[vox] : __half22float2(md.dw16[vox]);
+    uint8_t *F = reinterpret_cast<uint8_t *>(W.u.F4);
+    // region voxel (x, y, z): D at x + 9 (y + 9 z), flags at x + 16 (y + 9 z)
+    auto put = [&](int r, int fi, float2 dw) {
         const int f = (dw.y > 0.f ? 1 : 0) | (dw.x < 0.f ? 2 : 0);
         W.D[r] = dw.x;
-        reinterpret_cast<uint8_t *>(W.u.F4)[(v & 7) + 16 * (((v >> 3) & 7) + 9 * (v >> 6))] = (uint8_t)f;
+        F[fi] = (uint8_t)f;
         if (f & 1) seen |= (f & 2) ? 1 : 2;
+    };
+    // the block's own 512 voxels, two neighbours along x per read (16 bytes FP32, 8 FP16)
+#pragma unroll 4
+    for (int p = lane; p < BV / 2; p += 32) {
+        const int v = 2 * p, row = v >> 3, x = v & 7;            // row = y + 8 z
+        const int yz9 = (row & 7) + 9 * (row >> 3);               // y + 9 z
+        float2 a, b;
+        if (f32) {
+            const float4 q = reinterpret_cast<const float4 *>(md.dw32)[((long long)slot * BV + v) >> 1];
+            a = make_float2(q.x, q.y);
+            b = make_float2(q.z, q.w);
+        } else {
+            const uint2 q = reinterpret_cast<const uint2 *>(md.dw16)[((long long)slot * BV + v) >> 1];
+            a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
+            b = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
+        }
+        put(x + 9 * yz9, x + 16 * yz9, a);
+        put(x + 1 + 9 * yz9, x + 1 + 16 * yz9, b);
     }
     __syncwarp();
-#pragma unroll 2
-    for (int j = lane; j < 217; j += 32) {
-        int nbi;
-        const int r = face_pos(j, nbi);
-        const int s = W.nb[nbi];
-        float D = 0.f;
-        int f = 0;
-        if (s >= 0) {
-            const int x = r % 9, y = (r / 9) % 9, z = r / 81;
-            const long long vox = (long long)s * BV + (x & 7) + 8 * (y & 7) + 64 * (z & 7);
-            const float2 dw = f32 ? md.dw32[vox] : __half22float2(md.dw16[vox]);
-            D = dw.x;
-            f = (dw.y > 0.f ? 1 : 0) | (dw.x < 0.f ? 2 : 0);
+    auto nb_dw = [&](int s, int local) -> float2 {
+        if (s < 0) return make_float2(0.f, 0.f);
+        const long long vox = (long long)s * BV + local;
+        return f32 ? md.dw32[vox] : __half22float2(md.dw16[vox]);
+    };
+    // x = 8 face (rows y + 9 z = j): local x = 0 of the +x neighbours
+    for (int j = lane; j < 81; j += 32) {
+        const int y = j % 9, z = j / 9;
+        const int s = W.nb[1 | ((y >> 3) << 1) | ((z >> 3) << 2)];
+        put(8 + 9 * j, 8 + 16 * j, nb_dw(s, 8 * (y & 7) + 64 * (z & 7)));
+    }
+    // y = 8 face (x < 8, z = 0..8): local y = 0 of the +y neighbours
+    for (int j = lane; j < 72; j += 32) {
+        const int x = j & 7, z = j >> 3;
+        const int s = W.nb[2 | ((z >> 3) << 2)];
+        const int yz9 = 8 + 9 * z;
+        put(x + 9 * yz9, x + 16 * yz9, nb_dw(s, x + 64 * (z & 7)));
+    }
+    // z = 8 face (x < 8, y < 8): local z = 0 of the +z neighbour
+    {
+        const int s = W.nb[4];
+        for (int j = lane; j < 64; j += 32) {
+            const int x = j & 7, y = j >> 3;
+            const int yz9 = y + 72;
+            put(x + 9 * yz9, x + 16 * yz9, nb_dw(s, x + 8 * y));
         }
-        W.D[r] = D;
-        reinterpret_cast<uint8_t *>(W.u.F4)[r % 9 + 16 * (r / 9)] = (uint8_t)f;
-        if (f & 1) seen |= (f & 2) ? 1 : 2;
     }
     const bool any_neg = __any_sync(0xffffffffu, seen & 1), any_pos = __any_sync(0xffffffffu, seen & 2);
     int tot_m = 0;

@@ -246,8 +246,8 @@ def streams32(seed: int = 3, n_streams: int = 32) -> list[Workload]:
 
     Per stream: beams from {16, 32, 64, 128}, columns from {512, 1024, 2048},
     voxel size from {0.05, 0.1, 0.2, 0.4} m (uniform draws), truncation 3 x
-    voxel, +-22.5 deg, 100 m, sigma 3 cm, 20 classes with hard labels, its
-    own seeded 200 m x 200 m scene of 2,000 primitives on the 400 m loop
+    voxel, +-22.5 deg, 100 m, sigma 3 cm, 20-way class-probability vectors,
+    its own seeded 200 m x 200 m scene of 2,000 primitives on the 400 m loop
     (200 poses per lap, 2 m apart, as in the 64 x 2048 workload).
     """
     rng = np.random.default_rng([seed, 13])
@@ -257,7 +257,7 @@ def streams32(seed: int = 3, n_streams: int = 32) -> list[Workload]:
         W = int(rng.choice([512, 1024, 2048]))
         v = float(rng.choice([0.05, 0.1, 0.2, 0.4]))
         out.append(Workload(f"stream{i}_{H}x{W}_v{v}", lidar_deg(H, W, 22.5, -22.5, 100.0), 0.03, 200,
-                            v, 3.0 * v, 20, "hard", "loop", 1000 * seed + i, n_prims=2000, extent=200.0))
+                            v, 3.0 * v, 20, "probs", "loop", 1000 * seed + i, n_prims=2000, extent=200.0))
     return out
 
 
