@@ -6,6 +6,7 @@
 #pragma once
 
 #include "kernels.h"
+#include "poly_approx.h"
 
 namespace stsdf {
 
@@ -254,6 +255,26 @@ __device__ __forceinline__ unsigned remesh_offsets(int vi) {
     return (unsigned)(REMESH_TABLE >> (8 * z)) & 0xffu;
 }
 
+// atan2(y, x) in (-pi, pi] from the atan polynomial on [0, 1] and the octant
+// symmetries; error below 5e-7 rad (polynomial 1.8e-7, the quotient and the
+// octant subtractions one rounding each), atan2(+-0, x < 0) = +-pi as atan2f.
+__device__ __forceinline__ float atan2_poly(float y, float x) {
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float t = mx > 0.f ? __fdividef(mn, mx) : 0.f;
+    float a = t * atan_p(t * t);
+    if (ay > ax) a = 1.57079632679489662f - a;
+    if (x < 0.f) a = PI_F - a;
+    return copysignf(a, y);
+}
+
+// acos(c) for c in [-1, 1]: pi/2 - asin(c) from the asin polynomial when
+// |c| <= 1/2 (error below 3e-7 rad), acosf beyond.
+__device__ __forceinline__ float acos_poly(float c) {
+    if (fabsf(c) > 0.5f) return acosf(c);
+    return 1.57079632679489662f - c * asin_q(c * c);
+}
+
 // Pixel of voxel vi of block (bx, by, bz) (Sec. III-C.1), or -1 outside the
 // image; also returns the voxel's offset from the sensor in voxel units
 // (exact integer part minus the fraction's high part, m) and |x_l|^2 (rr2)
@@ -273,8 +294,10 @@ __device__ __forceinline__ int tsdf_pixel(const ScanConst &sc, int bx, int by, i
     irr = 0.f;
     if (!(rr2 > 0.f)) return -1;
     irr = rsqrtf(rr2);
-    const float uc = (PI_F - atan2f(x1, x0)) * sc.inv_dphi;
-    const float vc = (acosf(fminf(fmaxf(x2 * irr, -1.f), 1.f)) - sc.theta0) * sc.inv_dtheta;
+    // (polynomial atan2 / acos: their errors, < 5e-7 rad, stay far below the
+    // 1e-3-pixel margin within which FP32 and FP64 pixel choices may differ)
+    const float uc = (PI_F - atan2_poly(x1, x0)) * sc.inv_dphi;
+    const float vc = (acos_poly(fminf(fmaxf(x2 * irr, -1.f), 1.f)) - sc.theta0) * sc.inv_dtheta;
     int u = (int)floorf(uc + 0.5f);
     const int v = (int)floorf(vc + 0.5f);
     if (u >= sc.W) u -= sc.W;

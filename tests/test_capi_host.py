@@ -100,3 +100,33 @@ def test_config_defaults():
     assert cfg.voxel_size == pytest.approx(0.1) and cfg.truncation == pytest.approx(0.3)
     assert cfg.n_classes == 20 and cfg.weight_mode == 0 and cfg.storage == 0
     assert ctypes.sizeof(cfg) == 104
+
+
+def _poly_coeffs(name):
+    """Coefficients of atan_p / asin_q from the generated header (highest degree first)."""
+    import re
+    txt = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "paper_2412_00291_b300", "csrc", "poly_approx.h")).read()
+    body = txt[txt.index(name + "(float s)"):]
+    body = body[:body.index("return")]
+    return [float(v) for v in re.findall(r"([-+]?\d\.\d+e[-+]\d+)f", body)]
+
+
+def _horner_fma32(coeffs, s):
+    # float32 Horner with a single rounding per step (as fmaf)
+    r = np.full_like(s, coeffs[0], dtype=np.float64)
+    for c in coeffs[1:]:
+        r = (r * s.astype(np.float64) + np.float32(c)).astype(np.float32).astype(np.float64)
+    return r
+
+
+def test_projection_polynomials_meet_their_bounds():
+    """The voxel-projection polynomials (atan on [0, 1], asin on [0, 1/2]) against numpy's
+    double-precision arctan / arcsin: below 2e-7 rad, far inside the 1e-3-pixel margin
+    (3e-6 rad for 2048 columns, 1.2e-5 rad for 64 beams over 45 deg)."""
+    t = np.linspace(0.0, 1.0, 400001).astype(np.float32)
+    a = t.astype(np.float64) * _horner_fma32(_poly_coeffs("atan_p"), (t * t).astype(np.float32))
+    assert np.abs(a - np.arctan(t.astype(np.float64))).max() < 2e-7
+    c = np.linspace(0.0, 0.5, 400001).astype(np.float32)
+    b = c.astype(np.float64) * _horner_fma32(_poly_coeffs("asin_q"), (c * c).astype(np.float32))
+    assert np.abs(b - np.arcsin(c.astype(np.float64))).max() < 2e-7
