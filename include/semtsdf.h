@@ -194,9 +194,11 @@ map_status query_sdf_backward(map_t *map, const float *xyz_dev, const float *gra
                               float *grad_xyz_dev, double *pose_grad_dev, void *stream);
 
 /* Scan-to-map alignment: `iters` Gauss-Newton steps on sum_i D(T p_i)^2,
- * (H + mu I) delta = -g with mu = 1e-6 (trace(H)/6 + 1e-12) and
- * T <- Exp(delta) T, all on the device.  points_dev [n][3] float32 LiDAR
- * frame.  T0 and T_out are host double[16].  Synchronises `stream`. */
+ * (H + mu I) delta = -g with mu = 1e-6 (trace(H)/6 + 1e-12), the left
+ * perturbation taken about the current sensor position t:
+ * T <- Tr(t) Exp(delta) Tr(-t) T, all on the device.  points_dev [n][3]
+ * float32 LiDAR frame.  T0 and T_out are host double[16].  Synchronises
+ * `stream`. */
 map_status map_align_scan(map_t *map, const float *points_dev, int64_t n, const double T0[16], int32_t iters,
                           double T_out[16], void *stream);
 

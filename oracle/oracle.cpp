@@ -866,15 +866,50 @@ int64_t orc_pose_terms(void *h, const float *pts, int64_t n, const double *T16, 
 }
 
 /*
+ * Gauss-Newton system for a left perturbation about the sensor position c = t
+ * of T: x' = Exp(xi) applied to x - c, plus c, so dx/dxi = [I | -[x - c]x] and
+ * J_i = grad D(x_i)^T [I | -[R p_i]x] (x_i - c = R p_i).  Returns the number of
+ * valid points.
+ */
+static int64_t pose_terms_at_sensor(Map &m, const float *pts, int64_t n, const double *T16, double *H, double *g6) {
+    int64_t nv = 0;
+    for (int a = 0; a < 36; ++a) H[a] = 0.0;
+    for (int a = 0; a < 6; ++a) g6[a] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double p[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
+        if (!(std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]))) continue;
+        double q[3], x[3];
+        for (int r = 0; r < 3; ++r) {
+            q[r] = T16[4 * r] * p[0] + T16[4 * r + 1] * p[1] + T16[4 * r + 2] * p[2];
+            x[r] = q[r] + T16[4 * r + 3];
+        }
+        double s, gr[3];
+        if (!query(m, x, &s, gr)) continue;
+        ++nv;
+        const double J[6] = {gr[0], gr[1], gr[2], q[1] * gr[2] - q[2] * gr[1], q[2] * gr[0] - q[0] * gr[2],
+                             q[0] * gr[1] - q[1] * gr[0]};
+        for (int a = 0; a < 6; ++a) {
+            g6[a] += J[a] * s;
+            for (int b = 0; b < 6; ++b) H[6 * a + b] += J[a] * J[b];
+        }
+    }
+    return nv;
+}
+
+/*
  * Gauss-Newton scan-to-map alignment: iters steps of
- * (H + mu I) delta = -g with mu = 1e-6 (trace(H)/6 + 1e-12), T <- Exp(delta) T.
+ * (H + mu I) delta = -g with mu = 1e-6 (trace(H)/6 + 1e-12), then
+ * T <- Tr(c) Exp(delta) Tr(-c) T with c the current sensor position, i.e.
+ * R <- dR R, t <- t + dt for (dR, dt) = Exp(delta).  (About the world origin,
+ * far from a scan on a large map, the rotation needs a compensating
+ * translation of the lever arm's size, which the damping resists.)
  */
 int orc_align(void *h, const float *pts, int64_t n, const double *T0, int iters, double *T_out) {
     double T[16];
     std::memcpy(T, T0, sizeof(T));
     for (int it = 0; it < iters; ++it) {
         double H[36], g[6];
-        orc_pose_terms(h, pts, n, T, nullptr, nullptr, H, g);
+        pose_terms_at_sensor(*(Map *)h, pts, n, T, H, g);
         double tr = 0.0;
         for (int a = 0; a < 6; ++a) tr += H[7 * a];
         double mu = 1e-6 * (tr / 6.0 + 1e-12);
@@ -908,7 +943,7 @@ int orc_align(void *h, const float *pts, int64_t n, const double *T0, int iters,
         for (int r = 0; r < 3; ++r) {
             for (int c = 0; c < 3; ++c)
                 Tn[4 * r + c] = dR[3 * r] * T[c] + dR[3 * r + 1] * T[4 + c] + dR[3 * r + 2] * T[8 + c];
-            Tn[4 * r + 3] = dR[3 * r] * T[3] + dR[3 * r + 1] * T[7] + dR[3 * r + 2] * T[11] + dt[r];
+            Tn[4 * r + 3] = T[4 * r + 3] + dt[r];
         }
         std::memcpy(T, Tn, sizeof(T));
     }

@@ -155,7 +155,11 @@ __global__ void __launch_bounds__(256) k_query_bwd(MapDev md, const float *__res
     }
 }
 
-// Gauss-Newton accumulation: per CTA b, acc[32 b + 0..20] upper triangle of
+// Gauss-Newton terms for a left perturbation about the sensor position c = t
+// of T (x' = Exp(xi)(x - c) + c, so J = grad D^T [I | -[R p]x]; about the
+// world origin, far from a scan on a large map, a rotation needs a
+// compensating translation as long as the lever arm, which the damping
+// resists).  Accumulation: per CTA b, acc[32 b + 0..20] upper triangle of
 // H = sum J^T J, acc[32 b + 21..26] g = sum J^T D, acc[32 b + 27] loss sum
 // D^2, acc[32 b + 28] valid count (plain stores, no atomics; k_gn_step sums
 // the CTAs' rows in a fixed order).
@@ -193,11 +197,12 @@ __global__ void __launch_bounds__(256) k_gn_terms(MapDev md, const float *__rest
         if (!trilinear(md, s_k, g, D, dg)) continue;
         const float inv = 1.f / md.nu;
         const float gr[3] = {dg[0] * inv, dg[1] * inv, dg[2] * inv};
-        float x[3];
+        // rotation about the sensor position c = t: x - c = R p
+        float rp[3];
 #pragma unroll
-        for (int r = 0; r < 3; ++r) x[r] = md.nu * ((float)s_k[r] + g[r]);
-        const float J[6] = {gr[0], gr[1], gr[2], x[1] * gr[2] - x[2] * gr[1], x[2] * gr[0] - x[0] * gr[2],
-                            x[0] * gr[1] - x[1] * gr[0]};
+        for (int r = 0; r < 3; ++r) rp[r] = md.nu * (s_c[3 * r] * p0 + s_c[3 * r + 1] * p1 + s_c[3 * r + 2] * p2);
+        const float J[6] = {gr[0], gr[1], gr[2], rp[1] * gr[2] - rp[2] * gr[1], rp[2] * gr[0] - rp[0] * gr[2],
+                            rp[0] * gr[1] - rp[1] * gr[0]};
         float ph, pl;
         int q = 0;
 #pragma unroll
@@ -284,7 +289,7 @@ __device__ __forceinline__ void rodrigues_coeffs(double th2, double &A1, double 
 
 // One CTA: sum the per-CTA rows (fixed order), then one thread solves
 // (H + mu I) d = -g (Cholesky; H is a sum of outer products plus mu I) and
-// applies T <- Exp(d) T.
+// applies the step about the sensor position (see k_gn_terms).
 __global__ void __launch_bounds__(256) k_gn_step(double *T, const double *acc, int nparts) {
     __shared__ double s_p[8][32];
     __shared__ double s_a[32];
@@ -383,11 +388,11 @@ __global__ void __launch_bounds__(256) k_gn_step(double *T, const double *acc, i
             R[i][j] = I + A1 * K[i][j] + B1 * K2[i][j];
             V[i][j] = I + B1 * K[i][j] + C1 * K2[i][j];
         }
+    // T <- Tr(c) Exp(d) Tr(-c) T about the sensor position c = t: R <- dR R, t <- t + V rho
     double Tn[16];
     for (int r = 0; r < 3; ++r) {
         for (int c = 0; c < 3; ++c) Tn[4 * r + c] = R[r][0] * T[c] + R[r][1] * T[4 + c] + R[r][2] * T[8 + c];
-        Tn[4 * r + 3] = R[r][0] * T[3] + R[r][1] * T[7] + R[r][2] * T[11] + V[r][0] * rho[0] + V[r][1] * rho[1] +
-                        V[r][2] * rho[2];
+        Tn[4 * r + 3] = T[4 * r + 3] + V[r][0] * rho[0] + V[r][1] * rho[1] + V[r][2] * rho[2];
     }
     for (int r = 0; r < 12; ++r) T[r] = Tn[r];
 }
