@@ -840,7 +840,7 @@ extern "C" map_status map_batch_create(map_t *const *maps, int32_t n_maps, int32
         int bps = 0;
         cudaError_t e = batch_occupancy(c, bps);
         if (e != cudaSuccess || bps < 1) {
-            delete b;
+            map_batch_destroy(b);
             return bfail(nullptr, MAP_ERR_CUDA, std::string("batch kernel occupancy: ") + cudaGetErrorString(e));
         }
         b->grid[c] = bps * sms;
@@ -848,13 +848,12 @@ extern "C" map_status map_batch_create(map_t *const *maps, int32_t n_maps, int32
     if (cudaMalloc(&b->ctl, sizeof(BatchCtl)) != cudaSuccess ||
         cudaMalloc(&b->out_dev, BATCH_MAX * sizeof(BatchState)) != cudaSuccess ||
         cudaMallocHost(&b->out_host, BATCH_MAX * sizeof(BatchState)) != cudaSuccess) {
-        delete b;
+        map_batch_destroy(b);
         return bfail(nullptr, MAP_ERR_NOMEM, "batch allocation failed");
     }
-    cudaEventCreate(&b->ev_a);
-    cudaEventCreate(&b->ev_b);
-    cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming);
-    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaEventCreate(&b->ev_a) != cudaSuccess || cudaEventCreate(&b->ev_b) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
         map_batch_destroy(b);
         return bfail(nullptr, MAP_ERR_CUDA, "batch capture stream");
     }

@@ -221,3 +221,40 @@ def test_loop64_full_size_sampled():
                colors=full["colors"][used], triangles=remap[sub_t], triangle_anchors=full["triangle_anchors"][keep])
     mrep = compare_meshes(sub, om.mesh(np.array(sorted(base_set))), om, w.voxel_size)
     print("loop64 sampled mesh:", mrep)
+
+
+@pytest.mark.parametrize("storage,cls", [(0, "probs"), (1, "labels")])
+def test_generic_class_count(storage, cls):
+    """C = 7 classes (the kernels' generic class-count path) against the oracle, both class
+    inputs, both storage precisions (FP16 at its stated bound)."""
+    p = _lib()
+    w = synth.line16()
+    C = 7
+    L = _lidar(p, w.lidar)
+    gm = p.SemanticTSDF(w.voxel_size, w.truncation, C, storage=storage, max_blocks=32768,
+                        hash_capacity=1 << 16, max_points=32768, max_pixels=32768,
+                        mesh_vertex_capacity=1 << 22, mesh_triangle_capacity=1 << 23)
+    om = oracle.OracleMap(w.voxel_size, w.truncation, C)
+    rng = np.random.default_rng(7)
+    frames = list(synth.sequence(w, 4))
+    for f in frames:
+        lab = np.where(f.labels >= 0, f.labels % C, -1).astype(np.int32)
+        if cls == "probs":
+            q = rng.uniform(0.0, 1.0, size=(len(lab), C)).astype(np.float32)
+            q[np.arange(len(lab)), np.clip(lab, 0, C - 1)] += 4.0
+            q = (q / q.sum(axis=1, keepdims=True)).astype(np.float32)
+            gm.integrate(L, _dev(f.points), f.T, probs=_dev(q))
+            om.integrate(w.lidar, f.points, f.T, probs=q)
+        else:
+            gm.integrate(L, _dev(f.points), f.T, labels=_dev(lab))
+            om.integrate(w.lidar, f.points, f.T, labels=lab)
+    coords = _sorted(gm.blocks())
+    assert np.array_equal(coords, _sorted(om.alloc_blocks()))
+    if storage == 0:
+        rep = compare_blocks(gm, om, coords, w.voxel_size, len(frames), C)
+    else:
+        K = len(frames)
+        rep = compare_blocks(gm, om, coords, w.voxel_size, K, C, d_tol=K * 2.0 ** -11 * w.truncation,
+                             lp_tol=K * 2.0 ** -11 * 30.0 + 1e-3, label_gap=0.05, w_rel=K * 2.0 ** -11)
+    assert rep["semantic"] > 1000 and rep["label_checked"] > 100
+    gm.close()
