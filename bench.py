@@ -87,9 +87,9 @@ def algorithmic_bytes(st, n_points, H, W, C, s):
     semantic: C log-probabilities read and written (2 C s B), the label byte
               and the 8 B list entry per semantically updated voxel (the
               winners' class inputs are L2 reads).
-    mesh:     {D, W} + label (2s + 1 B) of the 512 own voxels and the segment
-              record (16 B) per re-meshed block, 24 B per vertex and 8 B per
-              triangle emitted (neighbour faces are re-reads).
+    mesh:     {D, W} (2s B) of the 512 own voxels and the segment record (16 B) per
+              re-meshed block, 24 B per vertex and 8 B per triangle emitted
+              (neighbour faces are re-reads; vertex classes are read at extraction).
     """
     upd, sem, touched, dirty, mv, mt = st[4], st[5], st[2], st[6], st[7], st[8]
     return {
@@ -97,7 +97,7 @@ def algorithmic_bytes(st, n_points, H, W, C, s):
         "points": n_points * 12,
         "tsdf": upd * 2 * (2 * s) + sem * 8 + touched * 16,
         "semantic": sem * (2 * C * s + 1 + 8),
-        "mesh": dirty * (512 * (2 * s + 1) + 16) + mv * 24 + mt * 8,
+        "mesh": dirty * (512 * 2 * s + 16) + mv * 24 + mt * 8,
     }
 
 

@@ -305,75 +305,95 @@ __device__ __forceinline__ int tsdf_pixel(const ScanConst &sc, int bx, int by, i
     return (v >= 0 && v < sc.H) ? v * sc.W + u : -1;
 }
 
+// A voxel of the truncation band awaiting the float-pair psi (see below).
+struct BandEntry {
+    int vi;          // voxel index within the block
+    unsigned idx;    // the pixel's winner point
+    float r;         // its range
+    float D, W;      // the voxel's stored {D, W}
+};
+
+// Per-warp shared state of the TSDF pass over one block.
+struct TsdfWarpSmem {
+    int2 wbuf[BV];           // class-update entries {voxel, winner point} of the block
+    BandEntry band[64];      // band voxels queued for the float-pair psi
+};
+
 // Projective psi and the running-average update of one voxel whose pixel's
 // range-image winner is `win` (range bits << 32 | point index, ~0 when the
 // pixel has no return) (Sec. III-C.2), given the voxel's stored {D, W} (read
-// ahead by the caller).  Returns true when the voxel also takes the class
-// update, with the winner's point index in `idx`.
+// ahead by the caller).  Plain FP32 psi is within ~1e-5 m of the exact value;
+// away from +-tau it decides the update exactly: beyond +tau (+1 mm) sdf = tau
+// and w = 1, below -tau (-1 mm) nothing.  Returns true for a voxel of the band
+// in between, which needs the float-pair psi (tsdf_band).
 template <bool F16>
-__device__ __forceinline__ bool tsdf_update(const ScanConst &sc, const MapDev &md, long long vox, int vi, int p,
-                                            unsigned long long win, float2 dw, float m0, float m1, float m2,
-                                            float rr2, float irr, long long &n_upd, unsigned &remesh, int &idx) {
+__device__ __forceinline__ bool tsdf_fast(const ScanConst &sc, const MapDev &md, long long vox, int vi, int p,
+                                          unsigned long long win, float2 dw, float rr2, float irr, long long &n_upd,
+                                          unsigned &remesh) {
     if (p < 0 || win == ~0ull) return false;
     const float tau = sc.tau;
     const float r = __uint_as_float((unsigned)(win >> 32));
-    // plain FP32 psi is within ~1e-5 m of the exact value; away from +-tau it
-    // decides the update exactly: beyond +tau (+1 mm) sdf = tau and w = 1, below
-    // -tau (-1 mm) nothing; only the band in between needs the float-pair psi
-    float psi = r - sc.nu * (rr2 * irr);
-    float sdf = tau, w = 1.f;
-    bool upd = psi >= -tau - 1e-3f, sem = false;
-    if (upd && psi <= tau + 1e-3f) {
-        // r^2 of the winner as an exact float pair, from its coordinates
-        idx = (int)(win & 0xffffffffu);
-        const float x = sc.pts[3 * (long long)idx], y = sc.pts[3 * (long long)idx + 1],
-                    z = sc.pts[3 * (long long)idx + 2];
-        float a, ae, b, be, c, ce, rh, rl;
-        two_prod(x, x, a, ae);
-        two_prod(y, y, b, be);
-        two_prod(z, z, c, ce);
-        df_add(a, ae, b, be, rh, rl);
-        df_add(rh, rl, c, ce, rh, rl);
-        float e0, e1, e2, t0, t1, t2;
-        two_sum(m0, -sc.fhi[0], t0, e0);
-        two_sum(m1, -sc.fhi[1], t1, e1);
-        two_sum(m2, -sc.fhi[2], t2, e2);
-        e0 = __fsub_rn(e0, sc.flo[0]);
-        e1 = __fsub_rn(e1, sc.flo[1]);
-        e2 = __fsub_rn(e2, sc.flo[2]);
-        // rho^2 in voxel units, then metres^2, as float pairs; psi = (r^2 - rho^2) / (r + rho)
-        float qh, ql, mh, ml, dh, dl;
-        two_prod(t0, t0, a, ae);
-        two_prod(t1, t1, b, be);
-        two_prod(t2, t2, c, ce);
-        ae = __fmaf_rn(2.f * t0, e0, ae);
-        be = __fmaf_rn(2.f * t1, e1, be);
-        ce = __fmaf_rn(2.f * t2, e2, ce);
-        df_add(a, ae, b, be, qh, ql);
-        df_add(qh, ql, c, ce, qh, ql);
-        df_mul(qh, ql, sc.nu2hi, sc.nu2lo, mh, ml);
-        df_add(rh, rl, -mh, -ml, dh, dl);
-        psi = __fdividef(dh + dl, r + mh * rsqrtf(mh));
-        sdf = fminf(psi, tau);
-        if (sc.weight_mode == 0) w = fminf(fmaxf((psi + tau) * sc.inv_2tau, 0.f), 1.f);
-        upd = psi >= -tau && w > 0.f;
-        if (upd && fabsf(psi) <= tau) {
-            // the winner carries a class likelihood: a probability row, or a label in range
-            if (sc.has_probs) {
-                sem = true;
-            } else {
-                const int l = sc.labels[idx];
-                sem = l >= 0 && l < sc.C;
-            }
-        }
-    }
-    if (upd) {
-        const float Wn = dw.y + w;
-        store_dw<F16>(md, vox, __fdividef(dw.y * dw.x + w * sdf, Wn), Wn);
-        ++n_upd;
-        remesh |= remesh_offsets(vi);
-    }
-    return sem;
+    const float psi = r - sc.nu * (rr2 * irr);
+    if (psi < -tau - 1e-3f) return false;
+    if (psi <= tau + 1e-3f) return true;
+    const float Wn = dw.y + 1.f;
+    store_dw<F16>(md, vox, __fdividef(dw.y * dw.x + tau, Wn), Wn);
+    ++n_upd;
+    remesh |= remesh_offsets(vi);
+    return false;
+}
+
+// The band voxel e of block (bx, by, bz) at pool slot `slot`: psi formed as
+// (r^2 - rho^2) / (r + rho) with r^2 (from the winner point) and rho^2 as
+// unevaluated float pairs, the linear weight and the running average.
+// Returns true when the voxel also takes the class update.
+template <bool F16>
+__device__ __forceinline__ bool tsdf_band(const ScanConst &sc, const MapDev &md, int slot, int bx, int by, int bz,
+                                          const BandEntry &e, long long &n_upd, unsigned &remesh) {
+    const float tau = sc.tau;
+    const int vi = e.vi, lx = vi & 7, ly = (vi >> 3) & 7, lz = vi >> 6;
+    const float m0 = (float)(8 * bx + lx - sc.k[0]), m1 = (float)(8 * by + ly - sc.k[1]),
+                m2 = (float)(8 * bz + lz - sc.k[2]);
+    const float x = sc.pts[3 * (long long)e.idx], y = sc.pts[3 * (long long)e.idx + 1],
+                z = sc.pts[3 * (long long)e.idx + 2];
+    float a, ae, b, be, c, ce, rh, rl;
+    two_prod(x, x, a, ae);
+    two_prod(y, y, b, be);
+    two_prod(z, z, c, ce);
+    df_add(a, ae, b, be, rh, rl);
+    df_add(rh, rl, c, ce, rh, rl);
+    float e0, e1, e2, t0, t1, t2;
+    two_sum(m0, -sc.fhi[0], t0, e0);
+    two_sum(m1, -sc.fhi[1], t1, e1);
+    two_sum(m2, -sc.fhi[2], t2, e2);
+    e0 = __fsub_rn(e0, sc.flo[0]);
+    e1 = __fsub_rn(e1, sc.flo[1]);
+    e2 = __fsub_rn(e2, sc.flo[2]);
+    // rho^2 in voxel units, then metres^2, as float pairs; psi = (r^2 - rho^2) / (r + rho)
+    float qh, ql, mh, ml, dh, dl;
+    two_prod(t0, t0, a, ae);
+    two_prod(t1, t1, b, be);
+    two_prod(t2, t2, c, ce);
+    ae = __fmaf_rn(2.f * t0, e0, ae);
+    be = __fmaf_rn(2.f * t1, e1, be);
+    ce = __fmaf_rn(2.f * t2, e2, ce);
+    df_add(a, ae, b, be, qh, ql);
+    df_add(qh, ql, c, ce, qh, ql);
+    df_mul(qh, ql, sc.nu2hi, sc.nu2lo, mh, ml);
+    df_add(rh, rl, -mh, -ml, dh, dl);
+    const float psi = __fdividef(dh + dl, e.r + mh * rsqrtf(mh));
+    const float sdf = fminf(psi, tau);
+    const float w = sc.weight_mode == 0 ? fminf(fmaxf((psi + tau) * sc.inv_2tau, 0.f), 1.f) : 1.f;
+    if (!(psi >= -tau && w > 0.f)) return false;
+    const float Wn = e.W + w;
+    store_dw<F16>(md, (long long)slot * BV + vi, __fdividef(e.W * e.D + w * sdf, Wn), Wn);
+    ++n_upd;
+    remesh |= remesh_offsets(vi);
+    if (fabsf(psi) > tau) return false;
+    // the winner carries a class likelihood: a probability row, or a label in range
+    if (sc.has_probs) return true;
+    const int l = sc.labels[e.idx];
+    return l >= 0 && l < sc.C;
 }
 
 // Class-update entries {voxel, winner point} collect in the warp's shared
@@ -384,11 +404,15 @@ __device__ __forceinline__ void tsdf_list(bool sem, int vox, int idx, int2 *wbuf
     wcount += __popc(mk);
 }
 
-// One touched block (hash slot h), processed by one warp.
+// One touched block (hash slot h), processed by one warp.  Voxels outside the
+// truncation band are finished on the spot; band voxels are queued, and the
+// queue is worked off 32 at a time with every lane busy (they take the long
+// float-pair path, which would otherwise idle the rest of the warp).
 template <bool F16>
 __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int h,
-                                                int2 *wbuf, long long &n_upd) {
+                                                TsdfWarpSmem &T, long long &n_upd) {
     const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const int slot = md.vals[h];
     if (slot < 0) return;
     const uint64_t key = md.keys[h];
@@ -397,7 +421,38 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
     // a block allocated in this frame links itself with its neighbours
     if (lane >= 8 && lane < 15 && md.slot_frame[slot] == sc.frame) link_block(md, key, slot, lane - 7);
     unsigned remesh = 0;
-    int wcount = 0;
+    int wcount = 0, qn = 0;
+    auto enqueue = [&](bool band, int vi, unsigned long long win, float2 dw) {
+        const unsigned mb = __ballot_sync(0xffffffffu, band);
+        if (band) {
+            BandEntry &e = T.band[qn + __popc(mb & lt)];
+            e.vi = vi;
+            e.idx = (unsigned)(win & 0xffffffffu);
+            e.r = __uint_as_float((unsigned)(win >> 32));
+            e.D = dw.x;
+            e.W = dw.y;
+        }
+        qn += __popc(mb);
+    };
+    // work off the first n (<= 32) queued voxels, one per lane, and move the rest up
+    auto drain = [&](int n) {
+        __syncwarp();
+        bool sem = false;
+        int vox = 0, idx = 0;
+        if (lane < n) {
+            const BandEntry e = T.band[lane];
+            sem = tsdf_band<F16>(sc, md, slot, bx, by, bz, e, n_upd, remesh);
+            vox = slot * BV + e.vi;
+            idx = (int)e.idx;
+        }
+        const bool keep = lane < qn - n;
+        BandEntry rest;
+        if (keep) rest = T.band[n + lane];
+        __syncwarp();
+        if (keep) T.band[lane] = rest;
+        qn -= n;
+        tsdf_list(sem, vox, idx, T.wbuf, wcount);
+    };
     // voxels vi and vi + 32 per step: both {D, W} reads are issued before the
     // projections and both pixel reads before either update, so that their
     // latencies overlap
@@ -409,13 +464,16 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
         const int pa = tsdf_pixel(sc, bx, by, bz, vi, ma0, ma1, ma2, ra, ia);
         const int pb = tsdf_pixel(sc, bx, by, bz, vi + 32, mb0, mb1, mb2, rb, ib);
         const unsigned long long wa = fd.win[pa < 0 ? 0 : pa], wb = fd.win[pb < 0 ? 0 : pb];
-        int ka = 0, kb = 0;
-        const bool sa = tsdf_update<F16>(sc, md, va, vi, pa, wa, dwa, ma0, ma1, ma2, ra, ia, n_upd, remesh, ka);
-        const bool sb = tsdf_update<F16>(sc, md, vb, vi + 32, pb, wb, dwb, mb0, mb1, mb2, rb, ib, n_upd, remesh, kb);
-        tsdf_list(sa, slot * BV + vi, ka, wbuf, wcount);
-        tsdf_list(sb, slot * BV + vi + 32, kb, wbuf, wcount);
+        const bool ba = tsdf_fast<F16>(sc, md, va, vi, pa, wa, dwa, ra, ia, n_upd, remesh);
+        const bool bb = tsdf_fast<F16>(sc, md, vb, vi + 32, pb, wb, dwb, rb, ib, n_upd, remesh);
+        enqueue(ba, vi, wa, dwa);
+        if (qn >= 32) drain(32);
+        enqueue(bb, vi + 32, wb, dwb);
+        if (qn >= 32) drain(32);
     }
+    if (qn > 0) drain(qn);
     __syncwarp();
+    int2 *wbuf = T.wbuf;
     // one append of the block's class-update entries
     if (wcount) {
         unsigned long long base = 0;

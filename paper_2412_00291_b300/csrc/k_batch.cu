@@ -63,7 +63,7 @@ __device__ __forceinline__ long long pad32(long long x) { return (x + 31) & ~31l
 template <int WARPS>
 struct BatchSmem {
     union {
-        int2 tsdf_buf[WARPS][BV];
+        TsdfWarpSmem tsdf[WARPS];
         struct {
             int8_t tri[256 * MC_MAXTRI * 3];
             uint8_t ntri[256];
@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch(const __grid_c
         const BatchItem &it = a.it[i];
         long long n_upd = 0;
         const int h = it.fd.touched[e - S.pre[i]];
-        if (it.md.storage == 0) tsdf_block_warp<false>(it.sc, it.md, it.fd, h, S.u.tsdf_buf[wid], n_upd);
-        else tsdf_block_warp<true>(it.sc, it.md, it.fd, h, S.u.tsdf_buf[wid], n_upd);
+        if (it.md.storage == 0) tsdf_block_warp<false>(it.sc, it.md, it.fd, h, S.u.tsdf[wid], n_upd);
+        else tsdf_block_warp<true>(it.sc, it.md, it.fd, h, S.u.tsdf[wid], n_upd);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) n_upd += __shfl_xor_sync(0xffffffffu, n_upd, o);
         if (lane == 0 && n_upd) atomicAdd(&it.fd.ctr[CT_UPD], (unsigned long long)n_upd);

@@ -24,14 +24,14 @@ namespace stsdf {
 
 template <bool F16>
 __global__ void __launch_bounds__(256, 4) k_tsdf(ScanConst sc, MapDev md, FrameDev fd) {
-    __shared__ int2 s_buf[8][BV];   // per-warp class-update entries of the current block
-    int2 *wbuf = s_buf[threadIdx.x >> 5];
+    __shared__ TsdfWarpSmem s_w[8];   // per-warp class-update entries and band queue
+    TsdfWarpSmem &tw = s_w[threadIdx.x >> 5];
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     long long n_upd = 0;
     unsigned long long nt = *(volatile unsigned long long *)&fd.ctr[CT_TOUCHED];
     if (nt > (unsigned long long)md.max_blocks) nt = md.max_blocks;
-    for (long long li = warp; li < (long long)nt; li += nwarps) tsdf_block_warp<F16>(sc, md, fd, fd.touched[li], wbuf, n_upd);
+    for (long long li = warp; li < (long long)nt; li += nwarps) tsdf_block_warp<F16>(sc, md, fd, fd.touched[li], tw, n_upd);
     long long cnt[1] = {n_upd};
     cta_count<1>(fd.ctr, {CT_UPD}, cnt);
 }
