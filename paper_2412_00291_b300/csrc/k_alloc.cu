@@ -12,7 +12,7 @@
 
 namespace stsdf {
 
-__global__ void __launch_bounds__(256) k_points(const float *__restrict__ pts, ScanConst sc, MapDev md, FrameDev fd) {
+__global__ void __launch_bounds__(128) k_points(const float *__restrict__ pts, ScanConst sc, MapDev md, FrameDev fd) {
     long long cnt[3] = {0, 0, 0};
     points_item(pts, sc, md, fd, (long long)blockIdx.x * blockDim.x + threadIdx.x, cnt);
     cta_count<3>(fd.ctr, {CT_VALID, CT_PIXEL, CT_NEW}, cnt);
@@ -159,7 +159,8 @@ __global__ void k_collect_blocks(MapDev md, int32_t *coords, unsigned long long 
 
 void launch_points(const float *pts, const ScanConst &sc, const MapDev &md, const FrameDev &fd, cudaStream_t s) {
     if (sc.n <= 0) return;
-    k_points<<<(unsigned)((sc.n + 255) / 256), 256, 0, s>>>(pts, sc, md, fd);
+    // 128-thread CTAs: ~7 per SM for a 131,072-point scan, evenly spread
+    k_points<<<(unsigned)((sc.n + 127) / 128), 128, 0, s>>>(pts, sc, md, fd);
 }
 void launch_list_all(const MapDev &md, const FrameDev &fd, int, cudaStream_t s) {
     k_list_all<<<1024, 256, 0, s>>>(md, fd);
