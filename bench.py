@@ -424,27 +424,39 @@ def run_ours(args, rank, world, local_rank):
     frame_bytes = float(np.mean([sum(algorithmic_bytes(fs, n_points, L.H, L.W, C, s_bytes).values())
                                  for fs in fstats]))
     # --- end to end through the host-buffer entry point ----------------------
+    # Every step: the scan's inputs from pinned host memory (H->D), the scan,
+    # and a D->H read of its counters.  The steps are pipelined as a serving
+    # loop would run them: step k's upload (on the map's copy stream) overlaps
+    # step k-1's kernels, and step k-1's counters are read right after step k
+    # is issued.  No L2 flush here: each scan's working set exceeds L2.
     e2e = None
     if not args.no_e2e:
         tsdf.close()
         tsdf2 = P.SemanticTSDF(w.voxel_size, w.truncation, C, storage=storage, **cfg)
+
+        def host_step(k):
+            hp, hq = host[k]
+            tsdf2.integrate_host(lid, hp, Ts[k], **({"probs": hq} if pr_d else {"labels": hq}))
+
         for k in range(args.warmup):
-            hp, hq = host[k]
-            tsdf2.integrate_host(lid, hp, Ts[k], **({"probs": hq} if pr_d else {"labels": hq}))
+            host_step(k)
         tsdf2.stats()
-        e2e_s = 0.0
+        f0 = tsdf2.frame_count()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        results = []
         for i in range(args.steps):
-            k = args.warmup + i
-            hp, hq = host[k]
-            flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            tsdf2.integrate_host(lid, hp, Ts[k], **({"probs": hq} if pr_d else {"labels": hq}))
-            tsdf2.stats()                       # device -> host read of the step's counters
-            e2e_s += time.perf_counter() - t0
+            host_step(args.warmup + i)
+            if i > 0:
+                results.append(tsdf2.frame_stats(f0 + i - 1))
+        results.append(tsdf2.frame_stats(f0 + args.steps - 1))
+        e2e_s = time.perf_counter() - t0
+        assert len(results) == args.steps and all(r["valid_points"] > 0 for r in results)
         h2d = n_points * 12 + (n_points * C * 4 if pr_d else n_points * 4)
         e2e = {"value": world * args.steps * n_points / e2e_s, "unit": "points/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": 16 * 8, "ms_per_step": 1e3 * e2e_s / args.steps}
+               "d2h_bytes_per_step": 16 * 8, "ms_per_step": 1e3 * e2e_s / args.steps,
+               "timing": "wall clock over the pipelined loop: per step H->D of the scan, the scan, D->H of its "
+                         "counters; uploads overlap the previous scan's kernels"}
         tsdf2.close()
     # --- CPU baseline: the oracle on the host cores --------------------------
     cpu = None

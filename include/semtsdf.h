@@ -144,11 +144,26 @@ map_status integrate_scan(map_t *map, const lidar_intrinsics *lidar, const float
                           const int32_t *labels_dev, const float *probs_dev, int64_t n,
                           const double T_world_lidar[16], void *stream);
 
-/* Same as integrate_scan, for HOST buffers (pinned for best speed): the
- * map copies them to its own device staging buffers on `stream` first. */
+/* Same as integrate_scan, for HOST buffers (pinned for best speed).  The
+ * map uploads them into one of two device staging sets on an internal copy
+ * stream; the scan's kernels on `stream` wait for the upload, and the upload
+ * waits only for the scan that last used the same set, so consecutive calls
+ * overlap a scan's upload with the previous scan's kernels.  Asynchronous:
+ * the host buffers must stay unchanged until this scan's counters are
+ * available (map_frame_stats for its frame index, map_sync, or any
+ * synchronising call). */
 map_status integrate_scan_host(map_t *map, const lidar_intrinsics *lidar, const float *points_host,
                                const int32_t *labels_host, const float *probs_host, int64_t n,
                                const double T_world_lidar[16], void *stream);
+
+/* Number of scans integrated so far; scan k (from 0) has frame index k. */
+int64_t map_frame_count(map_t *map);
+
+/* Counters (MAP_STAT_*) of frame `frame`, one of the last 8 integrated
+ * scans: waits for that scan only (not for later ones), then reads the copy
+ * taken at its end.  MAP_ERR_ARG for an older or future frame; the device
+ * error bits of that scan are reported as by map_sync. */
+map_status map_frame_stats(map_t *map, int64_t frame, int64_t *out);
 
 /* Gather every block's current mesh segment into one indexed mesh (device
  * arrays owned by the map).  Synchronises `stream` to learn the sizes. */

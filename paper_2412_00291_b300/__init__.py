@@ -77,6 +77,8 @@ _SIGS = {
     "query_sdf_backward": ([P, P, P, I64, P, P, P], I32),
     "map_align_scan": ([P, P, I64, P, I32, P, P], I32),
     "map_sync": ([P, P], I32),
+    "map_frame_count": ([P], I64),
+    "map_frame_stats": ([P, I64, P], I32),
     "map_get_frame_stats": ([P, P, P], I32),
     "map_get_blocks": ([P, P, I64, P], I32),
     "map_read_blocks": ([P, P, I64, P, P, P, P, P], I32),
@@ -288,6 +290,19 @@ def map_align_scan(h, points, T0, iters=20, stream=None):
     return out
 
 
+def map_frame_count(h) -> int:
+    return int(_lib.map_frame_count(h))
+
+
+def map_frame_stats(h, frame, check=True) -> dict:
+    """Counters of one of the last 8 scans (waits for that scan only)."""
+    out = np.zeros(16, np.int64)
+    st = _lib.map_frame_stats(h, int(frame), _np_ptr(out))
+    if check:
+        _check(st, h)
+    return dict(zip(MAP_STAT_NAMES, out[:len(MAP_STAT_NAMES)].tolist()))
+
+
 def map_sync(h, stream=None):
     _check(_lib.map_sync(h, _stream(stream)), h)
 
@@ -443,6 +458,12 @@ class SemanticTSDF:
 
     def integrate_host(self, lidar, points, T, labels=None, probs=None, stream=None):
         integrate_scan_host(self.h, lidar, points, T, labels=labels, probs=probs, stream=stream)
+
+    def frame_count(self):
+        return map_frame_count(self.h)
+
+    def frame_stats(self, frame, check=True):
+        return map_frame_stats(self.h, frame, check)
 
     def stats(self, stream=None, check=True):
         return map_get_frame_stats(self.h, stream, check)

@@ -47,9 +47,15 @@ struct map_t {
     long long known_frame = -1;
     double max_append = 0.0;         // largest per-frame growth of that fraction
     // staging for host inputs
-    float *stage_pts = nullptr;
-    int32_t *stage_lab = nullptr;
-    float *stage_probs = nullptr;
+    // integrate_scan_host: two staging sets, filled on a copy stream, so that a
+    // scan's upload overlaps the previous scan's kernels
+    float *stage_pts[2] = {};
+    int32_t *stage_lab[2] = {};
+    float *stage_probs[2] = {};
+    int stage_next = 0;
+    cudaStream_t cp = nullptr;
+    cudaEvent_t ev_copied[2] = {}, ev_used[2] = {};
+    unsigned long long *h_ring_ctr = nullptr;   // [RING][CT_COUNT] counters of the last RING frames
     // extracted mesh
     long long out_vcap = 0, out_tcap = 0;
     float *out_pos = nullptr;
@@ -127,7 +133,8 @@ static void free_all(map_t *m) {
                     m->md.lp16, m->md.label, m->md.slot_key, m->md.slot_frame, m->md.nbr, m->md.seg, m->md.av, m->md.ak, m->md.at,
                     m->av_alt, m->ak_alt, m->at_alt, m->st, m->fd.win,
                     m->fd.touched, m->fd.dirty, m->fd.sem_list, m->fd.ctr, m->gb.voff, m->gb.toff, m->gb.bsum_v, m->gb.bsum_t,
-                    m->gb.totals, m->stage_pts, m->stage_lab, m->stage_probs, m->out_pos, m->out_col,
+                    m->gb.totals, m->stage_pts[0], m->stage_lab[0], m->stage_probs[0], m->stage_pts[1],
+                    m->stage_lab[1], m->stage_probs[1], m->out_pos, m->out_col,
                     m->out_keys, m->out_tri, m->out_anchor, m->gn_T, m->gn_acc, m->pal_dev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -135,6 +142,12 @@ static void free_all(map_t *m) {
     if (m->h_st) cudaFreeHost(m->h_st);
     if (m->h_totals) cudaFreeHost(m->h_totals);
     if (m->h_ring) cudaFreeHost(m->h_ring);
+    if (m->h_ring_ctr) cudaFreeHost(m->h_ring_ctr);
+    for (int b = 0; b < 2; ++b) {
+        if (m->ev_copied[b]) cudaEventDestroy(m->ev_copied[b]);
+        if (m->ev_used[b]) cudaEventDestroy(m->ev_used[b]);
+    }
+    if (m->cp) cudaStreamDestroy(m->cp);
     for (auto &e : m->ev_ring)
         if (e) cudaEventDestroy(e);
     if (m->ev_fork) cudaEventDestroy(m->ev_fork);
@@ -244,7 +257,8 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     if (cudaMallocHost(&m->h_ctr, CT_COUNT * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&m->h_st, sizeof(DevState)) != cudaSuccess ||
         cudaMallocHost(&m->h_totals, 2 * sizeof(long long)) != cudaSuccess ||
-        cudaMallocHost(&m->h_ring, map_t::RING * sizeof(DevState)) != cudaSuccess) {
+        cudaMallocHost(&m->h_ring, map_t::RING * sizeof(DevState)) != cudaSuccess ||
+        cudaMallocHost(&m->h_ring_ctr, map_t::RING * CT_COUNT * sizeof(unsigned long long)) != cudaSuccess) {
         free_all(m);
         delete m;
         return fail(nullptr, MAP_ERR_NOMEM, "pinned host allocation failed");
@@ -253,7 +267,13 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     std::memset(m->h_st, 0, sizeof(DevState));
     std::memset(m->h_ring, 0, map_t::RING * sizeof(DevState));
     for (auto &e : m->ev_ring) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-    if (cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking) != cudaSuccess ||
+    std::memset(m->h_ring_ctr, 0, map_t::RING * CT_COUNT * sizeof(unsigned long long));
+    if (cudaStreamCreateWithFlags(&m->cp, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev_copied[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev_copied[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev_used[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev_used[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         free_all(m);
@@ -498,6 +518,8 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     if (st != MAP_OK) return st;
     CU(cudaMemcpyAsync(m->h_ctr, m->fd.ctr, CT_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     const int slot = m->frame % map_t::RING;
+    CU(cudaMemcpyAsync(m->h_ring_ctr + (size_t)slot * CT_COUNT, m->fd.ctr, CT_COUNT * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(&m->h_ring[slot], m->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CU(cudaEventRecord(m->ev_ring[slot], s));
     m->ring_frame[slot] = m->frame;
@@ -524,18 +546,28 @@ extern "C" map_status integrate_scan_host(map_t *m, const lidar_intrinsics *L, c
     if (n < 0 || n > m->cfg.max_points) return fail(m, MAP_ERR_ARG, "n out of range (<= max_points)");
     cudaStream_t s = (cudaStream_t)stream;
     const long long cap = m->cfg.max_points;
-    if (!m->stage_pts) CU(cudaMalloc(&m->stage_pts, cap * 3 * sizeof(float)));
-    if (labels_host && !m->stage_lab) CU(cudaMalloc(&m->stage_lab, cap * sizeof(int32_t)));
-    if (probs_host && !m->stage_probs) CU(cudaMalloc(&m->stage_probs, cap * m->C * sizeof(float)));
+    // alternate staging sets: this scan's upload (copy stream) waits only for the
+    // scan that last read the same set, so it overlaps the previous scan's kernels
+    const int b = m->stage_next;
+    m->stage_next ^= 1;
+    if (!m->stage_pts[b]) CU(cudaMalloc(&m->stage_pts[b], cap * 3 * sizeof(float)));
+    if (labels_host && !m->stage_lab[b]) CU(cudaMalloc(&m->stage_lab[b], cap * sizeof(int32_t)));
+    if (probs_host && !m->stage_probs[b]) CU(cudaMalloc(&m->stage_probs[b], cap * m->C * sizeof(float)));
+    CU(cudaStreamWaitEvent(m->cp, m->ev_used[b], 0));
     if (n > 0) {
-        CU(cudaMemcpyAsync(m->stage_pts, points_host, n * 3 * sizeof(float), cudaMemcpyHostToDevice, s));
+        CU(cudaMemcpyAsync(m->stage_pts[b], points_host, n * 3 * sizeof(float), cudaMemcpyHostToDevice, m->cp));
         if (labels_host)
-            CU(cudaMemcpyAsync(m->stage_lab, labels_host, n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            CU(cudaMemcpyAsync(m->stage_lab[b], labels_host, n * sizeof(int32_t), cudaMemcpyHostToDevice, m->cp));
         else
-            CU(cudaMemcpyAsync(m->stage_probs, probs_host, n * m->C * sizeof(float), cudaMemcpyHostToDevice, s));
+            CU(cudaMemcpyAsync(m->stage_probs[b], probs_host, n * m->C * sizeof(float), cudaMemcpyHostToDevice,
+                               m->cp));
     }
-    return run_frame(m, L, m->stage_pts, labels_host ? m->stage_lab : nullptr, probs_host ? m->stage_probs : nullptr,
-                     n, T_world_lidar, s);
+    CU(cudaEventRecord(m->ev_copied[b], m->cp));
+    CU(cudaStreamWaitEvent(s, m->ev_copied[b], 0));
+    const map_status st = run_frame(m, L, m->stage_pts[b], labels_host ? m->stage_lab[b] : nullptr,
+                                    probs_host ? m->stage_probs[b] : nullptr, n, T_world_lidar, s);
+    CU(cudaEventRecord(m->ev_used[b], s));
+    return st;
 }
 
 extern "C" map_status map_remesh_all(map_t *m, void *stream) {
@@ -552,6 +584,16 @@ extern "C" map_status map_remesh_all(map_t *m, void *stream) {
     return MAP_OK;
 }
 
+static map_status device_errors_of(map_t *m, const DevState &d) {
+    if (d.err & ERR_TIMEOUT) return fail(m, MAP_ERR_TIMEOUT, "a device-side wait gave up");
+    if (d.err) {
+        char buf[128];
+        std::snprintf(buf, sizeof buf, "device capacity exceeded (error bits 0x%x)", d.err);
+        return fail(m, MAP_ERR_CAPACITY, buf);
+    }
+    return MAP_OK;
+}
+
 static map_status device_errors(map_t *m) {
     if (m->h_st->err & ERR_TIMEOUT) return fail(m, MAP_ERR_TIMEOUT, "a device-side wait gave up");
     if (m->h_st->err) {
@@ -560,6 +602,24 @@ static map_status device_errors(map_t *m) {
         return fail(m, MAP_ERR_CAPACITY, buf);
     }
     return MAP_OK;
+}
+
+extern "C" int64_t map_frame_count(map_t *m) { return m ? (int64_t)m->frame : -1; }
+
+extern "C" map_status map_frame_stats(map_t *m, int64_t frame, int64_t *out) {
+    if (!m || !out) return fail(m, MAP_ERR_ARG, "null argument");
+    if (frame < 0 || frame >= m->frame || frame < m->frame - map_t::RING)
+        return fail(m, MAP_ERR_ARG, "frame out of range (one of the last 8 integrated scans)");
+    const int slot = (int)(frame % map_t::RING);
+    if (m->ring_frame[slot] != frame) return fail(m, MAP_ERR_ARG, "frame no longer held");
+    CU(cudaEventSynchronize(m->ev_ring[slot]));
+    for (int i = 0; i < MAP_STAT_COUNT; ++i) out[i] = 0;
+    const unsigned long long *c = m->h_ring_ctr + (size_t)slot * CT_COUNT;
+    for (int i = 0; i < CT_MT + 1; ++i) out[i] = (int64_t)c[i];
+    out[MAP_STAT_TOTAL_BLOCKS] = (int64_t)std::min<unsigned long long>(m->h_ring[slot].pool_count, m->md.max_blocks);
+    out[MAP_STAT_ERROR_BITS] = (int64_t)m->h_ring[slot].err;
+    out[MAP_STAT_KERNEL_LAUNCHES] = (int64_t)m->launches;
+    return device_errors_of(m, m->h_ring[slot]);
 }
 
 extern "C" map_status map_sync(map_t *m, void *stream) {
