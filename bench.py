@@ -58,6 +58,21 @@ def parse():
     return ap.parse_args()
 
 
+def rank_max(x, dist, device):
+    """The slowest rank's value (the job's time): an all-reduce MAX over the ranks (identity alone)."""
+    if not dist:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(points_per_step, steps, world, slowest_ms):
+    """Whole-job points/s: every rank fuses its own replica's scans (weak scaling)."""
+    return world * steps * points_per_step / (slowest_ms * 1e-3)
+
+
 def workload(name, rank=0):
     w = synth.loop64() if name == "loop64" else synth.line16()
     if rank:
@@ -374,10 +389,7 @@ def run_ours(args, rank, world, local_rank):
     launches = st_last["kernel_launches"] - launches0
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
     total_ms = float(step_ms.sum())
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = rank_max(total_ms, dist, dev)
     tsdf.close()
     # --- pass 2: the same scans into a fresh map with per-phase events --------
     tsdf = P.SemanticTSDF(w.voxel_size, w.truncation, C, storage=storage, **cfg)
@@ -395,7 +407,7 @@ def run_ours(args, rank, world, local_rank):
     if storage == 1 and not args.no_fp16_report:
         fp16 = fp16_report(P, w, lid, tsdf, make_step, args.warmup + args.steps, cfg, dev)
     n_points = L.H * L.W
-    value = world * args.steps * n_points / (total_ms * 1e-3)
+    value = job_throughput(n_points, args.steps, world, total_ms)
     # --- roofline of the dominant kernel ------------------------------------
     peak, peak_kind = measured_peaks()
     per_kernel = {}
