@@ -258,3 +258,81 @@ def test_generic_class_count(storage, cls):
                              lp_tol=K * 2.0 ** -11 * 30.0 + 1e-3, label_gap=0.05, w_rel=K * 2.0 ** -11)
     assert rep["semantic"] > 1000 and rep["label_checked"] > 100
     gm.close()
+
+
+def test_far_from_origin():
+    """The whole drive 10 km / -7 km / +30 m away from the world origin: the sensor-relative
+    voxel offsets (integer + float pair) keep FP32 psi at the same accuracy."""
+    p = _lib()
+    w = synth.line16()
+    L = _lidar(p, w.lidar)
+    gm = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=32768, hash_capacity=1 << 16,
+                        max_points=32768, max_pixels=32768, mesh_vertex_capacity=1 << 22,
+                        mesh_triangle_capacity=1 << 23)
+    om = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    shift = np.array([10000.0, -7000.0, 30.0])
+    frames = list(synth.sequence(w, 3))
+    for f in frames:
+        T = f.T.copy()
+        T[:3, 3] += shift
+        gm.integrate(L, _dev(f.points), T, labels=_dev(f.labels))
+        om.integrate(w.lidar, f.points, T, labels=f.labels)
+        gs, os_ = gm.stats(), om.stats()
+        for key in ("valid_points", "pixel_points", "touched_blocks", "new_blocks"):
+            assert gs[key] == os_[key], key
+    coords = _sorted(gm.blocks())
+    assert np.array_equal(coords, _sorted(om.alloc_blocks()))
+    assert coords[:, 0].min() > 5000          # blocks really are far away (0.2 m voxels, 8 per block)
+    rep = compare_blocks(gm, om, coords, w.voxel_size, len(frames), w.n_classes)
+    assert rep["max_dD"] <= 1e-4 * w.voxel_size and rep["observed"] > 50000
+    g = _mesh_np(gm.mesh())
+    # vertex positions are FP32 world coordinates: at 10 km one ulp is ~1 mm
+    ulp = np.spacing(np.float32(np.abs(g["positions"]).max()))
+    compare_meshes(g, om.mesh(), om, w.voxel_size, pos_tol=1e-4 + 2.0 * float(ulp))
+
+
+def test_duplicate_points_nearest_lowest_index_wins():
+    """Points sharing a pixel: the nearest wins the range image, equal ranges the lower index
+    (its label is the one fused)."""
+    p = _lib()
+    w = synth.line16()
+    L = _lidar(p, w.lidar)
+    f = next(iter(synth.sequence(w, 1)))
+    ok = np.isfinite(f.points).all(axis=1)
+    pts, lab = f.points[ok][:4000], f.labels[ok][:4000]
+    # every point twice: identical copies with another label, and a copy 1 cm farther
+    far = pts * (1.0 + 0.01 / np.linalg.norm(pts, axis=1, keepdims=True)).astype(np.float32)
+    P2 = np.concatenate([pts, pts, far]).astype(np.float32)
+    L2 = np.concatenate([lab, (lab + 1) % w.n_classes, (lab + 2) % w.n_classes]).astype(np.int32)
+    gm = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=16384, hash_capacity=1 << 15,
+                        max_points=32768, max_pixels=32768, mesh_vertex_capacity=1 << 21,
+                        mesh_triangle_capacity=1 << 22)
+    om = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    gm.integrate(L, _dev(P2), f.T, labels=_dev(L2))
+    om.integrate(w.lidar, P2, f.T, labels=L2)
+    coords = _sorted(gm.blocks())
+    assert np.array_equal(coords, _sorted(om.alloc_blocks()))
+    rep = compare_blocks(gm, om, coords, w.voxel_size, 1, w.n_classes)
+    assert rep["label_checked"] > 1000
+
+
+def test_mesh_arena_full_is_reported():
+    """A mesh arena too small for the scan: the capacity error is latched and reported, the
+    blocks that did not fit keep no segment, and nothing faults."""
+    p = _lib()
+    w = synth.line16()
+    L = _lidar(p, w.lidar)
+    f = next(iter(synth.sequence(w, 1)))
+    gm = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=16384, hash_capacity=1 << 15,
+                        max_points=32768, max_pixels=32768, mesh_vertex_capacity=4096,
+                        mesh_triangle_capacity=8192)
+    gm.integrate(L, _dev(f.points), f.T, labels=_dev(f.labels))
+    s = gm.stats(check=False)
+    assert s["error_bits"] & 8            # ERR_ARENA_FULL
+    with pytest.raises(p.MapError) as e:
+        gm.sync()
+    assert e.value.status == 3
+    m = gm.mesh()                          # what did fit is still a valid mesh
+    tri = m["triangles"].cpu().numpy()
+    assert tri.size == 0 or tri.max() < m["positions"].shape[0]
+    gm.close()
