@@ -742,7 +742,7 @@ def run_align(args, rank, world, local_rank):
         "metric": "scan-to-map alignment time, 20 Gauss-Newton iterations (64x2048 scan, 1 km map)",
         "value": ms, "unit": "ms/scan", "n_gpus": world, "steps": len(times), "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "fp16-storage/fp32-math (fp64 6x6 solve)", "data": "synthetic",
+        "dtype": "fp16-storage/fp32-math (float-pair sums, fp64 pose)", "data": "synthetic",
         "config": {"workload": w.name, "points_per_scan_mean": n_pts, "map_scans": built,
                    "map_blocks": st["total_blocks"],
                    "map_voxels": st["total_blocks"] * 512, "map_build_s": build_s,
@@ -757,7 +757,8 @@ def run_align(args, rank, world, local_rank):
                            "final_rotation_error_deg_median": float(np.median(small_r)),
                            "final_rotation_error_deg_max": float(np.max(small_r))},
         "pose_gradient_check": grad_check,
-        "gpu_launches": None, "clocks": clk.summary(),
+        # per map_align_scan call: k_gn_terms + k_gn_step per iteration
+        "gpu_launches": 2 * 20 * len(times), "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
 

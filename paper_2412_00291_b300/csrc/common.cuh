@@ -15,7 +15,6 @@ constexpr int MAX_PROBES = 256;       // linear-probing bound of the block hash
 constexpr int MAX_AXIS_CROSS = 4;     // band may cross <= 4 block planes per axis (tau <= 16 nu)
 constexpr int MAX_BAND_BLOCKS = 1 + 3 * MAX_AXIS_CROSS;
 constexpr int MC_MAXTRI = 8;          // triangles per cube case in the generated table
-constexpr int MC_EDGES = 3 * 8 * 9 * 9;  // lattice edges a block's cubes can use (1944)
 constexpr float PI_F = 3.14159265358979f;
 
 // latched device error bits
@@ -259,19 +258,6 @@ __device__ __forceinline__ int warp_exclusive_scan(int v, int &total) {
     }
     total = __shfl_sync(0xffffffffu, x, 31);
     return x - v;
-}
-
-// sum over the block, result valid in every thread
-__device__ __forceinline__ long long block_sum(long long v, long long *s_tmp) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) s_tmp[wid] = v;
-    __syncthreads();
-    long long t = 0;
-    for (int i = 0; i < nw; ++i) t += s_tmp[i];
-    __syncthreads();
-    return t;
 }
 
 // Per-CTA totals of per-thread statistics, added to the frame counters by

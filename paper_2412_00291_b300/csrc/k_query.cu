@@ -110,59 +110,91 @@ __global__ void __launch_bounds__(256) k_query(MapDev md, const float *__restric
     if (valid) valid[i] = ok ? 1 : 0;
 }
 
-__device__ __forceinline__ double block_sum_d(double v, double *s_tmp) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) s_tmp[wid] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int j = 0; j < nw; ++j) t += s_tmp[j];
-    __syncthreads();
-    return t;
-}
+// Backward of the query: grad_xyz = grad_sdf * dD/dx per point and, when
+// `part` is non-null, this CTA's row of the pose-gradient sums
+// (sum g, sum x x g) in part[8 b + 0..5], as float pairs (TwoProd / TwoSum)
+// on the FP32 pipes and without atomics; k_pose_finish adds the rows.
+constexpr int QB_MAX_CTAS = 148 * 8;
 
 __global__ void __launch_bounds__(256) k_query_bwd(MapDev md, const float *__restrict__ xyz,
                                                    const float *__restrict__ gsdf, long long m, float *gxyz,
-                                                   double *pose_grad) {
-    __shared__ double s_tmp[8];
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    float gx[3] = {0.f, 0.f, 0.f};
-    float x[3] = {0.f, 0.f, 0.f};
-    if (i < m) {
+                                                   double *part) {
+    __shared__ float s_h[8][6], s_l[8][6];
+    float ah[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, al[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (long long)gridDim.x * blockDim.x) {
         int k[3];
         float g[3], D, dg[3];
+        float gx[3] = {0.f, 0.f, 0.f};
         world_to_grid(md, xyz, i, k, g);
         if (trilinear(md, k, g, D, dg)) {
             const float s = gsdf[i] / md.nu;
 #pragma unroll
             for (int a = 0; a < 3; ++a) gx[a] = s * dg[a];
         }
+        float x[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             gxyz[3 * i + a] = gx[a];
             x[a] = xyz[3 * i + a];
         }
-    }
-    if (pose_grad) {
-        const double v[6] = {gx[0], gx[1], gx[2], (double)x[1] * gx[2] - (double)x[2] * gx[1],
-                             (double)x[2] * gx[0] - (double)x[0] * gx[2], (double)x[0] * gx[1] - (double)x[1] * gx[0]};
+        if (part) {
 #pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            const double t = block_sum_d(v[j], s_tmp);
-            if (threadIdx.x == 0 && t != 0.0) atomicAdd(&pose_grad[j], t);
+            for (int a = 0; a < 3; ++a) df_add(ah[a], al[a], gx[a], 0.f, ah[a], al[a]);
+            // x x g, each component a difference of two exact products
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int b = (a + 1) % 3, c = (a + 2) % 3;
+                float p1, e1, p2, e2, th, tl;
+                two_prod(x[b], gx[c], p1, e1);
+                two_prod(x[c], gx[b], p2, e2);
+                df_add(p1, e1, -p2, -e2, th, tl);
+                df_add(ah[3 + a], al[3 + a], th, tl, ah[3 + a], al[3 + a]);
+            }
         }
     }
+    if (!part) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float bh = __shfl_xor_sync(0xffffffffu, ah[j], o), bl = __shfl_xor_sync(0xffffffffu, al[j], o);
+            df_add(ah[j], al[j], bh, bl, ah[j], al[j]);
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            s_h[wid][j] = ah[j];
+            s_l[wid][j] = al[j];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float th = 0.f, tl = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) df_add(th, tl, s_h[w][threadIdx.x], s_l[w][threadIdx.x], th, tl);
+        part[8 * blockIdx.x + threadIdx.x] = (double)th + (double)tl;
+    }
+}
+
+// pose_grad[j] += sum over the CTA rows of part (fixed order).
+__global__ void k_pose_finish(const double *part, int nparts, double *pose_grad) {
+    const int j = threadIdx.x;
+    if (j >= 6) return;
+    double t = 0.0;
+    for (int b = 0; b < nparts; ++b) t += part[8 * b + j];
+    pose_grad[j] += t;
 }
 
 // Gauss-Newton terms for a left perturbation about the sensor position c = t
 // of T (x' = Exp(xi)(x - c) + c, so J = grad D^T [I | -[R p]x]; about the
 // world origin, far from a scan on a large map, a rotation needs a
 // compensating translation as long as the lever arm, which the damping
-// resists).  Accumulation: per CTA b, acc[32 b + 0..20] upper triangle of
-// H = sum J^T J, acc[32 b + 21..26] g = sum J^T D, acc[32 b + 27] loss sum
-// D^2, acc[32 b + 28] valid count (plain stores, no atomics; k_gn_step sums
-// the CTAs' rows in a fixed order).
+// resists).  Accumulation: per CTA b, row b of float pairs (hi, lo) viewed as
+// float2 row[32 b + j]: j = 0..20 upper triangle of H = sum J^T J, 21..26
+// g = sum J^T D, 27 loss sum D^2, 28 valid count (plain stores, no atomics;
+// k_gn_step sums the CTAs' rows in a fixed order).
 constexpr int GN_ACC = 29;
 constexpr int GN_MAX_CTAS = 148 * 8;
 
@@ -243,7 +275,7 @@ __global__ void __launch_bounds__(256) k_gn_terms(MapDev md, const float *__rest
     if (threadIdx.x < GN_ACC) {
         float th = 0.f, tl = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) df_add(th, tl, s_h[w][threadIdx.x], s_l[w][threadIdx.x], th, tl);
-        acc[32 * blockIdx.x + threadIdx.x] = (double)th + (double)tl;
+        reinterpret_cast<float2 *>(acc)[32 * blockIdx.x + threadIdx.x] = make_float2(th, tl);
     }
 }
 
@@ -288,121 +320,141 @@ __device__ __forceinline__ void rodrigues_coeffs(double th2, double &A1, double 
 }
 
 // One CTA: sum the per-CTA rows (fixed order), then one thread solves
-// (H + mu I) d = -g (Cholesky; H is a sum of outer products plus mu I) and
-// applies the step about the sensor position (see k_gn_terms).
+// (H + mu I) d = -g (Cholesky; H is a sum of outer products plus mu I), and
+// twelve threads apply the step about the sensor position (see k_gn_terms).
 __global__ void __launch_bounds__(256) k_gn_step(double *T, const double *acc, int nparts) {
-    __shared__ double s_p[8][32];
+    __shared__ float s_ph[8][32], s_pl[8][32];
     __shared__ double s_a[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const float2 *rows = reinterpret_cast<const float2 *>(acc);
     if (lane < GN_ACC) {
-        // rows wid, wid + 8, ... in order; eight loads in flight per step
-        double t = 0.0;
+        // rows wid, wid + 8, ... in order (float pairs, TwoSum on the FP32 pipes);
+        // eight loads in flight per step
+        float th = 0.f, tl = 0.f;
         for (int b0 = wid; b0 < nparts; b0 += 64) {
-            double v[8];
+            float2 v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = b0 + 8 * u < nparts ? acc[32 * (b0 + 8 * u) + lane] : 0.0;
+            for (int u = 0; u < 8; ++u)
+                v[u] = b0 + 8 * u < nparts ? rows[32 * (b0 + 8 * u) + lane] : make_float2(0.f, 0.f);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) t += v[u];
+            for (int u = 0; u < 8; ++u) df_add(th, tl, v[u].x, v[u].y, th, tl);
         }
-        s_p[wid][lane] = t;
+        s_ph[wid][lane] = th;
+        s_pl[wid][lane] = tl;
     }
     __syncthreads();
     if (threadIdx.x < GN_ACC) {
-        double t = 0.0;
-        for (int w = 0; w < 8; ++w) t += s_p[w][threadIdx.x];
-        s_a[threadIdx.x] = t;
+        float th = 0.f, tl = 0.f;
+        for (int w = 0; w < 8; ++w) df_add(th, tl, s_ph[w][threadIdx.x], s_pl[w][threadIdx.x], th, tl);
+        s_a[threadIdx.x] = (double)th + (double)tl;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    const double *a = s_a;
-    // H = sum J^T J (upper triangle, row-major in a[0..20]) + mu I, solved by a
-    // Cholesky factorisation held in registers (every index a compile-time constant)
-    double Hm[6][6];
-    {
-        int q = 0;
+    // the 6x6 solve and the step in FP32 (one thread; this GPU's FP64 latency
+    // is long): H is well conditioned with the sensor-centred perturbation, and
+    // the iteration's fixed point is set by g, which the float-pair sums carry
+    // exactly; only the pose composition below is FP64 (12 threads)
+    __shared__ float s_step[21];   // dR (row-major) and V rho
+    if (threadIdx.x == 0) {
+        const double *a = s_a;
+        float Hm[6][6];
+        {
+            int q = 0;
 #pragma unroll
-        for (int r = 0; r < 6; ++r)
+            for (int r = 0; r < 6; ++r)
 #pragma unroll
-            for (int c = r; c < 6; ++c) {
-                Hm[r][c] = a[q];
-                Hm[c][r] = a[q];
-                ++q;
-            }
-    }
-    double tr = 0.0;
-#pragma unroll
-    for (int r = 0; r < 6; ++r) tr += Hm[r][r];
-    const double mu = 1e-6 * (tr / 6.0 + 1e-12);
-    double Lc[6][6], inv_diag[6];
-    bool ok = true;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-#pragma unroll
-        for (int j = 0; j <= i; ++j) {
-            double sum = Hm[i][j] + (i == j ? mu : 0.0);
-#pragma unroll
-            for (int k = 0; k < j; ++k) sum -= Lc[i][k] * Lc[j][k];
-            if (i == j) {
-                ok = ok && sum > 0.0;
-                Lc[i][i] = sqrt(sum > 0.0 ? sum : 1.0);
-                inv_diag[i] = 1.0 / Lc[i][i];
-            } else {
-                Lc[i][j] = sum * inv_diag[j];
-            }
+                for (int c = r; c < 6; ++c) {
+                    Hm[r][c] = (float)a[q];
+                    Hm[c][r] = (float)a[q];
+                    ++q;
+                }
         }
-    }
-    double d[6] = {0, 0, 0, 0, 0, 0};
-    if (ok) {
-        double y[6];
+        float tr = 0.f;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) tr += Hm[r][r];
+        const float mu = 1e-6f * (tr / 6.f + 1e-12f);
+        float Lc[6][6], inv_diag[6];
+        bool ok = true;
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-            double sum = -a[21 + i];
 #pragma unroll
-            for (int k = 0; k < i; ++k) sum -= Lc[i][k] * y[k];
-            y[i] = sum * inv_diag[i];
+            for (int j = 0; j <= i; ++j) {
+                float sum = Hm[i][j] + (i == j ? mu : 0.f);
+#pragma unroll
+                for (int k = 0; k < j; ++k) sum -= Lc[i][k] * Lc[j][k];
+                if (i == j) {
+                    ok = ok && sum > 0.f;
+                    Lc[i][i] = sqrtf(sum > 0.f ? sum : 1.f);
+                    inv_diag[i] = 1.f / Lc[i][i];
+                } else {
+                    Lc[i][j] = sum * inv_diag[j];
+                }
+            }
         }
+        float d[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (ok) {
+            float y[6];
 #pragma unroll
-        for (int i = 5; i >= 0; --i) {
-            double sum = y[i];
+            for (int i = 0; i < 6; ++i) {
+                float sum = -(float)a[21 + i];
 #pragma unroll
-            for (int k = i + 1; k < 6; ++k) sum -= Lc[k][i] * d[k];
-            d[i] = sum * inv_diag[i];
+                for (int k = 0; k < i; ++k) sum -= Lc[i][k] * y[k];
+                y[i] = sum * inv_diag[i];
+            }
+#pragma unroll
+            for (int i = 5; i >= 0; --i) {
+                float sum = y[i];
+#pragma unroll
+                for (int k = i + 1; k < 6; ++k) sum -= Lc[k][i] * d[k];
+                d[i] = sum * inv_diag[i];
+            }
+        }
+        // Exp(rho, phi): Rodrigues rotation dR, translation V(phi) rho
+        const float *rho = d, *phi = d + 3;
+        const double th2 = (double)phi[0] * phi[0] + (double)phi[1] * phi[1] + (double)phi[2] * phi[2];
+        double A1d, B1d, C1d;
+        rodrigues_coeffs(th2, A1d, B1d, C1d);
+        const float A1 = (float)A1d, B1 = (float)B1d, C1 = (float)C1d;
+        const float K[3][3] = {{0.f, -phi[2], phi[1]}, {phi[2], 0.f, -phi[0]}, {-phi[1], phi[0], 0.f}};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            float vr = 0.f;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                float k2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) k2 += K[i][k] * K[k][j];
+                const float I = i == j ? 1.f : 0.f;
+                s_step[3 * i + j] = I + A1 * K[i][j] + B1 * k2;
+                vr += (I + B1 * K[i][j] + C1 * k2) * rho[j];
+            }
+            s_step[9 + i] = vr;
         }
     }
-    // Exp(rho, phi): Rodrigues rotation, translation V(phi) rho
-    const double *rho = d, *phi = d + 3;
-    const double th2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2];
-    double A1, B1, C1;
-    rodrigues_coeffs(th2, A1, B1, C1);
-    const double K[3][3] = {{0, -phi[2], phi[1]}, {phi[2], 0, -phi[0]}, {-phi[1], phi[0], 0}};
-    double K2[3][3], R[3][3], V[3][3];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double s = 0.0;
-            for (int k = 0; k < 3; ++k) s += K[i][k] * K[k][j];
-            K2[i][j] = s;
-        }
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            const double I = i == j ? 1.0 : 0.0;
-            R[i][j] = I + A1 * K[i][j] + B1 * K2[i][j];
-            V[i][j] = I + B1 * K[i][j] + C1 * K2[i][j];
-        }
+    __syncthreads();
     // T <- Tr(c) Exp(d) Tr(-c) T about the sensor position c = t: R <- dR R, t <- t + V rho
-    double Tn[16];
-    for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) Tn[4 * r + c] = R[r][0] * T[c] + R[r][1] * T[4 + c] + R[r][2] * T[8 + c];
-        Tn[4 * r + 3] = T[4 * r + 3] + V[r][0] * rho[0] + V[r][1] * rho[1] + V[r][2] * rho[2];
+    double v = 0.0;
+    const int e = threadIdx.x;
+    if (e < 9) {
+        const int r = e / 3, c = e % 3;
+        v = (double)s_step[3 * r] * T[c] + (double)s_step[3 * r + 1] * T[4 + c] + (double)s_step[3 * r + 2] * T[8 + c];
+    } else if (e < 12) {
+        v = T[4 * (e - 9) + 3] + (double)s_step[9 + (e - 9)];
     }
-    for (int r = 0; r < 12; ++r) T[r] = Tn[r];
+    __syncthreads();   // every thread has read T
+    if (e < 9) T[4 * (e / 3) + (e % 3)] = v;
+    else if (e < 12) T[4 * (e - 9) + 3] = v;
 }
 
 void launch_query(const MapDev &md, const float *xyz, long long m, float *sdf, uint8_t *valid, cudaStream_t s) {
     if (m > 0) k_query<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(md, xyz, m, sdf, valid);
 }
 void launch_query_bwd(const MapDev &md, const float *xyz, const float *gsdf, long long m, float *gxyz,
-                      double *pose_grad, cudaStream_t s) {
-    if (m > 0) k_query_bwd<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(md, xyz, gsdf, m, gxyz, pose_grad);
+                      double *pose_grad, double *part, cudaStream_t s) {
+    if (m <= 0) return;
+    long long grid = (m + 255) / 256;
+    if (grid > QB_MAX_CTAS) grid = QB_MAX_CTAS;
+    k_query_bwd<<<(unsigned)grid, 256, 0, s>>>(md, xyz, gsdf, m, gxyz, pose_grad ? part : nullptr);
+    if (pose_grad) k_pose_finish<<<1, 32, 0, s>>>(part, (int)grid, pose_grad);
 }
 int gn_terms_grid(long long n) {
     long long grid = (n + 255) / 256;

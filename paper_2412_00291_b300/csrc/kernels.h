@@ -40,8 +40,9 @@ void launch_set_cursors(const MapDev &md, const GatherBufs &g, cudaStream_t s);
 
 // k_query.cu: trilinear queries, gradients, Gauss-Newton
 void launch_query(const MapDev &md, const float *xyz, long long m, float *sdf, uint8_t *valid, cudaStream_t s);
+constexpr int QB_PART_DOUBLES = 148 * 8 * 8;   // per-CTA rows of pose-gradient partial sums
 void launch_query_bwd(const MapDev &md, const float *xyz, const float *gsdf, long long m, float *gxyz,
-                      double *pose_grad, cudaStream_t s);
+                      double *pose_grad, double *part, cudaStream_t s);
 void launch_gn_terms(const MapDev &md, const float *pts, long long n, const double *T_dev, double *acc,
                      cudaStream_t s);
 constexpr int GN_ACC_STRIDE = 32;             // doubles per CTA row of Gauss-Newton partial sums

@@ -68,6 +68,7 @@ struct map_t {
     uchar4 *pal_dev = nullptr;
     // alignment scratch
     double *gn_T = nullptr, *gn_acc = nullptr;
+    double *qb_part = nullptr;   // pose-gradient partial sums of query_sdf_backward
     int frame = 0;
     int grid_integrate = 0, grid_mesh = 0, grid_semantic = 0;
     // phase profiling: (MAP_PHASE_COUNT + 1) events per recorded frame
@@ -135,7 +136,7 @@ static void free_all(map_t *m) {
                     m->fd.touched, m->fd.dirty, m->fd.sem_list, m->fd.ctr, m->gb.voff, m->gb.toff, m->gb.bsum_v, m->gb.bsum_t,
                     m->gb.totals, m->stage_pts[0], m->stage_lab[0], m->stage_probs[0], m->stage_pts[1],
                     m->stage_lab[1], m->stage_probs[1], m->out_pos, m->out_col,
-                    m->out_keys, m->out_tri, m->out_anchor, m->gn_T, m->gn_acc, m->pal_dev};
+                    m->out_keys, m->out_tri, m->out_anchor, m->gn_T, m->gn_acc, m->qb_part, m->pal_dev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (m->h_ctr) cudaFreeHost(m->h_ctr);
@@ -251,6 +252,7 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     ALLOC(m->gb.totals, 2);
     ALLOC(m->gn_T, 16);
     ALLOC(m->gn_acc, (size_t)GN_ACC_ROWS * GN_ACC_STRIDE);
+    ALLOC(m->qb_part, (size_t)QB_PART_DOUBLES);
     ALLOC(m->pal_dev, 256);
     md.pal = m->pal_dev;
 #undef ALLOC
@@ -698,7 +700,7 @@ extern "C" map_status query_sdf_backward(map_t *m, const float *xyz_dev, const f
                                          float *grad_xyz_dev, double *pose_grad_dev, void *stream) {
     if (!m || n < 0 || (n > 0 && (!xyz_dev || !grad_sdf_dev || !grad_xyz_dev)))
         return fail(m, MAP_ERR_ARG, "bad backward arguments");
-    launch_query_bwd(m->md, xyz_dev, grad_sdf_dev, n, grad_xyz_dev, pose_grad_dev, (cudaStream_t)stream);
+    launch_query_bwd(m->md, xyz_dev, grad_sdf_dev, n, grad_xyz_dev, pose_grad_dev, m->qb_part, (cudaStream_t)stream);
     return launch_check(m, "query_sdf_backward");
 }
 
