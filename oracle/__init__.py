@@ -58,6 +58,10 @@ def _load():
         "orc_palette": ([I, P], None),
         "orc_point_blocks": ([P, P, P, P, I64], I64),
         "orc_point_band": ([P, P, P, P, P], None),
+        "orc_set_distance_mode": ([P, I], None),
+        "orc_get_normals": ([P, P, P, I64], I64),
+        "orc_read_grad": ([P, P, P], I),
+        "orc_nonproj_distance": ([D, P, P, P, I], D),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -79,11 +83,16 @@ class OracleMap:
     """Plain FP64 mapper: one std::unordered_map of 8^3-voxel blocks."""
 
     def __init__(self, voxel_size, truncation, n_classes=20, weight_mode=0, p_hit=0.9,
-                 logp_floor=-30.0, lik_floor=1e-6):
+                 logp_floor=-30.0, lik_floor=1e-6, distance="projective"):
         self.L = _load()
         self.C = n_classes
         self.h = self.L.orc_new(voxel_size, truncation, n_classes, weight_mode, p_hit, logp_floor, lik_floor)
         self.voxel_size = voxel_size
+        self.distance = distance
+        if distance == "nonprojective":
+            self.L.orc_set_distance_mode(self.h, 1)
+        elif distance != "projective":
+            raise ValueError(distance)
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -136,6 +145,20 @@ class OracleMap:
         if rc != 0:
             return None
         return dict(D=D, W=W, logP=lp, taint=taint, label=lab, gap=gap)
+
+    def read_grad(self, coord):
+        """Gradient g_i of one block's voxels, [3][512] (non-projective mode), or None."""
+        c = np.ascontiguousarray(coord, np.int32)
+        G = np.zeros((3, BV))
+        return G if self.L.orc_read_grad(self.h, _p(c), _p(G)) == 0 else None
+
+    def normals(self):
+        """The last scan's normal image (world frame) [H*W][3] and its flags (bit 0 valid, bit 1 near-ambiguous)."""
+        n = self.L.orc_get_normals(self.h, None, None, 0)
+        N = np.zeros((max(n, 1), 3))
+        f = np.zeros(max(n, 1), np.uint8)
+        self.L.orc_get_normals(self.h, _p(N), _p(f), n)
+        return N[:n], f[:n]
 
     def write_block(self, coord, D, W, logP=None):
         c = np.ascontiguousarray(coord, np.int32)
@@ -201,6 +224,14 @@ class OracleMap:
         e1 = np.zeros(3, np.float32)
         self.L.orc_point_band(self.h, _p(p), _p(T), _p(e0), _p(e1))
         return e0, e1
+
+
+def nonprojective_distance(psi, u, g, N=None) -> float:
+    """d_i of Eq. (distance) for projective distance psi, unit ray u (voxel toward sensor), gradient g, normal N."""
+    u = np.ascontiguousarray(u, np.float64)
+    g = np.ascontiguousarray(g, np.float64)
+    n = np.zeros(3) if N is None else np.ascontiguousarray(N, np.float64)
+    return float(_load().orc_nonproj_distance(float(psi), _p(u), _p(g), _p(n), 0 if N is None else 1))
 
 
 def edge_key(x, y, z, axis) -> int:

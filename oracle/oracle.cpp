@@ -28,6 +28,19 @@
  * are floored; marching-cubes faces with four crossings separate the inside
  * corners; a cube needs all 8 corners observed (W > 0).
  *
+ * Non-projective distance (Sec. III-C.2, Eq. distance), optional per map:
+ * the normal image from each pixel's back-projected point and its (u, v-1)
+ * and (u-1, v) neighbours, turned to face the sensor; the voxel gradient
+ * g_i as the weight-averaged, renormalised normal of the pixels the voxel
+ * projected to; d_i = psi (|cos theta| - sin theta tan(alpha / 2)) with a
+ * signed alpha (positive when g_i turns from the normal toward the ray,
+ * a convex surface), which is the printed curved-surface case derived from
+ * the figure's circle (the print lacks the factor psi on that term and
+ * drops the sign) and equals the printed flat case at alpha = 0; the flat
+ * case also where cos alpha <= 0, where the pixel has no normal (g_i kept)
+ * or the voxel has no gradient yet (then d_i = psi).  The weight and the
+ * skip below -tau stay on psi; Gamma(d_i, tau) is the fused value.
+ *
  * Precision: every value is FP64.  Two integer decisions are taken in the
  * precision the GPU takes them in, as both sides of a parity check must:
  * the per-point range used for validity and for the nearest-point winner
@@ -97,6 +110,7 @@ inline int64_t edge_key(int64_t x, int64_t y, int64_t z, int axis) {
 struct Block {
     std::vector<double> D, W, logP;  // D[512], W[512], logP[C][512] (class-major)
     std::vector<uint8_t> taint;      // bit 0: distance/weight, bit 1: semantics
+    std::vector<double> G;           // non-projective mode: gradient g_i, G[k][512] (k = x, y, z)
 };
 
 struct Lidar {
@@ -116,6 +130,7 @@ struct Map {
     double nu, tau;
     int C;
     int weight_mode;                 // 0: linear weight (Sec. III-C.2), 1: constant 1
+    int dist_mode = 0;               // 0: projective psi, 1: non-projective d_i (Eq. distance)
     double p_hit, logp_floor, lik_floor;
     double delta_px = 1e-3;          // pixel-boundary ambiguity band, in pixels
     double eps_psi;                  // psi ambiguity band around +-tau, metres
@@ -124,17 +139,20 @@ struct Map {
     std::unordered_set<I3, I3Hash> track_keys;
     std::unordered_set<I3, I3Hash> alloc;   // every allocated block (keys)
     std::vector<I3> touched;                // U_k of the last frame
+    std::vector<double> normals;            // non-projective mode: last normal image, world frame [H*W][3]
+    std::vector<uint8_t> normal_flag;       // bit 0: normal valid, bit 1: orientation nearly ambiguous
     Stats st;
     int64_t frame = 0;
 };
 
-Block new_block(int C) {
+Block new_block(int C, int dist_mode) {
     Block b;
     b.D.assign(BV, 0.0);
     b.W.assign(BV, 0.0);
     // uniform prior over the classes for every new voxel (Sec. III-C.3)
     b.logP.assign((size_t)C * BV, -std::log((double)C));
     b.taint.assign(BV, 0);
+    if (dist_mode == 1) b.G.assign(3 * BV, 0.0);   // no gradient until a normal is seen
     return b;
 }
 
@@ -241,6 +259,96 @@ BandConst band_const(const Map &m, const double R[9], const double t[3]) {
 
 inline double dist_to_int(double a) { return std::fabs(a - std::floor(a + 0.5)); }
 
+inline double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// ---------------------------------------------------------------------------
+// non-projective distance (Sec. III-C.2, Eq. distance)
+// ---------------------------------------------------------------------------
+// Unit ray of pixel (v, u): polar angle theta0 + v dtheta, azimuth pi - u dphi
+// (the range-image model of Sec. III-C.1 read backwards).
+inline void pixel_ray(const Lidar &L, int64_t v, int64_t u, double dir[3]) {
+    const double th = L.theta0 + (double)v * L.dtheta, ph = PI - (double)u * L.dphi;
+    dir[0] = std::sin(th) * std::cos(ph);
+    dir[1] = std::sin(th) * std::sin(ph);
+    dir[2] = std::cos(th);
+}
+
+/*
+ * Normal image N (Sec. III-C.2): p_j is the pixel's range r(u, v) along its
+ * ray, p_j1 the same for pixel (u, v - 1), p_j2 for (u - 1, v) (columns wrap
+ * around the scan); N(u, v) = (p_j1 - p_j) x (p_j2 - p_j) / |...|, turned to
+ * face the sensor (N . p_j <= 0), rotated into the world frame by R.  No
+ * normal on the top row, next to a pixel without a return, or where the
+ * cross product vanishes.  flag bit 0: valid; bit 1: |N . p_j| / |p_j| below
+ * 1e-5 (an FP32 evaluation may turn the normal the other way).
+ */
+void normal_image(const Lidar &L, const std::vector<double> &range, const double R[9], std::vector<double> &N,
+                  std::vector<uint8_t> &flag) {
+    const int64_t NP = (int64_t)L.H * L.W;
+    N.assign((size_t)NP * 3, 0.0);
+    flag.assign(NP, 0);
+    for (int64_t v = 1; v < L.H; ++v)
+        for (int64_t u = 0; u < L.W; ++u) {
+            const int64_t p = v * L.W + u, p1 = (v - 1) * L.W + u, p2 = v * L.W + (u + L.W - 1) % L.W;
+            if (range[p] < 0.0 || range[p1] < 0.0 || range[p2] < 0.0) continue;
+            double d0[3], d1[3], d2[3], q[3], q1[3], q2[3];
+            pixel_ray(L, v, u, d0);
+            pixel_ray(L, v - 1, u, d1);
+            pixel_ray(L, v, (u + L.W - 1) % L.W, d2);
+            for (int k = 0; k < 3; ++k) {
+                q[k] = range[p] * d0[k];
+                q1[k] = range[p1] * d1[k];
+                q2[k] = range[p2] * d2[k];
+            }
+            const double a[3] = {q1[0] - q[0], q1[1] - q[1], q1[2] - q[2]};
+            const double b[3] = {q2[0] - q[0], q2[1] - q[1], q2[2] - q[2]};
+            double c[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+            const double len = std::sqrt(dot3(c, c));
+            if (!(len > 0.0)) continue;
+            for (int k = 0; k < 3; ++k) c[k] /= len;
+            const double facing = dot3(c, q);
+            if (facing > 0.0)
+                for (int k = 0; k < 3; ++k) c[k] = -c[k];
+            uint8_t f = 1;
+            if (std::fabs(facing) < 1e-5 * range[p]) f |= 2;
+            for (int k = 0; k < 3; ++k) N[3 * p + k] = R[3 * k] * c[0] + R[3 * k + 1] * c[1] + R[3 * k + 2] * c[2];
+            flag[p] = f;
+        }
+}
+
+/*
+ * d_i of Eq. (distance) for a voxel at projective distance psi, with u the
+ * unit ray from the voxel toward the sensor, g its gradient (zero: none yet)
+ * and N the normal of its pixel (null: none).  theta is the angle between
+ * the ray and g, alpha the angle between g and N.  For a circle through the
+ * ray's surface point p_j with normal N whose point nearest the voxel has
+ * normal g (the figure's curved surface), the law of sines in the triangle
+ * (centre, p_j, voxel) gives the exact distance
+ *   d = psi (cos theta + sin theta (cos alpha - 1) / sin alpha)
+ *     = psi (cos theta - sin theta tan(alpha / 2)),
+ * alpha > 0 when g is turned from N toward the ray (convex) and < 0 away
+ * from it (concave).  The signed sin alpha is g's component along the unit
+ * tangent t = (u - (u.N) N) / |u - (u.N) N| and tan(alpha / 2) =
+ * sin alpha / (1 + cos alpha).  taint receives 1 where an FP32 evaluation
+ * may take another branch or lose the tangent's direction.
+ */
+double nonprojective_distance(double psi, const double u[3], const double g[3], const double *N, uint8_t *taint) {
+    if (!(dot3(g, g) > 0.0)) return psi;
+    const double ct = std::fabs(dot3(g, u));
+    if (!N) return ct * psi;
+    const double ca = dot3(g, N);
+    if (std::fabs(ca) < 1e-6 && taint) *taint |= 1;
+    if (!(ca > 0.0)) return ct * psi;
+    const double un = dot3(u, N);
+    const double up[3] = {u[0] - un * N[0], u[1] - un * N[1], u[2] - un * N[2]};
+    const double len = std::sqrt(dot3(up, up));
+    if (len < 1e-3 && taint) *taint |= 1;
+    if (!(len > 0.0)) return ct * psi;
+    const double sa = dot3(g, up) / len;
+    const double st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+    return psi * (ct - st * sa / (1.0 + ca));
+}
+
 // ---------------------------------------------------------------------------
 // one frame
 // ---------------------------------------------------------------------------
@@ -304,6 +412,18 @@ int integrate(Map &m, const Lidar &L, const float *pts, const int32_t *labels, c
         }
     }
 
+    // --- normal image (non-projective mode, Sec. III-C.2) ---------------------
+    if (m.dist_mode == 1) {
+        std::vector<double> range(NP, -1.0);
+        for (int64_t p = 0; p < NP; ++p) {
+            const int64_t i = win[p];
+            if (i < 0) continue;
+            const double X = pts[3 * i], Y = pts[3 * i + 1], Z = pts[3 * i + 2];
+            range[p] = std::sqrt(X * X + Y * Y + Z * Z);
+        }
+        normal_image(L, range, R, m.normals, m.normal_flag);
+    }
+
     // --- block allocation along each point's truncation band ------------------
     BandConst bc = band_const(m, R, t);
     std::unordered_set<I3, I3Hash> touched;
@@ -325,7 +445,7 @@ int integrate(Map &m, const Lidar &L, const float *pts, const int32_t *labels, c
         if (m.alloc.insert(b).second) m.st.new_blocks++;
         if (m.track && !m.track_keys.count(b)) continue;
         auto it = m.blocks.find(b);
-        if (it == m.blocks.end()) it = m.blocks.emplace(b, new_block(C)).first;
+        if (it == m.blocks.end()) it = m.blocks.emplace(b, new_block(C, m.dist_mode)).first;
         work.push_back(&it->second);
         work_key.push_back(b);
     }
@@ -384,9 +504,30 @@ int integrate(Map &m, const Lidar &L, const float *pts, const int32_t *labels, c
                         w = 1.0;
                     }
                     if (!(w > 0.0)) continue;
-                    // truncation Gamma(d, tau): min(d, tau) for d >= 0, max(d, -tau) otherwise
-                    double sdf = psi >= 0.0 ? std::min(psi, tau) : std::max(psi, -tau);
                     double Wo = blk.W[vi];
+                    double dist = psi;
+                    if (m.dist_mode == 1) {
+                        // gradient g_i: weight-averaged normal of the pixels seen, renormalised
+                        const double *Nw = (m.normal_flag[p] & 1) ? &m.normals[3 * p] : nullptr;
+                        if (m.normal_flag[p] & 2) { blk.taint[vi] |= 3; n_taint++; }
+                        double g[3] = {blk.G[vi], blk.G[BV + vi], blk.G[2 * BV + vi]};
+                        if (Nw) {
+                            double gs[3];
+                            for (int k = 0; k < 3; ++k) gs[k] = Wo * g[k] + w * Nw[k];
+                            const double gl = std::sqrt(dot3(gs, gs));
+                            if (gl < 1e-6 * (Wo + w)) { blk.taint[vi] |= 3; n_taint++; }
+                            if (gl > 0.0)
+                                for (int k = 0; k < 3; ++k) g[k] = gs[k] / gl;
+                            for (int k = 0; k < 3; ++k) blk.G[k * BV + vi] = g[k];
+                        }
+                        // unit ray from the voxel toward the sensor (world frame)
+                        const double uw[3] = {-d[0] / rho, -d[1] / rho, -d[2] / rho};
+                        uint8_t tf = 0;
+                        dist = nonprojective_distance(psi, uw, g, Nw, &tf);
+                        if (tf) { blk.taint[vi] |= 3; n_taint++; }
+                    }
+                    // truncation Gamma(d, tau): min(d, tau) for d >= 0, max(d, -tau) otherwise
+                    double sdf = dist >= 0.0 ? std::min(dist, tau) : std::max(dist, -tau);
                     blk.D[vi] = (Wo * blk.D[vi] + w * sdf) / (Wo + w);
                     blk.W[vi] = Wo + w;
                     n_upd++;
@@ -673,6 +814,33 @@ void *orc_new(double voxel_size, double truncation, int n_classes, int weight_mo
 
 void orc_free(void *h) { delete (Map *)h; }
 
+// 0: projective psi, 1: non-projective d_i (Eq. distance); set before the first scan
+void orc_set_distance_mode(void *h, int mode) { ((Map *)h)->dist_mode = mode; }
+
+// the last scan's normal image (world frame) and flags; returns H * W (0 in projective mode)
+int64_t orc_get_normals(void *h, double *N, uint8_t *flag, int64_t cap) {
+    Map *m = (Map *)h;
+    const int64_t np = (int64_t)m->normal_flag.size();
+    const int64_t k = std::min(cap, np);
+    if (N && k > 0) std::memcpy(N, m->normals.data(), sizeof(double) * 3 * k);
+    if (flag && k > 0) std::memcpy(flag, m->normal_flag.data(), k);
+    return np;
+}
+
+// one block's gradients G[3][512]; 0 when the block holds them, -1 otherwise
+int orc_read_grad(void *h, const int32_t *coord, double *G) {
+    Map *m = (Map *)h;
+    auto it = m->blocks.find({coord[0], coord[1], coord[2]});
+    if (it == m->blocks.end() || it->second.G.empty()) return -1;
+    std::memcpy(G, it->second.G.data(), sizeof(double) * 3 * BV);
+    return 0;
+}
+
+// d_i of Eq. (distance) for given psi, ray u, gradient g and normal N (has_n = 0: no normal)
+double orc_nonproj_distance(double psi, const double *u, const double *g, const double *N, int has_n) {
+    return nonprojective_distance(psi, u, g, has_n ? N : nullptr, nullptr);
+}
+
 void orc_set_bands(void *h, double delta_px, double eps_psi) {
     Map *m = (Map *)h;
     m->delta_px = delta_px;
@@ -762,7 +930,7 @@ int orc_write_block(void *h, const int32_t *coord, const double *D, const double
     Map *m = (Map *)h;
     I3 k{coord[0], coord[1], coord[2]};
     auto it = m->blocks.find(k);
-    if (it == m->blocks.end()) it = m->blocks.emplace(k, new_block(m->C)).first;
+    if (it == m->blocks.end()) it = m->blocks.emplace(k, new_block(m->C, m->dist_mode)).first;
     m->alloc.insert(k);
     Block &b = it->second;
     if (D) std::memcpy(b.D.data(), D, sizeof(double) * BV);
