@@ -73,7 +73,7 @@ typedef struct {
     double logp_floor;        /* lower bound of stored log-probabilities (default -30)   */
     double lik_floor;         /* lower bound of probability-vector entries (1e-6)        */
     int32_t storage;          /* 0: FP32 {D, W} and log-probabilities; 1: FP16 storage   */
-    int32_t reserved0;
+    int32_t distance_mode;    /* 0: projective psi; 1: non-projective d_i (see below)    */
     int64_t max_blocks;       /* block pool size (8^3 voxels each), at most 2^22             */
     int64_t hash_capacity;    /* hash slots, rounded up to a power of two                 */
     int64_t max_points;       /* largest scan accepted by integrate_scan                  */
@@ -81,6 +81,23 @@ typedef struct {
     int64_t mesh_vertex_capacity;    /* mesh arena sizes (vertices / triangles)          */
     int64_t mesh_triangle_capacity;
 } map_config;
+
+/* Non-projective distance (Sec. III-C.2, Eq. distance), distance_mode = 1:
+ * each scan's normal image N is built from the range image (pixel (u, v)
+ * back-projected along its ray at its range, with its (u, v - 1) and
+ * (u - 1, v) neighbours: N = (p1 - p) x (p2 - p) normalised, turned toward
+ * the sensor; none on the top row or next to a pixel without a return);
+ * every voxel keeps a unit gradient g_i, the weight-averaged normal of the
+ * pixels it projected to (12 B per voxel in FP32 storage, 6 B in FP16); the
+ * fused value is Gamma(d_i, tau) with
+ *   d_i = psi (|cos theta| - sin theta tan(alpha / 2)),
+ * theta the angle between the ray and g_i, alpha the signed angle between
+ * g_i and the pixel's normal (positive for a convex surface), which is the
+ * exact distance for a circular surface through the ray's end point and
+ * |cos theta| psi for a plane; the flat form where the pixel has no normal
+ * or cos alpha <= 0, and psi before the voxel's first normal.  The weight,
+ * the skip below -tau and the class-update gate stay on psi.  Needs
+ * max_pixels <= 2^23; not available to map_batch_* (MAP_ERR_ARG). */
 
 /* Device view of an extracted mesh (owned by the map; valid until the next
  * extract_mesh, integrate_scan or map_destroy on that map).
@@ -291,6 +308,11 @@ map_status map_get_blocks(map_t *map, int32_t *coords_host, int64_t cap, int64_t
 map_status map_read_blocks(map_t *map, const int32_t *coords_host, int64_t n, float *D, float *W,
                            float *logP, uint8_t *label, uint8_t *found);
 
+/* Read the gradients g_i of n blocks (distance_mode 1; MAP_ERR_STATE
+ * otherwise) into host G[n][3][512] (x, y, z planes, FP32 whatever the
+ * storage; zero before a voxel's first normal and for unallocated blocks). */
+map_status map_read_gradients(map_t *map, const int32_t *coords_host, int64_t n, float *G);
+
 /* Write n blocks from host arrays (allocating them when new): D, W
  * [n][512]; logP [n][C][512] or NULL (uniform).  The label plane is
  * recomputed as the argmax.  Marks nothing dirty (call map_remesh_all). */
@@ -305,7 +327,8 @@ map_status map_write_blocks(map_t *map, const int32_t *coords_host, int64_t n, c
  * less than the sum of its phases. */
 enum {
     MAP_PHASE_RESET = 0,      /* range-image and counter resets                               */
-    MAP_PHASE_POINTS = 1,     /* per point: range-image winner (Sec. III-C.1), band allocation */
+    MAP_PHASE_POINTS = 1,     /* per point: range-image winner (Sec. III-C.1), band allocation;
+                                 the normal image in the non-projective mode                  */
     MAP_PHASE_TSDF = 2,       /* projective TSDF update (Sec. III-C.2), re-mesh queue          */
     MAP_PHASE_SEMANTIC = 3,   /* Bayesian class fusion (Eq. bayesian_filter)                  */
     MAP_PHASE_MESH = 4,       /* incremental marching cubes                                   */

@@ -41,7 +41,7 @@ BV = 512
 
 class MapConfig(ctypes.Structure):
     _fields_ = [("voxel_size", D), ("truncation", D), ("n_classes", I32), ("weight_mode", I32),
-                ("p_hit", D), ("logp_floor", D), ("lik_floor", D), ("storage", I32), ("reserved0", I32),
+                ("p_hit", D), ("logp_floor", D), ("lik_floor", D), ("storage", I32), ("distance_mode", I32),
                 ("max_blocks", I64), ("hash_capacity", I64), ("max_points", I64), ("max_pixels", I64),
                 ("mesh_vertex_capacity", I64), ("mesh_triangle_capacity", I64)]
 
@@ -83,6 +83,7 @@ _SIGS = {
     "map_get_blocks": ([P, P, I64, P], I32),
     "map_read_blocks": ([P, P, I64, P, P, P, P, P], I32),
     "map_write_blocks": ([P, P, I64, P, P, P], I32),
+    "map_read_gradients": ([P, P, I64, P], I32),
     "map_last_error": ([P], ctypes.c_char_p),
     "map_profile_begin": ([P, I32], I32),
     "map_profile_end": ([P, P, P, P], I32),
@@ -337,6 +338,14 @@ def map_read_blocks(h, coords, n_classes, want_logp=True) -> dict:
     return out
 
 
+def map_read_gradients(h, coords) -> np.ndarray:
+    """Gradients g_i [n][3][512] of the listed blocks (non-projective maps)."""
+    c = np.ascontiguousarray(coords, np.int32).reshape(-1, 3)
+    G = np.zeros((len(c), 3, BV), np.float32)
+    _check(_lib.map_read_gradients(h, _np_ptr(c), len(c), _np_ptr(G)), h)
+    return G
+
+
 def map_write_blocks(h, coords, D, W, logP=None):
     c = np.ascontiguousarray(coords, np.int32).reshape(-1, 3)
     D = np.ascontiguousarray(D, np.float32)
@@ -437,7 +446,11 @@ def map_palette(n_classes) -> np.ndarray:
 class SemanticTSDF:
     """A map: ``SemanticTSDF(voxel_size, truncation, n_classes, **config)``."""
 
-    def __init__(self, voxel_size=0.1, truncation=0.3, n_classes=20, **cfg):
+    def __init__(self, voxel_size=0.1, truncation=0.3, n_classes=20, distance="projective", **cfg):
+        modes = {"projective": 0, "nonprojective": 1}
+        if distance not in modes:
+            raise ValueError(f"distance must be one of {sorted(modes)}")
+        cfg.setdefault("distance_mode", modes[distance])
         self.cfg = map_config_default(voxel_size=voxel_size, truncation=truncation, n_classes=n_classes, **cfg)
         self.h = map_create(self.cfg)
         self.n_classes = n_classes
@@ -476,6 +489,9 @@ class SemanticTSDF:
 
     def read_blocks(self, coords, want_logp=True):
         return map_read_blocks(self.h, coords, self.n_classes, want_logp)
+
+    def read_gradients(self, coords):
+        return map_read_gradients(self.h, coords)
 
     def write_block(self, coord, D, W, logP=None):
         map_write_blocks(self.h, np.asarray(coord).reshape(1, 3), np.asarray(D).reshape(1, BV),

@@ -102,6 +102,11 @@ struct ScanConst {
     const float *pts;
     const int32_t *labels;
     const float *probs;
+    // non-projective distance (Sec. III-C.2, Eq. distance): 0 off, 1 on
+    int dist_mode;
+    const float4 *row_dir;   // [H] beam v: {sin hi, sin lo, cos hi, cos lo} of its polar angle
+    const float4 *col_dir;   // [W] column u: {cos hi, cos lo, sin hi, sin lo} of its azimuth
+    float4 *nrm;             // [H*W] normal image, world frame; w = 1 where the pixel has a normal
 };
 
 // Device pointers of one map.
@@ -131,6 +136,8 @@ struct MapDev {
     long long av_cap, at_cap;
     DevState *st;
     float nu;
+    float *g32;          // non-projective mode: [slot][3][512] gradient g_i (x, y, z planes), FP32 storage
+    __half *g16;         //   the same in FP16 storage
 };
 
 // Per-frame scratch of one map.
@@ -167,6 +174,22 @@ __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, f
     e = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
     ph = __fadd_rn(p, e);
     pl = __fsub_rn(e, __fsub_rn(ph, p));
+}
+// sqrt(ah + al), ah > 0, as a pair: one Newton correction of the single-precision
+// root (Dekker 1971, double-length square root), the residual ah - s^2 exact by FMA
+__device__ __forceinline__ void df_sqrt(float ah, float al, float &sh, float &sl) {
+    const float s = __fsqrt_rn(ah);
+    const float r = __fadd_rn(__fmaf_rn(-s, s, ah), al);
+    const float c = __fdiv_rn(r, __fmul_rn(2.f, s));
+    sh = __fadd_rn(s, c);
+    sl = __fsub_rn(c, __fsub_rn(sh, s));
+}
+// a b - c d with one rounding error at most beyond the result's (Kahan's FMA scheme)
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+    const float w = __fmul_rn(c, d);
+    const float e = __fmaf_rn(-c, d, w);
+    const float f = __fmaf_rn(a, b, -w);
+    return __fadd_rn(f, e);
 }
 
 // Offset of class c of pool voxel vox (= slot * 512 + voxel index) in the log-probability array.

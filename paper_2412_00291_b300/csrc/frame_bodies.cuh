@@ -305,9 +305,117 @@ __device__ __forceinline__ int tsdf_pixel(const ScanConst &sc, int bx, int by, i
     return (v >= 0 && v < sc.H) ? v * sc.W + u : -1;
 }
 
+// ---------------------------------------------------------------------------
+// non-projective distance (Sec. III-C.2, Eq. distance)
+// ---------------------------------------------------------------------------
+template <bool F16>
+__device__ __forceinline__ float load_g(const MapDev &md, long long j) {
+    if (F16) return __half2float(md.g16[j]);
+    return md.g32[j];
+}
+template <bool F16>
+__device__ __forceinline__ void store_g(const MapDev &md, long long j, float v) {
+    if (F16) md.g16[j] = __float2half_rn(v);
+    else md.g32[j] = v;
+}
+
+// Back-projection of pixel (v, u) at its winner's range: r (from the winner
+// point, as a float pair) times the pixel's ray (float-pair tables), each
+// coordinate a float pair, so that neighbour differences keep full precision.
+__device__ __forceinline__ void backproject(const ScanConst &sc, unsigned long long win, int v, int u, float qh[3],
+                                            float ql[3]) {
+    const unsigned idx = (unsigned)(win & 0xffffffffu);
+    const float x = sc.pts[3 * (long long)idx], y = sc.pts[3 * (long long)idx + 1], z = sc.pts[3 * (long long)idx + 2];
+    float a, ae, b, be, c, ce, rh, rl;
+    two_prod(x, x, a, ae);
+    two_prod(y, y, b, be);
+    two_prod(z, z, c, ce);
+    df_add(a, ae, b, be, rh, rl);
+    df_add(rh, rl, c, ce, rh, rl);
+    df_sqrt(rh, rl, rh, rl);
+    const float4 rd = sc.row_dir[v], cd = sc.col_dir[u];
+    float dh, dl;
+    df_mul(rd.x, rd.y, cd.x, cd.y, dh, dl);     // sin(theta) cos(phi)
+    df_mul(rh, rl, dh, dl, qh[0], ql[0]);
+    df_mul(rd.x, rd.y, cd.z, cd.w, dh, dl);     // sin(theta) sin(phi)
+    df_mul(rh, rl, dh, dl, qh[1], ql[1]);
+    df_mul(rh, rl, rd.z, rd.w, qh[2], ql[2]);   // cos(theta)
+}
+
+// Normal image N at pixel p (Sec. III-C.2): with p_j the pixel's back-projected
+// point and p_j1, p_j2 those of pixels (u, v - 1) and (u - 1, v) (columns wrap),
+// N = (p_j1 - p_j) x (p_j2 - p_j) / |...|, turned toward the sensor and rotated
+// into the world frame.  No normal (w = 0) on the top row, next to a pixel
+// without a return, or for a vanishing cross product.
+__device__ __forceinline__ void normal_item(const ScanConst &sc, const unsigned long long *__restrict__ win, int p) {
+    const int v = p / sc.W, u = p - v * sc.W;
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (v > 0) {
+        const int u2 = u == 0 ? sc.W - 1 : u - 1;
+        const unsigned long long w0 = win[p], w1 = win[p - sc.W], w2 = win[v * sc.W + u2];
+        if (w0 != ~0ull && w1 != ~0ull && w2 != ~0ull) {
+            float qh[3], ql[3], ah[3], al[3], bh[3], bl[3], a[3], b[3];
+            backproject(sc, w0, v, u, qh, ql);
+            backproject(sc, w1, v - 1, u, ah, al);
+            backproject(sc, w2, v, u2, bh, bl);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float dh, dl;
+                df_add(ah[k], al[k], -qh[k], -ql[k], dh, dl);
+                a[k] = __fadd_rn(dh, dl);
+                df_add(bh[k], bl[k], -qh[k], -ql[k], dh, dl);
+                b[k] = __fadd_rn(dh, dl);
+            }
+            float c0 = diff_of_products(a[1], b[2], a[2], b[1]);
+            float c1 = diff_of_products(a[2], b[0], a[0], b[2]);
+            float c2 = diff_of_products(a[0], b[1], a[1], b[0]);
+            const float l2 = c0 * c0 + c1 * c1 + c2 * c2;
+            if (l2 > 0.f) {
+                float il = rsqrtf(l2);
+                if (c0 * qh[0] + c1 * qh[1] + c2 * qh[2] > 0.f) il = -il;   // face the sensor
+                c0 *= il;
+                c1 *= il;
+                c2 *= il;
+                // world frame: R N, R = (R^T)^T
+                out.x = sc.Rt[0] * c0 + sc.Rt[3] * c1 + sc.Rt[6] * c2;
+                out.y = sc.Rt[1] * c0 + sc.Rt[4] * c1 + sc.Rt[7] * c2;
+                out.z = sc.Rt[2] * c0 + sc.Rt[5] * c1 + sc.Rt[8] * c2;
+                out.w = 1.f;
+            }
+        }
+    }
+    sc.nrm[p] = out;
+}
+
+// d_i of Eq. (distance) for projective distance psi, unit ray u from the voxel
+// toward the sensor, gradient g (all zero: none yet) and the pixel's normal N
+// (N.w = 0: none): d = psi (|cos theta| - sin theta tan(alpha / 2)), theta the
+// angle between the ray and g, alpha the signed angle between g and N
+// (positive when g is turned from N toward the ray, a convex surface), so that
+// the distance is exact for a circular surface through the ray's end point;
+// the flat form |cos theta| psi without a normal or where cos alpha <= 0.
+// sin theta = |g x u|; sin alpha is g's component along the unit tangent
+// (u - (u.N) N) / |u - (u.N) N|; tan(alpha / 2) = sin alpha / (1 + cos alpha).
+__device__ __forceinline__ float nonproj_distance(float psi, float u0, float u1, float u2, float g0, float g1,
+                                                  float g2, float4 N) {
+    if (g0 == 0.f && g1 == 0.f && g2 == 0.f) return psi;
+    const float ct = fabsf(g0 * u0 + g1 * u1 + g2 * u2);
+    if (!(N.w > 0.f)) return ct * psi;
+    const float ca = g0 * N.x + g1 * N.y + g2 * N.z;
+    if (!(ca > 0.f)) return ct * psi;
+    const float c0 = g1 * u2 - g2 * u1, c1 = g2 * u0 - g0 * u2, c2 = g0 * u1 - g1 * u0;
+    const float st = sqrtf(c0 * c0 + c1 * c1 + c2 * c2);
+    const float un = u0 * N.x + u1 * N.y + u2 * N.z;
+    const float p0 = u0 - un * N.x, p1 = u1 - un * N.y, p2 = u2 - un * N.z;
+    const float l2 = p0 * p0 + p1 * p1 + p2 * p2;
+    if (!(l2 > 0.f)) return ct * psi;
+    const float sa = (g0 * p0 + g1 * p1 + g2 * p2) * rsqrtf(l2);
+    return psi * (ct - st * sa / (1.f + ca));
+}
+
 // A voxel of the truncation band awaiting the float-pair psi (see below).
 struct BandEntry {
-    int vi;          // voxel index within the block
+    int vi;          // voxel index within the block (bits 0-8); non-projective mode: the pixel in bits 9-31
     unsigned idx;    // the pixel's winner point
     float r;         // its range
     float D, W;      // the voxel's stored {D, W}
@@ -326,7 +434,7 @@ struct TsdfWarpSmem {
 // away from +-tau it decides the update exactly: beyond +tau (+1 mm) sdf = tau
 // and w = 1, below -tau (-1 mm) nothing.  Returns true for a voxel of the band
 // in between, which needs the float-pair psi (tsdf_band).
-template <bool F16>
+template <bool F16, bool DIST>
 __device__ __forceinline__ bool tsdf_fast(const ScanConst &sc, const MapDev &md, long long vox, int vi, int p,
                                           unsigned long long win, float2 dw, float rr2, float irr, long long &n_upd,
                                           unsigned &remesh) {
@@ -335,7 +443,8 @@ __device__ __forceinline__ bool tsdf_fast(const ScanConst &sc, const MapDev &md,
     const float r = __uint_as_float((unsigned)(win >> 32));
     const float psi = r - sc.nu * (rr2 * irr);
     if (psi < -tau - 1e-3f) return false;
-    if (psi <= tau + 1e-3f) return true;
+    // non-projective: d_i may fall inside the band whatever psi, every update takes the long path
+    if (DIST || psi <= tau + 1e-3f) return true;
     const float Wn = dw.y + 1.f;
     store_dw<F16>(md, vox, __fdividef(dw.y * dw.x + tau, Wn), Wn);
     ++n_upd;
@@ -347,11 +456,11 @@ __device__ __forceinline__ bool tsdf_fast(const ScanConst &sc, const MapDev &md,
 // (r^2 - rho^2) / (r + rho) with r^2 (from the winner point) and rho^2 as
 // unevaluated float pairs, the linear weight and the running average.
 // Returns true when the voxel also takes the class update.
-template <bool F16>
+template <bool F16, bool DIST>
 __device__ __forceinline__ bool tsdf_band(const ScanConst &sc, const MapDev &md, int slot, int bx, int by, int bz,
                                           const BandEntry &e, long long &n_upd, unsigned &remesh) {
     const float tau = sc.tau;
-    const int vi = e.vi, lx = vi & 7, ly = (vi >> 3) & 7, lz = vi >> 6;
+    const int vi = e.vi & (BV - 1), lx = vi & 7, ly = (vi >> 3) & 7, lz = vi >> 6;
     const float m0 = (float)(8 * bx + lx - sc.k[0]), m1 = (float)(8 * by + ly - sc.k[1]),
                 m2 = (float)(8 * bz + lz - sc.k[2]);
     const float x = sc.pts[3 * (long long)e.idx], y = sc.pts[3 * (long long)e.idx + 1],
@@ -382,9 +491,35 @@ __device__ __forceinline__ bool tsdf_band(const ScanConst &sc, const MapDev &md,
     df_mul(qh, ql, sc.nu2hi, sc.nu2lo, mh, ml);
     df_add(rh, rl, -mh, -ml, dh, dl);
     const float psi = __fdividef(dh + dl, e.r + mh * rsqrtf(mh));
-    const float sdf = fminf(psi, tau);
     const float w = sc.weight_mode == 0 ? fminf(fmaxf((psi + tau) * sc.inv_2tau, 0.f), 1.f) : 1.f;
     if (!(psi >= -tau && w > 0.f)) return false;
+    float sdf = fminf(psi, tau);
+    if (DIST) {
+        // gradient g_i: the weight-averaged normal of the pixels seen, renormalised
+        const long long gj = (long long)slot * 3 * BV + vi;
+        float g0 = load_g<F16>(md, gj), g1 = load_g<F16>(md, gj + BV), g2 = load_g<F16>(md, gj + 2 * BV);
+        const float4 N = sc.nrm[(unsigned)e.vi >> 9];
+        if (N.w > 0.f) {
+            const float s0 = __fmaf_rn(e.W, g0, w * N.x), s1 = __fmaf_rn(e.W, g1, w * N.y),
+                        s2 = __fmaf_rn(e.W, g2, w * N.z);
+            const float l2 = s0 * s0 + s1 * s1 + s2 * s2;
+            if (l2 > 0.f) {
+                const float il = rsqrtf(l2);
+                g0 = s0 * il;
+                g1 = s1 * il;
+                g2 = s2 * il;
+            }
+            store_g<F16>(md, gj, g0);
+            store_g<F16>(md, gj + BV, g1);
+            store_g<F16>(md, gj + 2 * BV, g2);
+        }
+        // unit ray from the voxel toward the sensor (world frame)
+        const float o0 = t0 + e0, o1 = t1 + e1, o2 = t2 + e2;
+        const float io = -rsqrtf(o0 * o0 + o1 * o1 + o2 * o2);
+        const float d = nonproj_distance(psi, o0 * io, o1 * io, o2 * io, g0, g1, g2, N);
+        // truncation Gamma(d, tau), both sides
+        sdf = d >= 0.f ? fminf(d, tau) : fmaxf(d, -tau);
+    }
     const float Wn = e.W + w;
     store_dw<F16>(md, (long long)slot * BV + vi, __fdividef(e.W * e.D + w * sdf, Wn), Wn);
     ++n_upd;
@@ -408,7 +543,7 @@ __device__ __forceinline__ void tsdf_list(bool sem, int vox, int idx, int2 *wbuf
 // truncation band are finished on the spot; band voxels are queued, and the
 // queue is worked off 32 at a time with every lane busy (they take the long
 // float-pair path, which would otherwise idle the rest of the warp).
-template <bool F16>
+template <bool F16, bool DIST = false>
 __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int h,
                                                 TsdfWarpSmem &T, long long &n_upd) {
     const int lane = threadIdx.x & 31;
@@ -422,11 +557,11 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
     if (lane >= 8 && lane < 15 && md.slot_frame[slot] == sc.frame) link_block(md, key, slot, lane - 7);
     unsigned remesh = 0;
     int wcount = 0, qn = 0;
-    auto enqueue = [&](bool band, int vi, unsigned long long win, float2 dw) {
+    auto enqueue = [&](bool band, int vi, unsigned long long win, float2 dw, int pix) {
         const unsigned mb = __ballot_sync(0xffffffffu, band);
         if (band) {
             BandEntry &e = T.band[qn + __popc(mb & lt)];
-            e.vi = vi;
+            e.vi = DIST ? (int)((unsigned)vi | ((unsigned)pix << 9)) : vi;
             e.idx = (unsigned)(win & 0xffffffffu);
             e.r = __uint_as_float((unsigned)(win >> 32));
             e.D = dw.x;
@@ -441,8 +576,8 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
         int vox = 0, idx = 0;
         if (lane < n) {
             const BandEntry e = T.band[lane];
-            sem = tsdf_band<F16>(sc, md, slot, bx, by, bz, e, n_upd, remesh);
-            vox = slot * BV + e.vi;
+            sem = tsdf_band<F16, DIST>(sc, md, slot, bx, by, bz, e, n_upd, remesh);
+            vox = slot * BV + (e.vi & (BV - 1));
             idx = (int)e.idx;
         }
         const bool keep = lane < qn - n;
@@ -464,11 +599,11 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
         const int pa = tsdf_pixel(sc, bx, by, bz, vi, ma0, ma1, ma2, ra, ia);
         const int pb = tsdf_pixel(sc, bx, by, bz, vi + 32, mb0, mb1, mb2, rb, ib);
         const unsigned long long wa = fd.win[pa < 0 ? 0 : pa], wb = fd.win[pb < 0 ? 0 : pb];
-        const bool ba = tsdf_fast<F16>(sc, md, va, vi, pa, wa, dwa, ra, ia, n_upd, remesh);
-        const bool bb = tsdf_fast<F16>(sc, md, vb, vi + 32, pb, wb, dwb, rb, ib, n_upd, remesh);
-        enqueue(ba, vi, wa, dwa);
+        const bool ba = tsdf_fast<F16, DIST>(sc, md, va, vi, pa, wa, dwa, ra, ia, n_upd, remesh);
+        const bool bb = tsdf_fast<F16, DIST>(sc, md, vb, vi + 32, pb, wb, dwb, rb, ib, n_upd, remesh);
+        enqueue(ba, vi, wa, dwa, pa);
         if (qn >= 32) drain(32);
-        enqueue(bb, vi + 32, wb, dwb);
+        enqueue(bb, vi + 32, wb, dwb, pb);
         if (qn >= 32) drain(32);
     }
     if (qn > 0) drain(qn);

@@ -97,7 +97,7 @@ __global__ void k_write_block(MapDev md, uint64_t key, const float *D, const flo
 }
 
 __global__ void k_read_blocks(MapDev md, const uint64_t *keys, int n, float *D, float *W, float *logP,
-                              uint8_t *label, uint8_t *found) {
+                              uint8_t *label, uint8_t *found, float *G) {
     const int b = blockIdx.x;
     if (b >= n) return;
     __shared__ int s_slot;
@@ -138,6 +138,17 @@ __global__ void k_read_blocks(MapDev md, const uint64_t *keys, int n, float *D, 
                 logP[((long long)b * md.C + c) * BV + v] = lp;
             }
         }
+        if (G) {
+            // gradient planes of the non-projective mode, [b][3][512]
+            for (int k = 0; k < 3; ++k) {
+                float g = 0.f;
+                if (slot >= 0) {
+                    const long long j = ((long long)slot * 3 + k) * BV + v;
+                    g = md.storage == 0 ? md.g32[j] : __half2float(md.g16[j]);
+                }
+                G[((long long)b * 3 + k) * BV + v] = g;
+            }
+        }
     }
 }
 
@@ -172,8 +183,8 @@ void launch_write_block(const MapDev &md, uint64_t key, const float *D, const fl
     k_write_block<<<1, 256, 0, s>>>(md, key, D, W, logP);
 }
 void launch_read_blocks(const MapDev &md, const uint64_t *keys, int n, float *D, float *W, float *logP,
-                        uint8_t *label, uint8_t *found, cudaStream_t s) {
-    if (n > 0) k_read_blocks<<<n, 256, 0, s>>>(md, keys, n, D, W, logP, label, found);
+                        uint8_t *label, uint8_t *found, float *G, cudaStream_t s) {
+    if (n > 0) k_read_blocks<<<n, 256, 0, s>>>(md, keys, n, D, W, logP, label, found, G);
 }
 void launch_collect_blocks(const MapDev &md, int32_t *coords, unsigned long long *count, cudaStream_t s) {
     k_collect_blocks<<<1024, 256, 0, s>>>(md, coords, count);

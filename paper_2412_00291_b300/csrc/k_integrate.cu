@@ -18,11 +18,21 @@
 // unevaluated float pairs, and the voxel's offset from the sensor carried
 // in voxel units as integer + float pair, so that a 100 m range costs no
 // absolute accuracy near the surface.
+//
+// Non-projective mode (Sec. III-C.2, Eq. distance): k_normals first builds
+// the scan's normal image from the range image; each updated voxel then
+// folds its pixel's normal into its gradient g_i and fuses Gamma(d_i, tau)
+// instead of min(psi, tau) (weight and skip still on psi).
 #include "frame_bodies.cuh"
 
 namespace stsdf {
 
-template <bool F16>
+__global__ void __launch_bounds__(256) k_normals(ScanConst sc, FrameDev fd) {
+    const int np = sc.H * sc.W;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) normal_item(sc, fd.win, p);
+}
+
+template <bool F16, bool DIST>
 __global__ void __launch_bounds__(256, 4) k_tsdf(ScanConst sc, MapDev md, FrameDev fd) {
     __shared__ TsdfWarpSmem s_w[8];   // per-warp class-update entries and band queue
     TsdfWarpSmem &tw = s_w[threadIdx.x >> 5];
@@ -31,7 +41,8 @@ __global__ void __launch_bounds__(256, 4) k_tsdf(ScanConst sc, MapDev md, FrameD
     long long n_upd = 0;
     unsigned long long nt = *(volatile unsigned long long *)&fd.ctr[CT_TOUCHED];
     if (nt > (unsigned long long)md.max_blocks) nt = md.max_blocks;
-    for (long long li = warp; li < (long long)nt; li += nwarps) tsdf_block_warp<F16>(sc, md, fd, fd.touched[li], tw, n_upd);
+    for (long long li = warp; li < (long long)nt; li += nwarps)
+        tsdf_block_warp<F16, DIST>(sc, md, fd, fd.touched[li], tw, n_upd);
     long long cnt[1] = {n_upd};
     cta_count<1>(fd.ctr, {CT_UPD}, cnt);
 }
@@ -52,9 +63,10 @@ static int occupancy(K kernel) {
     return n > 0 ? n : 1;
 }
 
-int integrate_blocks_per_sm(int storage, int C) {
+int integrate_blocks_per_sm(int storage, int C, int dist_mode) {
     (void)C;
-    return storage == 0 ? occupancy(k_tsdf<false>) : occupancy(k_tsdf<true>);
+    if (dist_mode) return storage == 0 ? occupancy(k_tsdf<false, true>) : occupancy(k_tsdf<true, true>);
+    return storage == 0 ? occupancy(k_tsdf<false, false>) : occupancy(k_tsdf<true, false>);
 }
 
 int semantic_blocks_per_sm(int storage, int C) {
@@ -63,8 +75,20 @@ int semantic_blocks_per_sm(int storage, int C) {
 }
 
 void launch_integrate(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s) {
-    if (md.storage == 0) k_tsdf<false><<<grid, 256, 0, s>>>(sc, md, fd);
-    else k_tsdf<true><<<grid, 256, 0, s>>>(sc, md, fd);
+    if (sc.dist_mode) {
+        if (md.storage == 0) k_tsdf<false, true><<<grid, 256, 0, s>>>(sc, md, fd);
+        else k_tsdf<true, true><<<grid, 256, 0, s>>>(sc, md, fd);
+    } else {
+        if (md.storage == 0) k_tsdf<false, false><<<grid, 256, 0, s>>>(sc, md, fd);
+        else k_tsdf<true, false><<<grid, 256, 0, s>>>(sc, md, fd);
+    }
+}
+
+void launch_normals(const ScanConst &sc, const FrameDev &fd, cudaStream_t s) {
+    const int np = sc.H * sc.W;
+    int grid = (np + 255) / 256;
+    if (grid > 148 * 8) grid = 148 * 8;
+    k_normals<<<grid, 256, 0, s>>>(sc, fd);
 }
 
 void launch_semantic(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s) {

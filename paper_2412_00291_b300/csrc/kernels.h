@@ -12,14 +12,17 @@ void launch_init_pool(const MapDev &md, cudaStream_t s);
 void launch_link_all(const MapDev &md, cudaStream_t s);
 void launch_write_block(const MapDev &md, uint64_t key, const float *D, const float *W, const float *logP,
                         cudaStream_t s);
+// G (may be null): gradient planes [n][3][512] of the non-projective mode
 void launch_read_blocks(const MapDev &md, const uint64_t *keys, int n, float *D, float *W, float *logP,
-                        uint8_t *label, uint8_t *found, cudaStream_t s);
+                        uint8_t *label, uint8_t *found, float *G, cudaStream_t s);
 void launch_collect_blocks(const MapDev &md, int32_t *coords, unsigned long long *count, cudaStream_t s);
 
 // k_integrate.cu: projective TSDF + Bayesian semantic fusion (Sec. III-C.2, III-C.3)
 void launch_integrate(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s);
 void launch_semantic(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s);
-int integrate_blocks_per_sm(int storage, int C);
+// non-projective mode: the scan's normal image (after launch_points, before launch_integrate)
+void launch_normals(const ScanConst &sc, const FrameDev &fd, cudaStream_t s);
+int integrate_blocks_per_sm(int storage, int C, int dist_mode);
 int semantic_blocks_per_sm(int storage, int C);
 
 // k_mesh.cu: incremental marching cubes and mesh gathering

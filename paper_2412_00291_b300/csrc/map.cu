@@ -66,6 +66,15 @@ struct map_t {
     // class palette (rgb per class, on the device as uchar4)
     uint8_t palette[256 * 3];
     uchar4 *pal_dev = nullptr;
+    // non-projective mode: pixel-ray tables (float pairs) for the current
+    // intrinsics, uploaded from a pinned copy when the intrinsics change
+    float4 *row_dir = nullptr, *col_dir = nullptr;
+    float4 *nrm = nullptr;           // [max_pixels] the scan's normal image
+    float4 *h_dir = nullptr;
+    long long h_dir_cap = 0;
+    cudaEvent_t ev_dir = nullptr;
+    lidar_intrinsics dir_for{};
+    bool dir_valid = false;
     // alignment scratch
     double *gn_T = nullptr, *gn_acc = nullptr;
     double *qb_part = nullptr;   // pose-gradient partial sums of query_sdf_backward
@@ -136,7 +145,8 @@ static void free_all(map_t *m) {
                     m->fd.touched, m->fd.dirty, m->fd.sem_list, m->fd.ctr, m->gb.voff, m->gb.toff, m->gb.bsum_v, m->gb.bsum_t,
                     m->gb.totals, m->stage_pts[0], m->stage_lab[0], m->stage_probs[0], m->stage_pts[1],
                     m->stage_lab[1], m->stage_probs[1], m->out_pos, m->out_col,
-                    m->out_keys, m->out_tri, m->out_anchor, m->gn_T, m->gn_acc, m->qb_part, m->pal_dev};
+                    m->out_keys, m->out_tri, m->out_anchor, m->gn_T, m->gn_acc, m->qb_part, m->pal_dev,
+                    m->md.g32, m->md.g16, m->nrm, m->row_dir, m->col_dir};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (m->h_ctr) cudaFreeHost(m->h_ctr);
@@ -144,6 +154,8 @@ static void free_all(map_t *m) {
     if (m->h_totals) cudaFreeHost(m->h_totals);
     if (m->h_ring) cudaFreeHost(m->h_ring);
     if (m->h_ring_ctr) cudaFreeHost(m->h_ring_ctr);
+    if (m->h_dir) cudaFreeHost(m->h_dir);
+    if (m->ev_dir) cudaEventDestroy(m->ev_dir);
     for (int b = 0; b < 2; ++b) {
         if (m->ev_copied[b]) cudaEventDestroy(m->ev_copied[b]);
         if (m->ev_used[b]) cudaEventDestroy(m->ev_used[b]);
@@ -168,8 +180,9 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     if (!(c.voxel_size > 0.0) || !(c.truncation > 0.0) || c.truncation > 15.0 * c.voxel_size)
         return fail(nullptr, MAP_ERR_ARG, "need 0 < truncation <= 15 voxel_size");
     if (c.n_classes < 2 || c.n_classes > 64) return fail(nullptr, MAP_ERR_ARG, "n_classes must be in [2, 64]");
-    if (c.weight_mode < 0 || c.weight_mode > 1 || c.storage < 0 || c.storage > 1)
-        return fail(nullptr, MAP_ERR_ARG, "bad weight_mode or storage");
+    if (c.weight_mode < 0 || c.weight_mode > 1 || c.storage < 0 || c.storage > 1 || c.distance_mode < 0 ||
+        c.distance_mode > 1)
+        return fail(nullptr, MAP_ERR_ARG, "bad weight_mode, storage or distance_mode");
     if (!(c.p_hit > 0.0 && c.p_hit < 1.0) || !(c.lik_floor > 0.0))
         return fail(nullptr, MAP_ERR_ARG, "need 0 < p_hit < 1 and lik_floor > 0");
     if (c.max_blocks < 1 || c.max_blocks > (1ll << 22) || c.hash_capacity < 2 || c.max_points < 1 ||
@@ -177,6 +190,8 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
         c.mesh_triangle_capacity < 1 || c.mesh_vertex_capacity > (1ll << 31) - 1 ||
         c.mesh_triangle_capacity > (1ll << 31) - 1)
         return fail(nullptr, MAP_ERR_ARG, "capacity out of range");
+    if (c.distance_mode == 1 && c.max_pixels > (1ll << 23))
+        return fail(nullptr, MAP_ERR_ARG, "non-projective mode: max_pixels <= 2^23");
     if (map_mc_table(nullptr) != 0) return fail(nullptr, MAP_ERR_STATE, "marching-cubes table generation failed");
 
     m = new map_t();
@@ -225,6 +240,13 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
         ALLOC(md.lp16, nvox * md.CP);
     }
     ALLOC(md.label, nvox);
+    if (c.distance_mode == 1) {
+        if (c.storage == 0) ALLOC(md.g32, nvox * 3);
+        else ALLOC(md.g16, nvox * 3);
+        ALLOC(m->nrm, c.max_pixels);
+        ALLOC(m->row_dir, c.max_pixels);
+        ALLOC(m->col_dir, c.max_pixels);
+    }
     ALLOC(md.slot_key, nb);
     ALLOC(md.slot_frame, nb);
     ALLOC(md.nbr, nb * 16);
@@ -277,7 +299,8 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
         cudaEventCreateWithFlags(&m->ev_used[1], cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev_dir, cudaEventDisableTiming) != cudaSuccess) {
         free_all(m);
         delete m;
         return fail(nullptr, MAP_ERR_CUDA, "stream / event creation failed");
@@ -291,6 +314,9 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     cudaMemsetAsync(md.dstamp_slot, 0xFF, nb * sizeof(int), s);
     cudaMemsetAsync(md.slot_frame, 0xFF, nb * sizeof(int), s);
     cudaMemsetAsync(md.nbr, 0xFF, nb * 16 * sizeof(int), s);
+    // no gradient before a voxel's first normal
+    if (md.g32) cudaMemsetAsync(md.g32, 0, (size_t)nvox * 3 * sizeof(float), s);
+    if (md.g16) cudaMemsetAsync(md.g16, 0, (size_t)nvox * 3 * sizeof(__half), s);
     {
         DevState init;
         std::memset(&init, 0, sizeof(init));
@@ -326,7 +352,7 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    m->grid_integrate = sms * integrate_blocks_per_sm(c.storage, c.n_classes);
+    m->grid_integrate = sms * integrate_blocks_per_sm(c.storage, c.n_classes, c.distance_mode);
     m->grid_semantic = 4 * sms * semantic_blocks_per_sm(c.storage, c.n_classes);
     m->grid_mesh = sms * mesh_blocks_per_sm();
     e = cudaStreamSynchronize(s);
@@ -346,6 +372,51 @@ extern "C" map_status map_destroy(map_t *m) {
     cudaDeviceSynchronize();
     free_all(m);
     delete m;
+    return MAP_OK;
+}
+
+// Pixel-ray tables of the non-projective mode for intrinsics L (Sec. III-C.1
+// read backwards: beam v at polar angle theta0 + v dtheta, column u at azimuth
+// pi - u dphi), each sine and cosine an FP64 value split into a float pair.
+// Uploaded when the intrinsics differ from the last upload's; the pinned copy
+// is rewritten only after that upload has completed.
+static map_status upload_pixel_rays(map_t *m, const lidar_intrinsics *L) {
+    if (m->dir_valid && m->dir_for.H == L->H && m->dir_for.W == L->W && m->dir_for.fov_up == L->fov_up &&
+        m->dir_for.fov_down == L->fov_down)
+        return MAP_OK;
+    CU(cudaEventSynchronize(m->ev_dir));
+    const long long need = (long long)L->H + L->W;
+    if (need > m->h_dir_cap) {
+        if (m->h_dir) cudaFreeHost(m->h_dir);
+        m->h_dir = nullptr;
+        m->h_dir_cap = 0;
+        if (cudaMallocHost(&m->h_dir, need * sizeof(float4)) != cudaSuccess)
+            return fail(m, MAP_ERR_NOMEM, "pinned host allocation failed");
+        m->h_dir_cap = need;
+    }
+    auto split = [](double x, float &hi, float &lo) {
+        hi = (float)x;
+        lo = (float)(x - (double)hi);
+    };
+    const double theta0 = M_PI / 2.0 - L->fov_up, dtheta = (L->fov_up - L->fov_down) / (L->H - 1);
+    const double dphi = 2.0 * M_PI / L->W;
+    for (int v = 0; v < L->H; ++v) {
+        const double th = theta0 + (double)v * dtheta;
+        float4 &q = m->h_dir[v];
+        split(std::sin(th), q.x, q.y);
+        split(std::cos(th), q.z, q.w);
+    }
+    for (int u = 0; u < L->W; ++u) {
+        const double ph = M_PI - (double)u * dphi;
+        float4 &q = m->h_dir[L->H + u];
+        split(std::cos(ph), q.x, q.y);
+        split(std::sin(ph), q.z, q.w);
+    }
+    CU(cudaMemcpyAsync(m->row_dir, m->h_dir, L->H * sizeof(float4), cudaMemcpyHostToDevice, m->cp));
+    CU(cudaMemcpyAsync(m->col_dir, m->h_dir + L->H, L->W * sizeof(float4), cudaMemcpyHostToDevice, m->cp));
+    CU(cudaEventRecord(m->ev_dir, m->cp));
+    m->dir_for = *L;
+    m->dir_valid = true;
     return MAP_OK;
 }
 
@@ -413,6 +484,14 @@ static map_status make_scan_const(map_t *m, const lidar_intrinsics *L, int64_t n
     sc.frame = m->frame;
     sc.has_probs = has_probs;
     sc.probs_vec4 = 0;
+    if (m->cfg.distance_mode == 1) {
+        map_status st = upload_pixel_rays(m, L);
+        if (st != MAP_OK) return st;
+        sc.dist_mode = 1;
+        sc.row_dir = m->row_dir;
+        sc.col_dir = m->col_dir;
+        sc.nrm = m->nrm;
+    }
     return MAP_OK;
 }
 
@@ -501,6 +580,11 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     CU(cudaMemsetAsync(m->fd.ctr, 0, CT_COUNT * sizeof(unsigned long long), s));
     if (ev) CU(cudaEventRecord(ev[1], s));
     launch_points(pts, sc, m->md, m->fd, s);
+    if (sc.dist_mode) {
+        CU(cudaStreamWaitEvent(s, m->ev_dir, 0));   // pixel-ray tables uploaded
+        launch_normals(sc, m->fd, s);
+        m->launches += 1;
+    }
     if (ev) CU(cudaEventRecord(ev[2], s));
     launch_integrate(sc, m->md, m->fd, m->grid_integrate, s);
     if (ev) CU(cudaEventRecord(ev[3], s));
@@ -764,7 +848,7 @@ extern "C" map_status map_read_blocks(map_t *m, const int32_t *coords, int64_t n
             const int cnt = (int)std::min<int64_t>(65535, n - off);
             launch_read_blocks(m->md, dk + off, cnt, dD ? dD + off * BV : nullptr, dW ? dW + off * BV : nullptr,
                                dL ? dL + off * BV * m->C : nullptr, dlab ? dlab + off * BV : nullptr,
-                               dfound ? dfound + off : nullptr, 0);
+                               dfound ? dfound + off : nullptr, nullptr, 0);
         }
         e = cudaGetLastError();
     }
@@ -776,6 +860,31 @@ extern "C" map_status map_read_blocks(map_t *m, const int32_t *coords, int64_t n
     void *ptrs[] = {dk, dD, dW, dL, dlab, dfound};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (e != cudaSuccess) return fail(m, MAP_ERR_CUDA, cudaGetErrorString(e));
+    return MAP_OK;
+}
+
+extern "C" map_status map_read_gradients(map_t *m, const int32_t *coords, int64_t n, float *G) {
+    if (!m || n < 0 || (n > 0 && (!coords || !G))) return fail(m, MAP_ERR_ARG, "bad arguments");
+    if (m->cfg.distance_mode != 1) return fail(m, MAP_ERR_STATE, "the map keeps no gradients (projective mode)");
+    if (n == 0) return MAP_OK;
+    std::vector<uint64_t> keys(n);
+    for (int64_t i = 0; i < n; ++i) keys[i] = pack_block(coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]);
+    uint64_t *dk = nullptr;
+    float *dG = nullptr;
+    cudaError_t e = cudaMalloc(&dk, n * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&dG, (size_t)n * 3 * BV * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(dk, keys.data(), n * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        for (int64_t off = 0; off < n; off += 65535) {
+            const int cnt = (int)std::min<int64_t>(65535, n - off);
+            launch_read_blocks(m->md, dk + off, cnt, nullptr, nullptr, nullptr, nullptr, nullptr, dG + off * 3 * BV, 0);
+        }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(G, dG, (size_t)n * 3 * BV * sizeof(float), cudaMemcpyDeviceToHost);
+    if (dk) cudaFree(dk);
+    if (dG) cudaFree(dG);
     if (e != cudaSuccess) return fail(m, MAP_ERR_CUDA, cudaGetErrorString(e));
     return MAP_OK;
 }
@@ -888,8 +997,11 @@ extern "C" map_status map_batch_create(map_t *const *maps, int32_t n_maps, int32
     map_batch_t *b = nullptr;
     if (!maps || !out || n_maps < 1 || n_maps > BATCH_MAX)
         return bfail(nullptr, MAP_ERR_ARG, "need 1 <= n_maps <= 48 and non-null pointers");
-    for (int i = 0; i < n_maps; ++i)
+    for (int i = 0; i < n_maps; ++i) {
         if (!maps[i]) return bfail(nullptr, MAP_ERR_ARG, "null map in batch");
+        if (maps[i]->cfg.distance_mode != 0)
+            return bfail(nullptr, MAP_ERR_ARG, "batched integration takes projective-distance maps only");
+    }
     int coop = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
