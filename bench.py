@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["loop64", "line16", "streams32", "align1km"], default="loop64")
     ap.add_argument("--storage", choices=["fp32", "fp16"], default="fp32")
+    ap.add_argument("--distance", choices=["projective", "nonprojective"], default="projective",
+                    help="fused distance: projective psi, or the non-projective d_i (normal image, gradients)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512)
@@ -91,14 +93,17 @@ def frames_for(w, n, nthreads=0):
 # --------------------------------------------------------------------------
 # algorithmic bytes per kernel (HBM traffic the method must do), per frame
 # --------------------------------------------------------------------------
-def algorithmic_bytes(st, n_points, H, W, C, s):
+def algorithmic_bytes(st, n_points, H, W, C, s, nonproj=False):
     """HBM bytes each kernel of one scan must move, from that scan's counters.
 
     st: per-scan counters (MAP_STAT_* order); s: bytes per stored scalar (4 FP32, 2 FP16).
     points:   the points (12 B each); winners and hash probes stay in L2.
+              Non-projective mode: plus the normal image written (16 B per pixel).
     tsdf:     {D, W} read and written (2 x 2s B) per updated voxel, an 8 B
               list entry per semantic voxel, a 16 B work record per touched block
               (range-image winners and winner points are L2 reads).
+              Non-projective mode: plus the gradient g_i read and written
+              (2 x 3s B) per updated voxel (the normal image is an L2 read).
     semantic: C log-probabilities read and written (2 C s B), the label byte
               and the 8 B list entry per semantically updated voxel (the
               winners' class inputs are L2 reads).
@@ -109,8 +114,8 @@ def algorithmic_bytes(st, n_points, H, W, C, s):
     upd, sem, touched, dirty, mv, mt = st[4], st[5], st[2], st[6], st[7], st[8]
     return {
         "reset": H * W * 8,
-        "points": n_points * 12,
-        "tsdf": upd * 2 * (2 * s) + sem * 8 + touched * 16,
+        "points": n_points * 12 + (H * W * 16 if nonproj else 0),
+        "tsdf": upd * 2 * (2 * s) + sem * 8 + touched * 16 + (upd * 2 * 3 * s if nonproj else 0),
         "semantic": sem * (2 * C * s + 1 + 8),
         "mesh": dirty * (512 * 2 * s + 16) + mv * 24 + mt * 8,
     }
@@ -257,11 +262,11 @@ def fp16_report(P, w, lid, m16, make_step, n_frames, cfg, dev):
             "mesh_vertex_p99_err_m": float(np.percentile(dp, 99)) if len(common) else 0.0}
 
 
-def cpu_baseline(w, budget_s=15.0, max_frames=8, col_stride=1):
+def cpu_baseline(w, budget_s=15.0, max_frames=8, col_stride=1, distance="projective"):
     """The FP64 oracle as it stands, on all host cores, over the first scans of the workload."""
     import oracle
     nthreads = os.cpu_count() or 1
-    m = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    m = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes, distance=distance)
     done_pts, secs, k = 0, 0.0, 0
     for f in frames_for(w, max_frames):
         pts, pr, lab = f.points, f.probs, f.labels
@@ -289,7 +294,7 @@ def run_reference(args, rank, world):
     import oracle
     w = workload(args.workload)
     nthreads = os.cpu_count() or 1
-    m = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    m = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes, distance=args.distance)
     stride = 8
     times, pts_done = [], 0
     for k, f in enumerate(frames_for(w, args.warmup + args.steps)):
@@ -309,7 +314,8 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / max(1, len(times)), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": w.name, "sample": f"every {stride}th column of each scan", "threads": nthreads},
+            "config": {"workload": w.name, "sample": f"every {stride}th column of each scan", "threads": nthreads,
+                       "distance": args.distance},
             "cpu_baseline": {"value": v, "unit": "points/s", "cores": nthreads, "kind": "oracle",
                              "sample": f"{len(times)} scans of {w.name}, every {stride}th column"},
             "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -346,7 +352,8 @@ def run_ours(args, rank, world, local_rank):
     t_gen = time.perf_counter() - t_gen
     storage = 0 if args.storage == "fp32" else 1
     s_bytes = 4 if storage == 0 else 2
-    cfg = {}
+    nonproj = args.distance == "nonprojective"
+    cfg = {"distance_mode": 1 if nonproj else 0}
     if args.max_blocks:
         cfg["max_blocks"] = args.max_blocks
         cfg["hash_capacity"] = 4 * args.max_blocks
@@ -414,7 +421,7 @@ def run_ours(args, rank, world, local_rank):
     for j, name in enumerate(PHASES):
         if name == "reset":
             continue
-        bytes_f = np.array([algorithmic_bytes(fs, n_points, L.H, L.W, C, s_bytes)[name] for fs in fstats], float)
+        bytes_f = np.array([algorithmic_bytes(fs, n_points, L.H, L.W, C, s_bytes, nonproj)[name] for fs in fstats], float)
         t = phase_ms[:, j].astype(float)
         per_kernel[name] = {"ms_mean": float(t.mean()), "share": float(t.sum() / phase_ms.sum()),
                             "bytes_mean": float(bytes_f.mean()),
@@ -422,7 +429,7 @@ def run_ours(args, rank, world, local_rank):
     # k_semantic and k_mesh run concurrently after k_tsdf: the stage lasts max of the two
     js, jm = PHASES.index("semantic"), PHASES.index("mesh")
     stage_t = np.maximum(phase_ms[:, js], phase_ms[:, jm]).astype(float)
-    stage_b = np.array([sum(algorithmic_bytes(fs, n_points, L.H, L.W, C, s_bytes)[k] for k in ("semantic", "mesh"))
+    stage_b = np.array([sum(algorithmic_bytes(fs, n_points, L.H, L.W, C, s_bytes, nonproj)[k] for k in ("semantic", "mesh"))
                         for fs in fstats], float)
     stage = {"ms_mean": float(stage_t.mean()), "bytes_mean": float(stage_b.mean()),
              "gbs": float(stage_b.sum() / (stage_t.sum() * 1e-3) / 1e9)}
@@ -433,7 +440,7 @@ def run_ours(args, rank, world, local_rank):
             "nominal_peak": 7700.0, "frac_nominal": ach / 7700.0,
             "peak_source": f"{peak_kind} hbm_gbs", "traffic": tr["bytes_per_launch"] if tr else None,
             "algorithmic_bytes_per_launch": per_kernel[dom]["bytes_mean"]}
-    frame_bytes = float(np.mean([sum(algorithmic_bytes(fs, n_points, L.H, L.W, C, s_bytes).values())
+    frame_bytes = float(np.mean([sum(algorithmic_bytes(fs, n_points, L.H, L.W, C, s_bytes, nonproj).values())
                                  for fs in fstats]))
     # --- end to end through the host-buffer entry point ----------------------
     # Every step: the scan's inputs from pinned host memory (H->D), the scan,
@@ -473,7 +480,7 @@ def run_ours(args, rank, world, local_rank):
     # --- CPU baseline: the oracle on the host cores --------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w)
+        cpu = cpu_baseline(w, distance=args.distance)
     if rank != 0:
         return
     clocks = clk.summary()
@@ -484,7 +491,7 @@ def run_ours(args, rank, world, local_rank):
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp32" if storage == 0 else "fp16-storage/fp32-math", "data": "synthetic",
         "config": {"workload": w.name, "points_per_scan": n_points, "voxel_size": w.voxel_size,
-                   "truncation": w.truncation, "n_classes": C, "labels": w.label_mode,
+                   "truncation": w.truncation, "n_classes": C, "labels": w.label_mode, "distance": args.distance,
                    "l2": f"flushed ({args.flush_mb} MB write) before every timed scan, outside its events",
                    "ms_median": float(np.median(step_ms)), "ms_p95": float(np.percentile(step_ms, 95)),
                    "bracketed_wall_s_incl_flush": t_wall, "parallelism": f"replicas x{world}",
