@@ -262,9 +262,9 @@ __device__ __forceinline__ float atan2_poly(float y, float x) {
     const float ax = fabsf(x), ay = fabsf(y);
     const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
     const float t = mx > 0.f ? __fdividef(mn, mx) : 0.f;
-    float a = t * atan_p(t * t);
-    if (ay > ax) a = 1.57079632679489662f - a;
-    if (x < 0.f) a = PI_F - a;
+    const float p = atan_p(__fmul_rn(t, t));
+    float a = ay > ax ? __fmaf_rn(-t, p, 1.57079632679489662f) : __fmul_rn(t, p);
+    if (x < 0.f) a = __fsub_rn(PI_F, a);
     return copysignf(a, y);
 }
 
@@ -272,7 +272,7 @@ __device__ __forceinline__ float atan2_poly(float y, float x) {
 // |c| <= 1/2 (error below 3e-7 rad), acosf beyond.
 __device__ __forceinline__ float acos_poly(float c) {
     if (fabsf(c) > 0.5f) return acosf(c);
-    return 1.57079632679489662f - c * asin_q(c * c);
+    return __fmaf_rn(-c, asin_q(__fmul_rn(c, c)), 1.57079632679489662f);
 }
 
 // Pixel of voxel vi of block (bx, by, bz) (Sec. III-C.1), or -1 outside the
@@ -285,21 +285,24 @@ __device__ __forceinline__ int tsdf_pixel(const ScanConst &sc, int bx, int by, i
     m0 = (float)(8 * bx + lx - sc.k[0]);
     m1 = (float)(8 * by + ly - sc.k[1]);
     m2 = (float)(8 * bz + lz - sc.k[2]);
-    const float s0 = m0 - sc.fhi[0], s1 = m1 - sc.fhi[1], s2 = m2 - sc.fhi[2];
+    // (every rounding is explicit here and in the update bodies below, so
+    // that each kernel that inlines them computes the same bits)
+    const float s0 = __fsub_rn(m0, sc.fhi[0]), s1 = __fsub_rn(m1, sc.fhi[1]), s2 = __fsub_rn(m2, sc.fhi[2]);
     // direction in the LiDAR frame (scale-free) -> pixel
-    const float x0 = sc.Rt[0] * s0 + sc.Rt[1] * s1 + sc.Rt[2] * s2;
-    const float x1 = sc.Rt[3] * s0 + sc.Rt[4] * s1 + sc.Rt[5] * s2;
-    const float x2 = sc.Rt[6] * s0 + sc.Rt[7] * s1 + sc.Rt[8] * s2;
-    rr2 = x0 * x0 + x1 * x1 + x2 * x2;
+    const float x0 = __fmaf_rn(sc.Rt[2], s2, __fmaf_rn(sc.Rt[1], s1, __fmul_rn(sc.Rt[0], s0)));
+    const float x1 = __fmaf_rn(sc.Rt[5], s2, __fmaf_rn(sc.Rt[4], s1, __fmul_rn(sc.Rt[3], s0)));
+    const float x2 = __fmaf_rn(sc.Rt[8], s2, __fmaf_rn(sc.Rt[7], s1, __fmul_rn(sc.Rt[6], s0)));
+    rr2 = __fmaf_rn(x2, x2, __fmaf_rn(x1, x1, __fmul_rn(x0, x0)));
     irr = 0.f;
     if (!(rr2 > 0.f)) return -1;
     irr = rsqrtf(rr2);
     // (polynomial atan2 / acos: their errors, < 5e-7 rad, stay far below the
     // 1e-3-pixel margin within which FP32 and FP64 pixel choices may differ)
-    const float uc = (PI_F - atan2_poly(x1, x0)) * sc.inv_dphi;
-    const float vc = (acos_poly(fminf(fmaxf(x2 * irr, -1.f), 1.f)) - sc.theta0) * sc.inv_dtheta;
-    int u = (int)floorf(uc + 0.5f);
-    const int v = (int)floorf(vc + 0.5f);
+    const float uc = __fmul_rn(__fsub_rn(PI_F, atan2_poly(x1, x0)), sc.inv_dphi);
+    const float vc = __fmul_rn(__fsub_rn(acos_poly(fminf(fmaxf(__fmul_rn(x2, irr), -1.f), 1.f)), sc.theta0),
+                               sc.inv_dtheta);
+    int u = (int)floorf(__fadd_rn(uc, 0.5f));
+    const int v = (int)floorf(__fadd_rn(vc, 0.5f));
     if (u >= sc.W) u -= sc.W;
     if (u < 0) u += sc.W;
     return (v >= 0 && v < sc.H) ? v * sc.W + u : -1;
@@ -441,12 +444,12 @@ __device__ __forceinline__ bool tsdf_fast(const ScanConst &sc, const MapDev &md,
     if (p < 0 || win == ~0ull) return false;
     const float tau = sc.tau;
     const float r = __uint_as_float((unsigned)(win >> 32));
-    const float psi = r - sc.nu * (rr2 * irr);
-    if (psi < -tau - 1e-3f) return false;
+    const float psi = __fmaf_rn(-sc.nu, __fmul_rn(rr2, irr), r);
+    if (psi < __fsub_rn(-tau, 1e-3f)) return false;
     // non-projective: d_i may fall inside the band whatever psi, every update takes the long path
-    if (DIST || psi <= tau + 1e-3f) return true;
-    const float Wn = dw.y + 1.f;
-    store_dw<F16>(md, vox, __fdividef(dw.y * dw.x + tau, Wn), Wn);
+    if (DIST || psi <= __fadd_rn(tau, 1e-3f)) return true;
+    const float Wn = __fadd_rn(dw.y, 1.f);
+    store_dw<F16>(md, vox, __fdividef(__fmaf_rn(dw.y, dw.x, tau), Wn), Wn);
     ++n_upd;
     remesh |= remesh_offsets(vi);
     return false;
@@ -490,8 +493,8 @@ __device__ __forceinline__ bool tsdf_band(const ScanConst &sc, const MapDev &md,
     df_add(qh, ql, c, ce, qh, ql);
     df_mul(qh, ql, sc.nu2hi, sc.nu2lo, mh, ml);
     df_add(rh, rl, -mh, -ml, dh, dl);
-    const float psi = __fdividef(dh + dl, e.r + mh * rsqrtf(mh));
-    const float w = sc.weight_mode == 0 ? fminf(fmaxf((psi + tau) * sc.inv_2tau, 0.f), 1.f) : 1.f;
+    const float psi = __fdividef(__fadd_rn(dh, dl), __fmaf_rn(mh, rsqrtf(mh), e.r));
+    const float w = sc.weight_mode == 0 ? fminf(fmaxf(__fmul_rn(__fadd_rn(psi, tau), sc.inv_2tau), 0.f), 1.f) : 1.f;
     if (!(psi >= -tau && w > 0.f)) return false;
     float sdf = fminf(psi, tau);
     if (DIST) {
@@ -520,8 +523,8 @@ __device__ __forceinline__ bool tsdf_band(const ScanConst &sc, const MapDev &md,
         // truncation Gamma(d, tau), both sides
         sdf = d >= 0.f ? fminf(d, tau) : fmaxf(d, -tau);
     }
-    const float Wn = e.W + w;
-    store_dw<F16>(md, (long long)slot * BV + vi, __fdividef(e.W * e.D + w * sdf, Wn), Wn);
+    const float Wn = __fadd_rn(e.W, w);
+    store_dw<F16>(md, (long long)slot * BV + vi, __fdividef(__fmaf_rn(e.W, e.D, __fmul_rn(w, sdf)), Wn), Wn);
     ++n_upd;
     remesh |= remesh_offsets(vi);
     if (fabsf(psi) > tau) return false;
@@ -539,13 +542,16 @@ __device__ __forceinline__ void tsdf_list(bool sem, int vox, int idx, int2 *wbuf
     wcount += __popc(mk);
 }
 
-// One touched block (hash slot h), processed by one warp.  Voxels outside the
-// truncation band are finished on the spot; band voxels are queued, and the
-// queue is worked off 32 at a time with every lane busy (they take the long
-// float-pair path, which would otherwise idle the rest of the warp).
+// Voxels [v0, v1) of one touched block (hash slot h; v1 - v0 a multiple of
+// 64), processed by one warp.  Voxels outside the truncation band are
+// finished on the spot; band voxels are queued, and the queue is worked off
+// 32 at a time with every lane busy (they take the long float-pair path,
+// which would otherwise idle the rest of the warp).  Every part of a new
+// block links it with its neighbours (the same writes), so that the part's
+// own re-mesh queueing below reads links it has set itself.
 template <bool F16, bool DIST = false>
 __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int h,
-                                                TsdfWarpSmem &T, long long &n_upd) {
+                                                TsdfWarpSmem &T, long long &n_upd, int v0 = 0, int v1 = BV) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int slot = md.vals[h];
@@ -592,7 +598,7 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
     // projections and both pixel reads before either update, so that their
     // latencies overlap
 #pragma unroll 1
-    for (int vi = lane; vi < BV; vi += 64) {
+    for (int vi = v0 + lane; vi < v1; vi += 64) {
         const long long va = (long long)slot * BV + vi, vb = va + 32;
         const float2 dwa = load_dw<F16>(md, va), dwb = load_dw<F16>(md, vb);
         float ma0, ma1, ma2, ra, ia, mb0, mb1, mb2, rb, ib;
@@ -731,31 +737,32 @@ __device__ __forceinline__ void semantic_item(const ScanConst &sc, const MapDev 
 #pragma unroll
                 for (int cc = 0; cc < (NC > 0 ? NC : 1); cc += 4) {
                     const float4 v = *reinterpret_cast<const float4 *>(q + cc);
-                    av[cc] += __logf(fmaxf(v.x, sc.lik_floor));
-                    av[cc + 1] += __logf(fmaxf(v.y, sc.lik_floor));
-                    av[cc + 2] += __logf(fmaxf(v.z, sc.lik_floor));
-                    av[cc + 3] += __logf(fmaxf(v.w, sc.lik_floor));
+                    av[cc] = __fadd_rn(av[cc], __logf(fmaxf(v.x, sc.lik_floor)));
+                    av[cc + 1] = __fadd_rn(av[cc + 1], __logf(fmaxf(v.y, sc.lik_floor)));
+                    av[cc + 2] = __fadd_rn(av[cc + 2], __logf(fmaxf(v.z, sc.lik_floor)));
+                    av[cc + 3] = __fadd_rn(av[cc + 3], __logf(fmaxf(v.w, sc.lik_floor)));
                 }
             } else {
 #pragma unroll
-                for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) av[cc] += __logf(fmaxf(q[cc], sc.lik_floor));
+                for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc)
+                    av[cc] = __fadd_rn(av[cc], __logf(fmaxf(q[cc], sc.lik_floor)));
             }
         } else {
             const int l = sc.labels[idx];
 #pragma unroll
-            for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) av[cc] += cc == l ? sc.log_phit : sc.log_pmiss;
+            for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) av[cc] = __fadd_rn(av[cc], cc == l ? sc.log_phit : sc.log_pmiss);
         }
 #pragma unroll
         for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) m = fmaxf(m, av[cc]);
         float ssum = 0.f;
 #pragma unroll
-        for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) ssum += __expf(av[cc] - m);
-        const float lse = m + __logf(ssum);
+        for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) ssum = __fadd_rn(ssum, __expf(__fsub_rn(av[cc], m)));
+        const float lse = __fadd_rn(m, __logf(ssum));
         int best = 0;
         float bv = -INFINITY;
 #pragma unroll
         for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) {
-            av[cc] = fmaxf(av[cc] - lse, sc.logp_floor);
+            av[cc] = fmaxf(__fsub_rn(av[cc], lse), sc.logp_floor);
             const float stored = F16 ? __half2float(__float2half_rn(av[cc])) : av[cc];
             if (stored > bv) {
                 bv = stored;
@@ -770,16 +777,16 @@ __device__ __forceinline__ void semantic_item(const ScanConst &sc, const MapDev 
         const int l = sc.has_probs ? -1 : sc.labels[idx];
         for (int cc = 0; cc < C; ++cc) {
             const float lik = sc.has_probs ? __logf(fmaxf(q[cc], sc.lik_floor)) : (cc == l ? sc.log_phit : sc.log_pmiss);
-            av[cc] = load_lp<F16>(md, lp_index(md, vox, cc)) + lik;
+            av[cc] = __fadd_rn(load_lp<F16>(md, lp_index(md, vox, cc)), lik);
             m = fmaxf(m, av[cc]);
         }
         float ssum = 0.f;
-        for (int cc = 0; cc < C; ++cc) ssum += __expf(av[cc] - m);
-        const float lse = m + __logf(ssum);
+        for (int cc = 0; cc < C; ++cc) ssum = __fadd_rn(ssum, __expf(__fsub_rn(av[cc], m)));
+        const float lse = __fadd_rn(m, __logf(ssum));
         int best = 0;
         float bv = -INFINITY;
         for (int cc = 0; cc < C; ++cc) {
-            const float nv = fmaxf(av[cc] - lse, sc.logp_floor);
+            const float nv = fmaxf(__fsub_rn(av[cc], lse), sc.logp_floor);
             store_lp<F16>(md, lp_index(md, vox, cc), nv);
             const float stored = F16 ? __half2float(__float2half_rn(nv)) : nv;
             if (stored > bv) {

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch(const __grid_c
     }
     if (!grid_sync(ctl, limit, gen)) return;
 
-    // ---- TSDF: one warp per touched block --------------------------------------
+    // ---- TSDF: one warp per half of a touched block ---------------------------
     if (threadIdx.x == 0) {
         for (int i = 0; i < n; ++i) {
             unsigned long long t = *(volatile unsigned long long *)&a.it[i].fd.ctr[CT_TOUCHED];
@@ -139,13 +139,16 @@ __global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch(const __grid_c
         }
     }
     __syncthreads();
-    for (long long e = gwarp; e < S.pre[n]; e += nwarps) {
+    // (half blocks, as the per-phase kernel: 256 voxels per unit)
+    for (long long u = gwarp; u < 2 * S.pre[n]; u += nwarps) {
+        const long long e = u >> 1;
+        const int v0 = (int)(u & 1) * (BV / 2);
         const int i = find_map(S.pre, n, e);
         const BatchItem &it = a.it[i];
         long long n_upd = 0;
         const int h = it.fd.touched[e - S.pre[i]];
-        if (it.md.storage == 0) tsdf_block_warp<false>(it.sc, it.md, it.fd, h, S.u.tsdf[wid], n_upd);
-        else tsdf_block_warp<true>(it.sc, it.md, it.fd, h, S.u.tsdf[wid], n_upd);
+        if (it.md.storage == 0) tsdf_block_warp<false>(it.sc, it.md, it.fd, h, S.u.tsdf[wid], n_upd, v0, v0 + BV / 2);
+        else tsdf_block_warp<true>(it.sc, it.md, it.fd, h, S.u.tsdf[wid], n_upd, v0, v0 + BV / 2);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) n_upd += __shfl_xor_sync(0xffffffffu, n_upd, o);
         if (lane == 0 && n_upd) atomicAdd(&it.fd.ctr[CT_UPD], (unsigned long long)n_upd);

@@ -32,6 +32,11 @@ __global__ void __launch_bounds__(256) k_normals(ScanConst sc, FrameDev fd) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) normal_item(sc, fd.win, p);
 }
 
+// Work unit: half a touched block (256 voxels, z < 4 or z >= 4), so that
+// the ~1.4 blocks per resident warp of a 64 x 2048 scan become ~2.8 units
+// and the last round of the grid-stride loop idles fewer warps.
+constexpr int TSDF_PARTS = 2;
+
 template <bool F16, bool DIST>
 __global__ void __launch_bounds__(256, 4) k_tsdf(ScanConst sc, MapDev md, FrameDev fd) {
     __shared__ TsdfWarpSmem s_w[8];   // per-warp class-update entries and band queue
@@ -41,8 +46,11 @@ __global__ void __launch_bounds__(256, 4) k_tsdf(ScanConst sc, MapDev md, FrameD
     long long n_upd = 0;
     unsigned long long nt = *(volatile unsigned long long *)&fd.ctr[CT_TOUCHED];
     if (nt > (unsigned long long)md.max_blocks) nt = md.max_blocks;
-    for (long long li = warp; li < (long long)nt; li += nwarps)
-        tsdf_block_warp<F16, DIST>(sc, md, fd, fd.touched[li], tw, n_upd);
+    constexpr int PV = BV / TSDF_PARTS;
+    for (long long u = warp; u < (long long)nt * TSDF_PARTS; u += nwarps) {
+        const int part = (int)(u % TSDF_PARTS);
+        tsdf_block_warp<F16, DIST>(sc, md, fd, fd.touched[u / TSDF_PARTS], tw, n_upd, part * PV, part * PV + PV);
+    }
     long long cnt[1] = {n_upd};
     cta_count<1>(fd.ctr, {CT_UPD}, cnt);
 }
