@@ -207,9 +207,20 @@ map_status extract_mesh_noalloc(map_t *map, float *positions, uint8_t *colors, i
                                 int32_t *triangles, int32_t *triangle_anchors, int64_t vertex_capacity,
                                 int64_t triangle_capacity, int64_t *n_vertices, int64_t *n_triangles, void *stream);
 
-/* Re-mesh every allocated block from scratch (replacing the incremental
- * segments); used to check that incremental meshing equals a full pass. */
+/* Re-mesh every allocated block from scratch, replacing all mesh segments
+ * (the arena is emptied first, nothing is compacted).  Asynchronous.  With
+ * per-frame meshing switched off this is the paper's regime: a global
+ * marching-cubes pass at a fixed rate (Sec. III-C.3, Table IV); it also
+ * checks that incremental meshing equals a full pass.  Afterwards
+ * map_get_frame_stats reports this pass: MAP_STAT_DIRTY_BLOCKS = blocks
+ * meshed, MAP_STAT_MESH_VERTICES / _TRIANGLES = the whole mesh. */
 map_status map_remesh_all(map_t *map, void *stream);
+
+/* Per-frame incremental meshing in integrate_scan: 1 (default) re-meshes
+ * the touched blocks and their -x/-y/-z neighbours every scan; 0 leaves
+ * the mesh as it is until map_remesh_all (the scan's kernels minus k_mesh).
+ * MAP_ERR_ARG for other values.  Applies to the following scans. */
+map_status map_set_incremental_mesh(map_t *map, int32_t enabled);
 
 /* Trilinear interpolation of D at m world points (from the 8 voxel centres
  * nu * v around x).  sdf_dev[m] float32 (NaN when any of the 8 voxels is

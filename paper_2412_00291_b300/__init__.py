@@ -72,6 +72,7 @@ _SIGS = {
     "integrate_scan_host": ([P, P, P, P, P, I64, P, P], I32),
     "extract_mesh": ([P, P, P], I32),
     "map_remesh_all": ([P, P], I32),
+    "map_set_incremental_mesh": ([P, I32], I32),
     "extract_mesh_noalloc": ([P, P, P, P, P, P, I64, I64, P, P, P], I32),
     "query_sdf": ([P, P, I64, P, P, P], I32),
     "query_sdf_backward": ([P, P, P, I64, P, P, P], I32),
@@ -257,6 +258,10 @@ def extract_mesh_noalloc(h, positions, colors, vertex_keys, triangles, triangle_
 
 def map_remesh_all(h, stream=None):
     _check(_lib.map_remesh_all(h, _stream(stream)), h)
+
+
+def map_set_incremental_mesh(h, enabled: bool):
+    _check(_lib.map_set_incremental_mesh(h, 1 if enabled else 0), h)
 
 
 def query_sdf(h, xyz, stream=None):
@@ -505,6 +510,9 @@ class SemanticTSDF:
 
     def remesh_all(self, stream=None):
         map_remesh_all(self.h, stream)
+
+    def set_incremental_mesh(self, enabled: bool):
+        map_set_incremental_mesh(self.h, enabled)
 
     def query(self, xyz, stream=None):
         return query_sdf(self.h, xyz, stream)

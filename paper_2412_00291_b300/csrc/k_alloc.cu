@@ -30,14 +30,14 @@ __global__ void k_link_all(MapDev md) {
 }
 
 // Every allocated block into the re-mesh list (full re-mesh).
+// Every allocated pool slot, in slot order, into the re-mesh list.
 __global__ void k_list_all(MapDev md, FrameDev fd) {
     unsigned long long pc = md.st->pool_count;
     if (pc > (unsigned long long)md.max_blocks) pc = md.max_blocks;
+    if (blockIdx.x == 0 && threadIdx.x == 0) fd.ctr[CT_DIRTY] = pc;
     for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; s < pc;
-         s += (unsigned long long)gridDim.x * blockDim.x) {
-        const unsigned long long idx = atomicAdd(&fd.ctr[CT_DIRTY], 1ull);
-        if (idx < (unsigned long long)md.max_blocks) fd.dirty[idx] = (int)s;
-    }
+         s += (unsigned long long)gridDim.x * blockDim.x)
+        fd.dirty[s] = (int)s;
 }
 
 // D = 0, W = 0, uniform class distribution, label 0, empty mesh segment.

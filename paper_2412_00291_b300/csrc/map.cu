@@ -79,6 +79,7 @@ struct map_t {
     double *gn_T = nullptr, *gn_acc = nullptr;
     double *qb_part = nullptr;   // pose-gradient partial sums of query_sdf_backward
     int frame = 0;
+    bool mesh_per_frame = true;     // incremental re-meshing in every integrate_scan
     int grid_integrate = 0, grid_mesh = 0, grid_semantic = 0;
     // phase profiling: (MAP_PHASE_COUNT + 1) events per recorded frame
     std::vector<cudaEvent_t> prof_ev;
@@ -593,11 +594,11 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     CU(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
     launch_semantic(sc, m->md, m->fd, m->grid_semantic, m->side);
     if (ev) CU(cudaEventRecord(ev[4], m->side));
-    launch_mesh(m->md, m->fd, m->grid_mesh, s);
+    if (m->mesh_per_frame) launch_mesh(m->md, m->fd, m->grid_mesh, s);
     if (ev) CU(cudaEventRecord(ev[5], s));
     CU(cudaEventRecord(m->ev_join, m->side));
     CU(cudaStreamWaitEvent(s, m->ev_join, 0));
-    m->launches += 4;
+    m->launches += m->mesh_per_frame ? 4 : 3;
     if (ev_stats)
         CU(cudaMemcpyAsync(ev_stats, m->fd.ctr, CT_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
     st = launch_check(m, "integrate_scan kernels");
@@ -659,14 +660,27 @@ extern "C" map_status integrate_scan_host(map_t *m, const lidar_intrinsics *L, c
 extern "C" map_status map_remesh_all(map_t *m, void *stream) {
     if (!m) return fail(nullptr, MAP_ERR_ARG, "null map");
     cudaStream_t s = (cudaStream_t)stream;
-    map_status st = compact_arena(m, s);
-    if (st != MAP_OK) return st;
+    // every block is re-meshed and rewrites its segment, so the old arena
+    // contents are dropped rather than compacted: cursors back to empty
+    CU(cudaMemsetAsync(m->gb.totals, 0, 2 * sizeof(long long), s));
+    launch_set_cursors(m->md, m->gb, s);
+    m->epoch++;
+    m->known_fill = 0.0;
+    m->known_frame = m->frame - 1;
     CU(cudaMemsetAsync(m->fd.ctr, 0, CT_COUNT * sizeof(unsigned long long), s));
     launch_list_all(m->md, m->fd, m->frame, s);
     launch_mesh(m->md, m->fd, m->grid_mesh, s);
-    m->launches += 2;
-    st = launch_check(m, "map_remesh_all");
+    m->launches += 3;
+    map_status st = launch_check(m, "map_remesh_all");
     if (st != MAP_OK) return st;
+    // map_get_frame_stats now reports this pass (blocks meshed, vertices, triangles)
+    CU(cudaMemcpyAsync(m->h_ctr, m->fd.ctr, CT_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    return MAP_OK;
+}
+
+extern "C" map_status map_set_incremental_mesh(map_t *m, int32_t enabled) {
+    if (!m || (enabled != 0 && enabled != 1)) return fail(m, MAP_ERR_ARG, "enabled must be 0 or 1");
+    m->mesh_per_frame = enabled == 1;
     return MAP_OK;
 }
 

@@ -99,6 +99,60 @@ def test_line16_mesh_and_incremental(line16_run):
     assert canon(inc) == canon(full)
 
 
+def _canon_mesh(m):
+    k = m["vertex_keys"]
+    t = k[m["triangles"]]
+    tri = sorted(map(tuple, np.concatenate([t, m["triangle_anchors"]], axis=1).tolist()))
+    v = sorted(zip(k.tolist(), map(tuple, m["positions"].tolist()), map(tuple, m["colors"].tolist())))
+    return tri, v
+
+
+def test_fixed_rate_full_meshing(line16_run):
+    """Per-frame meshing off, a full marching-cubes pass every 4 scans (the paper's fixed-rate
+    global mesh): the voxels are unaffected and each full pass equals the incremental map's mesh
+    at the same scan, and the oracle's."""
+    r = line16_run
+    p, w = r["p"], r["w"]
+    L = _lidar(p, w.lidar)
+    gm = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=32768, hash_capacity=1 << 16,
+                        max_points=32768, max_pixels=32768, mesh_vertex_capacity=1 << 22,
+                        mesh_triangle_capacity=1 << 23)
+    inc = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=32768, hash_capacity=1 << 16,
+                         max_points=32768, max_pixels=32768, mesh_vertex_capacity=1 << 22,
+                         mesh_triangle_capacity=1 << 23)
+    gm.set_incremental_mesh(False)
+    with pytest.raises(p.MapError):                      # only 0 and 1 are valid
+        p._check(p._lib.map_set_incremental_mesh(gm.h, 2), gm.h)
+    passes = 0
+    for k, f in enumerate(r["frames"]):
+        for m in (gm, inc):
+            m.integrate(L, _dev(f.points), f.T, labels=_dev(f.labels))
+        s = gm.stats()
+        assert s["mesh_vertices"] == 0 and s["mesh_triangles"] == 0
+        if k % 4 == 3 or k == len(r["frames"]) - 1:
+            gm.remesh_all()
+            a, b = _mesh_np(gm.mesh()), _mesh_np(inc.mesh())
+            assert len(a["triangles"]) > 1000
+            assert _canon_mesh(a) == _canon_mesh(b)
+            passes += 1
+    assert passes == 3
+    # a second full pass rebuilds the same mesh from an emptied arena
+    before = _canon_mesh(_mesh_np(gm.mesh()))
+    gm.remesh_all()
+    st = gm.stats()                                      # the counters describe the full pass
+    again = _mesh_np(gm.mesh())
+    assert _canon_mesh(again) == before
+    assert st["dirty_blocks"] == st["total_blocks"]
+    assert st["mesh_vertices"] == len(again["vertex_keys"]) and st["mesh_triangles"] == len(again["triangles"])
+    coords = r["om"].alloc_blocks()
+    x, y = gm.read_blocks(coords), inc.read_blocks(coords)
+    for key in ("D", "W", "label"):
+        assert np.array_equal(x[key], y[key])
+    compare_meshes(_mesh_np(gm.mesh()), r["om"].mesh(), r["om"], w.voxel_size)
+    gm.close()
+    inc.close()
+
+
 def test_edge_cases_empty_ragged_invalid():
     p = _lib()
     w = synth.line16()
