@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=195)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["loop64", "line16", "streams32", "align1km"], default="loop64")
+    ap.add_argument("--workload", choices=["loop64", "line16", "streams32", "align1km", "trav"], default="loop64")
     ap.add_argument("--storage", choices=["fp32", "fp16"], default="fp32")
     ap.add_argument("--distance", choices=["projective", "nonprojective"], default="projective",
                     help="fused distance: projective psi, or the non-projective d_i (normal image, gradients)")
@@ -695,6 +695,71 @@ def run_batch(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_trav(args, rank, world, local_rank):
+    """Mesh traversability (Sec. III-D, Table II thresholds, ground class only) of the whole mesh of
+    the 200-scan 64x2048 loop map: CUDA events around each map_traversability call on the
+    launching stream; the FP64 oracle timed beside it on the mesh of the first two scans."""
+    import torch
+    import paper_2412_00291_b300 as P
+    from oracle.traversability import traversability as oracle_trav
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = workload("loop64", rank)
+    L = w.lidar
+    lid = P.lidar_intrinsics(L.H, L.W, L.fov_up, L.fov_down, L.r_min, L.r_max)
+    m = P.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes)
+    cpu = None
+    for k, f in enumerate(frames_for(w, w.frames)):
+        m.integrate(lid, torch.from_numpy(f.points).to(dev), f.T, probs=torch.from_numpy(f.probs).to(dev))
+        if k == 1 and rank == 0 and not args.no_cpu_baseline:
+            mh = {kk: v.cpu().numpy() for kk, v in m.mesh().items()}
+            t0 = time.perf_counter()
+            oracle_trav(mh["positions"], mh["colors"], mh["vertex_keys"], mh["triangles"], allowed=[0])
+            dt = time.perf_counter() - t0
+            cpu = {"value": len(mh["vertex_keys"]) / dt, "unit": "vertices/s", "cores": 1, "kind": "oracle",
+                   "sample": f"mesh after the first 2 scans ({len(mh['vertex_keys'])} vertices, {dt:.1f} s, "
+                             "numpy + scipy k-d tree, FP64)"}
+    mesh = m.mesh()
+    nv, nt = int(mesh["vertex_keys"].shape[0]), int(mesh["triangles"].shape[0])
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        props, trav = m.traversability(nv, allowed_classes=[0])
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local_rank) as clk:
+        for a, b in ev:
+            a.record(stream)
+            props, trav = m.traversability(nv, allowed_classes=[0])
+            b.record(stream)
+        torch.cuda.synchronize()
+    ms = np.array([a.elapsed_time(b) for a, b in ev])
+    launches = m.stats()["kernel_launches"]
+    if rank != 0:
+        return
+    io_bytes = nv * (12 + 4 + 8 + 16 + 1) + nt * 12        # mesh in, properties and flags out
+    peak, kind = measured_peaks()
+    g = io_bytes / (float(np.mean(ms)) * 1e-3) / 1e9
+    line = {
+        "metric": "mesh traversability, vertices per second (whole 200-scan 64x2048 map)",
+        "value": nv / (float(np.mean(ms)) * 1e-3), "unit": "vertices/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+        "config": {"workload": "trav_" + w.name, "vertices": nv, "triangles": nt,
+                   "radius_m": 0.25, "t_hd_m": 0.6, "t_s_deg": 20.0,
+                   "t_r_deg": 30.0, "allowed_classes": [0], "ms_median": float(np.median(ms)),
+                   "traversable_fraction": float(trav.float().mean().item()),
+                   "mean_ball_size": float(props[:, 3].mean().item())},
+        "roofline": {"bound": "hbm", "kernel": "map_traversability (7 kernels)", "achieved": g, "peak": peak,
+                     "unit": "GB/s", "frac": g / peak, "peak_source": f"{kind} hbm_gbs", "traffic": None,
+                     "algorithmic_bytes_per_launch": io_bytes,
+                     "note": "mesh in and results out only; the weld and cell tables and the ball scans are "
+                             "L2/issue work"},
+        "cpu_baseline": cpu, "e2e": None, "gpu_launches": 7 * args.steps, "clocks": clk.summary(),
+        "map_kernel_launches_total": launches,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def _rot_err_deg(Ra, Rb):
     c = (np.trace(Ra.T @ Rb) - 1.0) / 2.0
     return math.degrees(math.acos(max(-1.0, min(1.0, c))))
@@ -895,6 +960,8 @@ def main():
         run_batch(args, rank, world, local_rank)
     elif args.workload == "align1km":
         run_align(args, rank, world, local_rank)
+    elif args.workload == "trav":
+        run_trav(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1 and args.impl == "ours":

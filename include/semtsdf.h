@@ -222,6 +222,43 @@ map_status map_remesh_all(map_t *map, void *stream);
  * MAP_ERR_ARG for other values.  Applies to the following scans. */
 map_status map_set_incremental_mesh(map_t *map, int32_t enabled);
 
+/* ---- mesh traversability (Sec. III-D, Table II) ---- */
+
+/* Thresholds of the traversability test.  Defaults (map_trav_params_default)
+ * are Table II's: radius 0.25 m, height difference 0.6 m, steepness 20 deg,
+ * roughness 30 deg; every class allowed.  With radius r the height
+ * difference within the ball cannot exceed 2 r, so at the defaults the 0.6 m
+ * threshold never rejects a vertex. */
+typedef struct {
+    double radius;            /* r, metres: the ball around each vertex                  */
+    double max_height_diff;   /* t_hd, metres                                            */
+    double max_steepness;     /* t_s, radians                                            */
+    double max_roughness;     /* t_r, radians                                            */
+    uint64_t class_mask;      /* bit c set: class c may be driven on (classes >= 64: no) */
+} trav_params;
+
+map_status map_trav_params_default(trav_params *params);
+
+/* Traversability of every vertex of the mesh the last extract_mesh returned
+ * (Sec. III-D): vertices are welded by vertex_keys (seam copies are one
+ * vertex), a vertex normal is the area-weighted sum of its triangles'
+ * normals, and within the ball B of radius r around the vertex
+ *   v_hd = max z - min z over B          (height difference, metres),
+ *   v_s  = angle of the normal from +z    (steepness, radians),
+ *   v_r  = angle between the normal and the mean normal of B (roughness);
+ * the vertex is traversable when v_hd < t_hd, v_s < t_s, v_r < t_r and its
+ * class (colors[v][3]) is in class_mask.  The printed formulas are garbled:
+ * the height difference is read as the elevation range, steepness and
+ * roughness as the angles above, and the printed "all larger than the
+ * thresholds" as all smaller (traversable).  Output per extracted vertex
+ * (copies get their welded vertex's values): props_dev[nv][4] float32 =
+ * {v_hd, v_s, v_r, |B|}, traversable_dev[nv] uint8.  Asynchronous;
+ * MAP_ERR_STATE before any extract_mesh.  Scratch (~80 B per vertex) is
+ * kept by the map and grown when a larger mesh comes (that growth
+ * synchronises `stream`). */
+map_status map_traversability(map_t *map, const trav_params *params, float *props_dev, uint8_t *traversable_dev,
+                              void *stream);
+
 /* Trilinear interpolation of D at m world points (from the 8 voxel centres
  * nu * v around x).  sdf_dev[m] float32 (NaN when any of the 8 voxels is
  * unallocated or unobserved, W = 0), valid_dev[m] uint8 (1 = valid), may be

@@ -45,26 +45,38 @@ def weld(positions, colors, vertex_keys, triangles):
 
 def vertex_normals(pos, tri):
     """Area-weighted vertex normals: sum of (b - a) x (c - a) over incident triangles, normalised
-    (zero where a vertex has no triangle of non-zero area)."""
+    (zero where a vertex has no triangle of non-zero area); and each normal's condition number
+    sum |(b - a) x (c - a)| / |sum (b - a) x (c - a)| (large where incident faces nearly cancel, so
+    that a rounding error in any one face turns the normal)."""
     a, b, c = pos[tri[:, 0]], pos[tri[:, 1]], pos[tri[:, 2]]
     fn = np.cross(b - a, c - a)
     acc = np.zeros_like(pos)
+    mag = np.zeros(len(pos))
+    fl = np.linalg.norm(fn, axis=1)
     for k in range(3):
         np.add.at(acc, tri[:, k], fn)
+        np.add.at(mag, tri[:, k], fl)
     ln = np.linalg.norm(acc, axis=1)
     out = np.zeros_like(acc)
     ok = ln > 0
     out[ok] = acc[ok] / ln[ok, None]
-    return out
+    cond = np.full(len(pos), np.inf)
+    cond[ok] = mag[ok] / ln[ok]
+    return out, cond
 
 
-def properties(pos, normals, r):
-    """(v_hd, v_s, v_r) per vertex, radians for the angles; the ball includes the vertex itself."""
+def properties(pos, normals, r, amb_rel=1e-6):
+    """(v_hd, v_s, v_r) per vertex, radians for the angles; the ball includes the vertex itself.
+
+    Also flags each vertex whose ball has a candidate at squared distance within amb_rel r^2 of
+    r^2 (single-precision distances may decide its membership the other way)."""
     tree = cKDTree(pos)
     balls = tree.query_ball_point(pos, r)
+    wide = tree.query_ball_point(pos, r * (1.0 + amb_rel))
     n = len(pos)
     hd = np.zeros(n)
     vr = np.zeros(n)
+    amb = np.zeros(n, bool)
     for i, b in enumerate(balls):
         b = np.asarray(b, np.int64)
         z = pos[b, 2]
@@ -72,8 +84,11 @@ def properties(pos, normals, r):
         m = normals[b].mean(axis=0)
         lm = np.linalg.norm(m)
         vr[i] = np.arccos(np.clip(normals[i] @ (m / lm), -1.0, 1.0)) if lm > 0 else 0.0
+        w = np.asarray(wide[i], np.int64)
+        d2 = np.sum((pos[w] - pos[i]) ** 2, axis=1)
+        amb[i] = bool(np.any(np.abs(d2 - r * r) < amb_rel * r * r))
     vs = np.arccos(np.clip(normals[:, 2], -1.0, 1.0))
-    return hd, vs, vr, balls
+    return hd, vs, vr, balls, amb
 
 
 def traversability(positions, colors, vertex_keys, triangles, r=0.25, t_hd=0.6, t_s_deg=20.0, t_r_deg=30.0,
@@ -83,9 +98,9 @@ def traversability(positions, colors, vertex_keys, triangles, r=0.25, t_hd=0.6, 
 
     allowed: iterable of classes a vertex may carry to be traversable (None: every class)."""
     pos, lab, tri, inv = weld(positions, colors, vertex_keys, triangles)
-    nrm = vertex_normals(pos, tri)
-    hd, vs, vr, balls = properties(pos, nrm, r)
+    nrm, cond = vertex_normals(pos, tri)
+    hd, vs, vr, balls, amb = properties(pos, nrm, r)
     ok_cls = np.ones(len(pos), bool) if allowed is None else np.isin(lab, np.asarray(list(allowed), np.int64))
     trav = (hd < t_hd) & (vs < np.radians(t_s_deg)) & (vr < np.radians(t_r_deg)) & ok_cls
     return dict(positions=pos, labels=lab, normals=nrm, hd=hd, s=vs, r=vr, traversable=trav, index=inv,
-                ball_sizes=np.array([len(b) for b in balls]))
+                ball_sizes=np.array([len(b) for b in balls]), ball_ambiguous=amb, normal_cond=cond)

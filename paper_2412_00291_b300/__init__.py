@@ -73,6 +73,8 @@ _SIGS = {
     "extract_mesh": ([P, P, P], I32),
     "map_remesh_all": ([P, P], I32),
     "map_set_incremental_mesh": ([P, I32], I32),
+    "map_trav_params_default": ([P], I32),
+    "map_traversability": ([P, P, P, P, P], I32),
     "extract_mesh_noalloc": ([P, P, P, P, P, P, I64, I64, P, P, P], I32),
     "query_sdf": ([P, P, I64, P, P, P], I32),
     "query_sdf_backward": ([P, P, P, I64, P, P, P], I32),
@@ -262,6 +264,35 @@ def map_remesh_all(h, stream=None):
 
 def map_set_incremental_mesh(h, enabled: bool):
     _check(_lib.map_set_incremental_mesh(h, 1 if enabled else 0), h)
+
+
+class TravParams(ctypes.Structure):
+    _fields_ = [("radius", D), ("max_height_diff", D), ("max_steepness", D), ("max_roughness", D),
+                ("class_mask", ctypes.c_uint64)]
+
+
+def map_traversability(h, n_vertices, radius=None, max_height_diff=None, max_steepness=None, max_roughness=None,
+                       allowed_classes=None, stream=None):
+    """Traversability of the last extracted mesh: (props [nv, 4] float32 CUDA tensor = height
+    difference, steepness, roughness, ball size; traversable [nv] uint8).  Angles in radians;
+    allowed_classes: iterable of classes (None: all)."""
+    p = TravParams()
+    _check(_lib.map_trav_params_default(ctypes.byref(p)))
+    for k, v in (("radius", radius), ("max_height_diff", max_height_diff), ("max_steepness", max_steepness),
+                 ("max_roughness", max_roughness)):
+        if v is not None:
+            setattr(p, k, float(v))
+    if allowed_classes is not None:
+        m = 0
+        for c in allowed_classes:
+            if 0 <= int(c) < 64:
+                m |= 1 << int(c)
+        p.class_mask = m
+    props = torch.empty((max(n_vertices, 1), 4), dtype=torch.float32, device="cuda")
+    trav = torch.empty(max(n_vertices, 1), dtype=torch.uint8, device="cuda")
+    _check(_lib.map_traversability(h, ctypes.byref(p), ctypes.c_void_p(props.data_ptr()),
+                                   ctypes.c_void_p(trav.data_ptr()), _stream(stream)), h)
+    return props[:n_vertices], trav[:n_vertices]
 
 
 def query_sdf(h, xyz, stream=None):
@@ -513,6 +544,10 @@ class SemanticTSDF:
 
     def set_incremental_mesh(self, enabled: bool):
         map_set_incremental_mesh(self.h, enabled)
+
+    def traversability(self, n_vertices, **params):
+        """After mesh(): per-vertex (props, traversable) of that mesh (see map_traversability)."""
+        return map_traversability(self.h, n_vertices, **params)
 
     def query(self, xyz, stream=None):
         return query_sdf(self.h, xyz, stream)

@@ -53,4 +53,28 @@ constexpr int GN_ACC_ROWS = 148 * 8;          // most CTAs of k_gn_terms
 int gn_terms_grid(long long n);
 void launch_gn_step(double *T_dev, const double *acc, int nparts, cudaStream_t s);
 
+// k_trav.cu: mesh traversability (Sec. III-D) over an extracted mesh
+struct TravDev {
+    uint64_t *vkeys;              // [vmask + 1] vertex-key hash
+    int *vfirst;                  // [vmask + 1] lowest vertex index of each key
+    uint64_t vmask;
+    int *rep;                     // [nv] representative (welded) vertex
+    float4 *nacc;                 // [nv] normal sums, then unit normals (w = 1 valid)
+    int *vcell;                   // [nv] cell slot of a representative, -1 otherwise
+    uint64_t *ckeys;              // [cmask + 1] cell hash
+    int *ccount, *cstart, *cfill; // [cmask + 1] per cell: vertices, first sorted index, fill cursor
+    uint64_t cmask;
+    float4 *spos, *snrm;          // [nv] cell-sorted representatives: {x, y, z, label bits}, normal
+    unsigned long long *cursor;   // sorted-array allocation cursor
+    unsigned *err;                // bit 1 (ERR_HASH_PROBES) when a hash overflows its probe bound
+    float inv_cell;               // 1 / cell edge (the radius, enlarged by 1e-5)
+};
+struct TravParamsDev {
+    float r2, t_hd, t_s, t_r;     // radius^2 (m^2), height (m), steepness and roughness (rad)
+    unsigned long long class_mask;
+};
+void launch_traversability(const TravDev &b, const TravParamsDev &p, const float *pos, const uint8_t *col,
+                           const int64_t *vkey, const int32_t *tri, long long nv, long long nt, float4 *props,
+                           uint8_t *trav, cudaStream_t s);
+
 }  // namespace stsdf

@@ -75,6 +75,11 @@ struct map_t {
     cudaEvent_t ev_dir = nullptr;
     lidar_intrinsics dir_for{};
     bool dir_valid = false;
+    // traversability scratch (grown on demand) and the last extract_mesh's size
+    TravDev trav{};
+    long long trav_nv_cap = 0;
+    bool ext_valid = false;
+    long long ext_nv = 0, ext_nt = 0;
     // alignment scratch
     double *gn_T = nullptr, *gn_acc = nullptr;
     double *qb_part = nullptr;   // pose-gradient partial sums of query_sdf_backward
@@ -147,7 +152,9 @@ static void free_all(map_t *m) {
                     m->gb.totals, m->stage_pts[0], m->stage_lab[0], m->stage_probs[0], m->stage_pts[1],
                     m->stage_lab[1], m->stage_probs[1], m->out_pos, m->out_col,
                     m->out_keys, m->out_tri, m->out_anchor, m->gn_T, m->gn_acc, m->qb_part, m->pal_dev,
-                    m->md.g32, m->md.g16, m->nrm, m->row_dir, m->col_dir};
+                    m->md.g32, m->md.g16, m->nrm, m->row_dir, m->col_dir, m->trav.vkeys, m->trav.vfirst,
+                    m->trav.rep, m->trav.nacc, m->trav.vcell, m->trav.ckeys, m->trav.ccount, m->trav.cstart,
+                    m->trav.cfill, m->trav.spos, m->trav.snrm, m->trav.cursor};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (m->h_ctr) cudaFreeHost(m->h_ctr);
@@ -777,6 +784,9 @@ extern "C" map_status extract_mesh(map_t *m, mesh_view *out, void *stream) {
                       m->out_keys, m->out_tri, m->out_anchor, s);
     map_status st = launch_check(m, "extract_mesh");
     if (st != MAP_OK) return st;
+    m->ext_valid = true;
+    m->ext_nv = nv;
+    m->ext_nt = nt;
     out->n_vertices = nv;
     out->n_triangles = nt;
     out->positions = m->out_pos;
@@ -785,6 +795,84 @@ extern "C" map_status extract_mesh(map_t *m, mesh_view *out, void *stream) {
     out->triangles = m->out_tri;
     out->triangle_anchors = m->out_anchor;
     return MAP_OK;
+}
+
+extern "C" map_status map_trav_params_default(trav_params *p) {
+    if (!p) return fail(nullptr, MAP_ERR_ARG, "null parameters");
+    p->radius = 0.25;
+    p->max_height_diff = 0.6;
+    p->max_steepness = 20.0 * M_PI / 180.0;
+    p->max_roughness = 30.0 * M_PI / 180.0;
+    p->class_mask = ~0ull;
+    return MAP_OK;
+}
+
+static void trav_free(TravDev &t) {
+    void *ptrs[] = {t.vkeys, t.vfirst, t.rep, t.nacc, t.vcell, t.ckeys, t.ccount, t.cstart, t.cfill, t.spos, t.snrm,
+                    t.cursor};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    t = TravDev{};
+}
+
+extern "C" map_status map_traversability(map_t *m, const trav_params *p, float *props_dev, uint8_t *trav_dev,
+                                         void *stream) {
+    if (!m || !p || (m->ext_nv > 0 && (!props_dev || !trav_dev))) return fail(m, MAP_ERR_ARG, "bad arguments");
+    if (!(p->radius > 0.0) || !(p->radius < 1e4)) return fail(m, MAP_ERR_ARG, "need 0 < radius < 1e4 m");
+    if (!m->ext_valid) return fail(m, MAP_ERR_STATE, "no extracted mesh (call extract_mesh first)");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long nv = m->ext_nv, nt = m->ext_nt;
+    if (nv == 0) return MAP_OK;
+    TravDev &b = m->trav;
+    if (nv > m->trav_nv_cap) {
+        CU(cudaStreamSynchronize(s));
+        trav_free(b);
+        m->trav_nv_cap = 0;
+        uint64_t cap = 1024;
+        while ((long long)cap < 2 * nv) cap <<= 1;
+        cudaError_t e = cudaSuccess;
+        auto A = [&](auto **q, size_t count) {
+            if (e == cudaSuccess) e = cudaMalloc((void **)q, count * sizeof(**q) + 16);
+        };
+        A(&b.vkeys, cap);
+        A(&b.vfirst, cap);
+        A(&b.ckeys, cap);
+        A(&b.ccount, cap);
+        A(&b.cstart, cap);
+        A(&b.cfill, cap);
+        A(&b.rep, (size_t)nv);
+        A(&b.nacc, (size_t)nv);
+        A(&b.vcell, (size_t)nv);
+        A(&b.spos, (size_t)nv);
+        A(&b.snrm, (size_t)nv);
+        A(&b.cursor, 1);
+        if (e != cudaSuccess) {
+            trav_free(b);
+            return fail(m, MAP_ERR_NOMEM, "traversability scratch allocation failed");
+        }
+        b.vmask = b.cmask = cap - 1;
+        m->trav_nv_cap = nv;
+    }
+    b.err = &m->st->err;
+    b.inv_cell = (float)(1.0 / (p->radius * (1.0 + 1e-5)));
+    const size_t tab = (size_t)(b.vmask + 1);
+    CU(cudaMemsetAsync(b.vkeys, 0xFF, tab * sizeof(uint64_t), s));
+    CU(cudaMemsetAsync(b.vfirst, 0x7F, tab * sizeof(int), s));
+    CU(cudaMemsetAsync(b.ckeys, 0xFF, tab * sizeof(uint64_t), s));
+    CU(cudaMemsetAsync(b.ccount, 0, tab * sizeof(int), s));
+    CU(cudaMemsetAsync(b.cfill, 0, tab * sizeof(int), s));
+    CU(cudaMemsetAsync(b.nacc, 0, (size_t)nv * sizeof(float4), s));
+    CU(cudaMemsetAsync(b.cursor, 0, sizeof(unsigned long long), s));
+    TravParamsDev pd;
+    pd.r2 = (float)(p->radius * p->radius);
+    pd.t_hd = (float)p->max_height_diff;
+    pd.t_s = (float)p->max_steepness;
+    pd.t_r = (float)p->max_roughness;
+    pd.class_mask = p->class_mask;
+    launch_traversability(b, pd, m->out_pos, m->out_col, m->out_keys, m->out_tri, nv, nt,
+                          reinterpret_cast<float4 *>(props_dev), trav_dev, s);
+    m->launches += nt > 0 ? 7 : 6;
+    return launch_check(m, "map_traversability");
 }
 
 extern "C" map_status query_sdf(map_t *m, const float *xyz_dev, int64_t n, float *sdf_dev, uint8_t *valid_dev,
