@@ -259,6 +259,30 @@ map_status map_trav_params_default(trav_params *params);
 map_status map_traversability(map_t *map, const trav_params *params, float *props_dev, uint8_t *traversable_dev,
                               void *stream);
 
+/* ---- map quality against a ground-truth point cloud (Sec. IV-B.1) ---- */
+
+typedef struct {
+    double re;        /* Reconstruction Error: sqrt(mean over M of d(p, G)^2), metres   */
+    double cd;        /* Chamfer-L1: mean_M d(p, G) / 2 + mean_G d(q, M) / 2, metres   */
+    double rc;        /* Reconstruction Coverage: fraction of G within trunc of M    */
+    double miou;      /* mean IoU over the classes that occur                          */
+    double acc;       /* fraction of correctly classed vertices                        */
+    int64_t n_map, n_gt, n_labeled, n_correct;
+} quality_report;
+
+/* Compare the mesh the last extract_mesh returned with a ground-truth cloud:
+ * M = its welded vertices (one per vertex key), G = gt_points_dev [n_gt][3]
+ * float32 (world frame) with classes gt_labels_dev [n_gt] int32;
+ * d(p, X) = min(trunc, distance to the nearest point of X) (the paper uses
+ * trunc = 2 nu).  mIoU and Acc count the vertices with a ground-truth point
+ * within trunc: the class of that nearest point against the vertex's class;
+ * IoU_c = TP / (TP + FP + FN) over the classes with TP + FP + FN > 0.
+ * confusion (may be NULL): host int64 [C][C], rows ground-truth class,
+ * columns vertex class.  Synchronises `stream`; MAP_ERR_STATE before any
+ * extract_mesh or for an empty mesh, MAP_ERR_ARG for n_gt < 1. */
+map_status map_quality(map_t *map, const float *gt_points_dev, const int32_t *gt_labels_dev, int64_t n_gt,
+                       double trunc, quality_report *out, int64_t *confusion, void *stream);
+
 /* Trilinear interpolation of D at m world points (from the 8 voxel centres
  * nu * v around x).  sdf_dev[m] float32 (NaN when any of the 8 voxels is
  * unallocated or unobserved, W = 0), valid_dev[m] uint8 (1 = valid), may be

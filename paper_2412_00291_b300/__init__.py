@@ -75,6 +75,7 @@ _SIGS = {
     "map_set_incremental_mesh": ([P, I32], I32),
     "map_trav_params_default": ([P], I32),
     "map_traversability": ([P, P, P, P, P], I32),
+    "map_quality": ([P, P, P, I64, D, P, P, P], I32),
     "extract_mesh_noalloc": ([P, P, P, P, P, P, I64, I64, P, P, P], I32),
     "query_sdf": ([P, P, I64, P, P, P], I32),
     "query_sdf_backward": ([P, P, P, I64, P, P, P], I32),
@@ -264,6 +265,25 @@ def map_remesh_all(h, stream=None):
 
 def map_set_incremental_mesh(h, enabled: bool):
     _check(_lib.map_set_incremental_mesh(h, 1 if enabled else 0), h)
+
+
+class QualityReport(ctypes.Structure):
+    _fields_ = [("re", D), ("cd", D), ("rc", D), ("miou", D), ("acc", D), ("n_map", I64), ("n_gt", I64),
+                ("n_labeled", I64), ("n_correct", I64)]
+
+
+def map_quality(h, n_classes, gt_points, gt_labels, trunc, stream=None) -> dict:
+    """Quality of the last extracted mesh against a ground-truth cloud (CUDA tensors [n, 3] float32,
+    [n] int32): dict of re, cd, rc, miou, acc, counts and the confusion matrix [gt class][vertex class]."""
+    rep = QualityReport()
+    conf = np.zeros((n_classes, n_classes), np.int64)
+    n = int(gt_points.shape[0])
+    _check(_lib.map_quality(h, _dev_ptr(gt_points, torch.float32, "gt_points", 3),
+                            _dev_ptr(gt_labels, torch.int32, "gt_labels"), n, float(trunc), ctypes.byref(rep),
+                            _np_ptr(conf), _stream(stream)), h)
+    out = {k: getattr(rep, k) for k, _ in QualityReport._fields_}
+    out["confusion"] = conf
+    return out
 
 
 class TravParams(ctypes.Structure):
@@ -544,6 +564,10 @@ class SemanticTSDF:
 
     def set_incremental_mesh(self, enabled: bool):
         map_set_incremental_mesh(self.h, enabled)
+
+    def quality(self, gt_points, gt_labels, trunc, stream=None):
+        """After mesh(): RE, Chamfer-L1, coverage, mIoU, accuracy against a ground-truth cloud."""
+        return map_quality(self.h, self.n_classes, gt_points, gt_labels, trunc, stream)
 
     def traversability(self, n_vertices, **params):
         """After mesh(): per-vertex (props, traversable) of that mesh (see map_traversability)."""

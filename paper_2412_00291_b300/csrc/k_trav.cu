@@ -193,10 +193,18 @@ __global__ void __launch_bounds__(256) k_trav_query(TravDev b, TravParamsDev p, 
     }
 }
 
+void launch_weld(const TravDev &b, const int64_t *vkey, long long nv, cudaStream_t s);
+
 static int grid_for(long long n, int per) {
     long long g = (n + per - 1) / per;
     if (g > 148 * 16) g = 148 * 16;
     return (int)(g < 1 ? 1 : g);
+}
+
+void launch_weld(const TravDev &b, const int64_t *vkey, long long nv, cudaStream_t s) {
+    if (nv <= 0) return;
+    k_trav_weld<<<grid_for(nv, 256), 256, 0, s>>>(b, vkey, nv);
+    k_trav_rep<<<grid_for(nv, 256), 256, 0, s>>>(b, nv);
 }
 
 void launch_traversability(const TravDev &b, const TravParamsDev &p, const float *pos, const uint8_t *col,

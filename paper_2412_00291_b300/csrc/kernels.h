@@ -76,5 +76,27 @@ struct TravParamsDev {
 void launch_traversability(const TravDev &b, const TravParamsDev &p, const float *pos, const uint8_t *col,
                            const int64_t *vkey, const int32_t *tri, long long nv, long long nt, float4 *props,
                            uint8_t *trav, cudaStream_t s);
+// welding only: rep[i] = lowest index with vertex i's key (the b.vkeys / b.vfirst tables reset before)
+void launch_weld(const TravDev &b, const int64_t *vkey, long long nv, cudaStream_t s);
+
+// k_quality.cu: map quality against a ground-truth cloud (Sec. IV-B.1)
+struct GridDev {                  // points of one cloud sorted by cell of edge ~truncation
+    uint64_t *ckeys;              // [cmask + 1] cell hash
+    int *ccount, *cstart, *cfill; // [cmask + 1]
+    uint64_t cmask;
+    float4 *spts;                 // [n] sorted {x, y, z, class bits}
+    int *slot;                    // [n] cell slot of each point (-1: not in the cloud)
+    unsigned long long *cursor;
+    unsigned *err;
+    float inv_cell;
+};
+struct QualityAcc {               // device accumulators, reset before a run
+    double sum_d_map, sum_d2_map, sum_d_gt;
+    unsigned long long n_map, n_gt, n_gt_covered, n_labeled;
+};
+// cloud 0 = welded mesh vertices (rep[i] == i), cloud 1 = ground truth
+void launch_quality(const GridDev &gmap, const GridDev &ggt, const int *rep, const float *mpos, const uint8_t *mcol,
+                    long long nv, const float *gpos, const int32_t *glab, long long ng, float trunc, int C,
+                    QualityAcc *acc, unsigned long long *conf, cudaStream_t s);
 
 }  // namespace stsdf

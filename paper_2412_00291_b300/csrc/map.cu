@@ -78,6 +78,11 @@ struct map_t {
     // traversability scratch (grown on demand) and the last extract_mesh's size
     TravDev trav{};
     long long trav_nv_cap = 0;
+    // map quality scratch: grids of the welded vertices and of the ground truth, accumulators
+    GridDev q_map{}, q_gt{};
+    long long q_map_cap = 0, q_gt_cap = 0;
+    QualityAcc *q_acc = nullptr;
+    unsigned long long *q_conf = nullptr;
     bool ext_valid = false;
     long long ext_nv = 0, ext_nt = 0;
     // alignment scratch
@@ -154,7 +159,10 @@ static void free_all(map_t *m) {
                     m->out_keys, m->out_tri, m->out_anchor, m->gn_T, m->gn_acc, m->qb_part, m->pal_dev,
                     m->md.g32, m->md.g16, m->nrm, m->row_dir, m->col_dir, m->trav.vkeys, m->trav.vfirst,
                     m->trav.rep, m->trav.nacc, m->trav.vcell, m->trav.ckeys, m->trav.ccount, m->trav.cstart,
-                    m->trav.cfill, m->trav.spos, m->trav.snrm, m->trav.cursor};
+                    m->trav.cfill, m->trav.spos, m->trav.snrm, m->trav.cursor, m->q_map.ckeys, m->q_map.ccount,
+                    m->q_map.cstart, m->q_map.cfill, m->q_map.spts, m->q_map.slot, m->q_map.cursor, m->q_gt.ckeys,
+                    m->q_gt.ccount, m->q_gt.cstart, m->q_gt.cfill, m->q_gt.spts, m->q_gt.slot, m->q_gt.cursor,
+                    m->q_acc, m->q_conf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (m->h_ctr) cudaFreeHost(m->h_ctr);
@@ -815,6 +823,152 @@ static void trav_free(TravDev &t) {
     t = TravDev{};
 }
 
+// Traversability / welding scratch for meshes of up to nv vertices (grows; synchronises `s` to grow).
+static map_status trav_ensure(map_t *m, long long nv, cudaStream_t s) {
+    TravDev &b = m->trav;
+    if (nv <= m->trav_nv_cap) return MAP_OK;
+    CU(cudaStreamSynchronize(s));
+    trav_free(b);
+    m->trav_nv_cap = 0;
+    uint64_t cap = 1024;
+    while ((long long)cap < 2 * nv) cap <<= 1;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto **q, size_t count) {
+        if (e == cudaSuccess) e = cudaMalloc((void **)q, count * sizeof(**q) + 16);
+    };
+    A(&b.vkeys, cap);
+    A(&b.vfirst, cap);
+    A(&b.ckeys, cap);
+    A(&b.ccount, cap);
+    A(&b.cstart, cap);
+    A(&b.cfill, cap);
+    A(&b.rep, (size_t)nv);
+    A(&b.nacc, (size_t)nv);
+    A(&b.vcell, (size_t)nv);
+    A(&b.spos, (size_t)nv);
+    A(&b.snrm, (size_t)nv);
+    A(&b.cursor, 1);
+    if (e != cudaSuccess) {
+        trav_free(b);
+        return fail(m, MAP_ERR_NOMEM, "mesh scratch allocation failed");
+    }
+    b.vmask = b.cmask = cap - 1;
+    m->trav_nv_cap = nv;
+    return MAP_OK;
+}
+
+static void grid_free(GridDev &g) {
+    void *ptrs[] = {g.ckeys, g.ccount, g.cstart, g.cfill, g.spts, g.slot, g.cursor};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    g = GridDev{};
+}
+
+// A point grid for clouds of up to n points (grows); returns false on allocation failure.
+static bool grid_ensure(GridDev &g, long long &cap_n, long long n) {
+    if (n <= cap_n) return true;
+    grid_free(g);
+    cap_n = 0;
+    uint64_t cap = 1024;
+    while ((long long)cap < 2 * n) cap <<= 1;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto **q, size_t count) {
+        if (e == cudaSuccess) e = cudaMalloc((void **)q, count * sizeof(**q) + 16);
+    };
+    A(&g.ckeys, cap);
+    A(&g.ccount, cap);
+    A(&g.cstart, cap);
+    A(&g.cfill, cap);
+    A(&g.spts, (size_t)n);
+    A(&g.slot, (size_t)n);
+    A(&g.cursor, 1);
+    if (e != cudaSuccess) {
+        grid_free(g);
+        return false;
+    }
+    g.cmask = cap - 1;
+    cap_n = n;
+    return true;
+}
+
+static map_status grid_reset(map_t *m, GridDev &g, double cell, cudaStream_t s) {
+    const size_t tab = (size_t)(g.cmask + 1);
+    CU(cudaMemsetAsync(g.ckeys, 0xFF, tab * sizeof(uint64_t), s));
+    CU(cudaMemsetAsync(g.ccount, 0, tab * sizeof(int), s));
+    CU(cudaMemsetAsync(g.cfill, 0, tab * sizeof(int), s));
+    CU(cudaMemsetAsync(g.cursor, 0, sizeof(unsigned long long), s));
+    g.err = &m->st->err;
+    g.inv_cell = (float)(1.0 / (cell * (1.0 + 1e-5)));
+    return MAP_OK;
+}
+
+extern "C" map_status map_quality(map_t *m, const float *gt_points_dev, const int32_t *gt_labels_dev, int64_t n_gt,
+                                  double trunc, quality_report *out, int64_t *confusion, void *stream) {
+    if (!m || !out || n_gt < 1 || !gt_points_dev || !gt_labels_dev || !(trunc > 0.0) || !(trunc < 1e3))
+        return fail(m, MAP_ERR_ARG, "bad quality arguments (need n_gt >= 1, 0 < trunc < 1e3)");
+    if (!m->ext_valid || m->ext_nv < 1) return fail(m, MAP_ERR_STATE, "no extracted mesh (call extract_mesh first)");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long nv = m->ext_nv;
+    const int C = m->C;
+    map_status st = trav_ensure(m, nv, s);
+    if (st != MAP_OK) return st;
+    if (!grid_ensure(m->q_map, m->q_map_cap, nv) || !grid_ensure(m->q_gt, m->q_gt_cap, n_gt))
+        return fail(m, MAP_ERR_NOMEM, "quality scratch allocation failed");
+    if (!m->q_acc) CU(cudaMalloc(&m->q_acc, sizeof(QualityAcc)));
+    if (!m->q_conf) CU(cudaMalloc(&m->q_conf, 64 * 64 * sizeof(unsigned long long)));
+    TravDev &b = m->trav;
+    b.err = &m->st->err;
+    CU(cudaMemsetAsync(b.vkeys, 0xFF, (size_t)(b.vmask + 1) * sizeof(uint64_t), s));
+    CU(cudaMemsetAsync(b.vfirst, 0x7F, (size_t)(b.vmask + 1) * sizeof(int), s));
+    st = grid_reset(m, m->q_map, trunc, s);
+    if (st == MAP_OK) st = grid_reset(m, m->q_gt, trunc, s);
+    if (st != MAP_OK) return st;
+    CU(cudaMemsetAsync(m->q_acc, 0, sizeof(QualityAcc), s));
+    CU(cudaMemsetAsync(m->q_conf, 0, (size_t)C * C * sizeof(unsigned long long), s));
+    launch_weld(b, m->out_keys, nv, s);
+    launch_quality(m->q_map, m->q_gt, b.rep, m->out_pos, m->out_col, nv, gt_points_dev, gt_labels_dev, n_gt,
+                   (float)trunc, C, m->q_acc, m->q_conf, s);
+    m->launches += 10;
+    st = launch_check(m, "map_quality");
+    if (st != MAP_OK) return st;
+    QualityAcc a;
+    std::vector<unsigned long long> conf((size_t)C * C);
+    CU(cudaMemcpyAsync(&a, m->q_acc, sizeof(a), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(conf.data(), m->q_conf, conf.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    st = map_sync(m, stream);
+    if (st != MAP_OK) return st;
+    out->n_map = (int64_t)a.n_map;
+    out->n_gt = (int64_t)a.n_gt;
+    out->n_labeled = (int64_t)a.n_labeled;
+    out->re = a.n_map ? std::sqrt(a.sum_d2_map / (double)a.n_map) : 0.0;
+    out->cd = (a.n_map && a.n_gt) ? 0.5 * a.sum_d_map / (double)a.n_map + 0.5 * a.sum_d_gt / (double)a.n_gt : 0.0;
+    out->rc = a.n_gt ? (double)a.n_gt_covered / (double)a.n_gt : 0.0;
+    // mIoU over the classes that occur, accuracy over the labelled vertices
+    double iou_sum = 0.0, tp_sum = 0.0, all = 0.0;
+    int occ = 0;
+    for (int c = 0; c < C; ++c) {
+        double tp = (double)conf[(size_t)c * C + c], row = 0.0, colsum = 0.0;
+        for (int k = 0; k < C; ++k) {
+            row += (double)conf[(size_t)c * C + k];
+            colsum += (double)conf[(size_t)k * C + c];
+        }
+        const double den = row + colsum - tp;
+        if (den > 0) {
+            iou_sum += tp / den;
+            ++occ;
+        }
+        tp_sum += tp;
+        all += row;
+    }
+    out->miou = occ ? iou_sum / occ : 0.0;
+    out->acc = all > 0 ? tp_sum / all : 0.0;
+    out->n_correct = (int64_t)tp_sum;
+    if (confusion)
+        for (size_t i = 0; i < conf.size(); ++i) confusion[i] = (int64_t)conf[i];
+    return MAP_OK;
+}
+
 extern "C" map_status map_traversability(map_t *m, const trav_params *p, float *props_dev, uint8_t *trav_dev,
                                          void *stream) {
     if (!m || !p || (m->ext_nv > 0 && (!props_dev || !trav_dev))) return fail(m, MAP_ERR_ARG, "bad arguments");
@@ -823,36 +977,9 @@ extern "C" map_status map_traversability(map_t *m, const trav_params *p, float *
     cudaStream_t s = (cudaStream_t)stream;
     const long long nv = m->ext_nv, nt = m->ext_nt;
     if (nv == 0) return MAP_OK;
+    map_status st = trav_ensure(m, nv, s);
+    if (st != MAP_OK) return st;
     TravDev &b = m->trav;
-    if (nv > m->trav_nv_cap) {
-        CU(cudaStreamSynchronize(s));
-        trav_free(b);
-        m->trav_nv_cap = 0;
-        uint64_t cap = 1024;
-        while ((long long)cap < 2 * nv) cap <<= 1;
-        cudaError_t e = cudaSuccess;
-        auto A = [&](auto **q, size_t count) {
-            if (e == cudaSuccess) e = cudaMalloc((void **)q, count * sizeof(**q) + 16);
-        };
-        A(&b.vkeys, cap);
-        A(&b.vfirst, cap);
-        A(&b.ckeys, cap);
-        A(&b.ccount, cap);
-        A(&b.cstart, cap);
-        A(&b.cfill, cap);
-        A(&b.rep, (size_t)nv);
-        A(&b.nacc, (size_t)nv);
-        A(&b.vcell, (size_t)nv);
-        A(&b.spos, (size_t)nv);
-        A(&b.snrm, (size_t)nv);
-        A(&b.cursor, 1);
-        if (e != cudaSuccess) {
-            trav_free(b);
-            return fail(m, MAP_ERR_NOMEM, "traversability scratch allocation failed");
-        }
-        b.vmask = b.cmask = cap - 1;
-        m->trav_nv_cap = nv;
-    }
     b.err = &m->st->err;
     b.inv_cell = (float)(1.0 / (p->radius * (1.0 + 1e-5)));
     const size_t tab = (size_t)(b.vmask + 1);
