@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--mesh-every", type=int, default=1,
                     help="1: incremental re-meshing every scan; K > 1: no per-scan meshing, a full "
                          "marching-cubes pass over the whole map every K scans (inside the timed steps)")
+    ap.add_argument("--quality", action="store_true",
+                    help="after the timed scans: RE, Chamfer-L1, coverage, mIoU, accuracy of the map's mesh "
+                         "against the noise-free scans of a denser scanner on the same trajectory")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512)
@@ -265,6 +268,34 @@ def fp16_report(P, w, lid, m16, make_step, n_frames, cfg, dev):
             "mesh_vertex_p99_err_m": float(np.percentile(dp, 99)) if len(common) else 0.0}
 
 
+def quality_report(P, w, m, n_frames, dev, every=5, dense=(2, 2)):
+    """Map quality (Sec. IV-B.1) of m after n_frames scans: its mesh against the noise-free scans of a
+    scanner with dense[0] x the beams and dense[1] x the columns on every `every`-th pose of the same
+    trajectory (true classes), truncation 2 nu."""
+    import dataclasses
+    import torch
+    L = w.lidar
+    lid = synth.Lidar(L.H * dense[0], L.W * dense[1], L.fov_up, L.fov_down, L.r_min, L.r_max)
+    wg = dataclasses.replace(w, sigma=0.0, label_mode="probs", lidar=lid)
+    scene = synth.make_scene(wg)
+    Ts = synth.trajectory(wg, n_frames)
+    pts, lab = [], []
+    for k in range(0, n_frames, every):
+        f = synth.make_frame(wg, scene, Ts[k], k)
+        ok = np.isfinite(f.points).all(axis=1)
+        p = f.points[ok].astype(np.float64)
+        pts.append(torch.from_numpy((p @ f.T[:3, :3].T + f.T[:3, 3]).astype(np.float32)))
+        lab.append(torch.from_numpy(f.labels[ok].astype(np.int32)))
+    G = torch.cat(pts).to(dev)
+    lg = torch.cat(lab).to(dev)
+    m.mesh()
+    q = m.quality(G, lg, 2 * w.voxel_size)
+    q = {k: v for k, v in q.items() if k != "confusion"}
+    q["ground_truth"] = (f"noise-free scans, {lid.H}x{lid.W} scanner, every {every}th of {n_frames} poses, "
+                         f"true classes ({int(G.shape[0])} points); truncation 2 nu = {2 * w.voxel_size} m")
+    return q
+
+
 def cpu_baseline(w, budget_s=15.0, max_frames=8, col_stride=1, distance="projective"):
     """The FP64 oracle as it stands, on all host cores, over the first scans of the workload."""
     import oracle
@@ -447,6 +478,9 @@ def run_ours(args, rank, world, local_rank):
         step(args.warmup + i)
     torch.cuda.synchronize()
     phase_ms, fstats = P.map_profile_end(tsdf.h, args.steps)
+    qual = None
+    if args.quality:
+        qual = quality_report(P, w, tsdf, args.warmup + args.steps, dev)
     fp16 = None
     if storage == 1 and not args.no_fp16_report:
         fp16 = fp16_report(P, w, lid, tsdf, make_step, args.warmup + args.steps, cfg, dev)
@@ -551,6 +585,7 @@ def run_ours(args, rank, world, local_rank):
                         "the shares are of the summed kernel times",
         "concurrent_semantic_and_mesh": stage,
         "full_mesh": full_mesh,
+        "quality": qual,
         "cpu_baseline": cpu,
         "fp16_vs_fp32": fp16,
         "e2e": e2e,
