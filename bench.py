@@ -296,7 +296,7 @@ def quality_report(P, w, m, n_frames, dev, every=5, dense=(2, 2)):
     return q
 
 
-def cpu_baseline(w, budget_s=15.0, max_frames=8, col_stride=1, distance="projective"):
+def cpu_baseline(w, budget_s=12.0, max_frames=200, col_stride=1, distance="projective"):
     """The FP64 oracle as it stands, on all host cores, over the first scans of the workload."""
     import oracle
     nthreads = os.cpu_count() or 1
