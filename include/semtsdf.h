@@ -222,6 +222,39 @@ map_status map_remesh_all(map_t *map, void *stream);
  * MAP_ERR_ARG for other values.  Applies to the following scans. */
 map_status map_set_incremental_mesh(map_t *map, int32_t enabled);
 
+/* ---- class update from camera label images (Sec. III-C.3) ---- */
+
+/* Pinhole camera: x right, y down, z forward; pixel (u, v) looks along
+ * ((u - cx) / fx, (v - cy) / fy, 1); surfaces are searched up to r_max. */
+typedef struct {
+    int32_t width, height;
+    double fx, fy, cx, cy;
+    double r_max;
+} camera_intrinsics;
+
+/* Fuse one label image: only visible, observed voxels (W > 0) in the camera
+ * frustum take its class likelihood (Sec. III-C.3, Eq. bayesian_filter).
+ * Visibility by ray casting the TSDF: each pixel's ray visits the voxels it
+ * passes through in order (exact cell traversal from the camera centre up
+ * to r_max); the first pair of consecutive observed voxels with D >= 0 then
+ * D < 0 is the visible surface, its range interpolated between the two
+ * voxel centres' ranges along the ray.  Every observed voxel that projects
+ * to a pixel with a surface and lies within the truncation of it
+ * (|range - distance from the camera| <= tau) takes the pixel's likelihood,
+ * exactly as a scan point's (hard label: p_hit model; probabilities:
+ * floored).  The metric map (D, W) and the mesh are unchanged; vertex
+ * classes follow at the next extract_mesh.
+ *   labels_dev [height][width] int32 (< 0 or >= C: no label) or NULL;
+ *   probs_dev [height][width][C] float32 or NULL (exactly one non-NULL);
+ *   T_world_cam host double[16] row-major pose of the camera;
+ *   range_dev [height][width] float32 (may be NULL): receives each pixel's
+ *   surface range (NaN where none).
+ * Asynchronous.  map_get_frame_stats then reports MAP_STAT_VOXELS_SEMANTIC
+ * for this image. */
+map_status integrate_labels_camera(map_t *map, const camera_intrinsics *cam, const int32_t *labels_dev,
+                                   const float *probs_dev, const double T_world_cam[16], float *range_dev,
+                                   void *stream);
+
 /* ---- mesh traversability (Sec. III-D, Table II) ---- */
 
 /* Thresholds of the traversability test.  Defaults (map_trav_params_default)

@@ -76,6 +76,7 @@ _SIGS = {
     "map_trav_params_default": ([P], I32),
     "map_traversability": ([P, P, P, P, P], I32),
     "map_quality": ([P, P, P, I64, D, P, P, P], I32),
+    "integrate_labels_camera": ([P, P, P, P, P, P, P], I32),
     "extract_mesh_noalloc": ([P, P, P, P, P, P, I64, I64, P, P, P], I32),
     "query_sdf": ([P, P, I64, P, P, P], I32),
     "query_sdf_backward": ([P, P, P, I64, P, P, P], I32),
@@ -265,6 +266,25 @@ def map_remesh_all(h, stream=None):
 
 def map_set_incremental_mesh(h, enabled: bool):
     _check(_lib.map_set_incremental_mesh(h, 1 if enabled else 0), h)
+
+
+class CameraIntrinsics(ctypes.Structure):
+    _fields_ = [("width", I32), ("height", I32), ("fx", D), ("fy", D), ("cx", D), ("cy", D), ("r_max", D)]
+
+
+def integrate_labels_camera(h, cam: dict, T_world_cam, labels=None, probs=None, stream=None):
+    """Class update from a camera label image (CUDA tensors: labels [H, W] int32 or probs [H, W, C]
+    float32).  cam: width, height, fx, fy, cx, cy, r_max.  Returns the per-pixel surface range
+    ([H, W] float32 CUDA tensor, NaN where none)."""
+    c = CameraIntrinsics(int(cam["width"]), int(cam["height"]), float(cam["fx"]), float(cam["fy"]),
+                         float(cam["cx"]), float(cam["cy"]), float(cam.get("r_max", 50.0)))
+    T = np.ascontiguousarray(T_world_cam, np.float64).reshape(16)
+    rng = torch.empty((c.height, c.width), dtype=torch.float32, device="cuda")
+    lp = None if labels is None else _dev_ptr(labels, torch.int32, "labels")
+    pp = None if probs is None else _dev_ptr(probs, torch.float32, "probs")
+    _check(_lib.integrate_labels_camera(h, ctypes.byref(c), lp, pp, _np_ptr(T), ctypes.c_void_p(rng.data_ptr()),
+                                        _stream(stream)), h)
+    return rng
 
 
 class QualityReport(ctypes.Structure):
@@ -564,6 +584,10 @@ class SemanticTSDF:
 
     def set_incremental_mesh(self, enabled: bool):
         map_set_incremental_mesh(self.h, enabled)
+
+    def integrate_camera(self, cam, T_world_cam, labels=None, probs=None, stream=None):
+        """Class update from a camera label image; returns the per-pixel surface range."""
+        return integrate_labels_camera(self.h, cam, T_world_cam, labels=labels, probs=probs, stream=stream)
 
     def quality(self, gt_points, gt_labels, trunc, stream=None):
         """After mesh(): RE, Chamfer-L1, coverage, mIoU, accuracy against a ground-truth cloud."""

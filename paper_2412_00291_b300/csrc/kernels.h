@@ -79,6 +79,19 @@ void launch_traversability(const TravDev &b, const TravParamsDev &p, const float
 // welding only: rep[i] = lowest index with vertex i's key (the b.vkeys / b.vfirst tables reset before)
 void launch_weld(const TravDev &b, const int64_t *vkey, long long nv, cudaStream_t s);
 
+// k_camera.cu: class update from a camera label image (Sec. III-C.3)
+struct CamConst {
+    int W, H, max_steps;          // image size; traversal step bound
+    float fx, fy, cx, cy, inv_fx, inv_fy;
+    float R[9];                   // world-from-camera rotation, row-major (x right, y down, z forward)
+    float c[3];                   // camera centre, world
+    float nu, inv_nu, r_max;
+};
+// range [H*W]: hit range per pixel (NaN: none); sc carries tau, C, the likelihood model and the
+// label image (labels or probs, per pixel) for the class update
+void launch_camera(const CamConst &cc, const ScanConst &sc, const MapDev &md, const FrameDev &fd, float *range,
+                   int grid_semantic, cudaStream_t s);
+
 // k_quality.cu: map quality against a ground-truth cloud (Sec. IV-B.1)
 struct GridDev {                  // points of one cloud sorted by cell of edge ~truncation
     uint64_t *ckeys;              // [cmask + 1] cell hash

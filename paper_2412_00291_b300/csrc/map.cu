@@ -83,6 +83,9 @@ struct map_t {
     long long q_map_cap = 0, q_gt_cap = 0;
     QualityAcc *q_acc = nullptr;
     unsigned long long *q_conf = nullptr;
+    // camera class update: hit ranges of the last image (when the caller passes none)
+    float *cam_range = nullptr;
+    long long cam_range_cap = 0;
     bool ext_valid = false;
     long long ext_nv = 0, ext_nt = 0;
     // alignment scratch
@@ -162,7 +165,7 @@ static void free_all(map_t *m) {
                     m->trav.cfill, m->trav.spos, m->trav.snrm, m->trav.cursor, m->q_map.ckeys, m->q_map.ccount,
                     m->q_map.cstart, m->q_map.cfill, m->q_map.spts, m->q_map.slot, m->q_map.cursor, m->q_gt.ckeys,
                     m->q_gt.ccount, m->q_gt.cstart, m->q_gt.cfill, m->q_gt.spts, m->q_gt.slot, m->q_gt.cursor,
-                    m->q_acc, m->q_conf};
+                    m->q_acc, m->q_conf, m->cam_range};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (m->h_ctr) cudaFreeHost(m->h_ctr);
@@ -802,6 +805,77 @@ extern "C" map_status extract_mesh(map_t *m, mesh_view *out, void *stream) {
     out->vertex_keys = m->out_keys;
     out->triangles = m->out_tri;
     out->triangle_anchors = m->out_anchor;
+    return MAP_OK;
+}
+
+extern "C" map_status integrate_labels_camera(map_t *m, const camera_intrinsics *cam, const int32_t *labels_dev,
+                                              const float *probs_dev, const double T_world_cam[16], float *range_dev,
+                                              void *stream) {
+    if (!m || !cam || !T_world_cam || ((labels_dev == nullptr) == (probs_dev == nullptr)))
+        return fail(m, MAP_ERR_ARG, "need intrinsics, a pose and exactly one of labels / probs");
+    if (cam->width < 1 || cam->height < 1 || (long long)cam->width * cam->height > (1ll << 26) ||
+        !(cam->fx > 0.0) || !(cam->fy > 0.0) || !(cam->r_max > 0.0) || !(cam->r_max < 1e4))
+        return fail(m, MAP_ERR_ARG, "bad camera intrinsics (1 <= W*H <= 2^26, fx, fy > 0, 0 < r_max < 1e4)");
+    for (int i = 0; i < 16; ++i)
+        if (!std::isfinite(T_world_cam[i])) return fail(m, MAP_ERR_BAD_POSE, "non-finite camera pose");
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double q = 0.0;
+            for (int k = 0; k < 3; ++k) q += T_world_cam[4 * k + a] * T_world_cam[4 * k + b];
+            if (std::fabs(q - (a == b ? 1.0 : 0.0)) > 1e-6) return fail(m, MAP_ERR_BAD_POSE, "rotation not orthonormal");
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long np = (long long)cam->width * cam->height;
+    float *range = range_dev;
+    if (!range) {
+        if (np > m->cam_range_cap) {
+            CU(cudaStreamSynchronize(s));
+            if (m->cam_range) cudaFree(m->cam_range);
+            m->cam_range = nullptr;
+            m->cam_range_cap = 0;
+            CU(cudaMalloc(&m->cam_range, np * sizeof(float)));
+            m->cam_range_cap = np;
+        }
+        range = m->cam_range;
+    }
+    CamConst cc;
+    cc.W = cam->width;
+    cc.H = cam->height;
+    const double nu = m->cfg.voxel_size;
+    cc.max_steps = (int)std::min(1e8, 3.0 * cam->r_max / nu + 8.0);
+    cc.fx = (float)cam->fx;
+    cc.fy = (float)cam->fy;
+    cc.cx = (float)cam->cx;
+    cc.cy = (float)cam->cy;
+    cc.inv_fx = (float)(1.0 / cam->fx);
+    cc.inv_fy = (float)(1.0 / cam->fy);
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) cc.R[3 * r + c] = (float)T_world_cam[4 * r + c];
+        cc.c[r] = (float)T_world_cam[4 * r + 3];
+    }
+    cc.nu = (float)nu;
+    cc.inv_nu = (float)(1.0 / nu);
+    cc.r_max = (float)cam->r_max;
+    // class-update constants: the likelihood model of the scans, per pixel of the image
+    ScanConst sc;
+    std::memset(&sc, 0, sizeof(sc));
+    sc.C = m->C;
+    sc.tau = (float)m->cfg.truncation;
+    sc.log_phit = (float)std::log(m->cfg.p_hit);
+    sc.log_pmiss = (float)std::log((1.0 - m->cfg.p_hit) / (m->C - 1));
+    sc.lik_floor = (float)m->cfg.lik_floor;
+    sc.logp_floor = (float)m->cfg.logp_floor;
+    sc.has_probs = probs_dev != nullptr;
+    sc.probs_vec4 = probs_dev && (m->C % 4 == 0) && (((uintptr_t)probs_dev & 15) == 0);
+    sc.labels = labels_dev;
+    sc.probs = probs_dev;
+    CU(cudaMemsetAsync(m->fd.ctr, 0, CT_COUNT * sizeof(unsigned long long), s));
+    launch_camera(cc, sc, m->md, m->fd, range, m->grid_semantic, s);
+    m->launches += 3;
+    map_status st = launch_check(m, "integrate_labels_camera");
+    if (st != MAP_OK) return st;
+    // map_get_frame_stats now reports this image (MAP_STAT_VOXELS_SEMANTIC)
+    CU(cudaMemcpyAsync(m->h_ctr, m->fd.ctr, CT_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     return MAP_OK;
 }
 
