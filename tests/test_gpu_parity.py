@@ -13,6 +13,7 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 import synth  # noqa: E402
+from tests.fields import block_voxels  # noqa: E402
 from tests.gpu_compare import compare_blocks, compare_meshes  # noqa: E402
 
 
@@ -275,6 +276,58 @@ def test_loop64_full_size_sampled():
                colors=full["colors"][used], triangles=remap[sub_t], triangle_anchors=full["triangle_anchors"][keep])
     mrep = compare_meshes(sub, om.mesh(np.array(sorted(base_set))), om, w.voxel_size)
     print("loop64 sampled mesh:", mrep)
+
+
+def test_loop64_error_binned_by_range():
+    """|dD| of the 64 x 2048 scans (0.1 m voxels, 100 m range) by the voxel's distance from the
+    sensor: blocks sampled evenly from four range bins; every bin within 1e-4 nu."""
+    p = _lib()
+    w = synth.loop64()
+    L = _lidar(p, w.lidar)
+    gm = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=65536, hash_capacity=1 << 17,
+                        mesh_vertex_capacity=1 << 23, mesh_triangle_capacity=1 << 24)
+    scene = synth.make_scene(w)
+    Ts = synth.trajectory(w)
+    K = 3
+    frames = [synth.make_frame(w, scene, Ts[k], k) for k in range(K)]
+    probe = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    probe.set_track(np.zeros((0, 3), np.int32))
+    for fr in frames:
+        probe.integrate(w.lidar, fr.points, fr.T, probs=fr.probs)
+    cand = probe.alloc_blocks()
+    centre = (cand + 0.5) * 8 * w.voxel_size
+    rng_m = np.linalg.norm(centre - frames[0].T[:3, 3], axis=1)
+    bins = [(0.0, 16.0), (16.0, 32.0), (32.0, 64.0), (64.0, 100.0)]
+    rs = np.random.default_rng(11)
+    pick = []
+    for lo, hi in bins:
+        idx = np.flatnonzero((rng_m >= lo) & (rng_m < hi))
+        pick.append(cand[rs.choice(idx, size=min(24, len(idx)), replace=False)])
+    track = np.concatenate(pick)
+    om = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    om.set_track(track)
+    for fr in frames:
+        gm.integrate(L, _dev(fr.points), fr.T, probs=_dev(fr.probs))
+        om.integrate(w.lidar, fr.points, fr.T, probs=fr.probs)
+    g = gm.read_blocks(track, want_logp=False)
+    tol = 1e-4 * w.voxel_size
+    rep = []
+    for lo, hi in bins:
+        d_all = []
+        for i, b in enumerate(track):
+            o = om.read_block(b)
+            if o is None:
+                continue
+            r = np.linalg.norm(block_voxels(b) * w.voxel_size - frames[0].T[:3, 3], axis=1)
+            sel = (o["taint"] & 1 == 0) & (o["W"] > 0) & (r >= lo) & (r < hi)
+            d_all.append(np.abs(g["D"][i] - o["D"])[sel])
+        d = np.concatenate(d_all) if d_all else np.zeros(0)
+        rep.append((lo, hi, len(d), float(d.max(initial=0)), float(np.percentile(d, 99)) if len(d) else 0.0))
+        assert len(d) > 100, (lo, hi, len(d))
+        assert d.max() <= tol, (lo, hi, d.max())
+    print("loop64 |dD| by range (m): " + "; ".join(f"[{lo:.0f}, {hi:.0f}) n {n} max {mx:.2e} p99 {p9:.2e}"
+                                                   for lo, hi, n, mx, p9 in rep))
+    gm.close()
 
 
 @pytest.mark.parametrize("storage,cls", [(0, "probs"), (1, "labels")])
