@@ -317,9 +317,21 @@ def cpu_baseline(w, budget_s=12.0, max_frames=200, col_stride=1, distance="proje
         k += 1
         if secs > budget_s:
             break
+    # the same oracle on one core, over the first scans of a fresh map (a bounded sample)
+    m1 = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes, distance=distance)
+    pts1, secs1, k1 = 0, 0.0, 0
+    for f in frames_for(w, 3):
+        t0 = time.perf_counter()
+        m1.integrate(w.lidar, f.points, f.T, labels=None if f.probs is not None else f.labels, probs=f.probs,
+                     nthreads=1)
+        secs1 += time.perf_counter() - t0
+        pts1 += len(f.points)
+        k1 += 1
     return {"value": done_pts / secs, "unit": "points/s", "cores": nthreads, "kind": "oracle",
             "sample": f"first {k} scans of {w.name}" + (f", every {col_stride}th column" if col_stride > 1 else "") +
-                      f" ({done_pts} points, {secs:.1f} s, fresh map, FP64, OpenMP over blocks)"}
+                      f" ({done_pts} points, {secs:.1f} s, fresh map, FP64, OpenMP over blocks)",
+            "single_thread": {"value": pts1 / secs1, "unit": "points/s", "cores": 1,
+                              "sample": f"first {k1} scans, fresh map ({pts1} points, {secs1:.1f} s)"}}
 
 
 def run_reference(args, rank, world):
