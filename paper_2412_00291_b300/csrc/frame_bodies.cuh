@@ -1,8 +1,8 @@
 // Device bodies of the per-frame pipeline, shared by the single-map kernels
-// (k_alloc.cu, k_scan.cu, k_integrate.cu, k_mesh.cu) and the batched
+// (k_alloc.cu, k_integrate.cu, k_mesh.cu, k_camera.cu) and the batched
 // persistent kernel (k_batch.cu).  Each body processes one work item: a point,
-// a pixel, a touched block (one warp), a class-update entry, a block to
-// re-mesh (one warp).
+// a pixel of the normal image, half of a touched block (one warp), a
+// class-update entry, a block to re-mesh (one warp).
 #pragma once
 
 #include "kernels.h"

@@ -29,8 +29,7 @@ __global__ void k_link_all(MapDev md) {
     }
 }
 
-// Every allocated block into the re-mesh list (full re-mesh).
-// Every allocated pool slot, in slot order, into the re-mesh list.
+// Every allocated pool slot, in slot order, into the re-mesh list (full re-mesh).
 __global__ void k_list_all(MapDev md, FrameDev fd) {
     unsigned long long pc = md.st->pool_count;
     if (pc > (unsigned long long)md.max_blocks) pc = md.max_blocks;

@@ -1,8 +1,8 @@
 // Projective TSDF update (Sec. III-C.2) and the recursive Bayesian class
-// update (Sec. III-C.3, Eq. bayesian_filter).  k_tsdf: one CTA per touched
-// block (persistent grid-stride over the device-side list U_k), one voxel per
-// thread per step, 512 voxels per block; it lists the voxels whose class
-// distribution must change, and k_semantic streams that list.
+// update (Sec. III-C.3, Eq. bayesian_filter).  k_tsdf: one warp per half of
+// a touched block (256 voxels; grid-stride over the device-side list U_k,
+// 8 warps per CTA); it lists the voxels whose class distribution must change,
+// and k_semantic streams that list, one voxel per thread.
 //
 // Per voxel v of block b:
 //   x_l   = R^T (nu v - t)            (its direction picks the pixel)
