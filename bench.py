@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--max-blocks", type=int, default=0, help="pool size override (profiling runs)")
+    ap.add_argument("--frames", type=int, default=0,
+                    help="trav / camera workloads: build the map from this many scans (default: all 200)")
     ap.add_argument("--mesh-cap", type=int, default=0, help="mesh arena vertex capacity override")
     ap.add_argument("--no-fp16-report", action="store_true", help="skip the FP16-vs-FP32 comparison")
     return ap.parse_args()
@@ -755,9 +757,11 @@ def run_trav(args, rank, world, local_rank):
     w = workload("loop64", rank)
     L = w.lidar
     lid = P.lidar_intrinsics(L.H, L.W, L.fov_up, L.fov_down, L.r_min, L.r_max)
-    m = P.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes)
+    cfg = {"max_blocks": args.max_blocks, "hash_capacity": 4 * args.max_blocks} if args.max_blocks else {}
+    m = P.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, **cfg)
+    n_frames = args.frames or w.frames
     cpu = None
-    for k, f in enumerate(frames_for(w, w.frames)):
+    for k, f in enumerate(frames_for(w, n_frames)):
         m.integrate(lid, torch.from_numpy(f.points).to(dev), f.T, probs=torch.from_numpy(f.probs).to(dev))
         if k == 1 and rank == 0 and not args.no_cpu_baseline:
             mh = {kk: v.cpu().numpy() for kk, v in m.mesh().items()}
@@ -788,7 +792,7 @@ def run_trav(args, rank, world, local_rank):
     peak, kind = measured_peaks()
     g = io_bytes / (float(np.mean(ms)) * 1e-3) / 1e9
     line = {
-        "metric": "mesh traversability, vertices per second (whole 200-scan 64x2048 map)",
+        "metric": f"mesh traversability, vertices per second (whole {n_frames}-scan 64x2048 map)",
         "value": nv / (float(np.mean(ms)) * 1e-3), "unit": "vertices/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
@@ -820,9 +824,11 @@ def run_camera(args, rank, world, local_rank):
     w = workload("loop64", rank)
     L = w.lidar
     lid = P.lidar_intrinsics(L.H, L.W, L.fov_up, L.fov_down, L.r_min, L.r_max)
-    m = P.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes)
+    cfg = {"max_blocks": args.max_blocks, "hash_capacity": 4 * args.max_blocks} if args.max_blocks else {}
+    m = P.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, **cfg)
+    n_frames = args.frames or w.frames
     Ts = []
-    for f in frames_for(w, w.frames):
+    for f in frames_for(w, n_frames):
         m.integrate(lid, torch.from_numpy(f.points).to(dev), f.T, probs=torch.from_numpy(f.probs).to(dev))
         Ts.append(f.T.copy())
     Wc, Hc = 2048, 1536
@@ -858,7 +864,7 @@ def run_camera(args, rank, world, local_rank):
         return
     ms = np.array(ms)
     line = {
-        "metric": "camera label images fused per second (2048x1536, 200-scan 64x2048 map)",
+        "metric": f"camera label images fused per second (2048x1536, {n_frames}-scan 64x2048 map)",
         "value": 1e3 / float(np.mean(ms)), "unit": "images/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp32", "data": "synthetic",

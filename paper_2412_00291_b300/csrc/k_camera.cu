@@ -3,9 +3,10 @@
 // likelihood, found by ray casting the TSDF, and the distribution is updated
 // by the recursive Bayesian filter (Eq. bayesian_filter).
 //
+//   k_block_bounds the bounding box of the allocated blocks;
 //   k_cam_raycast  per pixel: the voxels the pixel's ray passes through, in
 //                  order (exact cell traversal from the camera centre up to
-//                  r_max); the first pair of consecutive observed voxels with
+//                  r_max, or to where the ray leaves the box); the first pair of consecutive observed voxels with
 //                  D >= 0 then D < 0 is the visible surface, its range along
 //                  the ray interpolated between the two centres' ranges;
 //   k_cam_select   one warp per allocated block (blocks wholly behind the
@@ -20,8 +21,43 @@
 
 namespace stsdf {
 
-__global__ void __launch_bounds__(256) k_cam_raycast(CamConst cc, MapDev md, float *range) {
+// Bounding box of the allocated blocks, in block coordinates: bounds[0..2] min, [3..5] max
+// (initialised to +- large by the caller).  One atomic per warp and bound.
+__global__ void __launch_bounds__(256) k_block_bounds(MapDev md, int *bounds) {
+    unsigned long long pc = md.st->pool_count;
+    if (pc > (unsigned long long)md.max_blocks) pc = md.max_blocks;
+    int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
+    for (unsigned long long s = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; s < pc;
+         s += (unsigned long long)gridDim.x * blockDim.x) {
+        int b[3];
+        unpack_block(md.slot_key[s], b[0], b[1], b[2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = min(lo[k], b[k]);
+            hi[k] = max(hi[k], b[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int l = __reduce_min_sync(0xffffffffu, lo[k]), h = __reduce_max_sync(0xffffffffu, hi[k]);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&bounds[k], l);
+            atomicMax(&bounds[3 + k], h);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_cam_raycast(CamConst cc, MapDev md, const int *__restrict__ bounds,
+                                                     float *range) {
     const int np = cc.W * cc.H;
+    // the allocated blocks' box in metres: cells [nu (8 b - 1/2), nu (8 b + 7 + 1/2))
+    float blo[3], bhi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        // (in float: an empty map leaves the bounds at +-2^31 and an empty box)
+        blo[k] = ((float)bounds[k] * BS - 0.5f) * cc.nu;
+        bhi[k] = ((float)bounds[3 + k] * BS + (BS - 0.5f)) * cc.nu;
+    }
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
         const int u = p % cc.W, v = p / cc.W;
         float d0 = ((float)u - cc.cx) * cc.inv_fx, d1 = ((float)v - cc.cy) * cc.inv_fy, d2 = 1.f;
@@ -49,10 +85,27 @@ __global__ void __launch_bounds__(256) k_cam_raycast(CamConst cc, MapDev md, flo
                 tdel[k] = -cc.nu / d[k];
             }
         }
+        // no observed voxel lies outside the box: the traversal ends where the ray leaves it
+        // (a voxel's cells are entered before that, so the visited cells up to then are unchanged)
+        float t_end = cc.r_max;
+        {
+            float t_in = 0.f, t_out = cc.r_max;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (d[k] != 0.f) {
+                    const float a = (blo[k] - cc.c[k]) / d[k], b = (bhi[k] - cc.c[k]) / d[k];
+                    t_in = fmaxf(t_in, fminf(a, b));
+                    t_out = fminf(t_out, fmaxf(a, b));
+                } else if (cc.c[k] < blo[k] || cc.c[k] > bhi[k]) {
+                    t_out = -1.f;
+                }
+            }
+            t_end = t_in > t_out ? -1.f : fminf(cc.r_max, t_out + cc.nu);
+        }
         float hit = NAN, t = 0.f, pt = 0.f, pD = 0.f;
         bool prev = false;
         int bk[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, slot = -1;   // no block yet
-        for (int it = 0; it < cc.max_steps && t <= cc.r_max; ++it) {
+        for (int it = 0; it < cc.max_steps && t <= t_end; ++it) {
             int b[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) b[k] = vx[k] >= 0 ? vx[k] / BS : -((-vx[k] + BS - 1) / BS);
@@ -156,11 +209,15 @@ __global__ void __launch_bounds__(256) k_cam_select(CamConst cc, ScanConst sc, M
 }
 
 void launch_camera(const CamConst &cc, const ScanConst &sc, const MapDev &md, const FrameDev &fd, float *range,
-                   int grid_semantic, cudaStream_t s) {
+                   int *bounds, int grid_semantic, cudaStream_t s) {
     const int np = cc.W * cc.H;
     int g = (np + 255) / 256;
     if (g > 148 * 16) g = 148 * 16;
-    k_cam_raycast<<<g, 256, 0, s>>>(cc, md, range);
+    int gb = (md.max_blocks + 255) / 256;
+    if (gb > 148 * 4) gb = 148 * 4;
+    if (gb < 1) gb = 1;
+    k_block_bounds<<<gb, 256, 0, s>>>(md, bounds);
+    k_cam_raycast<<<g, 256, 0, s>>>(cc, md, bounds, range);
     int gs = (md.max_blocks + 7) / 8;
     if (gs > 148 * 8) gs = 148 * 8;
     if (gs < 1) gs = 1;

@@ -89,8 +89,9 @@ struct CamConst {
 };
 // range [H*W]: hit range per pixel (NaN: none); sc carries tau, C, the likelihood model and the
 // label image (labels or probs, per pixel) for the class update
+// bounds: int[6] scratch, set to {+big x3, -big x3} before the call
 void launch_camera(const CamConst &cc, const ScanConst &sc, const MapDev &md, const FrameDev &fd, float *range,
-                   int grid_semantic, cudaStream_t s);
+                   int *bounds, int grid_semantic, cudaStream_t s);
 
 // k_quality.cu: map quality against a ground-truth cloud (Sec. IV-B.1)
 struct GridDev {                  // points of one cloud sorted by cell of edge ~truncation

@@ -86,6 +86,7 @@ struct map_t {
     // camera class update: hit ranges of the last image (when the caller passes none)
     float *cam_range = nullptr;
     long long cam_range_cap = 0;
+    int *cam_bounds = nullptr;      // box of the allocated blocks (ray-cast bound)
     bool ext_valid = false;
     long long ext_nv = 0, ext_nt = 0;
     // alignment scratch
@@ -165,7 +166,7 @@ static void free_all(map_t *m) {
                     m->trav.cfill, m->trav.spos, m->trav.snrm, m->trav.cursor, m->q_map.ckeys, m->q_map.ccount,
                     m->q_map.cstart, m->q_map.cfill, m->q_map.spts, m->q_map.slot, m->q_map.cursor, m->q_gt.ckeys,
                     m->q_gt.ccount, m->q_gt.cstart, m->q_gt.cfill, m->q_gt.spts, m->q_gt.slot, m->q_gt.cursor,
-                    m->q_acc, m->q_conf, m->cam_range};
+                    m->q_acc, m->q_conf, m->cam_range, m->cam_bounds};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (m->h_ctr) cudaFreeHost(m->h_ctr);
@@ -870,8 +871,11 @@ extern "C" map_status integrate_labels_camera(map_t *m, const camera_intrinsics 
     sc.labels = labels_dev;
     sc.probs = probs_dev;
     CU(cudaMemsetAsync(m->fd.ctr, 0, CT_COUNT * sizeof(unsigned long long), s));
-    launch_camera(cc, sc, m->md, m->fd, range, m->grid_semantic, s);
-    m->launches += 3;
+    if (!m->cam_bounds) CU(cudaMalloc(&m->cam_bounds, 6 * sizeof(int)));
+    CU(cudaMemsetAsync(m->cam_bounds, 0x7F, 3 * sizeof(int), s));        // min: 0x7f7f7f7f
+    CU(cudaMemsetAsync(m->cam_bounds + 3, 0x80, 3 * sizeof(int), s));    // max: 0x80808080 (< any block)
+    launch_camera(cc, sc, m->md, m->fd, range, m->cam_bounds, m->grid_semantic, s);
+    m->launches += 4;
     map_status st = launch_check(m, "integrate_labels_camera");
     if (st != MAP_OK) return st;
     // map_get_frame_stats now reports this image (MAP_STAT_VOXELS_SEMANTIC)
