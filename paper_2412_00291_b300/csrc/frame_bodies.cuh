@@ -275,23 +275,25 @@ __device__ __forceinline__ float acos_poly(float c) {
     return __fmaf_rn(-c, asin_q(__fmul_rn(c, c)), 1.57079632679489662f);
 }
 
-// Pixel of voxel vi of block (bx, by, bz) (Sec. III-C.1), or -1 outside the
-// image; also returns the voxel's offset from the sensor in voxel units
-// (exact integer part minus the fraction's high part, m) and |x_l|^2 (rr2)
-// and its reciprocal square root (irr) in those units.
-__device__ __forceinline__ int tsdf_pixel(const ScanConst &sc, int bx, int by, int bz, int vi, float &m0, float &m1,
-                                          float &m2, float &rr2, float &irr) {
+// Direction of voxel vi of block (bx, by, bz) from the sensor, in the LiDAR
+// frame and voxel units (exact integer offset minus the fraction's high part,
+// rotated by R^T).  (Every rounding is explicit here and in the update bodies
+// below, so that each kernel that inlines them computes the same bits.)
+__device__ __forceinline__ void tsdf_dir(const ScanConst &sc, int bx, int by, int bz, int vi, float &x0, float &x1,
+                                         float &x2) {
     const int lx = vi & 7, ly = (vi >> 3) & 7, lz = vi >> 6;
-    m0 = (float)(8 * bx + lx - sc.k[0]);
-    m1 = (float)(8 * by + ly - sc.k[1]);
-    m2 = (float)(8 * bz + lz - sc.k[2]);
-    // (every rounding is explicit here and in the update bodies below, so
-    // that each kernel that inlines them computes the same bits)
-    const float s0 = __fsub_rn(m0, sc.fhi[0]), s1 = __fsub_rn(m1, sc.fhi[1]), s2 = __fsub_rn(m2, sc.fhi[2]);
-    // direction in the LiDAR frame (scale-free) -> pixel
-    const float x0 = __fmaf_rn(sc.Rt[2], s2, __fmaf_rn(sc.Rt[1], s1, __fmul_rn(sc.Rt[0], s0)));
-    const float x1 = __fmaf_rn(sc.Rt[5], s2, __fmaf_rn(sc.Rt[4], s1, __fmul_rn(sc.Rt[3], s0)));
-    const float x2 = __fmaf_rn(sc.Rt[8], s2, __fmaf_rn(sc.Rt[7], s1, __fmul_rn(sc.Rt[6], s0)));
+    const float s0 = __fsub_rn((float)(8 * bx + lx - sc.k[0]), sc.fhi[0]);
+    const float s1 = __fsub_rn((float)(8 * by + ly - sc.k[1]), sc.fhi[1]);
+    const float s2 = __fsub_rn((float)(8 * bz + lz - sc.k[2]), sc.fhi[2]);
+    x0 = __fmaf_rn(sc.Rt[2], s2, __fmaf_rn(sc.Rt[1], s1, __fmul_rn(sc.Rt[0], s0)));
+    x1 = __fmaf_rn(sc.Rt[5], s2, __fmaf_rn(sc.Rt[4], s1, __fmul_rn(sc.Rt[3], s0)));
+    x2 = __fmaf_rn(sc.Rt[8], s2, __fmaf_rn(sc.Rt[7], s1, __fmul_rn(sc.Rt[6], s0)));
+}
+
+// Pixel of a voxel at LiDAR-frame direction (x0, x1, x2) (Sec. III-C.1), or -1
+// outside the image; also returns |x_l|^2 (rr2) and its reciprocal square
+// root (irr) in voxel units.
+__device__ __forceinline__ int tsdf_pixel(const ScanConst &sc, float x0, float x1, float x2, float &rr2, float &irr) {
     rr2 = __fmaf_rn(x2, x2, __fmaf_rn(x1, x1, __fmul_rn(x0, x0)));
     irr = 0.f;
     if (!(rr2 > 0.f)) return -1;
@@ -598,12 +600,20 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
     // projections and both pixel reads before either update, so that their
     // latencies overlap
 #pragma unroll 1
+    // the lane's voxels are (x, y, z), (x, y + 4, z) with z one higher each step: their
+    // directions follow from the first by adding R^T's images of one z step and four y steps
+    float da0, da1, da2;
+    tsdf_dir(sc, bx, by, bz, v0 + lane, da0, da1, da2);
+    const float ey0 = __fmul_rn(4.f, sc.Rt[1]), ey1 = __fmul_rn(4.f, sc.Rt[4]), ey2 = __fmul_rn(4.f, sc.Rt[7]);
     for (int vi = v0 + lane; vi < v1; vi += 64) {
         const long long va = (long long)slot * BV + vi, vb = va + 32;
         const float2 dwa = load_dw<F16>(md, va), dwb = load_dw<F16>(md, vb);
-        float ma0, ma1, ma2, ra, ia, mb0, mb1, mb2, rb, ib;
-        const int pa = tsdf_pixel(sc, bx, by, bz, vi, ma0, ma1, ma2, ra, ia);
-        const int pb = tsdf_pixel(sc, bx, by, bz, vi + 32, mb0, mb1, mb2, rb, ib);
+        float ra, ia, rb, ib;
+        const int pa = tsdf_pixel(sc, da0, da1, da2, ra, ia);
+        const int pb = tsdf_pixel(sc, __fadd_rn(da0, ey0), __fadd_rn(da1, ey1), __fadd_rn(da2, ey2), rb, ib);
+        da0 = __fadd_rn(da0, sc.Rt[2]);
+        da1 = __fadd_rn(da1, sc.Rt[5]);
+        da2 = __fadd_rn(da2, sc.Rt[8]);
         const unsigned long long wa = fd.win[pa < 0 ? 0 : pa], wb = fd.win[pb < 0 ? 0 : pb];
         const bool ba = tsdf_fast<F16, DIST>(sc, md, va, vi, pa, wa, dwa, ra, ia, n_upd, remesh);
         const bool bb = tsdf_fast<F16, DIST>(sc, md, vb, vi + 32, pb, wb, dwb, rb, ib, n_upd, remesh);
