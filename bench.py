@@ -446,6 +446,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    import gc
+    gc.disable()          # no collector pauses while the host issues the timed scans
     with ClockSampler(local_rank) as clk:
         t_wall = time.perf_counter()
         for i in range(args.steps):
@@ -455,6 +457,7 @@ def run_ours(args, rank, world, local_rank):
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
+    gc.enable()
     if dist:
         dist.barrier()
     st_last = tsdf.stats()
@@ -586,6 +589,8 @@ def run_ours(args, rank, world, local_rank):
                    "meshing": "incremental, every scan" if K == 1 else f"full map every {K} scans",
                    "l2": f"flushed ({args.flush_mb} MB write) before every timed scan, outside its events",
                    "ms_median": float(np.median(step_ms)), "ms_p95": float(np.percentile(step_ms, 95)),
+                   "ms_max": float(step_ms.max()),
+                   "scans_over_1.5x_median": int((step_ms > 1.5 * np.median(step_ms)).sum()),
                    "bracketed_wall_s_incl_flush": t_wall, "parallelism": f"replicas x{world}",
                    "frame_algorithmic_bytes": frame_bytes,
                    "frame_gbs": frame_bytes / (total_ms / args.steps * 1e-3) / 1e9,
