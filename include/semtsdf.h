@@ -219,7 +219,8 @@ map_status map_remesh_all(map_t *map, void *stream);
 /* Per-frame incremental meshing in integrate_scan: 1 (default) re-meshes
  * the touched blocks and their -x/-y/-z neighbours every scan; 0 leaves
  * the mesh as it is until map_remesh_all (the scan's kernels minus k_mesh).
- * MAP_ERR_ARG for other values.  Applies to the following scans. */
+ * MAP_ERR_ARG for other values.  Applies to the following integrate_scan /
+ * integrate_scan_host calls; map_batch_integrate always re-meshes. */
 map_status map_set_incremental_mesh(map_t *map, int32_t enabled);
 
 /* ---- class update from camera label images (Sec. III-C.3) ---- */
