@@ -98,8 +98,47 @@ def test_config_defaults():
     import paper_2412_00291_b300 as p
     cfg = p.map_config_default()
     assert cfg.voxel_size == pytest.approx(0.1) and cfg.truncation == pytest.approx(0.3)
-    assert cfg.n_classes == 20 and cfg.weight_mode == 0 and cfg.storage == 0
+    assert cfg.n_classes == 20 and cfg.weight_mode == 0 and cfg.storage == 0 and cfg.distance_mode == 0
     assert ctypes.sizeof(cfg) == 104
+
+
+def test_traversability_defaults_are_table_ii():
+    """Radius 0.25 m, height 0.6 m, steepness 20 deg, roughness 30 deg, every class allowed."""
+    import math
+    import paper_2412_00291_b300 as p
+    t = p.TravParams()
+    assert p._lib.map_trav_params_default(ctypes.byref(t)) == 0
+    assert t.radius == pytest.approx(0.25) and t.max_height_diff == pytest.approx(0.6)
+    assert t.max_steepness == pytest.approx(math.radians(20.0)) and t.max_roughness == pytest.approx(math.radians(30.0))
+    assert t.class_mask == (1 << 64) - 1
+    assert p._lib.map_trav_params_default(None) != 0
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes mirror of a C struct of the header has the C compiler's size and field offsets."""
+    import shutil
+    import subprocess
+    import paper_2412_00291_b300 as p
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    mirrors = {"map_config": p.MapConfig, "lidar_intrinsics": p.LidarIntrinsics, "mesh_view": p.MeshView,
+               "scan_desc": p.ScanDesc, "trav_params": p.TravParams, "camera_intrinsics": p.CameraIntrinsics,
+               "quality_report": p.QualityReport}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "semtsdf.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for cname, py in mirrors.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
 
 
 def _poly_coeffs(name):
