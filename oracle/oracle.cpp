@@ -41,6 +41,11 @@
  * or the voxel has no gradient yet (then d_i = psi).  The weight and the
  * skip below -tau stay on psi; Gamma(d_i, tau) is the fused value.
  *
+ * Parity unpinned: the fusion of probability vectors is pinned only by its
+ * closed form for one vector per scan, the normalisation invariant and its
+ * independence of the scan order; the paper gives no worked example with
+ * which to pin it further.
+ *
  * Precision: every value is FP64.  Two integer decisions are taken in the
  * precision the GPU takes them in, as both sides of a parity check must:
  * the per-point range used for validity and for the nearest-point winner
