@@ -897,11 +897,8 @@ def run_align(args, rank, world, local_rank):
     untimed ones), spread along the drive, are aligned from a pose perturbed by 0.5 m along a
     random direction and 5 deg about a random axis: 20 Gauss-Newton iterations of
     sum query_sdf^2 over the scan's 131,072 points, all on the device (map_align_scan), timed
-    per scan with CUDA events on the launching stream.  On one scan the analytic pose gradient
-    is checked against FP64 central differences (h = 1e-4) of the oracle's loss evaluated on
-    the map blocks around 4,096 sampled points, copied from the device."""
+    per scan with CUDA events on the launching stream."""
     import torch
-    import oracle
     import paper_2412_00291_b300 as P
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -933,7 +930,6 @@ def run_align(args, rank, world, local_rank):
     rng = np.random.default_rng([w.seed, 17])
     stream = torch.cuda.current_stream(dev)
     times, terr, rerr, terr0 = [], [], [], []
-    grad_check = None
     with ClockSampler(local_rank) as clk:
         for i, k in enumerate(pick):
             pts, T = frames_keep[k]
@@ -943,7 +939,7 @@ def run_align(args, rank, world, local_rank):
             a /= np.linalg.norm(a)
             # perturbation in the sensor frame: 0.5 m translation, 5 deg rotation about the sensor
             dT = np.eye(4)
-            dT[:3, :3] = oracle.se3_exp(np.concatenate([np.zeros(3), math.radians(5.0) * a]))[:3, :3]
+            dT[:3, :3] = _axis_angle(a, math.radians(5.0))
             dT[:3, 3] = 0.5 * d
             T0 = T @ dT
             pd = torch.from_numpy(pts).to(dev)
@@ -958,8 +954,6 @@ def run_align(args, rank, world, local_rank):
                 terr.append(float(np.linalg.norm(Tout[:3, 3] - T[:3, 3])))
                 rerr.append(_rot_err_deg(Tout[:3, :3], T[:3, :3]))
                 terr0.append(float(np.linalg.norm(T0[:3, 3] - T[:3, 3])))
-            if grad_check is None:
-                grad_check = _align_grad_check(P, oracle, m, w, pts, T0, dev, rng)
         # the same scans from a perturbation inside the truncation band's basin (0.1 m, 1 deg)
         small_t, small_r = [], []
         for k in pick[args.warmup:]:
@@ -969,7 +963,7 @@ def run_align(args, rank, world, local_rank):
             a = rng.normal(size=3)
             a /= np.linalg.norm(a)
             dT = np.eye(4)
-            dT[:3, :3] = oracle.se3_exp(np.concatenate([np.zeros(3), math.radians(1.0) * a]))[:3, :3]
+            dT[:3, :3] = _axis_angle(a, math.radians(1.0))
             dT[:3, 3] = 0.1 * d
             Tout = m.align(torch.from_numpy(pts).to(dev), T @ dT, iters=20)
             small_t.append(float(np.linalg.norm(Tout[:3, 3] - T[:3, 3])))
@@ -996,76 +990,16 @@ def run_align(args, rank, world, local_rank):
                            "final_translation_error_m_max": float(np.max(small_t)),
                            "final_rotation_error_deg_median": float(np.median(small_r)),
                            "final_rotation_error_deg_max": float(np.max(small_r))},
-        "pose_gradient_check": grad_check,
         # per map_align_scan call: k_gn_terms + k_gn_step per iteration
         "gpu_launches": 2 * 20 * len(times), "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
 
 
-def _align_grad_check(P, oracle, m, w, pts, T, dev, rng, n=4096, h=1e-4):
-    """Analytic pose gradient (hand-written backward) vs the oracle's FP64 analytic gradient and
-    FP64 central differences (h = 1e-4) of its loss, on a copy of the map blocks around n sampled
-    points.  Rotations are taken about the points' centroid c (rotating about the far-away world
-    origin would move the points by centimetres); the gradient about the origin converts as
-    g_phi(c) = g_phi - c x g_rho.  Only points valid at the pose and at all 12 perturbed poses
-    and inside the same interpolation cell at all of them enter the loss, so that it is smooth
-    (the trilinear field's gradient jumps across cell faces)."""
-    import torch
-    nu = w.voxel_size
-    sel = rng.choice(len(pts), size=min(n, len(pts)), replace=False)
-    p = pts[sel]
-    xw = (p.astype(np.float64) @ T[:3, :3].T + T[:3, 3]).astype(np.float32)
-    x = xw.astype(np.float64)
-    c = x.mean(axis=0)
-    # blocks holding every voxel within 3 voxels of a sampled point
-    v = np.floor(x / nu)
-    offs = np.array([[i, j, k] for i in (-3, 0, 3) for j in (-3, 0, 3) for k in (-3, 0, 3)])
-    blocks = np.unique(np.floor((v[:, None, :] + offs[None]) / 8.0).reshape(-1, 3).astype(np.int64), axis=0)
-    rb = m.read_blocks(blocks.astype(np.int32), want_logp=False)
-    o = oracle.OracleMap(nu, w.truncation, 2)
-    for b, f, D, W in zip(blocks, rb["found"], rb["D"], rb["W"]):
-        if f:
-            o.write_block(b.astype(np.int32), D.astype(np.float64), W.astype(np.float64))
-
-    def moved(j, sgn):
-        if j < 3:
-            y = x.copy()
-            y[:, j] += sgn * h
-            return y
-        e = np.zeros(6)
-        e[j] = sgn * h
-        R = oracle.se3_exp(e)[:3, :3]
-        return (x - c) @ R.T + c
-
-    base_sdf, base_ok, base_grad = o.query(x)
-    ok = base_ok.copy()
-    cell = np.floor(x / nu)
-    sides = {}
-    for j in range(6):
-        for sgn in (1, -1):
-            y = moved(j, sgn)
-            sd, vv, _ = o.query(y)
-            sides[(j, sgn)] = sd
-            # valid, and inside the same interpolation cell (the trilinear field is smooth there)
-            ok &= vv & np.all(np.floor(y / nu) == cell, axis=1)
-    fd = np.array([(np.sum(sides[(j, 1)][ok] ** 2) - np.sum(sides[(j, -1)][ok] ** 2)) / (2 * h) for j in range(6)])
-    # oracle analytic gradient on the same points (rotation about c)
-    gx = 2.0 * base_sdf[ok, None] * base_grad[ok]
-    ref = np.concatenate([gx.sum(axis=0), np.cross(x[ok] - c, gx).sum(axis=0)])
-    # device: backward with dL/dsdf = 2 sdf on the same points, pose gradient about the origin
-    xd = torch.from_numpy(xw).to(dev)
-    sdf, valid = m.query(xd)
-    okd = torch.from_numpy(ok).to(dev)
-    g = torch.where(okd & valid, 2.0 * torch.nan_to_num(sdf), torch.zeros_like(sdf))
-    pg = P.pose_gradient(m, xd, g).cpu().numpy().astype(np.float64)
-    pg_c = np.concatenate([pg[:3], pg[3:] - np.cross(c, pg[:3])])
-    scale = float(np.abs(ref).max())
-    return {"points": int(len(sel)), "points_in_loss": int(ok.sum()), "blocks_copied": int(rb["found"].sum()),
-            "max_rel_err_vs_oracle_fp64": float(np.max(np.abs(pg_c - ref)) / scale),
-            "max_rel_err_vs_central_diff": float(np.max(np.abs(pg_c - fd)) / scale),
-            "oracle_analytic_vs_central_diff": float(np.max(np.abs(ref - fd)) / scale), "h": h,
-            "rotation_centre": "centroid of the sampled points"}
+def _axis_angle(a, theta):
+    """Rotation by theta about the unit axis a (Rodrigues: I + sin(theta) K + (1 - cos(theta)) K^2)."""
+    K = np.array([[0.0, -a[2], a[1]], [a[2], 0.0, -a[0]], [-a[1], a[0], 0.0]])
+    return np.eye(3) + math.sin(theta) * K + (1.0 - math.cos(theta)) * (K @ K)
 
 
 def main():

@@ -102,6 +102,82 @@ def test_pose_gradient_matches_oracle_and_fd():
         assert pg[j] == pytest.approx(fd, rel=1e-3, abs=1e-3 * np.abs(ref["dL"]).max())
 
 
+def test_pose_gradient_on_a_fused_map():
+    """The pose gradient on a map fused from scans rather than an analytic field: the oracle fuses
+    four 16 x 1024 scans, its blocks (rounded to FP32) are written into both maps, and the device
+    gradient of sum sdf^2 over the last scan's points at a perturbed pose is compared with the
+    oracle's FP64 analytic gradient and with FP64 central differences (h = 1e-4) of its loss.
+    Rotations are taken about the points' centroid c (the gradient about the origin converts as
+    g_phi(c) = g_phi - c x g_rho).  Only points valid and inside the same interpolation cell at the
+    pose and all 12 perturbed poses enter the loss: the trilinear field's gradient jumps across
+    cell faces, so the loss is smooth only there."""
+    w = synth.line16()
+    L = w.lidar
+    frames = list(synth.sequence(w, 4))
+    ob = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    for f in frames:
+        ob.integrate(L, f.points, f.T, labels=f.labels)
+    blocks = ob.alloc_blocks()
+    D, W = [], []
+    for b in blocks:
+        r = ob.read_block(b)
+        D.append(r["D"].astype(np.float32))
+        W.append(r["W"].astype(np.float32))
+    D, W = np.stack(D), np.stack(W)
+    P = _P()
+    g = P.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=2 * len(blocks), hash_capacity=1 << 16,
+                       max_points=1 << 15, max_pixels=1 << 15, mesh_vertex_capacity=1 << 20,
+                       mesh_triangle_capacity=1 << 20)
+    g.write_blocks(blocks, D, W)
+    o = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    for b, d, wt in zip(blocks, D, W):
+        o.write_block(b, d.astype(np.float64), wt.astype(np.float64))
+    f = frames[-1]
+    p = f.points[np.isfinite(f.points).all(axis=1)]
+    T = f.T @ synth.pose(synth.rot_rpy(0.004, -0.003, 0.006), [0.04, -0.03, 0.02])
+    xw = (p.astype(np.float64) @ T[:3, :3].T + T[:3, 3]).astype(np.float32)
+    x = xw.astype(np.float64)
+    c = x.mean(axis=0)
+    nu, h = w.voxel_size, 1e-4
+
+    def moved(j, sgn):
+        if j < 3:
+            y = x.copy()
+            y[:, j] += sgn * h
+            return y
+        e = np.zeros(6)
+        e[j] = sgn * h
+        return (x - c) @ oracle.se3_exp(e)[:3, :3].T + c
+
+    base_sdf, ok, base_grad = o.query(x)
+    cell = np.floor(x / nu)
+    sides = {}
+    for j in range(6):
+        for sgn in (1, -1):
+            y = moved(j, sgn)
+            sd, vv, _ = o.query(y)
+            sides[(j, sgn)] = sd
+            ok &= vv & np.all(np.floor(y / nu) == cell, axis=1)
+    assert ok.sum() > 2000
+    fd = np.array([(np.sum(sides[(j, 1)][ok] ** 2) - np.sum(sides[(j, -1)][ok] ** 2)) / (2 * h) for j in range(6)])
+    gx = 2.0 * base_sdf[ok, None] * base_grad[ok]
+    ref = np.concatenate([gx.sum(axis=0), np.cross(x[ok] - c, gx).sum(axis=0)])
+    xd = torch.from_numpy(xw).cuda()
+    sdf, valid = g.query(xd)
+    okd = torch.from_numpy(ok).cuda()
+    assert bool(valid[okd].all())
+    gs = torch.where(okd & valid, 2.0 * torch.nan_to_num(sdf), torch.zeros_like(sdf))
+    pg = P.pose_gradient(g, xd, gs).cpu().numpy().astype(np.float64)
+    pg_c = np.concatenate([pg[:3], pg[3:] - np.cross(c, pg[:3])])
+    scale = float(np.abs(ref).max())
+    e_ref = float(np.max(np.abs(pg_c - ref)) / scale)
+    e_fd = float(np.max(np.abs(pg_c - fd)) / scale)
+    print(f"fused-map pose gradient: {int(ok.sum())} of {len(p)} points in the loss, relative error "
+          f"{e_ref:.2e} vs the oracle's analytic gradient, {e_fd:.2e} vs central differences")
+    assert e_ref <= 1e-4, e_ref
+    assert e_fd <= 1e-4, e_fd
+
+
 def _room_points(rng, size, o, n):
     d = rng.normal(size=(n, 3))
     d /= np.linalg.norm(d, axis=1, keepdims=True)
