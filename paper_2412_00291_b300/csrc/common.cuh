@@ -2,6 +2,7 @@
 // of libsemtsdf.  Not part of the public C ABI (see include/semtsdf.h).
 #pragma once
 
+#include <utility>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -148,6 +149,12 @@ struct FrameDev {
     int2 *sem_list;            // [sem_cap] {pool voxel index, winner point index} awaiting the class update
     long long sem_cap;
     unsigned long long *ctr;   // [CT_COUNT]
+    // the other range-image and counter buffers (the next scan's), which the
+    // per-point kernel resets on the way: win_next[0, win_next_n) to ~0 and
+    // ctr_next to 0 (null in paths that reset their own buffers)
+    unsigned long long *win_next;
+    long long win_next_n;
+    unsigned long long *ctr_next;
 };
 
 // --- error-free transformations (Knuth TwoSum, Dekker/FMA TwoProduct) ----
@@ -302,6 +309,32 @@ __device__ __forceinline__ void cta_count(unsigned long long *ctr, const int (&i
         for (int i = 0; i < nw; ++i) t += s_part[threadIdx.x][i];
         if (t) atomicAdd(&ctr[idx[threadIdx.x]], (unsigned long long)t);
     }
+}
+
+// Programmatic dependent launch (PTX griddepcontrol): a kernel launched with
+// the programmatic-stream-serialization attribute may be scheduled while its
+// predecessor in the stream is still running.  pdl_wait() blocks until the
+// predecessor has completed and its writes are visible (a no-op for a kernel
+// launched without the attribute); pdl_trigger() lets the successor be
+// scheduled before this grid ends.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch with programmatic stream serialization (the kernel calls pdl_wait()
+// before it reads or writes anything its predecessor touches).
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
 }
 
 }  // namespace stsdf

@@ -8,14 +8,30 @@
 // [8b, 8b + 8) on every axis.  Endpoints and crossing parameters follow a
 // fixed IEEE single-precision recipe (correctly rounded intrinsics, no
 // contraction), which makes the allocated block set reproducible bit for bit.
+#include <algorithm>
+
 #include "frame_bodies.cuh"
 
 namespace stsdf {
 
 __global__ void __launch_bounds__(128) k_points(const float *__restrict__ pts, ScanConst sc, MapDev md, FrameDev fd) {
     long long cnt[3] = {0, 0, 0};
-    points_item(pts, sc, md, fd, (long long)blockIdx.x * blockDim.x + threadIdx.x, cnt);
+    pdl_trigger();   // the TSDF grid may be scheduled now; it waits for this grid's end
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // the next scan's buffers (no kernel of this scan reads them; the grid covers win_next_n)
+    if (fd.win_next && i < fd.win_next_n) fd.win_next[i] = ~0ull;
+    if (fd.ctr_next && i < CT_COUNT) fd.ctr_next[i] = 0ull;
+    points_item(pts, sc, md, fd, i, cnt);
     cta_count<3>(fd.ctr, {CT_VALID, CT_PIXEL, CT_NEW}, cnt);
+}
+
+// A scan's counters and the device state, copied after the scan's last kernel
+// into one record [counters | state] for the host to download.
+__global__ void k_snapshot(const unsigned long long *__restrict__ ctr, const DevState *__restrict__ st,
+                           unsigned long long *__restrict__ rec) {
+    constexpr int nst = (int)(sizeof(DevState) / sizeof(unsigned long long));
+    const unsigned long long *sw = reinterpret_cast<const unsigned long long *>(st);
+    for (int i = threadIdx.x; i < CT_COUNT + nst; i += blockDim.x) rec[i] = i < CT_COUNT ? ctr[i] : sw[i - CT_COUNT];
 }
 
 // Link every allocated block (after host-side writes).
@@ -168,9 +184,14 @@ __global__ void k_collect_blocks(MapDev md, int32_t *coords, unsigned long long 
 }
 
 void launch_points(const float *pts, const ScanConst &sc, const MapDev &md, const FrameDev &fd, cudaStream_t s) {
-    if (sc.n <= 0) return;
-    // 128-thread CTAs: ~7 per SM for a 131,072-point scan, evenly spread
-    k_points<<<(unsigned)((sc.n + 127) / 128), 128, 0, s>>>(pts, sc, md, fd);
+    // 128-thread CTAs: ~7 per SM for a 131,072-point scan, evenly spread; at least
+    // one CTA, and enough to reset the next scan's range image
+    const long long n = std::max<long long>({(long long)sc.n, fd.win_next ? fd.win_next_n : 0ll, 1ll});
+    k_points<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(pts, sc, md, fd);
+}
+void launch_snapshot(const unsigned long long *ctr, const DevState *st, unsigned char *rec, cudaStream_t s) {
+    static_assert(sizeof(DevState) % sizeof(unsigned long long) == 0, "DevState is a whole number of words");
+    k_snapshot<<<1, 128, 0, s>>>(ctr, st, reinterpret_cast<unsigned long long *>(rec));
 }
 void launch_list_all(const MapDev &md, const FrameDev &fd, int, cudaStream_t s) {
     k_list_all<<<1024, 256, 0, s>>>(md, fd);

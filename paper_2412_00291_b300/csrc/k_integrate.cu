@@ -28,6 +28,8 @@
 namespace stsdf {
 
 __global__ void __launch_bounds__(256) k_normals(ScanConst sc, FrameDev fd) {
+    pdl_wait();
+    pdl_trigger();
     const int np = sc.H * sc.W;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) normal_item(sc, fd.win, p);
 }
@@ -44,6 +46,8 @@ __global__ void __launch_bounds__(256, 4) k_tsdf(ScanConst sc, MapDev md, FrameD
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     long long n_upd = 0;
+    pdl_wait();      // the per-point grid's touched list and range image
+    pdl_trigger();   // the re-meshing grid may be scheduled now
     unsigned long long nt = *(volatile unsigned long long *)&fd.ctr[CT_TOUCHED];
     if (nt > (unsigned long long)md.max_blocks) nt = md.max_blocks;
     constexpr int PV = BV / TSDF_PARTS;
@@ -83,20 +87,16 @@ int semantic_blocks_per_sm(int storage, int C) {
 }
 
 void launch_integrate(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s) {
-    if (sc.dist_mode) {
-        if (md.storage == 0) k_tsdf<false, true><<<grid, 256, 0, s>>>(sc, md, fd);
-        else k_tsdf<true, true><<<grid, 256, 0, s>>>(sc, md, fd);
-    } else {
-        if (md.storage == 0) k_tsdf<false, false><<<grid, 256, 0, s>>>(sc, md, fd);
-        else k_tsdf<true, false><<<grid, 256, 0, s>>>(sc, md, fd);
-    }
+    auto k = sc.dist_mode ? (md.storage == 0 ? k_tsdf<false, true> : k_tsdf<true, true>)
+                          : (md.storage == 0 ? k_tsdf<false, false> : k_tsdf<true, false>);
+    launch_pdl(k, dim3(grid), dim3(256), 0, s, sc, md, fd);
 }
 
 void launch_normals(const ScanConst &sc, const FrameDev &fd, cudaStream_t s) {
     const int np = sc.H * sc.W;
     int grid = (np + 255) / 256;
     if (grid > 148 * 8) grid = 148 * 8;
-    k_normals<<<grid, 256, 0, s>>>(sc, fd);
+    launch_pdl(k_normals, dim3(grid), dim3(256), 0, s, sc, fd);
 }
 
 void launch_semantic(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s) {

@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(32 * MESH_WARPS) k_mesh(MapDev md, FrameDev fd
     for (int i = threadIdx.x; i < 256 * MC_MAXTRI * 3; i += blockDim.x) S.tri[i] = ttri[i];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) S.ntri[i] = tntri[i];
     __syncthreads();
+    pdl_wait();   // the TSDF grid's re-mesh list and voxel values
     const int wid = threadIdx.x >> 5;
     unsigned long long nd = *(volatile unsigned long long *)&fd.ctr[CT_DIRTY];
     if (nd > (unsigned long long)md.max_blocks) nd = md.max_blocks;
@@ -62,7 +63,8 @@ int mesh_blocks_per_sm() {
 }
 
 void launch_mesh(const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s) {
-    k_mesh<<<grid, 32 * MESH_WARPS, sizeof(MeshCtaSmem), s>>>(md, fd, h_tri_dev, h_ntri_dev);
+    launch_pdl(k_mesh, dim3(grid), dim3(32 * MESH_WARPS), sizeof(MeshCtaSmem), s, md, fd,
+               (const int8_t *)h_tri_dev, (const uint8_t *)h_ntri_dev);
 }
 
 // ---------------------------------------------------------------------------

@@ -7,6 +7,7 @@ namespace stsdf {
 
 // k_alloc.cu: per-point range-image winners and band allocation (touched list)
 void launch_points(const float *pts, const ScanConst &sc, const MapDev &md, const FrameDev &fd, cudaStream_t s);
+void launch_snapshot(const unsigned long long *ctr, const DevState *st, unsigned char *rec, cudaStream_t s);
 void launch_list_all(const MapDev &md, const FrameDev &fd, int frame, cudaStream_t s);
 void launch_init_pool(const MapDev &md, cudaStream_t s);
 void launch_link_all(const MapDev &md, cudaStream_t s);

@@ -20,21 +20,40 @@ struct map_t {
     MapDev md{};
     FrameDev fd{};
     DevState *st = nullptr;
+    // Per-scan buffers, two of each: a scan uses one set while its per-point
+    // kernel resets the other for the next scan (no memsets between scans).
+    unsigned long long *ctr_pair = nullptr;
+    unsigned long long *ctr_buf[2] = {};
+    unsigned long long *win_buf[2] = {};
+    long long win_dirty[2] = {};     // leading range-image entries that may hold a winner
+    bool ctr_clean[2] = {true, true};
+    int fcur = 1;                    // set m->fd points at; the next scan uses the other
     // second mesh arena for compaction
     float4 *av_alt = nullptr;
     int64_t *ak_alt = nullptr;
     ushort4 *at_alt = nullptr;
     GatherBufs gb{};
     int nchunks = 0;
-    // host views (pinned) of the last frame's counters and device state
+    // host views (pinned) of the last frame's counters and device state; when
+    // h_ctr_slot >= 0 the counters are those of that ring entry
     unsigned long long *h_ctr = nullptr;
+    int h_ctr_slot = -1;
     DevState *h_st = nullptr;
     long long *h_totals = nullptr;
     // Ring of per-frame device-state copies: bounds how far the host runs ahead
     // (at most RING frames in flight) and gives it a view of the mesh-arena
     // cursor that is at most RING frames old.
     static constexpr int RING = 8;
-    DevState *h_ring = nullptr;
+    static constexpr size_t CTR_BYTES = CT_COUNT * sizeof(unsigned long long);
+    static constexpr size_t REC_BYTES = CTR_BYTES + sizeof(DevState);
+    // A scan ends with a device-side snapshot of its counters and the device
+    // state into d_ring[slot] ([counters | state]); a download stream copies it
+    // to h_ring[slot] off the scan stream (a copy there would hold the next
+    // scan's kernels for the whole transfer).
+    unsigned char *h_ring = nullptr;   // [RING][REC_BYTES]
+    unsigned char *d_ring = nullptr;   // [RING][REC_BYTES]
+    cudaStream_t dl = nullptr;
+    cudaEvent_t ev_snap = nullptr;
     cudaEvent_t ev_ring[RING] = {};
     // the class update runs on a second stream beside the re-meshing (the mesh
     // does not read class labels); fork after the TSDF kernel, join before return
@@ -55,7 +74,6 @@ struct map_t {
     int stage_next = 0;
     cudaStream_t cp = nullptr;
     cudaEvent_t ev_copied[2] = {}, ev_used[2] = {};
-    unsigned long long *h_ring_ctr = nullptr;   // [RING][CT_COUNT] counters of the last RING frames
     // extracted mesh
     long long out_vcap = 0, out_tcap = 0;
     float *out_pos = nullptr;
@@ -156,8 +174,8 @@ static void free_all(map_t *m) {
     prof_clear(m);
     void *ptrs[] = {m->md.keys, m->md.vals, m->md.stamp, m->md.dstamp_slot, m->md.dw32, m->md.dw16, m->md.lp32,
                     m->md.lp16, m->md.label, m->md.slot_key, m->md.slot_frame, m->md.nbr, m->md.seg, m->md.av, m->md.ak, m->md.at,
-                    m->av_alt, m->ak_alt, m->at_alt, m->st, m->fd.win,
-                    m->fd.touched, m->fd.dirty, m->fd.sem_list, m->fd.ctr, m->gb.voff, m->gb.toff, m->gb.bsum_v, m->gb.bsum_t,
+                    m->av_alt, m->ak_alt, m->at_alt, m->st, m->ctr_pair, m->d_ring, m->win_buf[0], m->win_buf[1],
+                    m->fd.touched, m->fd.dirty, m->fd.sem_list, m->gb.voff, m->gb.toff, m->gb.bsum_v, m->gb.bsum_t,
                     m->gb.totals, m->stage_pts[0], m->stage_lab[0], m->stage_probs[0], m->stage_pts[1],
                     m->stage_lab[1], m->stage_probs[1], m->out_pos, m->out_col,
                     m->out_keys, m->out_tri, m->out_anchor, m->gn_T, m->gn_acc, m->qb_part, m->pal_dev,
@@ -173,7 +191,6 @@ static void free_all(map_t *m) {
     if (m->h_st) cudaFreeHost(m->h_st);
     if (m->h_totals) cudaFreeHost(m->h_totals);
     if (m->h_ring) cudaFreeHost(m->h_ring);
-    if (m->h_ring_ctr) cudaFreeHost(m->h_ring_ctr);
     if (m->h_dir) cudaFreeHost(m->h_dir);
     if (m->ev_dir) cudaEventDestroy(m->ev_dir);
     for (int b = 0; b < 2; ++b) {
@@ -186,6 +203,8 @@ static void free_all(map_t *m) {
     if (m->ev_fork) cudaEventDestroy(m->ev_fork);
     if (m->ev_join) cudaEventDestroy(m->ev_join);
     if (m->side) cudaStreamDestroy(m->side);
+    if (m->ev_snap) cudaEventDestroy(m->ev_snap);
+    if (m->dl) cudaStreamDestroy(m->dl);
 }
 
 template <typename T>
@@ -278,14 +297,20 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     ALLOC(m->ak_alt, c.mesh_vertex_capacity);
     ALLOC(m->at_alt, c.mesh_triangle_capacity);
     ALLOC(m->st, 1);
+    ALLOC(m->ctr_pair, 2 * CT_COUNT);
+    ALLOC(m->d_ring, map_t::RING * map_t::REC_BYTES);
+    m->ctr_buf[0] = m->ctr_pair;
+    m->ctr_buf[1] = m->ctr_pair + CT_COUNT;
     md.st = m->st;
     FrameDev &fd = m->fd;
-    ALLOC(fd.win, c.max_pixels);
+    ALLOC(m->win_buf[0], c.max_pixels);
+    ALLOC(m->win_buf[1], c.max_pixels);
+    fd.win = m->win_buf[1];
     ALLOC(fd.touched, nb);
     ALLOC(fd.dirty, nb);
     fd.sem_cap = std::min<long long>(nvox, 1ll << 25);
     ALLOC(fd.sem_list, fd.sem_cap);
-    ALLOC(fd.ctr, CT_COUNT);
+    fd.ctr = m->ctr_buf[1];
     m->nchunks = (int)((nb + 1023) / 1024);
     ALLOC(m->gb.voff, nb);
     ALLOC(m->gb.toff, nb);
@@ -301,23 +326,23 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     if (cudaMallocHost(&m->h_ctr, CT_COUNT * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&m->h_st, sizeof(DevState)) != cudaSuccess ||
         cudaMallocHost(&m->h_totals, 2 * sizeof(long long)) != cudaSuccess ||
-        cudaMallocHost(&m->h_ring, map_t::RING * sizeof(DevState)) != cudaSuccess ||
-        cudaMallocHost(&m->h_ring_ctr, map_t::RING * CT_COUNT * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMallocHost(&m->h_ring, map_t::RING * map_t::REC_BYTES) != cudaSuccess) {
         free_all(m);
         delete m;
         return fail(nullptr, MAP_ERR_NOMEM, "pinned host allocation failed");
     }
     std::memset(m->h_ctr, 0, CT_COUNT * sizeof(unsigned long long));
     std::memset(m->h_st, 0, sizeof(DevState));
-    std::memset(m->h_ring, 0, map_t::RING * sizeof(DevState));
+    std::memset(m->h_ring, 0, map_t::RING * map_t::REC_BYTES);
     for (auto &e : m->ev_ring) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-    std::memset(m->h_ring_ctr, 0, map_t::RING * CT_COUNT * sizeof(unsigned long long));
     if (cudaStreamCreateWithFlags(&m->cp, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->ev_copied[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->ev_copied[1], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->ev_used[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->ev_used[1], cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&m->dl, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev_snap, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->ev_dir, cudaEventDisableTiming) != cudaSuccess) {
@@ -348,7 +373,9 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
         }
         cudaMemcpy(m->st, &init, sizeof(init), cudaMemcpyHostToDevice);
     }
-    cudaMemsetAsync(fd.ctr, 0, CT_COUNT * sizeof(unsigned long long), s);
+    cudaMemsetAsync(m->ctr_pair, 0, 2 * map_t::CTR_BYTES, s);
+    cudaMemsetAsync(m->win_buf[0], 0xFF, (size_t)c.max_pixels * sizeof(unsigned long long), s);
+    cudaMemsetAsync(m->win_buf[1], 0xFF, (size_t)c.max_pixels * sizeof(unsigned long long), s);
     launch_init_pool(md, s);
     // tables
     std::vector<int8_t> tri(256 * MAP_MC_MAXTRI * 3);
@@ -527,11 +554,19 @@ static double arena_fill(const DevState &d) {
     return f;
 }
 
+// The device state and the counters held by a ring entry.
+static const DevState &ring_state(const map_t *m, int slot) {
+    return *reinterpret_cast<const DevState *>(m->h_ring + (size_t)slot * map_t::REC_BYTES + map_t::CTR_BYTES);
+}
+static const unsigned long long *ring_ctr(const map_t *m, int slot) {
+    return reinterpret_cast<const unsigned long long *>(m->h_ring + (size_t)slot * map_t::REC_BYTES);
+}
+
 // Fold a completed ring entry into the host's view of the arena fill.
 static void absorb(map_t *m, int slot) {
     if (m->ring_frame[slot] < 0 || m->ring_epoch[slot] != m->epoch) return;
     if (m->ring_frame[slot] > m->known_frame) {
-        const double f = arena_fill(m->h_ring[slot]);
+        const double f = arena_fill(ring_state(m, slot));
         if (m->known_frame >= 0 && f >= m->known_fill)
             m->max_append = std::max(m->max_append, (f - m->known_fill) / (double)(m->ring_frame[slot] - m->known_frame));
         m->known_fill = f;
@@ -589,6 +624,15 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
         if (st != MAP_OK) return st;
     }
     const long long np = (long long)L->H * L->W;
+    // this scan's range-image and counter set; the per-point kernel resets the other
+    const int cur = m->fcur ^ 1, nxt = m->fcur;
+    m->fcur = cur;
+    m->fd.win = m->win_buf[cur];
+    m->fd.ctr = m->ctr_buf[cur];
+    FrameDev fd = m->fd;
+    fd.win_next = m->win_buf[nxt];
+    fd.win_next_n = m->win_dirty[nxt];
+    fd.ctr_next = m->ctr_buf[nxt];
     cudaEvent_t *ev = nullptr;
     unsigned long long *ev_stats = nullptr;
     if (m->prof_n < m->prof_cap) {
@@ -596,10 +640,17 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
         ev = &m->prof_ev[(size_t)m->prof_n++ * (MAP_PHASE_COUNT + 1)];
     }
     if (ev) CU(cudaEventRecord(ev[0], s));
-    CU(cudaMemsetAsync(m->fd.win, 0xFF, np * sizeof(unsigned long long), s));
-    CU(cudaMemsetAsync(m->fd.ctr, 0, CT_COUNT * sizeof(unsigned long long), s));
+    // only when the previous scan did not leave this set clean (first use after
+    // a failed call): the resets the per-point kernel otherwise does ahead
+    if (m->win_dirty[cur] > 0)
+        CU(cudaMemsetAsync(fd.win, 0xFF, std::min(m->win_dirty[cur], (long long)m->cfg.max_pixels) * sizeof(unsigned long long), s));
+    if (!m->ctr_clean[cur]) CU(cudaMemsetAsync(fd.ctr, 0, map_t::CTR_BYTES, s));
     if (ev) CU(cudaEventRecord(ev[1], s));
-    launch_points(pts, sc, m->md, m->fd, s);
+    m->win_dirty[cur] = np;
+    m->ctr_clean[cur] = false;
+    launch_points(pts, sc, m->md, fd, s);
+    m->win_dirty[nxt] = 0;
+    m->ctr_clean[nxt] = true;
     if (sc.dist_mode) {
         CU(cudaStreamWaitEvent(s, m->ev_dir, 0));   // pixel-ray tables uploaded
         launch_normals(sc, m->fd, s);
@@ -622,12 +673,17 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
         CU(cudaMemcpyAsync(ev_stats, m->fd.ctr, CT_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
     st = launch_check(m, "integrate_scan kernels");
     if (st != MAP_OK) return st;
-    CU(cudaMemcpyAsync(m->h_ctr, m->fd.ctr, CT_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    // snapshot [counters | state] on the device, download it beside the next scan
     const int slot = m->frame % map_t::RING;
-    CU(cudaMemcpyAsync(m->h_ring_ctr + (size_t)slot * CT_COUNT, m->fd.ctr, CT_COUNT * sizeof(unsigned long long),
-                       cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(&m->h_ring[slot], m->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-    CU(cudaEventRecord(m->ev_ring[slot], s));
+    unsigned char *rec = m->d_ring + (size_t)slot * map_t::REC_BYTES;
+    launch_snapshot(m->fd.ctr, m->st, rec, s);
+    m->launches += 1;
+    CU(cudaEventRecord(m->ev_snap, s));
+    CU(cudaStreamWaitEvent(m->dl, m->ev_snap, 0));
+    CU(cudaMemcpyAsync(m->h_ring + (size_t)slot * map_t::REC_BYTES, rec, map_t::REC_BYTES, cudaMemcpyDeviceToHost,
+                       m->dl));
+    CU(cudaEventRecord(m->ev_ring[slot], m->dl));
+    m->h_ctr_slot = slot;
     m->ring_frame[slot] = m->frame;
     m->ring_epoch[slot] = m->epoch;
     m->frame++;
@@ -694,6 +750,7 @@ extern "C" map_status map_remesh_all(map_t *m, void *stream) {
     if (st != MAP_OK) return st;
     // map_get_frame_stats now reports this pass (blocks meshed, vertices, triangles)
     CU(cudaMemcpyAsync(m->h_ctr, m->fd.ctr, CT_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    m->h_ctr_slot = -1;
     return MAP_OK;
 }
 
@@ -733,12 +790,13 @@ extern "C" map_status map_frame_stats(map_t *m, int64_t frame, int64_t *out) {
     if (m->ring_frame[slot] != frame) return fail(m, MAP_ERR_ARG, "frame no longer held");
     CU(cudaEventSynchronize(m->ev_ring[slot]));
     for (int i = 0; i < MAP_STAT_COUNT; ++i) out[i] = 0;
-    const unsigned long long *c = m->h_ring_ctr + (size_t)slot * CT_COUNT;
+    const unsigned long long *c = ring_ctr(m, slot);
+    const DevState &d = ring_state(m, slot);
     for (int i = 0; i < CT_MT + 1; ++i) out[i] = (int64_t)c[i];
-    out[MAP_STAT_TOTAL_BLOCKS] = (int64_t)std::min<unsigned long long>(m->h_ring[slot].pool_count, m->md.max_blocks);
-    out[MAP_STAT_ERROR_BITS] = (int64_t)m->h_ring[slot].err;
+    out[MAP_STAT_TOTAL_BLOCKS] = (int64_t)std::min<unsigned long long>(d.pool_count, m->md.max_blocks);
+    out[MAP_STAT_ERROR_BITS] = (int64_t)d.err;
     out[MAP_STAT_KERNEL_LAUNCHES] = (int64_t)m->launches;
-    return device_errors_of(m, m->h_ring[slot]);
+    return device_errors_of(m, d);
 }
 
 extern "C" map_status map_sync(map_t *m, void *stream) {
@@ -754,6 +812,10 @@ extern "C" map_status map_sync(map_t *m, void *stream) {
 extern "C" map_status map_get_frame_stats(map_t *m, int64_t *out, void *stream) {
     if (!m || !out) return fail(m, MAP_ERR_ARG, "null argument");
     map_status st = map_sync(m, stream);
+    if (m->h_ctr_slot >= 0) {
+        CU(cudaEventSynchronize(m->ev_ring[m->h_ctr_slot]));
+        std::memcpy(m->h_ctr, ring_ctr(m, m->h_ctr_slot), map_t::CTR_BYTES);
+    }
     for (int i = 0; i < MAP_STAT_COUNT; ++i) out[i] = 0;
     for (int i = 0; i < CT_MT + 1; ++i) out[i] = (int64_t)m->h_ctr[i];
     out[MAP_STAT_TOTAL_BLOCKS] = (int64_t)std::min<unsigned long long>(m->h_st->pool_count, m->md.max_blocks);
@@ -880,6 +942,7 @@ extern "C" map_status integrate_labels_camera(map_t *m, const camera_intrinsics 
     if (st != MAP_OK) return st;
     // map_get_frame_stats now reports this image (MAP_STAT_VOXELS_SEMANTIC)
     CU(cudaMemcpyAsync(m->h_ctr, m->fd.ctr, CT_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    m->h_ctr_slot = -1;
     return MAP_OK;
 }
 
@@ -1380,6 +1443,7 @@ static map_status batch_retire(map_batch_t *b) {
         map_t *m = b->maps[i];
         *m->h_st = b->out_host[i].st;
         std::memcpy(m->h_ctr, b->out_host[i].ctr, sizeof(b->out_host[i].ctr));
+        m->h_ctr_slot = -1;
         const double f = arena_fill(*m->h_st);
         if (m->known_frame >= 0 && m->frame - 1 > m->known_frame && f >= m->known_fill)
             m->max_append = std::max(m->max_append, (f - m->known_fill) / (double)(m->frame - 1 - m->known_frame));
@@ -1438,7 +1502,8 @@ extern "C" map_status map_batch_integrate(map_batch_t *b, const scan_desc *scans
         BatchItem &it = args.it[i];
         it.sc = sc;
         it.md = m->md;
-        it.fd = m->fd;
+        it.fd = m->fd;      // the batch kernel resets this set's range image and counters itself
+        m->win_dirty[m->fcur] = m->cfg.max_pixels;
         it.sc.pts = d.points_dev;
         it.sc.labels = d.labels_dev;
         it.sc.probs = d.probs_dev;

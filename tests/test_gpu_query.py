@@ -102,18 +102,22 @@ def test_pose_gradient_matches_oracle_and_fd():
         assert pg[j] == pytest.approx(fd, rel=1e-3, abs=1e-3 * np.abs(ref["dL"]).max())
 
 
-def test_pose_gradient_on_a_fused_map():
+@pytest.mark.parametrize("name,storage", [("line16", 0), ("drive1km", 1)])
+def test_pose_gradient_on_a_fused_map(name, storage):
     """The pose gradient on a map fused from scans rather than an analytic field: the oracle fuses
-    four 16 x 1024 scans, its blocks (rounded to FP32) are written into both maps, and the device
+    the first four scans of the workload (16 x 1024 at 0.2 m voxels near the origin, FP32 storage;
+    64 x 2048 at 0.1 m voxels 480 m from it, FP16 storage), its blocks (rounded to the storage
+    type) are written into both maps, and the device
     gradient of sum sdf^2 over the last scan's points at a perturbed pose is compared with the
     oracle's FP64 analytic gradient and with FP64 central differences (h = 1e-4) of its loss.
     Rotations are taken about the points' centroid c (the gradient about the origin converts as
     g_phi(c) = g_phi - c x g_rho).  Only points valid and inside the same interpolation cell at the
     pose and all 12 perturbed poses enter the loss: the trilinear field's gradient jumps across
     cell faces, so the loss is smooth only there."""
-    w = synth.line16()
+    w = getattr(synth, name)()
     L = w.lidar
     frames = list(synth.sequence(w, 4))
+    cast = np.float16 if storage else np.float32
     ob = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
     for f in frames:
         ob.integrate(L, f.points, f.T, labels=f.labels)
@@ -121,12 +125,12 @@ def test_pose_gradient_on_a_fused_map():
     D, W = [], []
     for b in blocks:
         r = ob.read_block(b)
-        D.append(r["D"].astype(np.float32))
-        W.append(r["W"].astype(np.float32))
+        D.append(r["D"].astype(cast).astype(np.float32))
+        W.append(r["W"].astype(cast).astype(np.float32))
     D, W = np.stack(D), np.stack(W)
     P = _P()
-    g = P.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=2 * len(blocks), hash_capacity=1 << 16,
-                       max_points=1 << 15, max_pixels=1 << 15, mesh_vertex_capacity=1 << 20,
+    g = P.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, storage=storage, max_blocks=2 * len(blocks),
+                       hash_capacity=1 << 17, max_points=1 << 18, max_pixels=1 << 18, mesh_vertex_capacity=1 << 20,
                        mesh_triangle_capacity=1 << 20)
     g.write_blocks(blocks, D, W)
     o = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
@@ -172,7 +176,7 @@ def test_pose_gradient_on_a_fused_map():
     scale = float(np.abs(ref).max())
     e_ref = float(np.max(np.abs(pg_c - ref)) / scale)
     e_fd = float(np.max(np.abs(pg_c - fd)) / scale)
-    print(f"fused-map pose gradient: {int(ok.sum())} of {len(p)} points in the loss, relative error "
+    print(f"fused-map pose gradient ({name}): {int(ok.sum())} of {len(p)} points in the loss, relative error "
           f"{e_ref:.2e} vs the oracle's analytic gradient, {e_fd:.2e} vs central differences")
     assert e_ref <= 1e-4, e_ref
     assert e_fd <= 1e-4, e_fd
