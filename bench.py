@@ -216,13 +216,14 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-def traffic_record(kernel):
-    """Per-launch DRAM bytes from the committed ncu summary, if it matches the current source
-    (the kernel's file and the shared per-item bodies)."""
+def traffic_record(kernel, variant=""):
+    """Per-launch DRAM bytes from the committed ncu summary of this kernel variant ("" for FP32
+    storage and projective distance, "_nonproj" for the non-projective distance), if it matches the
+    current source (the kernel's file and the shared per-item bodies)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    rec = json.load(open(p)).get(kernel)
+    rec = json.load(open(p)).get(kernel + variant)
     if not rec:
         return None
     csrc = os.path.join(ROOT, "paper_2412_00291_b300", "csrc")
@@ -524,7 +525,8 @@ def run_ours(args, rank, world, local_rank):
              "gbs": float(stage_b.sum() / (stage_t.sum() * 1e-3) / 1e9)}
     dom = max(per_kernel, key=lambda k: per_kernel[k]["share"])
     ach = per_kernel[dom]["gbs"]
-    tr = traffic_record(dom)
+    # captured variants: FP32 storage, either distance (no FP16-storage capture: traffic null there)
+    tr = traffic_record(dom, "_nonproj" if nonproj else "") if storage == 0 else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "nominal_peak": 7700.0, "frac_nominal": ach / 7700.0,
             "peak_source": f"{peak_kind} hbm_gbs", "traffic": tr["bytes_per_launch"] if tr else None,

@@ -188,6 +188,49 @@ def test_edge_cases_empty_ragged_invalid():
     assert rep["observed"] > 10000
 
 
+def test_changing_image_sizes_and_interleaved_calls():
+    """Scans whose range images alternate between 16 x 1024 and 32 x 2048 pixels, with a full re-mesh
+    between some of them.  Each scan's range image and counters are reset
+    ahead of time by the previous scan's per-point kernel (two sets in turn), so a larger image after a
+    smaller one, or a re-mesh that reuses the counters between scans, must leave nothing stale: per-scan
+    counters, the download ring's copies of them, the block set, the voxels and the mesh all against
+    the oracle fed the same scans."""
+    import dataclasses
+    p = _lib()
+    w = synth.line16()
+    wide = dataclasses.replace(w, lidar=synth.lidar_deg(32, 2048, 15.0, -15.0, 50.0))
+    scene = synth.make_scene(w)
+    gm = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=32768, hash_capacity=1 << 16,
+                        max_points=65536, max_pixels=65536, mesh_vertex_capacity=1 << 22,
+                        mesh_triangle_capacity=1 << 23)
+    om = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    seen = []
+    for k, T in enumerate(synth.trajectory(w, 7)):
+        wk = wide if k in (1, 2, 5) else w
+        f = synth.make_frame(wk, scene, T, k)
+        gm.integrate(_lidar(p, wk.lidar), _dev(f.points), f.T, labels=_dev(f.labels))
+        os_ = om.integrate(wk.lidar, f.points, f.T, labels=f.labels)
+        gs = gm.stats()
+        seen.append(gs)
+        assert gs["error_bits"] == 0
+        for key in ("valid_points", "pixel_points", "touched_blocks", "new_blocks"):
+            assert gs[key] == os_[key], (k, key, gs[key], os_[key])
+        assert abs(gs["voxels_updated"] - os_["voxels_updated"]) <= max(10, os_["taint_events"])
+        if k in (2, 3):
+            gm.remesh_all()
+            assert gm.stats()["mesh_triangles"] > 0
+    for k, gs in enumerate(seen):
+        fs = gm.frame_stats(k)
+        for key in ("valid_points", "pixel_points", "touched_blocks", "new_blocks", "voxels_updated",
+                    "voxels_semantic", "mesh_vertices", "mesh_triangles"):
+            assert fs[key] == gs[key], (k, key)
+    np.testing.assert_array_equal(_sorted(gm.blocks()), _sorted(om.alloc_blocks()))
+    rep = compare_blocks(gm, om, om.alloc_blocks(), w.voxel_size, 7, w.n_classes)
+    assert rep["tainted_metric"] < 0.05 * rep["observed"]
+    compare_meshes(_mesh_np(gm.mesh()), om.mesh(), om, w.voxel_size)
+    gm.close()
+
+
 def test_errors_bad_pose_args_capacity():
     p = _lib()
     w = synth.line16()
