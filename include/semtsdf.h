@@ -430,9 +430,12 @@ map_status map_write_blocks(map_t *map, const int32_t *coords_host, int64_t n, c
 /* Phases of one integrate_scan, in launch order (one kernel each, after the resets).
  * The class update and the re-meshing run concurrently (two streams, both
  * after the TSDF kernel); each reports its own duration, so a scan takes
- * less than the sum of its phases. */
+ * less than the sum of its phases.  Recording puts an event between every
+ * two kernels, which also keeps the TSDF and re-meshing kernels from being
+ * scheduled before their predecessor ends (unrecorded scans let them). */
 enum {
-    MAP_PHASE_RESET = 0,      /* range-image and counter resets                               */
+    MAP_PHASE_RESET = 0,      /* range-image and counter resets: empty in the steady state (the
+                                 previous scan's per-point kernel resets this scan's set)     */
     MAP_PHASE_POINTS = 1,     /* per point: range-image winner (Sec. III-C.1), band allocation;
                                  the normal image in the non-projective mode                  */
     MAP_PHASE_TSDF = 2,       /* projective TSDF update (Sec. III-C.2), re-mesh queue          */
