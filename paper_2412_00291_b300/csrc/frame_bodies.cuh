@@ -596,15 +596,14 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
         qn -= n;
         tsdf_list(sem, vox, idx, T.wbuf, wcount);
     };
-    // voxels vi and vi + 32 per step: both {D, W} reads are issued before the
-    // projections and both pixel reads before either update, so that their
-    // latencies overlap
-#pragma unroll 1
     // the lane's voxels are (x, y, z), (x, y + 4, z) with z one higher each step: their
     // directions follow from the first by adding R^T's images of one z step and four y steps
     float da0, da1, da2;
     tsdf_dir(sc, bx, by, bz, v0 + lane, da0, da1, da2);
     const float ey0 = __fmul_rn(4.f, sc.Rt[1]), ey1 = __fmul_rn(4.f, sc.Rt[4]), ey2 = __fmul_rn(4.f, sc.Rt[7]);
+    // voxels vi and vi + 32 per step: both {D, W} reads are issued before the
+    // projections and both pixel reads before either update, so that their
+    // latencies overlap
     for (int vi = v0 + lane; vi < v1; vi += 64) {
         const long long va = (long long)slot * BV + vi, vb = va + 32;
         const float2 dwa = load_dw<F16>(md, va), dwb = load_dw<F16>(md, vb);
