@@ -568,10 +568,11 @@ def run_ours(args, rank, world, local_rank):
         e2e_s = time.perf_counter() - t0
         assert len(results) == args.steps and all(r["valid_points"] > 0 for r in results)
         h2d = n_points * 12 + (n_points * C * 4 if pr_d else n_points * 4)
+        # the D->H record of a scan: its 16 counters and the 784-byte device state
         e2e = {"value": world * args.steps * n_points / e2e_s, "unit": "points/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": 16 * 8, "ms_per_step": 1e3 * e2e_s / args.steps,
+               "d2h_bytes_per_step": 16 * 8 + 784, "ms_per_step": 1e3 * e2e_s / args.steps,
                "timing": "wall clock over the pipelined loop: per step H->D of the scan, the scan, D->H of its "
-                         "counters; uploads overlap the previous scan's kernels"}
+                         "counters and the device state; uploads overlap the previous scan's kernels"}
         tsdf2.close()
     # --- CPU baseline: the oracle on the host cores --------------------------
     cpu = None
