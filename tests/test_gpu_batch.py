@@ -151,6 +151,39 @@ def test_batch_map_against_oracle(batch_run):
     compare_meshes(g, om.mesh(), om, w.voxel_size)
 
 
+def test_batch_and_single_calls_on_one_map():
+    """Batched steps and single integrate_scan calls mixed on the same map: each call leaves the
+    range image and counters for the next one (the batch kernel resets the set it uses itself, a
+    single call's per-point kernel resets the other set), so the result must equal, bit for bit,
+    a map that took every scan through integrate_scan, and so must every per-scan counter."""
+    p = _lib()
+    w = synth.line16()
+    frames = list(synth.sequence(w, 8))
+    L = p.lidar_intrinsics(w.lidar.H, w.lidar.W, w.lidar.fov_up, w.lidar.fov_down, w.lidar.r_min, w.lidar.r_max)
+    ref = _new_map(p, w, w.voxel_size, w.truncation, 0)
+    mix = _new_map(p, w, w.voxel_size, w.truncation, 0)
+    b = p.map_batch_create([mix.h], p.MAP_BATCH_GRAPH)
+    for k, f in enumerate(frames):
+        pt, lb = _dev(f.points), _dev(f.labels)
+        ref.integrate(L, pt, f.T, labels=lb)
+        if k in (0, 1, 4, 7):
+            p.map_batch_integrate(b, [mix.h], [L], [pt], [f.T], labels=[lb])
+            p.map_batch_sync(b)
+        else:
+            mix.integrate(L, pt, f.T, labels=lb)
+        sr, sm = ref.stats(), mix.stats()
+        for key in COUNTERS:
+            assert sr[key] == sm[key], (k, key, sr[key], sm[key])
+    cr = _sorted(ref.blocks())
+    assert np.array_equal(cr, _sorted(mix.blocks()))
+    gr, gm = ref.read_blocks(cr), mix.read_blocks(cr)
+    for key in ("D", "W", "label", "logP"):
+        assert np.array_equal(gr[key].view(np.uint8), gm[key].view(np.uint8)), key
+    p.map_batch_destroy(b)
+    ref.close()
+    mix.close()
+
+
 def test_autotuner_visits_every_configuration(batch_run):
     p = batch_run["p"]
     # 8 steps: the tuner is still timing (3 steps per configuration)
