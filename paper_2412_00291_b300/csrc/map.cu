@@ -60,6 +60,7 @@ struct map_t {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     long long ring_frame[RING] = {};
+    long long absorbed = -1;        // ring entries up to this frame have been read
     int ring_epoch[RING] = {};
     int epoch = 0;                  // bumped by every compaction
     double known_fill = 0.0;         // largest used fraction of any arena partition
@@ -574,16 +575,21 @@ static void absorb(map_t *m, int slot) {
     }
 }
 
-// Before frame f: wait for frame f - RING's copy (frames-in-flight bound) and
-// read every completed copy.
+// Before frame f: read the completed ring entries.  They complete in frame
+// order (one download stream), so the scan starts at the oldest entry not yet
+// read and stops at the first still in flight; the entry of frame f - RING,
+// whose slot frame f reuses, is waited for (the frames-in-flight bound).
 static void poll_stats(map_t *m) {
-    const int slot = m->frame % map_t::RING;
-    if (m->ring_frame[slot] >= 0) {
-        cudaEventSynchronize(m->ev_ring[slot]);
-        absorb(m, slot);
+    const long long reuse = (long long)m->frame - map_t::RING;
+    for (long long f = std::max(m->absorbed + 1, reuse); f < m->frame; ++f) {
+        const int slot = (int)(f % map_t::RING);
+        if (f >= 0 && m->ring_frame[slot] == f) {
+            if (f == reuse) cudaEventSynchronize(m->ev_ring[slot]);
+            else if (cudaEventQuery(m->ev_ring[slot]) != cudaSuccess) break;
+            absorb(m, slot);
+        }
+        m->absorbed = f;    // read, or a batched step (no ring entry)
     }
-    for (int i = 0; i < map_t::RING; ++i)
-        if (m->ring_frame[i] >= 0 && cudaEventQuery(m->ev_ring[i]) == cudaSuccess) absorb(m, i);
 }
 
 // Compact when a partition could pass 3/4 of its space before the host sees it
