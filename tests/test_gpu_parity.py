@@ -231,6 +231,44 @@ def test_changing_image_sizes_and_interleaved_calls():
     gm.close()
 
 
+def test_capacities_at_their_limits():
+    """Sizes at the configured maxima: a scan of exactly max_points points on an image of exactly
+    max_pixels pixels into a pool of exactly the blocks it needs integrates without an error bit
+    and matches the oracle; one point more is refused on the host, and a pool one block short
+    latches the pool-full error on the device with the pool exactly full."""
+    p = _lib()
+    w = synth.line16()
+    f = next(iter(synth.sequence(w, 1)))
+    L = _lidar(p, w.lidar)
+    npix = w.lidar.H * w.lidar.W
+    assert len(f.points) == npix
+    om = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    om.integrate(w.lidar, f.points, f.T, labels=f.labels)
+    need = len(om.alloc_blocks())
+
+    def make(max_blocks):
+        return p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=max_blocks,
+                              hash_capacity=4 * max_blocks, max_points=npix, max_pixels=npix,
+                              mesh_vertex_capacity=1 << 21, mesh_triangle_capacity=1 << 22)
+    gm = make(need)
+    gm.integrate(L, _dev(f.points), f.T, labels=_dev(f.labels))
+    s = gm.stats()
+    assert s["error_bits"] == 0 and s["total_blocks"] == need
+    np.testing.assert_array_equal(_sorted(gm.blocks()), _sorted(om.alloc_blocks()))
+    rep = compare_blocks(gm, om, om.alloc_blocks(), w.voxel_size, 1, w.n_classes)
+    assert rep["observed"] > 10000
+    extra = np.concatenate([f.points, f.points[:1]])
+    with pytest.raises(p.MapError) as e:
+        gm.integrate(L, _dev(extra), f.T, labels=_dev(np.concatenate([f.labels, f.labels[:1]])))
+    assert e.value.status == 1
+    gm.close()
+    short = make(need - 1)
+    short.integrate(L, _dev(f.points), f.T, labels=_dev(f.labels))
+    s = short.stats(check=False)
+    assert s["error_bits"] & 1 and s["total_blocks"] == need - 1
+    short.close()
+
+
 def test_errors_bad_pose_args_capacity():
     p = _lib()
     w = synth.line16()
