@@ -269,6 +269,48 @@ def test_capacities_at_their_limits():
     short.close()
 
 
+def test_azimuth_seam_and_elevation_edges():
+    """Points on the azimuth seam behind the sensor (y = +0.0, -0.0 and a few ulps either side, where
+    atan2 jumps from pi to -pi and the column index wraps from W to 0), and points just inside and
+    well outside the top and bottom beams: pixel assignment, winners, the block set and the voxels
+    against the oracle, with a rotated, translated pose."""
+    p = _lib()
+    w = synth.line16()
+    Lw = w.lidar
+    L = _lidar(p, Lw)
+    pts = []
+    for v in range(Lw.H):
+        th = Lw.theta0 + v * Lw.dtheta
+        for r in (4.0, 9.5, 17.25, 31.0):
+            for y in (0.0, -0.0, 1e-6, -1e-6, 3e-7, -3e-7):
+                x = -r * np.sin(th)
+                pts.append((x, y, r * np.cos(th)))
+    for th in (Lw.theta0 - 0.2 * Lw.dtheta, Lw.theta0 + (Lw.H - 1.2) * Lw.dtheta,
+               Lw.theta0 - 1.0 * Lw.dtheta, Lw.theta0 + (Lw.H + 0.0) * Lw.dtheta):
+        for phi in np.linspace(-3.0, 3.0, 41):
+            r = 12.0
+            pts.append((r * np.sin(th) * np.cos(phi), r * np.sin(th) * np.sin(phi), r * np.cos(th)))
+    pts = np.array(pts, np.float32)
+    lab = (np.arange(len(pts)) % w.n_classes).astype(np.int32)
+    T = synth.pose(synth.rot_rpy(0.01, -0.02, 0.7), [3.2, -1.1, 1.8])
+    gm = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=16384, hash_capacity=1 << 15,
+                        max_points=32768, max_pixels=32768, mesh_vertex_capacity=1 << 21,
+                        mesh_triangle_capacity=1 << 22)
+    om = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    gm.integrate(L, _dev(pts), T, labels=_dev(lab))
+    os_ = om.integrate(Lw, pts, T, labels=lab)
+    gs = gm.stats()
+    assert os_["ambiguous_points"] == 0
+    for key in ("valid_points", "pixel_points", "touched_blocks", "new_blocks"):
+        assert gs[key] == os_[key], (key, gs[key], os_[key])
+    assert gs["pixel_points"] < gs["valid_points"]          # the points outside the beams have no pixel
+    np.testing.assert_array_equal(_sorted(gm.blocks()), _sorted(om.alloc_blocks()))
+    rep = compare_blocks(gm, om, om.alloc_blocks(), w.voxel_size, 1, w.n_classes)
+    print("seam and edges:", gs, rep)
+    assert rep["observed"] > 300 and rep["observed"] - rep["tainted_metric"] > 50
+    gm.close()
+
+
 def test_errors_bad_pose_args_capacity():
     p = _lib()
     w = synth.line16()
