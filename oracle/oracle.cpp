@@ -41,10 +41,13 @@
  * or the voxel has no gradient yet (then d_i = psi).  The weight and the
  * skip below -tau stay on psi; Gamma(d_i, tau) is the fused value.
  *
- * Parity unpinned: the fusion of probability vectors is pinned only by its
- * closed form for one vector per scan, the normalisation invariant and its
- * independence of the scan order; the paper gives no worked example with
- * which to pin it further.
+ * The fusion of probability vectors has no worked example in the paper; it
+ * is pinned by closed forms and invariants: the normalised product of the
+ * scans' vectors, the normalisation invariant, independence of the scan
+ * order, a uniform likelihood leaving the posterior unchanged, and the two
+ * floors (an entry below lik_floor counts as lik_floor; a class held there
+ * reaches logp_floor exactly while the others keep their product's closed
+ * form).
  *
  * Precision: every value is FP64.  Two integer decisions are taken in the
  * precision the GPU takes them in, as both sides of a parity check must:

@@ -490,6 +490,35 @@ def test_generic_class_count(storage, cls):
     gm.close()
 
 
+def test_probability_floors_against_oracle():
+    """Sharply peaked probability vectors with exact zeros: every class but the winner's enters at
+    the likelihood floor, and after three scans the log-probability floor binds for them.  The 20-
+    class fast path against the oracle, floored entries included (both sit at logp_floor)."""
+    p = _lib()
+    w = synth.line16()
+    C = w.n_classes
+    L = _lidar(p, w.lidar)
+    gm = p.SemanticTSDF(w.voxel_size, w.truncation, C, max_blocks=32768, hash_capacity=1 << 16,
+                        max_points=32768, max_pixels=32768, mesh_vertex_capacity=1 << 22,
+                        mesh_triangle_capacity=1 << 23)
+    om = oracle.OracleMap(w.voxel_size, w.truncation, C)
+    frames = list(synth.sequence(w, 4))
+    for f in frames:
+        q = np.zeros((len(f.labels), C), np.float32)
+        q[np.arange(len(f.labels)), np.clip(f.labels, 0, C - 1)] = 1.0
+        gm.integrate(L, _dev(f.points), f.T, probs=_dev(q))
+        om.integrate(w.lidar, f.points, f.T, probs=q)
+    coords = _sorted(om.alloc_blocks())
+    rep = compare_blocks(gm, om, coords, w.voxel_size, len(frames), C)
+    g = gm.read_blocks(coords)
+    n_floor_g = int((g["logP"] == -30.0).sum())
+    n_floor_o = sum(int((om.read_block(b)["logP"] == -30.0).sum()) for b in coords)
+    print("floors:", rep, n_floor_g, n_floor_o)
+    assert rep["semantic"] > 1000 and n_floor_o > 10000
+    assert abs(n_floor_g - n_floor_o) <= 0.01 * n_floor_o
+    gm.close()
+
+
 def test_far_from_origin():
     """The whole drive 10 km / -7 km / +30 m away from the world origin: the sensor-relative
     voxel offsets (integer + float pair) keep FP32 psi at the same accuracy."""

@@ -306,6 +306,44 @@ def test_probability_vector_closed_form_and_invariants():
         np.testing.assert_allclose(blk["logP"], b0, atol=1e-12)
 
 
+def test_probability_floors():
+    """The two floors of the class update.  A likelihood entry below lik_floor counts as lik_floor
+    (one update from the uniform prior gives log max(q, lik_floor) renormalised); a class whose
+    likelihood stays at the floor falls by ~ln(1e6) per scan until its log-probability sits at
+    logp_floor exactly, while the other classes keep the closed form of their product (the floored
+    class carries < e^-30 of the mass, far below the 1e-12 tolerance)."""
+    C, R_s, nu, tau = 6, 3.0, 0.2, 0.6
+    lik_floor, logp_floor = 1e-6, -30.0
+    lid, pts = _sphere_scan(R_s, H=48, W=192)
+    t0 = np.array([0.05, 0.1, -0.05])
+    T = _pose(random_rotation(np.random.default_rng(9)), t0)
+    q = np.array([0.0, 0.4, 0.3, 0.2, 0.1, 0.0], np.float32)       # classes 0 and 5 below the floor
+    m = oracle.OracleMap(nu, tau, n_classes=C, logp_floor=logp_floor, lik_floor=lik_floor)
+    probs = np.tile(q, (len(pts), 1))
+    lq = np.log(np.maximum(q.astype(np.float64), lik_floor))
+    for k in range(1, 5):
+        m.integrate(lid, pts, T, probs=probs)
+        a = k * lq
+        checked = 0
+        for blk, gate, _ in _sem_voxels(m, nu, t0, R_s, tau):
+            if not gate.any():
+                continue
+            lp = blk["logP"][:, gate]
+            expect = a - (a.max() + math.log(np.exp(a - a.max()).sum()))
+            if expect.min() > logp_floor:
+                # no log-probability floor binds yet: the closed form with the likelihood floor
+                np.testing.assert_allclose(lp, expect[:, None] * np.ones((1, gate.sum())), atol=1e-12)
+            else:
+                # classes 0 and 5 sit at the floor; the others keep the closed form of their product
+                assert np.all(lp[[0, 5]] == logp_floor)
+                live = np.array([1, 2, 3, 4])
+                al = a[live] - (a[live].max() + math.log(np.exp(a[live] - a[live].max()).sum()))
+                np.testing.assert_allclose(lp[live], al[:, None] * np.ones((1, gate.sum())), atol=1e-12)
+            checked += int(gate.sum())
+        assert checked > 500
+    assert 3 * (math.log(lik_floor) - math.log(0.4)) < logp_floor   # the floor binds from the third scan
+
+
 # ---------------------------------------------------------------------------
 # block allocation along the band: brute-force segment sampling
 # ---------------------------------------------------------------------------
