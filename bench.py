@@ -668,30 +668,26 @@ def run_batch(args, rank, world, local_rank):
         return [P.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, storage=1, **stream_config(w, n_frames))
                 for w in ws]
 
-    side = [torch.cuda.Stream(dev) for _ in ws]
-
     def run_arm(batched, concurrent=False):
         maps = new_maps()
-        b = P.map_batch_create([m.h for m in maps], P.MAP_BATCH_GRAPH | P.MAP_BATCH_AUTOTUNE) if batched else None
+        b = None
+        if batched:
+            b = P.map_batch_create([m.h for m in maps], P.MAP_BATCH_GRAPH | P.MAP_BATCH_AUTOTUNE)
+        elif concurrent:
+            # each map's integrate_scan kernels on a stream of the batch's own, forked and joined in the library
+            b = P.map_batch_create([m.h for m in maps], P.MAP_BATCH_STREAMS)
 
         def step(k):
-            if batched:
+            if batched or concurrent:
                 P.map_batch_integrate(b, [m.h for m in maps], lids, [p[k] for p in pts], [t[k] for t in Ts],
                                       probs=[q[k] for q in probs])
-            elif concurrent:
-                # each map's integrate_scan on a stream of its own, forked from and joined to the caller's
-                for i, m in enumerate(maps):
-                    side[i].wait_stream(stream)
-                    m.integrate(lids[i], pts[i][k], Ts[i][k], probs=probs[i][k], stream=side[i])
-                for s_ in side:
-                    stream.wait_stream(s_)
             else:
                 for i, m in enumerate(maps):
                     m.integrate(lids[i], pts[i][k], Ts[i][k], probs=probs[i][k])
 
         for k in range(warm):
             step(k)
-        if batched:
+        if b is not None:
             P.map_batch_sync(b)
         torch.cuda.synchronize()
         l0 = sum(m.stats()["kernel_launches"] for m in maps)
@@ -712,6 +708,8 @@ def run_batch(args, rank, world, local_rank):
             tuned = P.map_batch_config(b)
             launches = steps      # one cooperative kernel per step
         else:
+            if b is not None:
+                P.map_batch_sync(b)
             tuned = None
             launches = sum(m.stats()["kernel_launches"] for m in maps) - l0
         devms = [a.elapsed_time(c) for a, c in ev]
@@ -730,11 +728,12 @@ def run_batch(args, rank, world, local_rank):
         sample[i] = (c, seq_maps[i].read_blocks(c, want_logp=False))
     for m in seq_maps:
         m.close()
-    con_maps, _, con = run_arm(False, concurrent=True)
+    con_maps, bc, con = run_arm(False, concurrent=True)
     max_dd_c = 0.0
     for i, (c, g) in sample.items():
         h = con_maps[i].read_blocks(c, want_logp=False)
         max_dd_c = max(max_dd_c, float(np.abs(h["D"] - g["D"]).max(initial=0)))
+    P.map_batch_destroy(bc)
     for m in con_maps:
         m.close()
     bat_maps, b, bat = run_arm(True)

@@ -357,11 +357,16 @@ typedef struct map_batch_t map_batch_t;
 
 enum {
     MAP_BATCH_GRAPH = 1,     /* replay the launch from a CUDA graph (one per launch configuration) */
-    MAP_BATCH_AUTOTUNE = 2   /* time each launch configuration on the first steps, keep the fastest */
+    MAP_BATCH_AUTOTUNE = 2,  /* time each launch configuration on the first steps, keep the fastest */
+    MAP_BATCH_STREAMS = 4    /* instead of the cooperative kernel: each map's integrate_scan kernels on
+                                a stream of the batch's own, all maps concurrently, forked from and
+                                joined to the caller's stream (GRAPH and AUTOTUNE then do nothing) */
 };
 
 /* Group 1..48 maps (each used by this batch only while it exists).  The batch
- * kernel needs cooperative launch support; MAP_ERR_STATE otherwise. */
+ * kernel needs cooperative launch support (MAP_ERR_STATE otherwise) and maps
+ * in the projective distance mode (MAP_ERR_ARG otherwise, unless the batch
+ * is created with MAP_BATCH_STREAMS). */
 map_status map_batch_create(map_t *const *maps, int32_t n_maps, int32_t flags, map_batch_t **out);
 map_status map_batch_destroy(map_batch_t *batch);
 
@@ -376,6 +381,10 @@ map_status map_batch_destroy(map_batch_t *batch);
  * flight); errors of the previous step (MAP_ERR_TIMEOUT when a barrier wait
  * ran out, MAP_ERR_CAPACITY) are returned by the next call or map_batch_sync. */
 map_status map_batch_integrate(map_batch_t *batch, const scan_desc *scans, void *stream);
+
+/* With MAP_BATCH_STREAMS the step is n_maps integrate_scan calls, each on
+ * its own stream of the batch, run concurrently and joined to `stream`;
+ * per-map results are those of integrate_scan (map_frame_stats included). */
 
 /* Wait for the step in flight and report its errors. */
 map_status map_batch_sync(map_batch_t *batch, void *stream);

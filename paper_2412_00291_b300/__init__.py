@@ -62,6 +62,7 @@ class ScanDesc(ctypes.Structure):
 
 MAP_BATCH_GRAPH = 1
 MAP_BATCH_AUTOTUNE = 2
+MAP_BATCH_STREAMS = 4
 BATCH_MAX = 48
 
 _SIGS = {

@@ -1351,6 +1351,10 @@ struct map_batch_t {
     cudaStream_t cap = nullptr;       // private stream the graphs are captured on (never executes work)
     int pending_cfg = -1;             // configuration of the step in flight (timed when tuning)
     bool pending = false;
+    bool pending_streams = false;     // the step in flight ran on the per-map streams
+    std::vector<cudaStream_t> mstream;   // MAP_BATCH_STREAMS: one stream per map
+    std::vector<cudaEvent_t> mdone;      // ... and the event that joins it to the caller's stream
+    cudaEvent_t ev_fork = nullptr;
     unsigned long long fault_spin = 0;   // test hook: next launch lets CTA 0 leave at once
     BatchArgs args;                      // host staging of the kernel parameters
     std::string err;
@@ -1375,8 +1379,8 @@ extern "C" map_status map_batch_create(map_t *const *maps, int32_t n_maps, int32
         return bfail(nullptr, MAP_ERR_ARG, "need 1 <= n_maps <= 48 and non-null pointers");
     for (int i = 0; i < n_maps; ++i) {
         if (!maps[i]) return bfail(nullptr, MAP_ERR_ARG, "null map in batch");
-        if (maps[i]->cfg.distance_mode != 0)
-            return bfail(nullptr, MAP_ERR_ARG, "batched integration takes projective-distance maps only");
+        if (maps[i]->cfg.distance_mode != 0 && !(flags & MAP_BATCH_STREAMS))
+            return bfail(nullptr, MAP_ERR_ARG, "the batch kernel takes projective-distance maps only");
     }
     int coop = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -1408,6 +1412,18 @@ extern "C" map_status map_batch_create(map_t *const *maps, int32_t n_maps, int32
         return bfail(nullptr, MAP_ERR_CUDA, "batch capture stream");
     }
     if (!(flags & MAP_BATCH_AUTOTUNE)) b->fixed_cfg = kNumBatchConfigs - 2;   // 8 warps, 2 items per thread
+    if (flags & MAP_BATCH_STREAMS) {
+        b->mstream.assign(n_maps, nullptr);
+        b->mdone.assign(n_maps, nullptr);
+        bool ok = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; ok && i < n_maps; ++i)
+            ok = cudaStreamCreateWithFlags(&b->mstream[i], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&b->mdone[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            map_batch_destroy(b);
+            return bfail(nullptr, MAP_ERR_CUDA, "batch per-map streams");
+        }
+    }
     *out = b;
     return MAP_OK;
 }
@@ -1426,6 +1442,11 @@ extern "C" map_status map_batch_destroy(map_batch_t *b) {
     if (b->ev_b) cudaEventDestroy(b->ev_b);
     if (b->ev_done) cudaEventDestroy(b->ev_done);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (cudaStream_t st : b->mstream)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : b->mdone)
+        if (e) cudaEventDestroy(e);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     delete b;
     return MAP_OK;
 }
@@ -1435,6 +1456,10 @@ static map_status batch_retire(map_batch_t *b) {
     if (!b->pending) return MAP_OK;
     BCU(cudaEventSynchronize(b->ev_done));
     b->pending = false;
+    if (b->pending_streams) {           // the maps' own calls have recorded their results
+        b->pending_streams = false;
+        return MAP_OK;
+    }
     const int timed_cfg = b->pending_cfg;
     b->pending_cfg = -1;
     BatchCtl ctl;
@@ -1488,9 +1513,38 @@ extern "C" map_status map_batch_integrate(map_batch_t *b, const scan_desc *scans
     cudaStream_t s = (cudaStream_t)stream;
     map_status st = batch_retire(b);
     if (st != MAP_OK) return st;
+    const int n = (int)b->maps.size();
+    if (b->flags & MAP_BATCH_STREAMS) {
+        for (int i = 0; i < n; ++i)
+            if (scans[i].map != b->maps[i]) return bfail(b, MAP_ERR_ARG, "scans[i].map must be the batch's i-th map");
+        BCU(cudaEventRecord(b->ev_fork, s));
+        map_status first = MAP_OK;
+        for (int i = 0; i < n; ++i) {
+            const scan_desc &d = scans[i];
+            map_t *m = b->maps[i];
+            BCU(cudaStreamWaitEvent(b->mstream[i], b->ev_fork, 0));
+            map_status st_i = MAP_OK;
+            if (d.n > 0 && (!d.points_dev || ((d.labels_dev == nullptr) == (d.probs_dev == nullptr))))
+                st_i = fail(m, MAP_ERR_ARG, "need points and exactly one of labels / probs");
+            else
+                st_i = run_frame(m, &d.lidar, d.points_dev, d.labels_dev, d.probs_dev, d.n, d.T_world_lidar,
+                                 b->mstream[i]);
+            if (st_i != MAP_OK && first == MAP_OK) {
+                first = st_i;
+                b->err = m->err;
+            }
+            // join every map's stream, also after an error (what was enqueued completes before the caller's stream goes on)
+            BCU(cudaEventRecord(b->mdone[i], b->mstream[i]));
+            BCU(cudaStreamWaitEvent(s, b->mdone[i], 0));
+        }
+        BCU(cudaEventRecord(b->ev_done, s));
+        b->pending = true;
+        b->pending_streams = true;
+        if (first != MAP_OK) return bfail(b, first, b->err);
+        return MAP_OK;
+    }
     BatchArgs &args = b->args;   // copied into the launch (or the graph node) by the calls below
     std::memset(&args, 0, sizeof(args));
-    const int n = (int)b->maps.size();
     for (int i = 0; i < n; ++i) {
         map_t *m = b->maps[i];
         const scan_desc &d = scans[i];

@@ -184,6 +184,49 @@ def test_batch_and_single_calls_on_one_map():
     mix.close()
 
 
+def test_streams_batch_matches_single_calls():
+    """MAP_BATCH_STREAMS: every map's scan runs on a stream of the batch, all maps concurrently.  The
+    maps (different voxel sizes, storage precisions and class inputs, ragged and empty scans, one in
+    the non-projective distance mode, which the batch kernel does not take) must equal maps fed
+    single integrate_scan calls, bit for bit, with the same counters (the download ring's too)."""
+    p = _lib()
+    w = synth.line16()
+    frames = list(synth.sequence(w, 5))
+    L = p.lidar_intrinsics(w.lidar.H, w.lidar.W, w.lidar.fov_up, w.lidar.fov_down, w.lidar.r_min, w.lidar.r_max)
+
+    def maps():
+        out = [_new_map(p, w, s[0] or w.voxel_size, s[1] or w.truncation, s[2]) for s in SPECS]
+        out.append(p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, distance="nonprojective",
+                                  max_blocks=32768, hash_capacity=1 << 16, max_points=32768, max_pixels=32768,
+                                  mesh_vertex_capacity=1 << 22, mesh_triangle_capacity=1 << 23))
+        return out
+    specs = SPECS + [(None, None, 0, "labels", None)]
+    seq, con = maps(), maps()
+    b = p.map_batch_create([m.h for m in con], p.MAP_BATCH_STREAMS)
+    for k, f in enumerate(frames):
+        ins = [_inputs(w, frames, s_, k, f) for s_ in specs]
+        dev = [(_dev(pt), None if lb is None else _dev(lb), None if pr is None else _dev(pr)) for pt, lb, pr in ins]
+        for m, (pt, lb, pr) in zip(seq, dev):
+            m.integrate(L, pt, f.T, labels=lb, probs=pr)
+        p.map_batch_integrate(b, [m.h for m in con], [L] * len(con), [d[0] for d in dev], [f.T] * len(con),
+                              labels=[d[1] for d in dev], probs=[d[2] for d in dev])
+        p.map_batch_sync(b)
+        for i, (ms, mc) in enumerate(zip(seq, con)):
+            a, c = ms.stats(), mc.stats()
+            for name in COUNTERS + ("dirty_blocks",):
+                assert a[name] == c[name], (k, i, name, a[name], c[name])
+            assert mc.frame_stats(k)["voxels_updated"] == a["voxels_updated"]
+    for ms, mc in zip(seq, con):
+        cs = _sorted(ms.blocks())
+        assert np.array_equal(cs, _sorted(mc.blocks()))
+        gs, gc = ms.read_blocks(cs), mc.read_blocks(cs)
+        for key in ("D", "W", "label", "logP"):
+            assert np.array_equal(gs[key].view(np.uint8), gc[key].view(np.uint8)), key
+    p.map_batch_destroy(b)
+    for m in seq + con:
+        m.close()
+
+
 def test_autotuner_visits_every_configuration(batch_run):
     p = batch_run["p"]
     # 8 steps: the tuner is still timing (3 steps per configuration)
