@@ -384,7 +384,9 @@ map_status map_batch_integrate(map_batch_t *batch, const scan_desc *scans, void 
 
 /* With MAP_BATCH_STREAMS the step is n_maps integrate_scan calls, each on
  * its own stream of the batch, run concurrently and joined to `stream`;
- * per-map results are those of integrate_scan (map_frame_stats included). */
+ * per-map results are those of integrate_scan (map_frame_stats included).
+ * A map whose call is refused (bad arguments) is left as it was, the other
+ * maps are still fused, and the first refusal is returned. */
 
 /* Wait for the step in flight and report its errors. */
 map_status map_batch_sync(map_batch_t *batch, void *stream);
