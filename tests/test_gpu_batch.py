@@ -227,6 +227,29 @@ def test_streams_batch_matches_single_calls():
         m.close()
 
 
+def test_streams_batch_refusal_leaves_that_map_alone():
+    """Streams mode: a map whose scan is refused (a pose that is not a rotation) keeps its state, the
+    other map of the step is fused, and the refusal is returned."""
+    p = _lib()
+    w = synth.line16()
+    f = next(iter(synth.sequence(w, 1)))
+    L = p.lidar_intrinsics(w.lidar.H, w.lidar.W, w.lidar.fov_up, w.lidar.fov_down, w.lidar.r_min, w.lidar.r_max)
+    a, c = _new_map(p, w, w.voxel_size, w.truncation, 0), _new_map(p, w, w.voxel_size, w.truncation, 0)
+    b = p.map_batch_create([a.h, c.h], p.MAP_BATCH_STREAMS)
+    bad = f.T.copy()
+    bad[0, 0] *= 1.01
+    pt, lb = _dev(f.points), _dev(f.labels)
+    with pytest.raises(p.MapError) as e:
+        p.map_batch_integrate(b, [a.h, c.h], [L, L], [pt, pt], [f.T, bad], labels=[lb, lb])
+    assert e.value.status == 4
+    p.map_batch_sync(b)
+    assert a.stats()["valid_points"] > 0 and a.stats()["total_blocks"] > 0
+    assert c.stats()["total_blocks"] == 0 and c.frame_count() == 0
+    p.map_batch_destroy(b)
+    a.close()
+    c.close()
+
+
 def test_autotuner_visits_every_configuration(batch_run):
     p = batch_run["p"]
     # 8 steps: the tuner is still timing (3 steps per configuration)
