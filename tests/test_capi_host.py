@@ -102,16 +102,35 @@ def test_config_defaults():
     assert ctypes.sizeof(cfg) == 104
 
 
+def _table_ii():
+    """The traversability parameters of Table II, from the golden fixture (SI units, radians)."""
+    import math
+    out = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "table_ii_traversability.txt")):
+        if line.strip() and not line.startswith("#"):
+            name, value, unit = line.split()
+            out[name] = math.radians(float(value)) if unit == "deg" else float(value)
+    return out
+
+
 def test_traversability_defaults_are_table_ii():
-    """Radius 0.25 m, height 0.6 m, steepness 20 deg, roughness 30 deg, every class allowed."""
+    """The library's and the oracle's defaults are Table II's (radius, height difference, steepness,
+    roughness), every class allowed."""
+    import inspect
     import math
     import paper_2412_00291_b300 as p
+    from oracle.traversability import traversability
+    g = _table_ii()
     t = p.TravParams()
     assert p._lib.map_trav_params_default(ctypes.byref(t)) == 0
-    assert t.radius == pytest.approx(0.25) and t.max_height_diff == pytest.approx(0.6)
-    assert t.max_steepness == pytest.approx(math.radians(20.0)) and t.max_roughness == pytest.approx(math.radians(30.0))
+    assert t.radius == pytest.approx(g["radius"]) and t.max_height_diff == pytest.approx(g["max_height_difference"])
+    assert t.max_steepness == pytest.approx(g["max_steepness"]) and t.max_roughness == pytest.approx(g["max_roughness"])
     assert t.class_mask == (1 << 64) - 1
     assert p._lib.map_trav_params_default(None) != 0
+    d = inspect.signature(traversability).parameters
+    assert d["r"].default == pytest.approx(g["radius"]) and d["t_hd"].default == pytest.approx(g["max_height_difference"])
+    assert math.radians(d["t_s_deg"].default) == pytest.approx(g["max_steepness"])
+    assert math.radians(d["t_r_deg"].default) == pytest.approx(g["max_roughness"])
 
 
 def test_struct_layouts_match_the_header(tmp_path):
