@@ -925,8 +925,10 @@ def run_align(args, rank, world, local_rank):
     w = synth.drive1km(seed=5 + 100 * rank)
     L = w.lidar
     lid = P.lidar_intrinsics(L.H, L.W, L.fov_up, L.fov_down, L.r_min, L.r_max)
-    m = P.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, storage=1, max_blocks=1 << 18,
-                       hash_capacity=1 << 20, mesh_vertex_capacity=32 << 20, mesh_triangle_capacity=64 << 20)
+    nb = args.max_blocks or (1 << 18)
+    mv = args.mesh_cap or (32 << 20)
+    m = P.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, storage=1, max_blocks=nb,
+                       hash_capacity=4 * nb, mesh_vertex_capacity=mv, mesh_triangle_capacity=2 * mv)
     scene = synth.make_scene(w)
     Ts = synth.trajectory(w, w.frames)
     t0 = time.perf_counter()

@@ -198,7 +198,10 @@ __global__ void k_pose_finish(const double *part, int nparts, double *pose_grad)
 constexpr int GN_ACC = 29;
 constexpr int GN_MAX_CTAS = 148 * 8;
 
-__global__ void __launch_bounds__(256) k_gn_terms(MapDev md, const float *__restrict__ pts, long long n,
+// Three CTAs per SM (at most 85 registers; 29 float-pair sums per thread then
+// spill ~340 bytes to L1): 113,664 resident threads, so a scan's ~92,000
+// valid points run in one wave instead of two at 128 registers.
+__global__ void __launch_bounds__(256, 3) k_gn_terms(MapDev md, const float *__restrict__ pts, long long n,
                                                   const double *__restrict__ T, double *acc) {
     __shared__ float s_c[16];
     __shared__ int s_k[3];
