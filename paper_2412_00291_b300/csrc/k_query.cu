@@ -206,6 +206,8 @@ __global__ void __launch_bounds__(256, 3) k_gn_terms(MapDev md, const float *__r
     __shared__ float s_c[16];
     __shared__ int s_k[3];
     __shared__ float s_h[8][GN_ACC], s_l[8][GN_ACC];
+    pdl_wait();      // the previous step's pose, and its reads of acc done
+    pdl_trigger();   // the step kernel may be scheduled now
     if (threadIdx.x == 0) {
         // R / nu and the split t / nu = k + f (k integer)
         for (int r = 0; r < 3; ++r) {
@@ -328,6 +330,8 @@ __device__ __forceinline__ void rodrigues_coeffs(double th2, double &A1, double 
 __global__ void __launch_bounds__(256) k_gn_step(double *T, const double *acc, int nparts) {
     __shared__ float s_ph[8][32], s_pl[8][32];
     __shared__ double s_a[32];
+    pdl_wait();      // the terms kernel's rows
+    pdl_trigger();   // the next iteration's terms kernel may be scheduled now
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const float2 *rows = reinterpret_cast<const float2 *>(acc);
     if (lane < GN_ACC) {
@@ -467,10 +471,11 @@ int gn_terms_grid(long long n) {
 }
 void launch_gn_terms(const MapDev &md, const float *pts, long long n, const double *T_dev, double *acc,
                      cudaStream_t s) {
-    k_gn_terms<<<gn_terms_grid(n), 256, 0, s>>>(md, pts, n, T_dev, acc);
+    // both Gauss-Newton kernels are launched as programmatic dependents of the one before
+    launch_pdl(k_gn_terms, dim3(gn_terms_grid(n)), dim3(256), 0, s, md, pts, n, T_dev, acc);
 }
 void launch_gn_step(double *T_dev, const double *acc, int nparts, cudaStream_t s) {
-    k_gn_step<<<1, 256, 0, s>>>(T_dev, acc, nparts);
+    launch_pdl(k_gn_step, dim3(1), dim3(256), 0, s, T_dev, acc, nparts);
 }
 
 }  // namespace stsdf
