@@ -66,7 +66,66 @@ def parse():
                     help="trav / camera workloads: build the map from this many scans (default: all 200)")
     ap.add_argument("--mesh-cap", type=int, default=0, help="mesh arena vertex capacity override")
     ap.add_argument("--no-fp16-report", action="store_true", help="skip the FP16-vs-FP32 comparison")
+    ap.add_argument("--dry", action="store_true",
+                    help="CPU only: run the multi-rank job logic (gloo ranks, each generating its replica's "
+                         "first scan, barrier, slowest-rank time) and print its line, with no mapping work")
     return ap.parse_args()
+
+
+def launch_local_ranks(args):
+    """--gpus N > 1 with no launcher around this process: start N local ranks of this script
+    (torch.distributed.run, one per GPU, rendezvous on 127.0.0.1) and return their exit status.
+    Without N visible GPUs (and not --dry) it refuses, so a run never reports fewer GPUs than asked."""
+    import socket
+    import subprocess
+    if not args.dry:
+        import torch
+        have = torch.cuda.device_count()
+        if have < args.gpus:
+            print(f"bench.py: --gpus {args.gpus} but only {have} CUDA device(s) visible", file=sys.stderr)
+            return 2
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__)] + sys.argv[1:]
+    env = dict(os.environ, OMP_NUM_THREADS=os.environ.get("OMP_NUM_THREADS", "1"))
+    return subprocess.call(cmd, env=env)
+
+
+def run_dry(args, rank, world):
+    """The job logic of a multi-rank run without a GPU: each rank generates the first scan of its
+    own replica (its own scene seed) as its 'step', the job time is the slowest rank's, and rank 0
+    prints the line (value null: no mapping work was done)."""
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        dist.barrier()
+    w = workload(args.workload, rank)
+    t0 = time.perf_counter()
+    f = next(iter(frames_for(w, 1)))
+    local_ms = 1e3 * (time.perf_counter() - t0)
+    slowest = rank_max(local_ms, dist, "cpu")
+    seeds = [w.seed]
+    if dist:
+        import torch
+        t = torch.tensor([w.seed], dtype=torch.int64)
+        gathered = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
+        dist.all_gather(gathered, t)
+        seeds = [int(g.item()) for g in gathered]
+        dist.barrier()
+    if rank == 0:
+        line = {"metric": "scan points fused/s", "value": None, "unit": "points/s", "n_gpus": world, "steps": 1,
+                "warmup": 0, "ms_per_step": slowest, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": None, "data": "synthetic", "dry": True,
+                "config": {"workload": w.name, "parallelism": f"replicas x{world}", "replica_seeds": seeds,
+                           "points_per_scan": int(len(f.points)),
+                           "note": "dry run: rank logic only (per-rank replica input, slowest-rank time); "
+                                   "no mapping work, no GPU"}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 def rank_max(x, dist, device):
@@ -1026,9 +1085,14 @@ def _axis_angle(a, theta):
 
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ and args.impl == "ours":
+        sys.exit(launch_local_ranks(args))
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.dry:
+        run_dry(args, rank, world)
+        return
     if world > 1 and args.impl == "ours":
         import torch
         import torch.distributed as dist

@@ -141,9 +141,24 @@ enum {
  * FP32 storage, capacities for a 64 x 2048 scanner at 0.1 m. */
 map_status map_config_default(map_config *cfg);
 
-/* Create an empty map; allocates and initialises all device storage (every
- * pool voxel starts at D = 0, W = 0 and the uniform class distribution). */
+/* Create an empty map (Sec. III-C.2: voxels of size nu = voxel_size at
+ * centres nu * v_i, stored in 8x8x8-voxel blocks found through a hash table;
+ * truncation tau bounds the fused distance and sets the allocated band;
+ * n_classes is the size of the per-voxel class distribution of Sec. III-C.3).
+ * Allocates and initialises all device storage (every pool voxel starts at
+ * D = 0, W = 0 and the uniform class distribution).  Voxel coordinates are
+ * limited to |v| < 2^19 - 16 on every axis (the range of the block and mesh
+ * vertex keys): 52 km at 0.1 m voxels. */
 map_status map_create(const map_config *cfg, map_t **out);
+
+/* The pose checks integrate_scan applies, without a map: MAP_ERR_BAD_POSE
+ * when T_world_lidar is not a rigid transform (rotation orthonormal to 1e-6,
+ * det +1, last row 0 0 0 1) or when a voxel the scan can reach (any point up
+ * to lidar->r_max, plus the band's truncation) lies outside the coordinate
+ * range above on some axis: (|t_k| + r_max + tau) / voxel_size + 1 must stay
+ * below 2^19 - 16.  MAP_ERR_ARG for a null pointer or inconsistent
+ * intrinsics.  Host only; touches no device. */
+map_status map_check_scan_pose(const map_config *cfg, const lidar_intrinsics *lidar, const double T_world_lidar[16]);
 map_status map_destroy(map_t *map);
 
 /* Fuse one posed scan (Sec. III-C): range image, band allocation, projective
@@ -183,7 +198,11 @@ int64_t map_frame_count(map_t *map);
 map_status map_frame_stats(map_t *map, int64_t frame, int64_t *out);
 
 /* Gather every block's current mesh segment into one indexed mesh (device
- * arrays owned by the map).  Synchronises `stream` to learn the sizes. */
+ * arrays owned by the map).  The segments come from marching cubes over the
+ * TSDF (Sec. III-C.3: the mesh of the zero level set, each vertex labelled
+ * with its most probable class), re-run for the touched blocks by every
+ * integrate_scan or for all blocks by map_remesh_all.  Synchronises `stream`
+ * to learn the sizes. */
 map_status extract_mesh(map_t *map, mesh_view *out, void *stream);
 
 /* extract_mesh for callers that cannot allocate device memory (a real-time
@@ -197,12 +216,16 @@ map_status extract_mesh(map_t *map, mesh_view *out, void *stream);
  * *n_vertices / *n_triangles receive the mesh size; when it exceeds either
  * capacity nothing is written and MAP_ERR_CAPACITY is returned (call again
  * with larger buffers).  Allocates nothing: its scan scratch is one static
- * device array of 2^19 block slots (8.4 MB, kept by every GPU that loads the
- * library until exit); maps whose pool exceeds 2^19 blocks get MAP_ERR_ARG.
- * The first call on a device looks up that array's device address, so make
- * it before any stream capture.  All calls share the array: calls whose work
- * overlaps on the GPU (different streams or threads) race.  Synchronises
- * `stream` to learn the mesh size. */
+ * device array of 2^19 block slots (8.4 MB); maps whose pool exceeds 2^19
+ * blocks get MAP_ERR_ARG.  The CUDA runtime places that array in a device's
+ * memory when it is first used there (lazy module loading): map_create does
+ * that on the map's device, so create the maps before reserving the rest of
+ * the GPU's memory or capturing a stream; the array then stays until the
+ * process exits.  The map and all five buffers must be device memory of the
+ * current device (MAP_ERR_ARG otherwise); the three vertex buffers each hold
+ * vertex_capacity entries and the two triangle buffers triangle_capacity.
+ * All calls share the array: calls whose work overlaps on the GPU (different
+ * streams or threads) race.  Synchronises `stream` to learn the mesh size. */
 map_status extract_mesh_noalloc(map_t *map, float *positions, uint8_t *colors, int64_t *vertex_keys,
                                 int32_t *triangles, int32_t *triangle_anchors, int64_t vertex_capacity,
                                 int64_t triangle_capacity, int64_t *n_vertices, int64_t *n_triangles, void *stream);
@@ -318,9 +341,11 @@ map_status map_quality(map_t *map, const float *gt_points_dev, const int32_t *gt
                        double trunc, quality_report *out, int64_t *confusion, void *stream);
 
 /* Trilinear interpolation of D at m world points (from the 8 voxel centres
- * nu * v around x).  sdf_dev[m] float32 (NaN when any of the 8 voxels is
- * unallocated or unobserved, W = 0), valid_dev[m] uint8 (1 = valid), may be
- * NULL.  Asynchronous. */
+ * nu * v around x).  Not in the paper: a query interface for using the map
+ * (differentiable reads, scan-to-map alignment).  sdf_dev[m] float32 (NaN
+ * when any of the 8 voxels is unallocated or unobserved, W = 0, and for
+ * non-finite points or points outside the map's coordinate range),
+ * valid_dev[m] uint8 (1 = valid), may be NULL.  Asynchronous. */
 map_status query_sdf(map_t *map, const float *xyz_dev, int64_t m, float *sdf_dev, uint8_t *valid_dev,
                      void *stream);
 

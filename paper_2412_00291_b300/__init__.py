@@ -68,6 +68,7 @@ BATCH_MAX = 48
 _SIGS = {
     "map_config_default": ([P], I32),
     "map_create": ([P, P], I32),
+    "map_check_scan_pose": ([P, P, P], I32),
     "map_destroy": ([P], I32),
     "integrate_scan": ([P, P, P, P, P, I64, P, P], I32),
     "integrate_scan_host": ([P, P, P, P, P, I64, P, P], I32),
@@ -183,6 +184,12 @@ def map_destroy(h):
     _check(_lib.map_destroy(h))
 
 
+def map_check_scan_pose(cfg: MapConfig, lidar: LidarIntrinsics, T_world_lidar):
+    """The pose checks integrate_scan applies, on the host without a map (MapError on failure)."""
+    _, Tp = _pose(T_world_lidar)
+    _check(_lib.map_check_scan_pose(ctypes.byref(cfg), ctypes.byref(lidar), Tp))
+
+
 def integrate_scan(h, lidar: LidarIntrinsics, points, T_world_lidar, labels=None, probs=None, stream=None):
     n = 0 if points is None else int(points.shape[0])
     _, Tp = _pose(T_world_lidar)
@@ -248,8 +255,22 @@ def extract_mesh_noalloc(h, positions, colors, vertex_keys, triangles, triangle_
     positions [V, 3] float32, colors [V, 4] uint8, vertex_keys [V] int64,
     triangles [T, 3] int32, triangle_anchors [T, 3] int32, with V and T the
     capacities.  Returns (n_vertices, n_triangles); raises MapError
-    (MAP_ERR_CAPACITY, sizes in the message) when the mesh does not fit.
+    (MAP_ERR_CAPACITY, sizes in the message) when the mesh does not fit, and
+    ValueError, before anything reaches the library, when the three vertex
+    buffers or the two triangle buffers differ in length, or a buffer is not
+    on the current CUDA device.
     """
+    vbufs = dict(positions=positions, colors=colors, vertex_keys=vertex_keys)
+    tbufs = dict(triangles=triangles, triangle_anchors=triangle_anchors)
+    for group in (vbufs, tbufs):
+        lens = {k: int(v.shape[0]) if v.dim() > 0 else -1 for k, v in group.items()}
+        if len(set(lens.values())) != 1:
+            raise ValueError(f"extract_mesh_noalloc: buffers of one kind must have equal lengths, got {lens}")
+    cur = torch.cuda.current_device() if torch.cuda.is_available() else None
+    for k, v in {**vbufs, **tbufs}.items():
+        if not v.is_cuda or v.device.index != cur:
+            raise ValueError(f"extract_mesh_noalloc: {k} must be on the current CUDA device (cuda:{cur}), "
+                             f"not {v.device}")
     nv, nt = ctypes.c_int64(), ctypes.c_int64()
     _check(_lib.extract_mesh_noalloc(h, _dev_ptr(positions, torch.float32, "positions", 3),
                                      _dev_ptr(colors, torch.uint8, "colors", 4),

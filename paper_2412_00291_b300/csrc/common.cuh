@@ -56,6 +56,11 @@ __host__ __device__ inline void arena_partition(unsigned long long live, unsigne
     end = p == ARENA_PARTS - 1 ? cap : live + free_ / ARENA_PARTS * (p + 1);
 }
 
+// Largest |voxel coordinate| a map can hold on any axis: mesh edge keys keep
+// 20 bits per voxel coordinate (biased by 2^19), block keys 21 bits per block
+// coordinate; the margin covers a cube's upper corner and a band's rounding.
+constexpr int MAX_VOXEL_COORD = (1 << 19) - 16;
+
 // Block key: 21 bits per block coordinate, biased by 2^20.
 __host__ __device__ inline uint64_t pack_block(int x, int y, int z) {
     return ((uint64_t)(uint32_t)(x + (1 << 20)) << 42) | ((uint64_t)(uint32_t)(y + (1 << 20)) << 21) |

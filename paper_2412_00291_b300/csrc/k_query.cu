@@ -22,7 +22,10 @@ __device__ __forceinline__ bool trilinear(const MapDev &md, const int k[3], cons
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float fl = floorf(g[a]);
-        v0[a] = (int)fl + k[a];
+        // outside the map's coordinate range (its keys would alias), or not a number: invalid
+        const long long vl = (long long)fl + k[a];
+        if (!(fabsf(g[a]) < 1e9f) || vl <= -MAX_VOXEL_COORD || vl >= MAX_VOXEL_COORD) return false;
+        v0[a] = (int)vl;
         f[a] = g[a] - fl;
     }
     // block coordinates of the lower / upper corner along each axis

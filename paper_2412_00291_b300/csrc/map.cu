@@ -124,6 +124,10 @@ struct map_t {
 
 static std::string g_err;
 
+namespace stsdf {
+void noalloc_prepare_device();   // noalloc.cu: loads its static scratch array on the current device
+}
+
 static map_status fail(map_t *m, map_status s, const std::string &msg) {
     if (m) m->err = msg;
     else g_err = msg;
@@ -411,6 +415,9 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
         delete m;
         return fail(nullptr, MAP_ERR_CUDA, msg);
     }
+    // extract_mesh_noalloc's static scratch array is placed on this device now,
+    // while allocating is allowed, so that the call itself allocates nothing
+    noalloc_prepare_device();
     *out = m;
     return MAP_OK;
 }
@@ -468,32 +475,78 @@ static map_status upload_pixel_rays(map_t *m, const lidar_intrinsics *L) {
     return MAP_OK;
 }
 
+// Pose checks of a scan (no map needed): a proper rigid transform, and every
+// voxel the scan can reach (points up to r_max plus the band's tau) inside
+// the coordinate range of block and mesh-vertex keys.  Returns MAP_OK or the
+// status, with the reason in *why.
+static map_status check_scan_pose(double nu, double tau, const lidar_intrinsics *L, const double *T,
+                                  const char **why) {
+    if (!L || !T) {
+        *why = "null intrinsics or pose";
+        return MAP_ERR_ARG;
+    }
+    if (!(L->fov_up > L->fov_down) || !(L->r_max > L->r_min) || !(L->r_min >= 0.0) || !std::isfinite(L->r_max)) {
+        *why = "need fov_up > fov_down and 0 <= r_min < r_max (finite)";
+        return MAP_ERR_ARG;
+    }
+    double R[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) R[3 * r + c] = T[4 * r + c];
+    for (int i = 0; i < 16; ++i)
+        if (!std::isfinite(T[i])) {
+            *why = "non-finite pose";
+            return MAP_ERR_BAD_POSE;
+        }
+    // R^T R = I, det R = +1, last row (0, 0, 0, 1)
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += R[3 * k + a] * R[3 * k + b];
+            if (std::fabs(s - (a == b ? 1.0 : 0.0)) > 1e-6) {
+                *why = "rotation not orthonormal";
+                return MAP_ERR_BAD_POSE;
+            }
+        }
+    const double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
+                       R[2] * (R[3] * R[7] - R[4] * R[6]);
+    if (det < 0.0 || T[12] != 0.0 || T[13] != 0.0 || T[14] != 0.0 || T[15] != 1.0) {
+        *why = "not a proper rigid transform";
+        return MAP_ERR_BAD_POSE;
+    }
+    for (int k = 0; k < 3; ++k)
+        if ((std::fabs(T[4 * k + 3]) + L->r_max + tau) / nu + 1.0 >= (double)MAX_VOXEL_COORD) {
+            *why = "the scan reaches voxels beyond the map's coordinate range (|t| + r_max + tau < "
+                   "(2^19 - 16) voxel_size on every axis)";
+            return MAP_ERR_BAD_POSE;
+        }
+    return MAP_OK;
+}
+
+extern "C" map_status map_check_scan_pose(const map_config *cfg, const lidar_intrinsics *L,
+                                          const double T_world_lidar[16]) {
+    if (!cfg || !(cfg->voxel_size > 0.0) || !(cfg->truncation > 0.0))
+        return fail(nullptr, MAP_ERR_ARG, "need a config with voxel_size > 0 and truncation > 0");
+    const char *why = nullptr;
+    const map_status st = check_scan_pose(cfg->voxel_size, cfg->truncation, L, T_world_lidar, &why);
+    return st == MAP_OK ? MAP_OK : fail(nullptr, st, why);
+}
+
 static map_status make_scan_const(map_t *m, const lidar_intrinsics *L, int64_t n, const double *T, int has_probs,
                                   ScanConst &sc) {
     if (!L || !T) return fail(m, MAP_ERR_ARG, "null intrinsics or pose");
     if (L->H < 2 || L->W < 1 || (long long)L->H * L->W > m->cfg.max_pixels)
         return fail(m, MAP_ERR_ARG, "H * W out of range (H >= 2, H * W <= max_pixels)");
     if (n < 0 || n > m->cfg.max_points) return fail(m, MAP_ERR_ARG, "n out of range (<= max_points)");
-    if (!(L->fov_up > L->fov_down) || !(L->r_max > L->r_min) || !(L->r_min >= 0.0))
-        return fail(m, MAP_ERR_ARG, "need fov_up > fov_down and 0 <= r_min < r_max");
+    {
+        const char *why = nullptr;
+        const map_status pst = check_scan_pose(m->cfg.voxel_size, m->cfg.truncation, L, T, &why);
+        if (pst != MAP_OK) return fail(m, pst, why);
+    }
     double R[9], t[3];
     for (int r = 0; r < 3; ++r) {
         for (int c = 0; c < 3; ++c) R[3 * r + c] = T[4 * r + c];
         t[r] = T[4 * r + 3];
     }
-    for (int i = 0; i < 16; ++i)
-        if (!std::isfinite(T[i])) return fail(m, MAP_ERR_BAD_POSE, "non-finite pose");
-    // R^T R = I, det R = +1, last row (0, 0, 0, 1)
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-            double s = 0.0;
-            for (int k = 0; k < 3; ++k) s += R[3 * k + a] * R[3 * k + b];
-            if (std::fabs(s - (a == b ? 1.0 : 0.0)) > 1e-6) return fail(m, MAP_ERR_BAD_POSE, "rotation not orthonormal");
-        }
-    const double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
-                       R[2] * (R[3] * R[7] - R[4] * R[6]);
-    if (det < 0.0 || T[12] != 0.0 || T[13] != 0.0 || T[14] != 0.0 || T[15] != 1.0)
-        return fail(m, MAP_ERR_BAD_POSE, "not a proper rigid transform");
     const double nu = m->cfg.voxel_size, tau = m->cfg.truncation;
     const double dtheta = (L->fov_up - L->fov_down) / (L->H - 1);
     std::memset(&sc, 0, sizeof(sc));
@@ -893,6 +946,10 @@ extern "C" map_status integrate_labels_camera(map_t *m, const camera_intrinsics 
             for (int k = 0; k < 3; ++k) q += T_world_cam[4 * k + a] * T_world_cam[4 * k + b];
             if (std::fabs(q - (a == b ? 1.0 : 0.0)) > 1e-6) return fail(m, MAP_ERR_BAD_POSE, "rotation not orthonormal");
         }
+    for (int k = 0; k < 3; ++k)
+        if ((std::fabs(T_world_cam[4 * k + 3]) + cam->r_max) / m->cfg.voxel_size + 1.0 >= (double)MAX_VOXEL_COORD)
+            return fail(m, MAP_ERR_BAD_POSE, "the camera reaches voxels beyond the map's coordinate range "
+                                             "(|t| + r_max < (2^19 - 16) voxel_size on every axis)");
     cudaStream_t s = (cudaStream_t)stream;
     const long long np = (long long)cam->width * cam->height;
     float *range = range_dev;

@@ -6,8 +6,12 @@
 // synchronise the whole device), or a framework that hands the library only
 // the memory it reserved up front.  This entry point runs the same gather
 // kernels, writes into buffers the caller passes in, and keeps its scratch in
-// one file-scope device array of fixed size (held by every GPU that loads the
-// library, until the process exits).
+// one file-scope device array of fixed size.  The array lives in this file's
+// device module, which the CUDA runtime loads on a device when the array is
+// first used there (lazy module loading, the default): map_create looks its
+// address up on the map's device, so the array (8.4 MB) is taken when a map
+// is created there and stays until the process exits; extract_mesh_noalloc
+// itself then allocates nothing.
 #include <cstdio>
 #include <mutex>
 
@@ -35,33 +39,47 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 long long *g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (host code cannot use the symbol itself as a device pointer).
-map_status scratch_address(map_t *m, long long **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        map_set_error(m, "extract_mesh_noalloc: no usable current device");
-        return MAP_ERR_CUDA;
-    }
+// Device address of the scratch array on device `dev` (the current device),
+// looked up once per device (host code cannot use the symbol itself as a
+// device pointer).  The first lookup on a device loads this file's module
+// there, which places the array in that device's memory.
+cudaError_t scratch_lookup(int dev, long long **out) {
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_addr[dev]) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_extract_scratch);
-        if (e != cudaSuccess || !p) {
-            char buf[160];
-            std::snprintf(buf, sizeof buf, "extract_mesh_noalloc: cudaGetSymbolAddress failed: %s",
-                          cudaGetErrorString(e));
-            map_set_error(m, buf);
-            return MAP_ERR_CUDA;
-        }
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_extract_scratch);
+        if (e != cudaSuccess) return e;
+        if (!p) return cudaErrorInvalidSymbol;
         g_scratch_addr[dev] = (long long *)p;
     }
     *out = g_scratch_addr[dev];
-    return MAP_OK;
+    return cudaSuccess;
+}
+
+// Device holding `p` (device or managed memory), or -1 for host memory or an
+// unknown pointer.
+int owner_device(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the sticky-free error of a failed query
+        return -1;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return -1;
+    return a.device;
 }
 
 }  // namespace
+
+namespace stsdf {
+// Called by map_create with the map's device current: loads the scratch array
+// there ahead of any extract_mesh_noalloc call (errors are left to that call).
+void noalloc_prepare_device() {
+    int dev = -1;
+    long long *p = nullptr;
+    if (cudaGetDevice(&dev) == cudaSuccess && scratch_lookup(dev, &p) != cudaSuccess) cudaGetLastError();
+}
+}  // namespace stsdf
 
 extern "C" map_status extract_mesh_noalloc(map_t *map, float *positions, uint8_t *colors, int64_t *vertex_keys,
                                            int32_t *triangles, int32_t *triangle_anchors, int64_t vertex_capacity,
@@ -82,9 +100,33 @@ extern "C" map_status extract_mesh_noalloc(map_t *map, float *positions, uint8_t
         map_set_error(map, buf);
         return MAP_ERR_ARG;
     }
+    // the map, the five buffers and the scratch array must all be on the current device
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        map_set_error(map, "extract_mesh_noalloc: no usable current device");
+        return MAP_ERR_CUDA;
+    }
+    if (owner_device(md.keys) != dev) {
+        map_set_error(map, "extract_mesh_noalloc: the map was created on another device than the current one");
+        return MAP_ERR_ARG;
+    }
+    const void *bufs[5] = {positions, colors, vertex_keys, triangles, triangle_anchors};
+    const long long caps[5] = {vertex_capacity, vertex_capacity, vertex_capacity, triangle_capacity,
+                               triangle_capacity};
+    for (int i = 0; i < 5; ++i)
+        if (caps[i] > 0 && owner_device(bufs[i]) != dev) {
+            map_set_error(map, "extract_mesh_noalloc: an output buffer is not device memory of the current device");
+            return MAP_ERR_ARG;
+        }
     long long *scr = nullptr;
-    map_status st = scratch_address(map, &scr);
-    if (st != MAP_OK) return st;
+    cudaError_t le = scratch_lookup(dev, &scr);
+    if (le != cudaSuccess) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "extract_mesh_noalloc: cudaGetSymbolAddress failed: %s",
+                      cudaGetErrorString(le));
+        map_set_error(map, buf);
+        return MAP_ERR_CUDA;
+    }
     // Every word the kernels read is written earlier in the same call (offsets
     // of slots below the pool count, all chunk sums, both totals), so nothing
     // needs clearing.

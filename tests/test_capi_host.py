@@ -188,3 +188,52 @@ def test_projection_polynomials_meet_their_bounds():
     c = np.linspace(0.0, 0.5, 400001).astype(np.float32)
     b = c.astype(np.float64) * _horner_fma32(_poly_coeffs("asin_q"), (c * c).astype(np.float32))
     assert np.abs(b - np.arcsin(c.astype(np.float64))).max() < 2e-7
+
+
+def test_extract_mesh_noalloc_wrapper_rejects_bad_buffers_before_any_call():
+    """The Python binding checks buffer lengths and devices before calling the library: a
+    mismatch raises ValueError (CPU tensors here, so nothing could be launched anyway)."""
+    import torch
+
+    import paper_2412_00291_b300 as p
+    ok = dict(positions=torch.zeros((8, 3)), colors=torch.zeros((8, 4), dtype=torch.uint8),
+              vertex_keys=torch.zeros(8, dtype=torch.int64), triangles=torch.zeros((5, 3), dtype=torch.int32),
+              triangle_anchors=torch.zeros((5, 3), dtype=torch.int32))
+    for name, short in (("colors", torch.zeros((7, 4), dtype=torch.uint8)),
+                        ("vertex_keys", torch.zeros(4, dtype=torch.int64)),
+                        ("triangle_anchors", torch.zeros((4, 3), dtype=torch.int32))):
+        bad = dict(ok, **{name: short})
+        with pytest.raises(ValueError, match="equal lengths"):
+            p.extract_mesh_noalloc(None, **bad)
+    with pytest.raises(ValueError, match="current CUDA device"):
+        p.extract_mesh_noalloc(None, **ok)
+
+
+def test_scan_pose_range_check_through_the_c_abi():
+    """Voxel coordinates must stay within |v| < 2^19 - 16 (block and mesh-vertex keys): the
+    host-side pose check refuses a scan that could reach beyond, before any map is touched."""
+    import paper_2412_00291_b300 as p
+    cfg = p.map_config_default(voxel_size=0.1, truncation=0.3, n_classes=20)
+    lid = p.lidar_intrinsics(64, 2048, np.radians(22.5), np.radians(-22.5), 0.5, 100.0)
+    lim = (2 ** 19 - 16) * 0.1           # metres of the coordinate range at 0.1 m voxels
+    T = np.eye(4)
+    p.map_check_scan_pose(cfg, lid, T)
+    for axis in range(3):
+        for sign in (1.0, -1.0):
+            T = np.eye(4)
+            T[axis, 3] = sign * (lim - 100.0 - 0.3 - 0.2)      # just inside
+            p.map_check_scan_pose(cfg, lid, T)
+            T[axis, 3] = sign * (lim - 100.0 - 0.3 + 0.2)      # just beyond
+            with pytest.raises(p.MapError) as e:
+                p.map_check_scan_pose(cfg, lid, T)
+            assert e.value.status == 4 and "coordinate range" in str(e.value)
+    # the other pose checks come through the same call
+    T = np.eye(4)
+    T[0, 0] = 1.01
+    with pytest.raises(p.MapError) as e:
+        p.map_check_scan_pose(cfg, lid, T)
+    assert e.value.status == 4
+    T = np.eye(4)
+    T[1, 3] = np.nan
+    with pytest.raises(p.MapError):
+        p.map_check_scan_pose(cfg, lid, T)

@@ -342,6 +342,40 @@ def test_errors_bad_pose_args_capacity():
     assert s["total_blocks"] == 64
 
 
+def test_far_pose_refused_and_map_unchanged():
+    """A scan whose reach leaves the map's coordinate range (|voxel| < 2^19 - 16) is refused with
+    MAP_ERR_BAD_POSE before any launch, and the map, its frame count and its queries stay as they
+    were; a query point beyond the range is invalid (its block key would alias)."""
+    p = _lib()
+    w = synth.line16()
+    f = next(iter(synth.sequence(w, 1)))
+    L = _lidar(p, w.lidar)
+    gm = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=8192, hash_capacity=1 << 15,
+                        max_points=32768, max_pixels=32768, mesh_vertex_capacity=1 << 20,
+                        mesh_triangle_capacity=1 << 21)
+    pts, lab = _dev(f.points), _dev(f.labels)
+    gm.integrate(L, pts, f.T, labels=lab)
+    before = _sorted(gm.blocks())
+    n0 = gm.frame_count()
+    lim = (2 ** 19 - 16) * w.voxel_size
+    for axis in range(3):
+        T = f.T.copy()
+        T[axis, 3] = lim - w.lidar.r_max - w.truncation + 0.5 * w.voxel_size
+        with pytest.raises(p.MapError) as e:
+            gm.integrate(L, pts, T, labels=lab)
+        assert e.value.status == 4 and "coordinate range" in str(e.value)
+    gm.sync()
+    assert gm.frame_count() == n0
+    np.testing.assert_array_equal(_sorted(gm.blocks()), before)
+    # a query at a voxel aliasing onto an allocated block (block x + 2^21) is invalid
+    b = before[len(before) // 2].astype(np.float64)
+    x = (8 * b + 3.25) * w.voxel_size
+    xa = x.copy()
+    xa[0] += 8 * (2 ** 21) * w.voxel_size
+    sdf, valid = gm.query(torch.tensor(np.stack([x, xa]), dtype=torch.float32, device="cuda"))
+    assert not bool(valid[1]) and torch.isnan(sdf[1])
+
+
 @pytest.mark.slow
 def test_loop64_full_size_sampled():
     """The 200-scan 64 x 2048 workload at full size, in the benchmark's launch configuration.

@@ -52,3 +52,19 @@ def test_single_rank_is_identity():
     import bench
     assert bench.rank_max(3.5, None, "cpu") == 3.5
     assert bench.job_throughput(100, 2, 1, 1.0) == pytest.approx(2e5)
+
+
+def test_bench_spawns_its_own_ranks_when_asked_for_two_gpus():
+    """`bench.py --gpus 2` with no launcher around it starts two local ranks itself (here in its
+    CPU-only --dry form over gloo) and prints one line, from rank 0, with n_gpus = 2 and one
+    replica seed per rank."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2", "--dry", "--workload",
+                        "line16"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    line = lines[0]
+    assert line["n_gpus"] == 2 and line["dry"] is True and line["value"] is None
+    assert len(set(line["config"]["replica_seeds"])) == 2

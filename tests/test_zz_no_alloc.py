@@ -7,9 +7,13 @@ library offers extract_mesh_noalloc, which writes into the caller's buffers
 and keeps its scratch in one static device array shared by all calls.  This
 test checks, through the C ABI, that it returns exactly what extract_mesh
 returns, on two calls in a row with the map changing in between (the shared
-scratch still holds the previous call's contents), and that a too-small
-buffer is refused with the needed sizes.
+scratch still holds the previous call's contents), that the second call
+leaves the device's free memory and torch's allocator untouched, that a
+too-small buffer is refused with the needed sizes, and that a pool larger
+than the static scratch, or a host buffer, is refused before any launch.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -47,7 +51,14 @@ def test_extract_mesh_noalloc_matches_extract_mesh():
     for call in range(2):
         fuse(frames[2 + call])
         ref = P.extract_mesh(gm.h)
+        torch.cuda.synchronize()
+        free0, alloc0, resv0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated(), \
+            torch.cuda.memory_reserved()
         nv, nt = P.extract_mesh_noalloc(gm.h, **bufs)
+        torch.cuda.synchronize()
+        if call == 1:      # nothing allocated by the call itself (device or torch caching allocator)
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_allocated() == alloc0 and torch.cuda.memory_reserved() == resv0
         assert nv == ref["positions"].shape[0] and nt == ref["triangles"].shape[0]
         assert nt > 1000
         for name in ("positions", "colors", "vertex_keys", "triangles", "triangle_anchors"):
@@ -60,4 +71,30 @@ def test_extract_mesh_noalloc_matches_extract_mesh():
         P.extract_mesh_noalloc(gm.h, **small)
     assert e.value.status == 3
     assert f"{sizes[1][0]} vertices" in str(e.value) and f"{sizes[1][1]} triangles" in str(e.value)
+    gm.close()
+
+
+def test_extract_mesh_noalloc_refusals():
+    """A pool beyond the scratch's 2^19 blocks and host buffers are refused with MAP_ERR_ARG
+    before any kernel runs (the output counts stay untouched)."""
+    import paper_2412_00291_b300 as P
+    big = P.SemanticTSDF(0.2, 0.6, 2, max_blocks=(1 << 19) + 1, hash_capacity=1 << 21, max_points=1024,
+                         max_pixels=1024, mesh_vertex_capacity=1024, mesh_triangle_capacity=1024, storage=1)
+    bufs = _buffers(64, 64)
+    with pytest.raises(P.MapError) as e:
+        P.extract_mesh_noalloc(big.h, **bufs)
+    assert e.value.status == 1 and "524288" in str(e.value)
+    big.close()
+    w = synth.line16()
+    gm = P.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=4096, hash_capacity=1 << 13,
+                        max_points=16384, max_pixels=16384, mesh_vertex_capacity=1 << 16,
+                        mesh_triangle_capacity=1 << 17)
+    host = np.zeros(64 * 4, np.float32)
+    nv, nt = ctypes.c_int64(-7), ctypes.c_int64(-7)
+    d = {k: ctypes.c_void_p(v.data_ptr()) for k, v in bufs.items()}
+    st = P._lib.extract_mesh_noalloc(gm.h, ctypes.c_void_p(host.ctypes.data), d["colors"], d["vertex_keys"],
+                                     d["triangles"], d["triangle_anchors"], 64, 64, ctypes.byref(nv),
+                                     ctypes.byref(nt), P._stream(None))
+    assert st == 1 and nv.value == -7 and nt.value == -7
+    assert "not device memory" in P._lib.map_last_error(gm.h).decode()
     gm.close()
