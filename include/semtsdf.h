@@ -230,6 +230,43 @@ map_status extract_mesh_noalloc(map_t *map, float *positions, uint8_t *colors, i
                                 int32_t *triangles, int32_t *triangle_anchors, int64_t vertex_capacity,
                                 int64_t triangle_capacity, int64_t *n_vertices, int64_t *n_triangles, void *stream);
 
+/* ---- parity instrumentation (tests; not on the product path) ----
+ * These two calls make a map record the integer decisions its single-
+ * precision kernels take in each scan, so that a test can check them one by
+ * one against an FP64 reference that takes the same decisions in double
+ * precision and follows the recorded choice only where its own computation
+ * lies within an ambiguity band (a projection within 1e-3 pixel of a pixel
+ * boundary, a range within 2^-20 of r_min / r_max or of the pixel's nearest
+ * range, a block whose distance from the band segment is within rounding of
+ * zero, psi within rounding of +-tau).  The paper has no counterpart: this is
+ * verification machinery for Sec. III-C.1's range image, Sec. III-C.2's
+ * block allocation and voxel projection, and the class-update gate.
+ *
+ * map_set_decision_record(map, 1) allocates the record buffers (max_points
+ * ints and max_blocks * 512 ints; max_pixels must be <= 2^23) and makes every
+ * following integrate_scan / integrate_scan_host write:
+ *   per point i: the pixel v * W + u it was put in, -1 when valid (finite,
+ *     r_min <= r <= r_max) without a beam row, -2 when invalid;
+ *   per voxel of every touched block: (pixel + 1) | updated << 28 |
+ *     class-updated << 29 (pixel + 1 = 0: the voxel has no pixel).
+ * The scans compute the same values as without the record (the kernels only
+ * add the stores).  map_set_decision_record(map, 0) frees the buffers.
+ * Both synchronise the device.  map_batch_integrate records nothing.
+ *
+ * map_read_decision_record reads the record of the LAST scan (MAP_ERR_STATE
+ * when the last call on the map was not a recorded scan, or another call
+ * has used the map's frame buffers since): point_pix[n_points] (n_points =
+ * the scan's n), winner[n_pixels] (n_pixels = H * W: the range-image
+ * winner of each pixel, (float bits of its range << 32) | point index, or
+ * ~0 for none), the touched blocks' coordinates touched[touched_cap][3]
+ * with their count in *n_touched, and voxel_rec[touched_cap][512] in the
+ * same block order.  Any output may be NULL.  Synchronises the device;
+ * allocates two temporary device buffers. */
+map_status map_set_decision_record(map_t *map, int32_t enable);
+map_status map_read_decision_record(map_t *map, int32_t *point_pix, int64_t n_points, uint64_t *winner,
+                                    int64_t n_pixels, int32_t *touched, int64_t touched_cap, int64_t *n_touched,
+                                    int32_t *voxel_rec);
+
 /* Re-mesh every allocated block from scratch, replacing all mesh segments
  * (the arena is emptied first, nothing is compacted).  Asynchronous.  With
  * per-frame meshing switched off this is the paper's regime: a global

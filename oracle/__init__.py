@@ -40,12 +40,14 @@ def _load():
         "orc_free": ([P], None),
         "orc_set_bands": ([P, D, D], None),
         "orc_set_track": ([P, P, I64], None),
-        "orc_integrate": ([P, P, P, P, P, I64, P, I], I),
+        "orc_integrate": ([P, P, P, P, P, I64, P, I, P, P, P, I64, P], I),
+        "orc_check": ([P, P], None),
+        "orc_block_clearance": ([P, P, P], D),
         "orc_stats": ([P, P], None),
         "orc_num_alloc": ([P], I64),
         "orc_get_alloc": ([P, P, I64], I64),
         "orc_get_touched": ([P, P, I64], I64),
-        "orc_read_block": ([P, P, P, P, P, P, P, P], I),
+        "orc_read_block": ([P, P, P, P, P, P, P, P, P, P], I),
         "orc_write_block": ([P, P, P, P, P], I),
         "orc_mesh_build": ([P, I, P, I64, P], P),
         "orc_mesh_fetch": ([P, P, P, P, P, P, P, P, P], None),
@@ -56,8 +58,8 @@ def _load():
         "orc_align": ([P, P, I64, P, I, P], I),
         "orc_se3_exp": ([P, P, P], None),
         "orc_palette": ([I, P], None),
-        "orc_point_blocks": ([P, P, P, P, I64], I64),
-        "orc_point_band": ([P, P, P, P, P], None),
+        "orc_point_blocks": ([P, P, P, P, P, I64], I64),
+        "orc_point_band": ([P, P, P, P, P], D),
         "orc_set_distance_mode": ([P, I], None),
         "orc_get_normals": ([P, P, P, I64], I64),
         "orc_read_grad": ([P, P, P], I),
@@ -76,7 +78,21 @@ def _p(a):
 
 
 STAT_NAMES = ("valid_points", "pixel_points", "ambiguous_points", "touched_blocks", "new_blocks",
-              "voxels_updated", "voxels_semantic", "voxels_seen", "taint_events")
+              "voxels_updated", "voxels_semantic", "voxels_seen", "taint_events", "sure_blocks",
+              "ambiguous_blocks")
+
+# Candidate-acceptance counts of a scan integrated with a decision record
+# (orc_check, CK_* order): for each decision kind, how many were checked, how
+# many fell in the FP64 ambiguity band (the recorded choice was accepted as
+# one of the FP64 candidates and used), and how many were rejected.
+CHECK_NAMES = ("points", "points_ambiguous", "points_rejected",
+               "pixels", "winners_ambiguous", "winners_rejected",
+               "blocks_sure", "blocks_ambiguous", "blocks_ambiguous_taken", "blocks_missing", "blocks_extra",
+               "voxels", "voxel_pixels_ambiguous", "voxel_pixels_rejected", "voxel_updates_ambiguous",
+               "voxel_updates_rejected", "voxel_classes_ambiguous", "voxel_classes_rejected",
+               "voxels_without_record")
+REJECTIONS = ("points_rejected", "winners_rejected", "blocks_missing", "blocks_extra", "voxel_pixels_rejected",
+              "voxel_updates_rejected", "voxel_classes_rejected", "voxels_without_record")
 
 
 class OracleMap:
@@ -106,20 +122,49 @@ class OracleMap:
         c = np.ascontiguousarray(coords, np.int32).reshape(-1, 3)
         self.L.orc_set_track(self.h, _p(c), len(c))
 
-    def integrate(self, lidar, points, T, labels=None, probs=None, nthreads=0):
+    def integrate(self, lidar, points, T, labels=None, probs=None, nthreads=0, decisions=None):
+        """Fuse one scan.  `decisions` (optional): a single-precision implementation's choices for
+        this scan, a dict with point_pix [n] int32, winner [H*W] uint64, touched [k, 3] int32 and
+        vox [k, 512] int32 (see orc_integrate); ambiguous FP64 decisions then follow them when they
+        are FP64 candidates, and check() reports the counts."""
         lid = np.array([lidar.H, lidar.W, lidar.fov_up, lidar.fov_down, lidar.r_min, lidar.r_max], np.float64)
         pts = np.ascontiguousarray(points, np.float32)
         lab = None if labels is None else np.ascontiguousarray(labels, np.int32)
         pr = None if probs is None else np.ascontiguousarray(probs, np.float32)
         T = np.ascontiguousarray(T, np.float64)
-        rc = self.L.orc_integrate(self.h, _p(lid), _p(pts), _p(lab), _p(pr), len(pts), _p(T), nthreads)
+        d = decisions or {}
+        pp = None if d.get("point_pix") is None else np.ascontiguousarray(d["point_pix"], np.int32)
+        wi = None if d.get("winner") is None else np.ascontiguousarray(d["winner"], np.uint64)
+        tb = None if d.get("touched") is None else np.ascontiguousarray(d["touched"], np.int32).reshape(-1, 3)
+        vx = None if d.get("vox") is None else np.ascontiguousarray(d["vox"], np.int32)
+        if pp is not None:
+            assert len(pp) == len(pts)
+        if wi is not None:
+            assert len(wi) == lidar.H * lidar.W
+        if vx is not None:
+            assert tb is not None and vx.shape == (len(tb), BV)
+        if tb is not None and len(tb) == 0:          # an empty recorded set is still a record
+            tb = np.zeros((1, 3), np.int32)[:0]
+            tb_p = ctypes.c_void_p(np.zeros((1, 3), np.int32).ctypes.data)
+            self._keep = tb_p
+        else:
+            tb_p = _p(tb)
+        rc = self.L.orc_integrate(self.h, _p(lid), _p(pts), _p(lab), _p(pr), len(pts), _p(T), nthreads,
+                                  _p(pp), _p(wi), tb_p, 0 if tb is None else len(tb),
+                                  _p(vx) if vx is not None and vx.size else None)
         assert rc == 0
         return self.stats()
 
     def stats(self):
-        out = np.zeros(9, np.int64)
+        out = np.zeros(len(STAT_NAMES), np.int64)
         self.L.orc_stats(self.h, _p(out))
         return dict(zip(STAT_NAMES, out.tolist()))
+
+    def check(self):
+        """Candidate-acceptance counts of the last scan (CHECK_NAMES)."""
+        out = np.zeros(24, np.int64)
+        self.L.orc_check(self.h, _p(out))
+        return dict(zip(CHECK_NAMES, out[:len(CHECK_NAMES)].tolist()))
 
     def alloc_blocks(self):
         n = self.L.orc_num_alloc(self.h)
@@ -141,10 +186,13 @@ class OracleMap:
         taint = np.zeros(BV, np.uint8)
         lab = np.zeros(BV, np.int32)
         gap = np.zeros(BV)
-        rc = self.L.orc_read_block(self.h, _p(c), _p(D), _p(W), _p(lp), _p(taint), _p(lab), _p(gap))
+        nupd = np.zeros(BV, np.int32)
+        nsem = np.zeros(BV, np.int32)
+        rc = self.L.orc_read_block(self.h, _p(c), _p(D), _p(W), _p(lp), _p(taint), _p(lab), _p(gap), _p(nupd),
+                                   _p(nsem))
         if rc != 0:
             return None
-        return dict(D=D, W=W, logP=lp, taint=taint, label=lab, gap=gap)
+        return dict(D=D, W=W, logP=lp, taint=taint, label=lab, gap=gap, n_upd=nupd, n_sem=nsem)
 
     def read_grad(self, coord):
         """Gradient g_i of one block's voxels, [3][512] (non-projective mode), or None."""
@@ -211,19 +259,23 @@ class OracleMap:
         return out
 
     def point_blocks(self, pt, T):
+        """Band blocks of one point: (sure [k, 3], ambiguous [j, 3]) by the FP64 clearance test."""
         p = np.ascontiguousarray(pt, np.float32)
         T = np.ascontiguousarray(T, np.float64)
-        out = np.zeros((64, 3), np.int32)
-        n = self.L.orc_point_blocks(self.h, _p(p), _p(T), _p(out), 64)
-        return out[:n]
+        out = np.zeros((256, 3), np.int32)
+        cls = np.zeros(256, np.int8)
+        n = self.L.orc_point_blocks(self.h, _p(p), _p(T), _p(out), _p(cls), 256)
+        assert n <= 256
+        return out[:n][cls[:n] == 1], out[:n][cls[:n] == 0]
 
     def point_band(self, pt, T):
+        """FP64 band endpoints (voxel units + 1/2) of one point and the ambiguity margin."""
         p = np.ascontiguousarray(pt, np.float32)
         T = np.ascontiguousarray(T, np.float64)
-        e0 = np.zeros(3, np.float32)
-        e1 = np.zeros(3, np.float32)
-        self.L.orc_point_band(self.h, _p(p), _p(T), _p(e0), _p(e1))
-        return e0, e1
+        e0 = np.zeros(3)
+        e1 = np.zeros(3)
+        margin = self.L.orc_point_band(self.h, _p(p), _p(T), _p(e0), _p(e1))
+        return e0, e1, float(margin)
 
 
 def nonprojective_distance(psi, u, g, N=None) -> float:
@@ -247,6 +299,14 @@ def se3_exp(xi):
     T[:3, :3] = R.reshape(3, 3)
     T[:3, 3] = t
     return T
+
+
+def block_clearance(e0, e1, b) -> float:
+    """Clearance (voxel units) of block b from the segment e0 -> e1 (positive: runs through it)."""
+    a = np.ascontiguousarray(e0, np.float64)
+    c = np.ascontiguousarray(e1, np.float64)
+    bb = np.ascontiguousarray(b, np.int32)
+    return float(_load().orc_block_clearance(_p(a), _p(c), _p(bb)))
 
 
 def palette(C):

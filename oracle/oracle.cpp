@@ -49,15 +49,19 @@
  * reaches logp_floor exactly while the others keep their product's closed
  * form).
  *
- * Precision: every value is FP64.  Two integer decisions are taken in the
- * precision the GPU takes them in, as both sides of a parity check must:
- * the per-point range used for validity and for the nearest-point winner
- * (FP32 norm), and the block-allocation band endpoints (FP32 recipe below).
- * Pixel choices are FP64; a voxel projection within delta_px of a pixel
- * boundary, or a psi within eps_psi of +-tau, marks the voxel "tainted"
- * (the FP32 GPU may legitimately decide the other way), sticky for the
- * rest of the run, so that parity tests can compare untainted voxels
- * strictly.
+ * Precision: every value and every decision is FP64: point validity and
+ * pixel, the nearest-point winner of each pixel, the blocks met by each
+ * point's band (an exact segment-box clearance test, band_blocks below), each
+ * voxel's pixel and its update and class-update gates.  Each decision also
+ * has an ambiguity band in which a single-precision implementation may
+ * legitimately decide otherwise: a projection within delta_px of a pixel
+ * boundary, a range within 2^-20 (relative) of r_min, r_max or of the
+ * pixel's nearest range, a block whose clearance is within band_margin of
+ * zero, psi within eps_psi of +-tau.  Given such an implementation's
+ * recorded choices (struct Decisions), the oracle follows them inside those
+ * bands when they are FP64 candidates, and counts every choice outside them
+ * that differs from its own (orc_check); without a record it takes its own
+ * choices and marks ambiguous voxels "tainted" (sticky).
  */
 #include <algorithm>
 #include <cmath>
@@ -118,6 +122,7 @@ inline int64_t edge_key(int64_t x, int64_t y, int64_t z, int axis) {
 struct Block {
     std::vector<double> D, W, logP;  // D[512], W[512], logP[C][512] (class-major)
     std::vector<uint8_t> taint;      // bit 0: distance/weight, bit 1: semantics
+    std::vector<int32_t> nupd, nsem; // per voxel: distance updates and class updates so far
     std::vector<double> G;           // non-projective mode: gradient g_i, G[k][512] (k = x, y, z)
 };
 
@@ -132,6 +137,35 @@ struct Stats {
     int64_t touched_blocks = 0, new_blocks = 0;
     int64_t voxels_updated = 0, voxels_semantic = 0, voxels_seen = 0;
     int64_t taint_events = 0;
+    int64_t sure_blocks = 0, ambiguous_blocks = 0;   // band blocks: sure, and within the margin only
+};
+
+/*
+ * The choices a single-precision implementation made for one scan, offered
+ * for candidate acceptance.  Where the FP64 computation finds a decision
+ * within its ambiguity band (a point or voxel projecting within delta_px of
+ * a pixel boundary, a range within 2^-20 of r_min, r_max or of the pixel's
+ * nearest range, a block within the band margin, a psi within eps_psi of
+ * +-tau), the recorded choice is accepted if it is one of the FP64
+ * candidates and then used, so that both maps stay in step; everywhere else
+ * the recorded choice must equal the FP64 one.  Either way every mismatch
+ * is counted (Check) and the FP64 choice is kept.
+ */
+struct Decisions {
+    const int32_t *point_pix = nullptr;   // [n] pixel of each point, -1 valid without a pixel, -2 invalid
+    const uint64_t *winner = nullptr;     // [H*W] (range bits << 32) | winning point, ~0 for none
+    const int32_t *touched = nullptr;     // [n_touched][3] blocks of U_k
+    int64_t n_touched = 0;
+    const int32_t *vox = nullptr;         // [n_touched][512] per voxel: pixel + 1 (0: none) | upd << 28 | sem << 29
+};
+
+enum {
+    CK_POINTS = 0, CK_POINTS_AMB, CK_POINTS_BAD,
+    CK_PIXELS, CK_WINNERS_AMB, CK_WINNERS_BAD,
+    CK_BLOCKS_SURE, CK_BLOCKS_AMB, CK_BLOCKS_AMB_TAKEN, CK_BLOCKS_MISSING, CK_BLOCKS_EXTRA,
+    CK_VOXELS, CK_VOX_PIX_AMB, CK_VOX_PIX_BAD, CK_VOX_UPD_AMB, CK_VOX_UPD_BAD, CK_VOX_SEM_AMB, CK_VOX_SEM_BAD,
+    CK_VOX_NO_RECORD,
+    CK_COUNT = 24
 };
 
 struct Map {
@@ -150,6 +184,7 @@ struct Map {
     std::vector<double> normals;            // non-projective mode: last normal image, world frame [H*W][3]
     std::vector<uint8_t> normal_flag;       // bit 0: normal valid, bit 1: orientation nearly ambiguous
     Stats st;
+    int64_t check[CK_COUNT] = {};           // candidate-acceptance counts of the last scan
     int64_t frame = 0;
 };
 
@@ -160,6 +195,8 @@ Block new_block(int C, int dist_mode) {
     // uniform prior over the classes for every new voxel (Sec. III-C.3)
     b.logP.assign((size_t)C * BV, -std::log((double)C));
     b.taint.assign(BV, 0);
+    b.nupd.assign(BV, 0);
+    b.nsem.assign(BV, 0);
     if (dist_mode == 1) b.G.assign(3 * BV, 0.0);   // no gradient until a normal is seen
     return b;
 }
@@ -167,102 +204,102 @@ Block new_block(int C, int dist_mode) {
 inline int vidx(int lx, int ly, int lz) { return lx + BS * (ly + BS * lz); }
 
 // ---------------------------------------------------------------------------
-// FP32 decisions shared in precision (not in code) with the GPU path
+// band allocation in FP64 (Sec. III-C.2: the voxel blocks around each
+// measurement are found along its ray and inserted in the block hash)
 // ---------------------------------------------------------------------------
-// Range of a LiDAR-frame point as the GPU computes it: ((x*x + y*y) + z*z),
-// then a correctly rounded square root, all in IEEE single precision.
-inline float range_f32(float x, float y, float z) {
-    float s = x * x;
-    s = s + y * y;
-    s = s + z * z;
-    return std::sqrt(s);
-}
-
-struct BandConst {
-    float Rv[9];   // R / nu, row-major, rounded once from FP64
-    float tv[3];   // t / nu + 1/2, rounded once from FP64
-    float tau;
-};
-
 /*
- * Band endpoints of one point in "voxel units plus one half" (so voxel v
- * occupies [v, v + 1) and block b occupies [8 b, 8 b + 8) on every axis):
- *   q = tau / l, f0 = max(0, 1 - q), f1 = 1 + q,
- *   s = (Rv[k0] x0 + Rv[k1] x1) + Rv[k2] x2,   e0 = tv + s f0,  e1 = tv + s f1.
- * Every operation is one IEEE single-precision operation, in this order.
+ * Band endpoints of one point x (LiDAR frame) in voxel units plus one half,
+ * so that voxel v occupies [v, v + 1) and block b occupies [8 b, 8 b + 8) on
+ * every axis:  s = R x (the ray from the sensor to the world point
+ * p = s + t), l = |x|, q = tau / l,
+ *   e0 = (t + max(0, 1 - q) s) / nu + 1/2,   e1 = (t + (1 + q) s) / nu + 1/2,
+ * i.e. the symmetric band [p - tau d, p + tau d], d = s / l, started at the
+ * sensor when l < tau.
  */
-inline void band_endpoints(const BandConst &bc, float x0, float x1, float x2, float l, float e0[3], float e1[3]) {
-    float q = bc.tau / l;
-    float f0 = 1.0f - q;
-    if (f0 < 0.0f) f0 = 0.0f;
-    float f1 = 1.0f + q;
+void band_endpoints(const Map &m, const double R[9], const double t[3], const float x[3], double e0[3],
+                    double e1[3], double *len) {
+    const double X = x[0], Y = x[1], Z = x[2];
+    const double l = std::sqrt(X * X + Y * Y + Z * Z);
+    const double q = m.tau / l;
+    const double f0 = std::max(0.0, 1.0 - q), f1 = 1.0 + q;
     for (int k = 0; k < 3; ++k) {
-        float s = bc.Rv[3 * k] * x0;
-        s = s + bc.Rv[3 * k + 1] * x1;
-        s = s + bc.Rv[3 * k + 2] * x2;
-        float a = s * f0;
-        float b = s * f1;
-        e0[k] = bc.tv[k] + a;
-        e1[k] = bc.tv[k] + b;
+        const double sk = (R[3 * k] * X + R[3 * k + 1] * Y) + R[3 * k + 2] * Z;
+        e0[k] = (t[k] + f0 * sk) / m.nu + 0.5;
+        e1[k] = (t[k] + f1 * sk) / m.nu + 0.5;
     }
+    if (len) *len = l;
 }
 
 /*
- * Blocks met by the segment e(t) = e0 + t (e1 - e0), t in [0, 1], against
- * half-open blocks [8b, 8b+8).  The path starts in the block of e0, ends in
- * the block of e1 and, between them, crosses one block plane per event; the
- * events are ordered by the crossing parameter t* = (P - e0) / (e1 - e0)
- * (single precision).  A plane crossed upward is entered at t* itself; a
- * plane crossed downward is left only after t*; events with equal t* and
- * equal kind apply together.
+ * Clearance of block b from the segment e(u) = e0 + u (e1 - e0), u in [0, 1]:
+ * the largest, over the segment's points, of the distance from the point to
+ * the nearest face of b's box [8b, 8b + 8)^3, counted negative outside the
+ * box (an L-infinity depth).  It is the maximum over u of the minimum of six
+ * linear functions, a concave piecewise-linear function, so its maximum lies
+ * at u = 0, u = 1 or where two of the six lines cross: all are evaluated.
+ * Positive: the segment runs through the block's interior; negative: it
+ * misses the block; zero: it touches the boundary.
  */
-void band_blocks(const float e0[3], const float e1[3], std::vector<I3> &out) {
-    struct Ev { float t; int phase; int axis; int step; };
-    Ev ev[64];
-    int nev = 0;
-    int64_t cur[3];
+double block_clearance(const double e0[3], const double e1[3], const I3 &b) {
+    double a[6], sl[6];
+    const int64_t bb[3] = {b.x, b.y, b.z};
     for (int k = 0; k < 3; ++k) {
-        int64_t b0 = (int64_t)std::floor(e0[k] / 8.0f);
-        int64_t b1 = (int64_t)std::floor(e1[k] / 8.0f);
-        cur[k] = b0;
-        float d = e1[k] - e0[k];
-        if (b1 > b0) {
-            for (int64_t b = b0 + 1; b <= b1 && nev < 64; ++b) {
-                float P = (float)(8 * b);
-                float num = P - e0[k];
-                ev[nev++] = {num / d, 0, k, +1};
-            }
-        } else if (b1 < b0) {
-            for (int64_t b = b0; b > b1 && nev < 64; --b) {
-                float P = (float)(8 * b);
-                float num = P - e0[k];
-                ev[nev++] = {num / d, 1, k, -1};
-            }
-        }
+        const double lo = 8.0 * (double)bb[k], hi = lo + 8.0, d = e1[k] - e0[k];
+        a[2 * k] = e0[k] - lo;          // distance above the lower face
+        sl[2 * k] = d;
+        a[2 * k + 1] = hi - e0[k];      // distance below the upper face
+        sl[2 * k + 1] = -d;
     }
-    std::sort(ev, ev + nev, [](const Ev &a, const Ev &b) {
-        if (a.t != b.t) return a.t < b.t;
-        return a.phase < b.phase;
-    });
-    out.push_back({cur[0], cur[1], cur[2]});
-    int i = 0;
-    while (i < nev) {
-        int j = i;
-        while (j < nev && ev[j].t == ev[i].t && ev[j].phase == ev[i].phase) {
-            cur[ev[j].axis] += ev[j].step;
-            ++j;
+    auto depth = [&](double u) {
+        double v = INFINITY;
+        for (int j = 0; j < 6; ++j) v = std::min(v, a[j] + sl[j] * u);
+        return v;
+    };
+    double best = std::max(depth(0.0), depth(1.0));
+    for (int i = 0; i < 6; ++i)
+        for (int j = i + 1; j < 6; ++j) {
+            if (sl[i] == sl[j]) continue;
+            const double u = (a[j] - a[i]) / (sl[i] - sl[j]);
+            if (u > 0.0 && u < 1.0) best = std::max(best, depth(u));
         }
-        out.push_back({cur[0], cur[1], cur[2]});
-        i = j;
-    }
+    return best;
 }
 
-BandConst band_const(const Map &m, const double R[9], const double t[3]) {
-    BandConst bc;
-    for (int i = 0; i < 9; ++i) bc.Rv[i] = (float)(R[i] / m.nu);
-    for (int k = 0; k < 3; ++k) bc.tv[k] = (float)(t[k] / m.nu + 0.5);
-    bc.tau = (float)m.tau;
-    return bc;
+/*
+ * Half-width (voxel units) of the band of clearances within which an IEEE
+ * single-precision evaluation of the endpoints (R / nu and t / nu + 1/2
+ * rounded to FP32, a few roundings of magnitude |t / nu| + |s| / nu) may
+ * place the segment on the other side of a block face: 2^-20 (16 units of
+ * single-precision roundoff) times the magnitudes involved.
+ */
+double band_margin(const Map &m, const double t[3], double len) {
+    const double T = std::max(std::fabs(t[0]), std::max(std::fabs(t[1]), std::fabs(t[2]))) / m.nu + 0.5;
+    const double S = (len + m.tau) / m.nu;
+    return std::ldexp(T + 2.0 * S + 16.0, -20);
+}
+
+/*
+ * Blocks met by the band of one point: `sure` those whose clearance exceeds
+ * the margin (every faithful evaluation allocates them), `amb` those within
+ * the margin of zero (an FP32 evaluation may take them or not).  Candidates
+ * are the blocks overlapping the segment's bounding box widened by the
+ * margin.
+ */
+void band_blocks(const double e0[3], const double e1[3], double margin, std::vector<I3> &sure,
+                 std::vector<I3> &amb) {
+    int64_t lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = (int64_t)std::floor((std::min(e0[k], e1[k]) - margin) / 8.0);
+        hi[k] = (int64_t)std::floor((std::max(e0[k], e1[k]) + margin) / 8.0);
+    }
+    for (int64_t x = lo[0]; x <= hi[0]; ++x)
+        for (int64_t y = lo[1]; y <= hi[1]; ++y)
+            for (int64_t z = lo[2]; z <= hi[2]; ++z) {
+                const I3 b{x, y, z};
+                const double c = block_clearance(e0, e1, b);
+                if (c > margin) sure.push_back(b);
+                else if (c >= -margin) amb.push_back(b);
+            }
 }
 
 inline double dist_to_int(double a) { return std::fabs(a - std::floor(a + 0.5)); }
@@ -360,9 +397,39 @@ double nonprojective_distance(double psi, const double u[3], const double g[3], 
 // ---------------------------------------------------------------------------
 // one frame
 // ---------------------------------------------------------------------------
+// Candidate pixels of a projection (u_c, v_c) (Sec. III-C.1, rounding half
+// up): the FP64 pixel first and, within delta_px of a rounding boundary, the
+// pixel on the other side of it too (-1 for a row outside [0, H)).  Returns
+// the number written.
+int pixel_candidates(const Lidar &L, double uc, double vc, double delta, int64_t out[4], bool *amb) {
+    int64_t us[2], vs[2];
+    int nu_ = 1, nv_ = 1;
+    us[0] = (int64_t)std::floor(uc + 0.5);
+    vs[0] = (int64_t)std::floor(vc + 0.5);
+    const double bu = std::floor(uc + 0.5 + 0.5), bv = std::floor(vc + 0.5 + 0.5);   // nearest boundaries
+    if (std::fabs(uc + 0.5 - bu) < delta) {
+        us[1] = us[0] == (int64_t)bu ? (int64_t)bu - 1 : (int64_t)bu;
+        nu_ = 2;
+    }
+    if (std::fabs(vc + 0.5 - bv) < delta) {
+        vs[1] = vs[0] == (int64_t)bv ? (int64_t)bv - 1 : (int64_t)bv;
+        nv_ = 2;
+    }
+    *amb = nu_ > 1 || nv_ > 1;
+    int n = 0;
+    for (int j = 0; j < nv_; ++j)
+        for (int i = 0; i < nu_; ++i) {
+            const int64_t u = ((us[i] % L.W) + L.W) % L.W, v = vs[j];
+            out[n++] = (v < 0 || v >= L.H) ? -1 : v * L.W + u;
+        }
+    return n;
+}
+
 int integrate(Map &m, const Lidar &L, const float *pts, const int32_t *labels, const float *probs,
-              int64_t n, const double T[16], int nthreads) {
+              int64_t n, const double T[16], int nthreads, const Decisions *dec) {
     m.st = Stats();
+    std::memset(m.check, 0, sizeof(m.check));
+    int64_t *ck = m.check;
     const int C = m.C;
     double R[9], t[3];
     for (int r = 0; r < 3; ++r) {
@@ -370,36 +437,91 @@ int integrate(Map &m, const Lidar &L, const float *pts, const int32_t *labels, c
         t[r] = T[4 * r + 3];
     }
     const int64_t NP = (int64_t)L.H * L.W;
+    const double eps_r = std::ldexp(1.0, -20);   // relative range band of FP32 range decisions
 
     // --- measurement preprocessing: range image (Sec. III-C.1) -------------
-    std::vector<int64_t> win(NP, -1);
-    std::vector<float> win_l(NP, 0.0f);
-    std::vector<float> lr(n);
-    std::vector<uint8_t> valid(n, 0);
-    const float rmin_f = (float)L.r_min, rmax_f = (float)L.r_max;
+    // validity (finite, r_min <= r <= r_max) and pixel of each point, FP64
+    std::vector<int64_t> ppix(n, -2);            // pixel, -1 valid without one, -2 invalid
     for (int64_t i = 0; i < n; ++i) {
-        float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
-        if (!(std::isfinite(x) && std::isfinite(y) && std::isfinite(z))) continue;
-        float l = range_f32(x, y, z);
-        lr[i] = l;
-        if (!(l >= rmin_f && l <= rmax_f && l > 0.0f)) continue;
-        valid[i] = 1;
+        const float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+        if (!(std::isfinite(x) && std::isfinite(y) && std::isfinite(z))) {
+            if (dec && dec->point_pix) {
+                ck[CK_POINTS]++;
+                if (dec->point_pix[i] != -2) ck[CK_POINTS_BAD]++;
+            }
+            continue;
+        }
+        const double X = x, Y = y, Z = z;
+        const double r = std::sqrt(X * X + Y * Y + Z * Z);
+        bool valid = r >= L.r_min && r <= L.r_max && r > 0.0;
+        const bool amb_valid = std::fabs(r - L.r_min) <= eps_r * r || std::fabs(r - L.r_max) <= eps_r * r;
+        int64_t cand[4] = {-1, -1, -1, -1};
+        int nc = 0;
+        bool amb_pix = false;
+        if (r > 0.0) {
+            const double uc = (PI - std::atan2(Y, X)) / L.dphi;
+            const double vc = (std::acos(Z / r) - L.theta0) / L.dtheta;
+            nc = pixel_candidates(L, uc, vc, m.delta_px, cand, &amb_pix);
+        }
+        int64_t pix = valid ? cand[0] : -2;
+        if (amb_valid || (valid && amb_pix)) m.st.ambiguous_points++;
+        if (dec && dec->point_pix) {
+            const int64_t g = dec->point_pix[i];
+            ck[CK_POINTS]++;
+            bool ok;
+            if (g == -2) ok = !valid || amb_valid;
+            else {
+                ok = (valid || amb_valid) && r > 0.0;
+                bool in = false;
+                for (int j = 0; j < nc; ++j) in = in || cand[j] == g;
+                ok = ok && in && (g == pix || amb_pix || !valid);
+            }
+            if (!ok) ck[CK_POINTS_BAD]++;
+            else {
+                if (amb_valid || amb_pix) ck[CK_POINTS_AMB]++;
+                pix = g;
+            }
+        }
+        ppix[i] = pix;
+        if (pix == -2) continue;
         m.st.valid_points++;
-        double X = x, Y = y, Z = z;
-        double r = std::sqrt(X * X + Y * Y + Z * Z);
-        double uc = (PI - std::atan2(Y, X)) / L.dphi;
-        double vc = (std::acos(Z / r) - L.theta0) / L.dtheta;
-        if (dist_to_int(uc + 0.5) < m.delta_px || dist_to_int(vc + 0.5) < m.delta_px) m.st.ambiguous_points++;
-        int64_t u = (int64_t)std::floor(uc + 0.5);
-        int64_t v = (int64_t)std::floor(vc + 0.5);
-        u = ((u % L.W) + L.W) % L.W;
-        if (v < 0 || v >= L.H) continue;
-        m.st.pixel_points++;
-        int64_t p = v * L.W + u;
-        // nearest point wins the pixel; equal ranges go to the lower index
-        if (win[p] < 0 || l < win_l[p] || (l == win_l[p] && i < win[p])) {
+        if (pix >= 0) m.st.pixel_points++;
+    }
+    // nearest point wins the pixel (equal ranges: the lower index); FP64 ranges
+    std::vector<int64_t> win(NP, -1);
+    std::vector<double> win_r(NP, INFINITY);
+    std::vector<double> rng(n, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        if (ppix[i] == -2) continue;
+        const double X = pts[3 * i], Y = pts[3 * i + 1], Z = pts[3 * i + 2];
+        rng[i] = std::sqrt(X * X + Y * Y + Z * Z);
+        const int64_t p = ppix[i];
+        if (p < 0) continue;
+        if (rng[i] < win_r[p] || (rng[i] == win_r[p] && i < win[p])) {
             win[p] = i;
-            win_l[p] = l;
+            win_r[p] = rng[i];
+        }
+    }
+    if (dec && dec->winner) {
+        // candidates: the pixel's points within the FP32 range band of its nearest range
+        std::vector<uint8_t> cand(n, 0);
+        std::vector<int32_t> ncand(NP, 0);
+        for (int64_t i = 0; i < n; ++i)
+            if (ppix[i] >= 0 && rng[i] <= win_r[ppix[i]] * (1.0 + eps_r)) {
+                cand[i] = 1;
+                ncand[ppix[i]]++;
+            }
+        for (int64_t p = 0; p < NP; ++p) {
+            const uint64_t g = dec->winner[p];
+            const int64_t gi = g == ~0ull ? -1 : (int64_t)(g & 0xffffffffull);
+            ck[CK_PIXELS]++;
+            const bool ok = gi == win[p] || (gi >= 0 && win[p] >= 0 && gi < n && ppix[gi] == p && cand[gi]);
+            if (!ok) ck[CK_WINNERS_BAD]++;
+            else {
+                if (ncand[p] > 1) ck[CK_WINNERS_AMB]++;
+                win[p] = gi;
+                win_r[p] = gi >= 0 ? rng[gi] : INFINITY;
+            }
         }
     }
     // per-pixel log-likelihood of each class (Eq. bayesian_filter's P(O = l | I_k))
@@ -432,23 +554,59 @@ int integrate(Map &m, const Lidar &L, const float *pts, const int32_t *labels, c
         normal_image(L, range, R, m.normals, m.normal_flag);
     }
 
-    // --- block allocation along each point's truncation band ------------------
-    BandConst bc = band_const(m, R, t);
+    // --- block allocation along each point's truncation band (FP64) ----------
+    std::unordered_set<I3, I3Hash> sure, amb;
+    {
+        std::vector<I3> vs, va;
+        for (int64_t i = 0; i < n; ++i) {
+            if (ppix[i] == -2) continue;
+            double e0[3], e1[3], len;
+            band_endpoints(m, R, t, &pts[3 * i], e0, e1, &len);
+            vs.clear();
+            va.clear();
+            band_blocks(e0, e1, band_margin(m, t, len), vs, va);
+            for (const I3 &b : vs) sure.insert(b);
+            for (const I3 &b : va) amb.insert(b);
+        }
+        for (const I3 &b : sure) amb.erase(b);
+    }
+    m.st.sure_blocks = (int64_t)sure.size();
+    m.st.ambiguous_blocks = (int64_t)amb.size();
     std::unordered_set<I3, I3Hash> touched;
-    std::vector<I3> tmp;
-    for (int64_t i = 0; i < n; ++i) {
-        if (!valid[i]) continue;
-        float e0[3], e1[3];
-        band_endpoints(bc, pts[3 * i], pts[3 * i + 1], pts[3 * i + 2], lr[i], e0, e1);
-        tmp.clear();
-        band_blocks(e0, e1, tmp);
-        for (const I3 &b : tmp) touched.insert(b);
+    if (dec && dec->touched) {
+        // accept the recorded set when sure <= it <= sure + ambiguous
+        ck[CK_BLOCKS_SURE] = (int64_t)sure.size();
+        ck[CK_BLOCKS_AMB] = (int64_t)amb.size();
+        for (int64_t j = 0; j < dec->n_touched; ++j) {
+            const I3 b{dec->touched[3 * j], dec->touched[3 * j + 1], dec->touched[3 * j + 2]};
+            if (sure.count(b)) touched.insert(b);
+            else if (amb.count(b)) {
+                touched.insert(b);
+                ck[CK_BLOCKS_AMB_TAKEN]++;
+            } else {
+                ck[CK_BLOCKS_EXTRA]++;
+            }
+        }
+        for (const I3 &b : sure)
+            if (!touched.count(b)) {
+                ck[CK_BLOCKS_MISSING]++;
+                touched.insert(b);
+            }
+    } else {
+        // alone: the sure blocks and the ambiguous ones the exact segment touches
+        touched = sure;
+        for (const I3 &b : amb) touched.insert(b);
     }
     m.touched.assign(touched.begin(), touched.end());
     std::sort(m.touched.begin(), m.touched.end());
     m.st.touched_blocks = (int64_t)m.touched.size();
     std::vector<Block *> work;
     std::vector<I3> work_key;
+    std::vector<const int32_t *> work_rec;
+    std::unordered_map<I3, const int32_t *, I3Hash> recs;
+    if (dec && dec->vox)
+        for (int64_t j = 0; j < dec->n_touched; ++j)
+            recs[{dec->touched[3 * j], dec->touched[3 * j + 1], dec->touched[3 * j + 2]}] = dec->vox + j * BV;
     for (const I3 &b : m.touched) {
         if (m.alloc.insert(b).second) m.st.new_blocks++;
         if (m.track && !m.track_keys.count(b)) continue;
@@ -456,23 +614,38 @@ int integrate(Map &m, const Lidar &L, const float *pts, const int32_t *labels, c
         if (it == m.blocks.end()) it = m.blocks.emplace(b, new_block(C, m.dist_mode)).first;
         work.push_back(&it->second);
         work_key.push_back(b);
+        const int32_t *rec = nullptr;
+        if (dec && dec->vox) {
+            auto r = recs.find(b);
+            if (r == recs.end()) ck[CK_VOX_NO_RECORD]++;
+            else rec = r->second;
+        }
+        work_rec.push_back(rec);
     }
 
     // --- projective TSDF + Bayesian semantic update, per voxel ----------------
     const double nu = m.nu, tau = m.tau;
+    const bool follow = dec && dec->vox;
     int64_t n_upd = 0, n_sem = 0, n_seen = 0, n_taint = 0;
+    int64_t c_vox = 0, c_pa = 0, c_pb = 0, c_ua = 0, c_ub = 0, c_sa = 0, c_sb = 0;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 4) reduction(+ : n_upd, n_sem, n_seen, n_taint)
+#pragma omp parallel for schedule(dynamic, 4) \
+    reduction(+ : n_upd, n_sem, n_seen, n_taint, c_vox, c_pa, c_pb, c_ua, c_ub, c_sa, c_sb)
 #endif
     for (int64_t wi = 0; wi < (int64_t)work.size(); ++wi) {
         Block &blk = *work[wi];
         const I3 bk = work_key[wi];
+        const int32_t *rec = work_rec[wi];
         std::vector<double> a(C);
         for (int lz = 0; lz < BS; ++lz)
             for (int ly = 0; ly < BS; ++ly)
                 for (int lx = 0; lx < BS; ++lx) {
                     const int vi = vidx(lx, ly, lz);
+                    // the recorded choices of this voxel: pixel, updated, class update
+                    const int64_t gpix = rec ? (int64_t)(rec[vi] & 0x0fffffff) - 1 : -2;
+                    const bool gupd = rec && ((rec[vi] >> 28) & 1), gsem = rec && ((rec[vi] >> 29) & 1);
+                    if (rec) c_vox++;
                     // voxel centre x_i = nu * v_i (Sec. III-C.2)
                     double xw[3] = {nu * (double)(BS * bk.x + lx), nu * (double)(BS * bk.y + ly),
                                     nu * (double)(BS * bk.z + lz)};
@@ -480,28 +653,60 @@ int integrate(Map &m, const Lidar &L, const float *pts, const int32_t *labels, c
                     double xl[3];
                     for (int k = 0; k < 3; ++k) xl[k] = R[k] * d[0] + R[3 + k] * d[1] + R[6 + k] * d[2];
                     double rho = std::sqrt(xl[0] * xl[0] + xl[1] * xl[1] + xl[2] * xl[2]);
-                    if (!(rho > 0.0)) continue;
+                    if (!(rho > 0.0)) {
+                        if (rec && (gpix != -1 || gupd || gsem)) c_pb++;
+                        continue;
+                    }
                     n_seen++;
-                    double uc = (PI - std::atan2(xl[1], xl[0])) / L.dphi;
-                    double vc = (std::acos(xl[2] / rho) - L.theta0) / L.dtheta;
-                    if (dist_to_int(uc + 0.5) < m.delta_px || dist_to_int(vc + 0.5) < m.delta_px) {
+                    const double uc = (PI - std::atan2(xl[1], xl[0])) / L.dphi;
+                    const double vc = (std::acos(xl[2] / rho) - L.theta0) / L.dtheta;
+                    int64_t cand[4];
+                    bool amb_pix = false;
+                    const int nc = pixel_candidates(L, uc, vc, m.delta_px, cand, &amb_pix);
+                    int64_t p = cand[0];
+                    if (follow && rec) {
+                        bool in = false;
+                        for (int j = 0; j < nc; ++j) in = in || cand[j] == gpix;
+                        if (!in) c_pb++;
+                        else {
+                            if (amb_pix) c_pa++;
+                            p = gpix;
+                        }
+                    } else if (amb_pix) {
                         blk.taint[vi] |= 3;
                         n_taint++;
                     }
-                    int64_t u = (int64_t)std::floor(uc + 0.5);
-                    int64_t v = (int64_t)std::floor(vc + 0.5);
-                    u = ((u % L.W) + L.W) % L.W;
-                    if (v < 0 || v >= L.H) continue;
-                    int64_t p = v * L.W + u;
+                    const bool amb_psi_lo_rec = follow && rec;
+                    auto no_update = [&]() {
+                        if (rec && (gupd || gsem)) c_ub++;
+                    };
+                    if (p < 0) {
+                        no_update();
+                        continue;
+                    }
                     int64_t wpt = win[p];
-                    if (wpt < 0) continue;
+                    if (wpt < 0) {
+                        no_update();
+                        continue;
+                    }
                     double P0 = pts[3 * wpt], P1 = pts[3 * wpt + 1], P2 = pts[3 * wpt + 2];
                     double r = std::sqrt(P0 * P0 + P1 * P1 + P2 * P2);
                     // projective signed distance along the ray: > 0 in front of the surface
                     double psi = r - rho;
-                    if (std::fabs(psi + tau) < m.eps_psi) { blk.taint[vi] |= 3; n_taint++; }
-                    if (std::fabs(psi - tau) < m.eps_psi) { blk.taint[vi] |= 2; n_taint++; }
-                    if (psi < -tau) continue;
+                    // update iff psi > -tau (psi >= -tau and a positive weight)
+                    bool upd = psi >= -tau && (m.weight_mode != 0 || psi + tau > 0.0);
+                    if (std::fabs(psi + tau) < m.eps_psi) {
+                        if (amb_psi_lo_rec) {
+                            c_ua++;
+                            upd = gupd;
+                        } else {
+                            blk.taint[vi] |= 3;
+                            n_taint++;
+                        }
+                    } else if (rec && gupd != upd) {
+                        c_ub++;
+                    }
+                    if (!upd) continue;
                     double w;
                     if (m.weight_mode == 0) {
                         // linear weight (psi + tau) / (2 tau), clamped to [0, 1]
@@ -511,7 +716,6 @@ int integrate(Map &m, const Lidar &L, const float *pts, const int32_t *labels, c
                     } else {
                         w = 1.0;
                     }
-                    if (!(w > 0.0)) continue;
                     double Wo = blk.W[vi];
                     double dist = psi;
                     if (m.dist_mode == 1) {
@@ -539,7 +743,21 @@ int integrate(Map &m, const Lidar &L, const float *pts, const int32_t *labels, c
                     blk.D[vi] = (Wo * blk.D[vi] + w * sdf) / (Wo + w);
                     blk.W[vi] = Wo + w;
                     n_upd++;
-                    if (std::fabs(psi) <= tau && has_sem[p]) {
+                    blk.nupd[vi]++;
+                    // class update: the surface band |psi| <= tau, a pixel with a likelihood
+                    bool sem = std::fabs(psi) <= tau && has_sem[p];
+                    if (std::fabs(psi - tau) < m.eps_psi && has_sem[p]) {
+                        if (follow && rec) {
+                            c_sa++;
+                            sem = gsem;
+                        } else {
+                            blk.taint[vi] |= 2;
+                            n_taint++;
+                        }
+                    } else if (rec && gsem != sem) {
+                        c_sb++;
+                    }
+                    if (sem) {
                         // recursive Bayesian update in log space, normalised by Z
                         const double *lrow = &logL[(size_t)p * C];
                         double mx = -INFINITY;
@@ -553,12 +771,20 @@ int integrate(Map &m, const Lidar &L, const float *pts, const int32_t *labels, c
                         for (int c = 0; c < C; ++c)
                             blk.logP[(size_t)c * BV + vi] = std::max(a[c] - lse, m.logp_floor);
                         n_sem++;
+                        blk.nsem[vi]++;
                     }
                 }
     }
     m.st.voxels_updated = n_upd;
     m.st.voxels_semantic = n_sem;
     m.st.voxels_seen = n_seen;
+    ck[CK_VOXELS] = c_vox;
+    ck[CK_VOX_PIX_AMB] = c_pa;
+    ck[CK_VOX_PIX_BAD] = c_pb;
+    ck[CK_VOX_UPD_AMB] = c_ua;
+    ck[CK_VOX_UPD_BAD] = c_ub;
+    ck[CK_VOX_SEM_AMB] = c_sa;
+    ck[CK_VOX_SEM_BAD] = c_sb;
     m.st.taint_events = n_taint;
     m.frame++;
     return 0;
@@ -863,9 +1089,12 @@ void orc_set_track(void *h, const int32_t *coords, int64_t n) {
     for (int64_t i = 0; i < n; ++i) m->track_keys.insert({coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]});
 }
 
-// lidar6 = {H, W, fov_up, fov_down, r_min, r_max} (angles in radians)
+// lidar6 = {H, W, fov_up, fov_down, r_min, r_max} (angles in radians).  The
+// decision arguments (all may be null) are a single-precision implementation's
+// choices for this scan, for candidate acceptance (struct Decisions).
 int orc_integrate(void *h, const double *lidar6, const float *pts, const int32_t *labels, const float *probs,
-                  int64_t n, const double *T16, int nthreads) {
+                  int64_t n, const double *T16, int nthreads, const int32_t *point_pix, const uint64_t *winner,
+                  const int32_t *touched, int64_t n_touched, const int32_t *vox_rec) {
     Map *m = (Map *)h;
     Lidar L;
     L.H = (int)lidar6[0];
@@ -877,15 +1106,26 @@ int orc_integrate(void *h, const double *lidar6, const float *pts, const int32_t
     L.dphi = 2.0 * PI / L.W;
     L.dtheta = (L.fov_up - L.fov_down) / (L.H - 1);
     L.theta0 = PI / 2.0 - L.fov_up;
-    return integrate(*m, L, pts, labels, probs, n, T16, nthreads);
+    Decisions d;
+    d.point_pix = point_pix;
+    d.winner = winner;
+    d.touched = touched;
+    d.n_touched = n_touched;
+    d.vox = touched ? vox_rec : nullptr;
+    const bool any = point_pix || winner || touched;
+    return integrate(*m, L, pts, labels, probs, n, T16, nthreads, any ? &d : nullptr);
 }
+
+// candidate-acceptance counts of the last scan (CK_* order, CK_COUNT entries)
+void orc_check(void *h, int64_t *out) { std::memcpy(out, ((Map *)h)->check, sizeof(int64_t) * CK_COUNT); }
 
 // valid, in-pixel, ambiguous points; touched, new blocks; updated, semantic, seen voxels; taint events
 void orc_stats(void *h, int64_t *out) {
     Map *m = (Map *)h;
     const Stats &s = m->st;
-    int64_t v[9] = {s.valid_points, s.pixel_points, s.ambiguous_points, s.touched_blocks, s.new_blocks,
-                    s.voxels_updated, s.voxels_semantic, s.voxels_seen, s.taint_events};
+    int64_t v[11] = {s.valid_points, s.pixel_points, s.ambiguous_points, s.touched_blocks, s.new_blocks,
+                     s.voxels_updated, s.voxels_semantic, s.voxels_seen, s.taint_events, s.sure_blocks,
+                     s.ambiguous_blocks};
     std::memcpy(out, v, sizeof(v));
 }
 
@@ -919,7 +1159,7 @@ int64_t orc_get_touched(void *h, int32_t *coords, int64_t cap) {
 
 // Copy one block's voxels; returns 0 when the block holds data, -1 otherwise.
 int orc_read_block(void *h, const int32_t *coord, double *D, double *W, double *logP, uint8_t *taint,
-                   int32_t *label, double *gap) {
+                   int32_t *label, double *gap, int32_t *nupd, int32_t *nsem) {
     Map *m = (Map *)h;
     auto it = m->blocks.find({coord[0], coord[1], coord[2]});
     if (it == m->blocks.end()) return -1;
@@ -928,6 +1168,8 @@ int orc_read_block(void *h, const int32_t *coord, double *D, double *W, double *
     if (W) std::memcpy(W, b.W.data(), sizeof(double) * BV);
     if (logP) std::memcpy(logP, b.logP.data(), sizeof(double) * BV * m->C);
     if (taint) std::memcpy(taint, b.taint.data(), BV);
+    if (nupd) std::memcpy(nupd, b.nupd.data(), sizeof(int32_t) * BV);
+    if (nsem) std::memcpy(nsem, b.nsem.data(), sizeof(int32_t) * BV);
     if (label)
         for (int vi = 0; vi < BV; ++vi) label[vi] = argmax_label(*m, b, vi, gap ? gap + vi : nullptr);
     return 0;
@@ -1151,40 +1393,49 @@ void orc_palette(int C, uint8_t *rgb) {
     }
 }
 
-// Band blocks of one point (test hook for the allocation pins).
-int64_t orc_point_blocks(void *h, const float *pt, const double *T16, int32_t *out, int64_t cap) {
+// Band blocks of one point (test hook for the allocation pins): the sure
+// blocks, then the ambiguous ones; cls[i] = 1 for sure, 0 for ambiguous.
+int64_t orc_point_blocks(void *h, const float *pt, const double *T16, int32_t *out, int8_t *cls, int64_t cap) {
     Map *m = (Map *)h;
     double R[9], t[3];
     for (int r = 0; r < 3; ++r) {
         for (int c = 0; c < 3; ++c) R[3 * r + c] = T16[4 * r + c];
         t[r] = T16[4 * r + 3];
     }
-    BandConst bc = band_const(*m, R, t);
-    float l = range_f32(pt[0], pt[1], pt[2]);
-    float e0[3], e1[3];
-    band_endpoints(bc, pt[0], pt[1], pt[2], l, e0, e1);
-    std::vector<I3> v;
-    band_blocks(e0, e1, v);
-    int64_t n = std::min<int64_t>(cap, (int64_t)v.size());
-    for (int64_t i = 0; i < n; ++i) {
-        out[3 * i] = (int32_t)v[i].x;
-        out[3 * i + 1] = (int32_t)v[i].y;
-        out[3 * i + 2] = (int32_t)v[i].z;
-    }
-    return (int64_t)v.size();
+    double e0[3], e1[3], len;
+    band_endpoints(*m, R, t, pt, e0, e1, &len);
+    std::vector<I3> vs, va;
+    band_blocks(e0, e1, band_margin(*m, t, len), vs, va);
+    int64_t k = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (const I3 &b : pass == 0 ? vs : va) {
+            if (k < cap) {
+                out[3 * k] = (int32_t)b.x;
+                out[3 * k + 1] = (int32_t)b.y;
+                out[3 * k + 2] = (int32_t)b.z;
+                cls[k] = pass == 0 ? 1 : 0;
+            }
+            ++k;
+        }
+    return k;
 }
 
-// FP32 band endpoints of one point (test hook)
-void orc_point_band(void *h, const float *pt, const double *T16, float *e0, float *e1) {
+// FP64 band endpoints of one point (voxel units + 1/2) and the ambiguity margin (test hook)
+double orc_point_band(void *h, const float *pt, const double *T16, double *e0, double *e1) {
     Map *m = (Map *)h;
     double R[9], t[3];
     for (int r = 0; r < 3; ++r) {
         for (int c = 0; c < 3; ++c) R[3 * r + c] = T16[4 * r + c];
         t[r] = T16[4 * r + 3];
     }
-    BandConst bc = band_const(*m, R, t);
-    float l = range_f32(pt[0], pt[1], pt[2]);
-    band_endpoints(bc, pt[0], pt[1], pt[2], l, e0, e1);
+    double len;
+    band_endpoints(*m, R, t, pt, e0, e1, &len);
+    return band_margin(*m, t, len);
+}
+
+// clearance of block b from the segment e0 -> e1 (voxel units + 1/2; test hook)
+double orc_block_clearance(const double *e0, const double *e1, const int32_t *b) {
+    return block_clearance(e0, e1, I3{b[0], b[1], b[2]});
 }
 
 }  // extern "C"

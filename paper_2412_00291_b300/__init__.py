@@ -69,6 +69,8 @@ _SIGS = {
     "map_config_default": ([P], I32),
     "map_create": ([P, P], I32),
     "map_check_scan_pose": ([P, P, P], I32),
+    "map_set_decision_record": ([P, I32], I32),
+    "map_read_decision_record": ([P, P, I64, P, I64, P, I64, P, P], I32),
     "map_destroy": ([P], I32),
     "integrate_scan": ([P, P, P, P, P, I64, P, P], I32),
     "integrate_scan_host": ([P, P, P, P, P, I64, P, P], I32),
@@ -280,6 +282,27 @@ def extract_mesh_noalloc(h, positions, colors, vertex_keys, triangles, triangle_
                                      int(positions.shape[0]), int(triangles.shape[0]), ctypes.byref(nv),
                                      ctypes.byref(nt), _stream(stream)), h)
     return nv.value, nt.value
+
+
+def map_set_decision_record(h, enable: bool):
+    """Parity instrumentation: record each scan's point, pixel-winner, block and voxel decisions."""
+    _check(_lib.map_set_decision_record(h, 1 if enable else 0), h)
+
+
+def map_read_decision_record(h, n_points, n_pixels):
+    """The last scan's recorded decisions: dict(point_pix [n], winner [H*W] uint64,
+    touched [k, 3] int32, vox [k, 512] int32); synchronises the device."""
+    nt = ctypes.c_int64()
+    _check(_lib.map_read_decision_record(h, None, 0, None, 0, None, 0, ctypes.byref(nt), None), h)
+    k = nt.value
+    pp = np.zeros(max(n_points, 1), np.int32)
+    wi = np.zeros(max(n_pixels, 1), np.uint64)
+    tb = np.zeros((max(k, 1), 3), np.int32)
+    vx = np.zeros((max(k, 1), BV), np.int32)
+    _check(_lib.map_read_decision_record(h, _np_ptr(pp), n_points, _np_ptr(wi), n_pixels, _np_ptr(tb), k,
+                                         ctypes.byref(nt), _np_ptr(vx)), h)
+    assert nt.value == k
+    return dict(point_pix=pp[:n_points], winner=wi[:n_pixels], touched=tb[:k], vox=vx[:k])
 
 
 def map_remesh_all(h, stream=None):
@@ -600,6 +623,12 @@ class SemanticTSDF:
 
     def mesh(self, stream=None):
         return extract_mesh(self.h, stream)
+
+    def record_decisions(self, enable=True):
+        map_set_decision_record(self.h, enable)
+
+    def decisions(self, n_points, n_pixels):
+        return map_read_decision_record(self.h, n_points, n_pixels)
 
     def remesh_all(self, stream=None):
         map_remesh_all(self.h, stream)

@@ -160,6 +160,10 @@ struct FrameDev {
     unsigned long long *win_next;
     long long win_next_n;
     unsigned long long *ctr_next;
+    // parity instrumentation (null on the product path): the scan's choices,
+    // for comparison with an FP64 reference
+    int *dbg_point;            // [n] pixel of each point, -1 valid without a pixel, -2 invalid
+    int *dbg_vox;              // [slot][512] pixel + 1 (0: none) | updated << 28 | class update << 29
 };
 
 // --- error-free transformations (Knuth TwoSum, Dekker/FMA TwoProduct) ----

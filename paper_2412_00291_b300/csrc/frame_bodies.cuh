@@ -125,7 +125,7 @@ __device__ __forceinline__ int hash_insert(const MapDev &md, uint64_t key, int &
 // to `cnt`; the caller forms the totals.
 __device__ __forceinline__ void points_item(const float *__restrict__ pts, const ScanConst &sc, const MapDev &md,
                                             const FrameDev &fd, long long i, long long (&cnt)[3]) {
-    int nb = 0, valid = 0, inpix = 0;
+    int nb = 0, valid = 0, inpix = 0, pix = -2;
     int blocks[MAX_BAND_BLOCKS][3];
     if (i < sc.n) {
         const float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
@@ -134,6 +134,7 @@ __device__ __forceinline__ void points_item(const float *__restrict__ pts, const
             if (l >= sc.r_min && l <= sc.r_max && l > 0.f) {
                 valid = 1;
                 const int p = point_pixel(sc, x, y, z, l);
+                pix = p;
                 if (p >= 0) {
                     inpix = 1;
                     atomicMin(&fd.win[p], ((unsigned long long)__float_as_uint(l) << 32) | (unsigned)i);
@@ -142,6 +143,7 @@ __device__ __forceinline__ void points_item(const float *__restrict__ pts, const
             }
         }
     }
+    if (fd.dbg_point && i < sc.n) fd.dbg_point[i] = pix;
     cnt[0] += valid;
     cnt[1] += inpix;
     int n_new = 0;
@@ -442,7 +444,8 @@ struct TsdfWarpSmem {
 template <bool F16, bool DIST>
 __device__ __forceinline__ bool tsdf_fast(const ScanConst &sc, const MapDev &md, long long vox, int vi, int p,
                                           unsigned long long win, float2 dw, float rr2, float irr, long long &n_upd,
-                                          unsigned &remesh) {
+                                          unsigned &remesh, bool &upd) {
+    upd = false;
     if (p < 0 || win == ~0ull) return false;
     const float tau = sc.tau;
     const float r = __uint_as_float((unsigned)(win >> 32));
@@ -453,6 +456,7 @@ __device__ __forceinline__ bool tsdf_fast(const ScanConst &sc, const MapDev &md,
     const float Wn = __fadd_rn(dw.y, 1.f);
     store_dw<F16>(md, vox, __fdividef(__fmaf_rn(dw.y, dw.x, tau), Wn), Wn);
     ++n_upd;
+    upd = true;
     remesh |= remesh_offsets(vi);
     return false;
 }
@@ -463,7 +467,8 @@ __device__ __forceinline__ bool tsdf_fast(const ScanConst &sc, const MapDev &md,
 // Returns true when the voxel also takes the class update.
 template <bool F16, bool DIST>
 __device__ __forceinline__ bool tsdf_band(const ScanConst &sc, const MapDev &md, int slot, int bx, int by, int bz,
-                                          const BandEntry &e, long long &n_upd, unsigned &remesh) {
+                                          const BandEntry &e, long long &n_upd, unsigned &remesh, bool &upd) {
+    upd = false;
     const float tau = sc.tau;
     const int vi = e.vi & (BV - 1), lx = vi & 7, ly = (vi >> 3) & 7, lz = vi >> 6;
     const float m0 = (float)(8 * bx + lx - sc.k[0]), m1 = (float)(8 * by + ly - sc.k[1]),
@@ -528,6 +533,7 @@ __device__ __forceinline__ bool tsdf_band(const ScanConst &sc, const MapDev &md,
     const float Wn = __fadd_rn(e.W, w);
     store_dw<F16>(md, (long long)slot * BV + vi, __fdividef(__fmaf_rn(e.W, e.D, __fmul_rn(w, sdf)), Wn), Wn);
     ++n_upd;
+    upd = true;
     remesh |= remesh_offsets(vi);
     if (fabsf(psi) > tau) return false;
     // the winner carries a class likelihood: a probability row, or a label in range
@@ -551,7 +557,9 @@ __device__ __forceinline__ void tsdf_list(bool sem, int vox, int idx, int2 *wbuf
 // which would otherwise idle the rest of the warp).  Every part of a new
 // block links it with its neighbours (the same writes), so that the part's
 // own re-mesh queueing below reads links it has set itself.
-template <bool F16, bool DIST = false>
+// With DBG the warp also records each voxel's pixel, update and class-update
+// decisions in fd.dbg_vox (parity instrumentation; needs H * W <= 2^23).
+template <bool F16, bool DIST = false, bool DBG = false>
 __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int h,
                                                 TsdfWarpSmem &T, long long &n_upd, int v0 = 0, int v1 = BV) {
     const int lane = threadIdx.x & 31;
@@ -569,7 +577,7 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
         const unsigned mb = __ballot_sync(0xffffffffu, band);
         if (band) {
             BandEntry &e = T.band[qn + __popc(mb & lt)];
-            e.vi = DIST ? (int)((unsigned)vi | ((unsigned)pix << 9)) : vi;
+            e.vi = (DIST || DBG) ? (int)((unsigned)vi | ((unsigned)pix << 9)) : vi;
             e.idx = (unsigned)(win & 0xffffffffu);
             e.r = __uint_as_float((unsigned)(win >> 32));
             e.D = dw.x;
@@ -584,9 +592,12 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
         int vox = 0, idx = 0;
         if (lane < n) {
             const BandEntry e = T.band[lane];
-            sem = tsdf_band<F16, DIST>(sc, md, slot, bx, by, bz, e, n_upd, remesh);
+            bool upd;
+            sem = tsdf_band<F16, DIST>(sc, md, slot, bx, by, bz, e, n_upd, remesh, upd);
             vox = slot * BV + (e.vi & (BV - 1));
             idx = (int)e.idx;
+            if (DBG)
+                fd.dbg_vox[vox] = ((int)((unsigned)e.vi >> 9) + 1) | (upd ? 1 << 28 : 0) | (sem ? 1 << 29 : 0);
         }
         const bool keep = lane < qn - n;
         BandEntry rest;
@@ -614,8 +625,13 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
         da1 = __fadd_rn(da1, sc.Rt[5]);
         da2 = __fadd_rn(da2, sc.Rt[8]);
         const unsigned long long wa = fd.win[pa < 0 ? 0 : pa], wb = fd.win[pb < 0 ? 0 : pb];
-        const bool ba = tsdf_fast<F16, DIST>(sc, md, va, vi, pa, wa, dwa, ra, ia, n_upd, remesh);
-        const bool bb = tsdf_fast<F16, DIST>(sc, md, vb, vi + 32, pb, wb, dwb, rb, ib, n_upd, remesh);
+        bool ua, ub;
+        const bool ba = tsdf_fast<F16, DIST>(sc, md, va, vi, pa, wa, dwa, ra, ia, n_upd, remesh, ua);
+        const bool bb = tsdf_fast<F16, DIST>(sc, md, vb, vi + 32, pb, wb, dwb, rb, ib, n_upd, remesh, ub);
+        if (DBG) {
+            if (!ba) fd.dbg_vox[va] = (pa + 1) | (ua ? 1 << 28 : 0);
+            if (!bb) fd.dbg_vox[vb] = (pb + 1) | (ub ? 1 << 28 : 0);
+        }
         enqueue(ba, vi, wa, dwa, pa);
         if (qn >= 32) drain(32);
         enqueue(bb, vi + 32, wb, dwb, pb);

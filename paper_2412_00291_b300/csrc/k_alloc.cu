@@ -25,6 +25,32 @@ __global__ void __launch_bounds__(128) k_points(const float *__restrict__ pts, S
     cta_count<3>(fd.ctr, {CT_VALID, CT_PIXEL, CT_NEW}, cnt);
 }
 
+// Parity instrumentation: for each block of the touched list U_k (hash slots),
+// its coordinates and the 512 voxel decision records the TSDF kernel wrote.
+__global__ void k_dbg_gather(MapDev md, const int *__restrict__ touched, long long nt, const int *__restrict__ vrec,
+                             int32_t *coords, int32_t *out) {
+    for (long long j = blockIdx.x; j < nt; j += gridDim.x) {
+        const int h = touched[j];
+        const int slot = md.vals[h];
+        if (threadIdx.x == 0) {
+            int x, y, z;
+            unpack_block(md.keys[h], x, y, z);
+            coords[3 * j] = x;
+            coords[3 * j + 1] = y;
+            coords[3 * j + 2] = z;
+        }
+        for (int v = threadIdx.x; v < BV; v += blockDim.x)
+            out[j * BV + v] = slot < 0 ? 0 : vrec[(long long)slot * BV + v];
+    }
+}
+
+void launch_dbg_gather(const MapDev &md, const int *touched, long long nt, const int *vrec, int32_t *coords,
+                       int32_t *out, cudaStream_t s) {
+    if (nt <= 0) return;
+    const int grid = (int)std::min<long long>(nt, 148 * 16);
+    k_dbg_gather<<<grid, 128, 0, s>>>(md, touched, nt, vrec, coords, out);
+}
+
 // A scan's counters and the device state, copied after the scan's last kernel
 // into one record [counters | state] for the host to download.
 __global__ void k_snapshot(const unsigned long long *__restrict__ ctr, const DevState *__restrict__ st,

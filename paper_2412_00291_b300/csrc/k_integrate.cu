@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) k_normals(ScanConst sc, FrameDev fd) {
 // and the last round of the grid-stride loop idles fewer warps.
 constexpr int TSDF_PARTS = 2;
 
-template <bool F16, bool DIST>
+template <bool F16, bool DIST, bool DBG = false>
 __global__ void __launch_bounds__(256, 4) k_tsdf(ScanConst sc, MapDev md, FrameDev fd) {
     __shared__ TsdfWarpSmem s_w[8];   // per-warp class-update entries and band queue
     TsdfWarpSmem &tw = s_w[threadIdx.x >> 5];
@@ -53,7 +53,8 @@ __global__ void __launch_bounds__(256, 4) k_tsdf(ScanConst sc, MapDev md, FrameD
     constexpr int PV = BV / TSDF_PARTS;
     for (long long u = warp; u < (long long)nt * TSDF_PARTS; u += nwarps) {
         const int part = (int)(u % TSDF_PARTS);
-        tsdf_block_warp<F16, DIST>(sc, md, fd, fd.touched[u / TSDF_PARTS], tw, n_upd, part * PV, part * PV + PV);
+        tsdf_block_warp<F16, DIST, DBG>(sc, md, fd, fd.touched[u / TSDF_PARTS], tw, n_upd, part * PV,
+                                        part * PV + PV);
     }
     long long cnt[1] = {n_upd};
     cta_count<1>(fd.ctr, {CT_UPD}, cnt);
@@ -89,6 +90,9 @@ int semantic_blocks_per_sm(int storage, int C) {
 void launch_integrate(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s) {
     auto k = sc.dist_mode ? (md.storage == 0 ? k_tsdf<false, true> : k_tsdf<true, true>)
                           : (md.storage == 0 ? k_tsdf<false, false> : k_tsdf<true, false>);
+    if (fd.dbg_vox)   // decision record on: the recording instantiations
+        k = sc.dist_mode ? (md.storage == 0 ? k_tsdf<false, true, true> : k_tsdf<true, true, true>)
+                         : (md.storage == 0 ? k_tsdf<false, false, true> : k_tsdf<true, false, true>);
     launch_pdl(k, dim3(grid), dim3(256), 0, s, sc, md, fd);
 }
 

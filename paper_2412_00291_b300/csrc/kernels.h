@@ -17,6 +17,9 @@ void launch_write_block(const MapDev &md, uint64_t key, const float *D, const fl
 void launch_read_blocks(const MapDev &md, const uint64_t *keys, int n, float *D, float *W, float *logP,
                         uint8_t *label, uint8_t *found, float *G, cudaStream_t s);
 void launch_collect_blocks(const MapDev &md, int32_t *coords, unsigned long long *count, cudaStream_t s);
+// parity instrumentation: coordinates [nt][3] and voxel decision records [nt][512] of the touched list
+void launch_dbg_gather(const MapDev &md, const int *touched, long long nt, const int *vrec, int32_t *coords,
+                       int32_t *out, cudaStream_t s);
 
 // k_integrate.cu: projective TSDF + Bayesian semantic fusion (Sec. III-C.2, III-C.3)
 void launch_integrate(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s);

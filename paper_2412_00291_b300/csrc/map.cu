@@ -119,6 +119,10 @@ struct map_t {
     int prof_cap = 0, prof_n = 0;
     unsigned long long *prof_stats = nullptr;   // device [prof_cap][CT_COUNT]
     long long launches = 0;                     // kernels launched by this map
+    // parity instrumentation: decision records of the last scan (map_set_decision_record)
+    int *dbg_point = nullptr, *dbg_vox = nullptr;
+    long long dbg_frame = -1;                   // frame whose decisions the buffers hold
+    long long dbg_n = 0, dbg_np = 0;            // its point and pixel counts
     std::string err;
 };
 
@@ -210,6 +214,9 @@ static void free_all(map_t *m) {
     if (m->side) cudaStreamDestroy(m->side);
     if (m->ev_snap) cudaEventDestroy(m->ev_snap);
     if (m->dl) cudaStreamDestroy(m->dl);
+    if (m->dbg_point) cudaFree(m->dbg_point);
+    if (m->dbg_vox) cudaFree(m->dbg_vox);
+    m->dbg_point = m->dbg_vox = nullptr;
 }
 
 template <typename T>
@@ -708,6 +715,11 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     m->win_dirty[cur] = np;
     m->ctr_clean[cur] = false;
     launch_points(pts, sc, m->md, fd, s);
+    if (fd.dbg_point) {
+        m->dbg_frame = m->frame;
+        m->dbg_n = n;
+        m->dbg_np = np;
+    }
     m->win_dirty[nxt] = 0;
     m->ctr_clean[nxt] = true;
     if (sc.dist_mode) {
@@ -1385,6 +1397,65 @@ extern "C" map_status map_profile_end(map_t *m, float *ms_out, int64_t *stats_ou
     return MAP_OK;
 }
 
+extern "C" map_status map_set_decision_record(map_t *m, int32_t enable) {
+    if (!m) return fail(nullptr, MAP_ERR_ARG, "null map");
+    if (enable != 0 && enable != 1) return fail(m, MAP_ERR_ARG, "enable must be 0 or 1");
+    CU(cudaDeviceSynchronize());
+    if (!enable) {
+        if (m->dbg_point) cudaFree(m->dbg_point);
+        if (m->dbg_vox) cudaFree(m->dbg_vox);
+        m->dbg_point = m->dbg_vox = nullptr;
+    } else if (!m->dbg_point) {
+        if (m->cfg.max_pixels > (1ll << 23)) return fail(m, MAP_ERR_ARG, "decision record: max_pixels <= 2^23");
+        if (cudaMalloc(&m->dbg_point, (size_t)m->cfg.max_points * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&m->dbg_vox, (size_t)m->cfg.max_blocks * BV * sizeof(int)) != cudaSuccess) {
+            if (m->dbg_point) cudaFree(m->dbg_point);
+            m->dbg_point = nullptr;
+            cudaGetLastError();
+            return fail(m, MAP_ERR_NOMEM, "decision record: device allocation failed");
+        }
+    }
+    m->fd.dbg_point = m->dbg_point;
+    m->fd.dbg_vox = m->dbg_vox;
+    m->dbg_frame = -1;
+    return MAP_OK;
+}
+
+extern "C" map_status map_read_decision_record(map_t *m, int32_t *point_pix, int64_t n_points, uint64_t *winner,
+                                               int64_t n_pixels, int32_t *touched, int64_t touched_cap,
+                                               int64_t *n_touched, int32_t *voxel_rec) {
+    if (!m || !n_touched) return fail(m, MAP_ERR_ARG, "null map or count");
+    if (!m->dbg_point || m->dbg_frame < 0 || m->dbg_frame != m->frame - 1)
+        return fail(m, MAP_ERR_STATE, "no decision record of the last scan (map_set_decision_record, then a scan)");
+    if ((point_pix && n_points != m->dbg_n) || (winner && n_pixels != m->dbg_np))
+        return fail(m, MAP_ERR_ARG, "point or pixel count differs from the recorded scan's");
+    CU(cudaDeviceSynchronize());
+    unsigned long long ctr[CT_COUNT];
+    CU(cudaMemcpy(ctr, m->fd.ctr, sizeof(ctr), cudaMemcpyDeviceToHost));
+    const long long nt = (long long)std::min<unsigned long long>(ctr[CT_TOUCHED], (unsigned long long)m->cfg.max_blocks);
+    *n_touched = nt;
+    if (point_pix && n_points > 0)
+        CU(cudaMemcpy(point_pix, m->dbg_point, n_points * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (winner && n_pixels > 0)
+        CU(cudaMemcpy(winner, m->fd.win, n_pixels * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (touched && nt > 0) {
+        if (touched_cap < nt) return fail(m, MAP_ERR_CAPACITY, "touched_cap below the touched-block count");
+        int32_t *dc = nullptr, *dv = nullptr;
+        CU(cudaMalloc(&dc, nt * 3 * sizeof(int32_t)));
+        if (cudaMalloc(&dv, nt * BV * sizeof(int32_t)) != cudaSuccess) {
+            cudaFree(dc);
+            return fail(m, MAP_ERR_NOMEM, "decision record: gather buffer");
+        }
+        launch_dbg_gather(m->md, m->fd.touched, nt, m->dbg_vox, dc, dv, 0);
+        cudaError_t e = cudaMemcpy(touched, dc, nt * 3 * sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && voxel_rec) e = cudaMemcpy(voxel_rec, dv, nt * BV * sizeof(int32_t), cudaMemcpyDeviceToHost);
+        cudaFree(dc);
+        cudaFree(dv);
+        if (e != cudaSuccess) return fail(m, MAP_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return MAP_OK;
+}
+
 extern "C" const char *map_last_error(map_t *m) { return m ? m->err.c_str() : g_err.c_str(); }
 
 // ===========================================================================
@@ -1620,6 +1691,7 @@ extern "C" map_status map_batch_integrate(map_batch_t *b, const scan_desc *scans
         it.sc = sc;
         it.md = m->md;
         it.fd = m->fd;      // the batch kernel resets this set's range image and counters itself
+        it.fd.dbg_point = it.fd.dbg_vox = nullptr;   // no decision record in the batched form
         m->win_dirty[m->fcur] = m->cfg.max_pixels;
         it.sc.pts = d.points_dev;
         it.sc.labels = d.labels_dev;

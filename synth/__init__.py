@@ -16,7 +16,10 @@ equation of Sec. III-C.1): pixel (v, u) has polar angle
 ``theta0 + v * dtheta`` with ``theta0 = pi/2 - fov_up`` and
 ``dtheta = (fov_up - fov_down) / (H - 1)``, and azimuth ``pi - u * dphi`` with
 ``dphi = 2 pi / W``.  Generated points lie on their own pixel's centre ray,
-perturbed only along the ray by Gaussian range noise.
+perturbed along the ray by Gaussian range noise; a workload with ``jitter``
+> 0 also turns each ray by normal angular offsets (``jitter`` pixels std in
+both angles), so that points fall off their pixel's centre ray, some near
+pixel boundaries, some pixels receive two points and some none.
 """
 from __future__ import annotations
 
@@ -55,7 +58,7 @@ def _load():
                                    P, P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
-                                   P, P, P, P, P, ctypes.c_int]
+                                   P, P, P, P, P, ctypes.c_int, ctypes.c_double]
         lib.synth_scan.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -218,12 +221,19 @@ class Workload:
     seed: int
     n_prims: int = 0
     extent: float = 0.0
+    jitter: float = 0.0    # angular offset of each ray, std in pixels (0: points on the centre rays)
 
 
 def line16() -> Workload:
     """10 scans, 16 x 1024, +-15 deg, 50 m, sigma 2 cm, straight drive, hard labels, 0.2 m voxels."""
     return Workload("scan16x1024_line10_v0.2", lidar_deg(16, 1024, 15.0, -15.0, 50.0), 0.02, 10,
                     0.2, 0.6, 20, "hard", "line", 1)
+
+
+def line16_jitter() -> Workload:
+    """line16 with each ray turned by N(0, 0.35 px) in both angles (points off the pixel centres)."""
+    from dataclasses import replace
+    return replace(line16(), name="scan16x1024_line10_v0.2_jitter", jitter=0.35)
 
 
 def loop64() -> Workload:
@@ -354,7 +364,7 @@ def make_frame(w: Workload, scene: Scene, T: np.ndarray, k: int, dirs_l=None, nt
                    int(sc.ground_cls), _ptr(R), _ptr(t), L.H, L.W, L.theta0, L.dtheta, L.dphi, L.r_max,
                    w.sigma, C, 0 if w.label_mode == "hard" else 1, 0.1, w.seed, k,
                    _ptr(out.points), _ptr(out.labels), _ptr(out.probs) if out.probs is not None else None,
-                   _ptr(out.true_range), _ptr(out.true_cls), int(nthreads))
+                   _ptr(out.true_range), _ptr(out.true_cls), int(nthreads), float(w.jitter))
     return out
 
 

@@ -306,6 +306,11 @@ static double rng_normal(rng_t *r) {        /* Box-Muller, cosine branch */
  *               labels[i] = hit class.
  * Rows with no hit get label -1 and an all-zero probability row.
  * true_range / true_cls (optional) receive the analytic hit.
+ * jitter_px > 0: the ray of pixel (v, u) is turned by independent normal
+ * offsets of jitter_px * dtheta in polar angle and jitter_px * dphi in
+ * azimuth (a real scanner's firing-time and beam-angle spread), drawn from a
+ * stream of their own, so that points no longer lie on their pixel's centre
+ * ray; the point is (true range + noise) along the turned ray.
  */
 int synth_scan(const double *boxes, const int *box_cls, int nbox,
                const double *cyls, const int *cyl_cls, int ncyl,
@@ -313,7 +318,7 @@ int synth_scan(const double *boxes, const int *box_cls, int nbox,
                const double *R, const double *t, int H, int W, double theta0, double dtheta,
                double dphi, double r_max, double sigma, int n_classes, int label_mode,
                double p_flip, uint64_t seed, uint64_t frame, float *points, int *labels,
-               float *probs, double *true_range, int *true_cls, int nthreads) {
+               float *probs, double *true_range, int *true_cls, int nthreads, double jitter_px) {
     scene_t s;
     s.boxes = boxes; s.nbox = nbox; s.cyls = cyls; s.ncyl = ncyl; s.ramps = ramps; s.nramp = nramp;
     build_grid(&s, 4.0);
@@ -326,6 +331,11 @@ int synth_scan(const double *boxes, const int *box_cls, int nbox,
     for (long i = 0; i < n; ++i) {
         int v = (int)(i / W), u = (int)(i % W);
         double th = theta0 + v * dtheta, ph = 3.141592653589793 - u * dphi;
+        if (jitter_px > 0.0) {
+            rng_t rj = rng_at(seed, frame, (uint64_t)i + (1ULL << 40));
+            th += jitter_px * dtheta * rng_normal(&rj);
+            ph += jitter_px * dphi * rng_normal(&rj);
+        }
         double dl[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
         double dw[3];
         for (int k = 0; k < 3; ++k) dw[k] = R[3 * k] * dl[0] + R[3 * k + 1] * dl[1] + R[3 * k + 2] * dl[2];

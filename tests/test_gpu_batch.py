@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 import synth  # noqa: E402
-from tests.gpu_compare import compare_blocks, compare_meshes  # noqa: E402
+from tests.gpu_compare import Lockstep, compare_blocks, compare_meshes  # noqa: E402
 
 # dirty_blocks is left out: a block allocated in this scan links itself to its neighbours while
 # other warps read those links to queue lower neighbours for re-meshing, so a new block none of
@@ -87,19 +87,23 @@ def batch_run():
         bat.append(_new_map(p, w, nu, tau, s[2]))
     b = p.map_batch_create([m.h for m in bat], p.MAP_BATCH_GRAPH | p.MAP_BATCH_AUTOTUNE)
     om = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    assert SPECS[0][0] is None and SPECS[0][1] is None
+    ls = Lockstep(seq[0], om)
     stats_seq, stats_bat, configs = [], [], []
     for k, f in enumerate(frames):
         ins = [_inputs(w, frames, s, k, f) for s in SPECS]
         dev = [(_dev(pt), None if lb is None else _dev(lb), None if pr is None else _dev(pr)) for pt, lb, pr in ins]
-        for m, (pt, lb, pr) in zip(seq, dev):
-            m.integrate(L, pt, f.T, labels=lb, probs=pr)
+        for i, (m, (pt, lb, pr)) in enumerate(zip(seq, dev)):
+            if i == 0:        # map 0 in lockstep with the oracle (recorded decisions accepted)
+                ls.scan(L, w.lidar, ins[0][0], f.T, labels=ins[0][1], probs=ins[0][2])
+            else:
+                m.integrate(L, pt, f.T, labels=lb, probs=pr)
         p.map_batch_integrate(b, [m.h for m in bat], [L] * len(bat), [d[0] for d in dev], [f.T] * len(bat),
                               labels=[d[1] for d in dev], probs=[d[2] for d in dev])
         p.map_batch_sync(b)
         configs.append(p.map_batch_config(b))
         stats_seq.append([m.stats() for m in seq])
         stats_bat.append([m.stats() for m in bat])
-        om.integrate(w.lidar, ins[0][0], f.T, labels=ins[0][1])
     yield dict(p=p, w=w, seq=seq, bat=bat, b=b, om=om, stats_seq=stats_seq, stats_bat=stats_bat, configs=configs,
                n_frames=len(frames))
     p.map_batch_destroy(b)

@@ -23,7 +23,7 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 import synth  # noqa: E402
-from tests.gpu_compare import compare_blocks, compare_meshes  # noqa: E402
+from tests.gpu_compare import Lockstep, compare_blocks, compare_meshes  # noqa: E402
 
 KW = dict(max_blocks=32768, hash_capacity=1 << 16, max_points=32768, max_pixels=32768,
           mesh_vertex_capacity=1 << 22, mesh_triangle_capacity=1 << 23)
@@ -76,13 +76,14 @@ def line16_np():
     g16 = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, distance="nonprojective", storage=1, **KW)
     gpj = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, **KW)
     om = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes, distance="nonprojective")
+    ls = Lockstep(g32, om)
     per_frame = []
     for f in frames:
         pts, lab = _dev(f.points), _dev(f.labels)
-        for m in (g32, g16, gpj):
+        for m in (g16, gpj):
             m.integrate(L, pts, f.T, labels=lab)
-        os_ = om.integrate(w.lidar, f.points, f.T, labels=f.labels)
-        per_frame.append((g32.stats(), os_, _sorted(g32.blocks()), _sorted(om.alloc_blocks())))
+        gs, os_, _ = ls.scan(L, w.lidar, f.points, f.T, labels=f.labels)
+        per_frame.append((gs, os_, _sorted(g32.blocks()), _sorted(om.alloc_blocks())))
     return dict(p=p, w=w, g32=g32, g16=g16, gpj=gpj, om=om, per_frame=per_frame)
 
 
@@ -92,7 +93,6 @@ def test_nonproj_counts_and_block_sets(line16_np):
         for key in ("valid_points", "pixel_points", "touched_blocks", "new_blocks"):
             assert gs[key] == os_[key], (k, key)
         np.testing.assert_array_equal(gb, ob)
-        assert abs(gs["voxels_updated"] - os_["voxels_updated"]) <= max(10, os_["taint_events"])
 
 
 def test_nonproj_voxels_and_gradients(line16_np):
@@ -185,12 +185,9 @@ def test_nonproj_loop64_sampled():
     track = cand[rng.choice(len(cand), size=96, replace=False)]
     om = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes, distance="nonprojective")
     om.set_track(track)
+    ls = Lockstep(gm, om, exact_voxel_counts=False)
     for fr in frames:
-        gm.integrate(L, _dev(fr.points), fr.T, probs=_dev(fr.probs))
-        om.integrate(w.lidar, fr.points, fr.T, probs=fr.probs)
-        gs, os_ = gm.stats(), om.stats()
-        for key in ("valid_points", "pixel_points", "touched_blocks", "new_blocks"):
-            assert gs[key] == os_[key], key
+        ls.scan(L, w.lidar, fr.points, fr.T, probs=fr.probs)
     np.testing.assert_array_equal(_sorted(gm.blocks()), _sorted(om.alloc_blocks()))
     have = np.array([b for b in track if om.read_block(b) is not None])
     rep = compare_blocks(gm, om, have, w.voxel_size, K, w.n_classes)

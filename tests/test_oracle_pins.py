@@ -356,40 +356,99 @@ def _seg_box_dist(e0, e1, b):
     return np.linalg.norm(p - q, axis=1).min()
 
 
+def _segment64(p, T, nu, tau):
+    """The band segment of point p (LiDAR frame) written out independently, in FP64: the world
+    point, the unit ray from the sensor, [p - tau d, p + tau d] (start at the sensor when
+    |p| < tau), in voxel units + 1/2."""
+    pw = T[:3, :3] @ p.astype(np.float64) + T[:3, 3]
+    ray = pw - T[:3, 3]
+    ray /= np.linalg.norm(ray)
+    start = T[:3, 3] if np.linalg.norm(p.astype(np.float64)) < tau else pw - tau * ray
+    return start / nu + 0.5, (pw + tau * ray) / nu + 0.5
+
+
+def test_block_clearance_closed_forms():
+    """Clearance = the deepest L-infinity penetration of the segment into the block's box."""
+    b = np.array([0, 0, 0])
+    # along x through the middle, ending 3 voxels inside: limited by the end point (x = 3)
+    assert oracle.block_clearance([-2, 4, 4], [3, 4, 4], b) == pytest.approx(3.0)
+    # through the whole block along x: limited by the y/z half widths (4)
+    assert oracle.block_clearance([-2, 4, 4], [12, 4, 4], b) == pytest.approx(4.0)
+    # off-centre in y (y = 6.5): 1.5 from the upper y face
+    assert oracle.block_clearance([-2, 6.5, 4], [12, 6.5, 4], b) == pytest.approx(1.5)
+    # parallel outside (y = 9): -1
+    assert oracle.block_clearance([-2, 9, 4], [12, 9, 4], b) == pytest.approx(-1.0)
+    # diagonal through the corner (8, 8, z) in the xy plane: touches the block's edge only -> 0
+    assert oracle.block_clearance([7, 9, 4], [9, 7, 4], b) == pytest.approx(0.0, abs=1e-12)
+    # the same diagonal moved inward by 0.1 in x and y: depth 0.1 at the crossing point
+    assert oracle.block_clearance([6.9, 8.9, 4], [8.9, 6.9, 4], b) == pytest.approx(0.1)
+    # ... and outward: the nearest approach is 0.1 beyond the edge on both axes -> -0.1
+    assert oracle.block_clearance([7.1, 9.1, 4], [9.1, 7.1, 4], b) == pytest.approx(-0.1)
+    # a point-like segment inside
+    assert oracle.block_clearance([1, 2, 3], [1, 2, 3], b) == pytest.approx(1.0)
+    # other blocks: translation by 8 b
+    assert oracle.block_clearance([-2 + 8, 4 - 16, 4 + 24], [3 + 8, 4 - 16, 4 + 24], [1, -2, 3]) == \
+        pytest.approx(3.0)
+
+
 @pytest.mark.parametrize("nu,tau", [(0.1, 0.3), (0.25, 1.25)])
 def test_band_blocks_brute_force(nu, tau):
-    """tau = 3 nu (one crossing per axis at most) and tau = 5 nu (Table II: several)."""
+    """tau = 3 nu (one crossing per axis at most) and tau = 5 nu (Table II: several).
+
+    The oracle's FP64 endpoints equal the segment written out here; dense sampling of that
+    segment (1/40000 of its length per step) finds every sure block and only blocks in
+    sure + ambiguous; every ambiguous block lies within the margin of the segment."""
     rng = np.random.default_rng(9)
     m = oracle.OracleMap(nu, tau, n_classes=2)
-    n_diff = 0
-    for trial in range(150):
+    n_amb = 0
+    for trial in range(200):
         T = _pose(random_rotation(rng), rng.uniform(-30, 30, size=3))
         d = rng.normal(size=3)
         d /= np.linalg.norm(d)
-        p = (d * rng.uniform(0.6, 60.0)).astype(np.float32)
+        p = (d * rng.uniform(0.2, 60.0)).astype(np.float32)
         if trial % 25 == 0:       # exact block-plane hits on purpose
             p = np.array([8 * nu * 3, 0.0, 0.0], np.float32)
-        e0, e1 = m.point_band(p, T)
-        e0d, e1d = e0.astype(np.float64), e1.astype(np.float64)
-        # the FP32 endpoints sit on p_world -+ tau * ray direction (voxel units + 1/2)
-        pw = T[:3, :3] @ p.astype(np.float64) + T[:3, 3]
-        ray = pw - T[:3, 3]
-        ray /= np.linalg.norm(ray)
-        l = np.linalg.norm(p.astype(np.float64))
-        start = T[:3, 3] if l < tau else pw - tau * ray
-        assert np.allclose(e0d, start / nu + 0.5, atol=2e-3)
-        assert np.allclose(e1d, (pw + tau * ray) / nu + 0.5, atol=2e-3)
-        got = {tuple(b) for b in m.point_blocks(p, T)}
+            T = np.eye(4)
+        e0, e1, margin = m.point_band(p, T)
+        w0, w1 = _segment64(p, T, nu, tau)
+        np.testing.assert_allclose(e0, w0, rtol=0, atol=1e-9)
+        np.testing.assert_allclose(e1, w1, rtol=0, atol=1e-9)
+        assert 0 < margin < 1e-2
+        sure, amb = m.point_blocks(p, T)
+        sure = {tuple(b) for b in sure.tolist()}
+        amb = {tuple(b) for b in amb.tolist()}
+        assert not (sure & amb)
         ts = np.linspace(0.0, 1.0, 40001)[:, None]
-        samp = np.floor((e0d[None, :] + ts * (e1d - e0d)[None, :]) / 8.0).astype(np.int64)
-        change = np.concatenate([[True], np.any(samp[1:] != samp[:-1], axis=1)])
-        brute = {tuple(b) for b in samp[change]}
-        for b in got ^ brute:
-            # only blocks the segment merely grazes may differ
-            assert _seg_box_dist(e0d, e1d, np.array(b, float)) < 1e-3, (trial, b)
-            n_diff += 1
-        assert len(got) <= 1 + 3 * (int(2 * tau / nu) // 8 + 1)
-    assert n_diff < 20
+        samp = np.floor((w0[None, :] + ts * (w1 - w0)[None, :]) / 8.0).astype(np.int64)
+        brute = {tuple(b) for b in np.unique(samp, axis=0).tolist()}
+        assert sure <= brute, (trial, sure - brute)
+        assert brute <= sure | amb, (trial, brute - sure - amb)
+        for b in amb:
+            assert _seg_box_dist(w0, w1, np.array(b, float)) <= 2 * margin, (trial, b)
+            n_amb += 1
+        assert len(sure) <= 1 + 3 * (int(2 * tau / nu) // 8 + 1)
+    assert n_amb <= 20
+
+
+def test_band_blocks_margin_classes():
+    """A band ending just inside, on, or just outside a block plane: sure / ambiguous / absent."""
+    nu, tau = 0.1, 0.3
+    m = oracle.OracleMap(nu, tau, n_classes=2)
+    # a point on +x at range r: e1_x = (r + tau) / nu + 1/2; put it at 8 * 5 + delta voxels
+    for delta, want in ((0.05, "sure"), (1e-7, "ambiguous"), (-1e-7, "ambiguous"), (-0.05, "absent")):
+        r = ((8 * 5 + delta) - 0.5) * nu - tau
+        p = np.array([r, 0.0, 0.0], np.float32)
+        e0, e1, margin = m.point_band(p, np.eye(4))
+        assert abs(e1[0] - (40 + delta)) < 1e-5
+        sure, amb = m.point_blocks(p, np.eye(4))
+        blk = (5, 0, 0)
+        got = "sure" if blk in {tuple(b) for b in sure.tolist()} else \
+            ("ambiguous" if blk in {tuple(b) for b in amb.tolist()} else "absent")
+        if abs(e1[0] - 40) > margin:
+            assert got == ("sure" if e1[0] > 40 else "absent"), (delta, got)
+        else:
+            assert got == "ambiguous", (delta, got)
+        assert got == want, (delta, got, e1[0] - 40, margin)
 
 
 # ---------------------------------------------------------------------------

@@ -98,3 +98,36 @@ def test_probability_rows():
     assert (q.argmax(axis=1) == f.true_cls[ok]).mean() > 0.8
     assert np.all(f.probs[~ok] == 0)
     assert 0.5 < ok.mean() < 0.95
+
+
+def test_angular_jitter_moves_points_off_their_pixel_centres():
+    """jitter = 0.35 px: the FP64 projection (u_c, v_c) of each point sits N(0, 0.35) pixels from
+    its generating pixel in both angles, so about 15 % of the points land nearer another pixel;
+    ranges keep their noise model; the jitter draws leave the un-jittered streams unchanged."""
+    wj = synth.line16_jitter()
+    w0 = synth.line16()
+    sc = synth.make_scene(w0)
+    T = synth.trajectory(w0, 2)[1]
+    f = synth.make_frame(wj, sc, T, 1)
+    f0 = synth.make_frame(w0, sc, T, 1)
+    L = wj.lidar
+    ok = np.isfinite(f.points[:, 0])
+    p = f.points[ok].astype(np.float64)
+    r = np.linalg.norm(p, axis=1)
+    uc = (math.pi - np.arctan2(p[:, 1], p[:, 0])) / L.dphi
+    vc = (np.arccos(p[:, 2] / r) - L.theta0) / L.dtheta
+    idx = np.flatnonzero(ok)
+    u0, v0 = idx % L.W, idx // L.W
+    du = (uc - u0 + L.W / 2) % L.W - L.W / 2
+    dv = vc - v0
+    assert abs(du.std() - 0.35) < 0.02 and abs(dv.std() - 0.35) < 0.02
+    # (which rays hit something depends a little on the jitter, so allow a small selection bias)
+    assert abs(du.mean()) < 0.02 and abs(dv.mean()) < 0.02
+    moved = (np.floor(uc + 0.5) % L.W != u0) | (np.floor(vc + 0.5) != v0)
+    assert 0.2 < moved.mean() < 0.35          # 1 - (1 - 0.153)^2 = 0.28 expected
+    res = r - f.true_range[ok]
+    assert abs(res.std() / wj.sigma - 1) < 0.05
+    # the same seeds without jitter give the centre-ray scan, bit for bit the un-jittered workload's
+    assert np.isfinite(f0.points[:, 0]).sum() > 0
+    f0b = synth.make_frame(w0, sc, T, 1)
+    assert f0.points.tobytes() == f0b.points.tobytes()
