@@ -115,11 +115,18 @@ struct ScanConst {
     float4 *nrm;             // [H*W] normal image, world frame; w = 1 where the pixel has a normal
 };
 
+// One slot of the block hash: key (EMPTY_KEY when free), pool slot of the
+// block (-1: the pool was full), last frame the block was touched.  16 bytes,
+// so a probe brings the pool slot and the stamp into the same 32-byte sector.
+struct __align__(16) HashSlot {
+    uint64_t key;
+    int val;
+    int stamp;
+};
+
 // Device pointers of one map.
 struct MapDev {
-    uint64_t *keys;      // [cap] block keys, EMPTY_KEY when free
-    int *vals;           // [cap] pool slot of the key (-1: pool was full)
-    int *stamp;          // [cap] last frame the block was touched
+    HashSlot *hs;        // [cap] the block hash
     int *dstamp_slot;    // [slot] last frame the block was queued for meshing
     uint64_t mask;       // cap - 1
     int max_blocks;
@@ -235,10 +242,10 @@ __device__ __forceinline__ int point_pixel(const ScanConst &sc, float x, float y
     return (v >= 0 && v < sc.H) ? v * sc.W + u : -1;
 }
 
-__device__ __forceinline__ int hash_find(const uint64_t *__restrict__ keys, uint64_t mask, uint64_t key) {
+__device__ __forceinline__ int hash_find(const HashSlot *__restrict__ hs, uint64_t mask, uint64_t key) {
     uint64_t h = fmix64(key) & mask;
     for (int p = 0; p < MAX_PROBES; ++p) {
-        uint64_t k = keys[h];
+        uint64_t k = hs[h].key;
         if (k == key) return (int)h;
         if (k == EMPTY_KEY) return -1;
         h = (h + 1) & mask;
@@ -252,12 +259,12 @@ __device__ __forceinline__ void link_block(const MapDev &md, uint64_t key, int s
     int x, y, z;
     unpack_block(key, x, y, z);
     const int dx = o & 1, dy = (o >> 1) & 1, dz = o >> 2;
-    const int hp = hash_find(md.keys, md.mask, pack_block(x + dx, y + dy, z + dz));
-    const int np = hp < 0 ? -1 : md.vals[hp];
+    const int hp = hash_find(md.hs, md.mask, pack_block(x + dx, y + dy, z + dz));
+    const int np = hp < 0 ? -1 : md.hs[hp].val;
     md.nbr[s * 16 + o] = np;
     if (np >= 0) md.nbr[np * 16 + 8 + o] = s;
-    const int hm = hash_find(md.keys, md.mask, pack_block(x - dx, y - dy, z - dz));
-    const int nm = hm < 0 ? -1 : md.vals[hm];
+    const int hm = hash_find(md.hs, md.mask, pack_block(x - dx, y - dy, z - dz));
+    const int nm = hm < 0 ? -1 : md.hs[hm].val;
     md.nbr[s * 16 + 8 + o] = nm;
     if (nm >= 0) md.nbr[nm * 16 + o] = s;
 }

@@ -88,19 +88,19 @@ __device__ __forceinline__ int band_blocks(const ScanConst &sc, float x0, float 
 __device__ __forceinline__ int hash_insert(const MapDev &md, uint64_t key, int &is_new) {
     uint64_t h = fmix64(key) & md.mask;
     for (int p = 0; p < MAX_PROBES; ++p) {
-        const uint64_t k = md.keys[h];
+        const uint64_t k = md.hs[h].key;
         if (k == key) {
             is_new = 0;
             return (int)h;
         }
         if (k == EMPTY_KEY) {
-            const uint64_t old = atomicCAS((unsigned long long *)&md.keys[h], EMPTY_KEY, key);
+            const uint64_t old = atomicCAS((unsigned long long *)&md.hs[h].key, EMPTY_KEY, key);
             if (old == EMPTY_KEY) {
                 const unsigned long long s = atomicAdd(&md.st->pool_count, 1ull);
                 if (s < (unsigned long long)md.max_blocks) {
-                    md.vals[h] = (int)s;
+                    md.hs[h].val = (int)s;
                 } else {
-                    md.vals[h] = -1;
+                    md.hs[h].val = -1;
                     atomicOr(&md.st->err, ERR_POOL_FULL);
                 }
                 is_new = 1;
@@ -165,11 +165,19 @@ __device__ __forceinline__ void points_item(const float *__restrict__ pts, const
             const unsigned grp = __match_any_sync(0xffffffffu, key[q]);
             own[q] = j < nb && __ffs(grp) - 1 == lane;
         }
+        // the home slot's whole record: key, pool slot and frame stamp in one 16-byte load
         uint64_t probe[4];
+        int pstamp[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             h[q] = (int)(fmix64(key[q]) & md.mask);
-            probe[q] = own[q] ? md.keys[h[q]] : key[q];
+            pstamp[q] = -1;
+            probe[q] = key[q];
+            if (own[q]) {
+                const HashSlot r = md.hs[h[q]];
+                probe[q] = r.key;
+                pstamp[q] = r.stamp;
+            }
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -177,9 +185,10 @@ __device__ __forceinline__ void points_item(const float *__restrict__ pts, const
                 // not at its home slot: the full find-or-insert
                 int is_new = 0;
                 h[q] = hash_insert(md, key[q], is_new);
+                pstamp[q] = -1;
                 if (h[q] >= 0 && is_new) {
                     ++n_new;
-                    const int sl = md.vals[h[q]];
+                    const int sl = md.hs[h[q]].val;
                     if (sl >= 0) {
                         md.slot_key[sl] = key[q];
                         md.slot_frame[sl] = sc.frame;
@@ -187,10 +196,12 @@ __device__ __forceinline__ void points_item(const float *__restrict__ pts, const
                 }
             }
         }
+        // first touch in this scan: a stamp already at this frame was set by an exchange of this
+        // scan (stamps change only by that exchange), so the exchange is needed only otherwise
         bool first[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            first[q] = own[q] && h[q] >= 0 && atomicExch(&md.stamp[h[q]], sc.frame) != sc.frame;
+            first[q] = own[q] && h[q] >= 0 && pstamp[q] != sc.frame && atomicExch(&md.hs[h[q]].stamp, sc.frame) != sc.frame;
         const int cnt = (int)first[0] + (int)first[1] + (int)first[2] + (int)first[3];
         int tot;
         int off = warp_exclusive_scan(cnt, tot);
@@ -578,9 +589,10 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
                                                 TsdfWarpSmem &T, long long &n_upd, int v0 = 0, int v1 = BV) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int slot = md.vals[h];
+    const HashSlot hrec = md.hs[h];
+    const int slot = hrec.val;
     if (slot < 0) return;
-    const uint64_t key = md.keys[h];
+    const uint64_t key = hrec.key;
     int bx, by, bz;
     unpack_block(key, bx, by, bz);
     // a block allocated in this frame links itself with its neighbours
@@ -782,6 +794,54 @@ __device__ __forceinline__ void store_record(const MapDev &md, long long vox, co
     }
 }
 
+// The Bayesian class update of one voxel (Eq. bayesian_filter) for a
+// compile-time class count NC: av holds the voxel's stored log-probabilities
+// (as floats) and receives the new ones (floored); q is the winner point's
+// probability row (16-byte aligned when sc.probs_vec4), or null for the hard
+// label l.  Returns the most probable class of the values as they will be
+// stored (lowest class on ties).  Every path that updates classes (per-thread,
+// bulk-staged, batched) runs this same body, so all compute the same bits.
+template <bool F16, int NC>
+__device__ __forceinline__ int class_update(const ScanConst &sc, float *av, const float *q, int l) {
+    if (q) {
+        if (NC % 4 == 0 && sc.probs_vec4) {
+#pragma unroll
+            for (int cc = 0; cc < NC; cc += 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(q + cc);
+                av[cc] = __fadd_rn(av[cc], __logf(fmaxf(v.x, sc.lik_floor)));
+                av[cc + 1] = __fadd_rn(av[cc + 1], __logf(fmaxf(v.y, sc.lik_floor)));
+                av[cc + 2] = __fadd_rn(av[cc + 2], __logf(fmaxf(v.z, sc.lik_floor)));
+                av[cc + 3] = __fadd_rn(av[cc + 3], __logf(fmaxf(v.w, sc.lik_floor)));
+            }
+        } else {
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc) av[cc] = __fadd_rn(av[cc], __logf(fmaxf(q[cc], sc.lik_floor)));
+        }
+    } else {
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) av[cc] = __fadd_rn(av[cc], cc == l ? sc.log_phit : sc.log_pmiss);
+    }
+    float m = -INFINITY;
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) m = fmaxf(m, av[cc]);
+    float ssum = 0.f;
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) ssum = __fadd_rn(ssum, __expf(__fsub_rn(av[cc], m)));
+    const float lse = __fadd_rn(m, __logf(ssum));
+    int best = 0;
+    float bv = -INFINITY;
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) {
+        av[cc] = fmaxf(__fsub_rn(av[cc], lse), sc.logp_floor);
+        const float stored = F16 ? __half2float(__float2half_rn(av[cc])) : av[cc];
+        if (stored > bv) {
+            bv = stored;
+            best = cc;
+        }
+    }
+    return best;
+}
+
 template <bool F16, int NC>
 __device__ __forceinline__ void semantic_item(const ScanConst &sc, const MapDev &md, const FrameDev &fd,
                                               unsigned long long e) {
@@ -792,52 +852,17 @@ __device__ __forceinline__ void semantic_item(const ScanConst &sc, const MapDev 
     const int2 ent = fd.sem_list[e];
     const long long vox = ent.x;
     const long long idx = ent.y;   // the pixel's winner point: log P(O = l | I_k) from its input
-    float m = -INFINITY;
     if (NC > 0) {
-        float av[NC > 0 ? NC : 1];
-        load_record<F16, (NC > 0 ? NC : 1)>(md, vox, av);
-        if (sc.has_probs) {
-            const float *q = sc.probs + idx * C;
-            if (NC % 4 == 0 && sc.probs_vec4) {
-#pragma unroll
-                for (int cc = 0; cc < (NC > 0 ? NC : 1); cc += 4) {
-                    const float4 v = *reinterpret_cast<const float4 *>(q + cc);
-                    av[cc] = __fadd_rn(av[cc], __logf(fmaxf(v.x, sc.lik_floor)));
-                    av[cc + 1] = __fadd_rn(av[cc + 1], __logf(fmaxf(v.y, sc.lik_floor)));
-                    av[cc + 2] = __fadd_rn(av[cc + 2], __logf(fmaxf(v.z, sc.lik_floor)));
-                    av[cc + 3] = __fadd_rn(av[cc + 3], __logf(fmaxf(v.w, sc.lik_floor)));
-                }
-            } else {
-#pragma unroll
-                for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc)
-                    av[cc] = __fadd_rn(av[cc], __logf(fmaxf(q[cc], sc.lik_floor)));
-            }
-        } else {
-            const int l = sc.labels[idx];
-#pragma unroll
-            for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) av[cc] = __fadd_rn(av[cc], cc == l ? sc.log_phit : sc.log_pmiss);
-        }
-#pragma unroll
-        for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) m = fmaxf(m, av[cc]);
-        float ssum = 0.f;
-#pragma unroll
-        for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) ssum = __fadd_rn(ssum, __expf(__fsub_rn(av[cc], m)));
-        const float lse = __fadd_rn(m, __logf(ssum));
-        int best = 0;
-        float bv = -INFINITY;
-#pragma unroll
-        for (int cc = 0; cc < (NC > 0 ? NC : 1); ++cc) {
-            av[cc] = fmaxf(__fsub_rn(av[cc], lse), sc.logp_floor);
-            const float stored = F16 ? __half2float(__float2half_rn(av[cc])) : av[cc];
-            if (stored > bv) {
-                bv = stored;
-                best = cc;
-            }
-        }
-        store_record<F16, (NC > 0 ? NC : 1), NCP>(md, vox, av);
+        constexpr int N1 = NC > 0 ? NC : 1;
+        float av[N1];
+        load_record<F16, N1>(md, vox, av);
+        const int best = class_update<F16, N1>(sc, av, sc.has_probs ? sc.probs + idx * C : nullptr,
+                                               sc.has_probs ? 0 : sc.labels[idx]);
+        store_record<F16, N1, NCP>(md, vox, av);
         md.label[vox] = (uint8_t)best;
     } else {
         float av[MAXC_RT];
+        float m = -INFINITY;
         const float *q = sc.probs + idx * C;
         const int l = sc.has_probs ? -1 : sc.labels[idx];
         for (int cc = 0; cc < C; ++cc) {

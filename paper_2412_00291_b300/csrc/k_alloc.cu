@@ -31,10 +31,10 @@ __global__ void k_dbg_gather(MapDev md, const int *__restrict__ touched, long lo
                              int32_t *coords, int32_t *out) {
     for (long long j = blockIdx.x; j < nt; j += gridDim.x) {
         const int h = touched[j];
-        const int slot = md.vals[h];
+        const int slot = md.hs[h].val;
         if (threadIdx.x == 0) {
             int x, y, z;
-            unpack_block(md.keys[h], x, y, z);
+            unpack_block(md.hs[h].key, x, y, z);
             coords[3 * j] = x;
             coords[3 * j + 1] = y;
             coords[3 * j + 2] = z;
@@ -107,7 +107,7 @@ __global__ void k_write_block(MapDev md, uint64_t key, const float *D, const flo
     if (threadIdx.x == 0) {
         int is_new = 0;
         const int h = hash_insert(md, key, is_new);
-        s_slot = h < 0 ? -1 : md.vals[h];
+        s_slot = h < 0 ? -1 : md.hs[h].val;
         if (s_slot >= 0) {
             md.slot_key[s_slot] = key;
             if (is_new) md.slot_frame[s_slot] = -2;
@@ -156,8 +156,8 @@ __global__ void k_read_blocks(MapDev md, const uint64_t *keys, int n, float *D, 
     if (b >= n) return;
     __shared__ int s_slot;
     if (threadIdx.x == 0) {
-        const int h = hash_find(md.keys, md.mask, keys[b]);
-        s_slot = h < 0 ? -1 : md.vals[h];
+        const int h = hash_find(md.hs, md.mask, keys[b]);
+        s_slot = h < 0 ? -1 : md.hs[h].val;
         if (found) found[b] = s_slot >= 0;
     }
     __syncthreads();
@@ -209,8 +209,8 @@ __global__ void k_read_blocks(MapDev md, const uint64_t *keys, int n, float *D, 
 __global__ void k_collect_blocks(MapDev md, int32_t *coords, unsigned long long *count) {
     for (unsigned long long h = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; h <= md.mask;
          h += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint64_t k = md.keys[h];
-        if (k == EMPTY_KEY || md.vals[h] < 0) continue;
+        const uint64_t k = md.hs[h].key;
+        if (k == EMPTY_KEY || md.hs[h].val < 0) continue;
         const unsigned long long i = atomicAdd(count, 1ull);
         if (coords && i < (unsigned long long)md.max_blocks) {
             int x, y, z;

@@ -113,8 +113,8 @@ __global__ void __launch_bounds__(256) k_cam_raycast(CamConst cc, MapDev md, con
                 bk[0] = b[0];
                 bk[1] = b[1];
                 bk[2] = b[2];
-                const int h = hash_find(md.keys, md.mask, pack_block(b[0], b[1], b[2]));
-                slot = h < 0 ? -1 : md.vals[h];
+                const int h = hash_find(md.hs, md.mask, pack_block(b[0], b[1], b[2]));
+                slot = h < 0 ? -1 : md.hs[h].val;
             }
             bool cur = false;
             float ct = 0.f, cD = 0.f;

@@ -34,7 +34,7 @@ __device__ __forceinline__ bool trilinear(const MapDev &md, const int k[3], cons
     // block j = (jx, jy, jz) in {0,1}^3, needed only where the axis crosses
     uint64_t key[8];
     uint64_t hh[8];
-    uint64_t first[8];
+    HashSlot first[8];
     bool need[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -42,14 +42,21 @@ __device__ __forceinline__ bool trilinear(const MapDev &md, const int k[3], cons
         need[j] = (!jx || b1[0] != b0[0]) && (!jy || b1[1] != b0[1]) && (!jz || b1[2] != b0[2]);
         key[j] = pack_block(jx ? b1[0] : b0[0], jy ? b1[1] : b0[1], jz ? b1[2] : b0[2]);
         hh[j] = fmix64(key[j]) & md.mask;
-        first[j] = need[j] ? md.keys[hh[j]] : key[j];
+        // the home slot's key and pool slot in one load
+        if (need[j]) first[j] = md.hs[hh[j]];
+        else first[j].key = key[j], first[j].val = 0;
     }
     int slot[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        int h = (int)hh[j];
-        if (need[j] && first[j] != key[j]) h = first[j] == EMPTY_KEY ? -1 : hash_find(md.keys, md.mask, key[j]);
-        slot[j] = need[j] ? (h < 0 ? -1 : md.vals[h]) : 0;
+        slot[j] = 0;
+        if (!need[j]) continue;
+        if (first[j].key == key[j]) {
+            slot[j] = first[j].val;
+        } else {
+            const int h = first[j].key == EMPTY_KEY ? -1 : hash_find(md.hs, md.mask, key[j]);
+            slot[j] = h < 0 ? -1 : md.hs[h].val;
+        }
     }
     float2 dw[8];
     bool ok = true;

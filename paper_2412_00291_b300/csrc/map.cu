@@ -181,7 +181,7 @@ static void prof_clear(map_t *m) {
 
 static void free_all(map_t *m) {
     prof_clear(m);
-    void *ptrs[] = {m->md.keys, m->md.vals, m->md.stamp, m->md.dstamp_slot, m->md.dw32, m->md.dw16, m->md.lp32,
+    void *ptrs[] = {m->md.hs, m->md.dstamp_slot, m->md.dw32, m->md.dw16, m->md.lp32,
                     m->md.lp16, m->md.label, m->md.vmask, m->md.slot_key, m->md.slot_frame, m->md.nbr, m->md.seg, m->md.av, m->md.ak, m->md.at,
                     m->av_alt, m->ak_alt, m->at_alt, m->st, m->ctr_pair, m->d_ring, m->win_buf[0], m->win_buf[1],
                     m->fd.touched, m->fd.dirty, m->fd.sem_list, m->gb.voff, m->gb.toff, m->gb.bsum_v, m->gb.bsum_t,
@@ -279,9 +279,7 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
             return fail(nullptr, MAP_ERR_NOMEM, msg);                                  \
         }                                                                              \
     } while (0)
-    ALLOC(md.keys, cap);
-    ALLOC(md.vals, cap);
-    ALLOC(md.stamp, cap);
+    ALLOC(md.hs, cap);
     ALLOC(md.dstamp_slot, nb);
     if (c.storage == 0) {
         ALLOC(md.dw32, nvox);
@@ -366,9 +364,7 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     for (int i = 0; i < map_t::RING; ++i) m->ring_frame[i] = -1;
 
     cudaStream_t s = 0;
-    cudaMemsetAsync(md.keys, 0xFF, cap * sizeof(uint64_t), s);
-    cudaMemsetAsync(md.vals, 0xFF, cap * sizeof(int), s);
-    cudaMemsetAsync(md.stamp, 0xFF, cap * sizeof(int), s);
+    cudaMemsetAsync(md.hs, 0xFF, cap * sizeof(HashSlot), s);   // key EMPTY_KEY, slot -1, stamp -1
     cudaMemsetAsync(md.dstamp_slot, 0xFF, nb * sizeof(int), s);
     cudaMemsetAsync(md.slot_frame, 0xFF, nb * sizeof(int), s);
     cudaMemsetAsync(md.nbr, 0xFF, nb * 16 * sizeof(int), s);
@@ -415,7 +411,8 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     m->grid_integrate = sms * integrate_blocks_per_sm(c.storage, c.n_classes, c.distance_mode);
     m->grid_semantic = 4 * sms * semantic_blocks_per_sm(c.storage, c.n_classes);
-    m->grid_mesh = sms * mesh_blocks_per_sm();
+    // at most 4 re-meshing CTAs per SM: more crowd the class update that runs beside them
+    m->grid_mesh = sms * std::min(4, mesh_blocks_per_sm());
     e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {

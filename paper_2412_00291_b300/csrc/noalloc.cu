@@ -106,7 +106,7 @@ extern "C" map_status extract_mesh_noalloc(map_t *map, float *positions, uint8_t
         map_set_error(map, "extract_mesh_noalloc: no usable current device");
         return MAP_ERR_CUDA;
     }
-    if (owner_device(md.keys) != dev) {
+    if (owner_device(md.hs) != dev) {
         map_set_error(map, "extract_mesh_noalloc: the map was created on another device than the current one");
         return MAP_ERR_ARG;
     }
