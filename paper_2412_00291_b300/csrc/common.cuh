@@ -151,9 +151,6 @@ struct MapDev {
     float nu;
     float *g32;          // non-projective mode: [slot][3][512] gradient g_i (x, y, z planes), FP32 storage
     __half *g16;         //   the same in FP16 storage
-    // [slot][32] bit masks of the stored voxel values, bit b of word w = voxel 32 w + b (x + 8 y + 64 z):
-    // words 0..15 observed (W > 0), words 16..31 D < 0; kept by every writer of {D, W}, read by meshing
-    uint32_t *vmask;
 };
 
 // Per-frame scratch of one map.

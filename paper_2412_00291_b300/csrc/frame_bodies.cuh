@@ -232,12 +232,6 @@ __device__ __forceinline__ void store_dw(const MapDev &md, long long vox, float 
     if (F16) md.dw16[vox] = __floats2half2_rn(D, W);
     else md.dw32[vox] = make_float2(D, W);
 }
-// {D, W} as stored (FP16 storage rounds them), for the voxel bit masks
-template <bool F16>
-__device__ __forceinline__ float2 stored_dw(float D, float W) {
-    if (F16) return __half22float2(__floats2half2_rn(D, W));
-    return make_float2(D, W);
-}
 template <bool F16>
 __device__ __forceinline__ float load_lp(const MapDev &md, long long j) {
     if (F16) return __half2float(md.lp16[j]);
@@ -449,7 +443,6 @@ struct BandEntry {
 struct TsdfWarpSmem {
     int2 wbuf[BV];           // class-update entries {voxel, winner point} of the block
     BandEntry band[64];      // band voxels queued for the float-pair psi
-    uint32_t mask[32];       // bit masks of the voxels processed: [0, 16) observed, [16, 32) D < 0
 };
 
 // Projective psi and the running-average update of one voxel whose pixel's
@@ -462,9 +455,8 @@ struct TsdfWarpSmem {
 template <bool F16, bool DIST>
 __device__ __forceinline__ bool tsdf_fast(const ScanConst &sc, const MapDev &md, long long vox, int vi, int p,
                                           unsigned long long win, float2 dw, float rr2, float irr, long long &n_upd,
-                                          unsigned &remesh, bool &upd, float2 &fin) {
+                                          unsigned &remesh, bool &upd) {
     upd = false;
-    fin = dw;
     if (p < 0 || win == ~0ull) return false;
     const float tau = sc.tau;
     const float r = __uint_as_float((unsigned)(win >> 32));
@@ -473,9 +465,7 @@ __device__ __forceinline__ bool tsdf_fast(const ScanConst &sc, const MapDev &md,
     // non-projective: d_i may fall inside the band whatever psi, every update takes the long path
     if (DIST || psi <= __fadd_rn(tau, 1e-3f)) return true;
     const float Wn = __fadd_rn(dw.y, 1.f);
-    const float Dn = __fdividef(__fmaf_rn(dw.y, dw.x, tau), Wn);
-    store_dw<F16>(md, vox, Dn, Wn);
-    fin = stored_dw<F16>(Dn, Wn);
+    store_dw<F16>(md, vox, __fdividef(__fmaf_rn(dw.y, dw.x, tau), Wn), Wn);
     ++n_upd;
     upd = true;
     remesh |= remesh_offsets(vi);
@@ -488,10 +478,8 @@ __device__ __forceinline__ bool tsdf_fast(const ScanConst &sc, const MapDev &md,
 // Returns true when the voxel also takes the class update.
 template <bool F16, bool DIST>
 __device__ __forceinline__ bool tsdf_band(const ScanConst &sc, const MapDev &md, int slot, int bx, int by, int bz,
-                                          const BandEntry &e, long long &n_upd, unsigned &remesh, bool &upd,
-                                          float2 &fin) {
+                                          const BandEntry &e, long long &n_upd, unsigned &remesh, bool &upd) {
     upd = false;
-    fin = make_float2(e.D, e.W);
     const float tau = sc.tau;
     const int vi = e.vi & (BV - 1), lx = vi & 7, ly = (vi >> 3) & 7, lz = vi >> 6;
     const float m0 = (float)(8 * bx + lx - sc.k[0]), m1 = (float)(8 * by + ly - sc.k[1]),
@@ -554,9 +542,7 @@ __device__ __forceinline__ bool tsdf_band(const ScanConst &sc, const MapDev &md,
         sdf = d >= 0.f ? fminf(d, tau) : fmaxf(d, -tau);
     }
     const float Wn = __fadd_rn(e.W, w);
-    const float Dn = __fdividef(__fmaf_rn(e.W, e.D, __fmul_rn(w, sdf)), Wn);
-    store_dw<F16>(md, (long long)slot * BV + vi, Dn, Wn);
-    fin = stored_dw<F16>(Dn, Wn);
+    store_dw<F16>(md, (long long)slot * BV + vi, __fdividef(__fmaf_rn(e.W, e.D, __fmul_rn(w, sdf)), Wn), Wn);
     ++n_upd;
     upd = true;
     remesh |= remesh_offsets(vi);
@@ -619,14 +605,9 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
         if (lane < n) {
             const BandEntry e = T.band[lane];
             bool upd;
-            float2 fin;
-            sem = tsdf_band<F16, DIST>(sc, md, slot, bx, by, bz, e, n_upd, remesh, upd, fin);
+            sem = tsdf_band<F16, DIST>(sc, md, slot, bx, by, bz, e, n_upd, remesh, upd);
             vox = slot * BV + (e.vi & (BV - 1));
             idx = (int)e.idx;
-            // the band voxel's bits, left clear by the main loop
-            const int rel = (e.vi & (BV - 1)) - v0;
-            if (fin.y > 0.f) atomicOr(&T.mask[rel >> 5], 1u << (rel & 31));
-            if (fin.x < 0.f) atomicOr(&T.mask[16 + (rel >> 5)], 1u << (rel & 31));
             if (DBG)
                 fd.dbg_vox[vox] = ((int)((unsigned)e.vi >> 9) + 1) | (upd ? 1 << 28 : 0) | (sem ? 1 << 29 : 0);
         }
@@ -657,26 +638,11 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
         da2 = __fadd_rn(da2, sc.Rt[8]);
         const unsigned long long wa = fd.win[pa < 0 ? 0 : pa], wb = fd.win[pb < 0 ? 0 : pb];
         bool ua, ub;
-        float2 fa, fb;
-        const bool ba = tsdf_fast<F16, DIST>(sc, md, va, vi, pa, wa, dwa, ra, ia, n_upd, remesh, ua, fa);
-        const bool bb = tsdf_fast<F16, DIST>(sc, md, vb, vi + 32, pb, wb, dwb, rb, ib, n_upd, remesh, ub, fb);
+        const bool ba = tsdf_fast<F16, DIST>(sc, md, va, vi, pa, wa, dwa, ra, ia, n_upd, remesh, ua);
+        const bool bb = tsdf_fast<F16, DIST>(sc, md, vb, vi + 32, pb, wb, dwb, rb, ib, n_upd, remesh, ub);
         if (DBG) {
             if (!ba) fd.dbg_vox[va] = (pa + 1) | (ua ? 1 << 28 : 0);
             if (!bb) fd.dbg_vox[vb] = (pb + 1) | (ub ? 1 << 28 : 0);
-        }
-        {
-            // bit masks of the stored values (band voxels: set when drained), before any drain below
-            const unsigned oa = __ballot_sync(0xffffffffu, !ba && fa.y > 0.f);
-            const unsigned na = __ballot_sync(0xffffffffu, !ba && fa.x < 0.f);
-            const unsigned ob = __ballot_sync(0xffffffffu, !bb && fb.y > 0.f);
-            const unsigned nbm = __ballot_sync(0xffffffffu, !bb && fb.x < 0.f);
-            const int w = (vi - lane - v0) >> 5;
-            if (lane == 0) {
-                T.mask[w] = oa;
-                T.mask[w + 1] = ob;
-                T.mask[16 + w] = na;
-                T.mask[17 + w] = nbm;
-            }
         }
         enqueue(ba, vi, wa, dwa, pa);
         if (qn >= 32) drain(32);
@@ -685,12 +651,6 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
     }
     if (qn > 0) drain(qn);
     __syncwarp();
-    {
-        // the voxels' bit masks: words (v0 / 32) .. of the block's observed and D < 0 planes
-        const int nw = (v1 - v0) >> 5;
-        const int j = lane & 15;
-        if (j < nw) md.vmask[(long long)slot * 32 + (lane >> 4) * 16 + (v0 >> 5) + j] = T.mask[(lane >> 4) * 16 + j];
-    }
     int2 *wbuf = T.wbuf;
     // one append of the block's class-update entries
     if (wcount) {
@@ -890,10 +850,11 @@ __device__ __forceinline__ void semantic_item(const ScanConst &sc, const MapDev 
 
 constexpr int MESH_WARPS = 8;   // warps (blocks in flight) per CTA
 
-// Per-warp state of one block's extraction: the bit masks of the 9^3 region
-// (block + upper faces) it works on.  Voxel rows run along x and are indexed
-// rw = y + 9 z; cube rows are indexed cy + 8 cz.
+// Per-warp staging of one block: the 9^3 region (block + upper faces) and
+// the bit masks the extraction works on.  Voxel rows run along x and are
+// indexed rw = y + 9 z; cube rows are indexed cy + 8 cz.
 struct MeshWarpSmem {
+    float D[729];
     uint32_t rowm[81];    // per voxel row: bits 0..8 observed (x = 0..8), bits 16..24 D < 0
     uint32_t ew[81];      // per voxel row: lattice edges that carry a vertex, from voxel (x, y, z):
                           // bits 0..7 +x edges (x = 0..7), 8..16 +y edges, 17..25 +z edges (x = 0..8)
@@ -901,8 +862,8 @@ struct MeshWarpSmem {
     uint8_t okc[64];      // per cube row: cubes whose eight corners are observed (bit = ax)
     int nb[8];            // slots of this block (0) and its 7 upper neighbours, -1 if none
     union {
-        uint32_t msk[8][32];  // while staging: the voxel bit masks (MapDev::vmask) of the 8 blocks
-        uint16_t mc[512];     // then: the cubes that emit triangles (ax + 8 (ay + 8 az)), in order
+        uint4 F4[81];     // while staging: per voxel row, 16 bytes, byte x: bit 0 observed (W > 0), bit 1 D < 0
+        uint16_t mc[512]; // then: the cubes that emit triangles (ax + 8 (ay + 8 az)), in order
     } u;
 };
 
@@ -968,34 +929,78 @@ __device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev
     int bx, by, bz;
     unpack_block(md.slot_key[slot], bx, by, bz);
     // slots of the 7 upper neighbours, from the per-slot links
-    const int nbv = lane == 0 ? slot : (lane < 8 ? md.nbr[slot * 16 + lane] : -1);
-    if (lane < 8) W.nb[lane] = nbv;
-    // the 8 blocks' voxel bit masks (kept by every writer of {D, W}): one 128-byte row each,
-    // zero for a missing neighbour (nothing observed)
-#pragma unroll
-    for (int o = 0; o < 8; ++o) {
-        const int s = __shfl_sync(0xffffffffu, nbv, o);
-        W.u.msk[o][lane] = s >= 0 ? md.vmask[(long long)s * 32 + lane] : 0u;
+    if (lane < 8) W.nb[lane] = lane == 0 ? slot : md.nbr[slot * 16 + lane];
+    int seen = 0;   // bit 0: an observed voxel with D < 0, bit 1: one with D >= 0
+    uint8_t *F = reinterpret_cast<uint8_t *>(W.u.F4);
+    // region voxel (x, y, z): D at x + 9 (y + 9 z), flags at x + 16 (y + 9 z)
+    auto put = [&](int r, int fi, float2 dw) {
+        const int f = (dw.y > 0.f ? 1 : 0) | (dw.x < 0.f ? 2 : 0);
+        W.D[r] = dw.x;
+        F[fi] = (uint8_t)f;
+        if (f & 1) seen |= (f & 2) ? 1 : 2;
+    };
+    // the block's own 512 voxels, two neighbours along x per read (16 bytes FP32, 8 FP16)
+#pragma unroll 4
+    for (int p = lane; p < BV / 2; p += 32) {
+        const int v = 2 * p, row = v >> 3, x = v & 7;            // row = y + 8 z
+        const int yz9 = (row & 7) + 9 * (row >> 3);               // y + 9 z
+        float2 a, b;
+        if (f32) {
+            const float4 q = reinterpret_cast<const float4 *>(md.dw32)[((long long)slot * BV + v) >> 1];
+            a = make_float2(q.x, q.y);
+            b = make_float2(q.z, q.w);
+        } else {
+            const uint2 q = reinterpret_cast<const uint2 *>(md.dw16)[((long long)slot * BV + v) >> 1];
+            a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
+            b = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
+        }
+        put(x + 9 * yz9, x + 16 * yz9, a);
+        put(x + 1 + 9 * yz9, x + 1 + 16 * yz9, b);
     }
     __syncwarp();
-    // row masks of the 81 voxel rows: x < 8 from the block holding the row (this block, +y, +z or
-    // +y+z), x = 8 from that block's +x neighbour (local x = 0)
-    int seen = 0;   // bit 0: an observed voxel with D < 0, bit 1: one with D >= 0
-    for (int rw = lane; rw < 81; rw += 32) {
-        const int y = rw % 9, z = rw / 9;
-        const int ob = ((y >> 3) << 1) | ((z >> 3) << 2);
-        const int base = 8 * (y & 7) + 64 * (z & 7);
-        const int w = base >> 5, sh = base & 31;
-        const uint32_t lo = (W.u.msk[ob][w] >> sh) & 0xffu, ln = (W.u.msk[ob][16 + w] >> sh) & 0xffu;
-        const uint32_t hi = (W.u.msk[ob | 1][w] >> sh) & 1u, hn = (W.u.msk[ob | 1][16 + w] >> sh) & 1u;
-        const uint32_t obs = lo | (hi << 8), ng = ln | (hn << 8);
-        W.rowm[rw] = obs | (ng << 16);
-        if (obs & ng) seen |= 1;
-        if (obs & ~ng) seen |= 2;
+    auto nb_dw = [&](int s, int local) -> float2 {
+        if (s < 0) return make_float2(0.f, 0.f);
+        const long long vox = (long long)s * BV + local;
+        return f32 ? md.dw32[vox] : __half22float2(md.dw16[vox]);
+    };
+    // x = 8 face (rows y + 9 z = j): local x = 0 of the +x neighbours
+    for (int j = lane; j < 81; j += 32) {
+        const int y = j % 9, z = j / 9;
+        const int s = W.nb[1 | ((y >> 3) << 1) | ((z >> 3) << 2)];
+        put(8 + 9 * j, 8 + 16 * j, nb_dw(s, 8 * (y & 7) + 64 * (z & 7)));
+    }
+    // y = 8 face (x < 8, z = 0..8): local y = 0 of the +y neighbours
+    for (int j = lane; j < 72; j += 32) {
+        const int x = j & 7, z = j >> 3;
+        const int s = W.nb[2 | ((z >> 3) << 2)];
+        const int yz9 = 8 + 9 * z;
+        put(x + 9 * yz9, x + 16 * yz9, nb_dw(s, x + 64 * (z & 7)));
+    }
+    // z = 8 face (x < 8, y < 8): local z = 0 of the +z neighbour
+    {
+        const int s = W.nb[4];
+        for (int j = lane; j < 64; j += 32) {
+            const int x = j & 7, y = j >> 3;
+            const int yz9 = y + 72;
+            put(x + 9 * yz9, x + 16 * yz9, nb_dw(s, x + 8 * y));
+        }
     }
     const bool any_neg = __any_sync(0xffffffffu, seen & 1), any_pos = __any_sync(0xffffffffu, seen & 2);
     int tot_m = 0;
     if (any_neg && any_pos) {
+        __syncwarp();
+        // row masks of the 81 voxel rows
+        // (bit 0, resp. 1, of four bytes gathered into 4 bits by one multiply: the
+        // products b_i 2^(8i) 2^(24-7k) land on bit 24 + i for i = k, below bit 20
+        // for i < k without overlapping, and beyond bit 31 for i > k)
+        for (int rw = lane; rw < 81; rw += 32) {
+            const uint4 q = W.u.F4[rw];
+            const uint32_t ob = (((q.x & 0x01010101u) * 0x01020408u) >> 24) |
+                                ((((q.y & 0x01010101u) * 0x01020408u) >> 24) << 4) | ((q.z & 1u) << 8);
+            const uint32_t ng = ((((q.x >> 1) & 0x01010101u) * 0x01020408u) >> 24) |
+                                (((((q.y >> 1) & 0x01010101u) * 0x01020408u) >> 24) << 4) | (((q.z >> 1) & 1u) << 8);
+            W.rowm[rw] = ob | (ng << 16);
+        }
         __syncwarp();
         // cube rows 2 lane and 2 lane + 1: observed cubes, and the emitting ones among them
         uint32_t mixl = 0;
@@ -1010,8 +1015,7 @@ __device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev
             mixl |= (ok & (nn | (nn >> 1)) & ~(na & (na >> 1)) & 0xffu) << (8 * q);
         }
         const int moff = warp_exclusive_scan(__popc(mixl), tot_m);
-        // the staged masks are dead: list the emitting cubes in their place (cube 16 lane + b)
-        __syncwarp();
+        // the staging flags are dead: list the emitting cubes in their place (cube 16 lane + b)
         for (int o = moff; mixl; ++o) {
             const int b = __ffs(mixl) - 1;
             mixl &= mixl - 1u;
@@ -1105,14 +1109,7 @@ __device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev
             const int x = q - (axis == 0 ? 0 : (axis == 1 ? 8 : 17)), y = rw % 9, z = rw / 9;
             const int r0 = x + 9 * rw;
             const int r1 = r0 + (axis == 0 ? 1 : (axis == 1 ? 9 : 81));
-            // the two endpoints' stored D (both observed, so their blocks exist)
-            auto region_D = [&](int r) {
-                const int ex = r % 9, ey = (r / 9) % 9, ez = r / 81;
-                const int es = W.nb[(ex >> 3) | ((ey >> 3) << 1) | ((ez >> 3) << 2)];
-                const long long vox = (long long)es * BV + (ex & 7) + 8 * (ey & 7) + 64 * (ez & 7);
-                return f32 ? md.dw32[vox].x : __half2float(md.dw16[vox].x);
-            };
-            const float D0 = region_D(r0), D1 = region_D(r1);
+            const float D0 = W.D[r0], D1 = W.D[r1];
             const float t = D0 / (D0 - D1);
             const int gx = 8 * bx + x, gy = 8 * by + y, gz = 8 * bz + z;
             float px = md.nu * (float)gx, py = md.nu * (float)gy, pz = md.nu * (float)gz;

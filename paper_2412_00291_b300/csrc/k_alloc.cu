@@ -116,23 +116,10 @@ __global__ void k_write_block(MapDev md, uint64_t key, const float *D, const flo
     __syncthreads();
     const int slot = s_slot;
     if (slot < 0) return;
-    for (int v = threadIdx.x; v < BV; v += blockDim.x) {   // blockDim a multiple of 32 dividing 512
+    for (int v = threadIdx.x; v < BV; v += blockDim.x) {
         const long long vox = (long long)slot * BV + v;
-        float2 st;
-        if (md.storage == 0) {
-            st = make_float2(D[v], W[v]);
-            md.dw32[vox] = st;
-        } else {
-            const __half2 h = __floats2half2_rn(D[v], W[v]);
-            md.dw16[vox] = h;
-            st = __half22float2(h);
-        }
-        // observed / D < 0 bit masks of the stored values (one word per 32 voxels)
-        const unsigned mo = __ballot_sync(0xffffffffu, st.y > 0.f), mn = __ballot_sync(0xffffffffu, st.x < 0.f);
-        if ((threadIdx.x & 31) == 0) {
-            md.vmask[(long long)slot * 32 + (v >> 5)] = mo;
-            md.vmask[(long long)slot * 32 + 16 + (v >> 5)] = mn;
-        }
+        if (md.storage == 0) md.dw32[vox] = make_float2(D[v], W[v]);
+        else md.dw16[vox] = __floats2half2_rn(D[v], W[v]);
         int best = 0;
         float bv = -INFINITY;
         for (int c = 0; c < md.C; ++c) {

@@ -182,7 +182,7 @@ static void prof_clear(map_t *m) {
 static void free_all(map_t *m) {
     prof_clear(m);
     void *ptrs[] = {m->md.hs, m->md.dstamp_slot, m->md.dw32, m->md.dw16, m->md.lp32,
-                    m->md.lp16, m->md.label, m->md.vmask, m->md.slot_key, m->md.slot_frame, m->md.nbr, m->md.seg, m->md.av, m->md.ak, m->md.at,
+                    m->md.lp16, m->md.label, m->md.slot_key, m->md.slot_frame, m->md.nbr, m->md.seg, m->md.av, m->md.ak, m->md.at,
                     m->av_alt, m->ak_alt, m->at_alt, m->st, m->ctr_pair, m->d_ring, m->win_buf[0], m->win_buf[1],
                     m->fd.touched, m->fd.dirty, m->fd.sem_list, m->gb.voff, m->gb.toff, m->gb.bsum_v, m->gb.bsum_t,
                     m->gb.totals, m->stage_pts[0], m->stage_lab[0], m->stage_probs[0], m->stage_pts[1],
@@ -289,7 +289,6 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
         ALLOC(md.lp16, nvox * md.CP);
     }
     ALLOC(md.label, nvox);
-    ALLOC(md.vmask, nb * 32);
     if (c.distance_mode == 1) {
         if (c.storage == 0) ALLOC(md.g32, nvox * 3);
         else ALLOC(md.g16, nvox * 3);
@@ -368,7 +367,6 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     cudaMemsetAsync(md.dstamp_slot, 0xFF, nb * sizeof(int), s);
     cudaMemsetAsync(md.slot_frame, 0xFF, nb * sizeof(int), s);
     cudaMemsetAsync(md.nbr, 0xFF, nb * 16 * sizeof(int), s);
-    cudaMemsetAsync(md.vmask, 0, nb * 32 * sizeof(uint32_t), s);   // nothing observed
     // no gradient before a voxel's first normal
     if (md.g32) cudaMemsetAsync(md.g32, 0, (size_t)nvox * 3 * sizeof(float), s);
     if (md.g16) cudaMemsetAsync(md.g16, 0, (size_t)nvox * 3 * sizeof(__half), s);
