@@ -14,7 +14,6 @@ constexpr int BV = BS * BS * BS;
 constexpr uint64_t EMPTY_KEY = ~0ull;
 constexpr int MAX_PROBES = 256;       // linear-probing bound of the block hash
 constexpr int MAX_AXIS_CROSS = 4;     // band may cross <= 4 block planes per axis (tau <= 16 nu)
-constexpr int MAX_BAND_BLOCKS = 1 + 3 * MAX_AXIS_CROSS;
 constexpr int MC_MAXTRI = 8;          // triangles per cube case in the generated table
 constexpr float PI_F = 3.14159265358979f;
 
@@ -226,17 +225,6 @@ __device__ __forceinline__ float range_f32(float x, float y, float z) {
     s = __fadd_rn(s, __fmul_rn(y, y));
     s = __fadd_rn(s, __fmul_rn(z, z));
     return __fsqrt_rn(s);
-}
-
-// Pixel of a valid LiDAR-frame point (Sec. III-C.1), -1 when its beam row is outside [0, H).
-__device__ __forceinline__ int point_pixel(const ScanConst &sc, float x, float y, float z, float l) {
-    const float uc = (PI_F - atan2f(y, x)) * sc.inv_dphi;
-    const float vc = (acosf(fminf(fmaxf(z / l, -1.f), 1.f)) - sc.theta0) * sc.inv_dtheta;
-    int u = (int)floorf(uc + 0.5f);
-    const int v = (int)floorf(vc + 0.5f);
-    if (u >= sc.W) u -= sc.W;
-    if (u < 0) u += sc.W;
-    return (v >= 0 && v < sc.H) ? v * sc.W + u : -1;
 }
 
 __device__ __forceinline__ int hash_find(const HashSlot *__restrict__ hs, uint64_t mask, uint64_t key) {

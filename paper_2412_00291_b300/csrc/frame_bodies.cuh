@@ -10,76 +10,107 @@
 
 namespace stsdf {
 
-// Blocks met by the band of one point, in path order; returns their count.
-__device__ __forceinline__ int band_blocks(const ScanConst &sc, float x0, float x1, float x2, float l, int (*out)[3]) {
+// atan2(y, x) in (-pi, pi] from the atan polynomial on [0, 1] and the octant
+// symmetries; error below 5e-7 rad (polynomial 1.8e-7, the quotient and the
+// octant subtractions one rounding each), atan2(+-0, x < 0) = +-pi as atan2f.
+__device__ __forceinline__ float atan2_poly(float y, float x) {
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float t = mx > 0.f ? __fdividef(mn, mx) : 0.f;
+    const float p = atan_p(__fmul_rn(t, t));
+    float a = ay > ax ? __fmaf_rn(-t, p, 1.57079632679489662f) : __fmul_rn(t, p);
+    if (x < 0.f) a = __fsub_rn(PI_F, a);
+    return copysignf(a, y);
+}
+
+// acos(c) for c in [-1, 1]: pi/2 - asin(c) from the asin polynomial when
+// |c| <= 1/2 (error below 3e-7 rad), acosf beyond.
+__device__ __forceinline__ float acos_poly(float c) {
+    if (fabsf(c) > 0.5f) return acosf(c);
+    return __fmaf_rn(-c, asin_q(__fmul_rn(c, c)), 1.57079632679489662f);
+}
+
+// Blocks met by the band of one point, visited in path order without storing
+// them (registers only): a 3-D digital differential analyser over the lattice
+// of 8-voxel blocks.  The band [p - tau d, p + tau d] (start clipped to the
+// sensor when r < tau) is taken in voxel units plus one half, so that block b
+// occupies [8 b, 8 b + 8) on every axis: e = t / nu + 1/2 + (R x / nu) f with
+// f = max(0, 1 - tau / r) and 1 + tau / r at the two ends, each operation one
+// IEEE single-precision rounding.  From the block of e0, each step crosses
+// the block plane (or, on equal parameters, the planes) that the segment
+// reaches first, t = (plane - e0) / (e1 - e0), until the block of e1.
+struct BandWalk {
+    float e0[3], d[3];
+    float tn[3];      // parameter of the next plane crossing on each axis (infinite: none left)
+    int cur[3];       // current block
+    int rem[3];       // planes still to cross on each axis
+    int step[3];      // direction of the crossings (+1 / -1)
+    bool fresh;       // cur not yet yielded
+    bool live;        // blocks left to yield
+};
+
+__device__ __forceinline__ void band_begin(const ScanConst &sc, float x0, float x1, float x2, float l, BandWalk &w) {
     const float q = __fdiv_rn(sc.tau, l);
     float f0 = __fsub_rn(1.f, q);
     if (f0 < 0.f) f0 = 0.f;
     const float f1 = __fadd_rn(1.f, q);
-    float e0[3], e1[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         float s = __fmul_rn(sc.Rv[3 * k], x0);
         s = __fadd_rn(s, __fmul_rn(sc.Rv[3 * k + 1], x1));
         s = __fadd_rn(s, __fmul_rn(sc.Rv[3 * k + 2], x2));
-        e0[k] = __fadd_rn(sc.tv[k], __fmul_rn(s, f0));
-        e1[k] = __fadd_rn(sc.tv[k], __fmul_rn(s, f1));
+        const float a = __fadd_rn(sc.tv[k], __fmul_rn(s, f0));
+        const float e = __fadd_rn(sc.tv[k], __fmul_rn(s, f1));
+        const int b0 = (int)floorf(__fmul_rn(a, 0.125f));
+        const int b1 = (int)floorf(__fmul_rn(e, 0.125f));
+        w.e0[k] = a;
+        w.d[k] = __fsub_rn(e, a);
+        w.cur[k] = b0;
+        w.step[k] = b1 >= b0 ? 1 : -1;
+        w.rem[k] = min(abs(b1 - b0), MAX_AXIS_CROSS);
+        // first plane: 8 (b0 + 1) going up, 8 b0 going down
+        const float plane = (float)(8 * (b1 > b0 ? b0 + 1 : b0));
+        w.tn[k] = w.rem[k] > 0 ? __fdiv_rn(__fsub_rn(plane, a), w.d[k]) : INFINITY;
     }
-    // crossing events: parameter, kind (0: entered at t, 1: left after t), axis, step
-    float et[3 * MAX_AXIS_CROSS];
-    int einfo[3 * MAX_AXIS_CROSS];
-    int ne = 0;
-    int cur[3];
+    w.fresh = true;
+    w.live = true;
+}
+
+// The next block of the walk; false when none is left.
+__device__ __forceinline__ bool band_next(BandWalk &w, int &bx, int &by, int &bz) {
+    if (!w.live) return false;
+    if (!w.fresh) {
+        const float t = fminf(w.tn[0], fminf(w.tn[1], w.tn[2]));
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int b0 = (int)floorf(__fmul_rn(e0[k], 0.125f));
-        const int b1 = (int)floorf(__fmul_rn(e1[k], 0.125f));
-        cur[k] = b0;
-        const float d = __fsub_rn(e1[k], e0[k]);
-        if (b1 > b0) {
-            for (int b = b0 + 1, c = 0; b <= b1 && c < MAX_AXIS_CROSS; ++b, ++c) {
-                et[ne] = __fdiv_rn(__fsub_rn((float)(8 * b), e0[k]), d);
-                einfo[ne++] = (0 << 4) | (k << 1) | 1;
-            }
-        } else if (b1 < b0) {
-            for (int b = b0, c = 0; b > b1 && c < MAX_AXIS_CROSS; --b, ++c) {
-                et[ne] = __fdiv_rn(__fsub_rn((float)(8 * b), e0[k]), d);
-                einfo[ne++] = (1 << 4) | (k << 1) | 0;
+        for (int k = 0; k < 3; ++k) {
+            if (w.rem[k] > 0 && w.tn[k] == t) {
+                w.cur[k] += w.step[k];
+                --w.rem[k];
+                const int next = w.step[k] > 0 ? w.cur[k] + 1 : w.cur[k];
+                w.tn[k] = w.rem[k] > 0 ? __fdiv_rn(__fsub_rn((float)(8 * next), w.e0[k]), w.d[k]) : INFINITY;
             }
         }
     }
-    // insertion sort by (t, kind)
-    for (int i = 1; i < ne; ++i) {
-        float t = et[i];
-        int inf = einfo[i];
-        int j = i - 1;
-        while (j >= 0 && (et[j] > t || (et[j] == t && (einfo[j] >> 4) > (inf >> 4)))) {
-            et[j + 1] = et[j];
-            einfo[j + 1] = einfo[j];
-            --j;
-        }
-        et[j + 1] = t;
-        einfo[j + 1] = inf;
-    }
-    int nb = 0;
-    out[nb][0] = cur[0];
-    out[nb][1] = cur[1];
-    out[nb][2] = cur[2];
-    ++nb;
-    for (int i = 0; i < ne;) {
-        int j = i;
-        while (j < ne && et[j] == et[i] && (einfo[j] >> 4) == (einfo[i] >> 4)) {
-            const int ax = (einfo[j] >> 1) & 3;
-            cur[ax] += (einfo[j] & 1) ? 1 : -1;
-            ++j;
-        }
-        out[nb][0] = cur[0];
-        out[nb][1] = cur[1];
-        out[nb][2] = cur[2];
-        ++nb;
-        i = j;
-    }
-    return nb;
+    w.fresh = false;
+    bx = w.cur[0];
+    by = w.cur[1];
+    bz = w.cur[2];
+    if (w.rem[0] == 0 && w.rem[1] == 0 && w.rem[2] == 0) w.live = false;
+    return true;
+}
+
+// Pixel of a valid LiDAR-frame point with range l (Sec. III-C.1), -1 when its
+// beam row is outside [0, H): polynomial atan2 / acos (error < 5e-7 rad, far
+// inside the 1e-3-pixel band within which FP32 and FP64 choices may differ).
+__device__ __forceinline__ int point_pixel_poly(const ScanConst &sc, float x, float y, float z, float l) {
+    const float uc = __fmul_rn(__fsub_rn(PI_F, atan2_poly(y, x)), sc.inv_dphi);
+    const float vc =
+        __fmul_rn(__fsub_rn(acos_poly(fminf(fmaxf(__fdiv_rn(z, l), -1.f), 1.f)), sc.theta0), sc.inv_dtheta);
+    int u = (int)floorf(__fadd_rn(uc, 0.5f));
+    const int v = (int)floorf(__fadd_rn(vc, 0.5f));
+    if (u >= sc.W) u -= sc.W;
+    if (u < 0) u += sc.W;
+    return (v >= 0 && v < sc.H) ? v * sc.W + u : -1;
 }
 
 // Find or insert a block key; lock-free (compare-and-swap on the key slot).
@@ -125,21 +156,22 @@ __device__ __forceinline__ int hash_insert(const MapDev &md, uint64_t key, int &
 // to `cnt`; the caller forms the totals.
 __device__ __forceinline__ void points_item(const float *__restrict__ pts, const ScanConst &sc, const MapDev &md,
                                             const FrameDev &fd, long long i, long long (&cnt)[3]) {
-    int nb = 0, valid = 0, inpix = 0, pix = -2;
-    int blocks[MAX_BAND_BLOCKS][3];
+    int valid = 0, inpix = 0, pix = -2;
+    BandWalk w;
+    w.live = false;
     if (i < sc.n) {
         const float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
         if (isfinite(x) && isfinite(y) && isfinite(z)) {
             const float l = range_f32(x, y, z);
             if (l >= sc.r_min && l <= sc.r_max && l > 0.f) {
                 valid = 1;
-                const int p = point_pixel(sc, x, y, z, l);
+                const int p = point_pixel_poly(sc, x, y, z, l);
                 pix = p;
                 if (p >= 0) {
                     inpix = 1;
                     atomicMin(&fd.win[p], ((unsigned long long)__float_as_uint(l) << 32) | (unsigned)i);
                 }
-                nb = band_blocks(sc, x, y, z, l, blocks);
+                band_begin(sc, x, y, z, l, w);
             }
         }
     }
@@ -153,17 +185,17 @@ __device__ __forceinline__ void points_item(const float *__restrict__ pts, const
     // the owners' first hash probes, then their frame-stamp exchanges, are all
     // in flight together, and the blocks first touched in this frame are
     // appended to U_k with one counter update per warp.
-    const int nb_max = __reduce_max_sync(0xffffffffu, (unsigned)nb);
-    for (int j0 = 0; j0 < nb_max; j0 += 4) {
+    while (__any_sync(0xffffffffu, w.live)) {
         uint64_t key[4];
         bool own[4];
         int h[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int j = j0 + q;
-            key[q] = j < nb ? pack_block(blocks[j][0], blocks[j][1], blocks[j][2]) : EMPTY_KEY;
+            int bx, by, bz;
+            const bool got = band_next(w, bx, by, bz);
+            key[q] = got ? pack_block(bx, by, bz) : EMPTY_KEY;
             const unsigned grp = __match_any_sync(0xffffffffu, key[q]);
-            own[q] = j < nb && __ffs(grp) - 1 == lane;
+            own[q] = got && __ffs(grp) - 1 == lane;
         }
         // the home slot's whole record: key, pool slot and frame stamp in one 16-byte load
         uint64_t probe[4];
@@ -266,26 +298,6 @@ static_assert(REMESH_TABLE == 0xFF5533110F050301ull, "re-mesh offset table");
 __device__ __forceinline__ unsigned remesh_offsets(int vi) {
     const int z = ((vi & 7) == 0 ? 1 : 0) | (((vi >> 3) & 7) == 0 ? 2 : 0) | ((vi >> 6) == 0 ? 4 : 0);
     return (unsigned)(REMESH_TABLE >> (8 * z)) & 0xffu;
-}
-
-// atan2(y, x) in (-pi, pi] from the atan polynomial on [0, 1] and the octant
-// symmetries; error below 5e-7 rad (polynomial 1.8e-7, the quotient and the
-// octant subtractions one rounding each), atan2(+-0, x < 0) = +-pi as atan2f.
-__device__ __forceinline__ float atan2_poly(float y, float x) {
-    const float ax = fabsf(x), ay = fabsf(y);
-    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-    const float t = mx > 0.f ? __fdividef(mn, mx) : 0.f;
-    const float p = atan_p(__fmul_rn(t, t));
-    float a = ay > ax ? __fmaf_rn(-t, p, 1.57079632679489662f) : __fmul_rn(t, p);
-    if (x < 0.f) a = __fsub_rn(PI_F, a);
-    return copysignf(a, y);
-}
-
-// acos(c) for c in [-1, 1]: pi/2 - asin(c) from the asin polynomial when
-// |c| <= 1/2 (error below 3e-7 rad), acosf beyond.
-__device__ __forceinline__ float acos_poly(float c) {
-    if (fabsf(c) > 0.5f) return acosf(c);
-    return __fmaf_rn(-c, asin_q(__fmul_rn(c, c)), 1.57079632679489662f);
 }
 
 // Direction of voxel vi of block (bx, by, bz) from the sensor, in the LiDAR
