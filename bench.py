@@ -175,9 +175,10 @@ def algorithmic_bytes(st, n_points, H, W, C, s, nonproj=False):
     semantic: C log-probabilities read and written (2 C s B), the label byte
               and the 8 B list entry per semantically updated voxel (the
               winners' class inputs are L2 reads).
-    mesh:     {D, W} (2s B) of the 512 own voxels and the segment record (16 B) per
-              re-meshed block, 24 B per vertex and 8 B per triangle emitted
-              (neighbour faces are re-reads; vertex classes are read at extraction).
+    mesh:     {D, W} (2s B) of the 512 own voxels and of the 217 voxels of the upper
+              neighbours' faces it stages, the segment record (16 B) per re-meshed block,
+              24 B per vertex and 8 B per triangle emitted (vertex classes are read at
+              extraction, not here).
     """
     upd, sem, touched, dirty, mv, mt = st[4], st[5], st[2], st[6], st[7], st[8]
     return {
@@ -185,8 +186,20 @@ def algorithmic_bytes(st, n_points, H, W, C, s, nonproj=False):
         "points": n_points * 12 + (H * W * 16 if nonproj else 0),
         "tsdf": upd * 2 * (2 * s) + sem * 8 + touched * 16 + (upd * 2 * 3 * s if nonproj else 0),
         "semantic": sem * (2 * C * s + 1 + 8),
-        "mesh": dirty * (512 * 2 * s + 16) + mv * 24 + mt * 8,
+        "mesh": dirty * ((512 + 217) * 2 * s + 16) + mv * 24 + mt * 8,
     }
+
+
+def survey_model_bytes(st, n_points, H, W, C, s, probs):
+    """The frame's bytes by the byte model the method's scope table states, per scan:
+    inputs (12 B per point, plus C x 4 B of probabilities or a 4 B label), the range image
+    (8 B per pixel written and read), the TSDF (512 x 2s read per touched block, 2s written per
+    updated voxel), the classes (C x s read and written per class-updated voxel), marching cubes
+    (512 x 2s per re-meshed block, 7 x 64 x 2s of neighbour faces, C x s of class reads per
+    vertex, 16 B per vertex and 12 B per triangle out).  Hash probes (mostly L2) are not counted."""
+    upd, sem, touched, dirty, mv, mt = st[4], st[5], st[2], st[6], st[7], st[8]
+    return (n_points * (12 + (C * 4 if probs else 4)) + 2 * H * W * 8 + touched * 512 * 2 * s + upd * 2 * s +
+            sem * 2 * C * s + dirty * (512 + 7 * 64) * 2 * s + mv * (C * s + 16) + mt * 12)
 
 
 class ClockSampler:
@@ -528,7 +541,7 @@ def run_ours(args, rank, world, local_rank):
         tsdf.remesh_all()                  # one more pass, untimed, for its counters
         fs = tsdf.stats()
         blocks, nv, nt = fs["dirty_blocks"], fs["mesh_vertices"], fs["mesh_triangles"]
-        fbytes = blocks * (512 * 2 * s_bytes + 16) + 24 * nv + 8 * nt
+        fbytes = blocks * ((512 + 217) * 2 * s_bytes + 16) + 24 * nv + 8 * nt
         peak_fm, _ = measured_peaks()
         last_final = (args.warmup + args.steps) % K == 0     # the last timed pass meshed the final map
         full_mesh = {"every_scans": K, "passes_timed": int(len(fm)), "ms_median": float(np.median(fm)),
@@ -556,6 +569,20 @@ def run_ours(args, rank, world, local_rank):
         step(args.warmup + i)
     torch.cuda.synchronize()
     phase_ms, fstats = P.map_profile_end(tsdf.h, args.steps)
+    # --- pass 3: the same scans, class update after the re-meshing (each kernel alone) ---
+    tsdf_iso = P.SemanticTSDF(w.voxel_size, w.truncation, C, storage=storage, **cfg)
+    tsdf_iso.set_concurrent_phases(False)
+    step = make_step(tsdf_iso)
+    for k in range(args.warmup):
+        step(k)
+    tsdf_iso.stats()
+    P.map_profile_begin(tsdf_iso.h, args.steps)
+    for i in range(args.steps):
+        flush.zero_()
+        step(args.warmup + i)
+    torch.cuda.synchronize()
+    phase_iso, fstats_iso = P.map_profile_end(tsdf_iso.h, args.steps)
+    tsdf_iso.close()
     qual = None
     if args.quality:
         qual = quality_report(P, w, tsdf, args.warmup + args.steps, dev)
@@ -571,10 +598,15 @@ def run_ours(args, rank, world, local_rank):
         if name == "reset":
             continue
         bytes_f = np.array([algorithmic_bytes(fs, n_points, L.H, L.W, C, s_bytes, nonproj)[name] for fs in fstats], float)
+        bytes_i = np.array([algorithmic_bytes(fs, n_points, L.H, L.W, C, s_bytes, nonproj)[name] for fs in fstats_iso],
+                           float)
         t = phase_ms[:, j].astype(float)
+        ti = phase_iso[:, j].astype(float)
+        g = float(bytes_f.sum() / (t.sum() * 1e-3) / 1e9)
+        gi = float(bytes_i.sum() / (ti.sum() * 1e-3) / 1e9)
         per_kernel[name] = {"ms_mean": float(t.mean()), "share": float(t.sum() / phase_ms.sum()),
-                            "bytes_mean": float(bytes_f.mean()),
-                            "gbs": float(bytes_f.sum() / (t.sum() * 1e-3) / 1e9)}
+                            "bytes_mean": float(bytes_f.mean()), "gbs": g, "frac": g / peak,
+                            "ms_isolated": float(ti.mean()), "gbs_isolated": gi, "frac_isolated": gi / peak}
     # k_semantic and k_mesh run concurrently after k_tsdf: the stage lasts max of the two
     js, jm = PHASES.index("semantic"), PHASES.index("mesh")
     stage_t = np.maximum(phase_ms[:, js], phase_ms[:, jm]).astype(float)
@@ -587,11 +619,16 @@ def run_ours(args, rank, world, local_rank):
     # captured variants: FP32 storage, either distance (no FP16-storage capture: traffic null there)
     tr = traffic_record(dom, "_nonproj" if nonproj else "") if storage == 0 else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "timing": "the kernel's CUDA-event time in the scan as run (the class update and the re-meshing "
+                      "concurrently)",
+            "achieved_isolated": per_kernel[dom]["gbs_isolated"], "frac_isolated": per_kernel[dom]["frac_isolated"],
             "nominal_peak": 7700.0, "frac_nominal": ach / 7700.0,
             "peak_source": f"{peak_kind} hbm_gbs", "traffic": tr["bytes_per_launch"] if tr else None,
             "algorithmic_bytes_per_launch": per_kernel[dom]["bytes_mean"]}
     frame_bytes = float(np.mean([sum(algorithmic_bytes(fs, n_points, L.H, L.W, C, s_bytes, nonproj).values())
                                  for fs in fstats]))
+    frame_bytes_survey = float(np.mean([survey_model_bytes(fs, n_points, L.H, L.W, C, s_bytes, bool(pr_d))
+                                        for fs in fstats]))
     # --- end to end through the host-buffer entry point ----------------------
     # Every step: the scan's inputs from pinned host memory (H->D), the scan,
     # and a D->H read of its counters.  The steps are pipelined as a serving
@@ -656,6 +693,10 @@ def run_ours(args, rank, world, local_rank):
                    "bracketed_wall_s_incl_flush": t_wall, "parallelism": f"replicas x{world}",
                    "frame_algorithmic_bytes": frame_bytes,
                    "frame_gbs": frame_bytes / (total_ms / args.steps * 1e-3) / 1e9,
+                   "frame_frac": frame_bytes / (total_ms / args.steps * 1e-3) / 1e9 / peak,
+                   "frame_bytes_survey_model": frame_bytes_survey,
+                   "frame_gbs_survey_model": frame_bytes_survey / (total_ms / args.steps * 1e-3) / 1e9,
+                   "frame_frac_survey_model": frame_bytes_survey / (total_ms / args.steps * 1e-3) / 1e9 / peak,
                    "touched_blocks_mean": float(fstats[:, 2].mean()),
                    "voxels_updated_mean": float(fstats[:, 4].mean()),
                    "voxels_semantic_mean": float(fstats[:, 5].mean()),
@@ -664,7 +705,9 @@ def run_ours(args, rank, world, local_rank):
         "kernels": per_kernel,
         "kernels_note": "per-kernel times from a second pass over the same scans with CUDA events around "
                         "each kernel on its stream; k_semantic and k_mesh run concurrently (two streams), so "
-                        "the shares are of the summed kernel times",
+                        "the shares are of the summed kernel times; *_isolated: a third pass with the class "
+                        "update after the re-meshing (each kernel alone); frac = algorithmic GB/s / measured "
+                        "peak",
         "concurrent_semantic_and_mesh": stage,
         "full_mesh": full_mesh,
         "quality": qual,

@@ -521,6 +521,13 @@ enum {
  * integrate_scan calls (earlier recording is discarded). */
 map_status map_profile_begin(map_t *map, int32_t max_frames);
 
+/* Concurrency of a scan's last two phases: 1 (default) runs the class update
+ * on a second stream beside the re-meshing (it reads no class), joined before
+ * integrate_scan returns; 0 runs the class update after the re-meshing on the
+ * scan's stream, so each phase has the GPU to itself (to time the kernels
+ * alone).  MAP_ERR_ARG for other values.  The results are the same. */
+map_status map_set_concurrent_phases(map_t *map, int32_t concurrent);
+
 /* Stop recording; synchronises.  ms_out[max_frames][MAP_PHASE_COUNT]
  * receives each recorded frame's phase durations in milliseconds,
  * stats_out[max_frames][MAP_STAT_COUNT] (may be NULL) its per-frame

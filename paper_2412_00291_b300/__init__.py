@@ -70,6 +70,7 @@ _SIGS = {
     "map_create": ([P, P], I32),
     "map_check_scan_pose": ([P, P, P], I32),
     "map_set_decision_record": ([P, I32], I32),
+    "map_set_concurrent_phases": ([P, I32], I32),
     "map_read_decision_record": ([P, P, I64, P, I64, P, I64, P, P], I32),
     "map_destroy": ([P], I32),
     "integrate_scan": ([P, P, P, P, P, I64, P, P], I32),
@@ -303,6 +304,11 @@ def map_read_decision_record(h, n_points, n_pixels):
                                          ctypes.byref(nt), _np_ptr(vx)), h)
     assert nt.value == k
     return dict(point_pix=pp[:n_points], winner=wi[:n_pixels], touched=tb[:k], vox=vx[:k])
+
+
+def map_set_concurrent_phases(h, concurrent: bool):
+    """True (default): class update beside the re-meshing; False: after it (each phase alone)."""
+    _check(_lib.map_set_concurrent_phases(h, 1 if concurrent else 0), h)
 
 
 def map_remesh_all(h, stream=None):
@@ -623,6 +629,9 @@ class SemanticTSDF:
 
     def mesh(self, stream=None):
         return extract_mesh(self.h, stream)
+
+    def set_concurrent_phases(self, concurrent=True):
+        map_set_concurrent_phases(self.h, concurrent)
 
     def record_decisions(self, enable=True):
         map_set_decision_record(self.h, enable)

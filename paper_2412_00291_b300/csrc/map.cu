@@ -113,9 +113,11 @@ struct map_t {
     double *qb_part = nullptr;   // pose-gradient partial sums of query_sdf_backward
     int frame = 0;
     bool mesh_per_frame = true;     // incremental re-meshing in every integrate_scan
+    bool concurrent = true;         // class update beside the re-meshing (second stream)
     int grid_integrate = 0, grid_mesh = 0, grid_semantic = 0;
     // phase profiling: (MAP_PHASE_COUNT + 1) events per recorded frame
     std::vector<cudaEvent_t> prof_ev;
+    std::vector<char> prof_serial;              // per recorded frame: phases run one after the other
     int prof_cap = 0, prof_n = 0;
     unsigned long long *prof_stats = nullptr;   // device [prof_cap][CT_COUNT]
     long long launches = 0;                     // kernels launched by this map
@@ -700,6 +702,7 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     unsigned long long *ev_stats = nullptr;
     if (m->prof_n < m->prof_cap) {
         ev_stats = m->prof_stats + (size_t)m->prof_n * CT_COUNT;
+        m->prof_serial[m->prof_n] = m->concurrent ? 0 : 1;
         ev = &m->prof_ev[(size_t)m->prof_n++ * (MAP_PHASE_COUNT + 1)];
     }
     if (ev) CU(cudaEventRecord(ev[0], s));
@@ -727,15 +730,24 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     if (ev) CU(cudaEventRecord(ev[2], s));
     launch_integrate(sc, m->md, m->fd, m->grid_integrate, s);
     if (ev) CU(cudaEventRecord(ev[3], s));
-    // class update on the side stream, re-meshing on the caller's, concurrently
-    CU(cudaEventRecord(m->ev_fork, s));
-    CU(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
-    launch_semantic(sc, m->md, m->fd, m->grid_semantic, m->side);
-    if (ev) CU(cudaEventRecord(ev[4], m->side));
-    if (m->mesh_per_frame) launch_mesh(m->md, m->fd, m->grid_mesh, s);
-    if (ev) CU(cudaEventRecord(ev[5], s));
-    CU(cudaEventRecord(m->ev_join, m->side));
-    CU(cudaStreamWaitEvent(s, m->ev_join, 0));
+    if (m->concurrent) {
+        // class update on the side stream, re-meshing on the caller's, concurrently
+        CU(cudaEventRecord(m->ev_fork, s));
+        CU(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
+        launch_semantic(sc, m->md, m->fd, m->grid_semantic, m->side);
+        if (ev) CU(cudaEventRecord(ev[4], m->side));
+        if (m->mesh_per_frame) launch_mesh(m->md, m->fd, m->grid_mesh, s);
+        if (ev) CU(cudaEventRecord(ev[5], s));
+        CU(cudaEventRecord(m->ev_join, m->side));
+        CU(cudaStreamWaitEvent(s, m->ev_join, 0));
+    } else {
+        // one after the other on the caller's stream: re-meshing (a programmatic dependent of the
+        // TSDF grid, as above), then the class update
+        if (m->mesh_per_frame) launch_mesh(m->md, m->fd, m->grid_mesh, s);
+        if (ev) CU(cudaEventRecord(ev[5], s));
+        launch_semantic(sc, m->md, m->fd, m->grid_semantic, s);
+        if (ev) CU(cudaEventRecord(ev[4], s));
+    }
     m->launches += m->mesh_per_frame ? 4 : 3;
     if (ev_stats)
         CU(cudaMemcpyAsync(ev_stats, m->fd.ctr, CT_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
@@ -819,6 +831,13 @@ extern "C" map_status map_remesh_all(map_t *m, void *stream) {
     // map_get_frame_stats now reports this pass (blocks meshed, vertices, triangles)
     CU(cudaMemcpyAsync(m->h_ctr, m->fd.ctr, CT_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     m->h_ctr_slot = -1;
+    return MAP_OK;
+}
+
+extern "C" map_status map_set_concurrent_phases(map_t *m, int32_t concurrent) {
+    if (!m) return fail(nullptr, MAP_ERR_ARG, "null map");
+    if (concurrent != 0 && concurrent != 1) return fail(m, MAP_ERR_ARG, "concurrent must be 0 or 1");
+    m->concurrent = concurrent == 1;
     return MAP_OK;
 }
 
@@ -1361,6 +1380,7 @@ extern "C" map_status map_profile_begin(map_t *m, int32_t max_frames) {
     if (!m || max_frames < 0) return fail(m, MAP_ERR_ARG, "bad arguments");
     prof_clear(m);
     m->prof_ev.resize((size_t)max_frames * (MAP_PHASE_COUNT + 1));
+    m->prof_serial.assign((size_t)max_frames, 0);
     for (auto &e : m->prof_ev) CU(cudaEventCreate(&e));
     if (max_frames > 0) {
         CU(cudaMalloc(&m->prof_stats, (size_t)max_frames * CT_COUNT * sizeof(unsigned long long)));
@@ -1379,8 +1399,10 @@ extern "C" map_status map_profile_end(map_t *m, float *ms_out, int64_t *stats_ou
         CU(cudaEventSynchronize(ev[MAP_PHASE_COUNT]));
         CU(cudaEventSynchronize(ev[MAP_PHASE_SEMANTIC + 1]));
         for (int ph = 0; ph < MAP_PHASE_COUNT; ++ph) {
-            // the class update and the re-meshing both start at the end of the TSDF kernel
-            const int from = ph == MAP_PHASE_MESH ? MAP_PHASE_SEMANTIC : ph;
+            // the class update and the re-meshing both start at the end of the TSDF kernel, or,
+            // one after the other, the class update at the end of the re-meshing
+            int from = ph == MAP_PHASE_MESH ? MAP_PHASE_SEMANTIC : ph;
+            if (m->prof_serial[f] && ph == MAP_PHASE_SEMANTIC) from = MAP_PHASE_MESH + 1;
             float ms = 0.f;
             CU(cudaEventElapsedTime(&ms, ev[from], ev[ph + 1]));
             if (ms_out) ms_out[(size_t)f * MAP_PHASE_COUNT + ph] = ms;
