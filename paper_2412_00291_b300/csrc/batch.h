@@ -31,6 +31,7 @@ struct BatchArgs {
     BatchItem it[BATCH_MAX];
     int n;
     int fault_skip_cta0;     // test hook: CTA 0 leaves at once, the first barrier times out
+    int sem_staged;          // class update: 0 one voxel per thread, 1 / 2 warp-staged (FP32 / FP16 records)
     unsigned long long spin_limit;   // polls before a barrier wait gives up (0: default)
     BatchCtl *ctl;
     BatchState *out;

@@ -860,6 +860,123 @@ __device__ __forceinline__ void semantic_item(const ScanConst &sc, const MapDev 
     }
 }
 
+// --- the class update staged by a warp through shared memory ------------------
+// A lane's own 96-byte (FP32) or 64-byte (FP16) class record, loaded with one
+// 16-byte access per lane and instruction, touches a different cache line in
+// every lane, and the L1's tag lookups then bound the update; here the warp's
+// 32 lanes copy consecutive 16-byte chunks of the warp's 32 records (about five
+// records per instruction) into shared memory, update them there (class_update,
+// the same body as every other path) and write them back the same way.
+constexpr int SEM_NC = 20;    // the class count of the staged path
+template <bool F16>
+struct SemStage {
+    static constexpr int RC = F16 ? 4 : 6;    // 16-byte chunks per record (32 halves / 24 floats)
+    static constexpr int RB = 16 * RC;
+};
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// One warp updates the voxels of its active lanes (act): ent = {pool voxel,
+// winner point} of the lane's list entry in map md (the lanes' maps may
+// differ), R = 32 x RB bytes of the warp's shared memory, qrow = the lane's
+// probability row (shared or global memory, 16-byte aligned), or null for a
+// hard label.  Any cp.async copies the warp issued before are waited for too.
+template <bool F16>
+__device__ __forceinline__ void class_update_warp(const ScanConst &sc, const MapDev &md, bool act, int2 ent,
+                                                  unsigned char *R, const float *qrow) {
+    using S = SemStage<F16>;
+    const int lane = threadIdx.x & 31;
+    unsigned char *mine = nullptr;
+    if (act)
+        mine = F16 ? reinterpret_cast<unsigned char *>(md.lp16 + lp_index(md, ent.x, 0))
+                   : reinterpret_cast<unsigned char *>(md.lp32 + lp_index(md, ent.x, 0));
+    const unsigned long long mp = reinterpret_cast<unsigned long long>(mine);
+    // chunk k of the warp's records: record k / RC, 16-byte chunk k % RC
+#pragma unroll
+    for (int j = 0; j < S::RC; ++j) {
+        const int k = 32 * j + lane, r = k / S::RC, c = k - r * S::RC;
+        const unsigned long long src = __shfl_sync(0xffffffffu, mp, r);
+        if (src) cp_async16(R + r * S::RB + 16 * c, reinterpret_cast<const unsigned char *>(src) + 16 * c);
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    if (act) {
+        float av[SEM_NC];
+        unsigned char *rr = R + lane * S::RB;
+        if (F16) {
+            const uint4 *q = reinterpret_cast<const uint4 *>(rr);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const uint4 u = q[j];
+                const float2 f0 = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+                const float2 f1 = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+                const float2 f2 = __half22float2(*reinterpret_cast<const __half2 *>(&u.z));
+                const float2 f3 = __half22float2(*reinterpret_cast<const __half2 *>(&u.w));
+                const float g[8] = {f0.x, f0.y, f1.x, f1.y, f2.x, f2.y, f3.x, f3.y};
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (8 * j + k < SEM_NC) av[8 * j + k] = g[k];
+            }
+        } else {
+            const float4 *q = reinterpret_cast<const float4 *>(rr);
+#pragma unroll
+            for (int j = 0; j < SEM_NC / 4; ++j) {
+                const float4 v = q[j];
+                av[4 * j] = v.x;
+                av[4 * j + 1] = v.y;
+                av[4 * j + 2] = v.z;
+                av[4 * j + 3] = v.w;
+            }
+        }
+        const int best = class_update<F16, SEM_NC>(sc, av, qrow, qrow ? 0 : sc.labels[ent.y]);
+        // the new record in place, padding zero
+        if (F16) {
+            uint4 *q = reinterpret_cast<uint4 *>(rr);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float f[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) f[k] = (8 * j + k < SEM_NC) ? av[8 * j + k] : 0.f;
+                __half2 h0 = __floats2half2_rn(f[0], f[1]), h1 = __floats2half2_rn(f[2], f[3]);
+                __half2 h2 = __floats2half2_rn(f[4], f[5]), h3 = __floats2half2_rn(f[6], f[7]);
+                uint4 u;
+                u.x = *reinterpret_cast<unsigned *>(&h0);
+                u.y = *reinterpret_cast<unsigned *>(&h1);
+                u.z = *reinterpret_cast<unsigned *>(&h2);
+                u.w = *reinterpret_cast<unsigned *>(&h3);
+                q[j] = u;
+            }
+        } else {
+            float4 *q = reinterpret_cast<float4 *>(rr);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                float f[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) f[k] = (4 * j + k < SEM_NC) ? av[4 * j + k] : 0.f;
+                q[j] = make_float4(f[0], f[1], f[2], f[3]);
+            }
+        }
+        md.label[ent.x] = (uint8_t)best;
+    }
+    __syncwarp();
+    // the records back, chunk by chunk as they came
+#pragma unroll
+    for (int j = 0; j < S::RC; ++j) {
+        const int k = 32 * j + lane, r = k / S::RC, c = k - r * S::RC;
+        const unsigned long long dst = __shfl_sync(0xffffffffu, mp, r);
+        if (dst)
+            *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(dst) + 16 * c) =
+                *reinterpret_cast<const uint4 *>(R + r * S::RB + 16 * c);
+    }
+    __syncwarp();
+}
+
 constexpr int MESH_WARPS = 8;   // warps (blocks in flight) per CTA
 
 // Per-warp staging of one block: the 9^3 region (block + upper faces) and

@@ -169,7 +169,24 @@ __global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch(const __grid_c
         }
     }
     __syncthreads();
-    for (long long base = tid; base < S.pre[n]; base += nthreads * VPT) {
+    if (a.sem_staged) {
+        // warp-staged: 32 consecutive entries of the maps' concatenated lists per warp, the records
+        // staged in the warp's re-meshing slot (free until this warp meshes); probability rows
+        // read by each lane
+        static_assert(sizeof(MeshWarpSmem) >= 32 * SemStage<false>::RB, "staging fits the warp's slot");
+        unsigned char *R = reinterpret_cast<unsigned char *>(&S.u.mesh.w[wid]);
+        for (long long base = gwarp * 32; base < S.pre[n]; base += nwarps * 32) {
+            const long long e = base + lane;
+            const bool act = e < S.pre[n];
+            const int i = act ? find_map(S.pre, n, e) : 0;
+            const BatchItem &it = a.it[i];
+            const int2 ent = act ? it.fd.sem_list[e - S.pre[i]] : make_int2(0, 0);
+            const float *qrow = act && it.sc.has_probs ? it.sc.probs + (long long)ent.y * SEM_NC : nullptr;
+            if (a.sem_staged == 2) class_update_warp<true>(it.sc, it.md, act, ent, R, qrow);
+            else class_update_warp<false>(it.sc, it.md, act, ent, R, qrow);
+        }
+    }
+    for (long long base = tid; !a.sem_staged && base < S.pre[n]; base += nthreads * VPT) {
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
             const long long e = base + (long long)k * nthreads;

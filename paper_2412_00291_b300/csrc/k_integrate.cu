@@ -70,139 +70,35 @@ __global__ void __launch_bounds__(256) k_semantic(ScanConst sc, MapDev md, Frame
 }
 
 // The class update of the listed voxels with 20 classes, staged warp by warp
-// through shared memory.  A thread's own record (96 B FP32 / 64 B FP16) and
-// its winner's probability row (80 B) are each spread over several cache
-// lines per warp instruction when every lane loads its own (32 lines per
-// 16-byte load instruction: the L1's tag lookups, not DRAM, set the pace);
-// here the 32 lanes copy consecutive 16-byte chunks of the warp's 32 records
-// and rows (cp.async, global to shared without registers), so one
-// instruction covers about five records in a handful of lines.  Each lane
-// then updates its voxel from shared memory (class_update, the body every
-// other path runs, so the results are the same bits) and the lanes write the
-// records back chunk by chunk.
-constexpr int SEMC_NC = 20;
-template <bool F16>
-struct SemCoop {
-    static constexpr int RC = F16 ? 4 : 6;   // 16-byte chunks per record (32 halves / 24 floats)
-    static constexpr int QC = SEMC_NC / 4;   // 16-byte chunks per probability row
-    static constexpr int RB = 16 * RC;
-};
-
-__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
-                 "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
+// through shared memory (class_update_warp in frame_bodies.cuh): per warp 32
+// list entries, their class records and the winners' probability rows copied
+// as consecutive 16-byte chunks (cp.async) rather than one voxel per lane.
 template <bool F16>
 __global__ void __launch_bounds__(256, 4) k_semantic_coop(ScanConst sc, MapDev md, FrameDev fd) {
-    using S = SemCoop<F16>;
+    using S = SemStage<F16>;
     __shared__ __align__(16) unsigned char s_rec[8][32 * S::RB];
-    __shared__ __align__(16) float s_q[8][32 * SEMC_NC];
+    __shared__ __align__(16) float s_q[8][32 * SEM_NC];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *R = s_rec[wid];
     float *Q = s_q[wid];
     unsigned long long ns = *(volatile unsigned long long *)&fd.ctr[CT_SEM];
     if (ns > (unsigned long long)fd.sem_cap) ns = fd.sem_cap;
     const bool probs = sc.has_probs != 0;
-    auto rec = [&](long long vox) -> unsigned char * {
-        return F16 ? reinterpret_cast<unsigned char *>(md.lp16 + lp_index(md, vox, 0))
-                   : reinterpret_cast<unsigned char *>(md.lp32 + lp_index(md, vox, 0));
-    };
     for (unsigned long long base = ((unsigned long long)blockIdx.x * 8 + wid) * 32; base < ns;
          base += (unsigned long long)gridDim.x * 256) {
         const int nact = (int)min(32ull, ns - base);
         const bool act = lane < nact;
         const int2 ent = act ? fd.sem_list[base + lane] : make_int2(0, 0);
-        // chunk k of the warp's records: record k / RC, 16-byte chunk k % RC
-#pragma unroll
-        for (int j = 0; j < S::RC; ++j) {
-            const int k = 32 * j + lane, r = k / S::RC, c = k - r * S::RC;
-            const int vox = __shfl_sync(0xffffffffu, ent.x, r);
-            if (r < nact) cp_async16(R + r * S::RB + 16 * c, rec(vox) + 16 * c);
-        }
         if (probs) {
+            // the winners' probability rows, chunk by chunk like the records
 #pragma unroll
-            for (int j = 0; j < S::QC; ++j) {
-                const int k = 32 * j + lane, r = k / S::QC, c = k - r * S::QC;
+            for (int j = 0; j < SEM_NC / 4; ++j) {
+                const int k = 32 * j + lane, r = k / (SEM_NC / 4), c = k - r * (SEM_NC / 4);
                 const int idx = __shfl_sync(0xffffffffu, ent.y, r);
-                if (r < nact) cp_async16(Q + r * SEMC_NC + 4 * c, sc.probs + (long long)idx * SEMC_NC + 4 * c);
+                if (r < nact) cp_async16(Q + r * SEM_NC + 4 * c, sc.probs + (long long)idx * SEM_NC + 4 * c);
             }
         }
-        cp_async_wait_all();
-        __syncwarp();
-        if (act) {
-            float av[SEMC_NC];
-            unsigned char *rr = R + lane * S::RB;
-            if (F16) {
-                const uint4 *q = reinterpret_cast<const uint4 *>(rr);
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const uint4 u = q[j];
-                    const float2 f0 = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
-                    const float2 f1 = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
-                    const float2 f2 = __half22float2(*reinterpret_cast<const __half2 *>(&u.z));
-                    const float2 f3 = __half22float2(*reinterpret_cast<const __half2 *>(&u.w));
-                    const float g[8] = {f0.x, f0.y, f1.x, f1.y, f2.x, f2.y, f3.x, f3.y};
-#pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        if (8 * j + k < SEMC_NC) av[8 * j + k] = g[k];
-                }
-            } else {
-                const float4 *q = reinterpret_cast<const float4 *>(rr);
-#pragma unroll
-                for (int j = 0; j < SEMC_NC / 4; ++j) {
-                    const float4 v = q[j];
-                    av[4 * j] = v.x;
-                    av[4 * j + 1] = v.y;
-                    av[4 * j + 2] = v.z;
-                    av[4 * j + 3] = v.w;
-                }
-            }
-            const int best =
-                class_update<F16, SEMC_NC>(sc, av, probs ? Q + lane * SEMC_NC : nullptr, probs ? 0 : sc.labels[ent.y]);
-            // the new record in place, padding zero
-            if (F16) {
-                uint4 *q = reinterpret_cast<uint4 *>(rr);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float f[8];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) f[k] = (8 * j + k < SEMC_NC) ? av[8 * j + k] : 0.f;
-                    __half2 h0 = __floats2half2_rn(f[0], f[1]), h1 = __floats2half2_rn(f[2], f[3]);
-                    __half2 h2 = __floats2half2_rn(f[4], f[5]), h3 = __floats2half2_rn(f[6], f[7]);
-                    uint4 u;
-                    u.x = *reinterpret_cast<unsigned *>(&h0);
-                    u.y = *reinterpret_cast<unsigned *>(&h1);
-                    u.z = *reinterpret_cast<unsigned *>(&h2);
-                    u.w = *reinterpret_cast<unsigned *>(&h3);
-                    q[j] = u;
-                }
-            } else {
-                float4 *q = reinterpret_cast<float4 *>(rr);
-#pragma unroll
-                for (int j = 0; j < 6; ++j) {
-                    float f[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) f[k] = (4 * j + k < SEMC_NC) ? av[4 * j + k] : 0.f;
-                    q[j] = make_float4(f[0], f[1], f[2], f[3]);
-                }
-            }
-            md.label[ent.x] = (uint8_t)best;
-        }
-        __syncwarp();
-        // the records back, chunk by chunk as they came
-#pragma unroll
-        for (int j = 0; j < S::RC; ++j) {
-            const int k = 32 * j + lane, r = k / S::RC, c = k - r * S::RC;
-            const int vox = __shfl_sync(0xffffffffu, ent.x, r);
-            if (r < nact)
-                *reinterpret_cast<uint4 *>(rec(vox) + 16 * c) = *reinterpret_cast<const uint4 *>(R + r * S::RB + 16 * c);
-        }
-        __syncwarp();
+        class_update_warp<F16>(sc, md, act, ent, R, probs ? Q + lane * SEM_NC : nullptr);
     }
 }
 
@@ -242,7 +138,7 @@ void launch_normals(const ScanConst &sc, const FrameDev &fd, cudaStream_t s) {
 
 void launch_semantic(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s) {
     // 20 classes with a label or 16-byte-aligned probability rows: the warp-staged kernel
-    if (sc.C == SEMC_NC && (!sc.has_probs || sc.probs_vec4)) {
+    if (sc.C == SEM_NC && (!sc.has_probs || sc.probs_vec4)) {
         if (md.storage == 0) k_semantic_coop<false><<<grid, 256, 0, s>>>(sc, md, fd);
         else k_semantic_coop<true><<<grid, 256, 0, s>>>(sc, md, fd);
         return;

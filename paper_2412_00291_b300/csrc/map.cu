@@ -1716,6 +1716,16 @@ extern "C" map_status map_batch_integrate(map_batch_t *b, const scan_desc *scans
         it.sc.labels = d.labels_dev;
         it.sc.probs = d.probs_dev;
     }
+    // the warp-staged class update when every map has 20 classes, one storage type, and labels or
+    // 16-byte-aligned probability rows
+    {
+        bool staged = true;
+        for (int i = 0; i < n && staged; ++i) {
+            const BatchItem &it = args.it[i];
+            staged = it.sc.C == 20 && it.md.storage == args.it[0].md.storage && (!it.sc.has_probs || it.sc.probs_vec4);
+        }
+        args.sem_staged = staged && n > 0 ? (args.it[0].md.storage == 0 ? 1 : 2) : 0;
+    }
     args.n = n;
     args.ctl = b->ctl;
     args.out = b->out_dev;
