@@ -133,9 +133,9 @@ struct MapDev {
     int storage;         // 0 FP32, 1 FP16
     float2 *dw32;        // [slot][512] {D, W}
     __half2 *dw16;
-    float *lp32;         // [slot][512][CP] log-probabilities, one padded record per voxel
+    float *lp32;         // [slot][512][CP] log-probabilities, one record per voxel
     __half *lp16;
-    int CP;              // record stride in elements: C rounded up to whole 32-byte sectors
+    int CP;              // record stride in elements: C rounded up to whole 16-byte chunks
     uint8_t *label;      // [slot][512] most probable class
     const uchar4 *pal;   // [256] class colours (rgb)
     uint64_t *slot_key;  // [slot] block key owning the pool slot

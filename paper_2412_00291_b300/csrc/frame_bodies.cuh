@@ -701,7 +701,7 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
 // Recursive Bayesian class update (Eq. bayesian_filter) of the listed voxels,
 // one voxel per thread: logP_c += log L_c, renormalise by logsumexp, floor,
 // and refresh the voxel's argmax label.  A voxel's classes form one record of
-// whole 32-byte sectors (FP32: 24 floats, FP16: 32 halves for 20 classes),
+// whole 16-byte chunks (FP32: 20 floats, FP16: 24 halves for 20 classes),
 // read and written with vector accesses, padding included.  The logarithms
 // and exponentials use the MUFU approximations (__logf, __expf): their error,
 // ~1e-6 per term, is two orders below the class log-probability tolerance of
@@ -818,8 +818,8 @@ template <bool F16, int NC>
 __device__ __forceinline__ void semantic_item(const ScanConst &sc, const MapDev &md, const FrameDev &fd,
                                               unsigned long long e) {
     constexpr int MAXC_RT = 64;
-    // padded record length for the compile-time class count (32-byte sectors)
-    constexpr int NCP = NC > 0 ? (F16 ? ((NC + 15) / 16) * 16 : ((NC + 7) / 8) * 8) : 1;
+    // padded record length for the compile-time class count (16-byte chunks)
+    constexpr int NCP = NC > 0 ? (F16 ? ((NC + 7) / 8) * 8 : ((NC + 3) / 4) * 4) : 1;
     const int C = NC > 0 ? NC : sc.C;
     const int2 ent = fd.sem_list[e];
     const long long vox = ent.x;
@@ -861,7 +861,7 @@ __device__ __forceinline__ void semantic_item(const ScanConst &sc, const MapDev 
 }
 
 // --- the class update staged by a warp through shared memory ------------------
-// A lane's own 96-byte (FP32) or 64-byte (FP16) class record, loaded with one
+// A lane's own 80-byte (FP32) or 48-byte (FP16) class record, loaded with one
 // 16-byte access per lane and instruction, touches a different cache line in
 // every lane, and the L1's tag lookups then bound the update; here the warp's
 // 32 lanes copy consecutive 16-byte chunks of the warp's 32 records (about five
@@ -870,7 +870,7 @@ __device__ __forceinline__ void semantic_item(const ScanConst &sc, const MapDev 
 constexpr int SEM_NC = 20;    // the class count of the staged path
 template <bool F16>
 struct SemStage {
-    static constexpr int RC = F16 ? 4 : 6;    // 16-byte chunks per record (32 halves / 24 floats)
+    static constexpr int RC = F16 ? 3 : 5;    // 16-byte chunks per record (24 halves / 20 floats)
     static constexpr int RB = 16 * RC;
 };
 __device__ __forceinline__ void cp_async16(void *dst_smem, const void *src) {
@@ -939,7 +939,7 @@ __device__ __forceinline__ void class_update_warp(const ScanConst &sc, const Map
         if (F16) {
             uint4 *q = reinterpret_cast<uint4 *>(rr);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < S::RC; ++j) {
                 float f[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) f[k] = (8 * j + k < SEM_NC) ? av[8 * j + k] : 0.f;
@@ -955,7 +955,7 @@ __device__ __forceinline__ void class_update_warp(const ScanConst &sc, const Map
         } else {
             float4 *q = reinterpret_cast<float4 *>(rr);
 #pragma unroll
-            for (int j = 0; j < 6; ++j) {
+            for (int j = 0; j < S::RC; ++j) {
                 float f[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) f[k] = (4 * j + k < SEM_NC) ? av[4 * j + k] : 0.f;

@@ -263,9 +263,10 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     md.C = c.n_classes;
     md.storage = c.storage;
     {
-        // log-probability record per voxel padded to whole 32-byte sectors
-        const int per_sector = c.storage == 0 ? 8 : 16;
-        md.CP = ((c.n_classes + per_sector - 1) / per_sector) * per_sector;
+        // log-probability record per voxel padded to whole 16-byte chunks (the unit of the
+        // vector and staged accesses): 20 classes take 80 B in FP32, 48 B in FP16
+        const int per_chunk = c.storage == 0 ? 4 : 8;
+        md.CP = ((c.n_classes + per_chunk - 1) / per_chunk) * per_chunk;
     }
     md.nu = (float)c.voxel_size;
     md.av_cap = c.mesh_vertex_capacity;
