@@ -712,11 +712,12 @@ def run_ours(args, rank, world, local_rank):
         "full_mesh": full_mesh,
         "quality": qual,
         "cpu_baseline": cpu,
-        "fp16_vs_fp32": fp16,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if fp16 is not None:    # FP16 storage runs only: the same scans in FP32 storage, compared
+        line["fp16_vs_fp32"] = fp16
     print(json.dumps(line), flush=True)
 
 

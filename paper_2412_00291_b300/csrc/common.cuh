@@ -14,7 +14,8 @@ constexpr int BV = BS * BS * BS;
 constexpr uint64_t EMPTY_KEY = ~0ull;
 constexpr int MAX_PROBES = 256;       // linear-probing bound of the block hash
 constexpr int MAX_AXIS_CROSS = 4;     // band may cross <= 4 block planes per axis (tau <= 16 nu)
-constexpr int MC_MAXTRI = 8;          // triangles per cube case in the generated table
+constexpr int MC_MAXTRI = 5;          // triangles per cube case in the device copy of the generated table
+                                       // (its largest case; the C-ABI table has MAP_MC_MAXTRI slots)
 constexpr float PI_F = 3.14159265358979f;
 
 // latched device error bits

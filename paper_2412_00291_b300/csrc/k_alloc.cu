@@ -215,6 +215,10 @@ void launch_points(const float *pts, const ScanConst &sc, const MapDev &md, cons
     const long long n = std::max<long long>({(long long)sc.n, fd.win_next ? fd.win_next_n : 0ll, 1ll});
     k_points<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(pts, sc, md, fd);
 }
+void alloc_kernel_attributes() {
+    cudaFuncSetAttribute(k_points, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(k_snapshot, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+}
 void launch_snapshot(const unsigned long long *ctr, const DevState *st, unsigned char *rec, cudaStream_t s) {
     static_assert(sizeof(DevState) % sizeof(unsigned long long) == 0, "DevState is a whole number of words");
     k_snapshot<<<1, 128, 0, s>>>(ctr, st, reinterpret_cast<unsigned long long *>(rec));

@@ -73,19 +73,22 @@ __global__ void __launch_bounds__(256) k_semantic(ScanConst sc, MapDev md, Frame
 // through shared memory (class_update_warp in frame_bodies.cuh): per warp 32
 // list entries, their class records and the winners' probability rows copied
 // as consecutive 16-byte chunks (cp.async) rather than one voxel per lane.
+// Four warps per CTA (20 KB of staging in FP32): one such CTA fits on an SM
+// beside the four re-meshing CTAs that run at the same time.
+constexpr int SEM_WARPS = 4;
 template <bool F16>
-__global__ void __launch_bounds__(256, 4) k_semantic_coop(ScanConst sc, MapDev md, FrameDev fd) {
+__global__ void __launch_bounds__(32 * SEM_WARPS, 8) k_semantic_coop(ScanConst sc, MapDev md, FrameDev fd) {
     using S = SemStage<F16>;
-    __shared__ __align__(16) unsigned char s_rec[8][32 * S::RB];
-    __shared__ __align__(16) float s_q[8][32 * SEM_NC];
+    __shared__ __align__(16) unsigned char s_rec[SEM_WARPS][32 * S::RB];
+    __shared__ __align__(16) float s_q[SEM_WARPS][32 * SEM_NC];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *R = s_rec[wid];
     float *Q = s_q[wid];
     unsigned long long ns = *(volatile unsigned long long *)&fd.ctr[CT_SEM];
     if (ns > (unsigned long long)fd.sem_cap) ns = fd.sem_cap;
     const bool probs = sc.has_probs != 0;
-    for (unsigned long long base = ((unsigned long long)blockIdx.x * 8 + wid) * 32; base < ns;
-         base += (unsigned long long)gridDim.x * 256) {
+    for (unsigned long long base = ((unsigned long long)blockIdx.x * SEM_WARPS + wid) * 32; base < ns;
+         base += (unsigned long long)gridDim.x * 32 * SEM_WARPS) {
         const int nact = (int)min(32ull, ns - base);
         const bool act = lane < nact;
         const int2 ent = act ? fd.sem_list[base + lane] : make_int2(0, 0);
@@ -103,10 +106,31 @@ __global__ void __launch_bounds__(256, 4) k_semantic_coop(ScanConst sc, MapDev m
 }
 
 template <typename K>
-static int occupancy(K kernel) {
+static int occupancy(K kernel, int threads = 256) {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, 0);
     return n > 0 ? n : 1;
+}
+
+void integrate_kernel_attributes() {
+    const auto max_shared = [](auto k) {
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    };
+    max_shared(k_tsdf<false, false>);
+    max_shared(k_tsdf<true, false>);
+    max_shared(k_tsdf<false, true>);
+    max_shared(k_tsdf<true, true>);
+    max_shared(k_tsdf<false, false, true>);
+    max_shared(k_tsdf<true, false, true>);
+    max_shared(k_tsdf<false, true, true>);
+    max_shared(k_tsdf<true, true, true>);
+    max_shared(k_semantic_coop<false>);
+    max_shared(k_semantic_coop<true>);
+    max_shared(k_semantic<false, 0>);
+    max_shared(k_semantic<true, 0>);
+    max_shared(k_semantic<false, 20>);
+    max_shared(k_semantic<true, 20>);
+    max_shared(k_normals);
 }
 
 int integrate_blocks_per_sm(int storage, int C, int dist_mode) {
@@ -116,8 +140,13 @@ int integrate_blocks_per_sm(int storage, int C, int dist_mode) {
 }
 
 int semantic_blocks_per_sm(int storage, int C) {
-    if (storage == 0) return C == 20 ? occupancy(k_semantic_coop<false>) : occupancy(k_semantic<false, 0>);
-    return C == 20 ? occupancy(k_semantic_coop<true>) : occupancy(k_semantic<true, 0>);
+    // (in 256-thread equivalents, so that the grids span the same warps)
+    constexpr int per = 256 / (32 * SEM_WARPS);
+    if (storage == 0)
+        return C == 20 ? (occupancy(k_semantic_coop<false>, 32 * SEM_WARPS) + per - 1) / per
+                       : occupancy(k_semantic<false, 0>);
+    return C == 20 ? (occupancy(k_semantic_coop<true>, 32 * SEM_WARPS) + per - 1) / per
+                   : occupancy(k_semantic<true, 0>);
 }
 
 void launch_integrate(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s) {
@@ -139,8 +168,10 @@ void launch_normals(const ScanConst &sc, const FrameDev &fd, cudaStream_t s) {
 void launch_semantic(const ScanConst &sc, const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s) {
     // 20 classes with a label or 16-byte-aligned probability rows: the warp-staged kernel
     if (sc.C == SEM_NC && (!sc.has_probs || sc.probs_vec4)) {
-        if (md.storage == 0) k_semantic_coop<false><<<grid, 256, 0, s>>>(sc, md, fd);
-        else k_semantic_coop<true><<<grid, 256, 0, s>>>(sc, md, fd);
+        // grid counts 256-thread CTAs
+        const int g = grid * (256 / (32 * SEM_WARPS));
+        if (md.storage == 0) k_semantic_coop<false><<<g, 32 * SEM_WARPS, 0, s>>>(sc, md, fd);
+        else k_semantic_coop<true><<<g, 32 * SEM_WARPS, 0, s>>>(sc, md, fd);
         return;
     }
     if (md.storage == 0) {

@@ -14,6 +14,7 @@
 // the surface (lower endpoint on ties) and that class's palette colour.
 #include "batch.h"
 #include "frame_bodies.cuh"
+#include "semtsdf.h"
 
 namespace stsdf {
 
@@ -41,7 +42,13 @@ __global__ void __launch_bounds__(32 * MESH_WARPS) k_mesh(MapDev md, FrameDev fd
     cta_count<2>(fd.ctr, {CT_MV, CT_MT}, cnt);
 }
 
-int mesh_upload_tables(const int8_t *tri, const uint8_t *ntri) {
+int mesh_upload_tables(const int8_t *tri_abi, const uint8_t *ntri) {
+    // the device copy keeps MC_MAXTRI of the table's MAP_MC_MAXTRI slots per case
+    int8_t tri[256 * MC_MAXTRI * 3];
+    for (int c = 0; c < 256; ++c) {
+        if (ntri[c] > MC_MAXTRI) return -1;
+        for (int k = 0; k < MC_MAXTRI * 3; ++k) tri[c * MC_MAXTRI * 3 + k] = tri_abi[c * MAP_MC_MAXTRI * 3 + k];
+    }
     if (!h_tri_dev) {
         if (cudaMalloc(&h_tri_dev, 256 * MC_MAXTRI * 3) != cudaSuccess) return -1;
         if (cudaMalloc(&h_ntri_dev, 256) != cudaSuccess) return -1;
@@ -54,16 +61,28 @@ int mesh_upload_tables(const int8_t *tri, const uint8_t *ntri) {
 const int8_t *mesh_table_tri() { return h_tri_dev; }
 const uint8_t *mesh_table_ntri() { return h_ntri_dev; }
 
+// Shared memory per CTA, padded to 45 KB: four CTAs (4 x 46 KB with the
+// per-CTA reserve) and two four-warp class-update CTAs (2 x 21 KB) fit in an
+// SM's 228 KB, five CTAs do not, so the class update running beside the
+// re-meshing always has room on every SM.
+constexpr int MESH_SMEM_BYTES = 45 * 1024;
+static_assert(sizeof(MeshCtaSmem) <= MESH_SMEM_BYTES, "the staging fits the padded size");
+
+void mesh_kernel_attributes() {
+    cudaFuncSetAttribute(k_mesh, cudaFuncAttributeMaxDynamicSharedMemorySize, MESH_SMEM_BYTES);
+    cudaFuncSetAttribute(k_mesh, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+}
+
 int mesh_blocks_per_sm() {
-    const int bytes = (int)sizeof(MeshCtaSmem);
-    cudaFuncSetAttribute(k_mesh, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const int bytes = MESH_SMEM_BYTES;
+    mesh_kernel_attributes();
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mesh, 32 * MESH_WARPS, bytes);
     return n > 0 ? n : 1;
 }
 
 void launch_mesh(const MapDev &md, const FrameDev &fd, int grid, cudaStream_t s) {
-    launch_pdl(k_mesh, dim3(grid), dim3(32 * MESH_WARPS), sizeof(MeshCtaSmem), s, md, fd,
+    launch_pdl(k_mesh, dim3(grid), dim3(32 * MESH_WARPS), MESH_SMEM_BYTES, s, md, fd,
                (const int8_t *)h_tri_dev, (const uint8_t *)h_ntri_dev);
 }
 

@@ -5,6 +5,13 @@
 
 namespace stsdf {
 
+// The kernels of a scan all prefer the largest shared-memory carveout: an SM
+// changes its L1 / shared split only when idle, so kernels with different
+// splits could not share an SM as one scan's grids hand over to the next.
+void alloc_kernel_attributes();
+void integrate_kernel_attributes();
+void mesh_kernel_attributes();
+
 // k_alloc.cu: per-point range-image winners and band allocation (touched list)
 void launch_points(const float *pts, const ScanConst &sc, const MapDev &md, const FrameDev &fd, cudaStream_t s);
 void launch_snapshot(const unsigned long long *ctr, const DevState *st, unsigned char *rec, cudaStream_t s);

@@ -410,9 +410,12 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    alloc_kernel_attributes();
+    integrate_kernel_attributes();
+    mesh_kernel_attributes();
     m->grid_integrate = sms * integrate_blocks_per_sm(c.storage, c.n_classes, c.distance_mode);
     m->grid_semantic = 4 * sms * semantic_blocks_per_sm(c.storage, c.n_classes);
-    // at most 4 re-meshing CTAs per SM: more crowd the class update that runs beside them
+    // 4 re-meshing CTAs per SM (the padded staging admits no more)
     m->grid_mesh = sms * std::min(4, mesh_blocks_per_sm());
     e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();
