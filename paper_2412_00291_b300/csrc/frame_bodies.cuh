@@ -1068,23 +1068,41 @@ __device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev
         F[fi] = (uint8_t)f;
         if (f & 1) seen |= (f & 2) ? 1 : 2;
     };
-    // the block's own 512 voxels, two neighbours along x per read (16 bytes FP32, 8 FP16)
-#pragma unroll 4
-    for (int p = lane; p < BV / 2; p += 32) {
-        const int v = 2 * p, row = v >> 3, x = v & 7;            // row = y + 8 z
-        const int yz9 = (row & 7) + 9 * (row >> 3);               // y + 9 z
-        float2 a, b;
-        if (f32) {
-            const float4 q = reinterpret_cast<const float4 *>(md.dw32)[((long long)slot * BV + v) >> 1];
-            a = make_float2(q.x, q.y);
-            b = make_float2(q.z, q.w);
-        } else {
-            const uint2 q = reinterpret_cast<const uint2 *>(md.dw16)[((long long)slot * BV + v) >> 1];
-            a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
-            b = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
+    // The region's {D, W} in three rounds of reads, each round's reads issued
+    // before any of its stores to shared memory (a read placed after such a
+    // store would wait for it, one memory round trip per read): the block's
+    // own 512 voxels in two rounds of four reads per lane (two neighbours
+    // along x per read, 16 bytes FP32, 8 FP16), then the 217 voxels of the
+    // upper neighbours' faces.
+    const long long pair0 = (long long)slot * (BV / 2);
+#pragma unroll
+    for (int rnd = 0; rnd < 2; ++rnd) {
+        uint4 q[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long pi = pair0 + lane + 32 * (4 * rnd + k);
+            if (f32) {
+                q[k] = reinterpret_cast<const uint4 *>(md.dw32)[pi];
+            } else {
+                const uint2 u = reinterpret_cast<const uint2 *>(md.dw16)[pi];
+                q[k] = make_uint4(u.x, u.y, 0u, 0u);
+            }
         }
-        put(x + 9 * yz9, x + 16 * yz9, a);
-        put(x + 1 + 9 * yz9, x + 1 + 16 * yz9, b);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int v = 2 * (lane + 32 * (4 * rnd + k)), row = v >> 3, x = v & 7;   // row = y + 8 z
+            const int yz9 = (row & 7) + 9 * (row >> 3);                                // y + 9 z
+            float2 a, b;
+            if (f32) {
+                a = make_float2(__uint_as_float(q[k].x), __uint_as_float(q[k].y));
+                b = make_float2(__uint_as_float(q[k].z), __uint_as_float(q[k].w));
+            } else {
+                a = __half22float2(*reinterpret_cast<const __half2 *>(&q[k].x));
+                b = __half22float2(*reinterpret_cast<const __half2 *>(&q[k].y));
+            }
+            put(x + 9 * yz9, x + 16 * yz9, a);
+            put(x + 1 + 9 * yz9, x + 1 + 16 * yz9, b);
+        }
     }
     __syncwarp();
     auto nb_dw = [&](int s, int local) -> float2 {
@@ -1092,26 +1110,32 @@ __device__ __forceinline__ void mesh_block_warp(const MapDev &md, const FrameDev
         const long long vox = (long long)s * BV + local;
         return f32 ? md.dw32[vox] : __half22float2(md.dw16[vox]);
     };
-    // x = 8 face (rows y + 9 z = j): local x = 0 of the +x neighbours
-    for (int j = lane; j < 81; j += 32) {
-        const int y = j % 9, z = j / 9;
-        const int s = W.nb[1 | ((y >> 3) << 1) | ((z >> 3) << 2)];
-        put(8 + 9 * j, 8 + 16 * j, nb_dw(s, 8 * (y & 7) + 64 * (z & 7)));
+    // faces: x = 8 (rows y + 9 z = j < 81: local x = 0 of the +x neighbours),
+    // y = 8 (j = x + 8 z < 72: local y = 0 of the +y neighbours), z = 8
+    // (j = x + 8 y < 64: local z = 0 of the +z neighbour)
+    float2 fx[3], fy[3], fz[2];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const int j = lane + 32 * t;
+        fx[t] = fy[t] = make_float2(0.f, 0.f);
+        if (j < 81) {
+            const int y = j % 9, z = j / 9;
+            fx[t] = nb_dw(W.nb[1 | ((y >> 3) << 1) | ((z >> 3) << 2)], 8 * (y & 7) + 64 * (z & 7));
+        }
+        if (j < 72) fy[t] = nb_dw(W.nb[2 | ((j >> 6) << 2)], (j & 7) + 64 * ((j >> 3) & 7));
+        if (t < 2) fz[t] = nb_dw(W.nb[4], j);
     }
-    // y = 8 face (x < 8, z = 0..8): local y = 0 of the +y neighbours
-    for (int j = lane; j < 72; j += 32) {
-        const int x = j & 7, z = j >> 3;
-        const int s = W.nb[2 | ((z >> 3) << 2)];
-        const int yz9 = 8 + 9 * z;
-        put(x + 9 * yz9, x + 16 * yz9, nb_dw(s, x + 64 * (z & 7)));
-    }
-    // z = 8 face (x < 8, y < 8): local z = 0 of the +z neighbour
-    {
-        const int s = W.nb[4];
-        for (int j = lane; j < 64; j += 32) {
-            const int x = j & 7, y = j >> 3;
-            const int yz9 = y + 72;
-            put(x + 9 * yz9, x + 16 * yz9, nb_dw(s, x + 8 * y));
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const int j = lane + 32 * t;
+        if (j < 81) put(8 + 9 * j, 8 + 16 * j, fx[t]);
+        if (j < 72) {
+            const int yz9 = 8 + 9 * (j >> 3);
+            put((j & 7) + 9 * yz9, (j & 7) + 16 * yz9, fy[t]);
+        }
+        if (t < 2) {
+            const int yz9 = (j >> 3) + 72;
+            put((j & 7) + 9 * yz9, (j & 7) + 16 * yz9, fz[t]);
         }
     }
     const bool any_neg = __any_sync(0xffffffffu, seen & 1), any_pos = __any_sync(0xffffffffu, seen & 2);

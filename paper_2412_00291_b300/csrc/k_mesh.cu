@@ -22,7 +22,7 @@ namespace stsdf {
 static int8_t *h_tri_dev = nullptr;      // [256][MC_MAXTRI][3] cube-edge ids
 static uint8_t *h_ntri_dev = nullptr;    // [256] triangles per case
 
-__global__ void __launch_bounds__(32 * MESH_WARPS) k_mesh(MapDev md, FrameDev fd, const int8_t *__restrict__ ttri,
+__global__ void __launch_bounds__(32 * MESH_WARPS, 5) k_mesh(MapDev md, FrameDev fd, const int8_t *__restrict__ ttri,
                                                            const uint8_t *__restrict__ tntri) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MeshCtaSmem &S = *reinterpret_cast<MeshCtaSmem *>(smem_raw);
