@@ -88,6 +88,20 @@ def test_mc_table_uses_exactly_the_crossing_edges():
         assert (len(used) > 0) == (cs not in (0, 255))
 
 
+def test_mc_table_cases_fit_the_device_copy():
+    """The device copy of the table keeps 5 triangle slots per case (map_create refuses a table with a
+    larger case): every case has at most 5 triangles, the slots after a case's last triangle are -1,
+    and the largest case does use 5 (the classic marching-cubes maximum)."""
+    import paper_2412_00291_b300 as p
+    table = p.map_mc_table()
+    used = table[:, :, 0] >= 0
+    n = used.sum(axis=1)
+    assert n.max() == 5
+    for cs in range(256):
+        assert used[cs, :n[cs]].all() and not used[cs, n[cs]:].any(), cs
+        assert (table[cs, n[cs]:] == -1).all(), cs
+
+
 def test_palette_matches_oracle():
     import paper_2412_00291_b300 as p
     for C in (2, 7, 20, 64):
