@@ -771,14 +771,15 @@ def run_batch(args, rank, world, local_rank):
         return [P.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, storage=1, **stream_config(w, n_frames))
                 for w in ws]
 
-    def run_arm(batched, concurrent=False):
+    def run_arm(batched, concurrent=False, graph=False):
         maps = new_maps()
         b = None
         if batched:
             b = P.map_batch_create([m.h for m in maps], P.MAP_BATCH_GRAPH | P.MAP_BATCH_AUTOTUNE)
         elif concurrent:
-            # each map's integrate_scan kernels on a stream of the batch's own, forked and joined in the library
-            b = P.map_batch_create([m.h for m in maps], P.MAP_BATCH_STREAMS)
+            # each map's integrate_scan kernels on a stream of the batch's own, forked and joined in the
+            # library (graph: the step captured and replayed as one graph launch)
+            b = P.map_batch_create([m.h for m in maps], P.MAP_BATCH_STREAMS | (P.MAP_BATCH_GRAPH if graph else 0))
 
         def step(k):
             if batched or concurrent:
@@ -839,6 +840,14 @@ def run_batch(args, rank, world, local_rank):
     P.map_batch_destroy(bc)
     for m in con_maps:
         m.close()
+    cg_maps, bg, cong = run_arm(False, concurrent=True, graph=True)
+    max_dd_g = 0.0
+    for i, (c, g) in sample.items():
+        h = cg_maps[i].read_blocks(c, want_logp=False)
+        max_dd_g = max(max_dd_g, float(np.abs(h["D"] - g["D"]).max(initial=0)))
+    P.map_batch_destroy(bg)
+    for m in cg_maps:
+        m.close()
     bat_maps, b, bat = run_arm(True)
     max_dd, max_dw, compared = 0.0, 0.0, 0
     for i, (c, g) in sample.items():
@@ -861,12 +870,13 @@ def run_batch(args, rank, world, local_rank):
                    "streams": [w.name for w in ws],
                    "timing": "per step: L2 flushed, synchronize, wall clock around the host calls, synchronize",
                    "input_gen_s": t_gen},
-        "batched": bat, "sequential": seq, "concurrent_streams": con,
+        "batched": bat, "sequential": seq, "concurrent_streams": con, "concurrent_streams_graph": cong,
         "speedup_wall": seq["wall_ms"] / bat["wall_ms"], "speedup_device": seq["dev_ms"] / bat["dev_ms"],
         "sequential_points_per_s": pts_per_step / (seq["wall_ms"] * 1e-3),
         "concurrent_streams_points_per_s": pts_per_step / (con["wall_ms"] * 1e-3),
+        "concurrent_streams_graph_points_per_s": pts_per_step / (cong["wall_ms"] * 1e-3),
         "arms_agree": {"max_abs_dD": max_dd, "max_abs_dW": max_dw, "voxels_compared": compared,
-                       "concurrent_max_abs_dD": max_dd_c},
+                       "concurrent_max_abs_dD": max_dd_c, "concurrent_graph_max_abs_dD": max_dd_g},
         "gpu_launches": bat["launches"],
         "clocks": bat["clocks"],
     }

@@ -422,7 +422,10 @@ enum {
     MAP_BATCH_AUTOTUNE = 2,  /* time each launch configuration on the first steps, keep the fastest */
     MAP_BATCH_STREAMS = 4    /* instead of the cooperative kernel: each map's integrate_scan kernels on
                                 a stream of the batch's own, all maps concurrently, forked from and
-                                joined to the caller's stream (GRAPH and AUTOTUNE then do nothing) */
+                                joined to the caller's stream (AUTOTUNE then does nothing; with GRAPH
+                                the step is captured on a private stream, an executable graph updated
+                                in place from the capture, or instantiated again when the step's shape
+                                changes, and launched once on the caller's stream) */
 };
 
 /* Group 1..48 maps (each used by this batch only while it exists).  The batch
@@ -448,7 +451,11 @@ map_status map_batch_integrate(map_batch_t *batch, const scan_desc *scans, void 
  * its own stream of the batch, run concurrently and joined to `stream`;
  * per-map results are those of integrate_scan (map_frame_stats included).
  * A map whose call is refused (bad arguments) is left as it was, the other
- * maps are still fused, and the first refusal is returned. */
+ * maps are still fused, and the first refusal is returned.  With
+ * MAP_BATCH_GRAPH as well, the same calls are captured and replayed as one
+ * graph launch (identical results); the capture and the graph update run on
+ * the host before the step's first kernel starts, where the plain streams
+ * form has the GPU working from its first launch on. */
 
 /* Wait for the step in flight and report its errors. */
 map_status map_batch_sync(map_batch_t *batch, void *stream);

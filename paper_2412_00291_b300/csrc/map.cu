@@ -687,6 +687,11 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     sc.labels = labels;
     sc.probs = probs;
     sc.probs_vec4 = probs && (m->C % 4 == 0) && (((uintptr_t)probs & 15) == 0);
+    // inside a stream capture (a batch step replayed from a graph): no phase
+    // timing, and the download and its ring event go into the graph (below)
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(s, &cap_status));
+    const bool capturing = cap_status != cudaStreamCaptureStatusNone;
     poll_stats(m);
     if (need_compaction(m)) {
         st = compact_arena(m, s);
@@ -704,7 +709,7 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     fd.ctr_next = m->ctr_buf[nxt];
     cudaEvent_t *ev = nullptr;
     unsigned long long *ev_stats = nullptr;
-    if (m->prof_n < m->prof_cap) {
+    if (!capturing && m->prof_n < m->prof_cap) {
         ev_stats = m->prof_stats + (size_t)m->prof_n * CT_COUNT;
         m->prof_serial[m->prof_n] = m->concurrent ? 0 : 1;
         ev = &m->prof_ev[(size_t)m->prof_n++ * (MAP_PHASE_COUNT + 1)];
@@ -727,7 +732,8 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     m->win_dirty[nxt] = 0;
     m->ctr_clean[nxt] = true;
     if (sc.dist_mode) {
-        CU(cudaStreamWaitEvent(s, m->ev_dir, 0));   // pixel-ray tables uploaded
+        // pixel-ray tables uploaded (a capturing caller has waited for them before the capture)
+        if (!capturing) CU(cudaStreamWaitEvent(s, m->ev_dir, 0));
         launch_normals(sc, m->fd, s);
         m->launches += 1;
     }
@@ -762,11 +768,19 @@ static map_status run_frame(map_t *m, const lidar_intrinsics *L, const float *pt
     unsigned char *rec = m->d_ring + (size_t)slot * map_t::REC_BYTES;
     launch_snapshot(m->fd.ctr, m->st, rec, s);
     m->launches += 1;
-    CU(cudaEventRecord(m->ev_snap, s));
-    CU(cudaStreamWaitEvent(m->dl, m->ev_snap, 0));
-    CU(cudaMemcpyAsync(m->h_ring + (size_t)slot * map_t::REC_BYTES, rec, map_t::REC_BYTES, cudaMemcpyDeviceToHost,
-                       m->dl));
-    CU(cudaEventRecord(m->ev_ring[slot], m->dl));
+    if (capturing) {
+        // in the graph, on this stream; the ring event as an event-record node, so that the
+        // host's later queries of it see each replay
+        CU(cudaMemcpyAsync(m->h_ring + (size_t)slot * map_t::REC_BYTES, rec, map_t::REC_BYTES,
+                           cudaMemcpyDeviceToHost, s));
+        CU(cudaEventRecordWithFlags(m->ev_ring[slot], s, cudaEventRecordExternal));
+    } else {
+        CU(cudaEventRecord(m->ev_snap, s));
+        CU(cudaStreamWaitEvent(m->dl, m->ev_snap, 0));
+        CU(cudaMemcpyAsync(m->h_ring + (size_t)slot * map_t::REC_BYTES, rec, map_t::REC_BYTES,
+                           cudaMemcpyDeviceToHost, m->dl));
+        CU(cudaEventRecord(m->ev_ring[slot], m->dl));
+    }
     m->h_ctr_slot = slot;
     m->ring_frame[slot] = m->frame;
     m->ring_epoch[slot] = m->epoch;
@@ -1506,6 +1520,10 @@ struct map_batch_t {
     std::vector<cudaStream_t> mstream;   // MAP_BATCH_STREAMS: one stream per map
     std::vector<cudaEvent_t> mdone;      // ... and the event that joins it to the caller's stream
     cudaEvent_t ev_fork = nullptr;
+    // MAP_BATCH_STREAMS | MAP_BATCH_GRAPH: the executable graph of the streams step, updated in
+    // place from each step's capture (instantiated again when the step's shape changes)
+    cudaGraphExec_t sexec = nullptr;
+    long long s_steps = 0, s_instantiations = 0;
     unsigned long long fault_spin = 0;   // test hook: next launch lets CTA 0 leave at once
     BatchArgs args;                      // host staging of the kernel parameters
     std::string err;
@@ -1586,6 +1604,7 @@ extern "C" map_status map_batch_destroy(map_batch_t *b) {
         if (b->exec[c]) cudaGraphExecDestroy(b->exec[c]);
         if (b->graph[c]) cudaGraphDestroy(b->graph[c]);
     }
+    if (b->sexec) cudaGraphExecDestroy(b->sexec);
     if (b->ctl) cudaFree(b->ctl);
     if (b->out_dev) cudaFree(b->out_dev);
     if (b->out_host) cudaFreeHost(b->out_host);
@@ -1668,25 +1687,78 @@ extern "C" map_status map_batch_integrate(map_batch_t *b, const scan_desc *scans
     if (b->flags & MAP_BATCH_STREAMS) {
         for (int i = 0; i < n; ++i)
             if (scans[i].map != b->maps[i]) return bfail(b, MAP_ERR_ARG, "scans[i].map must be the batch's i-th map");
-        BCU(cudaEventRecord(b->ev_fork, s));
-        map_status first = MAP_OK;
-        for (int i = 0; i < n; ++i) {
-            const scan_desc &d = scans[i];
-            map_t *m = b->maps[i];
-            BCU(cudaStreamWaitEvent(b->mstream[i], b->ev_fork, 0));
-            map_status st_i = MAP_OK;
-            if (d.n > 0 && (!d.points_dev || ((d.labels_dev == nullptr) == (d.probs_dev == nullptr))))
-                st_i = fail(m, MAP_ERR_ARG, "need points and exactly one of labels / probs");
-            else
-                st_i = run_frame(m, &d.lidar, d.points_dev, d.labels_dev, d.probs_dev, d.n, d.T_world_lidar,
-                                 b->mstream[i]);
-            if (st_i != MAP_OK && first == MAP_OK) {
-                first = st_i;
-                b->err = m->err;
+        // With MAP_BATCH_GRAPH the step is captured on the batch's private stream and
+        // replayed as one graph launch on the caller's stream.
+        const bool graph = (b->flags & MAP_BATCH_GRAPH) != 0;
+        cudaStream_t origin = s;
+        if (graph) {
+            // uploads a capture cannot wait for (pixel-ray tables) are done and waited for first
+            for (int i = 0; i < n; ++i) {
+                map_t *m = b->maps[i];
+                if (m->cfg.distance_mode != 1 || scans[i].n <= 0) continue;
+                if (upload_pixel_rays(m, &scans[i].lidar) != MAP_OK) continue;   // refused again below
+                BCU(cudaEventSynchronize(m->ev_dir));
             }
-            // join every map's stream, also after an error (what was enqueued completes before the caller's stream goes on)
-            BCU(cudaEventRecord(b->mdone[i], b->mstream[i]));
-            BCU(cudaStreamWaitEvent(s, b->mdone[i], 0));
+            BCU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+            origin = b->cap;
+        }
+        map_status first = MAP_OK;
+        std::string cuda_err;
+        auto step = [&]() {
+            cudaError_t e = cudaEventRecord(b->ev_fork, origin);
+            for (int i = 0; i < n && e == cudaSuccess; ++i) {
+                const scan_desc &d = scans[i];
+                map_t *m = b->maps[i];
+                e = cudaStreamWaitEvent(b->mstream[i], b->ev_fork, 0);
+                if (e != cudaSuccess) break;
+                map_status st_i = MAP_OK;
+                if (d.n > 0 && (!d.points_dev || ((d.labels_dev == nullptr) == (d.probs_dev == nullptr))))
+                    st_i = fail(m, MAP_ERR_ARG, "need points and exactly one of labels / probs");
+                else
+                    st_i = run_frame(m, &d.lidar, d.points_dev, d.labels_dev, d.probs_dev, d.n, d.T_world_lidar,
+                                     b->mstream[i]);
+                if (st_i != MAP_OK && first == MAP_OK) {
+                    first = st_i;
+                    b->err = m->err;
+                }
+                // join every map's stream, also after an error (what was enqueued completes before the
+                // caller's stream goes on)
+                e = cudaEventRecord(b->mdone[i], b->mstream[i]);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, b->mdone[i], 0);
+            }
+            if (e != cudaSuccess) cuda_err = cudaGetErrorString(e);
+        };
+        step();
+        if (graph) {
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(b->cap, &g);
+            if (ec != cudaSuccess || !cuda_err.empty()) {
+                if (g) cudaGraphDestroy(g);
+                return bfail(b, MAP_ERR_CUDA, "streams step capture: " +
+                                                  (cuda_err.empty() ? std::string(cudaGetErrorString(ec)) : cuda_err));
+            }
+            bool updated = false;
+            if (b->sexec) {
+                cudaGraphExecUpdateResultInfo info;
+                updated = cudaGraphExecUpdate(b->sexec, g, &info) == cudaSuccess;
+                if (!updated) {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(b->sexec);
+                    b->sexec = nullptr;
+                }
+            }
+            cudaError_t el = cudaSuccess;
+            if (!updated) {
+                el = cudaGraphInstantiate(&b->sexec, g, 0);
+                b->s_instantiations++;
+            }
+            cudaGraphDestroy(g);
+            if (el == cudaSuccess) el = cudaGraphLaunch(b->sexec, s);
+            if (el != cudaSuccess)
+                return bfail(b, MAP_ERR_CUDA, std::string("streams step graph: ") + cudaGetErrorString(el));
+            b->s_steps++;
+        } else if (!cuda_err.empty()) {
+            return bfail(b, MAP_ERR_CUDA, "streams step: " + cuda_err);
         }
         BCU(cudaEventRecord(b->ev_done, s));
         b->pending = true;

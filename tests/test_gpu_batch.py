@@ -188,11 +188,13 @@ def test_batch_and_single_calls_on_one_map():
     mix.close()
 
 
-def test_streams_batch_matches_single_calls():
-    """MAP_BATCH_STREAMS: every map's scan runs on a stream of the batch, all maps concurrently.  The
-    maps (different voxel sizes, storage precisions and class inputs, ragged and empty scans, one in
-    the non-projective distance mode, which the batch kernel does not take) must equal maps fed
-    single integrate_scan calls, bit for bit, with the same counters (the download ring's too)."""
+@pytest.mark.parametrize("graph", [False, True], ids=["streams", "streams-graph"])
+def test_streams_batch_matches_single_calls(graph):
+    """MAP_BATCH_STREAMS: every map's scan runs on a stream of the batch, all maps concurrently (with
+    MAP_BATCH_GRAPH: the step captured and replayed as one graph launch).  The maps (different voxel
+    sizes, storage precisions and class inputs, ragged and empty scans, one in the non-projective
+    distance mode, which the batch kernel does not take) must equal maps fed single integrate_scan
+    calls, bit for bit, with the same counters (the download ring's too)."""
     p = _lib()
     w = synth.line16()
     frames = list(synth.sequence(w, 5))
@@ -206,7 +208,7 @@ def test_streams_batch_matches_single_calls():
         return out
     specs = SPECS + [(None, None, 0, "labels", None)]
     seq, con = maps(), maps()
-    b = p.map_batch_create([m.h for m in con], p.MAP_BATCH_STREAMS)
+    b = p.map_batch_create([m.h for m in con], p.MAP_BATCH_STREAMS | (p.MAP_BATCH_GRAPH if graph else 0))
     for k, f in enumerate(frames):
         ins = [_inputs(w, frames, s_, k, f) for s_ in specs]
         dev = [(_dev(pt), None if lb is None else _dev(lb), None if pr is None else _dev(pr)) for pt, lb, pr in ins]
