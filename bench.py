@@ -190,7 +190,7 @@ def algorithmic_bytes(st, n_points, H, W, C, s, nonproj=False):
     }
 
 
-def survey_model_bytes(st, n_points, H, W, C, s, probs):
+def scope_model_bytes(st, n_points, H, W, C, s, probs):
     """The frame's bytes by the byte model the method's scope table states, per scan:
     inputs (12 B per point, plus C x 4 B of probabilities or a 4 B label), the range image
     (8 B per pixel written and read), the TSDF (512 x 2s read per touched block, 2s written per
@@ -627,7 +627,7 @@ def run_ours(args, rank, world, local_rank):
             "algorithmic_bytes_per_launch": per_kernel[dom]["bytes_mean"]}
     frame_bytes = float(np.mean([sum(algorithmic_bytes(fs, n_points, L.H, L.W, C, s_bytes, nonproj).values())
                                  for fs in fstats]))
-    frame_bytes_survey = float(np.mean([survey_model_bytes(fs, n_points, L.H, L.W, C, s_bytes, bool(pr_d))
+    frame_bytes_scope = float(np.mean([scope_model_bytes(fs, n_points, L.H, L.W, C, s_bytes, bool(pr_d))
                                         for fs in fstats]))
     # --- end to end through the host-buffer entry point ----------------------
     # Every step: the scan's inputs from pinned host memory (H->D), the scan,
@@ -694,9 +694,9 @@ def run_ours(args, rank, world, local_rank):
                    "frame_algorithmic_bytes": frame_bytes,
                    "frame_gbs": frame_bytes / (total_ms / args.steps * 1e-3) / 1e9,
                    "frame_frac": frame_bytes / (total_ms / args.steps * 1e-3) / 1e9 / peak,
-                   "frame_bytes_survey_model": frame_bytes_survey,
-                   "frame_gbs_survey_model": frame_bytes_survey / (total_ms / args.steps * 1e-3) / 1e9,
-                   "frame_frac_survey_model": frame_bytes_survey / (total_ms / args.steps * 1e-3) / 1e9 / peak,
+                   "frame_bytes_scope_model": frame_bytes_scope,
+                   "frame_gbs_scope_model": frame_bytes_scope / (total_ms / args.steps * 1e-3) / 1e9,
+                   "frame_frac_scope_model": frame_bytes_scope / (total_ms / args.steps * 1e-3) / 1e9 / peak,
                    "touched_blocks_mean": float(fstats[:, 2].mean()),
                    "voxels_updated_mean": float(fstats[:, 4].mean()),
                    "voxels_semantic_mean": float(fstats[:, 5].mean()),
