@@ -211,13 +211,39 @@ __device__ __forceinline__ void points_item(const float *__restrict__ pts, const
                 pstamp[q] = r.stamp;
             }
         }
+        // Blocks not found at their home slot.  An empty home slot is claimed at once (its key
+        // was just read): the winner of that compare-and-swap has a new block, and its frame
+        // stamp exchange and pool slot allocation are issued together; a lost race to the
+        // same key leaves an existing block, to another key the full find-or-insert.
+        bool xchg[4], first[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
+            xchg[q] = false;
+            first[q] = false;
             if (own[q] && probe[q] != key[q]) {
-                // not at its home slot: the full find-or-insert
                 int is_new = 0;
-                h[q] = hash_insert(md, key[q], is_new);
                 pstamp[q] = -1;
+                if (probe[q] == EMPTY_KEY) {
+                    const uint64_t old = atomicCAS((unsigned long long *)&md.hs[h[q]].key,
+                                                   (unsigned long long)EMPTY_KEY, (unsigned long long)key[q]);
+                    if (old == EMPTY_KEY) {
+                        ++n_new;
+                        xchg[q] = true;
+                        first[q] = atomicExch(&md.hs[h[q]].stamp, sc.frame) != sc.frame;
+                        const unsigned long long s = atomicAdd(&md.st->pool_count, 1ull);
+                        if (s < (unsigned long long)md.max_blocks) {
+                            md.hs[h[q]].val = (int)s;
+                            md.slot_key[s] = key[q];
+                            md.slot_frame[s] = sc.frame;
+                        } else {
+                            md.hs[h[q]].val = -1;
+                            atomicOr(&md.st->err, ERR_POOL_FULL);
+                        }
+                        continue;
+                    }
+                    if (old == key[q]) continue;   // inserted meanwhile by another lane or warp
+                }
+                h[q] = hash_insert(md, key[q], is_new);
                 if (h[q] >= 0 && is_new) {
                     ++n_new;
                     const int sl = md.hs[h[q]].val;
@@ -230,10 +256,11 @@ __device__ __forceinline__ void points_item(const float *__restrict__ pts, const
         }
         // first touch in this scan: a stamp already at this frame was set by an exchange of this
         // scan (stamps change only by that exchange), so the exchange is needed only otherwise
-        bool first[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            first[q] = own[q] && h[q] >= 0 && pstamp[q] != sc.frame && atomicExch(&md.hs[h[q]].stamp, sc.frame) != sc.frame;
+            if (!xchg[q])
+                first[q] = own[q] && h[q] >= 0 && pstamp[q] != sc.frame &&
+                           atomicExch(&md.hs[h[q]].stamp, sc.frame) != sc.frame;
         const int cnt = (int)first[0] + (int)first[1] + (int)first[2] + (int)first[3];
         int tot;
         int off = warp_exclusive_scan(cnt, tot);
