@@ -266,6 +266,47 @@ def test_capacities_at_their_limits():
     short.close()
 
 
+def test_crowded_hash_table():
+    """The hash at the most crowded load the API allows (capacity: the smallest power of two at least
+    twice the pool): a pool of exactly the blocks k scans need, k chosen so that the load ends nearest
+    50 %.  Home slots then often hold another key (linear probing), neighbouring points of different
+    warps race to insert the same new block, and every scan must still match the oracle in lockstep:
+    the block set, the counters, every voxel, and no error bit."""
+    p = _lib()
+    w = synth.line16()
+    frames = list(synth.sequence(w, 10))
+    L = _lidar(p, w.lidar)
+    probe = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=1 << 14, hash_capacity=1 << 16,
+                           max_points=32768, max_pixels=32768, mesh_vertex_capacity=1 << 21,
+                           mesh_triangle_capacity=1 << 22)
+    need = []
+    for f in frames:
+        probe.integrate(L, _dev(f.points), f.T, labels=_dev(f.labels))
+        need.append(probe.stats()["total_blocks"])
+    probe.close()
+
+    def load(n):
+        cap = 1
+        while cap < 2 * n:
+            cap <<= 1
+        return n / cap
+    k = max(range(len(need)), key=lambda i: load(need[i]))
+    assert load(need[k]) > 0.4
+    gm = p.SemanticTSDF(w.voxel_size, w.truncation, w.n_classes, max_blocks=need[k], hash_capacity=2,
+                        max_points=32768, max_pixels=32768, mesh_vertex_capacity=1 << 21,
+                        mesh_triangle_capacity=1 << 22)
+    om = oracle.OracleMap(w.voxel_size, w.truncation, w.n_classes)
+    ls = Lockstep(gm, om)
+    for f in frames[:k + 1]:
+        s, _, _ = ls.scan(L, w.lidar, f.points, f.T, labels=f.labels)
+        assert s["error_bits"] == 0
+    assert gm.stats()["total_blocks"] == need[k]
+    np.testing.assert_array_equal(_sorted(gm.blocks()), _sorted(om.alloc_blocks()))
+    rep = compare_blocks(gm, om, om.alloc_blocks(), w.voxel_size, k + 1, w.n_classes)
+    assert rep["observed"] > 10000
+    gm.close()
+
+
 def test_azimuth_seam_and_elevation_edges():
     """Points on the azimuth seam behind the sensor (y = +0.0, -0.0 and a few ulps either side, where
     atan2 jumps from pi to -pi and the column index wraps from W to 0), and points just inside and
