@@ -730,9 +730,10 @@ __device__ __forceinline__ void tsdf_block_warp(const ScanConst &sc, const MapDe
 // and refresh the voxel's argmax label.  A voxel's classes form one record of
 // whole 16-byte chunks (FP32: 20 floats, FP16: 24 halves for 20 classes),
 // read and written with vector accesses, padding included.  The logarithms
-// and exponentials use the MUFU approximations (__logf, __expf): their error,
-// ~1e-6 per term, is two orders below the class log-probability tolerance of
-// the oracle comparison (1e-4 sqrt(K) + 1e-5 after K scans).
+// and exponentials use the MUFU approximations (base 2 in class_update,
+// __logf / __expf in the runtime-class-count path): their error, ~1e-6 per
+// term, is two orders below the class log-probability tolerance of the
+// oracle comparison (1e-4 sqrt(K) + 1e-5 after K scans).
 template <bool F16, int NC>
 __device__ __forceinline__ void load_record(const MapDev &md, long long vox, float *av) {
     if (F16) {
@@ -800,6 +801,21 @@ __device__ __forceinline__ void store_record(const MapDev &md, long long vox, co
 // label l.  Returns the most probable class of the values as they will be
 // stored (lowest class on ties).  Every path that updates classes (per-thread,
 // bulk-staged, batched) runs this same body, so all compute the same bits.
+// Base-2 logarithm and exponential by the MUFU approximations (PTX lg2.approx,
+// ex2.approx): the class update works in natural-log units and converts with
+// one multiply-add, ln x = ln 2 * log2 x and e^(a - m) = 2^(a log2 e - m log2 e).
+__device__ __forceinline__ float lg2_mufu(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_mufu(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+constexpr float LN2_F = 0.6931471805599453f, LOG2E_F = 1.4426950408889634f;
+
 template <bool F16, int NC>
 __device__ __forceinline__ int class_update(const ScanConst &sc, float *av, const float *q, int l) {
     if (q) {
@@ -807,14 +823,14 @@ __device__ __forceinline__ int class_update(const ScanConst &sc, float *av, cons
 #pragma unroll
             for (int cc = 0; cc < NC; cc += 4) {
                 const float4 v = *reinterpret_cast<const float4 *>(q + cc);
-                av[cc] = __fadd_rn(av[cc], __logf(fmaxf(v.x, sc.lik_floor)));
-                av[cc + 1] = __fadd_rn(av[cc + 1], __logf(fmaxf(v.y, sc.lik_floor)));
-                av[cc + 2] = __fadd_rn(av[cc + 2], __logf(fmaxf(v.z, sc.lik_floor)));
-                av[cc + 3] = __fadd_rn(av[cc + 3], __logf(fmaxf(v.w, sc.lik_floor)));
+                av[cc] = __fmaf_rn(lg2_mufu(fmaxf(v.x, sc.lik_floor)), LN2_F, av[cc]);
+                av[cc + 1] = __fmaf_rn(lg2_mufu(fmaxf(v.y, sc.lik_floor)), LN2_F, av[cc + 1]);
+                av[cc + 2] = __fmaf_rn(lg2_mufu(fmaxf(v.z, sc.lik_floor)), LN2_F, av[cc + 2]);
+                av[cc + 3] = __fmaf_rn(lg2_mufu(fmaxf(v.w, sc.lik_floor)), LN2_F, av[cc + 3]);
             }
         } else {
 #pragma unroll
-            for (int cc = 0; cc < NC; ++cc) av[cc] = __fadd_rn(av[cc], __logf(fmaxf(q[cc], sc.lik_floor)));
+            for (int cc = 0; cc < NC; ++cc) av[cc] = __fmaf_rn(lg2_mufu(fmaxf(q[cc], sc.lik_floor)), LN2_F, av[cc]);
         }
     } else {
 #pragma unroll
@@ -824,9 +840,10 @@ __device__ __forceinline__ int class_update(const ScanConst &sc, float *av, cons
 #pragma unroll
     for (int cc = 0; cc < NC; ++cc) m = fmaxf(m, av[cc]);
     float ssum = 0.f;
+    const float mb = __fmul_rn(m, LOG2E_F);
 #pragma unroll
-    for (int cc = 0; cc < NC; ++cc) ssum = __fadd_rn(ssum, __expf(__fsub_rn(av[cc], m)));
-    const float lse = __fadd_rn(m, __logf(ssum));
+    for (int cc = 0; cc < NC; ++cc) ssum = __fadd_rn(ssum, ex2_mufu(__fmaf_rn(av[cc], LOG2E_F, -mb)));
+    const float lse = __fmaf_rn(lg2_mufu(ssum), LN2_F, m);
     int best = 0;
     float bv = -INFINITY;
 #pragma unroll
