@@ -1067,21 +1067,32 @@ __device__ __forceinline__ int cube_case(const uint32_t *rowm, int a) {
                  (((rowm[r + 10] >> sh) & 3u) << 6));
 }
 
-// Vertex number of cube edge ce (axis ce >> 2, offsets ce & 1 and (ce >> 1) & 1
-// along the next two axes, cyclically) of the cube anchored at (ax, ay, az).
-__device__ __forceinline__ int cube_edge_vertex(const MeshWarpSmem &W, int ce, int ax, int ay, int az) {
-    const int axis = ce >> 2, o1 = ce & 1, o2 = (ce >> 1) & 1;
-    int rw, bit;
-    if (axis == 0) {
-        rw = ay + o1 + 9 * (az + o2);
-        bit = ax;
-    } else if (axis == 1) {
-        rw = ay + 9 * (az + o1);
-        bit = 8 + ax + o2;
-    } else {
-        rw = ay + o2 + 9 * az;
-        bit = 17 + ax + o1;
+// Cube edge ce (axis ce >> 2, offsets ce & 1 and (ce >> 1) & 1 along the next
+// two axes, cyclically) lies on voxel row (ay + dy) + 9 (az + dz) of its cube
+// and has bit b + ax of that row's edge mask: an x edge (dy, dz) = (o1, o2),
+// b = 0; a y edge (0, o1), b = 8 + o2; a z edge (o2, 0), b = 17 + o1.  The
+// 12 edges' (dy + 9 dz, b) in 9-bit fields, six to a word, so that a lookup
+// is a shift and a mask rather than a branch on the axis (the lanes of a warp
+// look up different edges).
+constexpr unsigned long long cube_edge_table(int half) {
+    unsigned long long t = 0;
+    for (int k = 0; k < 6; ++k) {
+        const int ce = 6 * half + k, axis = ce >> 2, o1 = ce & 1, o2 = (ce >> 1) & 1;
+        const int dy = axis == 0 ? o1 : (axis == 2 ? o2 : 0);
+        const int dz = axis == 0 ? o2 : (axis == 1 ? o1 : 0);
+        const int b = axis == 0 ? 0 : (axis == 1 ? 8 + o2 : 17 + o1);
+        t |= (unsigned long long)((dy + 9 * dz) | (b << 4)) << (9 * k);
     }
+    return t;
+}
+constexpr unsigned long long CUBE_EDGE_LO = cube_edge_table(0), CUBE_EDGE_HI = cube_edge_table(1);
+static_assert(CUBE_EDGE_LO == 0x11280050240200ull && CUBE_EDGE_HI == 0x24311904413290ull, "cube edge table");
+
+// Vertex number of cube edge ce of the cube anchored at (ax, ay, az).
+__device__ __forceinline__ int cube_edge_vertex(const MeshWarpSmem &W, int ce, int ax, int ay, int az) {
+    const bool hi = ce >= 6;
+    const int f = (int)(((hi ? CUBE_EDGE_HI : CUBE_EDGE_LO) >> (9 * (hi ? ce - 6 : ce))) & 0x1ffu);
+    const int rw = ay + 9 * az + (f & 15), bit = ax + (f >> 4);
     return W.woff[rw] + __popc(W.ew[rw] & ((1u << bit) - 1u));
 }
 
