@@ -414,7 +414,10 @@ extern "C" map_status map_create(const map_config *cfg_in, map_t **out) {
     integrate_kernel_attributes();
     mesh_kernel_attributes();
     m->grid_integrate = sms * integrate_blocks_per_sm(c.storage, c.n_classes, c.distance_mode);
-    m->grid_semantic = 4 * sms * semantic_blocks_per_sm(c.storage, c.n_classes);
+    // two waves of the class update's resident CTAs (measured best beside the re-meshing: one
+    // wave leaves the list's tail to too few warps, more waves queue CTAs that only start as
+    // earlier ones retire)
+    m->grid_semantic = 2 * sms * semantic_blocks_per_sm(c.storage, c.n_classes);
     // 4 re-meshing CTAs per SM (the padded staging admits no more)
     m->grid_mesh = sms * std::min(4, mesh_blocks_per_sm());
     e = cudaStreamSynchronize(s);
