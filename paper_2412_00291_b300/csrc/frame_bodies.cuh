@@ -816,9 +816,19 @@ __device__ __forceinline__ float ex2_mufu(float x) {
 }
 constexpr float LN2_F = 0.6931471805599453f, LOG2E_F = 1.4426950408889634f;
 
-template <bool F16, int NC>
+template <bool F16, int NC, bool QLOG2 = false>
 __device__ __forceinline__ int class_update(const ScanConst &sc, float *av, const float *q, int l) {
-    if (q) {
+    if (QLOG2 && q) {
+        // q already holds log2 max(q_c, lik_floor) (16-byte aligned)
+#pragma unroll
+        for (int cc = 0; cc < NC; cc += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(q + cc);
+            av[cc] = __fmaf_rn(v.x, LN2_F, av[cc]);
+            av[cc + 1] = __fmaf_rn(v.y, LN2_F, av[cc + 1]);
+            av[cc + 2] = __fmaf_rn(v.z, LN2_F, av[cc + 2]);
+            av[cc + 3] = __fmaf_rn(v.w, LN2_F, av[cc + 3]);
+        }
+    } else if (q) {
         if (NC % 4 == 0 && sc.probs_vec4) {
 #pragma unroll
             for (int cc = 0; cc < NC; cc += 4) {
@@ -931,9 +941,13 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // differ), R = 32 x RB bytes of the warp's shared memory, qrow = the lane's
 // probability row (shared or global memory, 16-byte aligned), or null for a
 // hard label.  Any cp.async copies the warp issued before are waited for too.
-template <bool F16>
+// With QLOG2 the warp's staged probability rows, qlog[0, nlog), are turned into
+// log2 max(q, lik_floor) once the copies have landed (each row once, however
+// many lanes share it), and qrow points at the lane's row there.
+template <bool F16, bool QLOG2 = false>
 __device__ __forceinline__ void class_update_warp(const ScanConst &sc, const MapDev &md, bool act, int2 ent,
-                                                  unsigned char *R, const float *qrow) {
+                                                  unsigned char *R, const float *qrow, float *qlog = nullptr,
+                                                  int nlog = 0) {
     using S = SemStage<F16>;
     const int lane = threadIdx.x & 31;
     unsigned char *mine = nullptr;
@@ -950,6 +964,10 @@ __device__ __forceinline__ void class_update_warp(const ScanConst &sc, const Map
     }
     cp_async_wait_all();
     __syncwarp();
+    if (QLOG2 && nlog > 0) {
+        for (int t = lane; t < nlog; t += 32) qlog[t] = lg2_mufu(fmaxf(qlog[t], sc.lik_floor));
+        __syncwarp();
+    }
     if (act) {
         float av[SEM_NC];
         unsigned char *rr = R + lane * S::RB;
@@ -978,7 +996,7 @@ __device__ __forceinline__ void class_update_warp(const ScanConst &sc, const Map
                 av[4 * j + 3] = v.w;
             }
         }
-        const int best = class_update<F16, SEM_NC>(sc, av, qrow, qrow ? 0 : sc.labels[ent.y]);
+        const int best = class_update<F16, SEM_NC, QLOG2>(sc, av, qrow, qrow ? 0 : sc.labels[ent.y]);
         // the new record in place, padding zero
         if (F16) {
             uint4 *q = reinterpret_cast<uint4 *>(rr);

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(32 * SEM_WARPS, 8) k_semantic_coop(ScanConst s
     using S = SemStage<F16>;
     __shared__ __align__(16) unsigned char s_rec[SEM_WARPS][32 * S::RB];
     __shared__ __align__(16) float s_q[SEM_WARPS][32 * SEM_NC];
+    __shared__ int s_pt[SEM_WARPS][32];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *R = s_rec[wid];
     float *Q = s_q[wid];
@@ -92,16 +93,28 @@ __global__ void __launch_bounds__(32 * SEM_WARPS, 8) k_semantic_coop(ScanConst s
         const int nact = (int)min(32ull, ns - base);
         const bool act = lane < nact;
         const int2 ent = act ? fd.sem_list[base + lane] : make_int2(0, 0);
+        const float *qrow = nullptr;
+        int nlog = 0;
         if (probs) {
-            // the winners' probability rows, chunk by chunk like the records
-#pragma unroll
-            for (int j = 0; j < SEM_NC / 4; ++j) {
-                const int k = 32 * j + lane, r = k / (SEM_NC / 4), c = k - r * (SEM_NC / 4);
-                const int idx = __shfl_sync(0xffffffffu, ent.y, r);
-                if (r < nact) cp_async16(Q + r * SEM_NC + 4 * c, sc.probs + (long long)idx * SEM_NC + 4 * c);
+            // the distinct winner points' probability rows, chunk by chunk like the records,
+            // each once however many of the round's voxels share it (one lane of each group
+            // of lanes with the same point lists it)
+            const unsigned grp = __match_any_sync(0xffffffffu, act ? ent.y : -1 - lane);
+            const int lead = __ffs(grp) - 1;
+            const bool leader = act && lead == lane;
+            const unsigned lm = __ballot_sync(0xffffffffu, leader);
+            const int nu = __popc(lm);
+            const int row = __popc(lm & ((1u << lead) - 1u));
+            if (leader) s_pt[wid][row] = ent.y;
+            __syncwarp();
+            for (int k = lane; k < nu * (SEM_NC / 4); k += 32) {
+                const int u = k / (SEM_NC / 4), c = k - u * (SEM_NC / 4);
+                cp_async16(Q + u * SEM_NC + 4 * c, sc.probs + (long long)s_pt[wid][u] * SEM_NC + 4 * c);
             }
+            qrow = Q + row * SEM_NC;
+            nlog = nu * SEM_NC;
         }
-        class_update_warp<F16>(sc, md, act, ent, R, probs ? Q + lane * SEM_NC : nullptr);
+        class_update_warp<F16, true>(sc, md, act, ent, R, qrow, Q, nlog);
     }
 }
 
