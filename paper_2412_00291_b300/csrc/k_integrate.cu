@@ -2,7 +2,9 @@
 // update (Sec. III-C.3, Eq. bayesian_filter).  k_tsdf: one warp per half of
 // a touched block (256 voxels; grid-stride over the device-side list U_k,
 // 8 warps per CTA); it lists the voxels whose class distribution must change,
-// and k_semantic streams that list, one voxel per thread.
+// and the class update works that list off: k_semantic_coop (20 classes)
+// warp by warp through shared memory, k_semantic (any class count) one voxel
+// per thread.
 //
 // Per voxel v of block b:
 //   x_l   = R^T (nu v - t)            (its direction picks the pixel)
@@ -72,9 +74,11 @@ __global__ void __launch_bounds__(256) k_semantic(ScanConst sc, MapDev md, Frame
 // The class update of the listed voxels with 20 classes, staged warp by warp
 // through shared memory (class_update_warp in frame_bodies.cuh): per warp 32
 // list entries, their class records and the winners' probability rows copied
-// as consecutive 16-byte chunks (cp.async) rather than one voxel per lane.
-// Four warps per CTA (20 KB of staging in FP32): one such CTA fits on an SM
-// beside the four re-meshing CTAs that run at the same time.
+// as consecutive 16-byte chunks (cp.async) rather than one voxel per lane; a
+// row shared by several of the 32 voxels is copied, and turned into log2
+// likelihoods, once.  Four warps per CTA (20 KB of staging in FP32): two
+// such CTAs fit on an SM beside the four re-meshing CTAs that run at the same
+// time.
 constexpr int SEM_WARPS = 4;
 template <bool F16>
 __global__ void __launch_bounds__(32 * SEM_WARPS, 8) k_semantic_coop(ScanConst sc, MapDev md, FrameDev fd) {
