@@ -32,6 +32,8 @@ struct BatchArgs {
     int n;
     int fault_skip_cta0;     // test hook: CTA 0 leaves at once, the first barrier times out
     int sem_staged;          // class update: 0 one voxel per thread, 1 / 2 warp-staged (FP32 / FP16 records)
+    int sem_rows_once;       // warp-staged: each (map, point) probability row staged and taken to log2
+                             // once per warp round (every map with the same likelihood floor)
     unsigned long long spin_limit;   // polls before a barrier wait gives up (0: default)
     BatchCtl *ctl;
     BatchState *out;

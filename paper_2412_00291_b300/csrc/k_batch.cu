@@ -72,6 +72,7 @@ struct BatchSmem {
     } u;
     long long pre[BATCH_MAX + 1];
     long long pre2[BATCH_MAX + 1];
+    uint8_t lead[WARPS][32];   // warp-staged class update: the lane that lists each staged row
 };
 
 template <int WARPS, int VPT>
@@ -173,8 +174,10 @@ __global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch(const __grid_c
         // warp-staged: 32 consecutive entries of the maps' concatenated lists per warp, the records
         // staged in the warp's re-meshing slot (free until this warp meshes); probability rows
         // read by each lane
-        static_assert(sizeof(MeshWarpSmem) >= 32 * SemStage<false>::RB, "staging fits the warp's slot");
+        static_assert(sizeof(MeshWarpSmem) >= 32 * SemStage<false>::RB + 32 * SEM_NC * 4,
+                      "records and rows fit the warp's slot");
         unsigned char *R = reinterpret_cast<unsigned char *>(&S.u.mesh.w[wid]);
+        float *Q = reinterpret_cast<float *>(R + 32 * SemStage<false>::RB);
         for (long long base = gwarp * 32; base < S.pre[n]; base += nwarps * 32) {
             const long long e = base + lane;
             const bool act = e < S.pre[n];
@@ -182,8 +185,33 @@ __global__ void __launch_bounds__(32 * WARPS, 32 / WARPS) k_batch(const __grid_c
             const BatchItem &it = a.it[i];
             const int2 ent = act ? it.fd.sem_list[e - S.pre[i]] : make_int2(0, 0);
             const float *qrow = act && it.sc.has_probs ? it.sc.probs + (long long)ent.y * SEM_NC : nullptr;
-            if (a.sem_staged == 2) class_update_warp<true>(it.sc, it.md, act, ent, R, qrow);
-            else class_update_warp<false>(it.sc, it.md, act, ent, R, qrow);
+            if (a.sem_rows_once) {
+                // the round's distinct (map, point) rows, staged once each (one lane of each group
+                // lists it) and taken to log2 once
+                const bool pr = qrow != nullptr;
+                const unsigned long long kv = pr ? ((unsigned long long)i << 32) | (unsigned)ent.y : ~0ull - lane;
+                const unsigned grp = __match_any_sync(0xffffffffu, kv);
+                const int lead = __ffs(grp) - 1;
+                const bool leader = pr && lead == lane;
+                const unsigned lm = __ballot_sync(0xffffffffu, leader);
+                const int nu = __popc(lm);
+                const int row = __popc(lm & ((1u << lead) - 1u));
+                if (leader) S.lead[wid][row] = (uint8_t)lane;
+                __syncwarp();
+                const unsigned long long rp = reinterpret_cast<unsigned long long>(qrow);
+#pragma unroll
+                for (int j = 0; j < SEM_NC / 4; ++j) {
+                    const int k = 32 * j + lane, u = k / (SEM_NC / 4), c = k - u * (SEM_NC / 4);
+                    const unsigned long long p = __shfl_sync(0xffffffffu, rp, S.lead[wid][u < nu ? u : 0]);
+                    if (u < nu) cp_async16(Q + u * SEM_NC + 4 * c, reinterpret_cast<const float *>(p) + 4 * c);
+                }
+                qrow = pr ? Q + row * SEM_NC : nullptr;
+                if (a.sem_staged == 2) class_update_warp<true, true>(it.sc, it.md, act, ent, R, qrow, Q, nu * SEM_NC);
+                else class_update_warp<false, true>(it.sc, it.md, act, ent, R, qrow, Q, nu * SEM_NC);
+            } else {
+                if (a.sem_staged == 2) class_update_warp<true>(it.sc, it.md, act, ent, R, qrow);
+                else class_update_warp<false>(it.sc, it.md, act, ent, R, qrow);
+            }
         }
     }
     for (long long base = tid; !a.sem_staged && base < S.pre[n]; base += nthreads * VPT) {

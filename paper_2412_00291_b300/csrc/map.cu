@@ -1804,6 +1804,9 @@ extern "C" map_status map_batch_integrate(map_batch_t *b, const scan_desc *scans
             staged = it.sc.C == 20 && it.md.storage == args.it[0].md.storage && (!it.sc.has_probs || it.sc.probs_vec4);
         }
         args.sem_staged = staged && n > 0 ? (args.it[0].md.storage == 0 ? 1 : 2) : 0;
+        bool one_floor = true;
+        for (int i = 1; i < n; ++i) one_floor = one_floor && args.it[i].sc.lik_floor == args.it[0].sc.lik_floor;
+        args.sem_rows_once = args.sem_staged && one_floor ? 1 : 0;
     }
     args.n = n;
     args.ctl = b->ctl;
